@@ -1,0 +1,51 @@
+"""The oracle pins are strong enough: each planted mistake must fail them.
+
+Every mutation is applied to a temporary copy of the oracle (on the CPU);
+the pin tests then run against that copy in a subprocess and must fail.
+"""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+MUTATIONS = {
+    "drop the father's weight": (
+        "rows.append(Bw[tree.father[t]] @ side.E_ext[t].T)", "pass"),
+    "drop the ancestor weight": (
+        "rows.append(B_prev @ side.E_ext[t].T)", "pass"),
+    "weights without sqrt(#T_t)": (
+        "om = math.sqrt(tree.subtree_count[t]) / nrm if nrm > 0 else 0.0",
+        "om = 1.0 / nrm if nrm > 0 else 0.0"),
+    "threshold eps instead of eps/2": (
+        "thr = (0.5 * eps) ** 2\n    tail = 0.0", "thr = (1.0 * eps) ** 2\n    tail = 0.0"),
+    "no transfer commit": (
+        "Fnew[side.root] = Rt[side.root] @ side.E_ext[side.root]",
+        "Fnew[side.root] = side.basis.transfer[side.root]"),
+    "transposed column factor": ("S_new[b] = Rt @ Sx @ Rs.T", "S_new[b] = Rt @ Sx @ Rs"),
+    "other side's R-factor ignored": ("rows.append(om * (Ro @ Sx))", "rows.append(om * Sx)"),
+    "nearfield not updated": ("N_new[b] = Z.N[b] + At @ Bs.T", "N_new[b] = Z.N[b]"),
+    "leaf SVD without weights": ("M = Vh @ Bw[t].T", "M = Vh"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pins_catch_mutation(name, tmp_path):
+    before, after = MUTATIONS[name]
+    shutil.copytree(os.path.join(ROOT, "oracle"), tmp_path / "oracle")
+    path = tmp_path / "oracle" / "update.py"
+    src = path.read_text()
+    assert before in src
+    path.write_text(src.replace(before, after))
+    env = dict(os.environ)
+    env["PYTHONPATH"] = os.pathsep.join([str(tmp_path), ROOT, os.path.join(ROOT, "tests")])
+    code = ("import sys, pytest; sys.path.insert(0, %r); import oracle; "
+            "assert oracle.__file__.startswith(%r); "
+            "sys.exit(pytest.main(['-q', '-x', '-p', 'no:cacheprovider', %r]))"
+            % (str(tmp_path), str(tmp_path), os.path.join(ROOT, "tests", "test_oracle_update.py")))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=str(tmp_path),
+                       env=env, timeout=600)
+    assert r.returncode != 0, r.stdout[-2000:]
