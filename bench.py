@@ -1,0 +1,336 @@
+#!/usr/bin/env python3
+"""Benchmark of the isolated batched local low-rank update on one GB300.
+
+Workload: 4096 rank-8 local low-rank updates Z|_{t0 x s0} <- trunc_eps(
+Z|_{t0 x s0} + A B^*) (Section 5 of arXiv:1402.5056) on an H^2 matrix over
+the 256 x 256 grid of cell centres (n = 65,536, leaf size 32, eta = 2),
+nested orthonormal bases of rank 16, couplings N(0,1)/16, target blocks
+drawn uniformly from the admissible leaves, A and B N(0,1), eps = 1e-8,
+float64.  Isolated mode: every update reads the same base matrix and writes
+its own result.  A step is one execution of the whole batch.
+
+Output: one JSON line (rank 0).  ``--impl reference`` times the CPU oracle
+instead (bounded samples of the same workload on the host cores).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "H²-LR setup s & low-rank updates/s, mixed vs FP64 GPU at equal ε; % roofline"
+UNIT = "updates/s"
+WORK = dict(N=256, leaf=32, eta=2.0, k=16, u=8, eps=1e-8, count=4096, seed=synth.SEED_BASE + 1)
+WORKLOAD_NAME = ("isolated H2 low-rank updates: 4096 rank-8 updates, 256x256-point H2 matrix "
+                 "(n=65536, leaf 32, eta 2, k=16), eps=1e-8, float64")
+# Float64 FMA throughput of one GB300 (TFLOP/s), from the DFMA probe recorded
+# with the design notes (profiles/fp64_peak.txt); the roofline denominator of
+# this ALU-bound path.
+FP64_PEAK_TFLOPS = 1.25
+FP64_PEAK_SOURCE = "nominal GB300 FP64 (1.25 TFLOP/s); measured probe pending"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def lib_workload(b, ctx, rank_offset: int = 0):
+    """Library-side H^2 matrix, update blocks and factors of the workload."""
+    w = WORK
+    pts = synth.grid_points_2d(w["N"])
+    Z = b.h2_matrix_create(ctx, pts, w["leaf"], w["eta"], 0.0, w["k"])
+    tc = b.h2_tree_clusters(Z)
+    tb = b.h2_tree_blocks(Z)
+    nc = len(tc["offset"])
+    leaves = [(t, int(tc["size"][t])) for t in range(nc) if tc["son0"][t] < 0]
+    pairs = [(int(tc["son0"][t]), int(tc["son1"][t])) for t in range(nc) if tc["son0"][t] >= 0]
+    adm = np.flatnonzero(tb["kind"] == 1)
+    near = np.flatnonzero(tb["kind"] == 2)
+    st = synth.streams(w["seed"] + rank_offset)
+    V = synth.nested_orthonormal_bases(st["bases"], leaves, pairs, nc, w["k"])
+    W = synth.nested_orthonormal_bases(st["bases"], leaves, pairs, nc, w["k"])
+    S = synth.gaussian_couplings(st["couplings"], len(adm), w["k"], 1.0 / w["k"])
+    Nf = synth.gaussian_nearfield(st["couplings"], [(int(tc["size"][tb["row"][c]]), int(tc["size"][tb["col"][c]]))
+                                                    for c in near], 1.0 / 16)
+    blocks = [int(x) for x in synth.choose_blocks(st["blocks"], adm, w["count"])]
+    A, B = synth.update_factors(st["ab"], [int(tc["size"][tb["row"][c]]) for c in blocks],
+                                [int(tc["size"][tb["col"][c]]) for c in blocks], w["u"])
+    if ctx is not None:
+        b.h2_set_basis(ctx, Z, 0, *V)
+        b.h2_set_basis(ctx, Z, 1, *W)
+        b.h2_set_couplings(ctx, Z, S)
+        b.h2_set_nearfield(ctx, Z, Nf)
+    return Z, blocks, A, B
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during timing."""
+
+    FIELDS = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id=None):
+        self.bus_id = (bus_id or "").lower()
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        rows = [r for r in self.rows if len(r) >= 10]
+        if self.bus_id:
+            mine = [r for r in rows if self.bus_id.endswith(r[1].lower()[-12:]) or r[1].lower().endswith(self.bus_id[-12:])]
+            rows = mine or rows
+        if not rows:
+            return None
+        idx = rows[0][0]
+        rows = [r for r in rows if r[0] == idx]
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[2]) for r in rows if num(r[2]) is not None]
+        mx = [num(r[3]) for r in rows if num(r[3]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[6 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def oracle_sample(seconds: float, start: int = 0, max_updates: int | None = None):
+    """Time the CPU oracle on the first updates of the workload until
+    ``seconds`` have passed; returns (updates done, wall s, cpu s, level mix)."""
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from oracle.update import local_update
+    from problems import draw_updates, oracle_problem
+    w = WORK
+    Zo, st, _ = oracle_problem(w["N"], w["k"], w["seed"], w["leaf"], w["eta"])
+    blocks, A, B = draw_updates(Zo, st, w["count"], w["u"])
+    done = 0
+    t0, c0 = time.perf_counter(), time.process_time()
+    j = start
+    while True:
+        local_update(Zo, blocks[j % len(blocks)], A[j % len(blocks)], B[j % len(blocks)], w["eps"])
+        done += 1
+        j += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or (max_updates and done >= max_updates):
+            break
+    return done, time.perf_counter() - t0, time.process_time() - c0, Zo, blocks
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return 0
+    per_step = []
+    done_tot = 0
+    cpu_tot = 0.0
+    wall_tot = 0.0
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from oracle.update import local_update
+    from problems import draw_updates, oracle_problem
+    w = WORK
+    Zo, st, _ = oracle_problem(w["N"], w["k"], w["seed"], w["leaf"], w["eta"])
+    blocks, A, B = draw_updates(Zo, st, w["count"], w["u"])
+    sample = args.ref_sample
+    j = 0
+    for step in range(args.warmup + args.steps):
+        t0, c0 = time.perf_counter(), time.process_time()
+        for _ in range(sample):
+            local_update(Zo, blocks[j % len(blocks)], A[j % len(blocks)], B[j % len(blocks)], w["eps"])
+            j += 1
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            per_step.append(dt)
+            done_tot += sample
+            wall_tot += dt
+            cpu_tot += time.process_time() - c0
+    value = done_tot / wall_tot
+    cores = max(1, round(cpu_tot / wall_tot))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall_tot / len(per_step),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, "step": "%d updates of the batch per step (bounded sample)" % sample,
+                       "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d updates per step x %d steps, in batch order" % (sample, args.steps)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-sample", type=int, default=24)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank)
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_1402_5056_gb300 import binding as b
+
+    stream = torch.cuda.current_stream()
+    ctx = b.h2_ctx_create(torch.cuda.current_device(), stream.cuda_stream)
+    Z, blocks, A, B = lib_workload(b, ctx, rank_offset=rank)
+    w = WORK
+    P = b.h2_batch_create(ctx, Z, blocks, w["u"])
+    lenA, lenB = b.h2_batch_factor_sizes(P)
+    Acat, Bcat = np.zeros(lenA), np.zeros(lenB)
+    for j in range(len(blocks)):
+        ra, oa, rb, ob = b.h2_batch_factor_layout(P, j)
+        Acat[oa:oa + ra * w["u"]] = A[j].ravel(order="F")
+        Bcat[ob:ob + rb * w["u"]] = B[j].ravel(order="F")
+    dA = torch.from_numpy(Acat).cuda()
+    dB = torch.from_numpy(Bcat).cuda()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    b.h2_batch_set_timing(P, True)
+    for _ in range(args.warmup):
+        b.h2_batch_execute(ctx, P, dA.data_ptr(), dB.data_ptr(), w["eps"])
+    b.h2_ctx_synchronize(ctx)
+
+    nph = len(b.PHASES)
+    phase_ms = [0.0] * nph
+    step_ms = []
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    sampler = ClockSampler(getattr(props, "pci_bus_id", None) if hasattr(props, "pci_bus_id") else None)
+    sampler.start()
+    time.sleep(0.5)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for s in range(args.steps):
+        flush.fill_(s)                       # write 512 MB (> L2) between steps
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.h2_batch_execute(ctx, P, dA.data_ptr(), dB.data_ptr(), w["eps"])
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        for ph in range(nph):
+            phase_ms[ph] += b.h2_batch_phase_stats(ctx, P, ph, flops=False)["ms"]
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    b.h2_ctx_synchronize(ctx)
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * len(blocks) / (ms_per_step / 1e3)
+    stats = b.h2_batch_stats(ctx, P)
+    phases = {}
+    for ph, name in enumerate(b.PHASES):
+        ps = b.h2_batch_phase_stats(ctx, P, ph)
+        phases[name] = {"launches": ps["launches"], "ms": phase_ms[ph] / args.steps,
+                        "gflop": ps["flops"] / 1e9,
+                        "tflops": (ps["flops"] / (phase_ms[ph] / args.steps * 1e-3) / 1e12) if phase_ms[ph] > 0 else None}
+    dom = max(phases, key=lambda k: phases[k]["ms"])
+    ach = phases[dom]["tflops"]
+    roof = {"bound": "alu", "kernel": "k_%s" % dom, "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": (ach / FP64_PEAK_TFLOPS) if ach else None, "traffic": None,
+            "peak_source": FP64_PEAK_SOURCE,
+            "launch_ms": phases[dom]["ms"] / max(1, phases[dom]["launches"])}
+
+    # end to end through the C ABI from pinned host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        pA = torch.from_numpy(Acat).pin_memory()
+        pB = torch.from_numpy(Bcat).pin_memory()
+        res = torch.empty(b.h2_batch_result_size(P), dtype=torch.float64).pin_memory()
+        b.h2_batch_execute_host(ctx, P, pA.numpy(), pB.numpy(), w["eps"], res.numpy())
+        ts = []
+        for _ in range(args.e2e_steps):
+            flush.fill_(7)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            b.h2_batch_execute_host(ctx, P, pA.numpy(), pB.numpy(), w["eps"], res.numpy())
+            ts.append(time.perf_counter() - t0)
+        e2e = {"value": len(blocks) / (sum(ts) / len(ts)), "unit": UNIT,
+               "h2d_bytes_per_step": 8 * (lenA + lenB), "d2h_bytes_per_step": 8 * int(res.numel())}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        done, wall, cpu_s, _, _ = oracle_sample(args.cpu_seconds)
+        cpu = {"value": done / wall, "unit": UNIT, "cores": max(1, round(cpu_s / wall)), "kind": "oracle",
+               "sample": "first %d updates of the 4096-update batch (%.1f s wall)" % (done, wall)}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, "mode": "isolated (each update reads the same base matrix)",
+                       "l2": "512 MB buffer written between timed steps",
+                       "cluster_tasks": stats["cluster_tasks"], "block_tasks": stats["block_tasks"]},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": stats["launches"] * args.steps,
+            "clocks": clocks, "phases": phases, "gflop_per_step": stats["flops"] / 1e9}
+    if rank == 0:
+        print(json.dumps(line))
+    b.h2_batch_free(P)
+    b.h2_matrix_free(Z)
+    b.h2_ctx_destroy(ctx)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,206 @@
+/*
+ * h2gb -- H^2-matrix local low-rank updates on one NVIDIA GB300 (sm_103a).
+ *
+ * C ABI of libh2gb.so.  Method: Boerm & Reimer, "Efficient arithmetic
+ * operations for rank-structured matrices based on hierarchical low-rank
+ * updates" (arXiv:1402.5056).  Section references below are to that paper.
+ *
+ * Conventions (every entry point):
+ *  - No exceptions cross the ABI; every call returns h2_status.  A non-OK
+ *    status leaves a message retrievable with h2_last_error(ctx).
+ *  - Argument errors (null pointer, id out of range, negative size, ...)
+ *    return H2_EINVAL and modify nothing.
+ *  - Host pointers are read or written synchronously before the call
+ *    returns.  Device pointers are used asynchronously on the context's
+ *    stream; the caller keeps ownership of every pointer it passes.
+ *  - Matrices are column-major float64 unless stated otherwise.
+ *  - Rows of a cluster basis and of update factors follow the TREE order of
+ *    the cluster's index set (h2_tree_permutation maps tree positions to
+ *    the caller's original point numbers).
+ *  - Cluster bases must be orthonormal (V_t^* V_t = I), as Section 4
+ *    assumes for the recompression; bases produced by this library are.
+ *  - A context is not thread-safe; use one per host thread.
+ */
+#ifndef H2GB_H
+#define H2GB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  H2_OK = 0,
+  H2_EINVAL = 1,       /* invalid argument                                   */
+  H2_ENOMEM = 2,       /* device or host allocation failed                   */
+  H2_ECUDA = 3,        /* a CUDA runtime call failed                         */
+  H2_ETIMEOUT = 4,     /* a bounded device wait ran out                      */
+  H2_EDEVICE = 5,      /* a kernel reported an internal limit (see message)  */
+  H2_EINTERNAL = 6     /* unexpected internal error                          */
+} h2_status;
+
+typedef struct h2_ctx h2_ctx;         /* device + stream + device error word  */
+typedef struct h2_matrix h2_matrix;   /* trees + device storage of one H^2 matrix */
+typedef struct h2_batch h2_batch;     /* plan and outputs of a batch of updates */
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a
+ * cudaStream_t to run on (NULL = the legacy default stream); the caller
+ * keeps ownership of the stream. */
+h2_status h2_ctx_create(int device, void* cuda_stream, h2_ctx** out);
+void h2_ctx_destroy(h2_ctx* ctx);
+/* Message of the last non-OK status on this context (never NULL). */
+const char* h2_last_error(const h2_ctx* ctx);
+/* Block until the context's stream is idle; returns H2_EDEVICE if any
+ * kernel since the last check reported an internal limit, H2_ECUDA on a
+ * CUDA error. */
+h2_status h2_ctx_synchronize(h2_ctx* ctx);
+
+/* ------------------------------------------------------------- structure */
+
+/* Build the cluster tree and block tree (Section 2, Defs. "Cluster tree" and
+ * "Block tree") for n points of dimension dim (host, row-major n x dim) and
+ * allocate device storage for an H^2 matrix with row and column bases of
+ * rank 0.
+ *  - cluster tree: geometric bisection of the points' bounding box along its
+ *    longest axis (ties: lowest axis) at the midpoint while a cluster has
+ *    more than leaf_size points; coordinates below the midpoint go to the
+ *    first son; clusters numbered in depth-first preorder, root 0;
+ *  - admissibility of (t,s): dist > 0 and max(diam t, diam s) <= eta * dist
+ *    with Euclidean box diameters/distance, boxes padded by `pad` per side;
+ *  - block tree: a block is subdivided while inadmissible and both clusters
+ *    have sons; blocks numbered in depth-first preorder, sons ordered
+ *    (t1,s1),(t1,s2),(t2,s1),(t2,s2).
+ * `kcap` (1..32) is the rank capacity of the storage; it grows on demand. */
+h2_status h2_matrix_create(h2_ctx* ctx, const double* points, int64_t n, int dim,
+                           int leaf_size, double eta, double pad, int kcap, h2_matrix** out);
+void h2_matrix_free(h2_matrix* Z);
+/* Deep copy (trees shared by value, device storage copied). */
+h2_status h2_matrix_clone(h2_ctx* ctx, const h2_matrix* Z, h2_matrix** out);
+
+/* Counts of the structure. Any output pointer may be NULL. */
+h2_status h2_tree_sizes(const h2_matrix* Z, int64_t* n, int64_t* n_clusters, int64_t* n_blocks,
+                        int64_t* n_admissible, int64_t* n_inadmissible, int* depth);
+/* Per-cluster arrays (length n_clusters, host): offset and size of the
+ * cluster's index range in tree order, father (-1 for the root), sons (-1
+ * for leaves), level (root 0), #T_t (clusters in its subtree). */
+h2_status h2_tree_clusters(const h2_matrix* Z, int64_t* offset, int64_t* size, int32_t* father,
+                           int32_t* son0, int32_t* son1, int32_t* level, int32_t* subtree);
+/* Per-block arrays (length n_blocks, host): row cluster, column cluster,
+ * kind (0 subdivided, 1 admissible leaf, 2 inadmissible leaf), father. */
+h2_status h2_tree_blocks(const h2_matrix* Z, int32_t* row, int32_t* col, int32_t* kind,
+                         int32_t* father);
+/* perm[i] = original point number of tree position i (host, length n). */
+h2_status h2_tree_permutation(const h2_matrix* Z, int64_t* perm);
+
+/* ------------------------------------------------------------------ data */
+
+/* Canonical host layouts (column-major per matrix, concatenated):
+ *   basis  : ranks[n_clusters]; leaf_data = V_t (size_t x k_t) for every
+ *            leaf in cluster order; transfer_data = E_t (k_t x k_father) for
+ *            every non-root cluster in cluster order (Eq. (nested)).
+ *   couplings: S_b (k_t x l_s) for every admissible leaf in block order
+ *            (Eq. (vsw)).
+ *   nearfield: G|_b (size_t x size_s) for every inadmissible leaf in block
+ *            order.
+ * side 0 = row basis V, side 1 = column basis W.  Setting a basis with new
+ * ranks invalidates the couplings (set them again afterwards). */
+h2_status h2_set_basis(h2_ctx* ctx, h2_matrix* Z, int side, const int32_t* ranks,
+                       const double* leaf_data, const double* transfer_data);
+h2_status h2_set_couplings(h2_ctx* ctx, h2_matrix* Z, const double* data);
+h2_status h2_set_nearfield(h2_ctx* ctx, h2_matrix* Z, const double* data);
+/* Element counts of the canonical layouts for the current ranks. */
+h2_status h2_data_sizes(const h2_matrix* Z, int side, int64_t* leaf_len, int64_t* transfer_len,
+                        int64_t* coupling_len, int64_t* nearfield_len);
+h2_status h2_get_ranks(const h2_matrix* Z, int side, int32_t* ranks);
+h2_status h2_get_basis(h2_ctx* ctx, const h2_matrix* Z, int side, double* leaf_data,
+                       double* transfer_data);
+h2_status h2_get_couplings(h2_ctx* ctx, const h2_matrix* Z, double* data);
+h2_status h2_get_nearfield(h2_ctx* ctx, const h2_matrix* Z, double* data);
+/* Single matrices (host outputs, column-major, leading dimension = rows):
+ * leaf basis of a leaf cluster (size_t x k_t), transfer of a non-root
+ * cluster (k_t x k_father), coupling of an admissible block (k_t x l_s). */
+h2_status h2_get_leaf(h2_ctx* ctx, const h2_matrix* Z, int side, int64_t cluster, double* out);
+h2_status h2_get_transfer(h2_ctx* ctx, const h2_matrix* Z, int side, int64_t cluster, double* out);
+h2_status h2_get_coupling(h2_ctx* ctx, const h2_matrix* Z, int64_t block, double* out);
+
+/* --------------------------------------------------------------- updates */
+
+/* Plan a batch of `count` local low-rank updates
+ *     Z|_{t0 x s0} <- trunc_eps(Z|_{t0 x s0} + A_j B_j^*)      (Section 5)
+ * on the blocks blocks[j] (any block-tree node, host array) with update
+ * rank u (1..31, k_t + u <= 32 for every cluster touched).  The plan holds
+ * the level-by-level task lists (clusters of the subtrees T_{t0}, T_{s0},
+ * every admissible block whose row lies in T_{t0} or whose column lies in
+ * T_{s0}) and the device workspace.  It reads the structure and ranks of Z
+ * at creation; Z must not change ranks before the plan is executed. */
+h2_status h2_batch_create(h2_ctx* ctx, const h2_matrix* Z, int64_t count, const int64_t* blocks,
+                          int u, h2_batch** out);
+void h2_batch_free(h2_batch* batch);
+/* Rows of update j's factors: A_j is rows_A x u, B_j is rows_B x u, stored
+ * at element offsets off_A, off_B of the concatenated factor arrays. */
+h2_status h2_batch_factor_layout(const h2_batch* batch, int64_t j, int64_t* rows_A,
+                                 int64_t* off_A, int64_t* rows_B, int64_t* off_B);
+h2_status h2_batch_factor_sizes(const h2_batch* batch, int64_t* len_A, int64_t* len_B);
+
+/* Execute the batch in ISOLATED mode: every update reads the same Z (the one
+ * given at planning) and writes its own result (new ranks, bases, transfer
+ * matrices and couplings) into the batch's output buffers; Z is not changed.
+ * A and B are DEVICE pointers to the concatenated factors (layout from
+ * h2_batch_factor_layout).  Truncation: block-relative accuracy eps
+ * (Sections 4 and 7), every admissible block keeps
+ * ||Z~|_b - Z_new|_b||_F <= eps/sqrt(2) ||Z~|_b||_F.  Asynchronous. */
+h2_status h2_batch_execute(h2_ctx* ctx, h2_batch* batch, const double* A, const double* B,
+                           double eps);
+/* Same, from HOST factor arrays: copies them in, executes, and copies the
+ * updates' new couplings and bases back to the host buffer `result` (length
+ * from h2_batch_result_size, layout internal), then synchronizes. */
+h2_status h2_batch_execute_host(h2_ctx* ctx, h2_batch* batch, const double* A_host,
+                                const double* B_host, double eps, double* result);
+h2_status h2_batch_result_size(const h2_batch* batch, int64_t* len);
+/* Commit update j's result into dst (Section 5: replace the bases in the
+ * subtrees, the transfer matrices E_{t0}, E_{s0} and every affected
+ * coupling; add A|_t B|_s^* to the inadmissible leaves inside the block --
+ * this last part reads A, B again, so pass the same device factors).  dst
+ * must have the structure of the planned matrix and, outside the touched
+ * subtrees, its ranks; its storage grows if a new rank exceeds capacity. */
+h2_status h2_batch_apply(h2_ctx* ctx, const h2_batch* batch, int64_t j, const double* A,
+                         const double* B, h2_matrix* dst);
+/* Statistics of the last execution (host, synchronizes): number of cluster
+ * tasks, block tasks, kernel launches, and the algorithmic float64 flop
+ * count of the executed path (rotations of the one-sided Jacobi counted as
+ * executed). */
+h2_status h2_batch_stats(h2_ctx* ctx, const h2_batch* batch, int64_t* n_cluster_tasks,
+                         int64_t* n_block_tasks, int64_t* n_launches, double* flops);
+
+/* Phases of an execution, for h2_batch_phase_stats. */
+typedef enum {
+  H2_PHASE_BASE_WEIGHTS = 0,  /* weights of the unchanged matrix (all clusters)   */
+  H2_PHASE_RFACTOR = 1,       /* step 2: basis R-factors                           */
+  H2_PHASE_NORMS = 2,         /* ||Z~|_b||_F of the blocks inside the update       */
+  H2_PHASE_WEIGHTS = 3,       /* step 3: weight matrices B~_t                      */
+  H2_PHASE_TRUNCATE = 4,      /* step 4: SVD truncation, new bases                 */
+  H2_PHASE_REPROJECT = 5,     /* step 5: reprojection of the couplings             */
+  H2_PHASE_COUNT = 6
+} h2_phase;
+
+/* Enable (on != 0) or disable CUDA-event timing of each phase in later
+ * executions of this batch (events on the context's stream). */
+h2_status h2_batch_set_timing(h2_batch* batch, int on);
+/* Launches, device time in ms (last execution, only with timing enabled,
+ * else -1) and algorithmic float64 flops of one phase.  Synchronizes. */
+h2_status h2_batch_phase_stats(h2_ctx* ctx, const h2_batch* batch, int phase, int64_t* launches,
+                               double* ms, double* flops);
+
+/* One update applied to Z in place (sequential semantics; Section 5).
+ * A (rows of block's row cluster x u, ld lda) and B (rows of column cluster
+ * x u, ld ldb) are DEVICE pointers. */
+h2_status h2_lowrank_update(h2_ctx* ctx, h2_matrix* Z, int64_t block, int u, const double* A,
+                            int64_t lda, const double* B, int64_t ldb, double eps);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* H2GB_H */

@@ -51,7 +51,9 @@ class ClusterTree:
         self.perm = np.concatenate([self.idx[t] for t in range(self.n_clusters) if not self.sons[t]])
         pos = np.empty(self.n, dtype=np.int64)
         pos[self.perm] = np.arange(self.n)
-        self.offset = [int(pos[self.idx[t][0]]) if len(self.idx[t]) else 0 for t in range(self.n_clusters)]
+        # a label is a contiguous range of the tree order; its offset is the
+        # smallest tree position of its indices
+        self.offset = [int(pos[self.idx[t]].min()) if len(self.idx[t]) else 0 for t in range(self.n_clusters)]
         self.size = [len(self.idx[t]) for t in range(self.n_clusters)]
         # number of clusters in the subtree rooted at t (#T_t)
         self.subtree_count = [0] * self.n_clusters

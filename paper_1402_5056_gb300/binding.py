@@ -1,0 +1,324 @@
+"""Thin ctypes binding of libh2gb (argument marshalling only).
+
+Every function keeps the name of its C entry point in ``include/h2gb.h``.
+Host arrays are numpy arrays; device pointers are plain integers (for
+example ``torch.Tensor.data_ptr()``).  A non-OK status raises ``H2Error``
+with the library's message.  Importing this module fails loudly when the
+compiled library is missing: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libh2gb.so")
+
+STATUS = {0: "H2_OK", 1: "H2_EINVAL", 2: "H2_ENOMEM", 3: "H2_ECUDA", 4: "H2_ETIMEOUT",
+          5: "H2_EDEVICE", 6: "H2_EINTERNAL"}
+
+EXPORTS = [
+    "h2_ctx_create", "h2_ctx_destroy", "h2_last_error", "h2_ctx_synchronize",
+    "h2_matrix_create", "h2_matrix_free", "h2_matrix_clone",
+    "h2_tree_sizes", "h2_tree_clusters", "h2_tree_blocks", "h2_tree_permutation",
+    "h2_set_basis", "h2_set_couplings", "h2_set_nearfield", "h2_data_sizes", "h2_get_ranks",
+    "h2_get_basis", "h2_get_couplings", "h2_get_nearfield", "h2_get_leaf", "h2_get_transfer",
+    "h2_get_coupling",
+    "h2_batch_create", "h2_batch_free", "h2_batch_factor_layout", "h2_batch_factor_sizes",
+    "h2_batch_execute", "h2_batch_execute_host", "h2_batch_result_size", "h2_batch_apply",
+    "h2_batch_stats", "h2_batch_set_timing", "h2_batch_phase_stats", "h2_lowrank_update",
+]
+
+PHASES = ("base_weights", "rfactor", "norms", "weights", "truncate", "reproject")
+
+
+class H2Error(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__("%s: %s" % (STATUS.get(status, status), message))
+        self.status = status
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libh2gb.so is not built (run paper_1402_5056_gb300.build.build()); "
+                      "there is no CPU fallback")
+_lib = C.CDLL(LIB_PATH)
+
+_p = C.c_void_p
+_i64 = C.c_int64
+_i32 = C.c_int32
+_int = C.c_int
+_dbl = C.c_double
+_pp = C.POINTER(C.c_void_p)
+
+
+def _sig(name, restype, *args):
+    f = getattr(_lib, name)
+    f.restype = restype
+    f.argtypes = list(args)
+    return f
+
+
+_sig("h2_ctx_create", _int, _int, _p, _pp)
+_sig("h2_ctx_destroy", None, _p)
+_sig("h2_last_error", C.c_char_p, _p)
+_sig("h2_ctx_synchronize", _int, _p)
+_sig("h2_matrix_create", _int, _p, _p, _i64, _int, _int, _dbl, _dbl, _int, _pp)
+_sig("h2_matrix_free", None, _p)
+_sig("h2_matrix_clone", _int, _p, _p, _pp)
+_sig("h2_tree_sizes", _int, _p, _p, _p, _p, _p, _p, _p)
+_sig("h2_tree_clusters", _int, _p, _p, _p, _p, _p, _p, _p, _p)
+_sig("h2_tree_blocks", _int, _p, _p, _p, _p, _p)
+_sig("h2_tree_permutation", _int, _p, _p)
+_sig("h2_set_basis", _int, _p, _p, _int, _p, _p, _p)
+_sig("h2_set_couplings", _int, _p, _p, _p)
+_sig("h2_set_nearfield", _int, _p, _p, _p)
+_sig("h2_data_sizes", _int, _p, _int, _p, _p, _p, _p)
+_sig("h2_get_ranks", _int, _p, _int, _p)
+_sig("h2_get_basis", _int, _p, _p, _int, _p, _p)
+_sig("h2_get_couplings", _int, _p, _p, _p)
+_sig("h2_get_nearfield", _int, _p, _p, _p)
+_sig("h2_get_leaf", _int, _p, _p, _int, _i64, _p)
+_sig("h2_get_transfer", _int, _p, _p, _int, _i64, _p)
+_sig("h2_get_coupling", _int, _p, _p, _i64, _p)
+_sig("h2_batch_create", _int, _p, _p, _i64, _p, _int, _pp)
+_sig("h2_batch_free", None, _p)
+_sig("h2_batch_factor_layout", _int, _p, _i64, _p, _p, _p, _p)
+_sig("h2_batch_factor_sizes", _int, _p, _p, _p)
+_sig("h2_batch_execute", _int, _p, _p, _p, _p, _dbl)
+_sig("h2_batch_execute_host", _int, _p, _p, _p, _p, _dbl, _p)
+_sig("h2_batch_result_size", _int, _p, _p)
+_sig("h2_batch_apply", _int, _p, _p, _i64, _p, _p, _p)
+_sig("h2_batch_stats", _int, _p, _p, _p, _p, _p, _p)
+_sig("h2_batch_set_timing", _int, _p, _int)
+_sig("h2_batch_phase_stats", _int, _p, _p, _int, _p, _p, _p)
+_sig("h2_lowrank_update", _int, _p, _p, _i64, _int, _p, _i64, _p, _i64, _dbl)
+
+
+def _check(status: int, ctx=None):
+    if status != 0:
+        msg = _lib.h2_last_error(ctx)
+        raise H2Error(status, msg.decode() if msg else "")
+
+
+def _ptr(a):
+    """Host pointer of a contiguous numpy array (or None)."""
+    if a is None:
+        return None
+    assert isinstance(a, np.ndarray) and (a.flags.c_contiguous or a.flags.f_contiguous)
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64).ravel(order="A"))
+
+
+# ------------------------------------------------------------------ context
+def h2_ctx_create(device: int = 0, stream: int | None = None):
+    out = C.c_void_p()
+    st = _lib.h2_ctx_create(int(device), C.c_void_p(stream) if stream else None, C.byref(out))
+    _check(st)
+    return out.value
+
+
+def h2_ctx_destroy(ctx):
+    _lib.h2_ctx_destroy(ctx)
+
+
+def h2_last_error(ctx) -> str:
+    m = _lib.h2_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def h2_ctx_synchronize(ctx):
+    _check(_lib.h2_ctx_synchronize(ctx), ctx)
+
+
+# ------------------------------------------------------------------- matrix
+def h2_matrix_create(ctx, points, leaf_size: int, eta: float, pad: float = 0.0, kcap: int = 16):
+    """``ctx`` may be None: structure only (trees, no device storage)."""
+    pts = np.ascontiguousarray(points, dtype=np.float64)
+    n, dim = pts.shape
+    out = C.c_void_p()
+    _check(_lib.h2_matrix_create(ctx, _ptr(pts), n, dim, int(leaf_size), float(eta), float(pad),
+                                 int(kcap), C.byref(out)), ctx)
+    return out.value
+
+
+def h2_matrix_free(Z):
+    _lib.h2_matrix_free(Z)
+
+
+def h2_matrix_clone(ctx, Z):
+    out = C.c_void_p()
+    _check(_lib.h2_matrix_clone(ctx, Z, C.byref(out)), ctx)
+    return out.value
+
+
+def h2_tree_sizes(Z) -> dict:
+    v = [C.c_int64() for _ in range(5)]
+    d = C.c_int()
+    _check(_lib.h2_tree_sizes(Z, *[C.byref(x) for x in v], C.byref(d)))
+    return dict(n=v[0].value, n_clusters=v[1].value, n_blocks=v[2].value, n_admissible=v[3].value,
+                n_inadmissible=v[4].value, depth=d.value)
+
+
+def h2_tree_clusters(Z) -> dict:
+    nc = h2_tree_sizes(Z)["n_clusters"]
+    off = np.zeros(nc, np.int64)
+    size = np.zeros(nc, np.int64)
+    a32 = [np.zeros(nc, np.int32) for _ in range(5)]
+    _check(_lib.h2_tree_clusters(Z, _ptr(off), _ptr(size), *[_ptr(a) for a in a32]))
+    return dict(offset=off, size=size, father=a32[0], son0=a32[1], son1=a32[2], level=a32[3],
+                subtree=a32[4])
+
+
+def h2_tree_blocks(Z) -> dict:
+    nb = h2_tree_sizes(Z)["n_blocks"]
+    a = [np.zeros(nb, np.int32) for _ in range(4)]
+    _check(_lib.h2_tree_blocks(Z, *[_ptr(x) for x in a]))
+    return dict(row=a[0], col=a[1], kind=a[2], father=a[3])
+
+
+def h2_tree_permutation(Z) -> np.ndarray:
+    n = h2_tree_sizes(Z)["n"]
+    p = np.zeros(n, np.int64)
+    _check(_lib.h2_tree_permutation(Z, _ptr(p)))
+    return p
+
+
+# --------------------------------------------------------------------- data
+def h2_set_basis(ctx, Z, side: int, ranks, leaf_data, transfer_data):
+    r = np.ascontiguousarray(ranks, dtype=np.int32)
+    _check(_lib.h2_set_basis(ctx, Z, int(side), _ptr(r), _ptr(_f64(leaf_data)), _ptr(_f64(transfer_data))), ctx)
+
+
+def h2_set_couplings(ctx, Z, data):
+    _check(_lib.h2_set_couplings(ctx, Z, _ptr(_f64(data))), ctx)
+
+
+def h2_set_nearfield(ctx, Z, data):
+    _check(_lib.h2_set_nearfield(ctx, Z, _ptr(_f64(data))), ctx)
+
+
+def h2_data_sizes(Z, side: int) -> dict:
+    v = [C.c_int64() for _ in range(4)]
+    _check(_lib.h2_data_sizes(Z, int(side), *[C.byref(x) for x in v]))
+    return dict(leaf=v[0].value, transfer=v[1].value, coupling=v[2].value, nearfield=v[3].value)
+
+
+def h2_get_ranks(Z, side: int) -> np.ndarray:
+    r = np.zeros(h2_tree_sizes(Z)["n_clusters"], np.int32)
+    _check(_lib.h2_get_ranks(Z, int(side), _ptr(r)))
+    return r
+
+
+def h2_get_basis(ctx, Z, side: int):
+    s = h2_data_sizes(Z, side)
+    leaf = np.zeros(s["leaf"])
+    tr = np.zeros(s["transfer"])
+    _check(_lib.h2_get_basis(ctx, Z, int(side), _ptr(leaf), _ptr(tr)), ctx)
+    return h2_get_ranks(Z, side), leaf, tr
+
+
+def h2_get_couplings(ctx, Z) -> np.ndarray:
+    out = np.zeros(h2_data_sizes(Z, 0)["coupling"])
+    _check(_lib.h2_get_couplings(ctx, Z, _ptr(out)), ctx)
+    return out
+
+
+def h2_get_nearfield(ctx, Z) -> np.ndarray:
+    out = np.zeros(h2_data_sizes(Z, 0)["nearfield"])
+    _check(_lib.h2_get_nearfield(ctx, Z, _ptr(out)), ctx)
+    return out
+
+
+def h2_get_leaf(ctx, Z, side: int, cluster: int, rows: int, rank: int) -> np.ndarray:
+    out = np.zeros(rows * rank)
+    _check(_lib.h2_get_leaf(ctx, Z, int(side), int(cluster), _ptr(out)), ctx)
+    return out.reshape((rows, rank), order="F")
+
+
+def h2_get_transfer(ctx, Z, side: int, cluster: int, rows: int, cols: int) -> np.ndarray:
+    out = np.zeros(rows * cols)
+    _check(_lib.h2_get_transfer(ctx, Z, int(side), int(cluster), _ptr(out)), ctx)
+    return out.reshape((rows, cols), order="F")
+
+
+def h2_get_coupling(ctx, Z, block: int, rows: int, cols: int) -> np.ndarray:
+    out = np.zeros(rows * cols)
+    _check(_lib.h2_get_coupling(ctx, Z, int(block), _ptr(out)), ctx)
+    return out.reshape((rows, cols), order="F")
+
+
+# ------------------------------------------------------------------ updates
+def h2_batch_create(ctx, Z, blocks, u: int):
+    """``ctx`` may be None: host-only plan (no device buffers)."""
+    b = np.ascontiguousarray(blocks, dtype=np.int64)
+    out = C.c_void_p()
+    _check(_lib.h2_batch_create(ctx, Z, len(b), _ptr(b), int(u), C.byref(out)), ctx)
+    return out.value
+
+
+def h2_batch_free(P):
+    _lib.h2_batch_free(P)
+
+
+def h2_batch_factor_layout(P, j: int):
+    v = [C.c_int64() for _ in range(4)]
+    _check(_lib.h2_batch_factor_layout(P, int(j), *[C.byref(x) for x in v]))
+    return tuple(x.value for x in v)   # rows_A, off_A, rows_B, off_B
+
+
+def h2_batch_factor_sizes(P):
+    a, b = C.c_int64(), C.c_int64()
+    _check(_lib.h2_batch_factor_sizes(P, C.byref(a), C.byref(b)))
+    return a.value, b.value
+
+
+def h2_batch_execute(ctx, P, A_dev: int, B_dev: int, eps: float):
+    _check(_lib.h2_batch_execute(ctx, P, C.c_void_p(A_dev), C.c_void_p(B_dev), float(eps)), ctx)
+
+
+def h2_batch_result_size(P) -> int:
+    n = C.c_int64()
+    _check(_lib.h2_batch_result_size(P, C.byref(n)))
+    return n.value
+
+
+def h2_batch_execute_host(ctx, P, A_host, B_host, eps: float, result=None):
+    if result is None:
+        result = np.zeros(h2_batch_result_size(P))
+    _check(_lib.h2_batch_execute_host(ctx, P, _ptr(_f64(A_host)), _ptr(_f64(B_host)), float(eps),
+                                      _ptr(result)), ctx)
+    return result
+
+
+def h2_batch_apply(ctx, P, j: int, A_dev: int, B_dev: int, dst):
+    _check(_lib.h2_batch_apply(ctx, P, int(j), C.c_void_p(A_dev), C.c_void_p(B_dev), dst), ctx)
+
+
+def h2_batch_stats(ctx, P, flops: bool = True) -> dict:
+    a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+    f = C.c_double()
+    _check(_lib.h2_batch_stats(ctx, P, C.byref(a), C.byref(b), C.byref(c), C.byref(f) if flops else None), ctx)
+    return dict(cluster_tasks=a.value, block_tasks=b.value, launches=c.value, flops=f.value if flops else None)
+
+
+def h2_batch_set_timing(P, on: bool):
+    _check(_lib.h2_batch_set_timing(P, 1 if on else 0))
+
+
+def h2_batch_phase_stats(ctx, P, phase: int, flops: bool = True) -> dict:
+    n = C.c_int64()
+    ms = C.c_double()
+    f = C.c_double()
+    _check(_lib.h2_batch_phase_stats(ctx, P, int(phase), C.byref(n), C.byref(ms),
+                                     C.byref(f) if flops else None), ctx)
+    return dict(launches=n.value, ms=ms.value, flops=f.value if flops else None)
+
+
+def h2_lowrank_update(ctx, Z, block: int, u: int, A_dev: int, lda: int, B_dev: int, ldb: int, eps: float):
+    _check(_lib.h2_lowrank_update(ctx, Z, int(block), int(u), C.c_void_p(A_dev), int(lda),
+                                  C.c_void_p(B_dev), int(ldb), float(eps)), ctx)

@@ -1,0 +1,1438 @@
+// C ABI of libh2gb: contexts, H^2 storage, the batch planner and the
+// execution of local low-rank updates (Sections 2, 4 and 5).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <unordered_map>
+
+#include "h2_internal.h"
+#include "update_kernels.h"
+
+using namespace h2;
+
+// ===================================================================== misc
+namespace {
+
+thread_local std::string g_null_ctx_error;
+
+template <typename T>
+T* dalloc(size_t count) {
+  if (count == 0) return nullptr;
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    throw Error(H2_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  return static_cast<T*>(p);
+}
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+template <typename T>
+T* upload(const std::vector<T>& v, cudaStream_t st) {
+  T* d = dalloc<T>(v.size());
+  if (!v.empty()) {
+    H2_CUDA(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+    H2_CUDA(cudaStreamSynchronize(st));
+  }
+  return d;
+}
+
+template <typename F>
+h2_status guard(h2_ctx* ctx, F&& f) {
+  try {
+    f();
+    return H2_OK;
+  } catch (const Error& e) {
+    if (ctx) ctx->last_error = e.what(); else g_null_ctx_error = e.what();
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    if (ctx) ctx->last_error = "host allocation failed"; else g_null_ctx_error = "host allocation failed";
+    return H2_ENOMEM;
+  } catch (const std::exception& e) {
+    if (ctx) ctx->last_error = e.what(); else g_null_ctx_error = e.what();
+    return H2_EINTERNAL;
+  }
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) H2_CUDA(cudaSetDevice(dev));
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+const ClusterTree& tree_of(const h2_matrix* Z, int side) { return side == 0 ? Z->rows : Z->cols; }
+DeviceBasis& basis_of(h2_matrix* Z, int side) { return side == 0 ? Z->V : Z->W; }
+const DeviceBasis& basis_of(const h2_matrix* Z, int side) { return side == 0 ? Z->V : Z->W; }
+
+bool has_storage(const h2_matrix* Z) { return Z->d_S != nullptr || Z->blocks.adm.empty(); }
+
+void free_basis(DeviceBasis& b) {
+  dfree(b.d_rank);
+  dfree(b.d_leaf);
+  dfree(b.d_transfer);
+  dfree(b.d_leaf_off);
+}
+
+// Allocate basis storage for capacity kcap, zero-filled.
+void alloc_basis(const ClusterTree& ct, int kcap, DeviceBasis& b, cudaStream_t st) {
+  const int32_t nc = ct.count();
+  b.leaf_off.assign(nc, -1);
+  int64_t tot = 0;
+  for (int32_t c = 0; c < nc; ++c)
+    if (ct.leaf(c)) {
+      b.leaf_off[c] = tot;
+      tot += ct.size[c] * kcap;
+    }
+  b.d_leaf = dalloc<double>(tot);
+  b.d_transfer = dalloc<double>((size_t)nc * kcap * kcap);
+  H2_CUDA(cudaMemsetAsync(b.d_leaf, 0, tot * sizeof(double), st));
+  H2_CUDA(cudaMemsetAsync(b.d_transfer, 0, (size_t)nc * kcap * kcap * sizeof(double), st));
+  b.d_leaf_off = upload(b.leaf_off, st);
+  if (b.rank.size() != (size_t)nc) b.rank.assign(nc, 0);
+  b.d_rank = upload(b.rank, st);
+}
+
+void sync_ranks(DeviceBasis& b, cudaStream_t st) {
+  H2_CUDA(cudaMemcpyAsync(b.d_rank, b.rank.data(), b.rank.size() * sizeof(int32_t),
+                          cudaMemcpyHostToDevice, st));
+}
+
+MatView view_of(const h2_matrix* Z) {
+  MatView M;
+  for (int s = 0; s < 2; ++s) {
+    const DeviceBasis& b = basis_of(Z, s);
+    M.leaf[s] = b.d_leaf;
+    M.transfer[s] = b.d_transfer;
+    M.leaf_off[s] = b.d_leaf_off;
+    M.rank[s] = b.d_rank;
+  }
+  M.father[0] = Z->d_father_r;
+  M.father[1] = Z->d_father_c;
+  M.subtree[0] = Z->d_subtree_r;
+  M.subtree[1] = Z->d_subtree_c;
+  M.S = Z->d_S;
+  M.kcap = Z->kcap;
+  return M;
+}
+
+// Re-layout the storage of Z for a larger rank capacity (device copies).
+void grow_kcap(h2_ctx* ctx, h2_matrix* Z, int kcap) {
+  if (kcap <= Z->kcap) return;
+  H2_REQUIRE(kcap <= kMaxCols, "rank capacity above 32");
+  cudaStream_t st = ctx->stream;
+  std::vector<CopyDesc> cd;
+  DeviceBasis nb[2];
+  for (int s = 0; s < 2; ++s) {
+    const ClusterTree& ct = tree_of(Z, s);
+    DeviceBasis& ob = basis_of(Z, s);
+    nb[s].rank = ob.rank;
+    alloc_basis(ct, kcap, nb[s], st);
+    for (int32_t c = 0; c < ct.count(); ++c) {
+      if (ct.leaf(c) && ob.rank[c] > 0)
+        cd.push_back({ob.d_leaf + ob.leaf_off[c], nb[s].d_leaf + nb[s].leaf_off[c], (int)ct.size[c],
+                      ob.rank[c], (int)ct.size[c], (int)ct.size[c]});
+      if (ct.father[c] >= 0 && ob.rank[c] > 0 && ob.rank[ct.father[c]] > 0)
+        cd.push_back({ob.d_transfer + (size_t)c * Z->kcap * Z->kcap,
+                      nb[s].d_transfer + (size_t)c * kcap * kcap, ob.rank[c], ob.rank[ct.father[c]],
+                      Z->kcap, kcap});
+    }
+  }
+  const size_t nadm = Z->blocks.adm.size();
+  double* nS = dalloc<double>(nadm * kcap * kcap);
+  H2_CUDA(cudaMemsetAsync(nS, 0, nadm * kcap * kcap * sizeof(double), st));
+  for (size_t a = 0; a < nadm; ++a) {
+    const int32_t b = Z->blocks.adm[a];
+    const int kt = Z->V.rank[Z->blocks.row[b]], ls = Z->W.rank[Z->blocks.col[b]];
+    if (kt > 0 && ls > 0)
+      cd.push_back({Z->d_S + a * Z->kcap * Z->kcap, nS + a * kcap * kcap, kt, ls, Z->kcap, kcap});
+  }
+  CopyDesc* dcd = upload(cd, st);
+  launch_copy(dcd, (int)cd.size(), st);
+  H2_CUDA(cudaGetLastError());
+  H2_CUDA(cudaStreamSynchronize(st));
+  dfree(dcd);
+  for (int s = 0; s < 2; ++s) {
+    free_basis(basis_of(Z, s));
+    basis_of(Z, s) = nb[s];
+  }
+  dfree(Z->d_S);
+  Z->d_S = nS;
+  Z->kcap = kcap;
+}
+
+}  // namespace
+
+// =================================================================== context
+extern "C" h2_status h2_ctx_create(int device, void* cuda_stream, h2_ctx** out) {
+  if (!out) return H2_EINVAL;
+  *out = nullptr;
+  auto ctx = std::make_unique<h2_ctx>();
+  h2_status s = guard(nullptr, [&] {
+    int n = 0;
+    H2_CUDA(cudaGetDeviceCount(&n));
+    H2_REQUIRE(device >= 0 && device < n, "h2_ctx_create: no such device");
+    ctx->device = device;
+    DeviceGuard g(device);
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    ctx->d_error = dalloc<int>(1);
+    H2_CUDA(cudaMemset(ctx->d_error, 0, sizeof(int)));
+  });
+  if (s == H2_OK) *out = ctx.release();
+  return s;
+}
+
+extern "C" void h2_ctx_destroy(h2_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->d_error) cudaFree(ctx->d_error);
+  delete ctx;
+}
+
+extern "C" const char* h2_last_error(const h2_ctx* ctx) {
+  return ctx ? ctx->last_error.c_str() : g_null_ctx_error.c_str();
+}
+
+static void check_device_error(h2_ctx* ctx) {
+  int e = 0;
+  H2_CUDA(cudaMemcpyAsync(&e, ctx->d_error, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  H2_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (e) {
+    H2_CUDA(cudaMemsetAsync(ctx->d_error, 0, sizeof(int), ctx->stream));
+    std::string m = "device reported:";
+    if (e & kErrRows) m += " matrix taller than the kernel tile;";
+    if (e & kErrCols) m += " more than 32 columns (k + u > 32);";
+    if (e & kErrJacobi) m += " one-sided Jacobi did not converge;";
+    if (e & kErrRank) m += " inconsistent ranks;";
+    throw Error(H2_EDEVICE, m);
+  }
+}
+
+extern "C" h2_status h2_ctx_synchronize(h2_ctx* ctx) {
+  if (!ctx) return H2_EINVAL;
+  return guard(ctx, [&] {
+    DeviceGuard g(ctx->device);
+    H2_CUDA(cudaStreamSynchronize(ctx->stream));
+    H2_CUDA(cudaGetLastError());
+    check_device_error(ctx);
+  });
+}
+
+// ==================================================================== matrix
+extern "C" h2_status h2_matrix_create(h2_ctx* ctx, const double* points, int64_t n, int dim,
+                                      int leaf_size, double eta, double pad, int kcap,
+                                      h2_matrix** out) {
+  if (!out) return H2_EINVAL;
+  *out = nullptr;
+  auto Z = std::make_unique<h2_matrix>();
+  h2_status s = guard(ctx, [&] {
+    H2_REQUIRE(points && n > 0 && dim >= 1 && dim <= 3, "h2_matrix_create: bad points");
+    H2_REQUIRE(leaf_size >= 1 && eta > 0 && pad >= 0, "h2_matrix_create: bad parameters");
+    H2_REQUIRE(kcap >= 1 && kcap <= kMaxCols, "h2_matrix_create: kcap must be in 1..32");
+    for (int64_t i = 0; i < n * dim; ++i) H2_REQUIRE(std::isfinite(points[i]), "non-finite point");
+    build_cluster_tree(points, n, dim, leaf_size, pad, Z->rows);
+    Z->cols = Z->rows;
+    build_block_tree(Z->rows, Z->cols, eta, Z->blocks);
+    Z->kcap = kcap;
+    Z->V.rank.assign(Z->rows.count(), 0);
+    Z->W.rank.assign(Z->cols.count(), 0);
+    if (!ctx) return;   // structure only (no device storage)
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = ctx->stream;
+    Z->device = ctx->device;
+    alloc_basis(Z->rows, kcap, Z->V, st);
+    alloc_basis(Z->cols, kcap, Z->W, st);
+    const BlockTree& bt = Z->blocks;
+    const size_t nadm = bt.adm.size();
+    Z->d_S = dalloc<double>(nadm * kcap * kcap);
+    H2_CUDA(cudaMemsetAsync(Z->d_S, 0, nadm * kcap * kcap * sizeof(double), st));
+    Z->near_off.resize(bt.near.size());
+    int64_t tot = 0;
+    for (size_t i = 0; i < bt.near.size(); ++i) {
+      Z->near_off[i] = tot;
+      tot += Z->rows.size[bt.row[bt.near[i]]] * Z->cols.size[bt.col[bt.near[i]]];
+    }
+    Z->near_len = tot;
+    Z->d_N = dalloc<double>(tot);
+    H2_CUDA(cudaMemsetAsync(Z->d_N, 0, tot * sizeof(double), st));
+    Z->d_row_off = upload(Z->rows.off, st);
+    Z->d_col_off = upload(Z->cols.off, st);
+    std::vector<int32_t> rs(Z->rows.size.begin(), Z->rows.size.end());
+    std::vector<int32_t> cs(Z->cols.size.begin(), Z->cols.size.end());
+    Z->d_row_size = upload(rs, st);
+    Z->d_col_size = upload(cs, st);
+    Z->d_subtree_r = upload(Z->rows.subtree, st);
+    Z->d_subtree_c = upload(Z->cols.subtree, st);
+    Z->d_father_r = upload(Z->rows.father, st);
+    Z->d_father_c = upload(Z->cols.father, st);
+    std::vector<int32_t> br(nadm), bc(nadm);
+    for (size_t a = 0; a < nadm; ++a) {
+      br[a] = bt.row[bt.adm[a]];
+      bc[a] = bt.col[bt.adm[a]];
+    }
+    Z->d_blk_row = upload(br, st);
+    Z->d_blk_col = upload(bc, st);
+    Z->d_row_ptr = upload(bt.row_ptr, st);
+    Z->d_row_adm = upload(bt.row_adm, st);
+    Z->d_col_ptr = upload(bt.col_ptr, st);
+    Z->d_col_adm = upload(bt.col_adm, st);
+    H2_CUDA(cudaStreamSynchronize(st));
+  });
+  if (s == H2_OK) *out = Z.release();
+  return s;
+}
+
+extern "C" void h2_matrix_free(h2_matrix* Z) {
+  if (!Z) return;
+  free_basis(Z->V);
+  free_basis(Z->W);
+  dfree(Z->d_S);
+  dfree(Z->d_N);
+  dfree(Z->d_row_off);
+  dfree(Z->d_col_off);
+  dfree(Z->d_row_size);
+  dfree(Z->d_col_size);
+  dfree(Z->d_subtree_r);
+  dfree(Z->d_subtree_c);
+  dfree(Z->d_father_r);
+  dfree(Z->d_father_c);
+  dfree(Z->d_blk_row);
+  dfree(Z->d_blk_col);
+  dfree(Z->d_row_ptr);
+  dfree(Z->d_row_adm);
+  dfree(Z->d_col_ptr);
+  dfree(Z->d_col_adm);
+  delete Z;
+}
+
+extern "C" h2_status h2_matrix_clone(h2_ctx* ctx, const h2_matrix* Z, h2_matrix** out) {
+  if (!ctx || !Z || !out) return H2_EINVAL;
+  *out = nullptr;
+  h2_matrix* C = nullptr;
+  h2_status s = guard(ctx, [&] {
+    H2_REQUIRE(has_storage(Z), "h2_matrix_clone: matrix has no device storage");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = ctx->stream;
+    std::unique_ptr<h2_matrix> Y(new h2_matrix());
+    Y->rows = Z->rows;
+    Y->cols = Z->cols;
+    Y->blocks = Z->blocks;
+    Y->kcap = Z->kcap;
+    Y->device = Z->device;
+    Y->near_off = Z->near_off;
+    Y->near_len = Z->near_len;
+    auto dup = [&](auto* src, size_t count) {
+      using T = std::remove_const_t<std::remove_pointer_t<decltype(src)>>;
+      T* d = dalloc<T>(count);
+      if (count) H2_CUDA(cudaMemcpyAsync(d, src, count * sizeof(T), cudaMemcpyDeviceToDevice, st));
+      return d;
+    };
+    for (int sd = 0; sd < 2; ++sd) {
+      const ClusterTree& ct = tree_of(Z, sd);
+      const DeviceBasis& ob = basis_of(Z, sd);
+      DeviceBasis& nb = basis_of(Y.get(), sd);
+      nb.rank = ob.rank;
+      nb.leaf_off = ob.leaf_off;
+      int64_t tot = 0;
+      for (int32_t c = 0; c < ct.count(); ++c)
+        if (ct.leaf(c)) tot += ct.size[c] * Z->kcap;
+      nb.d_leaf = dup(ob.d_leaf, tot);
+      nb.d_transfer = dup(ob.d_transfer, (size_t)ct.count() * Z->kcap * Z->kcap);
+      nb.d_leaf_off = dup(ob.d_leaf_off, ct.count());
+      nb.d_rank = dup(ob.d_rank, ct.count());
+    }
+    const size_t nadm = Z->blocks.adm.size();
+    const int32_t nr = Z->rows.count(), nc = Z->cols.count();
+    Y->d_S = dup(Z->d_S, nadm * Z->kcap * Z->kcap);
+    Y->d_N = dup(Z->d_N, Z->near_len);
+    Y->d_row_off = dup(Z->d_row_off, nr);
+    Y->d_col_off = dup(Z->d_col_off, nc);
+    Y->d_row_size = dup(Z->d_row_size, nr);
+    Y->d_col_size = dup(Z->d_col_size, nc);
+    Y->d_subtree_r = dup(Z->d_subtree_r, nr);
+    Y->d_subtree_c = dup(Z->d_subtree_c, nc);
+    Y->d_father_r = dup(Z->d_father_r, nr);
+    Y->d_father_c = dup(Z->d_father_c, nc);
+    Y->d_blk_row = dup(Z->d_blk_row, nadm);
+    Y->d_blk_col = dup(Z->d_blk_col, nadm);
+    Y->d_row_ptr = dup(Z->d_row_ptr, nr + 1);
+    Y->d_row_adm = dup(Z->d_row_adm, nadm);
+    Y->d_col_ptr = dup(Z->d_col_ptr, nc + 1);
+    Y->d_col_adm = dup(Z->d_col_adm, nadm);
+    H2_CUDA(cudaStreamSynchronize(st));
+    C = Y.release();
+  });
+  if (s == H2_OK) *out = C;
+  return s;
+}
+
+extern "C" h2_status h2_tree_sizes(const h2_matrix* Z, int64_t* n, int64_t* n_clusters, int64_t* n_blocks,
+                                   int64_t* n_admissible, int64_t* n_inadmissible, int* depth) {
+  if (!Z) return H2_EINVAL;
+  if (n) *n = Z->rows.n;
+  if (n_clusters) *n_clusters = Z->rows.count();
+  if (n_blocks) *n_blocks = Z->blocks.count();
+  if (n_admissible) *n_admissible = (int64_t)Z->blocks.adm.size();
+  if (n_inadmissible) *n_inadmissible = (int64_t)Z->blocks.near.size();
+  if (depth) *depth = Z->rows.depth;
+  return H2_OK;
+}
+
+extern "C" h2_status h2_tree_clusters(const h2_matrix* Z, int64_t* offset, int64_t* size,
+                                      int32_t* father, int32_t* son0, int32_t* son1, int32_t* level,
+                                      int32_t* subtree) {
+  if (!Z) return H2_EINVAL;
+  const ClusterTree& ct = Z->rows;
+  const size_t nc = ct.count();
+  if (offset) std::memcpy(offset, ct.off.data(), nc * sizeof(int64_t));
+  if (size) std::memcpy(size, ct.size.data(), nc * sizeof(int64_t));
+  if (father) std::memcpy(father, ct.father.data(), nc * sizeof(int32_t));
+  if (son0) std::memcpy(son0, ct.son0.data(), nc * sizeof(int32_t));
+  if (son1) std::memcpy(son1, ct.son1.data(), nc * sizeof(int32_t));
+  if (level) std::memcpy(level, ct.level.data(), nc * sizeof(int32_t));
+  if (subtree) std::memcpy(subtree, ct.subtree.data(), nc * sizeof(int32_t));
+  return H2_OK;
+}
+
+extern "C" h2_status h2_tree_blocks(const h2_matrix* Z, int32_t* row, int32_t* col, int32_t* kind,
+                                    int32_t* father) {
+  if (!Z) return H2_EINVAL;
+  const BlockTree& bt = Z->blocks;
+  const size_t nb = bt.count();
+  if (row) std::memcpy(row, bt.row.data(), nb * sizeof(int32_t));
+  if (col) std::memcpy(col, bt.col.data(), nb * sizeof(int32_t));
+  if (kind) std::memcpy(kind, bt.kind.data(), nb * sizeof(int32_t));
+  if (father) std::memcpy(father, bt.father.data(), nb * sizeof(int32_t));
+  return H2_OK;
+}
+
+extern "C" h2_status h2_tree_permutation(const h2_matrix* Z, int64_t* perm) {
+  if (!Z || !perm) return H2_EINVAL;
+  std::memcpy(perm, Z->rows.perm.data(), Z->rows.perm.size() * sizeof(int64_t));
+  return H2_OK;
+}
+
+// ====================================================================== data
+namespace {
+
+void basis_lengths(const h2_matrix* Z, int side, const std::vector<int32_t>& rank, int64_t& leaf,
+                   int64_t& transfer) {
+  const ClusterTree& ct = tree_of(Z, side);
+  leaf = 0;
+  transfer = 0;
+  for (int32_t c = 0; c < ct.count(); ++c) {
+    if (ct.leaf(c)) leaf += ct.size[c] * rank[c];
+    if (ct.father[c] >= 0) transfer += (int64_t)rank[c] * rank[ct.father[c]];
+  }
+}
+
+int64_t coupling_length(const h2_matrix* Z) {
+  int64_t tot = 0;
+  for (int32_t b : Z->blocks.adm) tot += (int64_t)Z->V.rank[Z->blocks.row[b]] * Z->W.rank[Z->blocks.col[b]];
+  return tot;
+}
+
+}  // namespace
+
+extern "C" h2_status h2_data_sizes(const h2_matrix* Z, int side, int64_t* leaf_len, int64_t* transfer_len,
+                                   int64_t* coupling_len, int64_t* nearfield_len) {
+  if (!Z || (side != 0 && side != 1)) return H2_EINVAL;
+  int64_t l = 0, t = 0;
+  basis_lengths(Z, side, basis_of(Z, side).rank, l, t);
+  if (leaf_len) *leaf_len = l;
+  if (transfer_len) *transfer_len = t;
+  if (coupling_len) *coupling_len = coupling_length(Z);
+  if (nearfield_len) {
+    int64_t nl = 0;
+    for (int32_t b : Z->blocks.near) nl += Z->rows.size[Z->blocks.row[b]] * Z->cols.size[Z->blocks.col[b]];
+    *nearfield_len = nl;
+  }
+  return H2_OK;
+}
+
+extern "C" h2_status h2_get_ranks(const h2_matrix* Z, int side, int32_t* ranks) {
+  if (!Z || !ranks || (side != 0 && side != 1)) return H2_EINVAL;
+  const DeviceBasis& b = basis_of(Z, side);
+  std::memcpy(ranks, b.rank.data(), b.rank.size() * sizeof(int32_t));
+  return H2_OK;
+}
+
+extern "C" h2_status h2_set_basis(h2_ctx* ctx, h2_matrix* Z, int side, const int32_t* ranks,
+                                  const double* leaf_data, const double* transfer_data) {
+  if (!ctx || !Z || !ranks || (side != 0 && side != 1)) return H2_EINVAL;
+  return guard(ctx, [&] {
+    H2_REQUIRE(has_storage(Z), "h2_set_basis: matrix has no device storage");
+    const ClusterTree& ct = tree_of(Z, side);
+    std::vector<int32_t> rk(ranks, ranks + ct.count());
+    int kmax = 0;
+    for (int32_t c = 0; c < ct.count(); ++c) {
+      H2_REQUIRE(rk[c] >= 0 && rk[c] <= kMaxCols, "h2_set_basis: rank out of 0..32");
+      if (ct.leaf(c)) H2_REQUIRE(rk[c] <= ct.size[c], "h2_set_basis: leaf rank above leaf size");
+      kmax = std::max(kmax, rk[c]);
+    }
+    int64_t ll = 0, tl = 0;
+    basis_lengths(Z, side, rk, ll, tl);
+    H2_REQUIRE(ll == 0 || leaf_data, "h2_set_basis: leaf_data missing");
+    H2_REQUIRE(tl == 0 || transfer_data, "h2_set_basis: transfer_data missing");
+    DeviceGuard g(ctx->device);
+    grow_kcap(ctx, Z, kmax);
+    const int kcap = Z->kcap;
+    DeviceBasis& b = basis_of(Z, side);
+    std::vector<double> leaf;
+    int64_t tot = 0;
+    for (int32_t c = 0; c < ct.count(); ++c)
+      if (ct.leaf(c)) tot += ct.size[c] * kcap;
+    leaf.assign(tot, 0.0);
+    std::vector<double> tr((size_t)ct.count() * kcap * kcap, 0.0);
+    int64_t pl = 0, pt = 0;
+    for (int32_t c = 0; c < ct.count(); ++c) {
+      if (ct.leaf(c)) {
+        const int64_t m = ct.size[c];
+        std::memcpy(leaf.data() + b.leaf_off[c], leaf_data + pl, m * rk[c] * sizeof(double));
+        pl += m * rk[c];
+      }
+      if (ct.father[c] >= 0) {
+        const int kf = rk[ct.father[c]];
+        for (int j = 0; j < kf; ++j)
+          for (int i = 0; i < rk[c]; ++i)
+            tr[(size_t)c * kcap * kcap + i + j * kcap] = transfer_data[pt + i + (int64_t)j * rk[c]];
+        pt += (int64_t)rk[c] * kf;
+      }
+    }
+    cudaStream_t st = ctx->stream;
+    if (tot) H2_CUDA(cudaMemcpyAsync(b.d_leaf, leaf.data(), tot * sizeof(double), cudaMemcpyHostToDevice, st));
+    H2_CUDA(cudaMemcpyAsync(b.d_transfer, tr.data(), tr.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    b.rank = rk;
+    sync_ranks(b, st);
+    H2_CUDA(cudaStreamSynchronize(st));
+  });
+}
+
+extern "C" h2_status h2_get_basis(h2_ctx* ctx, const h2_matrix* Z, int side, double* leaf_data,
+                                  double* transfer_data) {
+  if (!ctx || !Z || (side != 0 && side != 1)) return H2_EINVAL;
+  return guard(ctx, [&] {
+    H2_REQUIRE(has_storage(Z), "h2_get_basis: matrix has no device storage");
+    DeviceGuard g(ctx->device);
+    const ClusterTree& ct = tree_of(Z, side);
+    const DeviceBasis& b = basis_of(Z, side);
+    const int kcap = Z->kcap;
+    int64_t tot = 0;
+    for (int32_t c = 0; c < ct.count(); ++c)
+      if (ct.leaf(c)) tot += ct.size[c] * kcap;
+    std::vector<double> leaf(tot), tr((size_t)ct.count() * kcap * kcap);
+    cudaStream_t st = ctx->stream;
+    if (tot) H2_CUDA(cudaMemcpyAsync(leaf.data(), b.d_leaf, tot * sizeof(double), cudaMemcpyDeviceToHost, st));
+    H2_CUDA(cudaMemcpyAsync(tr.data(), b.d_transfer, tr.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    H2_CUDA(cudaStreamSynchronize(st));
+    int64_t pl = 0, pt = 0;
+    for (int32_t c = 0; c < ct.count(); ++c) {
+      if (ct.leaf(c)) {
+        const int64_t m = ct.size[c];
+        if (leaf_data) std::memcpy(leaf_data + pl, leaf.data() + b.leaf_off[c], m * b.rank[c] * sizeof(double));
+        pl += m * b.rank[c];
+      }
+      if (ct.father[c] >= 0) {
+        const int kf = b.rank[ct.father[c]];
+        if (transfer_data)
+          for (int j = 0; j < kf; ++j)
+            for (int i = 0; i < b.rank[c]; ++i)
+              transfer_data[pt + i + (int64_t)j * b.rank[c]] = tr[(size_t)c * kcap * kcap + i + j * kcap];
+        pt += (int64_t)b.rank[c] * kf;
+      }
+    }
+  });
+}
+
+extern "C" h2_status h2_set_couplings(h2_ctx* ctx, h2_matrix* Z, const double* data) {
+  if (!ctx || !Z) return H2_EINVAL;
+  return guard(ctx, [&] {
+    H2_REQUIRE(has_storage(Z), "h2_set_couplings: matrix has no device storage");
+    H2_REQUIRE(data || coupling_length(Z) == 0, "h2_set_couplings: data missing");
+    DeviceGuard g(ctx->device);
+    const int kcap = Z->kcap;
+    const BlockTree& bt = Z->blocks;
+    std::vector<double> S(bt.adm.size() * kcap * kcap, 0.0);
+    int64_t p = 0;
+    for (size_t a = 0; a < bt.adm.size(); ++a) {
+      const int kt = Z->V.rank[bt.row[bt.adm[a]]], ls = Z->W.rank[bt.col[bt.adm[a]]];
+      for (int j = 0; j < ls; ++j)
+        for (int i = 0; i < kt; ++i) S[a * kcap * kcap + i + j * kcap] = data[p + i + (int64_t)j * kt];
+      p += (int64_t)kt * ls;
+    }
+    if (!S.empty())
+      H2_CUDA(cudaMemcpyAsync(Z->d_S, S.data(), S.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    H2_CUDA(cudaStreamSynchronize(ctx->stream));
+  });
+}
+
+extern "C" h2_status h2_get_couplings(h2_ctx* ctx, const h2_matrix* Z, double* data) {
+  if (!ctx || !Z || !data) return H2_EINVAL;
+  return guard(ctx, [&] {
+    H2_REQUIRE(has_storage(Z), "h2_get_couplings: matrix has no device storage");
+    DeviceGuard g(ctx->device);
+    const int kcap = Z->kcap;
+    const BlockTree& bt = Z->blocks;
+    std::vector<double> S(bt.adm.size() * kcap * kcap);
+    if (!S.empty())
+      H2_CUDA(cudaMemcpyAsync(S.data(), Z->d_S, S.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    H2_CUDA(cudaStreamSynchronize(ctx->stream));
+    int64_t p = 0;
+    for (size_t a = 0; a < bt.adm.size(); ++a) {
+      const int kt = Z->V.rank[bt.row[bt.adm[a]]], ls = Z->W.rank[bt.col[bt.adm[a]]];
+      for (int j = 0; j < ls; ++j)
+        for (int i = 0; i < kt; ++i) data[p + i + (int64_t)j * kt] = S[a * kcap * kcap + i + j * kcap];
+      p += (int64_t)kt * ls;
+    }
+  });
+}
+
+extern "C" h2_status h2_set_nearfield(h2_ctx* ctx, h2_matrix* Z, const double* data) {
+  if (!ctx || !Z) return H2_EINVAL;
+  return guard(ctx, [&] {
+    H2_REQUIRE(has_storage(Z), "h2_set_nearfield: matrix has no device storage");
+    H2_REQUIRE(data || Z->near_len == 0, "h2_set_nearfield: data missing");
+    DeviceGuard g(ctx->device);
+    if (Z->near_len)
+      H2_CUDA(cudaMemcpyAsync(Z->d_N, data, Z->near_len * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    H2_CUDA(cudaStreamSynchronize(ctx->stream));
+  });
+}
+
+extern "C" h2_status h2_get_nearfield(h2_ctx* ctx, const h2_matrix* Z, double* data) {
+  if (!ctx || !Z || !data) return H2_EINVAL;
+  return guard(ctx, [&] {
+    H2_REQUIRE(has_storage(Z), "h2_get_nearfield: matrix has no device storage");
+    DeviceGuard g(ctx->device);
+    if (Z->near_len)
+      H2_CUDA(cudaMemcpyAsync(data, Z->d_N, Z->near_len * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    H2_CUDA(cudaStreamSynchronize(ctx->stream));
+  });
+}
+
+extern "C" h2_status h2_get_leaf(h2_ctx* ctx, const h2_matrix* Z, int side, int64_t cluster, double* out) {
+  if (!ctx || !Z || !out || (side != 0 && side != 1)) return H2_EINVAL;
+  return guard(ctx, [&] {
+    const ClusterTree& ct = tree_of(Z, side);
+    H2_REQUIRE(has_storage(Z), "h2_get_leaf: no device storage");
+    H2_REQUIRE(cluster >= 0 && cluster < ct.count() && ct.leaf((int32_t)cluster), "h2_get_leaf: not a leaf");
+    DeviceGuard g(ctx->device);
+    const DeviceBasis& b = basis_of(Z, side);
+    const size_t len = ct.size[cluster] * b.rank[cluster];
+    if (len)
+      H2_CUDA(cudaMemcpyAsync(out, b.d_leaf + b.leaf_off[cluster], len * sizeof(double), cudaMemcpyDeviceToHost,
+                              ctx->stream));
+    H2_CUDA(cudaStreamSynchronize(ctx->stream));
+  });
+}
+
+extern "C" h2_status h2_get_transfer(h2_ctx* ctx, const h2_matrix* Z, int side, int64_t cluster, double* out) {
+  if (!ctx || !Z || !out || (side != 0 && side != 1)) return H2_EINVAL;
+  return guard(ctx, [&] {
+    const ClusterTree& ct = tree_of(Z, side);
+    H2_REQUIRE(has_storage(Z), "h2_get_transfer: no device storage");
+    H2_REQUIRE(cluster > 0 && cluster < ct.count(), "h2_get_transfer: cluster out of range");
+    DeviceGuard g(ctx->device);
+    const DeviceBasis& b = basis_of(Z, side);
+    const int k = b.rank[cluster], kf = b.rank[ct.father[cluster]];
+    if (k && kf)
+      H2_CUDA(cudaMemcpy2DAsync(out, k * sizeof(double), b.d_transfer + cluster * Z->kcap * Z->kcap,
+                                Z->kcap * sizeof(double), k * sizeof(double), kf, cudaMemcpyDeviceToHost,
+                                ctx->stream));
+    H2_CUDA(cudaStreamSynchronize(ctx->stream));
+  });
+}
+
+extern "C" h2_status h2_get_coupling(h2_ctx* ctx, const h2_matrix* Z, int64_t block, double* out) {
+  if (!ctx || !Z || !out) return H2_EINVAL;
+  return guard(ctx, [&] {
+    const BlockTree& bt = Z->blocks;
+    H2_REQUIRE(has_storage(Z), "h2_get_coupling: no device storage");
+    H2_REQUIRE(block >= 0 && block < bt.count() && bt.kind[block] == kAdm, "h2_get_coupling: not admissible");
+    DeviceGuard g(ctx->device);
+    const int kt = Z->V.rank[bt.row[block]], ls = Z->W.rank[bt.col[block]];
+    if (kt && ls)
+      H2_CUDA(cudaMemcpy2DAsync(out, kt * sizeof(double), Z->d_S + (size_t)bt.slot[block] * Z->kcap * Z->kcap,
+                                Z->kcap * sizeof(double), kt * sizeof(double), ls, cudaMemcpyDeviceToHost,
+                                ctx->stream));
+    H2_CUDA(cudaStreamSynchronize(ctx->stream));
+  });
+}
+
+// ================================================================== batches
+struct h2_batch {
+  const h2_matrix* Z = nullptr;
+  int device = 0;
+  int u = 0;
+  int64_t count = 0;
+  std::vector<int64_t> blocks;
+  std::vector<int64_t> offA, rowsA, offB, rowsB;
+  int64_t lenA = 0, lenB = 0;
+  // host plan
+  std::vector<Item> items;
+  std::vector<Entry> ents;
+  std::vector<Task> tasks;
+  std::vector<NormTask> norms;
+  std::vector<int64_t> upd_item, upd_task;      // per update: first item / task (+ sentinel)
+  std::vector<int32_t> lvl_list;                // items sorted by level
+  std::vector<int32_t> lvl_ptr;                 // per level
+  std::vector<int32_t> lvl_maxrows;             // per level: bound on rows of the truncation
+  std::vector<int32_t> cl_list[2], cl_ptr[2];   // all clusters by level, per side
+  int depth = 0;
+  int kl = 0;                                   // max extended rank
+  int64_t qlen = 0;
+  // result packing (execute_host)
+  std::vector<int64_t> res_task_off, res_item_off;
+  int64_t res_len = 0;
+  // device
+  Item* d_items = nullptr;
+  Entry* d_ents = nullptr;
+  Task* d_tasks = nullptr;
+  NormTask* d_norms = nullptr;
+  int32_t* d_lvl = nullptr;
+  int32_t* d_cl[2] = {nullptr, nullptr};
+  ItemBuffers IB{};
+  BaseWeights BW{};
+  double* d_A = nullptr;   // staging for execute_host
+  double* d_B = nullptr;
+  double* d_res = nullptr;
+  int64_t* d_res_task_off = nullptr;
+  int64_t* d_res_item_off = nullptr;
+  int64_t launches = 0;
+  int64_t phase_launches[H2_PHASE_COUNT] = {0, 0, 0, 0, 0, 0};
+  bool executed = false;
+  bool timing = false;
+  cudaEvent_t ev[H2_PHASE_COUNT + 1] = {};
+};
+
+namespace {
+
+void plan_batch(h2_batch& P) {
+  const h2_matrix* Z = P.Z;
+  const ClusterTree* tr[2] = {&Z->rows, &Z->cols};
+  const BlockTree& bt = Z->blocks;
+  const int u = P.u;
+  std::vector<int32_t> item_of[2];
+  item_of[0].assign(Z->rows.count(), -1);
+  item_of[1].assign(Z->cols.count(), -1);
+  std::unordered_map<int32_t, int32_t> norm_of;   // coupling slot -> norm task (per update)
+  P.depth = std::max(Z->rows.depth, Z->cols.depth);
+  P.upd_item.assign(P.count + 1, 0);
+  P.upd_task.assign(P.count + 1, 0);
+  int64_t qoff = 0;
+  for (int64_t j = 0; j < P.count; ++j) {
+    const int32_t b0 = (int32_t)P.blocks[j];
+    const int32_t root[2] = {bt.row[b0], bt.col[b0]};
+    P.upd_item[j] = (int64_t)P.items.size();
+    P.upd_task[j] = (int64_t)P.tasks.size();
+    std::vector<int32_t> sub[2];
+    for (int sd = 0; sd < 2; ++sd) {
+      const ClusterTree& ct = *tr[sd];
+      const DeviceBasis& bs = basis_of(Z, sd);
+      // depth-first preorder of the subtree
+      std::vector<int32_t> stack{root[sd]};
+      while (!stack.empty()) {
+        const int32_t c = stack.back();
+        stack.pop_back();
+        sub[sd].push_back(c);
+        if (!ct.leaf(c)) {
+          stack.push_back(ct.son1[c]);
+          stack.push_back(ct.son0[c]);
+        }
+      }
+      for (int32_t c : sub[sd]) {
+        Item it{};
+        it.side = sd;
+        it.cluster = c;
+        it.parent = (c == root[sd]) ? -1 : item_of[sd][ct.father[c]];
+        it.son0 = it.son1 = -1;
+        it.flags = 0;
+        if (ct.leaf(c)) it.flags |= kItemLeaf;
+        if (c == root[sd]) it.flags |= kItemRoot;
+        if (ct.father[c] < 0) it.flags |= kItemTreeRoot;
+        it.k = bs.rank[c];
+        it.kf = ct.father[c] >= 0 ? bs.rank[ct.father[c]] : 0;
+        H2_REQUIRE(it.k + u <= kMaxCols, "h2_batch_create: k_t + u exceeds 32");
+        it.size = (int32_t)ct.size[c];
+        it.rowoff = (int32_t)(ct.off[c] - ct.off[root[sd]]);
+        it.ld = (int32_t)ct.size[root[sd]];
+        it.foff = sd == 0 ? P.offA[j] : P.offB[j];
+        it.qoff = -1;
+        if (ct.leaf(c)) {
+          it.qoff = qoff;
+          qoff += ct.size[c] * (it.k + u);
+        }
+        item_of[sd][c] = (int32_t)P.items.size();
+        P.items.push_back(it);
+      }
+      for (int32_t c : sub[sd])
+        if (!ct.leaf(c)) {
+          Item& it = P.items[item_of[sd][c]];
+          it.son0 = item_of[sd][ct.son0[c]];
+          it.son1 = item_of[sd][ct.son1[c]];
+        }
+    }
+    // entries and tasks
+    norm_of.clear();
+    for (int sd = 0; sd < 2; ++sd) {
+      const std::vector<int32_t>& ptr = sd == 0 ? bt.row_ptr : bt.col_ptr;
+      const std::vector<int32_t>& adm = sd == 0 ? bt.row_adm : bt.col_adm;
+      for (int32_t c : sub[sd]) {
+        const int32_t iid = item_of[sd][c];
+        Item& it = P.items[iid];
+        it.ent_begin = (int32_t)P.ents.size();
+        for (int32_t e = ptr[c]; e < ptr[c + 1]; ++e) {
+          const int32_t slot = adm[e];
+          const int32_t blk = bt.adm[slot];
+          const int32_t o = sd == 0 ? bt.col[blk] : bt.row[blk];
+          const int32_t oi = item_of[1 - sd][o];
+          Entry en{slot, oi, o, -1};
+          if (oi >= 0) {
+            auto f = norm_of.find(slot);
+            if (f == norm_of.end()) {
+              const int32_t nid = (int32_t)P.norms.size();
+              P.norms.push_back(NormTask{slot, sd == 0 ? iid : oi, sd == 0 ? oi : iid, 0});
+              norm_of.emplace(slot, nid);
+              en.norm = nid;
+            } else {
+              en.norm = f->second;
+            }
+            it.flags |= kItemInside;
+          }
+          P.ents.push_back(en);
+          const int kt = Z->V.rank[bt.row[blk]], ls = Z->W.rank[bt.col[blk]];
+          if (sd == 0)
+            P.tasks.push_back(Task{slot, iid, oi, kt, ls});
+          else if (oi < 0)
+            P.tasks.push_back(Task{slot, -1, iid, kt, ls});
+        }
+        it.ent_end = (int32_t)P.ents.size();
+      }
+    }
+    for (int sd = 0; sd < 2; ++sd)
+      for (int32_t c : sub[sd]) item_of[sd][c] = -1;
+  }
+  P.upd_item[P.count] = (int64_t)P.items.size();
+  P.upd_task[P.count] = (int64_t)P.tasks.size();
+  P.qlen = qoff;
+  H2_REQUIRE(P.items.size() < (size_t)INT32_MAX && P.tasks.size() < (size_t)INT32_MAX,
+             "h2_batch_create: batch too large");
+  // level lists
+  const int L = P.depth + 1;
+  P.lvl_ptr.assign(L + 1, 0);
+  P.lvl_maxrows.assign(L, 0);
+  P.kl = 0;
+  for (const Item& it : P.items) {
+    const int lev = tr[it.side]->level[it.cluster];
+    P.lvl_ptr[lev + 1]++;
+    P.kl = std::max(P.kl, it.k + u);
+  }
+  for (int l = 0; l < L; ++l) P.lvl_ptr[l + 1] += P.lvl_ptr[l];
+  P.lvl_list.assign(P.items.size(), 0);
+  std::vector<int32_t> fill(P.lvl_ptr.begin(), P.lvl_ptr.end() - 1);
+  for (size_t i = 0; i < P.items.size(); ++i) {
+    const Item& it = P.items[i];
+    const int lev = tr[it.side]->level[it.cluster];
+    P.lvl_list[fill[lev]++] = (int32_t)i;
+    int rows = it.size;
+    if (!(it.flags & kItemLeaf)) rows = P.items[it.son0].k + P.items[it.son1].k + 2 * u;
+    P.lvl_maxrows[lev] = std::max(P.lvl_maxrows[lev], rows);
+  }
+  for (int l = 0; l < L; ++l)
+    H2_REQUIRE(P.lvl_maxrows[l] <= 64, "h2_batch_create: leaf clusters above 64 indices are not supported");
+  // all clusters by level (prepass)
+  for (int sd = 0; sd < 2; ++sd) {
+    const ClusterTree& ct = *tr[sd];
+    P.cl_ptr[sd].assign(L + 1, 0);
+    for (int32_t c = 0; c < ct.count(); ++c) P.cl_ptr[sd][ct.level[c] + 1]++;
+    for (int l = 0; l < L; ++l) P.cl_ptr[sd][l + 1] += P.cl_ptr[sd][l];
+    P.cl_list[sd].assign(ct.count(), 0);
+    std::vector<int32_t> f2(P.cl_ptr[sd].begin(), P.cl_ptr[sd].end() - 1);
+    for (int32_t c = 0; c < ct.count(); ++c) P.cl_list[sd][f2[ct.level[c]]++] = c;
+  }
+  // packed result layout: [ranks of items][couplings][leaf bases / transfers]
+  int64_t off = (int64_t)P.items.size();
+  P.res_task_off.resize(P.tasks.size());
+  for (size_t t = 0; t < P.tasks.size(); ++t) {
+    const Task& tk = P.tasks[t];
+    const int R = tk.it >= 0 ? tk.kt + u : tk.kt;
+    const int C = tk.is >= 0 ? tk.ls + u : tk.ls;
+    P.res_task_off[t] = off;
+    off += (int64_t)R * C;
+  }
+  P.res_item_off.resize(P.items.size());
+  for (size_t i = 0; i < P.items.size(); ++i) {
+    const Item& it = P.items[i];
+    P.res_item_off[i] = off;
+    const int K = it.k + u;
+    if (it.flags & kItemLeaf) off += (int64_t)it.size * K;
+    if (!(it.flags & kItemTreeRoot)) {
+      const int Kf = (it.flags & kItemRoot) ? it.kf : it.kf + u;
+      off += (int64_t)K * Kf;
+    }
+  }
+  P.res_len = off;
+}
+
+void alloc_batch(h2_ctx* ctx, h2_batch& P) {
+  cudaStream_t st = ctx->stream;
+  P.d_items = upload(P.items, st);
+  P.d_ents = upload(P.ents, st);
+  P.d_tasks = upload(P.tasks, st);
+  P.d_norms = upload(P.norms, st);
+  P.d_lvl = upload(P.lvl_list, st);
+  for (int sd = 0; sd < 2; ++sd) P.d_cl[sd] = upload(P.cl_list[sd], st);
+  const size_t ni = P.items.size();
+  P.IB.Rq = dalloc<double>(ni * kSlot);
+  P.IB.Bw = dalloc<double>(ni * kSlot);
+  P.IB.Rt = dalloc<double>(ni * kSlot);
+  P.IB.F = dalloc<double>(ni * kSlot);
+  P.IB.Q = dalloc<double>(P.qlen);
+  P.IB.rank = dalloc<int32_t>(ni);
+  P.IB.norms = dalloc<double>(P.norms.size());
+  P.IB.S_out = dalloc<double>(P.tasks.size() * kSlot);
+  P.IB.jac = dalloc<unsigned long long>(2 * ni);
+  if (ni) H2_CUDA(cudaMemsetAsync(P.IB.jac, 0, 2 * ni * sizeof(unsigned long long), st));
+  const int32_t ncl[2] = {P.Z->rows.count(), P.Z->cols.count()};
+  for (int sd = 0; sd < 2; ++sd) {
+    P.BW.G[sd] = dalloc<double>((size_t)ncl[sd] * kSlot);
+    P.BW.B[sd] = dalloc<double>((size_t)ncl[sd] * kSlot);
+  }
+  H2_CUDA(cudaStreamSynchronize(st));
+}
+
+void free_batch_device(h2_batch& P) {
+  dfree(P.d_items);
+  dfree(P.d_ents);
+  dfree(P.d_tasks);
+  dfree(P.d_norms);
+  dfree(P.d_lvl);
+  for (int sd = 0; sd < 2; ++sd) {
+    dfree(P.d_cl[sd]);
+    dfree(P.BW.G[sd]);
+    dfree(P.BW.B[sd]);
+  }
+  dfree(P.IB.Rq);
+  dfree(P.IB.Bw);
+  dfree(P.IB.Rt);
+  dfree(P.IB.F);
+  dfree(P.IB.Q);
+  dfree(P.IB.rank);
+  dfree(P.IB.norms);
+  dfree(P.IB.S_out);
+  dfree(P.IB.jac);
+  dfree(P.d_A);
+  dfree(P.d_B);
+  dfree(P.d_res);
+  dfree(P.d_res_task_off);
+  dfree(P.d_res_item_off);
+}
+
+void execute(h2_ctx* ctx, h2_batch& P, const double* A, const double* B, double eps) {
+  const h2_matrix* Z = P.Z;
+  cudaStream_t st = ctx->stream;
+  const MatView M = view_of(Z);
+  const int L = P.depth + 1;
+  int64_t* pl = P.phase_launches;
+  for (int ph = 0; ph < H2_PHASE_COUNT; ++ph) pl[ph] = 0;
+  auto mark = [&](int ph) {
+    if (P.timing) H2_CUDA(cudaEventRecord(P.ev[ph], st));
+  };
+  // base-matrix weights, top-down (both sides)
+  mark(H2_PHASE_BASE_WEIGHTS);
+  for (int sd = 0; sd < 2; ++sd) {
+    const int32_t* dptr = sd == 0 ? Z->d_row_ptr : Z->d_col_ptr;
+    const int32_t* dadm = sd == 0 ? Z->d_row_adm : Z->d_col_adm;
+    const int32_t* doth = sd == 0 ? Z->d_blk_col : Z->d_blk_row;
+    for (int l = 0; l < L; ++l) {
+      const int n = P.cl_ptr[sd][l + 1] - P.cl_ptr[sd][l];
+      if (!n) continue;
+      launch_prepass(M, sd, P.d_cl[sd] + P.cl_ptr[sd][l], n, dptr, dadm, doth, P.BW, ctx->d_error, st);
+      ++pl[H2_PHASE_BASE_WEIGHTS];
+    }
+  }
+  // step 2: basis R-factors, bottom-up
+  mark(H2_PHASE_RFACTOR);
+  for (int l = L - 1; l >= 0; --l) {
+    const int n = P.lvl_ptr[l + 1] - P.lvl_ptr[l];
+    if (!n) continue;
+    launch_rfactor(M, P.d_items, P.d_lvl + P.lvl_ptr[l], n, P.u, A, B, P.IB, ctx->d_error, st);
+    ++pl[H2_PHASE_RFACTOR];
+  }
+  mark(H2_PHASE_NORMS);
+  if (!P.norms.empty()) {
+    launch_norms(M, P.d_items, P.d_norms, (int)P.norms.size(), P.u, P.IB, st);
+    ++pl[H2_PHASE_NORMS];
+  }
+  // step 3: weights, top-down
+  mark(H2_PHASE_WEIGHTS);
+  for (int l = 0; l < L; ++l) {
+    const int n = P.lvl_ptr[l + 1] - P.lvl_ptr[l];
+    if (!n) continue;
+    launch_weights(M, P.d_items, P.d_ents, P.d_lvl + P.lvl_ptr[l], n, P.u, P.BW, P.IB, ctx->d_error, st);
+    ++pl[H2_PHASE_WEIGHTS];
+  }
+  // step 4: truncation, bottom-up
+  mark(H2_PHASE_TRUNCATE);
+  for (int l = L - 1; l >= 0; --l) {
+    const int n = P.lvl_ptr[l + 1] - P.lvl_ptr[l];
+    if (!n) continue;
+    launch_truncate(M, P.d_items, P.d_lvl + P.lvl_ptr[l], n, P.u, P.kl, P.lvl_maxrows[l], eps, A, B, P.IB,
+                    ctx->d_error, st);
+    ++pl[H2_PHASE_TRUNCATE];
+  }
+  // step 5: reprojection
+  mark(H2_PHASE_REPROJECT);
+  if (!P.tasks.empty()) {
+    launch_reproject(M, P.d_items, P.d_tasks, (int)P.tasks.size(), P.u, P.IB, st);
+    ++pl[H2_PHASE_REPROJECT];
+  }
+  mark(H2_PHASE_COUNT);
+  H2_CUDA(cudaGetLastError());
+  int64_t launches = 0;
+  for (int ph = 0; ph < H2_PHASE_COUNT; ++ph) launches += pl[ph];
+  P.launches = launches;
+  P.executed = true;
+}
+
+}  // namespace
+
+extern "C" h2_status h2_batch_create(h2_ctx* ctx, const h2_matrix* Z, int64_t count, const int64_t* blocks,
+                                     int u, h2_batch** out) {
+  if (!Z || !out || count < 0 || (count > 0 && !blocks)) return H2_EINVAL;
+  *out = nullptr;
+  auto P = std::make_unique<h2_batch>();
+  h2_status s = guard(ctx, [&] {
+    H2_REQUIRE(u >= 1 && u < kMaxCols, "h2_batch_create: update rank must be in 1..31");
+    const BlockTree& bt = Z->blocks;
+    P->Z = Z;
+    P->u = u;
+    P->count = count;
+    P->blocks.assign(blocks, blocks + count);
+    P->offA.resize(count);
+    P->offB.resize(count);
+    P->rowsA.resize(count);
+    P->rowsB.resize(count);
+    for (int64_t j = 0; j < count; ++j) {
+      H2_REQUIRE(blocks[j] >= 0 && blocks[j] < bt.count(), "h2_batch_create: block id out of range");
+      P->rowsA[j] = Z->rows.size[bt.row[blocks[j]]];
+      P->rowsB[j] = Z->cols.size[bt.col[blocks[j]]];
+      P->offA[j] = P->lenA;
+      P->offB[j] = P->lenB;
+      P->lenA += P->rowsA[j] * u;
+      P->lenB += P->rowsB[j] * u;
+    }
+    plan_batch(*P);
+    if (!ctx) return;   // host-only plan
+    H2_REQUIRE(has_storage(Z), "h2_batch_create: matrix has no device storage");
+    DeviceGuard g(ctx->device);
+    P->device = ctx->device;
+    alloc_batch(ctx, *P);
+  });
+  if (s == H2_OK) *out = P.release();
+  return s;
+}
+
+extern "C" void h2_batch_free(h2_batch* P) {
+  if (!P) return;
+  for (cudaEvent_t& e : P->ev)
+    if (e) cudaEventDestroy(e);
+  free_batch_device(*P);
+  delete P;
+}
+
+extern "C" h2_status h2_batch_factor_layout(const h2_batch* P, int64_t j, int64_t* rows_A, int64_t* off_A,
+                                            int64_t* rows_B, int64_t* off_B) {
+  if (!P || j < 0 || j >= P->count) return H2_EINVAL;
+  if (rows_A) *rows_A = P->rowsA[j];
+  if (off_A) *off_A = P->offA[j];
+  if (rows_B) *rows_B = P->rowsB[j];
+  if (off_B) *off_B = P->offB[j];
+  return H2_OK;
+}
+
+extern "C" h2_status h2_batch_factor_sizes(const h2_batch* P, int64_t* len_A, int64_t* len_B) {
+  if (!P) return H2_EINVAL;
+  if (len_A) *len_A = P->lenA;
+  if (len_B) *len_B = P->lenB;
+  return H2_OK;
+}
+
+extern "C" h2_status h2_batch_execute(h2_ctx* ctx, h2_batch* P, const double* A, const double* B, double eps) {
+  if (!ctx || !P) return H2_EINVAL;
+  return guard(ctx, [&] {
+    H2_REQUIRE(P->d_items || P->items.empty(), "h2_batch_execute: plan has no device buffers");
+    H2_REQUIRE((A || P->lenA == 0) && (B || P->lenB == 0), "h2_batch_execute: factors missing");
+    H2_REQUIRE(std::isfinite(eps) && eps >= 0, "h2_batch_execute: eps must be finite and >= 0");
+    DeviceGuard g(ctx->device);
+    execute(ctx, *P, A, B, eps);
+  });
+}
+
+namespace {
+__global__ void k_pack(const Item* items, int ni, const Task* tasks, int nt, int u, ItemBuffers IB,
+                       const int64_t* task_off, const int64_t* item_off, double* res) {
+  // block-stride over tasks then items; one block per object
+  const int o = blockIdx.x;
+  if (o < nt) {
+    const Task tk = tasks[o];
+    const int rt = tk.it >= 0 ? IB.rank[tk.it] : tk.kt;
+    const int rs = tk.is >= 0 ? IB.rank[tk.is] : tk.ls;
+    const double* S = IB.S_out + (size_t)o * kSlot;
+    double* d = res + task_off[o];
+    for (int e = threadIdx.x; e < rt * rs; e += blockDim.x) d[e] = S[(e % rt) + (e / rt) * 32];
+    return;
+  }
+  const int i = o - nt;
+  if (i >= ni) return;
+  const Item it = items[i];
+  const int r = IB.rank[i];
+  if (threadIdx.x == 0) res[i] = (double)r;
+  double* d = res + item_off[i];
+  if (it.flags & kItemLeaf) {
+    const double* Q = IB.Q + it.qoff;
+    for (int e = threadIdx.x; e < it.size * r; e += blockDim.x) d[e] = Q[e];
+    d += (size_t)it.size * (it.k + u);
+  }
+  if (!(it.flags & kItemTreeRoot)) {
+    const int rf = (it.flags & kItemRoot) ? it.kf : IB.rank[it.parent];
+    const double* F = IB.F + (size_t)i * kSlot;
+    for (int e = threadIdx.x; e < r * rf; e += blockDim.x) d[e] = F[(e % r) + (e / r) * 32];
+  }
+}
+}  // namespace
+
+extern "C" h2_status h2_batch_result_size(const h2_batch* P, int64_t* len) {
+  if (!P || !len) return H2_EINVAL;
+  *len = P->res_len;
+  return H2_OK;
+}
+
+extern "C" h2_status h2_batch_execute_host(h2_ctx* ctx, h2_batch* P, const double* A_host, const double* B_host,
+                                           double eps, double* result) {
+  if (!ctx || !P || !result) return H2_EINVAL;
+  return guard(ctx, [&] {
+    H2_REQUIRE((A_host || P->lenA == 0) && (B_host || P->lenB == 0), "h2_batch_execute_host: factors missing");
+    H2_REQUIRE(std::isfinite(eps) && eps >= 0, "h2_batch_execute_host: eps must be finite and >= 0");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = ctx->stream;
+    if (!P->d_A && P->lenA) P->d_A = dalloc<double>(P->lenA);
+    if (!P->d_B && P->lenB) P->d_B = dalloc<double>(P->lenB);
+    if (!P->d_res && P->res_len) {
+      P->d_res = dalloc<double>(P->res_len);
+      P->d_res_task_off = upload(P->res_task_off, st);
+      P->d_res_item_off = upload(P->res_item_off, st);
+    }
+    if (P->lenA) H2_CUDA(cudaMemcpyAsync(P->d_A, A_host, P->lenA * sizeof(double), cudaMemcpyHostToDevice, st));
+    if (P->lenB) H2_CUDA(cudaMemcpyAsync(P->d_B, B_host, P->lenB * sizeof(double), cudaMemcpyHostToDevice, st));
+    execute(ctx, *P, P->d_A, P->d_B, eps);
+    const int nt = (int)P->tasks.size(), ni = (int)P->items.size();
+    if (nt + ni > 0) {
+      k_pack<<<nt + ni, 128, 0, st>>>(P->d_items, ni, P->d_tasks, nt, P->u, P->IB, P->d_res_task_off,
+                                      P->d_res_item_off, P->d_res);
+      H2_CUDA(cudaGetLastError());
+      P->launches += 1;
+    }
+    if (P->res_len)
+      H2_CUDA(cudaMemcpyAsync(result, P->d_res, P->res_len * sizeof(double), cudaMemcpyDeviceToHost, st));
+    H2_CUDA(cudaStreamSynchronize(st));
+    check_device_error(ctx);
+  });
+}
+
+extern "C" h2_status h2_batch_apply(h2_ctx* ctx, const h2_batch* P, int64_t j, const double* A, const double* B,
+                                    h2_matrix* dst) {
+  if (!ctx || !P || !dst || j < 0 || j >= P->count) return H2_EINVAL;
+  return guard(ctx, [&] {
+    H2_REQUIRE(P->executed, "h2_batch_apply: batch not executed");
+    H2_REQUIRE(has_storage(dst), "h2_batch_apply: destination has no device storage");
+    const h2_matrix* Z = P->Z;
+    H2_REQUIRE(dst->rows.count() == Z->rows.count() && dst->blocks.count() == Z->blocks.count(),
+               "h2_batch_apply: destination has another structure");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = ctx->stream;
+    const int64_t i0 = P->upd_item[j], i1 = P->upd_item[j + 1];
+    const int64_t t0 = P->upd_task[j], t1 = P->upd_task[j + 1];
+    std::vector<int32_t> rk(i1 - i0);
+    if (i1 > i0)
+      H2_CUDA(cudaMemcpyAsync(rk.data(), P->IB.rank + i0, (i1 - i0) * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    H2_CUDA(cudaStreamSynchronize(st));
+    check_device_error(ctx);
+    int kmax = 0;
+    for (int32_t r : rk) kmax = std::max(kmax, r);
+    grow_kcap(ctx, dst, kmax);
+    const int kcap = dst->kcap;
+    std::vector<CopyDesc> cd;
+    auto rank_of_item = [&](int32_t id) { return rk[id - i0]; };
+    for (int64_t i = i0; i < i1; ++i) {
+      const Item& it = P->items[i];
+      DeviceBasis& db = basis_of(dst, it.side);
+      const ClusterTree& ct = tree_of(dst, it.side);
+      const int r = rank_of_item((int32_t)i);
+      if ((it.flags & kItemLeaf) && r > 0)
+        cd.push_back({P->IB.Q + it.qoff, db.d_leaf + db.leaf_off[it.cluster], it.size, r, it.size, it.size});
+      if (!(it.flags & kItemTreeRoot)) {
+        const int rf = (it.flags & kItemRoot) ? db.rank[ct.father[it.cluster]] : rank_of_item(it.parent);
+        if (r > 0 && rf > 0)
+          cd.push_back({P->IB.F + (size_t)i * kSlot, db.d_transfer + (size_t)it.cluster * kcap * kcap, r, rf, 32,
+                        kcap});
+      }
+    }
+    for (int64_t t = t0; t < t1; ++t) {
+      const Task& tk = P->tasks[t];
+      const int rt = tk.it >= 0 ? rank_of_item(tk.it) : tk.kt;
+      const int rs = tk.is >= 0 ? rank_of_item(tk.is) : tk.ls;
+      if (rt > 0 && rs > 0)
+        cd.push_back({P->IB.S_out + (size_t)t * kSlot, dst->d_S + (size_t)tk.slot * kcap * kcap, rt, rs, 32, kcap});
+    }
+    // nearfield leaves inside the block
+    std::vector<NearDesc> nd;
+    const BlockTree& bt = Z->blocks;
+    const int32_t b0 = (int32_t)P->blocks[j];
+    std::vector<int32_t> stack{b0};
+    while (!stack.empty()) {
+      const int32_t b = stack.back();
+      stack.pop_back();
+      if (bt.kind[b] == kSub) {
+        for (int i = 3; i >= 0; --i)
+          if (bt.son4[4 * b + i] >= 0) stack.push_back(bt.son4[4 * b + i]);
+      } else if (bt.kind[b] == kNear) {
+        const int32_t t = bt.row[b], s = bt.col[b];
+        const int64_t ro = Z->rows.off[t] - Z->rows.off[bt.row[b0]];
+        const int64_t co = Z->cols.off[s] - Z->cols.off[bt.col[b0]];
+        NearDesc d{};
+        d.N = dst->d_N + dst->near_off[bt.slot[b]];
+        d.A = A + P->offA[j] + ro;
+        d.B = B + P->offB[j] + co;
+        d.rows = (int)Z->rows.size[t];
+        d.cols = (int)Z->cols.size[s];
+        d.ldn = d.rows;
+        d.lda = (int)P->rowsA[j];
+        d.ldb = (int)P->rowsB[j];
+        nd.push_back(d);
+      }
+    }
+    H2_REQUIRE(nd.empty() || (A && B), "h2_batch_apply: factors needed for the nearfield part");
+    CopyDesc* dcd = upload(cd, st);
+    NearDesc* dnd = upload(nd, st);
+    launch_copy(dcd, (int)cd.size(), st);
+    launch_near_add(dnd, (int)nd.size(), P->u, st);
+    H2_CUDA(cudaGetLastError());
+    for (int64_t i = i0; i < i1; ++i) {
+      const Item& it = P->items[i];
+      basis_of(dst, it.side).rank[it.cluster] = rank_of_item((int32_t)i);
+    }
+    sync_ranks(dst->V, st);
+    sync_ranks(dst->W, st);
+    H2_CUDA(cudaStreamSynchronize(st));
+    dfree(dcd);
+    dfree(dnd);
+  });
+}
+
+namespace {
+
+// Algorithmic float64 flops per phase of the last execution (standard
+// counts: Householder QR 2mn^2 - 2n^3/3, products 2mnk with triangular
+// factors halved, one-sided Jacobi 6m per pair checked plus 6m per
+// rotation as counted on the device).
+void phase_flops(h2_ctx* ctx, const h2_batch* P, double f[H2_PHASE_COUNT]) {
+  for (int ph = 0; ph < H2_PHASE_COUNT; ++ph) f[ph] = 0.0;
+  const size_t ni = P->items.size();
+  std::vector<unsigned long long> jac(2 * ni);
+  std::vector<int32_t> rk(ni);
+  if (ni) {
+    H2_CUDA(cudaMemcpyAsync(jac.data(), P->IB.jac, 2 * ni * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                            ctx->stream));
+    H2_CUDA(cudaMemcpyAsync(rk.data(), P->IB.rank, ni * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  H2_CUDA(cudaStreamSynchronize(ctx->stream));
+  const double u = P->u;
+  auto qr = [](double m, double n) {
+    return m >= n ? 2 * m * n * n - 2.0 / 3.0 * n * n * n : 2 * n * m * m - 2.0 / 3.0 * m * m * m;
+  };
+  const h2_matrix* Z = P->Z;
+  for (int sd = 0; sd < 2; ++sd) {
+    const ClusterTree& ct = tree_of(Z, sd);
+    const DeviceBasis& bs = basis_of(Z, sd);
+    const DeviceBasis& o = basis_of(Z, 1 - sd);
+    const std::vector<int32_t>& ptr = sd == 0 ? Z->blocks.row_ptr : Z->blocks.col_ptr;
+    const std::vector<int32_t>& adm = sd == 0 ? Z->blocks.row_adm : Z->blocks.col_adm;
+    for (int32_t c = 0; c < ct.count(); ++c) {
+      const double k = bs.rank[c];
+      double rows = 0;
+      for (int32_t e = ptr[c]; e < ptr[c + 1]; ++e) {
+        const int32_t blk = Z->blocks.adm[adm[e]];
+        const double l = o.rank[sd == 0 ? Z->blocks.col[blk] : Z->blocks.row[blk]];
+        rows += l;
+        f[H2_PHASE_BASE_WEIGHTS] += 2 * k * l;
+      }
+      f[H2_PHASE_BASE_WEIGHTS] += qr(rows, k);
+      if (ct.father[c] >= 0) {
+        const double kf = bs.rank[ct.father[c]];
+        f[H2_PHASE_BASE_WEIGHTS] += kf * kf * k + qr(kf + k, k);
+      }
+    }
+  }
+  for (const NormTask& nt : P->norms) {
+    const double Kt = P->items[nt.it].k + u, Ks = P->items[nt.is].k + u;
+    f[H2_PHASE_NORMS] += 2 * P->items[nt.it].k * P->items[nt.is].k * Ks + Kt * Kt * Ks + 2 * Kt * Ks;
+  }
+  for (size_t i = 0; i < ni; ++i) {
+    const Item& it = P->items[i];
+    const double k = it.k, K = it.k + u;
+    if (it.flags & kItemLeaf) {
+      f[H2_PHASE_RFACTOR] += qr(it.size, K);
+    } else {
+      const double k0 = P->items[it.son0].k, k1 = P->items[it.son1].k;
+      f[H2_PHASE_RFACTOR] += (k0 + u) * k0 * k + (k1 + u) * k1 * k + qr(k0 + k1 + 2 * u, K);
+    }
+    // weights: stack rows folded into the K x K factor
+    double rows = 0;
+    if (!(it.flags & kItemInside)) {
+      rows += k;
+    } else {
+      for (int32_t e = it.ent_begin; e < it.ent_end; ++e) {
+        const Entry& en = P->ents[e];
+        if (en.other < 0) {
+          const double l = basis_of(Z, 1 - it.side).rank[en.other_cluster];
+          rows += l;
+          f[H2_PHASE_WEIGHTS] += 2 * k * l;
+        } else {
+          const double l = P->items[en.other].k;
+          rows += l + u;
+          f[H2_PHASE_WEIGHTS] += (l + u) * l * k;
+        }
+      }
+    }
+    if (!(it.flags & kItemTreeRoot)) {
+      const double kf = (it.flags & kItemRoot) ? it.kf : it.kf + u;
+      f[H2_PHASE_WEIGHTS] += kf * it.kf * k;
+      rows += kf;
+    }
+    f[H2_PHASE_WEIGHTS] += 2 * K * K * rows;   // fold of `rows` rows into an upper K x K factor
+    // truncation
+    const double m = (it.flags & kItemLeaf) ? it.size : rk[it.son0] + rk[it.son1];
+    double ft = 0;
+    if (!(it.flags & kItemLeaf)) {
+      const double k0 = P->items[it.son0].k, k1 = P->items[it.son1].k;
+      ft += 2 * rk[it.son0] * k0 * k + 2 * rk[it.son1] * k1 * k;
+    }
+    ft += m * K * K;                                               // V^ times triangular B~^*
+    ft += 6.0 * m * (double)jac[2 * i] + 6.0 * m * (double)jac[2 * i + 1];
+    ft += 2 * m * K * rk[i];                                       // R_t = Q^* V^
+    if ((it.flags & kItemRoot) && !(it.flags & kItemTreeRoot)) ft += 2 * rk[i] * k * it.kf;
+    f[H2_PHASE_TRUNCATE] += ft;
+  }
+  for (const Task& tk : P->tasks) {
+    if (tk.it >= 0 && tk.is >= 0)
+      f[H2_PHASE_REPROJECT] += 2.0 * (tk.kt + u) * tk.ls * rk[tk.is] + 2.0 * rk[tk.it] * (tk.kt + u) * rk[tk.is];
+    else if (tk.it >= 0)
+      f[H2_PHASE_REPROJECT] += 2.0 * rk[tk.it] * tk.kt * tk.ls;
+    else
+      f[H2_PHASE_REPROJECT] += 2.0 * tk.kt * tk.ls * rk[tk.is];
+  }
+}
+
+}  // namespace
+
+extern "C" h2_status h2_batch_stats(h2_ctx* ctx, const h2_batch* P, int64_t* n_cluster_tasks,
+                                    int64_t* n_block_tasks, int64_t* n_launches, double* flops) {
+  if (!P) return H2_EINVAL;
+  return guard(ctx, [&] {
+    if (n_cluster_tasks) *n_cluster_tasks = (int64_t)P->items.size();
+    if (n_block_tasks) *n_block_tasks = (int64_t)P->tasks.size();
+    if (n_launches) *n_launches = P->launches;
+    if (!flops) return;
+    H2_REQUIRE(ctx && P->executed, "h2_batch_stats: flops need an executed batch and a context");
+    DeviceGuard g(ctx->device);
+    double f[H2_PHASE_COUNT];
+    phase_flops(ctx, P, f);
+    double tot = 0;
+    for (double x : f) tot += x;
+    *flops = tot;
+  });
+}
+
+extern "C" h2_status h2_batch_set_timing(h2_batch* P, int on) {
+  if (!P) return H2_EINVAL;
+  return guard(nullptr, [&] {
+    if (on && !P->ev[0]) {
+      DeviceGuard g(P->device);
+      for (cudaEvent_t& e : P->ev) H2_CUDA(cudaEventCreate(&e));
+    }
+    P->timing = on != 0;
+  });
+}
+
+extern "C" h2_status h2_batch_phase_stats(h2_ctx* ctx, const h2_batch* P, int phase, int64_t* launches,
+                                          double* ms, double* flops) {
+  if (!ctx || !P || phase < 0 || phase >= H2_PHASE_COUNT) return H2_EINVAL;
+  return guard(ctx, [&] {
+    H2_REQUIRE(P->executed, "h2_batch_phase_stats: batch not executed");
+    DeviceGuard g(ctx->device);
+    if (launches) *launches = P->phase_launches[phase];
+    if (ms) {
+      *ms = -1.0;
+      if (P->timing && P->ev[0]) {
+        H2_CUDA(cudaEventSynchronize(P->ev[phase + 1]));
+        float t = 0;
+        H2_CUDA(cudaEventElapsedTime(&t, P->ev[phase], P->ev[phase + 1]));
+        *ms = t;
+      }
+    }
+    if (flops) {
+      double f[H2_PHASE_COUNT];
+      phase_flops(ctx, P, f);
+      *flops = f[phase];
+    }
+  });
+}
+
+// ============================================================ single update
+extern "C" h2_status h2_lowrank_update(h2_ctx* ctx, h2_matrix* Z, int64_t block, int u, const double* A,
+                                       int64_t lda, const double* B, int64_t ldb, double eps) {
+  if (!ctx || !Z || !A || !B) return H2_EINVAL;
+  return guard(ctx, [&] {
+    H2_REQUIRE(block >= 0 && block < Z->blocks.count(), "h2_lowrank_update: block out of range");
+    const int64_t rows = Z->rows.size[Z->blocks.row[block]];
+    const int64_t cols = Z->cols.size[Z->blocks.col[block]];
+    H2_REQUIRE(lda >= rows && ldb >= cols, "h2_lowrank_update: leading dimension too small");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = ctx->stream;
+    h2_batch* P = nullptr;
+    h2_status s = h2_batch_create(ctx, Z, 1, &block, u, &P);
+    if (s != H2_OK) throw Error(s, ctx->last_error);
+    std::unique_ptr<h2_batch, void (*)(h2_batch*)> hold(P, h2_batch_free);
+    double* dA = dalloc<double>(rows * u);
+    double* dB = dalloc<double>(cols * u);
+    H2_CUDA(cudaMemcpy2DAsync(dA, rows * sizeof(double), A, lda * sizeof(double), rows * sizeof(double), u,
+                              cudaMemcpyDeviceToDevice, st));
+    H2_CUDA(cudaMemcpy2DAsync(dB, cols * sizeof(double), B, ldb * sizeof(double), cols * sizeof(double), u,
+                              cudaMemcpyDeviceToDevice, st));
+    try {
+      execute(ctx, *P, dA, dB, eps);
+      s = h2_batch_apply(ctx, P, 0, dA, dB, Z);
+      if (s != H2_OK) throw Error(s, ctx->last_error);
+    } catch (...) {
+      cudaStreamSynchronize(st);
+      dfree(dA);
+      dfree(dB);
+      throw;
+    }
+    H2_CUDA(cudaStreamSynchronize(st));
+    dfree(dA);
+    dfree(dB);
+  });
+}

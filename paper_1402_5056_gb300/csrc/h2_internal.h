@@ -1,0 +1,111 @@
+// Internal declarations of libh2gb (host C++ and CUDA).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/h2gb.h"
+
+namespace h2 {
+
+// Largest supported extended rank k_t + u (one warp lane per column).
+constexpr int kMaxCols = 32;
+
+struct Error : std::runtime_error {
+  h2_status code;
+  Error(h2_status c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define H2_CUDA(call)                                                              \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess)                                                         \
+      throw ::h2::Error(H2_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define H2_REQUIRE(cond, msg) \
+  do {                        \
+    if (!(cond)) throw ::h2::Error(H2_EINVAL, msg); \
+  } while (0)
+
+// ----------------------------------------------------------------- trees
+struct ClusterTree {
+  int64_t n = 0;
+  int dim = 0;
+  std::vector<int64_t> perm;            // tree position -> original index
+  std::vector<int64_t> off, size;       // per cluster, tree order
+  std::vector<int32_t> father, son0, son1, level, subtree;
+  std::vector<double> lo, hi;           // dim per cluster (padded boxes)
+  int depth = 0;
+  int max_leaf = 0;
+  int32_t count() const { return (int32_t)off.size(); }
+  bool leaf(int32_t c) const { return son0[c] < 0; }
+};
+
+enum BlockKind : int32_t { kSub = 0, kAdm = 1, kNear = 2 };
+
+struct BlockTree {
+  std::vector<int32_t> row, col, kind, father;
+  std::vector<int32_t> son4;       // 4 entries per block (-1 where absent), order (t1,s1),(t1,s2),(t2,s1),(t2,s2)
+  std::vector<int32_t> slot;       // admissible: coupling slot; near: nearfield slot; sub: -1
+  std::vector<int32_t> adm, near;  // block ids of the leaves, in block order
+  // admissible slots by row cluster and by column cluster (CSR)
+  std::vector<int32_t> row_ptr, row_adm, col_ptr, col_adm;
+  int32_t count() const { return (int32_t)row.size(); }
+};
+
+void build_cluster_tree(const double* pts, int64_t n, int dim, int leaf_size, double pad,
+                        ClusterTree& ct);
+void build_block_tree(const ClusterTree& rt, const ClusterTree& ct, double eta, BlockTree& bt);
+
+// --------------------------------------------------------------- storage
+// One cluster basis on the device.  Leaf matrices: size_t x kcap slots with
+// leading dimension size_t; transfers: kcap x kcap slots (ld kcap).
+struct DeviceBasis {
+  std::vector<int32_t> rank;       // host copy of the ranks
+  int32_t* d_rank = nullptr;
+  double* d_leaf = nullptr;        // concatenated leaf slots
+  double* d_transfer = nullptr;    // n_clusters slots of kcap*kcap
+  std::vector<int64_t> leaf_off;   // per cluster (leaves), element offset
+  int64_t* d_leaf_off = nullptr;
+};
+
+}  // namespace h2
+
+struct h2_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string last_error;
+  int* d_error = nullptr;          // device error word (0 = fine)
+};
+
+struct h2_matrix {
+  h2::ClusterTree rows, cols;      // row and column trees (identical index sets here)
+  h2::BlockTree blocks;
+  int kcap = 0;
+  int device = 0;
+  h2::DeviceBasis V, W;
+  double* d_S = nullptr;           // n_adm slots of kcap*kcap (ld kcap)
+  double* d_N = nullptr;           // nearfield, concatenated size_t x size_s
+  std::vector<int64_t> near_off;   // per nearfield slot
+  int64_t near_len = 0;
+  // device copies of the structure needed by kernels
+  int64_t* d_row_off = nullptr;    // cluster offsets (tree order), row tree
+  int64_t* d_col_off = nullptr;
+  int32_t* d_row_size = nullptr;
+  int32_t* d_col_size = nullptr;
+  int32_t* d_subtree_r = nullptr;
+  int32_t* d_subtree_c = nullptr;
+  int32_t* d_blk_row = nullptr;    // per admissible slot: row / col cluster
+  int32_t* d_blk_col = nullptr;
+  int32_t* d_row_ptr = nullptr;    // CSR admissible slots by row cluster
+  int32_t* d_row_adm = nullptr;
+  int32_t* d_col_ptr = nullptr;
+  int32_t* d_col_adm = nullptr;
+  int32_t* d_father_r = nullptr;
+  int32_t* d_father_c = nullptr;
+};

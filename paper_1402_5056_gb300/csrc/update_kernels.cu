@@ -1,0 +1,776 @@
+// Batched FP64 kernels of the H^2 local low-rank update (Sections 4 and 5).
+//
+// Execution model: one warp per cluster task ("item") or per coupling
+// task; lane c owns column c of every small matrix (at most 32 columns),
+// so Householder reflections and Jacobi rotations are column operations
+// without cross-lane reductions.  All clusters of one tree level of every
+// update of the batch go into one launch; the host walks the levels
+// bottom-up (R-factors, truncation) or top-down (weights).
+#include <cfloat>
+#include <cstdio>
+
+#include "h2_internal.h"
+#include "update_kernels.h"
+
+namespace h2 {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kLdr = 33;          // leading dimension of R tiles in shared memory
+constexpr int kCh = 32;           // rows per folded chunk
+constexpr int kMaxSweeps = 40;
+
+__device__ __forceinline__ void flag(int* err, int code) { atomicOr(err, code); }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+// R (ncol x ncol, upper triangular, shared, ld kLdr) <- R-factor of [R; X].
+// X has `ch` rows; lane c < ncol holds column c of X in x[].  Householder
+// reflections in the LAPACK dlarfg convention; R keeps ncol rows (rows
+// beyond the rank stay zero).
+__device__ void fold(double* R, double (&x)[kCh], int ch, int ncol, double* vb, int lane) {
+  for (int j = 0; j < ncol; ++j) {
+    if (lane == j) {
+      double s2 = 0.0;
+#pragma unroll
+      for (int i = 0; i < kCh; ++i)
+        if (i < ch) s2 = fma(x[i], x[i], s2);
+      double tau = 0.0;
+      if (s2 > 0.0) {
+        const double alpha = R[j + j * kLdr];
+        const double nrm = sqrt(fma(alpha, alpha, s2));
+        const double beta = alpha >= 0.0 ? -nrm : nrm;
+        tau = (beta - alpha) / beta;
+        const double sc = 1.0 / (alpha - beta);
+#pragma unroll
+        for (int i = 0; i < kCh; ++i)
+          if (i < ch) {
+            vb[i] = x[i] * sc;
+            x[i] = 0.0;
+          }
+        R[j + j * kLdr] = beta;
+      }
+      vb[kCh] = tau;
+    }
+    __syncwarp();
+    const double tau = vb[kCh];
+    if (tau != 0.0 && lane > j && lane < ncol) {
+      double w = R[j + lane * kLdr];
+#pragma unroll
+      for (int i = 0; i < kCh; ++i)
+        if (i < ch) w = fma(vb[i], x[i], w);
+      w *= tau;
+      R[j + lane * kLdr] -= w;
+#pragma unroll
+      for (int i = 0; i < kCh; ++i)
+        if (i < ch) x[i] = fma(-w, vb[i], x[i]);
+    }
+    __syncwarp();
+  }
+}
+
+__device__ __forceinline__ void zero_tile(double* R, int lane) {
+  for (int c = 0; c < 32; ++c) R[lane + c * kLdr] = 0.0;
+  __syncwarp();
+}
+
+// Copy the ncol x ncol upper part of a shared R tile to a global 32x32 slot.
+__device__ __forceinline__ void store_tile(double* dst, const double* R, int ncol, int lane) {
+  __syncwarp();
+  if (lane < ncol)
+    for (int i = 0; i < 32; ++i) dst[i + lane * 32] = (i < ncol) ? R[i + lane * kLdr] : 0.0;
+  __syncwarp();
+}
+
+// One-sided (Hestenes) Jacobi on the columns held by the lanes (a[] rows
+// valid): on return the columns are U * Sigma with mutually orthogonal
+// columns.  Round-robin pairing; both lanes of a pair evaluate the same
+// dot products in the same order, so they take the same rotation.
+template <int MR>
+__device__ void jacobi(double (&a)[MR], int rows, int ncol, int lane, unsigned long long* cnt,
+                       int* err) {
+  const int n2 = ncol + (ncol & 1);
+  const int nr = n2 - 1;
+  const double tol = 16.0 * DBL_EPSILON;
+  unsigned long long pairs = 0, rots = 0;
+  bool converged = (ncol < 2);
+  for (int sweep = 0; sweep < kMaxSweeps && !converged; ++sweep) {
+    int any = 0;
+    for (int r = 0; r < nr; ++r) {
+      int p;
+      if (lane >= n2) {
+        p = lane;
+      } else if (lane == nr) {
+        p = r;
+      } else if (lane == r) {
+        p = nr;
+      } else {
+        p = (2 * r - lane) % nr;
+        if (p < 0) p += nr;
+      }
+      const bool lo = lane < p;
+      double al = 0.0, be = 0.0, ga = 0.0;
+#pragma unroll
+      for (int i = 0; i < MR; ++i)
+        if (i < rows) {
+          const double o = __shfl_sync(kFull, a[i], p);
+          const double xx = lo ? a[i] : o;
+          const double yy = lo ? o : a[i];
+          al = fma(xx, xx, al);
+          be = fma(yy, yy, be);
+          ga = fma(xx, yy, ga);
+        }
+      const bool active = lane < n2 && p != lane;
+      const bool rot = active && al > 0.0 && be > 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be);
+      double c = 1.0, s = 0.0;
+      if (rot) {
+        const double zeta = (be - al) / (2.0 * ga);
+        const double t = copysign(1.0, zeta) / (fabs(zeta) + hypot(1.0, zeta));
+        c = 1.0 / sqrt(fma(t, t, 1.0));
+        s = c * t;
+      }
+#pragma unroll
+      for (int i = 0; i < MR; ++i)
+        if (i < rows) {
+          const double o = __shfl_sync(kFull, a[i], p);
+          if (rot) a[i] = lo ? fma(c, a[i], -s * o) : fma(s, o, c * a[i]);
+        }
+      if (active && lo) {
+        pairs += 1;
+        rots += rot ? 1 : 0;
+      }
+      any |= rot ? 1 : 0;
+    }
+    converged = !__any_sync(kFull, any);
+  }
+  if (!converged && lane == 0) flag(err, kErrJacobi);
+  // per-item counters (pairs checked, rotations) for the flop statistics
+  unsigned long long ps = pairs, rs = rots;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    ps += __shfl_xor_sync(kFull, ps, o);
+    rs += __shfl_xor_sync(kFull, rs, o);
+  }
+  if (lane == 0 && cnt) {
+    cnt[0] = ps;
+    cnt[1] = rs;
+  }
+}
+
+// --------------------------------------------------------------- prepass
+// Weights of the unchanged matrix for every cluster of one level (Section
+// 4, Algorithm of the weight matrices):
+//   G_t  = qr_R([omega_b S_b^* for b in row(t)])
+//   B~_t = qr_R([G_t; B~_{t+} E_t^*])
+// omega_b = sqrt(#T_t) / ||S_b||_F (block-relative reading).  Column side:
+// the same with S_b instead of S_b^* and col(s).
+__global__ void k_prepass(MatView M, int side, const int32_t* __restrict__ clusters, int n,
+                          const int32_t* __restrict__ ptr, const int32_t* __restrict__ adm,
+                          const int32_t* __restrict__ other_cl, BaseWeights BW, int* err) {
+  extern __shared__ double smem[];
+  const int lane = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5;
+  const int idx = blockIdx.x * (blockDim.x >> 5) + w;
+  if (idx >= n) return;
+  double* R = smem + w * (32 * kLdr + kCh + 1);
+  double* vb = R + 32 * kLdr;
+  const int c = clusters[idx];
+  const int k = M.rank[side][c];
+  const int kcap = M.kcap;
+  if (k > 32) {
+    if (lane == 0) flag(err, kErrCols);
+    return;
+  }
+  zero_tile(R, lane);
+  const double st = sqrt((double)M.subtree[side][c]);
+  double x[kCh];
+  for (int e = ptr[c]; e < ptr[c + 1]; ++e) {
+    const int slot = adm[e];
+    const int o = other_cl[slot];
+    const int l = M.rank[1 - side][o];
+    const double* S = M.S + (size_t)slot * kcap * kcap;
+    // ||S_b||_F
+    double part = 0.0;
+    const int scols = side == 0 ? l : k;
+    const int srows = side == 0 ? k : l;
+    if (lane < scols)
+      for (int i = 0; i < srows; ++i) {
+        const double v = S[i + lane * kcap];
+        part = fma(v, v, part);
+      }
+    const double nrm = sqrt(warp_sum(part));
+    const double om = nrm > 0.0 ? st / nrm : 0.0;
+    // rows of the stack: side 0 -> S^* (l x k), side 1 -> S (l x k); l = other side's rank
+    const int ch = l;
+#pragma unroll
+    for (int i = 0; i < kCh; ++i) {
+      double v = 0.0;
+      if (i < ch && lane < k) v = side == 0 ? S[lane + i * kcap] : S[i + lane * kcap];
+      x[i] = om * v;
+    }
+    fold(R, x, ch, k, vb, lane);
+  }
+  store_tile(BW.G[side] + (size_t)c * kSlot, R, k, lane);
+  const int f = M.father[side][c];
+  if (f >= 0) {
+    const int kf = M.rank[side][f];
+    const double* P = BW.B[side] + (size_t)f * kSlot;
+    const double* E = M.transfer[side] + (size_t)c * kcap * kcap;   // k x kf
+#pragma unroll
+    for (int i = 0; i < kCh; ++i) {
+      double v = 0.0;
+      if (i < kf && lane < k)
+        for (int q = 0; q < kf; ++q) v = fma(P[i + q * 32], E[lane + q * kcap], v);
+      x[i] = v;
+    }
+    fold(R, x, kf, k, vb, lane);
+  }
+  store_tile(BW.B[side] + (size_t)c * kSlot, R, k, lane);
+}
+
+// ------------------------------------------------------------- step 2
+// Basis R-factors bottom-up: leaf qr_R((V_t, F|_t)); inner
+// qr_R([R_{t1} E~_{t1}; R_{t2} E~_{t2}]) with E~ = diag(E, I_u).
+__global__ void k_rfactor(MatView M, const Item* __restrict__ items, const int32_t* __restrict__ list,
+                          int n, int u, const double* __restrict__ A, const double* __restrict__ B,
+                          ItemBuffers IB, int* err) {
+  extern __shared__ double smem[];
+  const int lane = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5;
+  const int idx = blockIdx.x * (blockDim.x >> 5) + w;
+  if (idx >= n) return;
+  double* R = smem + w * (32 * kLdr + kCh + 1);
+  double* vb = R + 32 * kLdr;
+  const int id = list[idx];
+  const Item it = items[id];
+  const int side = it.side;
+  const int k = it.k;
+  const int K = k + u;
+  if (K > 32) {
+    if (lane == 0) flag(err, kErrCols);
+    return;
+  }
+  zero_tile(R, lane);
+  double x[kCh];
+  if (it.flags & kItemLeaf) {
+    const double* V = M.leaf[side] + M.leaf_off[side][it.cluster];
+    const double* F = (side == 0 ? A : B) + it.foff;
+    const int m = it.size;
+    for (int r0 = 0; r0 < m; r0 += kCh) {
+      const int ch = min(kCh, m - r0);
+#pragma unroll
+      for (int i = 0; i < kCh; ++i) {
+        double v = 0.0;
+        if (i < ch) {
+          if (lane < k)
+            v = V[(r0 + i) + lane * m];
+          else if (lane < K)
+            v = F[(it.rowoff + r0 + i) + (size_t)(lane - k) * it.ld];
+        }
+        x[i] = v;
+      }
+      fold(R, x, ch, K, vb, lane);
+    }
+  } else {
+    const int sons[2] = {it.son0, it.son1};
+    for (int si = 0; si < 2; ++si) {
+      const Item sn = items[sons[si]];
+      const int ks = sn.k;
+      const int Ks = ks + u;
+      const double* Rs = IB.Rq + (size_t)sons[si] * kSlot;
+      const double* E = M.transfer[side] + (size_t)sn.cluster * M.kcap * M.kcap;   // ks x k
+#pragma unroll
+      for (int i = 0; i < kCh; ++i) {
+        double v = 0.0;
+        if (i < Ks) {
+          if (lane < k) {
+            for (int q = 0; q < ks; ++q) v = fma(Rs[i + q * 32], E[q + lane * M.kcap], v);
+          } else if (lane < K) {
+            v = Rs[i + (ks + lane - k) * 32];
+          }
+        }
+        x[i] = v;
+      }
+      fold(R, x, Ks, K, vb, lane);
+    }
+  }
+  store_tile(IB.Rq + (size_t)id * kSlot, R, K, lane);
+}
+
+// Norms ||R_t S~_b R_s^*||_F of the blocks inside the update (both sides
+// extended), needed for omega_b.
+__global__ void k_norms(MatView M, const Item* __restrict__ items, const NormTask* __restrict__ tasks,
+                        int n, int u, ItemBuffers IB) {
+  const int lane = threadIdx.x & 31;
+  const int idx = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (idx >= n) return;
+  const NormTask tk = tasks[idx];
+  const Item it = items[tk.it];
+  const Item is = items[tk.is];
+  const int kt = it.k, ls = is.k;
+  const int Kt = kt + u, Ks = ls + u;
+  const double* S = M.S + (size_t)tk.slot * M.kcap * M.kcap;
+  const double* Rt = IB.Rq + (size_t)tk.it * kSlot;
+  const double* Rs = IB.Rq + (size_t)tk.is * kSlot;
+  double part = 0.0;
+  if (lane < Ks) {
+    // T[:, lane] = S~ R_s^*[:, lane] = S~ * row `lane` of R_s
+    double T[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      double v = 0.0;
+      if (i < kt) {
+        for (int q = 0; q < ls; ++q) v = fma(S[i + q * M.kcap], Rs[lane + q * 32], v);
+      } else if (i < Kt) {
+        v = Rs[lane + (ls + i - kt) * 32];
+      }
+      T[i] = v;
+    }
+    for (int p = 0; p < Kt; ++p) {
+      double y = 0.0;
+#pragma unroll
+      for (int i = 0; i < 32; ++i)
+        if (i >= p && i < Kt) y = fma(Rt[p + i * 32], T[i], y);
+      part = fma(y, y, part);
+    }
+  }
+  const double s = warp_sum(part);
+  if (lane == 0) IB.norms[idx] = sqrt(s);
+}
+
+// ------------------------------------------------------------- step 3
+// Weights top-down: B~_t = qr_R([omega_b R_{W,s} S~_b^* for s in row(t);
+// B~_{t+} E~_t^*]).  Blocks outside the update enter through the
+// precomputed G_t when no block of row(t) lies inside the update.
+__global__ void k_weights(MatView M, const Item* __restrict__ items, const Entry* __restrict__ ents,
+                          const int32_t* __restrict__ list, int n, int u, BaseWeights BW,
+                          ItemBuffers IB, int* err) {
+  extern __shared__ double smem[];
+  const int lane = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5;
+  const int idx = blockIdx.x * (blockDim.x >> 5) + w;
+  if (idx >= n) return;
+  double* R = smem + w * (32 * kLdr + kCh + 1);
+  double* vb = R + 32 * kLdr;
+  const int id = list[idx];
+  const Item it = items[id];
+  const int side = it.side;
+  const int k = it.k;
+  const int K = k + u;
+  const int kcap = M.kcap;
+  zero_tile(R, lane);
+  double x[kCh];
+  const double st = sqrt((double)M.subtree[side][it.cluster]);
+  if (!(it.flags & kItemInside)) {
+    const double* G = BW.G[side] + (size_t)it.cluster * kSlot;
+    if (lane < k)
+      for (int i = 0; i <= lane; ++i) R[i + lane * kLdr] = G[i + lane * 32];
+    __syncwarp();
+  } else {
+    for (int e = it.ent_begin; e < it.ent_end; ++e) {
+      const Entry en = ents[e];
+      const double* S = M.S + (size_t)en.slot * kcap * kcap;
+      if (en.other < 0) {
+        const int l = M.rank[1 - side][en.other_cluster];
+        double part = 0.0;
+        const int scols = side == 0 ? l : k;
+        const int srows = side == 0 ? k : l;
+        if (lane < scols)
+          for (int i = 0; i < srows; ++i) {
+            const double v = S[i + lane * kcap];
+            part = fma(v, v, part);
+          }
+        const double nrm = sqrt(warp_sum(part));
+        const double om = nrm > 0.0 ? st / nrm : 0.0;
+        const int ch = l;
+#pragma unroll
+        for (int i = 0; i < kCh; ++i) {
+          double v = 0.0;
+          if (i < ch && lane < k) v = side == 0 ? S[lane + i * kcap] : S[i + lane * kcap];
+          x[i] = om * v;
+        }
+        fold(R, x, ch, K, vb, lane);
+      } else {
+        const Item ot = items[en.other];
+        const int l = ot.k;
+        const int Ko = l + u;
+        const double nrm = IB.norms[en.norm];
+        const double om = nrm > 0.0 ? st / nrm : 0.0;
+        const double* Ro = IB.Rq + (size_t)en.other * kSlot;
+#pragma unroll
+        for (int i = 0; i < kCh; ++i) {
+          double v = 0.0;
+          if (i < Ko) {
+            if (lane < k) {
+              // side 0: (R_W,s S~^*)[i, lane] = sum_q R[i,q] S[lane,q]
+              // side 1: (R_V,t S~)[i, lane]   = sum_q R[i,q] S[q,lane]
+              for (int q = i; q < l; ++q)
+                v = fma(Ro[i + q * 32], side == 0 ? S[lane + q * kcap] : S[q + lane * kcap], v);
+            } else if (lane < K) {
+              v = Ro[i + (l + lane - k) * 32];
+            }
+          }
+          x[i] = om * v;
+        }
+        fold(R, x, Ko, K, vb, lane);
+      }
+    }
+  }
+  // father's part
+  if (it.flags & kItemRoot) {
+    if (!(it.flags & kItemTreeRoot)) {
+      const int f = M.father[side][it.cluster];
+      const int kf = it.kf;
+      const double* P = BW.B[side] + (size_t)f * kSlot;
+      const double* E = M.transfer[side] + (size_t)it.cluster * kcap * kcap;   // k x kf
+#pragma unroll
+      for (int i = 0; i < kCh; ++i) {
+        double v = 0.0;
+        if (i < kf && lane < k)
+          for (int q = i; q < kf; ++q) v = fma(P[i + q * 32], E[lane + q * kcap], v);
+        x[i] = v;
+      }
+      fold(R, x, kf, K, vb, lane);
+    }
+  } else {
+    const Item pt = items[it.parent];
+    const int kf = pt.k;
+    const int Kf = kf + u;
+    const double* P = IB.Bw + (size_t)it.parent * kSlot;
+    const double* E = M.transfer[side] + (size_t)it.cluster * kcap * kcap;   // k x kf
+#pragma unroll
+    for (int i = 0; i < kCh; ++i) {
+      double v = 0.0;
+      if (i < Kf) {
+        if (lane < k) {
+          for (int q = i; q < kf; ++q) v = fma(P[i + q * 32], E[lane + q * kcap], v);
+        } else if (lane < K) {
+          v = P[i + (kf + lane - k) * 32];
+        }
+      }
+      x[i] = v;
+    }
+    fold(R, x, Kf, K, vb, lane);
+  }
+  store_tile(IB.Bw + (size_t)id * kSlot, R, K, lane);
+  (void)err;
+}
+
+// ------------------------------------------------------------- step 4
+// Truncation bottom-up: SVD of V^_t B~_t^* (leaf: V^_t = V~_t) by one-sided
+// Jacobi, rank by the block-relative rule sum_{i>r} sigma_i^2 <= (eps/2)^2,
+// Q^_t from the leading left singular vectors, R_t = Q^_t^* V^_t; the rows
+// of Q^_t become the sons' new transfer matrices (Eq. (Qt_nested)), and the
+// subtree root commits E_t0 <- R_t0 [E_t0; 0].
+template <int MR>
+__global__ void k_truncate(MatView M, const Item* __restrict__ items, const int32_t* __restrict__ list,
+                           int n, int u, int kl, double eps, const double* __restrict__ A,
+                           const double* __restrict__ B, ItemBuffers IB, int* err) {
+  extern __shared__ double smem[];
+  const int lane = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5;
+  const int idx = blockIdx.x * (blockDim.x >> 5) + w;
+  if (idx >= n) return;
+  double* Vh = smem + (size_t)w * (2 * MR * kl);
+  double* Qs = Vh + MR * kl;
+  const int id = list[idx];
+  const Item it = items[id];
+  const int side = it.side;
+  const int k = it.k;
+  const int K = k + u;
+  const int kcap = M.kcap;
+  if (K > kl) {
+    if (lane == 0) flag(err, kErrCols);
+    return;
+  }
+  int rows = 0;
+  int r1 = 0, r2 = 0;
+  if (it.flags & kItemLeaf) {
+    rows = it.size;
+  } else {
+    r1 = IB.rank[it.son0];
+    r2 = IB.rank[it.son1];
+    rows = r1 + r2;
+  }
+  if (rows > MR) {
+    if (lane == 0) flag(err, kErrRows);
+    return;
+  }
+  // V^_t into shared memory (ld MR), one column per lane
+  if (it.flags & kItemLeaf) {
+    const double* V = M.leaf[side] + M.leaf_off[side][it.cluster];
+    const double* F = (side == 0 ? A : B) + it.foff;
+    if (lane < K)
+      for (int i = 0; i < rows; ++i)
+        Vh[i + lane * MR] = lane < k ? V[i + lane * rows] : F[(it.rowoff + i) + (size_t)(lane - k) * it.ld];
+  } else {
+    const int sons[2] = {it.son0, it.son1};
+    int row0 = 0;
+    for (int si = 0; si < 2; ++si) {
+      const Item sn = items[sons[si]];
+      const int ks = sn.k;
+      const int rs = si == 0 ? r1 : r2;
+      const double* Rt = IB.Rt + (size_t)sons[si] * kSlot;
+      const double* E = M.transfer[side] + (size_t)sn.cluster * kcap * kcap;   // ks x k
+      if (lane < K)
+        for (int p = 0; p < rs; ++p) {
+          double v = 0.0;
+          if (lane < k) {
+            for (int q = 0; q < ks; ++q) v = fma(Rt[p + q * 32], E[q + lane * kcap], v);
+          } else {
+            v = Rt[p + (ks + lane - k) * 32];
+          }
+          Vh[row0 + p + lane * MR] = v;
+        }
+      row0 += rs;
+    }
+  }
+  __syncwarp();
+  // M = V^ B~^*, column `lane` = V^ * row `lane` of B~
+  const double* Bw = IB.Bw + (size_t)id * kSlot;
+  double a[MR];
+#pragma unroll
+  for (int i = 0; i < MR; ++i) a[i] = 0.0;
+  if (lane < K)
+    for (int q = lane; q < K; ++q) {   // B~ is upper triangular: B~[lane, q] = 0 for q < lane
+      const double b = Bw[lane + q * 32];
+#pragma unroll
+      for (int i = 0; i < MR; ++i)
+        if (i < rows) a[i] = fma(Vh[i + q * MR], b, a[i]);
+    }
+  jacobi<MR>(a, rows, K, lane, IB.jac + 2 * (size_t)id, err);
+  // singular values, order, rank
+  double s2 = -1.0;
+  if (lane < K) {
+    s2 = 0.0;
+#pragma unroll
+    for (int i = 0; i < MR; ++i)
+      if (i < rows) s2 = fma(a[i], a[i], s2);
+  }
+  int pos = 0;
+  for (int d = 0; d < 32; ++d) {
+    const double o = __shfl_sync(kFull, s2, d);
+    if (d < K && (o > s2 || (o == s2 && d < lane))) ++pos;
+  }
+  double tail = 0.0;
+  for (int d = 0; d < 32; ++d) {
+    const double o = __shfl_sync(kFull, s2, d);
+    const int op = __shfl_sync(kFull, pos, d);
+    if (d < K && op >= pos) tail += o;
+  }
+  const double thr = 0.25 * eps * eps;
+  const bool keep = lane < K && rows > 0 && tail > thr;
+  const int r = __popc(__ballot_sync(kFull, keep));
+  if (keep) {
+    const double inv = 1.0 / sqrt(s2);
+#pragma unroll
+    for (int i = 0; i < MR; ++i)
+      if (i < rows) Qs[i + pos * MR] = a[i] * inv;
+  }
+  __syncwarp();
+  // R_t = Q^* V^ (r x K)
+  double* Rt = IB.Rt + (size_t)id * kSlot;
+  if (lane < K)
+    for (int p = 0; p < 32; ++p) {
+      double v = 0.0;
+      if (p < r)
+        for (int i = 0; i < rows; ++i) v = fma(Qs[i + p * MR], Vh[i + lane * MR], v);
+      Rt[p + lane * 32] = v;
+    }
+  if (lane == 0) IB.rank[id] = r;
+  // outputs: leaf basis or the sons' transfer matrices
+  if (it.flags & kItemLeaf) {
+    double* Q = IB.Q + it.qoff;
+    if (lane < r)
+      for (int i = 0; i < rows; ++i) Q[i + (size_t)lane * rows] = Qs[i + lane * MR];
+  } else {
+    double* F1 = IB.F + (size_t)it.son0 * kSlot;
+    double* F2 = IB.F + (size_t)it.son1 * kSlot;
+    if (lane < r) {
+      for (int p = 0; p < r1; ++p) F1[p + lane * 32] = Qs[p + lane * MR];
+      for (int p = 0; p < r2; ++p) F2[p + lane * 32] = Qs[r1 + p + lane * MR];
+    }
+  }
+  if ((it.flags & kItemRoot) && !(it.flags & kItemTreeRoot)) {
+    // E_t0 <- R_t0 [E_t0; 0]  (r x kf)
+    __syncwarp();
+    const double* E = M.transfer[side] + (size_t)it.cluster * kcap * kcap;   // k x kf
+    double* Fo = IB.F + (size_t)id * kSlot;
+    if (lane < it.kf)
+      for (int p = 0; p < r; ++p) {
+        double v = 0.0;
+        for (int q = 0; q < k; ++q) v = fma(Rt[p + q * 32], E[q + lane * kcap], v);
+        Fo[p + lane * 32] = v;
+      }
+  }
+}
+
+// ------------------------------------------------------------- step 5
+// Reprojection S_b <- R_t S~_b R_s^* for every affected admissible block.
+__global__ void k_reproject(MatView M, const Item* __restrict__ items, const Task* __restrict__ tasks,
+                            int n, int u, ItemBuffers IB) {
+  const int lane = threadIdx.x & 31;
+  const int idx = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (idx >= n) return;
+  const Task tk = tasks[idx];
+  const int kcap = M.kcap;
+  const double* S = M.S + (size_t)tk.slot * kcap * kcap;
+  double* out = IB.S_out + (size_t)idx * kSlot;
+  if (tk.it >= 0 && tk.is >= 0) {
+    const int kt = items[tk.it].k, ls = items[tk.is].k;
+    const int Kt = kt + u;
+    const int rt = IB.rank[tk.it], rs = IB.rank[tk.is];
+    const double* Rt = IB.Rt + (size_t)tk.it * kSlot;
+    const double* Rs = IB.Rt + (size_t)tk.is * kSlot;
+    if (lane < rs) {
+      double T[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        double v = 0.0;
+        if (i < kt) {
+          for (int q = 0; q < ls; ++q) v = fma(S[i + q * kcap], Rs[lane + q * 32], v);
+        } else if (i < Kt) {
+          v = Rs[lane + (ls + i - kt) * 32];
+        }
+        T[i] = v;
+      }
+      for (int p = 0; p < rt; ++p) {
+        double y = 0.0;
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+          if (i < Kt) y = fma(Rt[p + i * 32], T[i], y);
+        out[p + lane * 32] = y;
+      }
+    }
+  } else if (tk.it >= 0) {
+    const int kt = items[tk.it].k;
+    const int rt = IB.rank[tk.it];
+    const double* Rt = IB.Rt + (size_t)tk.it * kSlot;
+    const int ls = tk.ls;
+    if (lane < ls)
+      for (int p = 0; p < rt; ++p) {
+        double y = 0.0;
+        for (int i = 0; i < kt; ++i) y = fma(Rt[p + i * 32], S[i + lane * kcap], y);
+        out[p + lane * 32] = y;
+      }
+  } else {
+    const int ls = items[tk.is].k;
+    const int rs = IB.rank[tk.is];
+    const int kt = tk.kt;
+    const double* Rs = IB.Rt + (size_t)tk.is * kSlot;
+    if (lane < rs)
+      for (int p = 0; p < kt; ++p) {
+        double y = 0.0;
+        for (int q = 0; q < ls; ++q) y = fma(S[p + q * kcap], Rs[lane + q * 32], y);
+        out[p + lane * 32] = y;
+      }
+  }
+}
+
+// Batched copies of column-major matrices (commit of one update).
+__global__ void k_copy(const CopyDesc* __restrict__ d, int n) {
+  const int idx = blockIdx.x;
+  if (idx >= n) return;
+  const CopyDesc c = d[idx];
+  for (int e = threadIdx.x; e < c.rows * c.cols; e += blockDim.x) {
+    const int i = e % c.rows, j = e / c.rows;
+    c.dst[i + (size_t)j * c.ldd] = c.src[i + (size_t)j * c.lds];
+  }
+}
+
+// Nearfield G|_b += A|_t B|_s^* for the inadmissible leaves inside b0.
+__global__ void k_near_add(const NearDesc* __restrict__ d, int n, int u) {
+  const int idx = blockIdx.x;
+  if (idx >= n) return;
+  const NearDesc c = d[idx];
+  for (int e = threadIdx.x; e < c.rows * c.cols; e += blockDim.x) {
+    const int i = e % c.rows, j = e / c.rows;
+    double v = c.N[i + (size_t)j * c.ldn];
+    for (int q = 0; q < u; ++q) v = fma(c.A[i + (size_t)q * c.lda], c.B[j + (size_t)q * c.ldb], v);
+    c.N[i + (size_t)j * c.ldn] = v;
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ launchers
+static constexpr int kWarps = 4;
+
+void launch_prepass(const MatView& M, int side, const int32_t* clusters, int n, const int32_t* ptr,
+                    const int32_t* adm, const int32_t* other_cl, const BaseWeights& BW, int* err,
+                    cudaStream_t st) {
+  if (n <= 0) return;
+  const size_t sm = (size_t)kWarps * (32 * kLdr + kCh + 1) * sizeof(double);
+  k_prepass<<<(n + kWarps - 1) / kWarps, 32 * kWarps, sm, st>>>(M, side, clusters, n, ptr, adm,
+                                                                 other_cl, BW, err);
+}
+
+void launch_rfactor(const MatView& M, const Item* items, const int32_t* list, int n, int u,
+                    const double* A, const double* B, const ItemBuffers& IB, int* err, cudaStream_t st) {
+  if (n <= 0) return;
+  const size_t sm = (size_t)kWarps * (32 * kLdr + kCh + 1) * sizeof(double);
+  k_rfactor<<<(n + kWarps - 1) / kWarps, 32 * kWarps, sm, st>>>(M, items, list, n, u, A, B, IB, err);
+}
+
+void launch_norms(const MatView& M, const Item* items, const NormTask* tasks, int n, int u,
+                  const ItemBuffers& IB, cudaStream_t st) {
+  if (n <= 0) return;
+  k_norms<<<(n + kWarps - 1) / kWarps, 32 * kWarps, 0, st>>>(M, items, tasks, n, u, IB);
+}
+
+void launch_weights(const MatView& M, const Item* items, const Entry* ents, const int32_t* list, int n,
+                    int u, const BaseWeights& BW, const ItemBuffers& IB, int* err, cudaStream_t st) {
+  if (n <= 0) return;
+  const size_t sm = (size_t)kWarps * (32 * kLdr + kCh + 1) * sizeof(double);
+  k_weights<<<(n + kWarps - 1) / kWarps, 32 * kWarps, sm, st>>>(M, items, ents, list, n, u, BW, IB, err);
+}
+
+template <int MR>
+static void launch_truncate_mr(const MatView& M, const Item* items, const int32_t* list, int n, int u,
+                               int kl, double eps, const double* A, const double* B,
+                               const ItemBuffers& IB, int* err, cudaStream_t st) {
+  const int warps = 2;
+  const size_t sm = (size_t)warps * 2 * MR * kl * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    H2_CUDA(cudaFuncSetAttribute(k_truncate<MR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 2 * 2 * MR * 32 * (int)sizeof(double)));
+    attr = true;
+  }
+  k_truncate<MR><<<(n + warps - 1) / warps, 32 * warps, sm, st>>>(M, items, list, n, u, kl, eps, A, B,
+                                                                  IB, err);
+}
+
+void launch_truncate(const MatView& M, const Item* items, const int32_t* list, int n, int u, int kl,
+                     int max_rows, double eps, const double* A, const double* B, const ItemBuffers& IB,
+                     int* err, cudaStream_t st) {
+  if (n <= 0) return;
+  if (max_rows <= 32)
+    launch_truncate_mr<32>(M, items, list, n, u, kl, eps, A, B, IB, err, st);
+  else if (max_rows <= 48)
+    launch_truncate_mr<48>(M, items, list, n, u, kl, eps, A, B, IB, err, st);
+  else
+    launch_truncate_mr<64>(M, items, list, n, u, kl, eps, A, B, IB, err, st);
+}
+
+void launch_reproject(const MatView& M, const Item* items, const Task* tasks, int n, int u,
+                      const ItemBuffers& IB, cudaStream_t st) {
+  if (n <= 0) return;
+  k_reproject<<<(n + kWarps - 1) / kWarps, 32 * kWarps, 0, st>>>(M, items, tasks, n, u, IB);
+}
+
+void launch_copy(const CopyDesc* d, int n, cudaStream_t st) {
+  if (n <= 0) return;
+  k_copy<<<n, 128, 0, st>>>(d, n);
+}
+
+void launch_near_add(const NearDesc* d, int n, int u, cudaStream_t st) {
+  if (n <= 0) return;
+  k_near_add<<<n, 128, 0, st>>>(d, n, u);
+}
+
+}  // namespace h2

@@ -65,3 +65,48 @@ def weighted_block_row(Zt, Z, t, row_side=True):
     if not cols:
         return np.zeros((tree.size[t], 0))
     return np.hstack(cols)
+
+
+def basis_row(tree, basis, leaf_of, i, t):
+    """Row of V_t at tree position i (i inside t^), via Eq. (nested)."""
+    c = leaf_of[i]
+    row = basis.leaf[c][i - tree.offset[c]]
+    while c != t:
+        row = row @ basis.transfer[c]
+        c = tree.father[c]
+    return row
+
+
+def leaf_index(tree):
+    """leaf_of[i] = leaf cluster containing tree position i."""
+    out = np.zeros(tree.n, dtype=np.int64)
+    for c in range(tree.n_clusters):
+        if not tree.sons[c]:
+            out[tree.offset[c]:tree.offset[c] + tree.size[c]] = c
+    return out
+
+
+def entries(Z, I, J):
+    """Entries Z[I[k], J[k]] (tree positions) of an H^2 matrix, one by one:
+    descend the block tree to the leaf containing (i, j) and evaluate
+    V_t S_b W_s^* there (Eq. (vsw)) or read the nearfield block."""
+    bt = Z.blocks
+    rt, ct = Z.V.tree, Z.W.tree
+    lr, lc = leaf_index(rt), leaf_index(ct)
+    out = np.zeros(len(I))
+    for k, (i, j) in enumerate(zip(I, J)):
+        b = 0
+        while bt.kind[b] == bt.SUB:
+            for c in bt.sons[b]:
+                t, s = bt.row[c], bt.col[c]
+                if rt.offset[t] <= i < rt.offset[t] + rt.size[t] and ct.offset[s] <= j < ct.offset[s] + ct.size[s]:
+                    b = c
+                    break
+        t, s = bt.row[b], bt.col[b]
+        if bt.kind[b] == bt.ADM:
+            v = basis_row(rt, Z.V, lr, i, t)
+            w = basis_row(ct, Z.W, lc, j, s)
+            out[k] = v @ Z.S[b] @ w
+        else:
+            out[k] = Z.N[b][i - rt.offset[t], j - ct.offset[s]]
+    return out

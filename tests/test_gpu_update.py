@@ -1,0 +1,233 @@
+"""Parity of the CUDA local low-rank update with the CPU oracle (Section 5).
+
+The library and the oracle build their own trees and receive the same
+seeded draws; results are compared on the assembled matrices:
+
+* small problems (n <= 1024): the whole updated matrix densely, relative
+  Frobenius error <= 1e-10, and the new ranks;
+* the isolated-update workload at full size (256 x 256 points, k = 16,
+  rank-8 updates, eps = 1e-8): sampled updates, compared entry by entry on
+  rows of T_t0 and columns of T_s0 (where the update acts) plus random
+  entries elsewhere, and properties of the whole 4096-update batch.
+"""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1402_5056_gb300 import binding as b  # noqa: E402
+
+import synth  # noqa: E402
+from dense_ref import entries  # noqa: E402
+from gpu_util import applied_delta, concat_factors, run_isolated  # noqa: E402
+from libside import lib_problem, to_oracle  # noqa: E402
+from oracle.tree import BlockTree  # noqa: E402
+from oracle.update import apply_delta, local_update, sequential_batch  # noqa: E402
+from problems import draw_updates, oracle_problem  # noqa: E402
+
+TOL = 1e-10   # relative Frobenius error on assembled matrices
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = b.h2_ctx_create(0, torch.cuda.current_stream().cuda_stream)
+    yield c
+    b.h2_ctx_destroy(c)
+
+
+def _extra(Zo, u, rng):
+    bt = Zo.blocks
+    sub = [c for c in range(1, bt.n_blocks) if bt.kind[c] == BlockTree.SUB]
+    extra = [0, sub[len(sub) // 2], bt.inadmissible[len(bt.inadmissible) // 3]]
+    A = [rng.standard_normal((Zo.V.tree.size[bt.row[c]], u)) for c in extra]
+    B = [rng.standard_normal((Zo.W.tree.size[bt.col[c]], u)) for c in extra]
+    return extra, A, B
+
+
+def _rank_check(Zo, d, rV, rW):
+    if d["margin"] < 1e-6:
+        return
+    for t, r in d["V"]["rank"].items():
+        assert rV[t] == r, ("row rank", t)
+    for t, r in d["W"]["rank"].items():
+        assert rW[t] == r, ("column rank", t)
+
+
+@pytest.mark.parametrize("N,leaf,k,u,eps", [
+    (24, 16, 6, 3, 1e-8),
+    (24, 16, 6, 3, 0.5),
+    (24, 16, 6, 3, 2.0),
+    (32, 32, 8, 4, 1e-8),
+    (32, 32, 8, 4, 1.0),
+    (20, 10, 4, 5, 0.3),
+])
+def test_isolated_batch_matches_oracle_dense(ctx, N, leaf, k, u, eps):
+    seed = 100 + N + k
+    Zo, st, _ = oracle_problem(N, k, seed, leaf)
+    blocks, A, B = draw_updates(Zo, st, 6, u)
+    eb, eA, eB = _extra(Zo, u, np.random.default_rng(seed))
+    blocks += eb
+    A += eA
+    B += eB
+    Zl, _, _ = lib_problem(ctx, N, k, seed, leaf)
+    P, dA, dB = run_isolated(torch, ctx, Zl, blocks, A, B, u, eps)
+    try:
+        for j, b0 in enumerate(blocks):
+            d = local_update(Zo, b0, A[j], B[j], eps)
+            ref = apply_delta(Zo, d).dense()
+            C = b.h2_matrix_clone(ctx, Zl)
+            try:
+                b.h2_batch_apply(ctx, P, j, dA.data_ptr(), dB.data_ptr(), C)
+                got = to_oracle(ctx, C, Zo).dense()
+                rV, rW = b.h2_get_ranks(C, 0), b.h2_get_ranks(C, 1)
+            finally:
+                b.h2_matrix_free(C)
+            err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+            assert err <= TOL, (j, b0, err)
+            _rank_check(Zo, d, rV, rW)
+    finally:
+        b.h2_batch_free(P)
+        b.h2_matrix_free(Zl)
+
+
+def test_execute_host_path_matches(ctx):
+    N, leaf, k, u, eps = 24, 16, 6, 3, 0.5
+    Zo, st, _ = oracle_problem(N, k, 7, leaf)
+    blocks, A, B = draw_updates(Zo, st, 5, u)
+    Zl, _, _ = lib_problem(ctx, N, k, 7, leaf)
+    P = b.h2_batch_create(ctx, Zl, blocks, u)
+    try:
+        Acat, Bcat = concat_factors(P, A, B, u)
+        res = b.h2_batch_execute_host(ctx, P, Acat, Bcat, eps)
+        n_items = b.h2_batch_stats(ctx, P, flops=False)["cluster_tasks"]
+        rk = res[:n_items]
+        assert np.all(rk == np.round(rk)) and rk.max() <= k + u and rk.min() >= 0
+        res2 = b.h2_batch_execute_host(ctx, P, Acat, Bcat, eps)
+        np.testing.assert_array_equal(res, res2)   # deterministic
+        dA = torch.from_numpy(Acat).cuda()
+        dB = torch.from_numpy(Bcat).cuda()
+        for j, b0 in enumerate(blocks):
+            d = local_update(Zo, b0, A[j], B[j], eps)
+            ref = apply_delta(Zo, d).dense()
+            C = b.h2_matrix_clone(ctx, Zl)
+            try:
+                b.h2_batch_apply(ctx, P, j, dA.data_ptr(), dB.data_ptr(), C)
+                got = to_oracle(ctx, C, Zo).dense()
+            finally:
+                b.h2_matrix_free(C)
+            assert np.linalg.norm(got - ref) <= TOL * np.linalg.norm(ref)
+    finally:
+        b.h2_batch_free(P)
+        b.h2_matrix_free(Zl)
+
+
+@pytest.mark.parametrize("eps", [1e-8, 0.5])
+def test_sequential_updates_in_place(ctx, eps):
+    N, leaf, k, u = 24, 16, 5, 3
+    Zo, st, _ = oracle_problem(N, k, 21, leaf)
+    blocks, A, B = draw_updates(Zo, st, 4, u)
+    # a repeated block and a block of another level
+    blocks = blocks + [blocks[0]]
+    A = A + [A[0] * 0.5]
+    B = B + [B[0]]
+    Zl, _, _ = lib_problem(ctx, N, k, 21, leaf)
+    try:
+        for j, b0 in enumerate(blocks):
+            dA = torch.from_numpy(np.asfortranarray(A[j]).ravel(order="F")).cuda()
+            dB = torch.from_numpy(np.asfortranarray(B[j]).ravel(order="F")).cuda()
+            b.h2_lowrank_update(ctx, Zl, b0, u, dA.data_ptr(), A[j].shape[0], dB.data_ptr(), B[j].shape[0], eps)
+            b.h2_ctx_synchronize(ctx)
+        ref = sequential_batch(Zo, blocks, A, B, eps).dense()
+        got = to_oracle(ctx, Zl, Zo).dense()
+        assert np.linalg.norm(got - ref) <= TOL * np.linalg.norm(ref)
+    finally:
+        b.h2_matrix_free(Zl)
+
+
+# ---------------------------------------------------------------- full size
+FULL_N, FULL_K, FULL_U, FULL_EPS, FULL_COUNT = 256, 16, 8, 1e-8, 4096
+FULL_SEED = synth.SEED_BASE + 1
+
+
+@pytest.fixture(scope="module")
+def full(ctx):
+    Zo, st, _ = oracle_problem(FULL_N, FULL_K, FULL_SEED, 32)
+    blocks, A, B = draw_updates(Zo, st, FULL_COUNT, FULL_U)
+    Zl, _, _ = lib_problem(ctx, FULL_N, FULL_K, FULL_SEED, 32)
+    yield Zo, Zl, blocks, A, B
+    b.h2_matrix_free(Zl)
+
+
+def _sample_positions(Zo, b0, rng, m=40):
+    bt = Zo.blocks
+    t0, s0 = bt.row[b0], bt.col[b0]
+    rt, ct = Zo.V.tree, Zo.W.tree
+    n = rt.n
+    I1 = rng.integers(rt.offset[t0], rt.offset[t0] + rt.size[t0], m)
+    J1 = rng.integers(0, n, m)
+    I2 = rng.integers(0, n, m)
+    J2 = rng.integers(ct.offset[s0], ct.offset[s0] + ct.size[s0], m)
+    I3 = rng.integers(rt.offset[t0], rt.offset[t0] + rt.size[t0], m)
+    J3 = rng.integers(ct.offset[s0], ct.offset[s0] + ct.size[s0], m)
+    I4 = rng.integers(0, n, m // 2)
+    J4 = rng.integers(0, n, m // 2)
+    return np.concatenate([I1, I2, I3, I4]), np.concatenate([J1, J2, J3, J4])
+
+
+def test_full_size_sampled_updates_match_oracle(ctx, full):
+    Zo, Zl, blocks, A, B = full
+    # the first 48 updates of the benchmark batch, in one isolated launch set
+    nb = 48
+    P, dA, dB = run_isolated(torch, ctx, Zl, blocks[:nb], A[:nb], B[:nb], FULL_U, FULL_EPS)
+    rng = np.random.default_rng(0)
+    levels = [Zo.V.tree.level[Zo.blocks.row[c]] for c in blocks[:nb]]
+    # every level present among the first updates, plus a few more
+    pick = sorted({levels.index(l) for l in set(levels)} | {0, 1, 2})
+    try:
+        for j in pick:
+            b0 = blocks[j]
+            d = local_update(Zo, b0, A[j], B[j], FULL_EPS)
+            ref_m = apply_delta(Zo, d)
+            got_m, rV, rW = applied_delta(ctx, Zl, P, j, dA, dB, Zo, b0)
+            _rank_check(Zo, d, rV, rW)
+            I, J = _sample_positions(Zo, b0, rng)
+            ref = entries(ref_m, I, J)
+            got = entries(got_m, I, J)
+            err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+            assert err <= TOL, (j, levels[j], err)
+    finally:
+        b.h2_batch_free(P)
+
+
+def test_full_batch_properties(ctx, full):
+    """All 4096 updates in the benchmark's launch configuration: no device
+    error, ranks within k + u, orthonormal new leaf bases (sampled)."""
+    Zo, Zl, blocks, A, B = full
+    P = b.h2_batch_create(ctx, Zl, blocks, FULL_U)
+    try:
+        Acat, Bcat = concat_factors(P, A, B, FULL_U)
+        res = b.h2_batch_execute_host(ctx, P, Acat, Bcat, FULL_EPS)
+        st = b.h2_batch_stats(ctx, P)
+        rk = res[:st["cluster_tasks"]]
+        assert rk.min() >= 0 and rk.max() <= FULL_K + FULL_U
+        assert np.all(np.isfinite(res))
+        assert st["flops"] > 0
+        dA = torch.from_numpy(Acat).cuda()
+        dB = torch.from_numpy(Bcat).cuda()
+        rng = np.random.default_rng(1)
+        for j in rng.choice(len(blocks), 4, replace=False):
+            b0 = blocks[j]
+            got_m, _, _ = applied_delta(ctx, Zl, P, int(j), dA, dB, Zo, b0)
+            t0 = Zo.blocks.row[b0]
+            for t in got_m.V.tree.descendants(t0):
+                if got_m.V.tree.is_leaf(t):
+                    Q = got_m.V.leaf[t]
+                    np.testing.assert_allclose(Q.T @ Q, np.eye(Q.shape[1]), atol=1e-13)
+    finally:
+        b.h2_batch_free(P)

@@ -1,0 +1,121 @@
+"""Host-side checks of libh2gb (no GPU needed).
+
+* the shared library loads and exports every entry point ``include/h2gb.h``
+  declares;
+* the library's trees are bit-identical to the oracle's independent ones;
+* the batch planner's task counts and factor layout follow the definitions
+  of Section 5 (subtrees T_t0, T_s0 and the blocks whose row lies in T_t0 or
+  whose column lies in T_s0).
+"""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+from oracle.tree import BlockTree, ClusterTree
+
+b = pytest.importorskip("paper_1402_5056_gb300.binding")
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_library_exports_every_declared_symbol():
+    hdr = open(os.path.join(ROOT, "include", "h2gb.h")).read()
+    declared = set(re.findall(r"\b(h2_[a-z0-9_]+)\s*\(", hdr))
+    assert declared, "no declarations found"
+    missing = [n for n in sorted(declared) if not hasattr(b._lib, n)]
+    assert not missing, missing
+    assert declared == set(b.EXPORTS)
+
+
+def _compare_trees(pts, leaf, eta):
+    Z = b.h2_matrix_create(None, pts, leaf, eta, 0.0, 8)
+    try:
+        tc = b.h2_tree_clusters(Z)
+        tb = b.h2_tree_blocks(Z)
+        perm = b.h2_tree_permutation(Z)
+    finally:
+        b.h2_matrix_free(Z)
+    ct = ClusterTree(pts, leaf)
+    bt = BlockTree(ct, ct, eta)
+    nc = ct.n_clusters
+    assert len(tc["offset"]) == nc
+    np.testing.assert_array_equal(tc["offset"], ct.offset)
+    np.testing.assert_array_equal(tc["size"], ct.size)
+    np.testing.assert_array_equal(tc["father"], ct.father)
+    np.testing.assert_array_equal(tc["level"], ct.level)
+    np.testing.assert_array_equal(tc["subtree"], ct.subtree_count)
+    np.testing.assert_array_equal(tc["son0"], [s[0] if s else -1 for s in ct.sons])
+    np.testing.assert_array_equal(tc["son1"], [s[1] if s else -1 for s in ct.sons])
+    np.testing.assert_array_equal(perm, ct.perm)
+    assert len(tb["row"]) == bt.n_blocks
+    np.testing.assert_array_equal(tb["row"], bt.row)
+    np.testing.assert_array_equal(tb["col"], bt.col)
+    np.testing.assert_array_equal(tb["kind"], bt.kind)
+    np.testing.assert_array_equal(tb["father"], bt.father)
+
+
+@pytest.mark.parametrize("N,leaf,eta", [(16, 8, 2.0), (24, 32, 2.0), (32, 32, 2.0), (37, 20, 1.5)])
+def test_trees_bit_identical_on_grids(N, leaf, eta):
+    _compare_trees(synth.grid_points_2d(N), leaf, eta)
+
+
+@pytest.mark.parametrize("seed,dim", [(0, 2), (1, 3), (2, 1)])
+def test_trees_bit_identical_on_random_points(seed, dim):
+    pts = np.random.default_rng(seed).uniform(size=(1500, dim))
+    _compare_trees(pts, 24, 2.0)
+
+
+def test_trees_bit_identical_isolated_update_workload():
+    # 256 x 256 grid, leaf 32, eta 2 (the isolated-update benchmark structure)
+    _compare_trees(synth.grid_points_2d(256), 32, 2.0)
+
+
+def test_host_plan_counts_and_layout():
+    N, leaf, u = 32, 16, 3
+    pts = synth.grid_points_2d(N)
+    Z = b.h2_matrix_create(None, pts, leaf, 2.0, 0.0, 8)
+    ct = ClusterTree(pts, leaf)
+    bt = BlockTree(ct, ct, 2.0)
+    rng = np.random.default_rng(3)
+    blocks = list(rng.choice(bt.admissible, 7)) + [0, bt.inadmissible[3]]
+    P = b.h2_batch_create(None, Z, blocks, u)
+    try:
+        st = b.h2_batch_stats(None, P, flops=False)
+        items = 0
+        tasks = 0
+        offA = offB = 0
+        for j, blk in enumerate(blocks):
+            t0, s0 = bt.row[blk], bt.col[blk]
+            Tt, Ts = set(ct.descendants(t0)), set(ct.descendants(s0))
+            items += len(Tt) + len(Ts)
+            tasks += sum(1 for c in bt.admissible if bt.row[c] in Tt or bt.col[c] in Ts)
+            lay = b.h2_batch_factor_layout(P, j)
+            assert lay == (ct.size[t0], offA, ct.size[s0], offB)
+            offA += ct.size[t0] * u
+            offB += ct.size[s0] * u
+        assert st["cluster_tasks"] == items
+        assert st["block_tasks"] == tasks
+        assert b.h2_batch_factor_sizes(P) == (offA, offB)
+    finally:
+        b.h2_batch_free(P)
+        b.h2_matrix_free(Z)
+
+
+def test_invalid_arguments_rejected():
+    pts = synth.grid_points_2d(8)
+    with pytest.raises(b.H2Error) as e:
+        b.h2_matrix_create(None, pts, 0, 2.0)
+    assert e.value.status == 1
+    Z = b.h2_matrix_create(None, pts, 8, 2.0, 0.0, 4)
+    try:
+        with pytest.raises(b.H2Error):
+            b.h2_batch_create(None, Z, [10 ** 6], 2)
+        with pytest.raises(b.H2Error):
+            b.h2_batch_create(None, Z, [0], 0)
+        with pytest.raises(b.H2Error):
+            b.h2_batch_create(None, Z, [0], 32)
+    finally:
+        b.h2_matrix_free(Z)

@@ -17,9 +17,13 @@ def _box(points):
     return points.min(axis=0), points.max(axis=0)
 
 
-@pytest.mark.parametrize("N,leaf", [(16, 8), (24, 32), (32, 32), (13, 5)])
+@pytest.mark.parametrize("N,leaf", [(16, 8), (24, 32), (32, 32), (13, 5), (-1, 10)])
 def test_leaf_labels_partition_index_set(N, leaf):
-    pts = synth.grid_points_2d(N)
+    if N > 0:
+        pts = synth.grid_points_2d(N)
+    else:
+        N = 30
+        pts = np.random.default_rng(4).uniform(size=(N * N, 2))
     ct = ClusterTree(pts, leaf)
     # Def. "Cluster tree": root labelled by I, sons partition the father
     assert sorted(ct.idx[0].tolist()) == list(range(N * N))
@@ -36,8 +40,11 @@ def test_leaf_labels_partition_index_set(N, leaf):
             assert ct.offset[b] == ct.offset[t] + ct.size[a]
         else:
             assert ct.size[t] <= leaf
-    # leaves partition I; perm is a permutation
+    # leaves partition I; perm is a permutation; labels are contiguous in it
     assert sorted(ct.perm.tolist()) == list(range(N * N))
+    for t in range(ct.n_clusters):
+        seg = ct.perm[ct.offset[t]:ct.offset[t] + ct.size[t]]
+        assert sorted(seg.tolist()) == sorted(ct.idx[t].tolist())
     # depth-first preorder numbering: every son has a larger id than its father
     assert all(ct.father[t] < t for t in range(1, ct.n_clusters))
 
