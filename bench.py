@@ -36,11 +36,12 @@ UNIT = "updates/s"
 WORK = dict(N=256, leaf=32, eta=2.0, k=16, u=8, eps=1e-8, count=4096, seed=synth.SEED_BASE + 1)
 WORKLOAD_NAME = ("isolated H2 low-rank updates: 4096 rank-8 updates, 256x256-point H2 matrix "
                  "(n=65536, leaf 32, eta 2, k=16), eps=1e-8, float64")
-# Float64 FMA throughput of one GB300 (TFLOP/s), from the DFMA probe recorded
-# with the design notes (profiles/fp64_peak.txt); the roofline denominator of
-# this ALU-bound path.
-FP64_PEAK_TFLOPS = 1.25
-FP64_PEAK_SOURCE = "nominal GB300 FP64 (1.25 TFLOP/s); measured probe pending"
+# Float64 FMA peak of one GB300: 2 DFMA per clock per SM (measured by the
+# probe paper_1402_5056_gb300/csrc/fp64_probe.cu: 1.254 TFLOP/s at 2070 MHz)
+# x 152 SMs x 2 flop x 2.070 GHz; the roofline denominator of this
+# ALU-bound path.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+FP64_PEAK_SOURCE = "derived: 152 SM x 2 DFMA/clk x 2 flop x 2070 MHz (DFMA probe: 1.254 TFLOP/s measured)"
 L2_FLUSH_BYTES = 512 << 20
 
 

@@ -194,6 +194,19 @@ h2_status h2_batch_set_timing(h2_batch* batch, int on);
 h2_status h2_batch_phase_stats(h2_ctx* ctx, const h2_batch* batch, int phase, int64_t* launches,
                                double* ms, double* flops);
 
+/* Intermediate results of one cluster task of the last execution, for
+ * step-by-step parity checks.  info (host, 8 entries): update index, side,
+ * cluster, rank before, new rank, flags (1 leaf, 2 subtree root, 4 inside
+ * blocks, 8 tree root), 0, 0.  which: 0 basis R-factor (step 2), 1 weight
+ * matrix B~_t (step 3), 2 R_t = Q_t^* V~_t (step 4); out = the 32 x 32 tile
+ * (column-major, ld 32, zero outside the (k+u) x (k+u) or r x (k+u) part).
+ * Synchronizes. */
+h2_status h2_batch_item_info(const h2_batch* batch, int64_t item, int32_t* info);
+h2_status h2_batch_item_tile(h2_ctx* ctx, const h2_batch* batch, int64_t item, int which,
+                             double* out);
+/* Cluster tasks of update j occupy items [first, last). */
+h2_status h2_batch_update_items(const h2_batch* batch, int64_t j, int64_t* first, int64_t* last);
+
 /* One update applied to Z in place (sequential semantics; Section 5).
  * A (rows of block's row cluster x u, ld lda) and B (rows of column cluster
  * x u, ld ldb) are DEVICE pointers. */

@@ -28,7 +28,8 @@ EXPORTS = [
     "h2_get_coupling",
     "h2_batch_create", "h2_batch_free", "h2_batch_factor_layout", "h2_batch_factor_sizes",
     "h2_batch_execute", "h2_batch_execute_host", "h2_batch_result_size", "h2_batch_apply",
-    "h2_batch_stats", "h2_batch_set_timing", "h2_batch_phase_stats", "h2_lowrank_update",
+    "h2_batch_stats", "h2_batch_set_timing", "h2_batch_phase_stats", "h2_batch_item_info", "h2_batch_item_tile",
+    "h2_batch_update_items", "h2_lowrank_update",
 ]
 
 PHASES = ("base_weights", "rfactor", "norms", "weights", "truncate", "reproject")
@@ -93,6 +94,9 @@ _sig("h2_batch_apply", _int, _p, _p, _i64, _p, _p, _p)
 _sig("h2_batch_stats", _int, _p, _p, _p, _p, _p, _p)
 _sig("h2_batch_set_timing", _int, _p, _int)
 _sig("h2_batch_phase_stats", _int, _p, _p, _int, _p, _p, _p)
+_sig("h2_batch_item_info", _int, _p, _i64, _p)
+_sig("h2_batch_item_tile", _int, _p, _p, _i64, _int, _p)
+_sig("h2_batch_update_items", _int, _p, _i64, _p, _p)
 _sig("h2_lowrank_update", _int, _p, _p, _i64, _int, _p, _i64, _p, _i64, _dbl)
 
 
@@ -317,6 +321,25 @@ def h2_batch_phase_stats(ctx, P, phase: int, flops: bool = True) -> dict:
     _check(_lib.h2_batch_phase_stats(ctx, P, int(phase), C.byref(n), C.byref(ms),
                                      C.byref(f) if flops else None), ctx)
     return dict(launches=n.value, ms=ms.value, flops=f.value if flops else None)
+
+
+def h2_batch_item_info(P, item: int) -> dict:
+    a = np.zeros(8, np.int32)
+    _check(_lib.h2_batch_item_info(P, int(item), _ptr(a)))
+    return dict(update=int(a[0]), side=int(a[1]), cluster=int(a[2]), k=int(a[3]), rank=int(a[4]),
+                flags=int(a[5]))
+
+
+def h2_batch_item_tile(ctx, P, item: int, which: int) -> np.ndarray:
+    out = np.zeros(32 * 32)
+    _check(_lib.h2_batch_item_tile(ctx, P, int(item), int(which), _ptr(out)), ctx)
+    return out.reshape((32, 32), order="F")
+
+
+def h2_batch_update_items(P, j: int):
+    a, c = C.c_int64(), C.c_int64()
+    _check(_lib.h2_batch_update_items(P, int(j), C.byref(a), C.byref(c)))
+    return a.value, c.value
 
 
 def h2_lowrank_update(ctx, Z, block: int, u: int, A_dev: int, lda: int, B_dev: int, ldb: int, eps: float):

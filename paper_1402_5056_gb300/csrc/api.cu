@@ -1400,6 +1400,44 @@ extern "C" h2_status h2_batch_phase_stats(h2_ctx* ctx, const h2_batch* P, int ph
   });
 }
 
+extern "C" h2_status h2_batch_item_info(const h2_batch* P, int64_t item, int32_t* info) {
+  if (!P || !info || item < 0 || item >= (int64_t)P->items.size()) return H2_EINVAL;
+  const Item& it = P->items[item];
+  int64_t j = std::upper_bound(P->upd_item.begin(), P->upd_item.end(), item) - P->upd_item.begin() - 1;
+  info[0] = (int32_t)j;
+  info[1] = it.side;
+  info[2] = it.cluster;
+  info[3] = it.k;
+  info[4] = -1;
+  if (P->executed) {
+    int32_t r = -1;
+    if (cudaMemcpy(&r, P->IB.rank + item, sizeof(int32_t), cudaMemcpyDeviceToHost) == cudaSuccess) info[4] = r;
+  }
+  info[5] = it.flags;
+  info[6] = 0;
+  info[7] = 0;
+  return H2_OK;
+}
+
+extern "C" h2_status h2_batch_item_tile(h2_ctx* ctx, const h2_batch* P, int64_t item, int which, double* out) {
+  if (!ctx || !P || !out || item < 0 || item >= (int64_t)P->items.size() || which < 0 || which > 2)
+    return H2_EINVAL;
+  return guard(ctx, [&] {
+    H2_REQUIRE(P->executed, "h2_batch_item_tile: batch not executed");
+    DeviceGuard g(ctx->device);
+    const double* src = (which == 0 ? P->IB.Rq : which == 1 ? P->IB.Bw : P->IB.Rt) + (size_t)item * kSlot;
+    H2_CUDA(cudaMemcpyAsync(out, src, kSlot * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    H2_CUDA(cudaStreamSynchronize(ctx->stream));
+  });
+}
+
+extern "C" h2_status h2_batch_update_items(const h2_batch* P, int64_t j, int64_t* first, int64_t* last) {
+  if (!P || j < 0 || j >= P->count) return H2_EINVAL;
+  if (first) *first = P->upd_item[j];
+  if (last) *last = P->upd_item[j + 1];
+  return H2_OK;
+}
+
 // ============================================================ single update
 extern "C" h2_status h2_lowrank_update(h2_ctx* ctx, h2_matrix* Z, int64_t block, int u, const double* A,
                                        int64_t lda, const double* B, int64_t ldb, double eps) {

@@ -365,7 +365,19 @@ __global__ void k_weights(MatView M, const Item* __restrict__ items, const Entry
   zero_tile(R, lane);
   double x[kCh];
   const double st = sqrt((double)M.subtree[side][it.cluster]);
-  if (!(it.flags & kItemInside)) {
+  // Is V_t orthonormal?  Then the leading k x k block of its R-factor is
+  // diag(+-1) and ||Z~|_b||_F = ||R_kk S_b||_F equals ||S_b||_F for the
+  // blocks whose other cluster lies outside the update.
+  const double* Rown = IB.Rq + (size_t)id * kSlot;
+  bool orth = true;
+  if (lane < k)
+    for (int i = 0; i < k; ++i) {
+      const double v = Rown[i + lane * 32];
+      const double want = (i == lane) ? copysign(1.0, v) : 0.0;
+      if (fabs(v - want) > 64.0 * DBL_EPSILON) orth = false;
+    }
+  orth = __all_sync(kFull, orth);
+  if (!(it.flags & kItemInside) && orth) {
     const double* G = BW.G[side] + (size_t)it.cluster * kSlot;
     if (lane < k)
       for (int i = 0; i <= lane; ++i) R[i + lane * kLdr] = G[i + lane * 32];
@@ -376,13 +388,14 @@ __global__ void k_weights(MatView M, const Item* __restrict__ items, const Entry
       const double* S = M.S + (size_t)en.slot * kcap * kcap;
       if (en.other < 0) {
         const int l = M.rank[1 - side][en.other_cluster];
+        // ||R_kk S_b||_F (side 0, S is k x l) or ||S_b R_kk^*||_F (side 1, S is l x k)
         double part = 0.0;
-        const int scols = side == 0 ? l : k;
-        const int srows = side == 0 ? k : l;
-        if (lane < scols)
-          for (int i = 0; i < srows; ++i) {
-            const double v = S[i + lane * kcap];
-            part = fma(v, v, part);
+        if (lane < l)
+          for (int p = 0; p < k; ++p) {
+            double y = 0.0;
+            for (int q = p; q < k; ++q)
+              y = fma(Rown[p + q * 32], side == 0 ? S[q + lane * kcap] : S[lane + q * kcap], y);
+            part = fma(y, y, part);
           }
         const double nrm = sqrt(warp_sum(part));
         const double om = nrm > 0.0 ? st / nrm : 0.0;

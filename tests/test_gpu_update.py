@@ -129,23 +129,38 @@ def test_execute_host_path_matches(ctx):
 
 @pytest.mark.parametrize("eps", [1e-8, 0.5])
 def test_sequential_updates_in_place(ctx, eps):
+    """Updates applied one after the other in place (ranks grow or shrink,
+    storage capacity grows).  Each step is compared with the oracle applied
+    to the library's own state before that step: chained truncations make
+    the end state depend on rounding through near-degenerate singular values
+    at the cut, so per-step parity is the meaningful check."""
     N, leaf, k, u = 24, 16, 5, 3
     Zo, st, _ = oracle_problem(N, k, 21, leaf)
     blocks, A, B = draw_updates(Zo, st, 4, u)
-    # a repeated block and a block of another level
+    # a repeated block
     blocks = blocks + [blocks[0]]
     A = A + [A[0] * 0.5]
     B = B + [B[0]]
     Zl, _, _ = lib_problem(ctx, N, k, 21, leaf)
     try:
         for j, b0 in enumerate(blocks):
+            before = to_oracle(ctx, Zl, Zo)
+            d = local_update(before, b0, A[j], B[j], eps)
+            ref = apply_delta(before, d).dense()
             dA = torch.from_numpy(np.asfortranarray(A[j]).ravel(order="F")).cuda()
             dB = torch.from_numpy(np.asfortranarray(B[j]).ravel(order="F")).cuda()
             b.h2_lowrank_update(ctx, Zl, b0, u, dA.data_ptr(), A[j].shape[0], dB.data_ptr(), B[j].shape[0], eps)
             b.h2_ctx_synchronize(ctx)
-        ref = sequential_batch(Zo, blocks, A, B, eps).dense()
-        got = to_oracle(ctx, Zl, Zo).dense()
-        assert np.linalg.norm(got - ref) <= TOL * np.linalg.norm(ref)
+            got = to_oracle(ctx, Zl, Zo)
+            err = np.linalg.norm(got.dense() - ref) / np.linalg.norm(ref)
+            assert err <= TOL, (j, err)
+            if d["margin"] >= 1e-6:
+                assert list(got.V.rank) == list(apply_delta(before, d).V.rank)
+                assert list(got.W.rank) == list(apply_delta(before, d).W.rank)
+        if eps < 1e-6:
+            # no truncation happens: the chain equals the oracle's chain
+            ref = sequential_batch(Zo, blocks, A, B, eps).dense()
+            assert np.linalg.norm(to_oracle(ctx, Zl, Zo).dense() - ref) <= TOL * np.linalg.norm(ref)
     finally:
         b.h2_matrix_free(Zl)
 
