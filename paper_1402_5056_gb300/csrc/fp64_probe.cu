@@ -2,6 +2,7 @@
 // float64 and float32 FMA rate of one GPU with full and partly masked warps;
 // the float64 figure is the roofline denominator of the update kernels.
 // Build: nvcc -gencode arch=compute_103a,code=sm_103a -O3 fp64_probe.cu
+#include <cstdio>
 #include <cuda_runtime.h>
 template <typename T>
 __global__ void fma_loop(T* out, int iters, int active_lanes, T b, T c) {
