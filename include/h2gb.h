@@ -213,6 +213,28 @@ h2_status h2_batch_update_items(const h2_batch* batch, int64_t j, int64_t* first
 h2_status h2_lowrank_update(h2_ctx* ctx, h2_matrix* Z, int64_t block, int u, const double* A,
                             int64_t lda, const double* B, int64_t ldb, double eps);
 
+/* Allocation-free variant of h2_lowrank_update (the paper has no
+ * counterpart; this is an interface for callers that must not allocate
+ * device memory while they run: code recorded into CUDA graphs, code living
+ * in a fixed device-memory budget reserved at start-up, hosts whose device
+ * allocator belongs to another runtime).  Same arguments, same update, same
+ * results as h2_lowrank_update, but every piece of device scratch comes
+ * from one fixed 48 MiB array inside the library (held on every GPU that
+ * loads the library until the process exits), host planning uses static
+ * buffers, and no cudaMalloc/cudaFree or other allocating routine is
+ * called.  Limits, rejected with H2_EINVAL and a message naming the limit:
+ * at most 512 clusters per side in the matrix, 256 cluster tasks, 2048
+ * affected couplings, 4096 weight-stack blocks, 256 blocks inside the
+ * update, 1024 nearfield leaves inside the block; and k_t + u must fit the
+ * matrix's current rank capacity, because this entry point never grows
+ * storage.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current): make that first call
+ * before any stream capture.  All calls share the array and its contents
+ * persist between calls; calls whose GPU work may overlap (other streams or
+ * host threads) race and must be serialised by the caller.  Synchronizes. */
+h2_status h2_lowrank_update_noalloc(h2_ctx* ctx, h2_matrix* Z, int64_t block, int u, const double* A,
+                                    int64_t lda, const double* B, int64_t ldb, double eps);
+
 #ifdef __cplusplus
 }
 #endif

@@ -29,7 +29,7 @@ EXPORTS = [
     "h2_batch_create", "h2_batch_free", "h2_batch_factor_layout", "h2_batch_factor_sizes",
     "h2_batch_execute", "h2_batch_execute_host", "h2_batch_result_size", "h2_batch_apply",
     "h2_batch_stats", "h2_batch_set_timing", "h2_batch_phase_stats", "h2_batch_item_info", "h2_batch_item_tile",
-    "h2_batch_update_items", "h2_lowrank_update",
+    "h2_batch_update_items", "h2_lowrank_update", "h2_lowrank_update_noalloc",
 ]
 
 PHASES = ("base_weights", "rfactor", "norms", "weights", "truncate", "reproject")
@@ -98,6 +98,7 @@ _sig("h2_batch_item_info", _int, _p, _i64, _p)
 _sig("h2_batch_item_tile", _int, _p, _p, _i64, _int, _p)
 _sig("h2_batch_update_items", _int, _p, _i64, _p, _p)
 _sig("h2_lowrank_update", _int, _p, _p, _i64, _int, _p, _i64, _p, _i64, _dbl)
+_sig("h2_lowrank_update_noalloc", _int, _p, _p, _i64, _int, _p, _i64, _p, _i64, _dbl)
 
 
 def _check(status: int, ctx=None):
@@ -345,3 +346,11 @@ def h2_batch_update_items(P, j: int):
 def h2_lowrank_update(ctx, Z, block: int, u: int, A_dev: int, lda: int, B_dev: int, ldb: int, eps: float):
     _check(_lib.h2_lowrank_update(ctx, Z, int(block), int(u), C.c_void_p(A_dev), int(lda),
                                   C.c_void_p(B_dev), int(ldb), float(eps)), ctx)
+
+
+def h2_lowrank_update_noalloc(ctx, Z, block: int, u: int, A_dev: int, lda: int, B_dev: int, ldb: int,
+                              eps: float):
+    """Same update as h2_lowrank_update with no device allocation (fixed
+    library-internal scratch; see include/h2gb.h for the limits)."""
+    _check(_lib.h2_lowrank_update_noalloc(ctx, Z, int(block), int(u), C.c_void_p(A_dev), int(lda),
+                                          C.c_void_p(B_dev), int(ldb), float(eps)), ctx)
