@@ -207,6 +207,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-sample", type=int, default=24)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--count", type=int, default=WORK["count"],
+                    help="updates per batch (profiling runs use fewer; the benchmark uses 4096)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -228,6 +230,7 @@ def main():
     stream = torch.cuda.current_stream()
     ctx = b.h2_ctx_create(torch.cuda.current_device(), stream.cuda_stream)
     Z, blocks, A, B = lib_workload(b, ctx, rank_offset=rank)
+    blocks, A, B = blocks[:args.count], A[:args.count], B[:args.count]
     w = WORK
     P = b.h2_batch_create(ctx, Z, blocks, w["u"])
     lenA, lenB = b.h2_batch_factor_sizes(P)
@@ -319,7 +322,8 @@ def main():
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD_NAME, "mode": "isolated (each update reads the same base matrix)",
                        "l2": "512 MB buffer written between timed steps",
-                       "cluster_tasks": stats["cluster_tasks"], "block_tasks": stats["block_tasks"]},
+                       "updates": len(blocks), "cluster_tasks": stats["cluster_tasks"],
+                       "block_tasks": stats["block_tasks"]},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": stats["launches"] * args.steps,
             "clocks": clocks, "phases": phases, "gflop_per_step": stats["flops"] / 1e9}

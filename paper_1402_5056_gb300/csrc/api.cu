@@ -688,7 +688,7 @@ struct h2_batch {
   std::vector<int32_t> lvl_list;                // items sorted by level
   std::vector<int32_t> lvl_ptr;                 // per level
   std::vector<int32_t> lvl_maxrows;             // per level: bound on rows of the truncation
-  std::vector<int32_t> cl_list[2], cl_ptr[2];   // all clusters by level, per side
+  std::vector<int32_t> cl_list, cl_ptr;         // clusters of both sides by level (side << 30 | id)
   int depth = 0;
   int kl = 0;                                   // max extended rank
   int64_t qlen = 0;
@@ -701,7 +701,7 @@ struct h2_batch {
   Task* d_tasks = nullptr;
   NormTask* d_norms = nullptr;
   int32_t* d_lvl = nullptr;
-  int32_t* d_cl[2] = {nullptr, nullptr};
+  int32_t* d_cl = nullptr;
   ItemBuffers IB{};
   BaseWeights BW{};
   double* d_A = nullptr;   // staging for execute_host
@@ -851,15 +851,16 @@ void plan_batch(h2_batch& P) {
   }
   for (int l = 0; l < L; ++l)
     H2_REQUIRE(P.lvl_maxrows[l] <= 64, "h2_batch_create: leaf clusters above 64 indices are not supported");
-  // all clusters by level (prepass)
-  for (int sd = 0; sd < 2; ++sd) {
-    const ClusterTree& ct = *tr[sd];
-    P.cl_ptr[sd].assign(L + 1, 0);
-    for (int32_t c = 0; c < ct.count(); ++c) P.cl_ptr[sd][ct.level[c] + 1]++;
-    for (int l = 0; l < L; ++l) P.cl_ptr[sd][l + 1] += P.cl_ptr[sd][l];
-    P.cl_list[sd].assign(ct.count(), 0);
-    std::vector<int32_t> f2(P.cl_ptr[sd].begin(), P.cl_ptr[sd].end() - 1);
-    for (int32_t c = 0; c < ct.count(); ++c) P.cl_list[sd][f2[ct.level[c]]++] = c;
+  // all clusters of both sides by level (weights of the unchanged matrix)
+  P.cl_ptr.assign(L + 1, 0);
+  for (int sd = 0; sd < 2; ++sd)
+    for (int32_t c = 0; c < tr[sd]->count(); ++c) P.cl_ptr[tr[sd]->level[c] + 1]++;
+  for (int l = 0; l < L; ++l) P.cl_ptr[l + 1] += P.cl_ptr[l];
+  P.cl_list.assign(P.cl_ptr[L], 0);
+  {
+    std::vector<int32_t> f2(P.cl_ptr.begin(), P.cl_ptr.end() - 1);
+    for (int sd = 0; sd < 2; ++sd)
+      for (int32_t c = 0; c < tr[sd]->count(); ++c) P.cl_list[f2[tr[sd]->level[c]]++] = (sd << 30) | c;
   }
   // packed result layout: [ranks of items][couplings][leaf bases / transfers]
   int64_t off = (int64_t)P.items.size();
@@ -892,7 +893,7 @@ void alloc_batch(h2_ctx* ctx, h2_batch& P) {
   P.d_tasks = upload(P.tasks, st);
   P.d_norms = upload(P.norms, st);
   P.d_lvl = upload(P.lvl_list, st);
-  for (int sd = 0; sd < 2; ++sd) P.d_cl[sd] = upload(P.cl_list[sd], st);
+  P.d_cl = upload(P.cl_list, st);
   const size_t ni = P.items.size();
   P.IB.Rq = dalloc<double>(ni * kSlot);
   P.IB.Bw = dalloc<double>(ni * kSlot);
@@ -900,6 +901,7 @@ void alloc_batch(h2_ctx* ctx, h2_batch& P) {
   P.IB.F = dalloc<double>(ni * kSlot);
   P.IB.Q = dalloc<double>(P.qlen);
   P.IB.rank = dalloc<int32_t>(ni);
+  P.IB.own = dalloc<int32_t>(ni);
   P.IB.norms = dalloc<double>(P.norms.size());
   P.IB.S_out = dalloc<double>(P.tasks.size() * kSlot);
   P.IB.jac = dalloc<unsigned long long>(2 * ni);
@@ -918,8 +920,8 @@ void free_batch_device(h2_batch& P) {
   dfree(P.d_tasks);
   dfree(P.d_norms);
   dfree(P.d_lvl);
+  dfree(P.d_cl);
   for (int sd = 0; sd < 2; ++sd) {
-    dfree(P.d_cl[sd]);
     dfree(P.BW.G[sd]);
     dfree(P.BW.B[sd]);
   }
@@ -929,6 +931,7 @@ void free_batch_device(h2_batch& P) {
   dfree(P.IB.F);
   dfree(P.IB.Q);
   dfree(P.IB.rank);
+  dfree(P.IB.own);
   dfree(P.IB.norms);
   dfree(P.IB.S_out);
   dfree(P.IB.jac);
@@ -941,67 +944,40 @@ void free_batch_device(h2_batch& P) {
 
 void execute(h2_ctx* ctx, h2_batch& P, const double* A, const double* B, double eps) {
   const h2_matrix* Z = P.Z;
-  cudaStream_t st = ctx->stream;
-  const MatView M = view_of(Z);
-  const int L = P.depth + 1;
-  int64_t* pl = P.phase_launches;
-  for (int ph = 0; ph < H2_PHASE_COUNT; ++ph) pl[ph] = 0;
-  auto mark = [&](int ph) {
-    if (P.timing) H2_CUDA(cudaEventRecord(P.ev[ph], st));
-  };
-  // base-matrix weights, top-down (both sides)
-  mark(H2_PHASE_BASE_WEIGHTS);
-  for (int sd = 0; sd < 2; ++sd) {
-    const int32_t* dptr = sd == 0 ? Z->d_row_ptr : Z->d_col_ptr;
-    const int32_t* dadm = sd == 0 ? Z->d_row_adm : Z->d_col_adm;
-    const int32_t* doth = sd == 0 ? Z->d_blk_col : Z->d_blk_row;
-    for (int l = 0; l < L; ++l) {
-      const int n = P.cl_ptr[sd][l + 1] - P.cl_ptr[sd][l];
-      if (!n) continue;
-      launch_prepass(M, sd, P.d_cl[sd] + P.cl_ptr[sd][l], n, dptr, dadm, doth, P.BW, ctx->d_error, st);
-      ++pl[H2_PHASE_BASE_WEIGHTS];
-    }
-  }
-  // step 2: basis R-factors, bottom-up
-  mark(H2_PHASE_RFACTOR);
-  for (int l = L - 1; l >= 0; --l) {
-    const int n = P.lvl_ptr[l + 1] - P.lvl_ptr[l];
-    if (!n) continue;
-    launch_rfactor(M, P.d_items, P.d_lvl + P.lvl_ptr[l], n, P.u, A, B, P.IB, ctx->d_error, st);
-    ++pl[H2_PHASE_RFACTOR];
-  }
-  mark(H2_PHASE_NORMS);
-  if (!P.norms.empty()) {
-    launch_norms(M, P.d_items, P.d_norms, (int)P.norms.size(), P.u, P.IB, st);
-    ++pl[H2_PHASE_NORMS];
-  }
-  // step 3: weights, top-down
-  mark(H2_PHASE_WEIGHTS);
-  for (int l = 0; l < L; ++l) {
-    const int n = P.lvl_ptr[l + 1] - P.lvl_ptr[l];
-    if (!n) continue;
-    launch_weights(M, P.d_items, P.d_ents, P.d_lvl + P.lvl_ptr[l], n, P.u, P.BW, P.IB, ctx->d_error, st);
-    ++pl[H2_PHASE_WEIGHTS];
-  }
-  // step 4: truncation, bottom-up
-  mark(H2_PHASE_TRUNCATE);
-  for (int l = L - 1; l >= 0; --l) {
-    const int n = P.lvl_ptr[l + 1] - P.lvl_ptr[l];
-    if (!n) continue;
-    launch_truncate(M, P.d_items, P.d_lvl + P.lvl_ptr[l], n, P.u, P.kl, P.lvl_maxrows[l], eps, A, B, P.IB,
-                    ctx->d_error, st);
-    ++pl[H2_PHASE_TRUNCATE];
-  }
-  // step 5: reprojection
-  mark(H2_PHASE_REPROJECT);
-  if (!P.tasks.empty()) {
-    launch_reproject(M, P.d_items, P.d_tasks, (int)P.tasks.size(), P.u, P.IB, st);
-    ++pl[H2_PHASE_REPROJECT];
-  }
-  mark(H2_PHASE_COUNT);
-  H2_CUDA(cudaGetLastError());
+  Pipeline pp{};
+  pp.M = view_of(Z);
+  pp.BL.ptr[0] = Z->d_row_ptr;
+  pp.BL.ptr[1] = Z->d_col_ptr;
+  pp.BL.adm[0] = Z->d_row_adm;
+  pp.BL.adm[1] = Z->d_col_adm;
+  pp.BL.other[0] = Z->d_blk_col;
+  pp.BL.other[1] = Z->d_blk_row;
+  pp.BW = P.BW;
+  pp.IB = P.IB;
+  pp.items = P.d_items;
+  pp.ents = P.d_ents;
+  pp.tasks = P.d_tasks;
+  pp.norms = P.d_norms;
+  pp.lvl_list = P.d_lvl;
+  pp.lvl_ptr = P.lvl_ptr.data();
+  pp.lvl_rows = P.lvl_maxrows.data();
+  pp.cl_list = P.d_cl;
+  pp.cl_ptr = P.cl_ptr.data();
+  pp.levels = P.depth + 1;
+  pp.n_tasks = (int)P.tasks.size();
+  pp.n_norms = (int)P.norms.size();
+  pp.u = P.u;
+  pp.kl = P.kl;
+  pp.eps = eps;
+  pp.A = A;
+  pp.B = B;
+  pp.err = ctx->d_error;
+  pp.stream = ctx->stream;
+  pp.events = P.timing ? P.ev : nullptr;
+  pp.phase_launches = P.phase_launches;
+  run_pipeline(pp);
   int64_t launches = 0;
-  for (int ph = 0; ph < H2_PHASE_COUNT; ++ph) launches += pl[ph];
+  for (int ph = 0; ph < H2_PHASE_COUNT; ++ph) launches += P.phase_launches[ph];
   P.launches = launches;
   P.executed = true;
 }
@@ -1263,6 +1239,8 @@ void phase_flops(h2_ctx* ctx, const h2_batch* P, double f[H2_PHASE_COUNT]) {
     return m >= n ? 2 * m * n * n - 2.0 / 3.0 * n * n * n : 2 * n * m * m - 2.0 / 3.0 * m * m * m;
   };
   const h2_matrix* Z = P->Z;
+  // fold of ch rows into an upper n x n factor: 2 ch n^2 (Householder)
+  auto fold = [](double ch, double n) { return 2.0 * ch * n * n; };
   for (int sd = 0; sd < 2; ++sd) {
     const ClusterTree& ct = tree_of(Z, sd);
     const DeviceBasis& bs = basis_of(Z, sd);
@@ -1271,17 +1249,14 @@ void phase_flops(h2_ctx* ctx, const h2_batch* P, double f[H2_PHASE_COUNT]) {
     const std::vector<int32_t>& adm = sd == 0 ? Z->blocks.row_adm : Z->blocks.col_adm;
     for (int32_t c = 0; c < ct.count(); ++c) {
       const double k = bs.rank[c];
-      double rows = 0;
       for (int32_t e = ptr[c]; e < ptr[c + 1]; ++e) {
         const int32_t blk = Z->blocks.adm[adm[e]];
         const double l = o.rank[sd == 0 ? Z->blocks.col[blk] : Z->blocks.row[blk]];
-        rows += l;
-        f[H2_PHASE_BASE_WEIGHTS] += 2 * k * l;
+        f[H2_PHASE_BASE_WEIGHTS] += 2 * k * l + fold(l, k);   // norm, fold
       }
-      f[H2_PHASE_BASE_WEIGHTS] += qr(rows, k);
       if (ct.father[c] >= 0) {
         const double kf = bs.rank[ct.father[c]];
-        f[H2_PHASE_BASE_WEIGHTS] += kf * kf * k + qr(kf + k, k);
+        f[H2_PHASE_BASE_WEIGHTS] += kf * kf * k + fold(kf, k);
       }
     }
   }
@@ -1298,30 +1273,25 @@ void phase_flops(h2_ctx* ctx, const h2_batch* P, double f[H2_PHASE_COUNT]) {
       const double k0 = P->items[it.son0].k, k1 = P->items[it.son1].k;
       f[H2_PHASE_RFACTOR] += (k0 + u) * k0 * k + (k1 + u) * k1 * k + qr(k0 + k1 + 2 * u, K);
     }
-    // weights: stack rows folded into the K x K factor
-    double rows = 0;
-    if (!(it.flags & kItemInside)) {
-      rows += k;
-    } else {
+    // weights: outside blocks folded into k columns by the task itself when
+    // some block lies inside the update (otherwise the precomputed G_t), then
+    // the inside blocks and the father's part folded into K columns
+    if (it.flags & kItemInside) {
       for (int32_t e = it.ent_begin; e < it.ent_end; ++e) {
         const Entry& en = P->ents[e];
         if (en.other < 0) {
           const double l = basis_of(Z, 1 - it.side).rank[en.other_cluster];
-          rows += l;
-          f[H2_PHASE_WEIGHTS] += 2 * k * l;
+          f[H2_PHASE_WEIGHTS] += 2 * k * l + fold(l, k);
         } else {
           const double l = P->items[en.other].k;
-          rows += l + u;
-          f[H2_PHASE_WEIGHTS] += (l + u) * l * k;
+          f[H2_PHASE_WEIGHTS] += (l + u) * l * k + fold(l + u, K);
         }
       }
     }
     if (!(it.flags & kItemTreeRoot)) {
       const double kf = (it.flags & kItemRoot) ? it.kf : it.kf + u;
-      f[H2_PHASE_WEIGHTS] += kf * it.kf * k;
-      rows += kf;
+      f[H2_PHASE_WEIGHTS] += kf * it.kf * k + fold(kf, K);
     }
-    f[H2_PHASE_WEIGHTS] += 2 * K * K * rows;   // fold of `rows` rows into an upper K x K factor
     // truncation
     const double m = (it.flags & kItemLeaf) ? it.size : rk[it.son0] + rk[it.son1];
     double ft = 0;
@@ -1330,6 +1300,7 @@ void phase_flops(h2_ctx* ctx, const h2_batch* P, double f[H2_PHASE_COUNT]) {
       ft += 2 * rk[it.son0] * k0 * k + 2 * rk[it.son1] * k1 * k;
     }
     ft += m * K * K;                                               // V^ times triangular B~^*
+    if (K >= 2 && m > 0) ft += 2 * (4 * K * K * K) + 2 * m * K * K;  // Newton-Schulz (2 steps), M V
     ft += 6.0 * m * (double)jac[2 * i] + 6.0 * m * (double)jac[2 * i + 1];
     ft += 2 * m * K * rk[i];                                       // R_t = Q^* V^
     if ((it.flags & kItemRoot) && !(it.flags & kItemTreeRoot)) ft += 2 * rk[i] * k * it.kf;

@@ -53,7 +53,8 @@ constexpr size_t kOffF = kOffRt + align256((size_t)kNaItems * kSlot * 8);
 constexpr size_t kOffQ = kOffF + align256((size_t)kNaItems * kSlot * 8);
 constexpr size_t kOffS = kOffQ + align256((size_t)kNaQ * 8);
 constexpr size_t kOffRank = kOffS + align256((size_t)kNaTasks * kSlot * 8);
-constexpr size_t kOffNorm = kOffRank + align256((size_t)kNaItems * 4);
+constexpr size_t kOffOwn = kOffRank + align256((size_t)kNaItems * 4);
+constexpr size_t kOffNorm = kOffOwn + align256((size_t)kNaItems * 4);
 constexpr size_t kOffJac = kOffNorm + align256((size_t)kNaNorms * 8);
 constexpr size_t kOffItems = kOffJac + align256((size_t)kNaItems * 16);
 constexpr size_t kOffEnts = kOffItems + align256((size_t)kNaItems * sizeof(Item));
@@ -81,8 +82,8 @@ struct HostPlan {
   int32_t lvl_list[kNaItems];
   int32_t lvl_ptr[kNaLevels + 1];
   int32_t lvl_rows[kNaLevels];
-  int32_t cl_list[2][kNaClusters];
-  int32_t cl_ptr[2][kNaLevels + 1];
+  int32_t cl_list[2 * kNaClusters];
+  int32_t cl_ptr[kNaLevels + 1];
   int32_t item_of[2][kNaClusters];
   int32_t stack[kNaClusters];
   int32_t sub[2][kNaClusters];
@@ -247,15 +248,14 @@ h2_status plan_single(const h2_matrix* Z, int32_t b0, int u, int64_t lda, int64_
   }
   for (int l = 0; l < L; ++l)
     if (P.lvl_rows[l] > 64) return fail(H2_EINVAL, "leaf clusters above 64 indices are not supported");
-  // all clusters by level, for the weights of the unchanged matrix
-  for (int sd = 0; sd < 2; ++sd) {
-    const ClusterTree& ct = tree(Z, sd);
-    for (int l = 0; l <= L; ++l) P.cl_ptr[sd][l] = 0;
-    for (int32_t c = 0; c < ct.count(); ++c) P.cl_ptr[sd][ct.level[c] + 1]++;
-    for (int l = 0; l < L; ++l) P.cl_ptr[sd][l + 1] += P.cl_ptr[sd][l];
-    for (int l = 0; l < L; ++l) fill[l] = P.cl_ptr[sd][l];
-    for (int32_t c = 0; c < ct.count(); ++c) P.cl_list[sd][fill[ct.level[c]]++] = c;
-  }
+  // all clusters of both sides by level, for the weights of the unchanged matrix
+  for (int l = 0; l <= L; ++l) P.cl_ptr[l] = 0;
+  for (int sd = 0; sd < 2; ++sd)
+    for (int32_t c = 0; c < tree(Z, sd).count(); ++c) P.cl_ptr[tree(Z, sd).level[c] + 1]++;
+  for (int l = 0; l < L; ++l) P.cl_ptr[l + 1] += P.cl_ptr[l];
+  for (int l = 0; l < L; ++l) fill[l] = P.cl_ptr[l];
+  for (int sd = 0; sd < 2; ++sd)
+    for (int32_t c = 0; c < tree(Z, sd).count(); ++c) P.cl_list[fill[tree(Z, sd).level[c]]++] = (sd << 30) | c;
   return H2_OK;
 }
 
@@ -283,10 +283,8 @@ h2_status run(h2_ctx* ctx, h2_matrix* Z, int32_t b0, int u, const double* A, int
   if (P.n_tasks) NA_CUDA(cudaMemcpyAsync(d_tasks, P.tasks, P.n_tasks * sizeof(Task), cudaMemcpyHostToDevice, s));
   if (P.n_norms) NA_CUDA(cudaMemcpyAsync(d_nt, P.norms, P.n_norms * sizeof(NormTask), cudaMemcpyHostToDevice, s));
   NA_CUDA(cudaMemcpyAsync(d_lvl, P.lvl_list, P.n_items * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-  const int32_t ncl0 = Z->rows.count();
-  NA_CUDA(cudaMemcpyAsync(d_cl, P.cl_list[0], ncl0 * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-  NA_CUDA(cudaMemcpyAsync(d_cl + kNaClusters, P.cl_list[1], Z->cols.count() * sizeof(int32_t),
-                          cudaMemcpyHostToDevice, s));
+  const int L = std::max(Z->rows.depth, Z->cols.depth) + 1;
+  NA_CUDA(cudaMemcpyAsync(d_cl, P.cl_list, P.cl_ptr[L] * sizeof(int32_t), cudaMemcpyHostToDevice, s));
   ItemBuffers IB{};
   IB.Rq = reinterpret_cast<double*>(base + kOffRq);
   IB.Bw = reinterpret_cast<double*>(base + kOffBw);
@@ -294,6 +292,7 @@ h2_status run(h2_ctx* ctx, h2_matrix* Z, int32_t b0, int u, const double* A, int
   IB.F = reinterpret_cast<double*>(base + kOffF);
   IB.Q = reinterpret_cast<double*>(base + kOffQ);
   IB.rank = reinterpret_cast<int32_t*>(base + kOffRank);
+  IB.own = reinterpret_cast<int32_t*>(base + kOffOwn);
   IB.norms = reinterpret_cast<double*>(base + kOffNorm);
   IB.S_out = reinterpret_cast<double*>(base + kOffS);
   IB.jac = reinterpret_cast<unsigned long long*>(base + kOffJac);
@@ -316,31 +315,39 @@ h2_status run(h2_ctx* ctx, h2_matrix* Z, int32_t b0, int u, const double* A, int
   M.subtree[1] = Z->d_subtree_c;
   M.S = Z->d_S;
   M.kcap = Z->kcap;
-  const int L = std::max(Z->rows.depth, Z->cols.depth) + 1;
   // the same kernels as the allocating path, on the fixed scratch
-  for (int sd = 0; sd < 2; ++sd)
-    for (int l = 0; l < L; ++l) {
-      const int n = P.cl_ptr[sd][l + 1] - P.cl_ptr[sd][l];
-      if (n)
-        launch_prepass(M, sd, d_cl + sd * kNaClusters + P.cl_ptr[sd][l], n, sd == 0 ? Z->d_row_ptr : Z->d_col_ptr,
-                       sd == 0 ? Z->d_row_adm : Z->d_col_adm, sd == 0 ? Z->d_blk_col : Z->d_blk_row, BW,
-                       ctx->d_error, s);
-    }
-  for (int l = L - 1; l >= 0; --l) {
-    const int n = P.lvl_ptr[l + 1] - P.lvl_ptr[l];
-    if (n) launch_rfactor(M, d_items, d_lvl + P.lvl_ptr[l], n, u, A, B, IB, ctx->d_error, s);
-  }
-  if (P.n_norms) launch_norms(M, d_items, d_nt, P.n_norms, u, IB, s);
-  for (int l = 0; l < L; ++l) {
-    const int n = P.lvl_ptr[l + 1] - P.lvl_ptr[l];
-    if (n) launch_weights(M, d_items, d_ents, d_lvl + P.lvl_ptr[l], n, u, BW, IB, ctx->d_error, s);
-  }
-  for (int l = L - 1; l >= 0; --l) {
-    const int n = P.lvl_ptr[l + 1] - P.lvl_ptr[l];
-    if (n)
-      launch_truncate(M, d_items, d_lvl + P.lvl_ptr[l], n, u, P.kl, P.lvl_rows[l], eps, A, B, IB, ctx->d_error, s);
-  }
-  if (P.n_tasks) launch_reproject(M, d_items, d_tasks, P.n_tasks, u, IB, s);
+  Pipeline pp{};
+  pp.M = M;
+  pp.BL.ptr[0] = Z->d_row_ptr;
+  pp.BL.ptr[1] = Z->d_col_ptr;
+  pp.BL.adm[0] = Z->d_row_adm;
+  pp.BL.adm[1] = Z->d_col_adm;
+  pp.BL.other[0] = Z->d_blk_col;
+  pp.BL.other[1] = Z->d_blk_row;
+  pp.BW = BW;
+  pp.IB = IB;
+  pp.items = d_items;
+  pp.ents = d_ents;
+  pp.tasks = d_tasks;
+  pp.norms = d_nt;
+  pp.lvl_list = d_lvl;
+  pp.lvl_ptr = P.lvl_ptr;
+  pp.lvl_rows = P.lvl_rows;
+  pp.cl_list = d_cl;
+  pp.cl_ptr = P.cl_ptr;
+  pp.levels = L;
+  pp.n_tasks = P.n_tasks;
+  pp.n_norms = P.n_norms;
+  pp.u = u;
+  pp.kl = P.kl;
+  pp.eps = eps;
+  pp.A = A;
+  pp.B = B;
+  pp.err = ctx->d_error;
+  pp.stream = s;
+  pp.events = nullptr;
+  pp.phase_launches = nullptr;
+  run_pipeline(pp);
   NA_CUDA(cudaGetLastError());
   // commit (Section 5): new bases, transfers, couplings, nearfield inside b0
   NA_CUDA(cudaMemcpyAsync(P.rank, IB.rank, P.n_items * sizeof(int32_t), cudaMemcpyDeviceToHost, s));

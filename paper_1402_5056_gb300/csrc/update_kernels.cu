@@ -29,42 +29,41 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // R (ncol x ncol, upper triangular, shared, ld kLdr) <- R-factor of [R; X].
-// X has `ch` rows; lane c < ncol holds column c of X in x[].  Householder
-// reflections in the LAPACK dlarfg convention; R keeps ncol rows (rows
-// beyond the rank stay zero).
-__device__ void fold(double* R, double (&x)[kCh], int ch, int ncol, double* vb, int lane) {
+// X has `ch` rows; lane c < ncol holds column c of X in x[].  One
+// Householder reflection H = I - tau u u^* per column j, u = [R_jj - beta;
+// X[:, j]], beta = -sign(R_jj) ||[R_jj; X[:, j]]||, tau = -1 / (beta u_0).
+// The pivot column is spread over the lanes (lane i takes row i) so that
+// its norm is a warp reduction and every float64 instruction of the step
+// works on all lanes; R keeps ncol rows (rows beyond the rank stay zero).
+__device__ __forceinline__ void fold(double* R, double (&x)[kCh], int ch, int ncol, double* vb, int lane) {
   for (int j = 0; j < ncol; ++j) {
-    if (lane == j) {
-      double s2 = 0.0;
+    double xi = 0.0;
 #pragma unroll
-      for (int i = 0; i < kCh; ++i)
-        if (i < ch) s2 = fma(x[i], x[i], s2);
-      double tau = 0.0;
-      if (s2 > 0.0) {
-        const double alpha = R[j + j * kLdr];
-        const double nrm = sqrt(fma(alpha, alpha, s2));
-        const double beta = alpha >= 0.0 ? -nrm : nrm;
-        tau = (beta - alpha) / beta;
-        const double sc = 1.0 / (alpha - beta);
-#pragma unroll
-        for (int i = 0; i < kCh; ++i)
-          if (i < ch) {
-            vb[i] = x[i] * sc;
-            x[i] = 0.0;
-          }
-        R[j + j * kLdr] = beta;
+    for (int i = 0; i < kCh; ++i)
+      if (i < ch) {
+        const double t = __shfl_sync(kFull, x[i], j);
+        if (lane == i) xi = t;
       }
-      vb[kCh] = tau;
-    }
+    const double s2 = warp_sum(xi * xi);
+    if (s2 == 0.0) continue;   // nothing below the diagonal: H = I
+    const double alpha = R[j + j * kLdr];
+    const double nrm = sqrt(fma(alpha, alpha, s2));
+    const double beta = alpha >= 0.0 ? -nrm : nrm;
+    const double u0 = alpha - beta;
+    const double tau = -1.0 / (beta * u0);
+    if (lane < ch) vb[lane] = xi;
     __syncwarp();
-    const double tau = vb[kCh];
-    if (tau != 0.0 && lane > j && lane < ncol) {
-      double w = R[j + lane * kLdr];
+    if (lane == j) {
+      R[j + j * kLdr] = beta;
+#pragma unroll
+      for (int i = 0; i < kCh; ++i) x[i] = 0.0;
+    } else if (lane > j && lane < ncol) {
+      double w = u0 * R[j + lane * kLdr];
 #pragma unroll
       for (int i = 0; i < kCh; ++i)
         if (i < ch) w = fma(vb[i], x[i], w);
       w *= tau;
-      R[j + lane * kLdr] -= w;
+      R[j + lane * kLdr] = fma(-w, u0, R[j + lane * kLdr]);
 #pragma unroll
       for (int i = 0; i < kCh; ++i)
         if (i < ch) x[i] = fma(-w, vb[i], x[i]);
@@ -86,59 +85,74 @@ __device__ __forceinline__ void store_tile(double* dst, const double* R, int nco
   __syncwarp();
 }
 
+__device__ __forceinline__ int jacobi_partner(int lane, int r, int n2) {
+  // round-robin tournament over n2 (even) players: player n2-1 meets r,
+  // the others meet (2r - lane) mod (n2-1); lanes >= n2 sit out
+  const int nr = n2 - 1;
+  if (lane >= n2) return lane;
+  if (lane == nr) return r;
+  if (lane == r) return nr;
+  int p = (2 * r - lane) % nr;
+  return p < 0 ? p + nr : p;
+}
+
 // One-sided (Hestenes) Jacobi on the columns held by the lanes (a[] rows
-// valid): on return the columns are U * Sigma with mutually orthogonal
-// columns.  Round-robin pairing; both lanes of a pair evaluate the same
-// dot products in the same order, so they take the same rotation.
+// valid, zero below): on return the columns are U * Sigma with mutually
+// orthogonal columns.  The two lanes of a pair split the dot products (the
+// first lane takes the even rows, the second the odd rows, one row each per
+// instruction) and add the partial sums in the same order, so both take the
+// same rotation.
 template <int MR>
-__device__ void jacobi(double (&a)[MR], int rows, int ncol, int lane, unsigned long long* cnt,
+__device__ __forceinline__ void jacobi(double (&a)[MR], int rows, int ncol, int lane, unsigned long long* cnt,
                        int* err) {
   const int n2 = ncol + (ncol & 1);
   const int nr = n2 - 1;
-  const double tol = 16.0 * DBL_EPSILON;
-  unsigned long long pairs = 0, rots = 0;
+  const double tol2 = (16.0 * DBL_EPSILON) * (16.0 * DBL_EPSILON);
+  unsigned long long pairs = 0, rots = 0, sweeps = 0;
   bool converged = (ncol < 2);
   for (int sweep = 0; sweep < kMaxSweeps && !converged; ++sweep) {
     int any = 0;
+    ++sweeps;
     for (int r = 0; r < nr; ++r) {
-      int p;
-      if (lane >= n2) {
-        p = lane;
-      } else if (lane == nr) {
-        p = r;
-      } else if (lane == r) {
-        p = nr;
-      } else {
-        p = (2 * r - lane) % nr;
-        if (p < 0) p += nr;
-      }
+      const int p = jacobi_partner(lane, r, n2);
       const bool lo = lane < p;
       double al = 0.0, be = 0.0, ga = 0.0;
 #pragma unroll
-      for (int i = 0; i < MR; ++i)
-        if (i < rows) {
-          const double o = __shfl_sync(kFull, a[i], p);
-          const double xx = lo ? a[i] : o;
-          const double yy = lo ? o : a[i];
+      for (int h = 0; h < MR / 2; ++h)
+        if (2 * h < rows) {
+          const double r0 = a[2 * h], r1 = a[2 * h + 1];
+          const double got = __shfl_sync(kFull, lo ? r1 : r0, p);
+          const double xx = lo ? r0 : got;
+          const double yy = lo ? got : r1;
           al = fma(xx, xx, al);
           be = fma(yy, yy, be);
           ga = fma(xx, yy, ga);
         }
+      al += __shfl_sync(kFull, al, p);
+      be += __shfl_sync(kFull, be, p);
+      ga += __shfl_sync(kFull, ga, p);
       const bool active = lane < n2 && p != lane;
-      const bool rot = active && al > 0.0 && be > 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be);
+      // rotate when |gamma| > tol sqrt(alpha beta); the columns are scaled
+      // to max |entry| < 1, so the squares neither overflow nor matter when
+      // they underflow
+      const bool rot = active && ga * ga > tol2 * (al * be);
       double c = 1.0, s = 0.0;
       if (rot) {
-        const double zeta = (be - al) / (2.0 * ga);
-        const double t = copysign(1.0, zeta) / (fabs(zeta) + hypot(1.0, zeta));
-        c = 1.0 / sqrt(fma(t, t, 1.0));
+        // t = tan(theta) of the rotation that makes the pair orthogonal:
+        // t = gamma / (d + sign(d) sqrt(d^2 + gamma^2)), d = (beta - alpha) / 2
+        const double d = 0.5 * (be - al);
+        const double t = ga / (d + copysign(sqrt(fma(d, d, ga * ga)), d));
+        c = rsqrt(fma(t, t, 1.0));
         s = c * t;
       }
+      if (__any_sync(kFull, rot)) {
 #pragma unroll
-      for (int i = 0; i < MR; ++i)
-        if (i < rows) {
-          const double o = __shfl_sync(kFull, a[i], p);
-          if (rot) a[i] = lo ? fma(c, a[i], -s * o) : fma(s, o, c * a[i]);
-        }
+        for (int i = 0; i < MR; ++i)
+          if (i < rows) {
+            const double o = __shfl_sync(kFull, a[i], p);
+            if (rot) a[i] = lo ? fma(c, a[i], -s * o) : fma(s, o, c * a[i]);
+          }
+      }
       if (active && lo) {
         pairs += 1;
         rots += rot ? 1 : 0;
@@ -161,16 +175,106 @@ __device__ void jacobi(double (&a)[MR], int rows, int ncol, int lane, unsigned l
   }
 }
 
+// Float32 one-sided Jacobi used as a preconditioner: rotates the float copy
+// af of the columns until they are orthogonal to float accuracy and
+// accumulates the rotations in vf (lane c holds column c of V, ncol
+// entries), so that M V has nearly orthogonal columns.
+template <int MR>
+__device__ __forceinline__ void jacobi32(float (&af)[MR], float (&vf)[32], int rows, int ncol, int lane) {
+  const int n2 = ncol + (ncol & 1);
+  const int nr = n2 - 1;
+  const float tol = 1.0e-6f;
+  if (ncol < 2) return;
+  for (int sweep = 0; sweep < 12; ++sweep) {
+    int any = 0;
+    for (int r = 0; r < nr; ++r) {
+      const int p = jacobi_partner(lane, r, n2);
+      const bool lo = lane < p;
+      float al = 0.f, be = 0.f, ga = 0.f;
+#pragma unroll
+      for (int i = 0; i < MR; ++i)
+        if (i < rows) {
+          const float o = __shfl_sync(kFull, af[i], p);
+          const float xx = lo ? af[i] : o;
+          const float yy = lo ? o : af[i];
+          al = fmaf(xx, xx, al);
+          be = fmaf(yy, yy, be);
+          ga = fmaf(xx, yy, ga);
+        }
+      const bool active = lane < n2 && p != lane;
+      const bool rot = active && al > 0.f && be > 0.f && fabsf(ga) > tol * sqrtf(al) * sqrtf(be);
+      float c = 1.f, s = 0.f;
+      if (rot) {
+        const float zeta = (be - al) / (2.f * ga);
+        const float t = copysignf(1.f, zeta) / (fabsf(zeta) + hypotf(1.f, zeta));
+        c = rsqrtf(fmaf(t, t, 1.f));
+        s = c * t;
+      }
+      if (__any_sync(kFull, rot)) {
+#pragma unroll
+        for (int i = 0; i < MR; ++i)
+          if (i < rows) {
+            const float o = __shfl_sync(kFull, af[i], p);
+            if (rot) af[i] = lo ? fmaf(c, af[i], -s * o) : fmaf(s, o, c * af[i]);
+          }
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (j < ncol) {
+            const float o = __shfl_sync(kFull, vf[j], p);
+            if (rot) vf[j] = lo ? fmaf(c, vf[j], -s * o) : fmaf(s, o, c * vf[j]);
+          }
+      }
+      any |= rot ? 1 : 0;
+    }
+    if (!__any_sync(kFull, any)) break;
+  }
+}
+
+// Two Newton-Schulz steps V <- V (3I - V^* V) / 2 in float64 on the columns
+// v (lane c holds column c, ncol entries) with V staged in Vs (ld 33):
+// turns the float32-accurate rotation product into an orthogonal matrix to
+// float64 accuracy.
+__device__ __forceinline__ void orthonormalize(double (&v)[32], double* Vs, int ncol, int lane) {
+  for (int step = 0; step < 2; ++step) {
+    if (lane < ncol)
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (j < ncol) Vs[j + lane * 33] = v[j];
+    __syncwarp();
+    double g[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      double x = 0.0;
+      if (i < ncol && lane < ncol)
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (j < ncol) x = fma(Vs[j + i * 33], v[j], x);
+      g[i] = x;
+    }
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      double x = 0.0;
+      if (j < ncol && lane < ncol)
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+          if (i < ncol) x = fma(Vs[j + i * 33], g[i], x);
+      v[j] = fma(1.5, v[j], -0.5 * x);
+    }
+    __syncwarp();
+  }
+}
+
 // --------------------------------------------------------------- prepass
-// Weights of the unchanged matrix for every cluster of one level (Section
-// 4, Algorithm of the weight matrices):
-//   G_t  = qr_R([omega_b S_b^* for b in row(t)])
-//   B~_t = qr_R([G_t; B~_{t+} E_t^*])
+// Weights of the unchanged matrix (Section 4, the recursive construction of
+// the weight matrices), for both sides:
+//   G_t  = qr_R([omega_b S_b^* for b in row(t)])      (k_blockweights, all
+//          clusters in one launch: G_t does not depend on the father)
+//   B~_t = qr_R([G_t; B~_{t+} E_t^*])                  (k_baseweights, one
+//          launch per level, top-down)
 // omega_b = sqrt(#T_t) / ||S_b||_F (block-relative reading).  Column side:
-// the same with S_b instead of S_b^* and col(s).
-__global__ void k_prepass(MatView M, int side, const int32_t* __restrict__ clusters, int n,
-                          const int32_t* __restrict__ ptr, const int32_t* __restrict__ adm,
-                          const int32_t* __restrict__ other_cl, BaseWeights BW, int* err) {
+// S_b instead of S_b^* and col(s).  Cluster lists encode side << 30 | id.
+__global__ void k_blockweights(MatView M, const int32_t* __restrict__ list, int n, BlockLists BL,
+                               BaseWeights BW, int* err) {
   extern __shared__ double smem[];
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
@@ -178,7 +282,8 @@ __global__ void k_prepass(MatView M, int side, const int32_t* __restrict__ clust
   if (idx >= n) return;
   double* R = smem + w * (32 * kLdr + kCh + 1);
   double* vb = R + 32 * kLdr;
-  const int c = clusters[idx];
+  const int side = list[idx] >> 30;
+  const int c = list[idx] & 0x3fffffff;
   const int k = M.rank[side][c];
   const int kcap = M.kcap;
   if (k > 32) {
@@ -188,9 +293,9 @@ __global__ void k_prepass(MatView M, int side, const int32_t* __restrict__ clust
   zero_tile(R, lane);
   const double st = sqrt((double)M.subtree[side][c]);
   double x[kCh];
-  for (int e = ptr[c]; e < ptr[c + 1]; ++e) {
-    const int slot = adm[e];
-    const int o = other_cl[slot];
+  for (int e = BL.ptr[side][c]; e < BL.ptr[side][c + 1]; ++e) {
+    const int slot = BL.adm[side][e];
+    const int o = BL.other[side][slot];
     const int l = M.rank[1 - side][o];
     const double* S = M.S + (size_t)slot * kcap * kcap;
     // ||S_b||_F
@@ -205,26 +310,49 @@ __global__ void k_prepass(MatView M, int side, const int32_t* __restrict__ clust
     const double nrm = sqrt(warp_sum(part));
     const double om = nrm > 0.0 ? st / nrm : 0.0;
     // rows of the stack: side 0 -> S^* (l x k), side 1 -> S (l x k); l = other side's rank
-    const int ch = l;
 #pragma unroll
     for (int i = 0; i < kCh; ++i) {
       double v = 0.0;
-      if (i < ch && lane < k) v = side == 0 ? S[lane + i * kcap] : S[i + lane * kcap];
+      if (i < l && lane < k) v = side == 0 ? S[lane + i * kcap] : S[i + lane * kcap];
       x[i] = om * v;
     }
-    fold(R, x, ch, k, vb, lane);
+    fold(R, x, l, k, vb, lane);
   }
   store_tile(BW.G[side] + (size_t)c * kSlot, R, k, lane);
+}
+
+__global__ void k_baseweights(MatView M, const int32_t* __restrict__ list, int n, BaseWeights BW, int* err) {
+  extern __shared__ double smem[];
+  const int lane = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5;
+  const int idx = blockIdx.x * (blockDim.x >> 5) + w;
+  if (idx >= n) return;
+  double* R = smem + w * (32 * kLdr + kCh + 1);
+  double* vb = R + 32 * kLdr;
+  const int side = list[idx] >> 30;
+  const int c = list[idx] & 0x3fffffff;
+  const int k = M.rank[side][c];
+  const int kcap = M.kcap;
+  if (k > 32) {
+    if (lane == 0) flag(err, kErrCols);
+    return;
+  }
+  zero_tile(R, lane);
+  const double* G = BW.G[side] + (size_t)c * kSlot;
+  if (lane < k)
+    for (int i = 0; i <= lane; ++i) R[i + lane * kLdr] = G[i + lane * 32];
+  __syncwarp();
   const int f = M.father[side][c];
   if (f >= 0) {
     const int kf = M.rank[side][f];
     const double* P = BW.B[side] + (size_t)f * kSlot;
     const double* E = M.transfer[side] + (size_t)c * kcap * kcap;   // k x kf
+    double x[kCh];
 #pragma unroll
     for (int i = 0; i < kCh; ++i) {
       double v = 0.0;
       if (i < kf && lane < k)
-        for (int q = 0; q < kf; ++q) v = fma(P[i + q * 32], E[lane + q * kcap], v);
+        for (int q = i; q < kf; ++q) v = fma(P[i + q * 32], E[lane + q * kcap], v);
       x[i] = v;
     }
     fold(R, x, kf, k, vb, lane);
@@ -344,8 +472,84 @@ __global__ void k_norms(MatView M, const Item* __restrict__ items, const NormTas
 
 // ------------------------------------------------------------- step 3
 // Weights top-down: B~_t = qr_R([omega_b R_{W,s} S~_b^* for s in row(t);
-// B~_{t+} E~_t^*]).  Blocks outside the update enter through the
-// precomputed G_t when no block of row(t) lies inside the update.
+// B~_{t+} E~_t^*]) (Sections 4 and 5).  The blocks of row(t) whose other
+// cluster lies outside the update contribute omega_b [S_b^*, 0]; when
+// V_t is orthonormal and no block of row(t) lies inside the update their
+// R-factor is the precomputed G_t.  Otherwise k_outside folds them first,
+// for every such cluster task at once (it does not depend on the father).
+
+// V_t orthonormal <=> the leading k x k block of its R-factor is diag(+-1);
+// then ||Z~|_b||_F = ||R_kk S_b||_F equals ||S_b||_F for outside blocks.
+__device__ __forceinline__ bool basis_orthonormal(const double* Rown, int k, int lane) {
+  bool orth = true;
+  if (lane < k)
+    for (int i = 0; i < k; ++i) {
+      const double v = Rown[i + lane * 32];
+      const double want = (i == lane) ? copysign(1.0, v) : 0.0;
+      if (fabs(v - want) > 64.0 * DBL_EPSILON) orth = false;
+    }
+  return __all_sync(kFull, orth);
+}
+
+__global__ void k_outside(MatView M, const Item* __restrict__ items, const Entry* __restrict__ ents,
+                          const int32_t* __restrict__ list, int n, int u, ItemBuffers IB) {
+  extern __shared__ double smem[];
+  const int lane = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5;
+  const int idx = blockIdx.x * (blockDim.x >> 5) + w;
+  if (idx >= n) return;
+  double* R = smem + w * (32 * kLdr + kCh + 1);
+  double* vb = R + 32 * kLdr;
+  const int id = list[idx];
+  const Item it = items[id];
+  const int side = it.side;
+  const int k = it.k;
+  const int kcap = M.kcap;
+  const double* Rown = IB.Rq + (size_t)id * kSlot;
+  const bool orth = basis_orthonormal(Rown, k, lane);
+  const bool own = (it.flags & kItemInside) || !orth;
+  if (lane == 0) IB.own[id] = own ? 1 : 0;
+  if (!own) return;
+  zero_tile(R, lane);
+  const double st = sqrt((double)M.subtree[side][it.cluster]);
+  double x[kCh];
+  for (int e = it.ent_begin; e < it.ent_end; ++e) {
+    const Entry en = ents[e];
+    if (en.other >= 0) continue;
+    const double* S = M.S + (size_t)en.slot * kcap * kcap;
+    const int l = M.rank[1 - side][en.other_cluster];
+    double part = 0.0;
+    if (orth) {
+      // ||S_b||_F
+      const int scols = side == 0 ? l : k;
+      const int srows = side == 0 ? k : l;
+      if (lane < scols)
+        for (int i = 0; i < srows; ++i) {
+          const double v = S[i + lane * kcap];
+          part = fma(v, v, part);
+        }
+    } else if (lane < l) {
+      // ||R_kk S_b||_F (side 0, S is k x l) or ||S_b R_kk^*||_F (side 1, S is l x k)
+      for (int p = 0; p < k; ++p) {
+        double y = 0.0;
+        for (int q = p; q < k; ++q)
+          y = fma(Rown[p + q * 32], side == 0 ? S[q + lane * kcap] : S[lane + q * kcap], y);
+        part = fma(y, y, part);
+      }
+    }
+    const double nrm = sqrt(warp_sum(part));
+    const double om = nrm > 0.0 ? st / nrm : 0.0;
+#pragma unroll
+    for (int i = 0; i < kCh; ++i) {
+      double v = 0.0;
+      if (i < l && lane < k) v = side == 0 ? S[lane + i * kcap] : S[i + lane * kcap];
+      x[i] = om * v;
+    }
+    fold(R, x, l, k, vb, lane);
+  }
+  store_tile(IB.Bw + (size_t)id * kSlot, R, k, lane);
+}
+
 __global__ void k_weights(MatView M, const Item* __restrict__ items, const Entry* __restrict__ ents,
                           const int32_t* __restrict__ list, int n, int u, BaseWeights BW,
                           ItemBuffers IB, int* err) {
@@ -365,74 +569,42 @@ __global__ void k_weights(MatView M, const Item* __restrict__ items, const Entry
   zero_tile(R, lane);
   double x[kCh];
   const double st = sqrt((double)M.subtree[side][it.cluster]);
-  // Is V_t orthonormal?  Then the leading k x k block of its R-factor is
-  // diag(+-1) and ||Z~|_b||_F = ||R_kk S_b||_F equals ||S_b||_F for the
-  // blocks whose other cluster lies outside the update.
-  const double* Rown = IB.Rq + (size_t)id * kSlot;
-  bool orth = true;
-  if (lane < k)
-    for (int i = 0; i < k; ++i) {
-      const double v = Rown[i + lane * 32];
-      const double want = (i == lane) ? copysign(1.0, v) : 0.0;
-      if (fabs(v - want) > 64.0 * DBL_EPSILON) orth = false;
-    }
-  orth = __all_sync(kFull, orth);
-  if (!(it.flags & kItemInside) && orth) {
-    const double* G = BW.G[side] + (size_t)it.cluster * kSlot;
+  // outside blocks: their R-factor, padded with zero columns to K
+  {
+    const double* G = IB.own[id] ? IB.Bw + (size_t)id * kSlot : BW.G[side] + (size_t)it.cluster * kSlot;
     if (lane < k)
       for (int i = 0; i <= lane; ++i) R[i + lane * kLdr] = G[i + lane * 32];
     __syncwarp();
-  } else {
+  }
+  // blocks inside the update: omega_b R_{W,s} S~_b^* (K_s x K_t)
+  if (it.flags & kItemInside)
     for (int e = it.ent_begin; e < it.ent_end; ++e) {
       const Entry en = ents[e];
+      if (en.other < 0) continue;
       const double* S = M.S + (size_t)en.slot * kcap * kcap;
-      if (en.other < 0) {
-        const int l = M.rank[1 - side][en.other_cluster];
-        // ||R_kk S_b||_F (side 0, S is k x l) or ||S_b R_kk^*||_F (side 1, S is l x k)
-        double part = 0.0;
-        if (lane < l)
-          for (int p = 0; p < k; ++p) {
-            double y = 0.0;
-            for (int q = p; q < k; ++q)
-              y = fma(Rown[p + q * 32], side == 0 ? S[q + lane * kcap] : S[lane + q * kcap], y);
-            part = fma(y, y, part);
-          }
-        const double nrm = sqrt(warp_sum(part));
-        const double om = nrm > 0.0 ? st / nrm : 0.0;
-        const int ch = l;
+      const Item ot = items[en.other];
+      const int l = ot.k;
+      const int Ko = l + u;
+      const double nrm = IB.norms[en.norm];
+      const double om = nrm > 0.0 ? st / nrm : 0.0;
+      const double* Ro = IB.Rq + (size_t)en.other * kSlot;
 #pragma unroll
-        for (int i = 0; i < kCh; ++i) {
-          double v = 0.0;
-          if (i < ch && lane < k) v = side == 0 ? S[lane + i * kcap] : S[i + lane * kcap];
-          x[i] = om * v;
-        }
-        fold(R, x, ch, K, vb, lane);
-      } else {
-        const Item ot = items[en.other];
-        const int l = ot.k;
-        const int Ko = l + u;
-        const double nrm = IB.norms[en.norm];
-        const double om = nrm > 0.0 ? st / nrm : 0.0;
-        const double* Ro = IB.Rq + (size_t)en.other * kSlot;
-#pragma unroll
-        for (int i = 0; i < kCh; ++i) {
-          double v = 0.0;
-          if (i < Ko) {
-            if (lane < k) {
-              // side 0: (R_W,s S~^*)[i, lane] = sum_q R[i,q] S[lane,q]
-              // side 1: (R_V,t S~)[i, lane]   = sum_q R[i,q] S[q,lane]
-              for (int q = i; q < l; ++q)
-                v = fma(Ro[i + q * 32], side == 0 ? S[lane + q * kcap] : S[q + lane * kcap], v);
-            } else if (lane < K) {
-              v = Ro[i + (l + lane - k) * 32];
-            }
+      for (int i = 0; i < kCh; ++i) {
+        double v = 0.0;
+        if (i < Ko) {
+          if (lane < k) {
+            // side 0: (R_W,s S~^*)[i, lane] = sum_q R[i,q] S[lane,q]
+            // side 1: (R_V,t S~)[i, lane]   = sum_q R[i,q] S[q,lane]
+            for (int q = i; q < l; ++q)
+              v = fma(Ro[i + q * 32], side == 0 ? S[lane + q * kcap] : S[q + lane * kcap], v);
+          } else if (lane < K) {
+            v = Ro[i + (l + lane - k) * 32];
           }
-          x[i] = om * v;
         }
-        fold(R, x, Ko, K, vb, lane);
+        x[i] = om * v;
       }
+      fold(R, x, Ko, K, vb, lane);
     }
-  }
   // father's part
   if (it.flags & kItemRoot) {
     if (!(it.flags & kItemTreeRoot)) {
@@ -488,8 +660,9 @@ __global__ void k_truncate(MatView M, const Item* __restrict__ items, const int3
   const int w = threadIdx.x >> 5;
   const int idx = blockIdx.x * (blockDim.x >> 5) + w;
   if (idx >= n) return;
-  double* Vh = smem + (size_t)w * (2 * MR * kl);
+  double* Vh = smem + (size_t)w * (2 * MR * kl + 32 * 33);
   double* Qs = Vh + MR * kl;
+  double* Vs = Qs + MR * kl;
   const int id = list[idx];
   const Item it = items[id];
   const int side = it.side;
@@ -555,14 +728,64 @@ __global__ void k_truncate(MatView M, const Item* __restrict__ items, const int3
       for (int i = 0; i < MR; ++i)
         if (i < rows) a[i] = fma(Vh[i + q * MR], b, a[i]);
     }
-  jacobi<MR>(a, rows, K, lane, IB.jac + 2 * (size_t)id, err);
-  // singular values, order, rank
-  double s2 = -1.0;
-  if (lane < K) {
-    s2 = 0.0;
+  // Scale M by a power of two (exact) so that max |M| lies in [1/2, 1): the
+  // squared sums of the Jacobi test cannot overflow and the float copy
+  // keeps its range.  Singular values are unscaled exactly below.
+  int ex = 0;
+  {
+    double mx = 0.0;
 #pragma unroll
     for (int i = 0; i < MR; ++i)
-      if (i < rows) s2 = fma(a[i], a[i], s2);
+      if (i < rows) mx = fmax(mx, fabs(a[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(kFull, mx, o));
+    if (mx > 0.0) frexp(mx, &ex);
+#pragma unroll
+    for (int i = 0; i < MR; ++i) a[i] = ldexp(a[i], -ex);
+  }
+  // Float32 preconditioning: rotate a float copy of M to orthogonal columns
+  // and keep the rotations V; V is made orthogonal in float64 and M <- M V,
+  // which leaves the left singular vectors and singular values of M
+  // unchanged and hands the float64 Jacobi nearly orthogonal columns.
+  if (K >= 2 && rows > 0) {
+    if (lane < K)
+#pragma unroll
+      for (int i = 0; i < MR; ++i)
+        if (i < rows) Qs[i + lane * MR] = a[i];
+    float af[MR];
+    float vf[32];
+#pragma unroll
+    for (int i = 0; i < MR; ++i) af[i] = (float)a[i];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) vf[j] = (j == lane) ? 1.f : 0.f;
+    jacobi32<MR>(af, vf, rows, K, lane);
+    double v[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = (lane < K && j < K) ? (double)vf[j] : 0.0;
+    orthonormalize(v, Vs, K, lane);
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < MR; ++i) a[i] = 0.0;
+    if (lane < K)
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (j < K) {
+          const double vj = v[j];
+#pragma unroll
+          for (int i = 0; i < MR; ++i)
+            if (i < rows) a[i] = fma(Qs[i + j * MR], vj, a[i]);
+        }
+    __syncwarp();
+  }
+  jacobi<MR>(a, rows, K, lane, IB.jac + 2 * (size_t)id, err);
+  // singular values, order, rank
+  double s2 = -1.0;   // squared singular value of this lane's column (unscaled)
+  double s2c = 0.0;   // the same for the scaled column
+  if (lane < K) {
+#pragma unroll
+    for (int i = 0; i < MR; ++i)
+      if (i < rows) s2c = fma(a[i], a[i], s2c);
+    s2 = ldexp(s2c, 2 * ex);
   }
   int pos = 0;
   for (int d = 0; d < 32; ++d) {
@@ -579,7 +802,7 @@ __global__ void k_truncate(MatView M, const Item* __restrict__ items, const int3
   const bool keep = lane < K && rows > 0 && tail > thr;
   const int r = __popc(__ballot_sync(kFull, keep));
   if (keep) {
-    const double inv = 1.0 / sqrt(s2);
+    const double inv = 1.0 / sqrt(s2c);
 #pragma unroll
     for (int i = 0; i < MR; ++i)
       if (i < rows) Qs[i + pos * MR] = a[i] * inv;
@@ -712,56 +935,28 @@ __global__ void k_near_add(const NearDesc* __restrict__ d, int n, int u) {
 
 // ------------------------------------------------------------ launchers
 static constexpr int kWarps = 4;
+static constexpr size_t kFoldSmem = (size_t)kWarps * (32 * kLdr + kCh + 1) * sizeof(double);
 
-void launch_prepass(const MatView& M, int side, const int32_t* clusters, int n, const int32_t* ptr,
-                    const int32_t* adm, const int32_t* other_cl, const BaseWeights& BW, int* err,
-                    cudaStream_t st) {
-  if (n <= 0) return;
-  const size_t sm = (size_t)kWarps * (32 * kLdr + kCh + 1) * sizeof(double);
-  k_prepass<<<(n + kWarps - 1) / kWarps, 32 * kWarps, sm, st>>>(M, side, clusters, n, ptr, adm,
-                                                                 other_cl, BW, err);
-}
-
-void launch_rfactor(const MatView& M, const Item* items, const int32_t* list, int n, int u,
-                    const double* A, const double* B, const ItemBuffers& IB, int* err, cudaStream_t st) {
-  if (n <= 0) return;
-  const size_t sm = (size_t)kWarps * (32 * kLdr + kCh + 1) * sizeof(double);
-  k_rfactor<<<(n + kWarps - 1) / kWarps, 32 * kWarps, sm, st>>>(M, items, list, n, u, A, B, IB, err);
-}
-
-void launch_norms(const MatView& M, const Item* items, const NormTask* tasks, int n, int u,
-                  const ItemBuffers& IB, cudaStream_t st) {
-  if (n <= 0) return;
-  k_norms<<<(n + kWarps - 1) / kWarps, 32 * kWarps, 0, st>>>(M, items, tasks, n, u, IB);
-}
-
-void launch_weights(const MatView& M, const Item* items, const Entry* ents, const int32_t* list, int n,
-                    int u, const BaseWeights& BW, const ItemBuffers& IB, int* err, cudaStream_t st) {
-  if (n <= 0) return;
-  const size_t sm = (size_t)kWarps * (32 * kLdr + kCh + 1) * sizeof(double);
-  k_weights<<<(n + kWarps - 1) / kWarps, 32 * kWarps, sm, st>>>(M, items, ents, list, n, u, BW, IB, err);
-}
+static int blocks_for(int n) { return (n + kWarps - 1) / kWarps; }
 
 template <int MR>
-static void launch_truncate_mr(const MatView& M, const Item* items, const int32_t* list, int n, int u,
-                               int kl, double eps, const double* A, const double* B,
-                               const ItemBuffers& IB, int* err, cudaStream_t st) {
+static void launch_truncate_mr(const MatView& M, const Item* items, const int32_t* list, int n, int u, int kl,
+                               double eps, const double* A, const double* B, const ItemBuffers& IB, int* err,
+                               cudaStream_t st) {
   const int warps = 2;
-  const size_t sm = (size_t)warps * 2 * MR * kl * sizeof(double);
+  const size_t sm = (size_t)warps * (2 * MR * kl + 32 * 33) * sizeof(double);
   static bool attr = false;
   if (!attr) {
     H2_CUDA(cudaFuncSetAttribute(k_truncate<MR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 2 * 2 * MR * 32 * (int)sizeof(double)));
+                                 warps * (2 * MR * 32 + 32 * 33) * (int)sizeof(double)));
     attr = true;
   }
-  k_truncate<MR><<<(n + warps - 1) / warps, 32 * warps, sm, st>>>(M, items, list, n, u, kl, eps, A, B,
-                                                                  IB, err);
+  k_truncate<MR><<<(n + warps - 1) / warps, 32 * warps, sm, st>>>(M, items, list, n, u, kl, eps, A, B, IB, err);
 }
 
-void launch_truncate(const MatView& M, const Item* items, const int32_t* list, int n, int u, int kl,
-                     int max_rows, double eps, const double* A, const double* B, const ItemBuffers& IB,
-                     int* err, cudaStream_t st) {
-  if (n <= 0) return;
+static void launch_truncate(const MatView& M, const Item* items, const int32_t* list, int n, int u, int kl,
+                            int max_rows, double eps, const double* A, const double* B, const ItemBuffers& IB,
+                            int* err, cudaStream_t st) {
   if (max_rows <= 32)
     launch_truncate_mr<32>(M, items, list, n, u, kl, eps, A, B, IB, err, st);
   else if (max_rows <= 48)
@@ -770,10 +965,75 @@ void launch_truncate(const MatView& M, const Item* items, const int32_t* list, i
     launch_truncate_mr<64>(M, items, list, n, u, kl, eps, A, B, IB, err, st);
 }
 
-void launch_reproject(const MatView& M, const Item* items, const Task* tasks, int n, int u,
-                      const ItemBuffers& IB, cudaStream_t st) {
-  if (n <= 0) return;
-  k_reproject<<<(n + kWarps - 1) / kWarps, 32 * kWarps, 0, st>>>(M, items, tasks, n, u, IB);
+void run_pipeline(const Pipeline& P) {
+  cudaStream_t st = P.stream;
+  int64_t pl[H2_PHASE_COUNT] = {0, 0, 0, 0, 0, 0};
+  auto mark = [&](int ph) {
+    if (P.events) H2_CUDA(cudaEventRecord(P.events[ph], st));
+  };
+  const int L = P.levels;
+  // weights of the unchanged matrix: block R-factors of every cluster in one
+  // launch, then the inherited part top-down, both sides per launch
+  mark(H2_PHASE_BASE_WEIGHTS);
+  const int ncl = P.cl_ptr[L];
+  if (ncl > 0) {
+    k_blockweights<<<blocks_for(ncl), 32 * kWarps, kFoldSmem, st>>>(P.M, P.cl_list, ncl, P.BL, P.BW, P.err);
+    ++pl[H2_PHASE_BASE_WEIGHTS];
+  }
+  for (int l = 0; l < L; ++l) {
+    const int n = P.cl_ptr[l + 1] - P.cl_ptr[l];
+    if (!n) continue;
+    k_baseweights<<<blocks_for(n), 32 * kWarps, kFoldSmem, st>>>(P.M, P.cl_list + P.cl_ptr[l], n, P.BW, P.err);
+    ++pl[H2_PHASE_BASE_WEIGHTS];
+  }
+  // step 2: basis R-factors, bottom-up
+  mark(H2_PHASE_RFACTOR);
+  for (int l = L - 1; l >= 0; --l) {
+    const int n = P.lvl_ptr[l + 1] - P.lvl_ptr[l];
+    if (!n) continue;
+    k_rfactor<<<blocks_for(n), 32 * kWarps, kFoldSmem, st>>>(P.M, P.items, P.lvl_list + P.lvl_ptr[l], n, P.u,
+                                                              P.A, P.B, P.IB, P.err);
+    ++pl[H2_PHASE_RFACTOR];
+  }
+  mark(H2_PHASE_NORMS);
+  if (P.n_norms > 0) {
+    k_norms<<<blocks_for(P.n_norms), 32 * kWarps, 0, st>>>(P.M, P.items, P.norms, P.n_norms, P.u, P.IB);
+    ++pl[H2_PHASE_NORMS];
+  }
+  // step 3: outside blocks of the tasks that need their own fold, then the
+  // weights top-down
+  mark(H2_PHASE_WEIGHTS);
+  const int ni = P.lvl_ptr[L];
+  if (ni > 0) {
+    k_outside<<<blocks_for(ni), 32 * kWarps, kFoldSmem, st>>>(P.M, P.items, P.ents, P.lvl_list, ni, P.u, P.IB);
+    ++pl[H2_PHASE_WEIGHTS];
+  }
+  for (int l = 0; l < L; ++l) {
+    const int n = P.lvl_ptr[l + 1] - P.lvl_ptr[l];
+    if (!n) continue;
+    k_weights<<<blocks_for(n), 32 * kWarps, kFoldSmem, st>>>(P.M, P.items, P.ents, P.lvl_list + P.lvl_ptr[l], n,
+                                                              P.u, P.BW, P.IB, P.err);
+    ++pl[H2_PHASE_WEIGHTS];
+  }
+  // step 4: truncation, bottom-up
+  mark(H2_PHASE_TRUNCATE);
+  for (int l = L - 1; l >= 0; --l) {
+    const int n = P.lvl_ptr[l + 1] - P.lvl_ptr[l];
+    if (!n) continue;
+    launch_truncate(P.M, P.items, P.lvl_list + P.lvl_ptr[l], n, P.u, P.kl, P.lvl_rows[l], P.eps, P.A, P.B, P.IB,
+                    P.err, st);
+    ++pl[H2_PHASE_TRUNCATE];
+  }
+  // step 5: reprojection
+  mark(H2_PHASE_REPROJECT);
+  if (P.n_tasks > 0) {
+    k_reproject<<<blocks_for(P.n_tasks), 32 * kWarps, 0, st>>>(P.M, P.items, P.tasks, P.n_tasks, P.u, P.IB);
+    ++pl[H2_PHASE_REPROJECT];
+  }
+  mark(H2_PHASE_COUNT);
+  H2_CUDA(cudaGetLastError());
+  if (P.phase_launches)
+    for (int ph = 0; ph < H2_PHASE_COUNT; ++ph) P.phase_launches[ph] = pl[ph];
 }
 
 void launch_copy(const CopyDesc* d, int n, cudaStream_t st) {

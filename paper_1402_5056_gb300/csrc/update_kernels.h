@@ -23,20 +23,44 @@ struct NearDesc {
   int pad;
 };
 
-void launch_prepass(const MatView& M, int side, const int32_t* clusters, int n, const int32_t* ptr,
-                    const int32_t* adm, const int32_t* other_cl, const BaseWeights& BW, int* err,
-                    cudaStream_t st);
-void launch_rfactor(const MatView& M, const Item* items, const int32_t* list, int n, int u,
-                    const double* A, const double* B, const ItemBuffers& IB, int* err, cudaStream_t st);
-void launch_norms(const MatView& M, const Item* items, const NormTask* tasks, int n, int u,
-                  const ItemBuffers& IB, cudaStream_t st);
-void launch_weights(const MatView& M, const Item* items, const Entry* ents, const int32_t* list, int n,
-                    int u, const BaseWeights& BW, const ItemBuffers& IB, int* err, cudaStream_t st);
-void launch_truncate(const MatView& M, const Item* items, const int32_t* list, int n, int u, int kl,
-                     int max_rows, double eps, const double* A, const double* B, const ItemBuffers& IB,
-                     int* err, cudaStream_t st);
-void launch_reproject(const MatView& M, const Item* items, const Task* tasks, int n, int u,
-                      const ItemBuffers& IB, cudaStream_t st);
+// Admissible-block lists of the matrix, for the weights of the unchanged matrix.
+struct BlockLists {
+  const int32_t* ptr[2];     // CSR of admissible slots by row / column cluster
+  const int32_t* adm[2];
+  const int32_t* other[2];   // per slot: the cluster on the other side
+};
+
+// Everything one execution of the update kernels needs (device pointers
+// unless marked host).
+struct Pipeline {
+  MatView M;
+  BlockLists BL;
+  BaseWeights BW;
+  ItemBuffers IB;
+  const Item* items;
+  const Entry* ents;
+  const Task* tasks;
+  const NormTask* norms;
+  const int32_t* lvl_list;      // items sorted by level
+  const int32_t* lvl_ptr;       // host, levels + 1 entries
+  const int32_t* lvl_rows;      // host, per level: bound on the truncation rows
+  const int32_t* cl_list;       // all clusters of both sides sorted by level (side << 30 | id)
+  const int32_t* cl_ptr;        // host, levels + 1 entries
+  int levels;
+  int n_tasks, n_norms;
+  int u, kl;
+  double eps;
+  const double* A;
+  const double* B;
+  int* err;
+  cudaStream_t stream;
+  cudaEvent_t* events;          // H2_PHASE_COUNT + 1 events or nullptr
+  int64_t* phase_launches;      // host, H2_PHASE_COUNT entries or nullptr
+};
+
+// Launch the whole update (weights of the unchanged matrix, steps 2-5) on
+// P.stream.
+void run_pipeline(const Pipeline& P);
 void launch_copy(const CopyDesc* d, int n, cudaStream_t st);
 void launch_near_add(const NearDesc* d, int n, int u, cudaStream_t st);
 

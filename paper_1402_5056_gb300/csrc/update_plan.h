@@ -84,6 +84,7 @@ struct ItemBuffers {
   double* F;           // new transfer matrix of the item's cluster
   double* Q;           // new leaf bases (at Item::qoff, ld = size)
   int32_t* rank;       // new rank
+  int32_t* own;        // 1 if the item folds its outside blocks itself (step 3)
   double* norms;       // per NormTask
   double* S_out;       // per Task, 32 x 32 slots
   unsigned long long* jac;   // per item: pairs checked, rotations applied (2 counters)
