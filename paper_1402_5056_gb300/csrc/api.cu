@@ -904,8 +904,8 @@ void alloc_batch(h2_ctx* ctx, h2_batch& P) {
   P.IB.own = dalloc<int32_t>(ni);
   P.IB.norms = dalloc<double>(P.norms.size());
   P.IB.S_out = dalloc<double>(P.tasks.size() * kSlot);
-  P.IB.jac = dalloc<unsigned long long>(2 * ni);
-  if (ni) H2_CUDA(cudaMemsetAsync(P.IB.jac, 0, 2 * ni * sizeof(unsigned long long), st));
+  P.IB.jac = dalloc<unsigned long long>(4 * ni);
+  if (ni) H2_CUDA(cudaMemsetAsync(P.IB.jac, 0, 4 * ni * sizeof(unsigned long long), st));
   const int32_t ncl[2] = {P.Z->rows.count(), P.Z->cols.count()};
   for (int sd = 0; sd < 2; ++sd) {
     P.BW.G[sd] = dalloc<double>((size_t)ncl[sd] * kSlot);
@@ -1226,10 +1226,10 @@ namespace {
 void phase_flops(h2_ctx* ctx, const h2_batch* P, double f[H2_PHASE_COUNT]) {
   for (int ph = 0; ph < H2_PHASE_COUNT; ++ph) f[ph] = 0.0;
   const size_t ni = P->items.size();
-  std::vector<unsigned long long> jac(2 * ni);
+  std::vector<unsigned long long> jac(4 * ni);
   std::vector<int32_t> rk(ni);
   if (ni) {
-    H2_CUDA(cudaMemcpyAsync(jac.data(), P->IB.jac, 2 * ni * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+    H2_CUDA(cudaMemcpyAsync(jac.data(), P->IB.jac, 4 * ni * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                             ctx->stream));
     H2_CUDA(cudaMemcpyAsync(rk.data(), P->IB.rank, ni * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
   }
@@ -1300,8 +1300,14 @@ void phase_flops(h2_ctx* ctx, const h2_batch* P, double f[H2_PHASE_COUNT]) {
       ft += 2 * rk[it.son0] * k0 * k + 2 * rk[it.son1] * k1 * k;
     }
     ft += m * K * K;                                               // V^ times triangular B~^*
-    if (K >= 2 && m > 0) ft += 2 * (4 * K * K * K) + 2 * m * K * K;  // Newton-Schulz (2 steps), M V
-    ft += 6.0 * m * (double)jac[2 * i] + 6.0 * m * (double)jac[2 * i + 1];
+    if (jac[4 * i + 2]) {
+      // certificate and two Cholesky-QR passes: 2 Grams, 3 factorisations,
+      // 2 triangular inverses, 2 triangular products
+      ft += 2 * (2 * m * K * K) + 3 * (K * K * K / 3) + 2 * (K * K * K / 3) + 2 * (m * K * K);
+    } else {
+      if (K >= 2 && m > 0) ft += 2 * (4 * K * K * K) + 2 * m * K * K;  // Newton-Schulz (2 steps), M V
+      ft += 6.0 * m * (double)jac[4 * i] + 6.0 * m * (double)jac[4 * i + 1];
+    }
     ft += 2 * m * K * rk[i];                                       // R_t = Q^* V^
     if ((it.flags & kItemRoot) && !(it.flags & kItemTreeRoot)) ft += 2 * rk[i] * k * it.kf;
     f[H2_PHASE_TRUNCATE] += ft;

@@ -56,7 +56,7 @@ constexpr size_t kOffRank = kOffS + align256((size_t)kNaTasks * kSlot * 8);
 constexpr size_t kOffOwn = kOffRank + align256((size_t)kNaItems * 4);
 constexpr size_t kOffNorm = kOffOwn + align256((size_t)kNaItems * 4);
 constexpr size_t kOffJac = kOffNorm + align256((size_t)kNaNorms * 8);
-constexpr size_t kOffItems = kOffJac + align256((size_t)kNaItems * 16);
+constexpr size_t kOffItems = kOffJac + align256((size_t)kNaItems * 32);
 constexpr size_t kOffEnts = kOffItems + align256((size_t)kNaItems * sizeof(Item));
 constexpr size_t kOffTasks = kOffEnts + align256((size_t)kNaEntries * sizeof(Entry));
 constexpr size_t kOffNT = kOffTasks + align256((size_t)kNaTasks * sizeof(Task));

@@ -645,6 +645,102 @@ __global__ void k_weights(MatView M, const Item* __restrict__ items, const Entry
   (void)err;
 }
 
+// ---------------------------------------------- certified full-rank path
+// When every singular value of the weighted matrix M exceeds the
+// truncation threshold, the rank rule keeps all of range(M) and any
+// orthonormal basis of range(M) gives the same projection Q Q^* V^ as the
+// singular vectors (Eq. (Qt_condensed)).  The certificate is the Cholesky
+// factorisation of M^* M - (tau + delta) I succeeding, tau = (eps/2)^2 and
+// delta a bound on the rounding of the Gram matrix and of the
+// factorisation; the basis then comes from two Cholesky-QR passes.  All of
+// it is float64 matrix-matrix work with every lane busy.
+
+// Gram G = X^* X of the K columns of X (smem, ld ldx); lane c holds column
+// c of X in xc[].  G goes to Gs (ld 33).
+template <int MR>
+__device__ __forceinline__ void gram(const double* X, int ldx, const double (&xc)[MR], int rows, int K, double* Gs,
+                                     int lane) {
+  if (lane < K)
+    for (int j = 0; j < K; ++j) {
+      double g = 0.0;
+#pragma unroll
+      for (int i = 0; i < MR; ++i)
+        if (i < rows) g = fma(X[i + j * ldx], xc[i], g);
+      Gs[j + lane * 33] = g;
+    }
+  __syncwarp();
+}
+
+// In-place Cholesky G - shift I = L L^* of the lower triangle of Gs (ld
+// 33); lane i owns row i.  Returns false (on every lane alike) when a pivot
+// is not positive.
+__device__ __forceinline__ bool chol(double* Gs, int K, double shift, int lane) {
+  if (lane < K) Gs[lane + lane * 33] -= shift;
+  __syncwarp();
+  for (int j = 0; j < K; ++j) {
+    const double d = Gs[j + j * 33];
+    if (!(d > 0.0)) return false;
+    const double ljj = sqrt(d);
+    const double inv = 1.0 / ljj;
+    __syncwarp();
+    if (lane == j) Gs[j + j * 33] = ljj;
+    if (lane > j && lane < K) Gs[lane + j * 33] *= inv;
+    __syncwarp();
+    if (lane > j && lane < K) {
+      const double lij = Gs[lane + j * 33];
+      for (int k = j + 1; k <= lane; ++k) Gs[lane + k * 33] = fma(-lij, Gs[k + j * 33], Gs[lane + k * 33]);
+    }
+    __syncwarp();
+  }
+  return true;
+}
+
+// Xs = L^{-1} (lower triangular, ld 33) for the Cholesky factor in Ls;
+// lane c computes column c.  dinv (K entries of shared memory) receives
+// the reciprocal diagonal.
+__device__ __forceinline__ void trinv(const double* Ls, double* Xs, double* dinv, int K, int lane) {
+  if (lane < K) dinv[lane] = 1.0 / Ls[lane + lane * 33];
+  __syncwarp();
+  if (lane < K) {
+    const int c = lane;
+    Xs[c + c * 33] = dinv[c];
+    for (int i = c + 1; i < K; ++i) {
+      double t = 0.0;
+      for (int p = c; p < i; ++p) t = fma(Ls[i + p * 33], Xs[p + c * 33], t);
+      Xs[i + c * 33] = -t * dinv[i];
+    }
+  }
+  __syncwarp();
+}
+
+// One Cholesky-QR pass on the K columns of X (smem, ld ldx; lane c holds
+// column c in xc[]): G = X^* X = L L^*, X <- X L^{-*}.  Uses Gs, Xs, dinv;
+// returns false if the factorisation breaks down.  xc[] receives the new
+// column.
+template <int MR>
+__device__ __forceinline__ bool cholqr_pass(double* X, int ldx, double (&xc)[MR], int rows, int K, double* Gs,
+                                            double* Xs, double* dinv, int lane) {
+  gram<MR>(X, ldx, xc, rows, K, Gs, lane);
+  if (!chol(Gs, K, 0.0, lane)) return false;
+  trinv(Gs, Xs, dinv, K, lane);
+#pragma unroll
+  for (int i = 0; i < MR; ++i) xc[i] = 0.0;
+  if (lane < K)
+    for (int j = 0; j <= lane; ++j) {
+      const double x = Xs[lane + j * 33];
+#pragma unroll
+      for (int i = 0; i < MR; ++i)
+        if (i < rows) xc[i] = fma(X[i + j * ldx], x, xc[i]);
+    }
+  __syncwarp();
+  if (lane < K)
+#pragma unroll
+    for (int i = 0; i < MR; ++i)
+      if (i < rows) X[i + lane * ldx] = xc[i];
+  __syncwarp();
+  return true;
+}
+
 // ------------------------------------------------------------- step 4
 // Truncation bottom-up: SVD of V^_t B~_t^* (leaf: V^_t = V~_t) by one-sided
 // Jacobi, rank by the block-relative rule sum_{i>r} sigma_i^2 <= (eps/2)^2,
@@ -660,7 +756,7 @@ __global__ void k_truncate(MatView M, const Item* __restrict__ items, const int3
   const int w = threadIdx.x >> 5;
   const int idx = blockIdx.x * (blockDim.x >> 5) + w;
   if (idx >= n) return;
-  double* Vh = smem + (size_t)w * (2 * MR * kl + 32 * 33);
+  double* Vh = smem + (size_t)w * (2 * MR * kl + 2 * 32 * 33 + 32);
   double* Qs = Vh + MR * kl;
   double* Vs = Qs + MR * kl;
   const int id = list[idx];
@@ -716,96 +812,132 @@ __global__ void k_truncate(MatView M, const Item* __restrict__ items, const int3
     }
   }
   __syncwarp();
-  // M = V^ B~^*, column `lane` = V^ * row `lane` of B~
+  // M = V^ B~^*, column `lane` = V^ * row `lane` of B~, scaled by a power
+  // of two (exact) so that max |M| lies in [1/2, 1): the squared sums of
+  // the Jacobi test cannot overflow and the float copy keeps its range;
+  // singular values are unscaled exactly below.
   const double* Bw = IB.Bw + (size_t)id * kSlot;
   double a[MR];
-#pragma unroll
-  for (int i = 0; i < MR; ++i) a[i] = 0.0;
-  if (lane < K)
-    for (int q = lane; q < K; ++q) {   // B~ is upper triangular: B~[lane, q] = 0 for q < lane
-      const double b = Bw[lane + q * 32];
-#pragma unroll
-      for (int i = 0; i < MR; ++i)
-        if (i < rows) a[i] = fma(Vh[i + q * MR], b, a[i]);
-    }
-  // Scale M by a power of two (exact) so that max |M| lies in [1/2, 1): the
-  // squared sums of the Jacobi test cannot overflow and the float copy
-  // keeps its range.  Singular values are unscaled exactly below.
   int ex = 0;
-  {
+  auto form_m = [&]() {
+#pragma unroll
+    for (int i = 0; i < MR; ++i) a[i] = 0.0;
+    if (lane < K)
+      for (int q = lane; q < K; ++q) {   // B~ is upper triangular: B~[lane, q] = 0 for q < lane
+        const double b = Bw[lane + q * 32];
+#pragma unroll
+        for (int i = 0; i < MR; ++i)
+          if (i < rows) a[i] = fma(Vh[i + q * MR], b, a[i]);
+      }
     double mx = 0.0;
 #pragma unroll
     for (int i = 0; i < MR; ++i)
       if (i < rows) mx = fmax(mx, fabs(a[i]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(kFull, mx, o));
+    ex = 0;
     if (mx > 0.0) frexp(mx, &ex);
 #pragma unroll
     for (int i = 0; i < MR; ++i) a[i] = ldexp(a[i], -ex);
-  }
-  // Float32 preconditioning: rotate a float copy of M to orthogonal columns
-  // and keep the rotations V; V is made orthogonal in float64 and M <- M V,
-  // which leaves the left singular vectors and singular values of M
-  // unchanged and hands the float64 Jacobi nearly orthogonal columns.
-  if (K >= 2 && rows > 0) {
+  };
+  form_m();
+  double* Gs = Vs;                 // K x K Gram / Cholesky factor (ld 33)
+  double* Xs = Vs + 32 * 33;       // K x K inverse factor (ld 33)
+  double* dinv = Xs + 32 * 33;     // K reciprocal pivots
+  const double thr = 0.25 * eps * eps;
+  unsigned long long* cnt = IB.jac + 4 * (size_t)id;
+  // certified full-rank path: M^* M - (tau + delta) I positive definite
+  bool certified = false;
+  if (rows >= K && K >= 1 && lane < 32) {
     if (lane < K)
 #pragma unroll
       for (int i = 0; i < MR; ++i)
         if (i < rows) Qs[i + lane * MR] = a[i];
-    float af[MR];
-    float vf[32];
-#pragma unroll
-    for (int i = 0; i < MR; ++i) af[i] = (float)a[i];
-#pragma unroll
-    for (int j = 0; j < 32; ++j) vf[j] = (j == lane) ? 1.f : 0.f;
-    jacobi32<MR>(af, vf, rows, K, lane);
-    double v[32];
-#pragma unroll
-    for (int j = 0; j < 32; ++j) v[j] = (lane < K && j < K) ? (double)vf[j] : 0.0;
-    orthonormalize(v, Vs, K, lane);
     __syncwarp();
-#pragma unroll
-    for (int i = 0; i < MR; ++i) a[i] = 0.0;
-    if (lane < K)
-#pragma unroll
-      for (int j = 0; j < 32; ++j)
-        if (j < K) {
-          const double vj = v[j];
-#pragma unroll
-          for (int i = 0; i < MR; ++i)
-            if (i < rows) a[i] = fma(Qs[i + j * MR], vj, a[i]);
-        }
-    __syncwarp();
+    gram<MR>(Qs, MR, a, rows, K, Gs, lane);
+    double trace = 0.0;
+    for (int j = 0; j < K; ++j) trace += Gs[j + j * 33];
+    const double tau = ldexp(thr, -2 * ex);
+    const double delta = 4.0 * (double)(rows + K * K) * DBL_EPSILON * trace;
+    if (chol(Gs, K, tau + delta, lane)) {
+      certified = cholqr_pass<MR>(Qs, MR, a, rows, K, Gs, Xs, dinv, lane) &&
+                  cholqr_pass<MR>(Qs, MR, a, rows, K, Gs, Xs, dinv, lane);
+      if (!certified) form_m();   // a factorisation broke down after the certificate
+    }
   }
-  jacobi<MR>(a, rows, K, lane, IB.jac + 2 * (size_t)id, err);
-  // singular values, order, rank
-  double s2 = -1.0;   // squared singular value of this lane's column (unscaled)
-  double s2c = 0.0;   // the same for the scaled column
-  if (lane < K) {
+  int r = 0;
+  if (certified) {
+    r = K;   // Qs holds an orthonormal basis of range(M)
+    if (lane == 0 && cnt) {
+      cnt[0] = 0;
+      cnt[1] = 0;
+      cnt[2] = 1;
+    }
+  } else {
+    // Float32 preconditioning: rotate a float copy of M to orthogonal
+    // columns and keep the rotations V; V is made orthogonal in float64 and
+    // M <- M V, which leaves the left singular vectors and singular values
+    // of M unchanged and hands the float64 Jacobi nearly orthogonal columns.
+    if (K >= 2 && rows > 0) {
+      if (lane < K)
 #pragma unroll
-    for (int i = 0; i < MR; ++i)
-      if (i < rows) s2c = fma(a[i], a[i], s2c);
-    s2 = ldexp(s2c, 2 * ex);
-  }
-  int pos = 0;
-  for (int d = 0; d < 32; ++d) {
-    const double o = __shfl_sync(kFull, s2, d);
-    if (d < K && (o > s2 || (o == s2 && d < lane))) ++pos;
-  }
-  double tail = 0.0;
-  for (int d = 0; d < 32; ++d) {
-    const double o = __shfl_sync(kFull, s2, d);
-    const int op = __shfl_sync(kFull, pos, d);
-    if (d < K && op >= pos) tail += o;
-  }
-  const double thr = 0.25 * eps * eps;
-  const bool keep = lane < K && rows > 0 && tail > thr;
-  const int r = __popc(__ballot_sync(kFull, keep));
-  if (keep) {
-    const double inv = 1.0 / sqrt(s2c);
+        for (int i = 0; i < MR; ++i)
+          if (i < rows) Qs[i + lane * MR] = a[i];
+      float af[MR];
+      float vf[32];
 #pragma unroll
-    for (int i = 0; i < MR; ++i)
-      if (i < rows) Qs[i + pos * MR] = a[i] * inv;
+      for (int i = 0; i < MR; ++i) af[i] = (float)a[i];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) vf[j] = (j == lane) ? 1.f : 0.f;
+      jacobi32<MR>(af, vf, rows, K, lane);
+      double v[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) v[j] = (lane < K && j < K) ? (double)vf[j] : 0.0;
+      orthonormalize(v, Vs, K, lane);
+      __syncwarp();
+#pragma unroll
+      for (int i = 0; i < MR; ++i) a[i] = 0.0;
+      if (lane < K)
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (j < K) {
+            const double vj = v[j];
+#pragma unroll
+            for (int i = 0; i < MR; ++i)
+              if (i < rows) a[i] = fma(Qs[i + j * MR], vj, a[i]);
+          }
+      __syncwarp();
+    }
+    jacobi<MR>(a, rows, K, lane, cnt, err);
+    if (lane == 0 && cnt) cnt[2] = 0;
+    // singular values, order, rank
+    double s2 = -1.0;   // squared singular value of this lane's column (unscaled)
+    double s2c = 0.0;   // the same for the scaled column
+    if (lane < K) {
+#pragma unroll
+      for (int i = 0; i < MR; ++i)
+        if (i < rows) s2c = fma(a[i], a[i], s2c);
+      s2 = ldexp(s2c, 2 * ex);
+    }
+    int pos = 0;
+    for (int d = 0; d < 32; ++d) {
+      const double o = __shfl_sync(kFull, s2, d);
+      if (d < K && (o > s2 || (o == s2 && d < lane))) ++pos;
+    }
+    double tail = 0.0;
+    for (int d = 0; d < 32; ++d) {
+      const double o = __shfl_sync(kFull, s2, d);
+      const int op = __shfl_sync(kFull, pos, d);
+      if (d < K && op >= pos) tail += o;
+    }
+    const bool keep = lane < K && rows > 0 && tail > thr;
+    r = __popc(__ballot_sync(kFull, keep));
+    if (keep) {
+      const double inv = 1.0 / sqrt(s2c);
+#pragma unroll
+      for (int i = 0; i < MR; ++i)
+        if (i < rows) Qs[i + pos * MR] = a[i] * inv;
+    }
   }
   __syncwarp();
   // R_t = Q^* V^ (r x K)
@@ -944,11 +1076,11 @@ static void launch_truncate_mr(const MatView& M, const Item* items, const int32_
                                double eps, const double* A, const double* B, const ItemBuffers& IB, int* err,
                                cudaStream_t st) {
   const int warps = 2;
-  const size_t sm = (size_t)warps * (2 * MR * kl + 32 * 33) * sizeof(double);
+  const size_t sm = (size_t)warps * (2 * MR * kl + 2 * 32 * 33 + 32) * sizeof(double);
   static bool attr = false;
   if (!attr) {
     H2_CUDA(cudaFuncSetAttribute(k_truncate<MR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 warps * (2 * MR * 32 + 32 * 33) * (int)sizeof(double)));
+                                 warps * (2 * MR * 32 + 2 * 32 * 33 + 32) * (int)sizeof(double)));
     attr = true;
   }
   k_truncate<MR><<<(n + warps - 1) / warps, 32 * warps, sm, st>>>(M, items, list, n, u, kl, eps, A, B, IB, err);

@@ -87,7 +87,8 @@ struct ItemBuffers {
   int32_t* own;        // 1 if the item folds its outside blocks itself (step 3)
   double* norms;       // per NormTask
   double* S_out;       // per Task, 32 x 32 slots
-  unsigned long long* jac;   // per item: pairs checked, rotations applied (2 counters)
+  unsigned long long* jac;   // per item: Jacobi pairs checked, rotations applied, 1 if the
+                             // full-rank certificate held (no Jacobi), reserved (4 counters)
 };
 
 constexpr int kSlot = 32 * 32;
