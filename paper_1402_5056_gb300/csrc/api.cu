@@ -1301,9 +1301,10 @@ void phase_flops(h2_ctx* ctx, const h2_batch* P, double f[H2_PHASE_COUNT]) {
     }
     ft += m * K * K;                                               // V^ times triangular B~^*
     if (jac[4 * i + 2]) {
-      // certificate and two Cholesky-QR passes: 2 Grams, 3 factorisations,
-      // 2 triangular inverses, 2 triangular products
-      ft += 2 * (2 * m * K * K) + 3 * (K * K * K / 3) + 2 * (K * K * K / 3) + 2 * (m * K * K);
+      // certificate factorisation used as the first Cholesky-QR pass, then a
+      // polish: 2 Grams, 1 factorisation, 1 triangular inverse, 1
+      // triangular product, 1 product
+      ft += 2 * (2 * m * K * K) + (K * K * K / 3) + (K * K * K / 3) + (m * K * K) + 2 * m * K * K;
     } else {
       if (K >= 2 && m > 0) ft += 2 * (4 * K * K * K) + 2 * m * K * K;  // Newton-Schulz (2 steps), M V
       ft += 6.0 * m * (double)jac[4 * i] + 6.0 * m * (double)jac[4 * i + 1];

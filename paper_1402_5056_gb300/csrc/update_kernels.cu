@@ -717,11 +717,10 @@ __device__ __forceinline__ void trinv(const double* Ls, double* Xs, double* dinv
 // column c in xc[]): G = X^* X = L L^*, X <- X L^{-*}.  Uses Gs, Xs, dinv;
 // returns false if the factorisation breaks down.  xc[] receives the new
 // column.
+// X <- X L^{-*} for the Cholesky factor L in Gs (lower, ld 33).
 template <int MR>
-__device__ __forceinline__ bool cholqr_pass(double* X, int ldx, double (&xc)[MR], int rows, int K, double* Gs,
-                                            double* Xs, double* dinv, int lane) {
-  gram<MR>(X, ldx, xc, rows, K, Gs, lane);
-  if (!chol(Gs, K, 0.0, lane)) return false;
+__device__ __forceinline__ void apply_inverse_factor(double* X, int ldx, double (&xc)[MR], int rows, int K,
+                                                     const double* Gs, double* Xs, double* dinv, int lane) {
   trinv(Gs, Xs, dinv, K, lane);
 #pragma unroll
   for (int i = 0; i < MR; ++i) xc[i] = 0.0;
@@ -732,6 +731,47 @@ __device__ __forceinline__ bool cholqr_pass(double* X, int ldx, double (&xc)[MR]
       for (int i = 0; i < MR; ++i)
         if (i < rows) xc[i] = fma(X[i + j * ldx], x, xc[i]);
     }
+  __syncwarp();
+  if (lane < K)
+#pragma unroll
+    for (int i = 0; i < MR; ++i)
+      if (i < rows) X[i + lane * ldx] = xc[i];
+  __syncwarp();
+}
+
+template <int MR>
+__device__ __forceinline__ bool cholqr_pass(double* X, int ldx, double (&xc)[MR], int rows, int K, double* Gs,
+                                            double* Xs, double* dinv, int lane) {
+  gram<MR>(X, ldx, xc, rows, K, Gs, lane);
+  if (!chol(Gs, K, 0.0, lane)) return false;
+  apply_inverse_factor<MR>(X, ldx, xc, rows, K, Gs, Xs, dinv, lane);
+  return true;
+}
+
+// Second orthogonalisation of X (smem, ld ldx; lane c holds column c in
+// xc[]) when it is already orthonormal to within 1e-7: with G = X^* X,
+// X <- X (3I - G) / 2 leaves an orthogonality error of order |G - I|^2.
+// Returns false, leaving X unchanged, when |G - I| is larger.
+template <int MR>
+__device__ __forceinline__ bool polish(double* X, int ldx, double (&xc)[MR], int rows, int K, double* Gs, int lane) {
+  gram<MR>(X, ldx, xc, rows, K, Gs, lane);
+  double dev = 0.0;
+  if (lane < K)
+    for (int j = 0; j < K; ++j) dev = fmax(dev, fabs(Gs[j + lane * 33] - (j == lane ? 1.0 : 0.0)));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) dev = fmax(dev, __shfl_xor_sync(kFull, dev, o));
+  if (!(dev < 1e-7)) return false;
+  // column c: 1.5 x_c - 0.5 sum_j x_j G[j][c]
+  if (lane < K) {
+#pragma unroll
+    for (int i = 0; i < MR; ++i) xc[i] *= 1.5;
+    for (int j = 0; j < K; ++j) {
+      const double g = -0.5 * Gs[j + lane * 33];
+#pragma unroll
+      for (int i = 0; i < MR; ++i)
+        if (i < rows) xc[i] = fma(X[i + j * ldx], g, xc[i]);
+    }
+  }
   __syncwarp();
   if (lane < K)
 #pragma unroll
@@ -860,8 +900,14 @@ __global__ void k_truncate(MatView M, const Item* __restrict__ items, const int3
     const double tau = ldexp(thr, -2 * ex);
     const double delta = 4.0 * (double)(rows + K * K) * DBL_EPSILON * trace;
     if (chol(Gs, K, tau + delta, lane)) {
-      certified = cholqr_pass<MR>(Qs, MR, a, rows, K, Gs, Xs, dinv, lane) &&
-                  cholqr_pass<MR>(Qs, MR, a, rows, K, Gs, Xs, dinv, lane);
+      // The certificate's factor L (L L^* = M^* M - (tau + delta) I) is the
+      // first Cholesky-QR pass: M L^{-*} deviates from orthonormality only
+      // by (tau + delta) |(L L^*)^{-1}|; a polish (or a second full pass)
+      // removes the rest.
+      apply_inverse_factor<MR>(Qs, MR, a, rows, K, Gs, Xs, dinv, lane);
+      certified = polish<MR>(Qs, MR, a, rows, K, Gs, lane) ||
+                  (cholqr_pass<MR>(Qs, MR, a, rows, K, Gs, Xs, dinv, lane) &&
+                   polish<MR>(Qs, MR, a, rows, K, Gs, lane));
       if (!certified) form_m();   // a factorisation broke down after the certificate
     }
   }
