@@ -226,10 +226,11 @@ def main():
     else:
         torch.cuda.set_device(0)
     from paper_1402_5056_gb300 import binding as b
+    from paper_1402_5056_gb300.dist import rank_seed, reduce_max
 
     stream = torch.cuda.current_stream()
     ctx = b.h2_ctx_create(torch.cuda.current_device(), stream.cuda_stream)
-    Z, blocks, A, B = lib_workload(b, ctx, rank_offset=rank)
+    Z, blocks, A, B = lib_workload(b, ctx, rank_offset=rank_seed(0, rank))
     blocks, A, B = blocks[:args.count], A[:args.count], B[:args.count]
     w = WORK
     P = b.h2_batch_create(ctx, Z, blocks, w["u"])
@@ -273,11 +274,7 @@ def main():
         dist.barrier()
     clocks = sampler.stop()
     b.h2_ctx_synchronize(ctx)
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = reduce_max(sum(step_ms), dist, device="cuda")
     ms_per_step = total_ms / args.steps
     value = world * len(blocks) / (ms_per_step / 1e3)
     stats = b.h2_batch_stats(ctx, P)

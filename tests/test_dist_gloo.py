@@ -1,0 +1,56 @@
+"""Host-side multi-rank logic of the benchmark harness (gloo, 2 ranks, CPU):
+shard ranges cover a batch exactly once and the timing reductions agree."""
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+from paper_1402_5056_gb300.dist import rank_seed, reduce_max, reduce_sum, shard_range  # noqa: E402
+
+
+def test_shard_ranges_partition():
+    for count in (0, 1, 7, 4096):
+        for world in (1, 2, 3, 8):
+            got = [shard_range(count, r, world) for r in range(world)]
+            assert got[0][0] == 0 and got[-1][1] == count
+            assert all(got[i][1] == got[i + 1][0] for i in range(world - 1))
+            sizes = [e - b for b, e in got]
+            assert max(sizes) - min(sizes) <= 1
+    with pytest.raises(ValueError):
+        shard_range(5, 2, 2)
+    assert len({rank_seed(7, r) for r in range(8)}) == 8
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        b, e = shard_range(10, rank, world)
+        n = reduce_sum(e - b, dist)
+        t = reduce_max(1.0 + rank, dist)
+        out[rank] = (n, t)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_gloo_two_ranks():
+    world = 2
+    port = _free_port()
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
+        res = dict(out)
+    assert res[0] == res[1] == (10.0, 2.0)
