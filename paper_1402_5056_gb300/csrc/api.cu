@@ -713,7 +713,9 @@ struct h2_batch {
   int64_t phase_launches[H2_PHASE_COUNT] = {0, 0, 0, 0, 0, 0};
   bool executed = false;
   bool timing = false;
-  cudaEvent_t ev[H2_PHASE_COUNT + 1] = {};
+  cudaEvent_t ev[2 * H2_PHASE_COUNT] = {};   // start and end of every phase
+  cudaStream_t side = nullptr;               // stream of the weights of the unchanged matrix
+  cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 namespace {
@@ -888,6 +890,9 @@ void plan_batch(h2_batch& P) {
 
 void alloc_batch(h2_ctx* ctx, h2_batch& P) {
   cudaStream_t st = ctx->stream;
+  H2_CUDA(cudaStreamCreateWithFlags(&P.side, cudaStreamNonBlocking));
+  H2_CUDA(cudaEventCreateWithFlags(&P.fork, cudaEventDisableTiming));
+  H2_CUDA(cudaEventCreateWithFlags(&P.join, cudaEventDisableTiming));
   P.d_items = upload(P.items, st);
   P.d_ents = upload(P.ents, st);
   P.d_tasks = upload(P.tasks, st);
@@ -915,6 +920,12 @@ void alloc_batch(h2_ctx* ctx, h2_batch& P) {
 }
 
 void free_batch_device(h2_batch& P) {
+  if (P.side) cudaStreamSynchronize(P.side);
+  if (P.fork) cudaEventDestroy(P.fork);
+  if (P.join) cudaEventDestroy(P.join);
+  if (P.side) cudaStreamDestroy(P.side);
+  P.fork = P.join = nullptr;
+  P.side = nullptr;
   dfree(P.d_items);
   dfree(P.d_ents);
   dfree(P.d_tasks);
@@ -973,6 +984,9 @@ void execute(h2_ctx* ctx, h2_batch& P, const double* A, const double* B, double 
   pp.B = B;
   pp.err = ctx->d_error;
   pp.stream = ctx->stream;
+  pp.side = P.side;
+  pp.fork = P.fork;
+  pp.join = P.join;
   pp.events = P.timing ? P.ev : nullptr;
   pp.phase_launches = P.phase_launches;
   run_pipeline(pp);
@@ -1364,9 +1378,9 @@ extern "C" h2_status h2_batch_phase_stats(h2_ctx* ctx, const h2_batch* P, int ph
     if (ms) {
       *ms = -1.0;
       if (P->timing && P->ev[0]) {
-        H2_CUDA(cudaEventSynchronize(P->ev[phase + 1]));
+        H2_CUDA(cudaEventSynchronize(P->ev[2 * phase + 1]));
         float t = 0;
-        H2_CUDA(cudaEventElapsedTime(&t, P->ev[phase], P->ev[phase + 1]));
+        H2_CUDA(cudaEventElapsedTime(&t, P->ev[2 * phase], P->ev[2 * phase + 1]));
         *ms = t;
       }
     }

@@ -345,6 +345,9 @@ h2_status run(h2_ctx* ctx, h2_matrix* Z, int32_t b0, int u, const double* A, int
   pp.B = B;
   pp.err = ctx->d_error;
   pp.stream = s;
+  pp.side = nullptr;
+  pp.fork = nullptr;
+  pp.join = nullptr;
   pp.events = nullptr;
   pp.phase_launches = nullptr;
   run_pipeline(pp);

@@ -234,12 +234,12 @@ __device__ __forceinline__ void jacobi32(float (&af)[MR], float (&vf)[32], int r
 // v (lane c holds column c, ncol entries) with V staged in Vs (ld 33):
 // turns the float32-accurate rotation product into an orthogonal matrix to
 // float64 accuracy.
-__device__ __forceinline__ void orthonormalize(double (&v)[32], double* Vs, int ncol, int lane) {
+__device__ __forceinline__ void orthonormalize(double (&v)[32], double* Vs, int ncol, int ldg, int lane) {
   for (int step = 0; step < 2; ++step) {
     if (lane < ncol)
 #pragma unroll
       for (int j = 0; j < 32; ++j)
-        if (j < ncol) Vs[j + lane * 33] = v[j];
+        if (j < ncol) Vs[j + lane * ldg] = v[j];
     __syncwarp();
     double g[32];
 #pragma unroll
@@ -248,7 +248,7 @@ __device__ __forceinline__ void orthonormalize(double (&v)[32], double* Vs, int 
       if (i < ncol && lane < ncol)
 #pragma unroll
         for (int j = 0; j < 32; ++j)
-          if (j < ncol) x = fma(Vs[j + i * 33], v[j], x);
+          if (j < ncol) x = fma(Vs[j + i * ldg], v[j], x);
       g[i] = x;
     }
 #pragma unroll
@@ -257,7 +257,7 @@ __device__ __forceinline__ void orthonormalize(double (&v)[32], double* Vs, int 
       if (j < ncol && lane < ncol)
 #pragma unroll
         for (int i = 0; i < 32; ++i)
-          if (i < ncol) x = fma(Vs[j + i * 33], g[i], x);
+          if (i < ncol) x = fma(Vs[j + i * ldg], g[i], x);
       v[j] = fma(1.5, v[j], -0.5 * x);
     }
     __syncwarp();
@@ -656,39 +656,39 @@ __global__ void k_weights(MatView M, const Item* __restrict__ items, const Entry
 // it is float64 matrix-matrix work with every lane busy.
 
 // Gram G = X^* X of the K columns of X (smem, ld ldx); lane c holds column
-// c of X in xc[].  G goes to Gs (ld 33).
+// c of X in xc[].  G goes to Gs (ld ldg).
 template <int MR>
 __device__ __forceinline__ void gram(const double* X, int ldx, const double (&xc)[MR], int rows, int K, double* Gs,
-                                     int lane) {
+                                     int ldg, int lane) {
   if (lane < K)
     for (int j = 0; j < K; ++j) {
       double g = 0.0;
 #pragma unroll
       for (int i = 0; i < MR; ++i)
         if (i < rows) g = fma(X[i + j * ldx], xc[i], g);
-      Gs[j + lane * 33] = g;
+      Gs[j + lane * ldg] = g;
     }
   __syncwarp();
 }
 
 // In-place Cholesky G - shift I = L L^* of the lower triangle of Gs (ld
-// 33); lane i owns row i.  Returns false (on every lane alike) when a pivot
+// ldg); lane i owns row i.  Returns false (on every lane alike) when a pivot
 // is not positive.
-__device__ __forceinline__ bool chol(double* Gs, int K, double shift, int lane) {
-  if (lane < K) Gs[lane + lane * 33] -= shift;
+__device__ __forceinline__ bool chol(double* Gs, int K, double shift, int ldg, int lane) {
+  if (lane < K) Gs[lane + lane * ldg] -= shift;
   __syncwarp();
   for (int j = 0; j < K; ++j) {
-    const double d = Gs[j + j * 33];
+    const double d = Gs[j + j * ldg];
     if (!(d > 0.0)) return false;
     const double ljj = sqrt(d);
     const double inv = 1.0 / ljj;
     __syncwarp();
-    if (lane == j) Gs[j + j * 33] = ljj;
-    if (lane > j && lane < K) Gs[lane + j * 33] *= inv;
+    if (lane == j) Gs[j + j * ldg] = ljj;
+    if (lane > j && lane < K) Gs[lane + j * ldg] *= inv;
     __syncwarp();
     if (lane > j && lane < K) {
-      const double lij = Gs[lane + j * 33];
-      for (int k = j + 1; k <= lane; ++k) Gs[lane + k * 33] = fma(-lij, Gs[k + j * 33], Gs[lane + k * 33]);
+      const double lij = Gs[lane + j * ldg];
+      for (int k = j + 1; k <= lane; ++k) Gs[lane + k * ldg] = fma(-lij, Gs[k + j * ldg], Gs[lane + k * ldg]);
     }
     __syncwarp();
   }
@@ -698,16 +698,16 @@ __device__ __forceinline__ bool chol(double* Gs, int K, double shift, int lane) 
 // Xs = L^{-1} (lower triangular, ld 33) for the Cholesky factor in Ls;
 // lane c computes column c.  dinv (K entries of shared memory) receives
 // the reciprocal diagonal.
-__device__ __forceinline__ void trinv(const double* Ls, double* Xs, double* dinv, int K, int lane) {
-  if (lane < K) dinv[lane] = 1.0 / Ls[lane + lane * 33];
+__device__ __forceinline__ void trinv(const double* Ls, double* Xs, double* dinv, int K, int ldg, int lane) {
+  if (lane < K) dinv[lane] = 1.0 / Ls[lane + lane * ldg];
   __syncwarp();
   if (lane < K) {
     const int c = lane;
-    Xs[c + c * 33] = dinv[c];
+    Xs[c + c * ldg] = dinv[c];
     for (int i = c + 1; i < K; ++i) {
       double t = 0.0;
-      for (int p = c; p < i; ++p) t = fma(Ls[i + p * 33], Xs[p + c * 33], t);
-      Xs[i + c * 33] = -t * dinv[i];
+      for (int p = c; p < i; ++p) t = fma(Ls[i + p * ldg], Xs[p + c * ldg], t);
+      Xs[i + c * ldg] = -t * dinv[i];
     }
   }
   __syncwarp();
@@ -720,13 +720,14 @@ __device__ __forceinline__ void trinv(const double* Ls, double* Xs, double* dinv
 // X <- X L^{-*} for the Cholesky factor L in Gs (lower, ld 33).
 template <int MR>
 __device__ __forceinline__ void apply_inverse_factor(double* X, int ldx, double (&xc)[MR], int rows, int K,
-                                                     const double* Gs, double* Xs, double* dinv, int lane) {
-  trinv(Gs, Xs, dinv, K, lane);
+                                                     const double* Gs, double* Xs, double* dinv, int ldg,
+                                                     int lane) {
+  trinv(Gs, Xs, dinv, K, ldg, lane);
 #pragma unroll
   for (int i = 0; i < MR; ++i) xc[i] = 0.0;
   if (lane < K)
     for (int j = 0; j <= lane; ++j) {
-      const double x = Xs[lane + j * 33];
+      const double x = Xs[lane + j * ldg];
 #pragma unroll
       for (int i = 0; i < MR; ++i)
         if (i < rows) xc[i] = fma(X[i + j * ldx], x, xc[i]);
@@ -741,10 +742,10 @@ __device__ __forceinline__ void apply_inverse_factor(double* X, int ldx, double 
 
 template <int MR>
 __device__ __forceinline__ bool cholqr_pass(double* X, int ldx, double (&xc)[MR], int rows, int K, double* Gs,
-                                            double* Xs, double* dinv, int lane) {
-  gram<MR>(X, ldx, xc, rows, K, Gs, lane);
-  if (!chol(Gs, K, 0.0, lane)) return false;
-  apply_inverse_factor<MR>(X, ldx, xc, rows, K, Gs, Xs, dinv, lane);
+                                            double* Xs, double* dinv, int ldg, int lane) {
+  gram<MR>(X, ldx, xc, rows, K, Gs, ldg, lane);
+  if (!chol(Gs, K, 0.0, ldg, lane)) return false;
+  apply_inverse_factor<MR>(X, ldx, xc, rows, K, Gs, Xs, dinv, ldg, lane);
   return true;
 }
 
@@ -753,11 +754,12 @@ __device__ __forceinline__ bool cholqr_pass(double* X, int ldx, double (&xc)[MR]
 // X <- X (3I - G) / 2 leaves an orthogonality error of order |G - I|^2.
 // Returns false, leaving X unchanged, when |G - I| is larger.
 template <int MR>
-__device__ __forceinline__ bool polish(double* X, int ldx, double (&xc)[MR], int rows, int K, double* Gs, int lane) {
-  gram<MR>(X, ldx, xc, rows, K, Gs, lane);
+__device__ __forceinline__ bool polish(double* X, int ldx, double (&xc)[MR], int rows, int K, double* Gs, int ldg,
+                                       int lane) {
+  gram<MR>(X, ldx, xc, rows, K, Gs, ldg, lane);
   double dev = 0.0;
   if (lane < K)
-    for (int j = 0; j < K; ++j) dev = fmax(dev, fabs(Gs[j + lane * 33] - (j == lane ? 1.0 : 0.0)));
+    for (int j = 0; j < K; ++j) dev = fmax(dev, fabs(Gs[j + lane * ldg] - (j == lane ? 1.0 : 0.0)));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) dev = fmax(dev, __shfl_xor_sync(kFull, dev, o));
   if (!(dev < 1e-7)) return false;
@@ -766,7 +768,7 @@ __device__ __forceinline__ bool polish(double* X, int ldx, double (&xc)[MR], int
 #pragma unroll
     for (int i = 0; i < MR; ++i) xc[i] *= 1.5;
     for (int j = 0; j < K; ++j) {
-      const double g = -0.5 * Gs[j + lane * 33];
+      const double g = -0.5 * Gs[j + lane * ldg];
 #pragma unroll
       for (int i = 0; i < MR; ++i)
         if (i < rows) xc[i] = fma(X[i + j * ldx], g, xc[i]);
@@ -796,7 +798,8 @@ __global__ void k_truncate(MatView M, const Item* __restrict__ items, const int3
   const int w = threadIdx.x >> 5;
   const int idx = blockIdx.x * (blockDim.x >> 5) + w;
   if (idx >= n) return;
-  double* Vh = smem + (size_t)w * (2 * MR * kl + 2 * 32 * 33 + 32);
+  const int ldg = kl + 1;   // leading dimension of the K x K tiles
+  double* Vh = smem + (size_t)w * (2 * MR * kl + 2 * kl * ldg + kl);
   double* Qs = Vh + MR * kl;
   double* Vs = Qs + MR * kl;
   const int id = list[idx];
@@ -881,9 +884,9 @@ __global__ void k_truncate(MatView M, const Item* __restrict__ items, const int3
     for (int i = 0; i < MR; ++i) a[i] = ldexp(a[i], -ex);
   };
   form_m();
-  double* Gs = Vs;                 // K x K Gram / Cholesky factor (ld 33)
-  double* Xs = Vs + 32 * 33;       // K x K inverse factor (ld 33)
-  double* dinv = Xs + 32 * 33;     // K reciprocal pivots
+  double* Gs = Vs;                 // K x K Gram / Cholesky factor (ld ldg)
+  double* Xs = Vs + kl * ldg;      // K x K inverse factor (ld ldg)
+  double* dinv = Xs + kl * ldg;    // K reciprocal pivots
   const double thr = 0.25 * eps * eps;
   unsigned long long* cnt = IB.jac + 4 * (size_t)id;
   // certified full-rank path: M^* M - (tau + delta) I positive definite
@@ -894,20 +897,20 @@ __global__ void k_truncate(MatView M, const Item* __restrict__ items, const int3
       for (int i = 0; i < MR; ++i)
         if (i < rows) Qs[i + lane * MR] = a[i];
     __syncwarp();
-    gram<MR>(Qs, MR, a, rows, K, Gs, lane);
+    gram<MR>(Qs, MR, a, rows, K, Gs, ldg, lane);
     double trace = 0.0;
-    for (int j = 0; j < K; ++j) trace += Gs[j + j * 33];
+    for (int j = 0; j < K; ++j) trace += Gs[j + j * ldg];
     const double tau = ldexp(thr, -2 * ex);
     const double delta = 4.0 * (double)(rows + K * K) * DBL_EPSILON * trace;
-    if (chol(Gs, K, tau + delta, lane)) {
+    if (chol(Gs, K, tau + delta, ldg, lane)) {
       // The certificate's factor L (L L^* = M^* M - (tau + delta) I) is the
       // first Cholesky-QR pass: M L^{-*} deviates from orthonormality only
       // by (tau + delta) |(L L^*)^{-1}|; a polish (or a second full pass)
       // removes the rest.
-      apply_inverse_factor<MR>(Qs, MR, a, rows, K, Gs, Xs, dinv, lane);
-      certified = polish<MR>(Qs, MR, a, rows, K, Gs, lane) ||
-                  (cholqr_pass<MR>(Qs, MR, a, rows, K, Gs, Xs, dinv, lane) &&
-                   polish<MR>(Qs, MR, a, rows, K, Gs, lane));
+      apply_inverse_factor<MR>(Qs, MR, a, rows, K, Gs, Xs, dinv, ldg, lane);
+      certified = polish<MR>(Qs, MR, a, rows, K, Gs, ldg, lane) ||
+                  (cholqr_pass<MR>(Qs, MR, a, rows, K, Gs, Xs, dinv, ldg, lane) &&
+                   polish<MR>(Qs, MR, a, rows, K, Gs, ldg, lane));
       if (!certified) form_m();   // a factorisation broke down after the certificate
     }
   }
@@ -939,7 +942,7 @@ __global__ void k_truncate(MatView M, const Item* __restrict__ items, const int3
       double v[32];
 #pragma unroll
       for (int j = 0; j < 32; ++j) v[j] = (lane < K && j < K) ? (double)vf[j] : 0.0;
-      orthonormalize(v, Vs, K, lane);
+      orthonormalize(v, Vs, K, ldg, lane);
       __syncwarp();
 #pragma unroll
       for (int i = 0; i < MR; ++i) a[i] = 0.0;
@@ -1122,7 +1125,7 @@ static void launch_truncate_mr(const MatView& M, const Item* items, const int32_
                                double eps, const double* A, const double* B, const ItemBuffers& IB, int* err,
                                cudaStream_t st) {
   const int warps = 2;
-  const size_t sm = (size_t)warps * (2 * MR * kl + 2 * 32 * 33 + 32) * sizeof(double);
+  const size_t sm = (size_t)warps * (2 * MR * kl + 2 * kl * (kl + 1) + kl) * sizeof(double);
   static bool attr = false;
   if (!attr) {
     H2_CUDA(cudaFuncSetAttribute(k_truncate<MR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1145,27 +1148,37 @@ static void launch_truncate(const MatView& M, const Item* items, const int32_t* 
 
 void run_pipeline(const Pipeline& P) {
   cudaStream_t st = P.stream;
+  cudaStream_t bs = P.side ? P.side : P.stream;   // stream of the weights of the unchanged matrix
   int64_t pl[H2_PHASE_COUNT] = {0, 0, 0, 0, 0, 0};
-  auto mark = [&](int ph) {
-    if (P.events) H2_CUDA(cudaEventRecord(P.events[ph], st));
+  auto start = [&](int ph, cudaStream_t s) {
+    if (P.events) H2_CUDA(cudaEventRecord(P.events[2 * ph], s));
+  };
+  auto stop = [&](int ph, cudaStream_t s) {
+    if (P.events) H2_CUDA(cudaEventRecord(P.events[2 * ph + 1], s));
   };
   const int L = P.levels;
+  if (P.side) {
+    H2_CUDA(cudaEventRecord(P.fork, st));
+    H2_CUDA(cudaStreamWaitEvent(P.side, P.fork, 0));
+  }
   // weights of the unchanged matrix: block R-factors of every cluster in one
   // launch, then the inherited part top-down, both sides per launch
-  mark(H2_PHASE_BASE_WEIGHTS);
+  start(H2_PHASE_BASE_WEIGHTS, bs);
   const int ncl = P.cl_ptr[L];
   if (ncl > 0) {
-    k_blockweights<<<blocks_for(ncl), 32 * kWarps, kFoldSmem, st>>>(P.M, P.cl_list, ncl, P.BL, P.BW, P.err);
+    k_blockweights<<<blocks_for(ncl), 32 * kWarps, kFoldSmem, bs>>>(P.M, P.cl_list, ncl, P.BL, P.BW, P.err);
     ++pl[H2_PHASE_BASE_WEIGHTS];
   }
   for (int l = 0; l < L; ++l) {
     const int n = P.cl_ptr[l + 1] - P.cl_ptr[l];
     if (!n) continue;
-    k_baseweights<<<blocks_for(n), 32 * kWarps, kFoldSmem, st>>>(P.M, P.cl_list + P.cl_ptr[l], n, P.BW, P.err);
+    k_baseweights<<<blocks_for(n), 32 * kWarps, kFoldSmem, bs>>>(P.M, P.cl_list + P.cl_ptr[l], n, P.BW, P.err);
     ++pl[H2_PHASE_BASE_WEIGHTS];
   }
+  stop(H2_PHASE_BASE_WEIGHTS, bs);
+  if (P.side) H2_CUDA(cudaEventRecord(P.join, P.side));
   // step 2: basis R-factors, bottom-up
-  mark(H2_PHASE_RFACTOR);
+  start(H2_PHASE_RFACTOR, st);
   for (int l = L - 1; l >= 0; --l) {
     const int n = P.lvl_ptr[l + 1] - P.lvl_ptr[l];
     if (!n) continue;
@@ -1173,19 +1186,22 @@ void run_pipeline(const Pipeline& P) {
                                                               P.A, P.B, P.IB, P.err);
     ++pl[H2_PHASE_RFACTOR];
   }
-  mark(H2_PHASE_NORMS);
+  stop(H2_PHASE_RFACTOR, st);
+  start(H2_PHASE_NORMS, st);
   if (P.n_norms > 0) {
     k_norms<<<blocks_for(P.n_norms), 32 * kWarps, 0, st>>>(P.M, P.items, P.norms, P.n_norms, P.u, P.IB);
     ++pl[H2_PHASE_NORMS];
   }
-  // step 3: outside blocks of the tasks that need their own fold, then the
-  // weights top-down
-  mark(H2_PHASE_WEIGHTS);
+  stop(H2_PHASE_NORMS, st);
+  // step 3: outside blocks of the tasks that need their own fold, then
+  // (after the weights of the unchanged matrix) the weights top-down
+  start(H2_PHASE_WEIGHTS, st);
   const int ni = P.lvl_ptr[L];
   if (ni > 0) {
     k_outside<<<blocks_for(ni), 32 * kWarps, kFoldSmem, st>>>(P.M, P.items, P.ents, P.lvl_list, ni, P.u, P.IB);
     ++pl[H2_PHASE_WEIGHTS];
   }
+  if (P.side) H2_CUDA(cudaStreamWaitEvent(st, P.join, 0));
   for (int l = 0; l < L; ++l) {
     const int n = P.lvl_ptr[l + 1] - P.lvl_ptr[l];
     if (!n) continue;
@@ -1193,8 +1209,9 @@ void run_pipeline(const Pipeline& P) {
                                                               P.u, P.BW, P.IB, P.err);
     ++pl[H2_PHASE_WEIGHTS];
   }
+  stop(H2_PHASE_WEIGHTS, st);
   // step 4: truncation, bottom-up
-  mark(H2_PHASE_TRUNCATE);
+  start(H2_PHASE_TRUNCATE, st);
   for (int l = L - 1; l >= 0; --l) {
     const int n = P.lvl_ptr[l + 1] - P.lvl_ptr[l];
     if (!n) continue;
@@ -1202,13 +1219,14 @@ void run_pipeline(const Pipeline& P) {
                     P.err, st);
     ++pl[H2_PHASE_TRUNCATE];
   }
+  stop(H2_PHASE_TRUNCATE, st);
   // step 5: reprojection
-  mark(H2_PHASE_REPROJECT);
+  start(H2_PHASE_REPROJECT, st);
   if (P.n_tasks > 0) {
     k_reproject<<<blocks_for(P.n_tasks), 32 * kWarps, 0, st>>>(P.M, P.items, P.tasks, P.n_tasks, P.u, P.IB);
     ++pl[H2_PHASE_REPROJECT];
   }
-  mark(H2_PHASE_COUNT);
+  stop(H2_PHASE_REPROJECT, st);
   H2_CUDA(cudaGetLastError());
   if (P.phase_launches)
     for (int ph = 0; ph < H2_PHASE_COUNT; ++ph) P.phase_launches[ph] = pl[ph];

@@ -54,7 +54,12 @@ struct Pipeline {
   const double* B;
   int* err;
   cudaStream_t stream;
-  cudaEvent_t* events;          // H2_PHASE_COUNT + 1 events or nullptr
+  // optional second stream for the weights of the unchanged matrix, which
+  // overlap steps 2 and the outside folds of step 3; fork/join events
+  // required when side != nullptr
+  cudaStream_t side;
+  cudaEvent_t fork, join;
+  cudaEvent_t* events;          // 2 * H2_PHASE_COUNT events (start, end per phase) or nullptr
   int64_t* phase_launches;      // host, H2_PHASE_COUNT entries or nullptr
 };
 
