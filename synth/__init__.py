@@ -87,6 +87,39 @@ def nested_orthonormal_bases(rng: np.random.Generator, leaf_sizes, sibling_pairs
     return ranks, leaf_data, transfer_data
 
 
+def nested_orthonormal_bases_general(rng: np.random.Generator, sizes, sons, k: int):
+    """Random orthonormal nested cluster basis with ranks capped by the sizes.
+
+    sizes -- #t for every cluster in cluster order
+    sons  -- (son1, son2) or None for every cluster in cluster order
+    Ranks: r_t = min(k, #t) for leaves, min(k, r_son1 + r_son2) above.  Draws
+    as in ``nested_orthonormal_bases`` (leaves in cluster order, then one
+    orthonormalised Gaussian (r_son1 + r_son2) x r_t matrix per inner cluster
+    in cluster order, split into the sons' transfers), so both agree when
+    every leaf has at least k indices.
+    """
+    n = len(sizes)
+    ranks = np.zeros(n, dtype=np.int32)
+    for t in reversed(range(n)):
+        ranks[t] = min(k, sizes[t]) if sons[t] is None else min(k, ranks[sons[t][0]] + ranks[sons[t][1]])
+    leaves = []
+    for t in range(n):
+        if sons[t] is None:
+            leaves.append(_orthonormal_columns(rng.standard_normal((sizes[t], ranks[t]))))
+    transfers = {}
+    for t in range(n):
+        if sons[t] is not None:
+            s1, s2 = sons[t]
+            q = _orthonormal_columns(rng.standard_normal((ranks[s1] + ranks[s2], ranks[t])))
+            transfers[s1] = q[:ranks[s1]]
+            transfers[s2] = q[ranks[s1]:]
+    leaf_data = np.concatenate([v.ravel(order="F") for v in leaves]) if leaves else np.zeros(0)
+    nonroot = sorted(transfers)
+    transfer_data = (np.concatenate([transfers[c].ravel(order="F") for c in nonroot])
+                     if nonroot else np.zeros(0))
+    return ranks, leaf_data, transfer_data
+
+
 def gaussian_couplings(rng: np.random.Generator, n_adm: int, k: int, scale: float) -> np.ndarray:
     """n_adm coupling matrices k x k with entries N(0,1)*scale, canonical layout."""
     s = rng.standard_normal((n_adm, k, k)) * scale
@@ -98,6 +131,12 @@ def gaussian_nearfield(rng: np.random.Generator, shapes, scale: float) -> np.nda
     """Dense nearfield blocks (rows x cols per entry of ``shapes``), N(0,1)*scale."""
     parts = [rng.standard_normal(r * c) * scale for r, c in shapes]
     return np.concatenate(parts) if parts else np.zeros(0)
+
+
+def gaussian_blocks(rng: np.random.Generator, shapes, scale: float) -> np.ndarray:
+    """Dense blocks (rows x cols per entry of ``shapes``), N(0,1)*scale,
+    concatenated column-major (coupling matrices of varying ranks)."""
+    return gaussian_nearfield(rng, shapes, scale)
 
 
 def choose_blocks(rng: np.random.Generator, candidates, count: int) -> np.ndarray:

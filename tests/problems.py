@@ -32,9 +32,10 @@ def draw_matrix(tree_sizes, leaf_ids, sibling_pairs, n_clusters, adm_shapes, nea
 
 
 def oracle_problem(N: int, k: int, seed: int, leaf: int = 32, eta: float = 2.0,
-                   coupling_scale=None):
-    """Oracle H^2 matrix on the N x N grid of cell centres with rank k."""
-    pts = synth.grid_points_2d(N)
+                   coupling_scale=None, points=None):
+    """Oracle H^2 matrix on the N x N grid of cell centres (or on ``points``)
+    with rank k."""
+    pts = synth.grid_points_2d(N) if points is None else np.ascontiguousarray(points, dtype=np.float64)
     ct = ClusterTree(pts, leaf)
     bt = BlockTree(ct, ct, eta)
     leaf_ids = [t for t in range(ct.n_clusters) if ct.is_leaf(t)]
@@ -71,3 +72,34 @@ def embed(Z: H2Matrix, b0: int, A: np.ndarray, B: np.ndarray) -> np.ndarray:
     r0, c0 = Z.V.tree.offset[t0], Z.W.tree.offset[s0]
     out[r0:r0 + A.shape[0], c0:c0 + B.shape[0]] = A @ B.T
     return out
+
+
+def draw_matrix_general(sizes, sons, adm_rc, near_shapes, k, seed, coupling_scale=None, near_scale=1.0 / 16):
+    """Like ``draw_matrix`` with ranks capped by the cluster sizes
+    (``synth.nested_orthonormal_bases_general``); adm_rc = (row, col)
+    cluster of every admissible block in block order."""
+    st = synth.streams(seed)
+    V = synth.nested_orthonormal_bases_general(st["bases"], sizes, sons, k)
+    W = synth.nested_orthonormal_bases_general(st["bases"], sizes, sons, k)
+    scale = 1.0 / max(k, 1) if coupling_scale is None else coupling_scale
+    shapes = [(int(V[0][t]), int(W[0][s])) for t, s in adm_rc]
+    S = synth.gaussian_blocks(st["couplings"], shapes, scale)
+    N = synth.gaussian_nearfield(st["couplings"], near_shapes, near_scale)
+    return dict(V=V, W=W, S=S, N=N, streams=st)
+
+
+def oracle_problem_general(points, k, seed, leaf, eta=2.0):
+    """Oracle H^2 matrix on arbitrary points with ranks capped by the sizes."""
+    pts = np.ascontiguousarray(points, dtype=np.float64)
+    ct = ClusterTree(pts, leaf)
+    bt = BlockTree(ct, ct, eta)
+    sons = [tuple(ct.sons[t]) if ct.sons[t] else None for t in range(ct.n_clusters)]
+    adm_rc = [(bt.row[b], bt.col[b]) for b in bt.admissible]
+    near_shapes = [(ct.size[bt.row[b]], ct.size[bt.col[b]]) for b in bt.inadmissible]
+    d = draw_matrix_general(ct.size, sons, adm_rc, near_shapes, k, seed)
+    V = ClusterBasis.from_canonical(ct, *d["V"])
+    W = ClusterBasis.from_canonical(ct, *d["W"])
+    Z = H2Matrix(bt, V, W)
+    Z.set_couplings(d["S"])
+    Z.set_nearfield(d["N"])
+    return Z, d["streams"], pts
