@@ -31,6 +31,11 @@ if ROOT not in sys.path:
 
 import synth  # noqa: E402
 
+# kernels behind each phase of h2_batch_phase_stats
+PHASE_KERNELS = {"base_weights": "k_bgram+k_bgram_down", "rfactor": "k_fgram", "norms": "k_fnorms",
+                 "weights": "k_fweights", "truncate": "k_certify+k_fbasis", "reproject": "k_reproject",
+                 "exact": "exact path (k_blockweights..k_truncate)"}
+
 METRIC = "H²-LR setup s & low-rank updates/s, mixed vs FP64 GPU at equal ε; % roofline"
 UNIT = "updates/s"
 WORK = dict(N=256, leaf=32, eta=2.0, k=16, u=8, eps=1e-8, count=4096, seed=synth.SEED_BASE + 1)
@@ -286,7 +291,9 @@ def main():
                         "tflops": (ps["flops"] / (phase_ms[ph] / args.steps * 1e-3) / 1e12) if phase_ms[ph] > 0 else None}
     dom = max(phases, key=lambda k: phases[k]["ms"])
     ach = phases[dom]["tflops"]
-    roof = {"bound": "alu", "kernel": "k_%s" % dom, "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+    n_exact = int(b.h2_batch_paths(ctx, P, len(blocks)).sum())
+    roof = {"bound": "alu", "kernel": PHASE_KERNELS[dom], "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+            "unit": "TFLOP/s",
             "frac": (ach / FP64_PEAK_TFLOPS) if ach else None, "traffic": None,
             "peak_source": FP64_PEAK_SOURCE,
             "launch_ms": phases[dom]["ms"] / max(1, phases[dom]["launches"])}
@@ -320,7 +327,7 @@ def main():
             "config": {"workload": WORKLOAD_NAME, "mode": "isolated (each update reads the same base matrix)",
                        "l2": "512 MB buffer written between timed steps",
                        "updates": len(blocks), "cluster_tasks": stats["cluster_tasks"],
-                       "block_tasks": stats["block_tasks"]},
+                       "block_tasks": stats["block_tasks"], "exact_path_updates": n_exact},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": stats["launches"] * args.steps,
             "clocks": clocks, "phases": phases, "gflop_per_step": stats["flops"] / 1e9}

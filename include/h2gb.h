@@ -175,16 +175,42 @@ h2_status h2_batch_apply(h2_ctx* ctx, const h2_batch* batch, int64_t j, const do
 h2_status h2_batch_stats(h2_ctx* ctx, const h2_batch* batch, int64_t* n_cluster_tasks,
                          int64_t* n_block_tasks, int64_t* n_launches, double* flops);
 
-/* Phases of an execution, for h2_batch_phase_stats. */
+/* Phases of an execution, for h2_batch_phase_stats.  Phases 0-4 are the
+ * certified Gram path (every update), phase 5 the exact path (the updates
+ * whose certificate failed, see h2_batch_set_mode), phase 6 the
+ * reprojection of every update. */
 typedef enum {
-  H2_PHASE_BASE_WEIGHTS = 0,  /* weights of the unchanged matrix (all clusters)   */
-  H2_PHASE_RFACTOR = 1,       /* step 2: basis R-factors                           */
-  H2_PHASE_NORMS = 2,         /* ||Z~|_b||_F of the blocks inside the update       */
-  H2_PHASE_WEIGHTS = 3,       /* step 3: weight matrices B~_t                      */
-  H2_PHASE_TRUNCATE = 4,      /* step 4: SVD truncation, new bases                 */
-  H2_PHASE_REPROJECT = 5,     /* step 5: reprojection of the couplings             */
-  H2_PHASE_COUNT = 6
+  H2_PHASE_BASE_WEIGHTS = 0,  /* Gram matrices of the weights of the unchanged
+                                 matrix (all clusters)                           */
+  H2_PHASE_RFACTOR = 1,       /* step 2: basis Gram matrices R_t^* R_t           */
+  H2_PHASE_NORMS = 2,         /* ||Z~|_b||_F of the blocks inside the update     */
+  H2_PHASE_WEIGHTS = 3,       /* step 3: weight Gram matrices B~_t^* B~_t        */
+  H2_PHASE_TRUNCATE = 4,      /* step 4: full-rank certificate, new bases        */
+  H2_PHASE_REPROJECT = 5,     /* step 5: reprojection of the couplings           */
+  H2_PHASE_EXACT = 6,         /* steps 2-4 by Householder R-factors and one-sided
+                                 Jacobi SVD for the updates the certificate
+                                 did not cover (with the weights of the
+                                 unchanged matrix they need)                     */
+  H2_PHASE_COUNT = 7
 } h2_phase;
+
+/* Path selection of later executions of this batch.
+ *   H2_MODE_AUTO (default): every update first takes the certified Gram
+ *     path.  Its certificate proves, with a margin covering rounding, that
+ *     the rank rule of step 4 keeps the full extended rank k_t + u at every
+ *     cluster of the update; then every orthonormal basis of range(V~_t)
+ *     gives the same truncated matrix as the singular vectors, and the path
+ *     builds one from the Gram matrix of V~_t.  Updates for which any
+ *     cluster fails the certificate are recomputed by the exact path.
+ *   H2_MODE_EXACT: every update takes the exact path (Householder R-factors,
+ *     one-sided Jacobi SVD; Sections 4 and 5 step by step).
+ * Both produce the truncation the rank rule defines; bases may differ by an
+ * orthogonal change of basis. */
+typedef enum { H2_MODE_AUTO = 0, H2_MODE_EXACT = 1 } h2_mode;
+h2_status h2_batch_set_mode(h2_batch* batch, int mode);
+/* Per update of the last execution (host array of `count` entries): 1 if
+ * the exact path computed it, 0 if the certified path did.  Synchronizes. */
+h2_status h2_batch_paths(h2_ctx* ctx, const h2_batch* batch, int32_t* exact);
 
 /* Enable (on != 0) or disable CUDA-event timing of each phase in later
  * executions of this batch (events on the context's stream). */
@@ -197,10 +223,10 @@ h2_status h2_batch_phase_stats(h2_ctx* ctx, const h2_batch* batch, int phase, in
 /* Intermediate results of one cluster task of the last execution, for
  * step-by-step parity checks.  info (host, 8 entries): update index, side,
  * cluster, rank before, new rank, flags (1 leaf, 2 subtree root, 4 inside
- * blocks, 8 tree root), 0, 0.  which: 0 basis R-factor (step 2), 1 weight
- * matrix B~_t (step 3), 2 R_t = Q_t^* V~_t (step 4); out = the 32 x 32 tile
- * (column-major, ld 32, zero outside the (k+u) x (k+u) or r x (k+u) part).
- * Synchronizes. */
+ * blocks, 8 tree root), 0, 0.  which: 0 Gram matrix R^* R of the basis
+ * R-factor (step 2), 1 Gram matrix B~_t^* B~_t of the weights (step 3), 2
+ * R_t = Q_t^* V~_t (step 4); out = the 32 x 32 tile (column-major, ld 32,
+ * zero outside the (k+u) x (k+u) or r x (k+u) part).  Synchronizes. */
 h2_status h2_batch_item_info(const h2_batch* batch, int64_t item, int32_t* info);
 h2_status h2_batch_item_tile(h2_ctx* ctx, const h2_batch* batch, int64_t item, int which,
                              double* out);

@@ -29,10 +29,13 @@ EXPORTS = [
     "h2_batch_create", "h2_batch_free", "h2_batch_factor_layout", "h2_batch_factor_sizes",
     "h2_batch_execute", "h2_batch_execute_host", "h2_batch_result_size", "h2_batch_apply",
     "h2_batch_stats", "h2_batch_set_timing", "h2_batch_phase_stats", "h2_batch_item_info", "h2_batch_item_tile",
-    "h2_batch_update_items", "h2_lowrank_update", "h2_lowrank_update_noalloc",
+    "h2_batch_update_items", "h2_batch_set_mode", "h2_batch_paths", "h2_lowrank_update",
+    "h2_lowrank_update_noalloc",
 ]
 
-PHASES = ("base_weights", "rfactor", "norms", "weights", "truncate", "reproject")
+PHASES = ("base_weights", "rfactor", "norms", "weights", "truncate", "reproject", "exact")
+
+MODE_AUTO, MODE_EXACT = 0, 1
 
 
 class H2Error(RuntimeError):
@@ -93,6 +96,8 @@ _sig("h2_batch_result_size", _int, _p, _p)
 _sig("h2_batch_apply", _int, _p, _p, _i64, _p, _p, _p)
 _sig("h2_batch_stats", _int, _p, _p, _p, _p, _p, _p)
 _sig("h2_batch_set_timing", _int, _p, _int)
+_sig("h2_batch_set_mode", _int, _p, _int)
+_sig("h2_batch_paths", _int, _p, _p, _p)
 _sig("h2_batch_phase_stats", _int, _p, _p, _int, _p, _p, _p)
 _sig("h2_batch_item_info", _int, _p, _i64, _p)
 _sig("h2_batch_item_tile", _int, _p, _p, _i64, _int, _p)
@@ -313,6 +318,19 @@ def h2_batch_stats(ctx, P, flops: bool = True) -> dict:
 
 def h2_batch_set_timing(P, on: bool):
     _check(_lib.h2_batch_set_timing(P, 1 if on else 0))
+
+
+def h2_batch_set_mode(P, mode: int):
+    """MODE_AUTO: certified Gram path, exact path for the updates it does not
+    cover; MODE_EXACT: exact path for every update."""
+    _check(_lib.h2_batch_set_mode(P, int(mode)))
+
+
+def h2_batch_paths(ctx, P, count: int) -> np.ndarray:
+    """Per update of the last execution: 1 if the exact path computed it."""
+    out = np.zeros(max(count, 1), dtype=np.int32)
+    _check(_lib.h2_batch_paths(ctx, P, out.ctypes.data))
+    return out[:count]
 
 
 def h2_batch_phase_stats(ctx, P, phase: int, flops: bool = True) -> dict:

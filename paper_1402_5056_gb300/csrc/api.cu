@@ -710,7 +710,8 @@ struct h2_batch {
   int64_t* d_res_task_off = nullptr;
   int64_t* d_res_item_off = nullptr;
   int64_t launches = 0;
-  int64_t phase_launches[H2_PHASE_COUNT] = {0, 0, 0, 0, 0, 0};
+  int64_t phase_launches[H2_PHASE_COUNT] = {};
+  int mode = H2_MODE_AUTO;
   bool executed = false;
   bool timing = false;
   cudaEvent_t ev[2 * H2_PHASE_COUNT] = {};   // start and end of every phase
@@ -755,6 +756,7 @@ void plan_batch(h2_batch& P) {
       }
       for (int32_t c : sub[sd]) {
         Item it{};
+        it.update = (int32_t)j;
         it.side = sd;
         it.cluster = c;
         it.parent = (c == root[sd]) ? -1 : item_of[sd][ct.father[c]];
@@ -902,6 +904,9 @@ void alloc_batch(h2_ctx* ctx, h2_batch& P) {
   const size_t ni = P.items.size();
   P.IB.Rq = dalloc<double>(ni * kSlot);
   P.IB.Bw = dalloc<double>(ni * kSlot);
+  P.IB.Gv = dalloc<double>(ni * kSlot);
+  P.IB.Wg = dalloc<double>(ni * kSlot);
+  P.IB.fail = dalloc<int32_t>(P.count);
   P.IB.Rt = dalloc<double>(ni * kSlot);
   P.IB.F = dalloc<double>(ni * kSlot);
   P.IB.Q = dalloc<double>(P.qlen);
@@ -915,6 +920,11 @@ void alloc_batch(h2_ctx* ctx, h2_batch& P) {
   for (int sd = 0; sd < 2; ++sd) {
     P.BW.G[sd] = dalloc<double>((size_t)ncl[sd] * kSlot);
     P.BW.B[sd] = dalloc<double>((size_t)ncl[sd] * kSlot);
+    // the certified path's Gram matrices are dead before the exact path
+    // writes G and B
+    P.BW.Wo[sd] = P.BW.G[sd];
+    P.BW.W0[sd] = P.BW.B[sd];
+    P.BW.need[sd] = dalloc<int32_t>(ncl[sd]);
   }
   H2_CUDA(cudaStreamSynchronize(st));
 }
@@ -935,9 +945,14 @@ void free_batch_device(h2_batch& P) {
   for (int sd = 0; sd < 2; ++sd) {
     dfree(P.BW.G[sd]);
     dfree(P.BW.B[sd]);
+    dfree(P.BW.need[sd]);
+    P.BW.Wo[sd] = P.BW.W0[sd] = nullptr;
   }
   dfree(P.IB.Rq);
   dfree(P.IB.Bw);
+  dfree(P.IB.Gv);
+  dfree(P.IB.Wg);
+  dfree(P.IB.fail);
   dfree(P.IB.Rt);
   dfree(P.IB.F);
   dfree(P.IB.Q);
@@ -975,6 +990,10 @@ void execute(h2_ctx* ctx, h2_batch& P, const double* A, const double* B, double 
   pp.cl_list = P.d_cl;
   pp.cl_ptr = P.cl_ptr.data();
   pp.levels = P.depth + 1;
+  pp.n_updates = (int)P.count;
+  pp.ncl[0] = Z->rows.count();
+  pp.ncl[1] = Z->cols.count();
+  pp.exact_only = P.mode == H2_MODE_EXACT ? 1 : 0;
   pp.n_tasks = (int)P.tasks.size();
   pp.n_norms = (int)P.norms.size();
   pp.u = P.u;
@@ -1235,26 +1254,49 @@ namespace {
 
 // Algorithmic float64 flops per phase of the last execution (standard
 // counts: Householder QR 2mn^2 - 2n^3/3, products 2mnk with triangular
-// factors halved, one-sided Jacobi 6m per pair checked plus 6m per
-// rotation as counted on the device).
+// factors halved, symmetric products on their lower triangle, one-sided
+// Jacobi 6m per pair checked plus 6m per rotation as counted on the device).
+// The certified path counts for every update (it runs for all of them), the
+// exact path for the updates it recomputed and the clusters it marked.
 void phase_flops(h2_ctx* ctx, const h2_batch* P, double f[H2_PHASE_COUNT]) {
   for (int ph = 0; ph < H2_PHASE_COUNT; ++ph) f[ph] = 0.0;
   const size_t ni = P->items.size();
   std::vector<unsigned long long> jac(4 * ni);
   std::vector<int32_t> rk(ni);
+  std::vector<int32_t> fail(P->count, 1);
   if (ni) {
     H2_CUDA(cudaMemcpyAsync(jac.data(), P->IB.jac, 4 * ni * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                             ctx->stream));
     H2_CUDA(cudaMemcpyAsync(rk.data(), P->IB.rank, ni * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
   }
+  if (P->count)
+    H2_CUDA(cudaMemcpyAsync(fail.data(), P->IB.fail, P->count * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                            ctx->stream));
   H2_CUDA(cudaStreamSynchronize(ctx->stream));
+  const bool gram = P->mode != H2_MODE_EXACT;
   const double u = P->u;
   auto qr = [](double m, double n) {
     return m >= n ? 2 * m * n * n - 2.0 / 3.0 * n * n * n : 2 * n * m * m - 2.0 / 3.0 * m * m * m;
   };
+  auto tri = [](double n) { return n * (n + 1) / 2; };
+  // LDL^*: per pivot the scaled column and the symmetric trailing update
+  auto ldl = [&](double n) {
+    double x = 0;
+    for (double m = n - 1; m >= 0; m -= 1) x += m + 2 * tri(m);
+    return x;
+  };
   const h2_matrix* Z = P->Z;
   // fold of ch rows into an upper n x n factor: 2 ch n^2 (Householder)
   auto fold = [](double ch, double n) { return 2.0 * ch * n * n; };
+  // clusters whose weights of the unchanged matrix the exact path computed
+  std::vector<char> need[2];
+  for (int sd = 0; sd < 2; ++sd) need[sd].assign(tree_of(Z, sd).count(), gram ? 0 : 1);
+  if (gram)
+    for (size_t i = 0; i < ni; ++i) {
+      const Item& it = P->items[i];
+      if (!fail[it.update]) continue;
+      for (int32_t c = it.cluster; c >= 0; c = tree_of(Z, it.side).father[c]) need[it.side][c] = 1;
+    }
   for (int sd = 0; sd < 2; ++sd) {
     const ClusterTree& ct = tree_of(Z, sd);
     const DeviceBasis& bs = basis_of(Z, sd);
@@ -1266,26 +1308,73 @@ void phase_flops(h2_ctx* ctx, const h2_batch* P, double f[H2_PHASE_COUNT]) {
       for (int32_t e = ptr[c]; e < ptr[c + 1]; ++e) {
         const int32_t blk = Z->blocks.adm[adm[e]];
         const double l = o.rank[sd == 0 ? Z->blocks.col[blk] : Z->blocks.row[blk]];
-        f[H2_PHASE_BASE_WEIGHTS] += 2 * k * l + fold(l, k);   // norm, fold
+        if (gram) f[H2_PHASE_BASE_WEIGHTS] += 2 * k * l + 2 * tri(k) * l + 2 * tri(k);
+        if (need[sd][c]) f[H2_PHASE_EXACT] += 2 * k * l + fold(l, k);   // norm, fold
       }
       if (ct.father[c] >= 0) {
         const double kf = bs.rank[ct.father[c]];
-        f[H2_PHASE_BASE_WEIGHTS] += kf * kf * k + fold(kf, k);
+        if (gram) f[H2_PHASE_BASE_WEIGHTS] += 2 * k * kf * kf + 2 * tri(k) * kf;
+        if (need[sd][c]) f[H2_PHASE_EXACT] += kf * kf * k + fold(kf, k);
       }
     }
   }
   for (const NormTask& nt : P->norms) {
-    const double Kt = P->items[nt.it].k + u, Ks = P->items[nt.is].k + u;
-    f[H2_PHASE_NORMS] += 2 * P->items[nt.it].k * P->items[nt.is].k * Ks + Kt * Kt * Ks + 2 * Kt * Ks;
+    const double kt = P->items[nt.it].k, ls = P->items[nt.is].k;
+    const double Kt = kt + u, Ks = ls + u;
+    if (gram) f[H2_PHASE_NORMS] += 2 * Kt * ls * kt + 2 * kt * Ks * ls + 2 * Kt * Ks;
+    if (fail[P->items[nt.it].update]) f[H2_PHASE_EXACT] += 2 * kt * ls * Ks + Kt * Kt * Ks + 2 * Kt * Ks;
   }
   for (size_t i = 0; i < ni; ++i) {
     const Item& it = P->items[i];
     const double k = it.k, K = it.k + u;
-    if (it.flags & kItemLeaf) {
-      f[H2_PHASE_RFACTOR] += qr(it.size, K);
+    const bool leaf = it.flags & kItemLeaf;
+    const bool root = it.flags & kItemRoot;
+    const bool troot = it.flags & kItemTreeRoot;
+    const double kf = it.kf;
+    if (gram) {
+      // step 2: basis Gram matrices
+      if (leaf) {
+        f[H2_PHASE_RFACTOR] += 2 * tri(K) * it.size;
+      } else {
+        for (int32_t sid : {it.son0, it.son1}) {
+          const double ks = P->items[sid].k;
+          f[H2_PHASE_RFACTOR] += 2 * (ks + u) * k * ks + 2 * tri(k) * ks + (tri(K) - tri(k));
+        }
+      }
+      // step 3: weight Gram matrices (jac[3] = 1: V_t not orthonormal)
+      const bool orth = jac[4 * i + 3] == 0;
+      for (int32_t e = it.ent_begin; e < it.ent_end; ++e) {
+        const Entry& en = P->ents[e];
+        const double l = basis_of(Z, 1 - it.side).rank[en.other_cluster];
+        if (en.other >= 0) {
+          if (orth) f[H2_PHASE_WEIGHTS] += 2 * k * l + 2 * tri(k) * l + 2 * tri(k);
+          f[H2_PHASE_WEIGHTS] += 2 * k * (l + u) * l + 2 * (k * K - tri(k - 1)) * l + 2 * tri(K);
+        } else if (!orth) {
+          f[H2_PHASE_WEIGHTS] += 2 * k * k * l + 2 * k * l + 2 * tri(k) * l + 2 * tri(k);
+        }
+      }
+      if (root && !troot) {
+        f[H2_PHASE_WEIGHTS] += 2 * k * kf * kf + 2 * tri(k) * kf;
+      } else if (!root) {
+        f[H2_PHASE_WEIGHTS] += 2 * k * (kf + u) * kf + 2 * (k * K - tri(k - 1)) * kf;
+      }
+      // step 4: certificate (two LDL^*, W L_G, L_G^* (W L_G)) and new bases
+      f[H2_PHASE_TRUNCATE] += 2 * ldl(K) + 2 * K * tri(K) + (K * K * K + 3 * K * K + 2 * K) / 3;
+      if (!fail[it.update]) {
+        if (leaf) f[H2_PHASE_TRUNCATE] += (double)it.size * K * K;
+        if (!troot) {
+          f[H2_PHASE_TRUNCATE] += 2 * tri(k) * kf;
+          if (!root) f[H2_PHASE_TRUNCATE] += K * (kf + u) * (kf + u);
+        }
+      }
+    }
+    if (!fail[it.update]) continue;
+    // exact path
+    if (leaf) {
+      f[H2_PHASE_EXACT] += qr(it.size, K);
     } else {
       const double k0 = P->items[it.son0].k, k1 = P->items[it.son1].k;
-      f[H2_PHASE_RFACTOR] += (k0 + u) * k0 * k + (k1 + u) * k1 * k + qr(k0 + k1 + 2 * u, K);
+      f[H2_PHASE_EXACT] += (k0 + u) * k0 * k + (k1 + u) * k1 * k + qr(k0 + k1 + 2 * u, K);
     }
     // weights: outside blocks folded into k columns by the task itself when
     // some block lies inside the update (otherwise the precomputed G_t), then
@@ -1295,21 +1384,21 @@ void phase_flops(h2_ctx* ctx, const h2_batch* P, double f[H2_PHASE_COUNT]) {
         const Entry& en = P->ents[e];
         if (en.other < 0) {
           const double l = basis_of(Z, 1 - it.side).rank[en.other_cluster];
-          f[H2_PHASE_WEIGHTS] += 2 * k * l + fold(l, k);
+          f[H2_PHASE_EXACT] += 2 * k * l + fold(l, k);
         } else {
           const double l = P->items[en.other].k;
-          f[H2_PHASE_WEIGHTS] += (l + u) * l * k + fold(l + u, K);
+          f[H2_PHASE_EXACT] += (l + u) * l * k + fold(l + u, K);
         }
       }
     }
-    if (!(it.flags & kItemTreeRoot)) {
-      const double kf = (it.flags & kItemRoot) ? it.kf : it.kf + u;
-      f[H2_PHASE_WEIGHTS] += kf * it.kf * k + fold(kf, K);
+    if (!troot) {
+      const double kfx = root ? kf : kf + u;
+      f[H2_PHASE_EXACT] += kfx * kf * k + fold(kfx, K);
     }
     // truncation
-    const double m = (it.flags & kItemLeaf) ? it.size : rk[it.son0] + rk[it.son1];
+    const double m = leaf ? it.size : rk[it.son0] + rk[it.son1];
     double ft = 0;
-    if (!(it.flags & kItemLeaf)) {
+    if (!leaf) {
       const double k0 = P->items[it.son0].k, k1 = P->items[it.son1].k;
       ft += 2 * rk[it.son0] * k0 * k + 2 * rk[it.son1] * k1 * k;
     }
@@ -1324,8 +1413,8 @@ void phase_flops(h2_ctx* ctx, const h2_batch* P, double f[H2_PHASE_COUNT]) {
       ft += 6.0 * m * (double)jac[4 * i] + 6.0 * m * (double)jac[4 * i + 1];
     }
     ft += 2 * m * K * rk[i];                                       // R_t = Q^* V^
-    if ((it.flags & kItemRoot) && !(it.flags & kItemTreeRoot)) ft += 2 * rk[i] * k * it.kf;
-    f[H2_PHASE_TRUNCATE] += ft;
+    if (root && !troot) ft += 2 * rk[i] * k * kf;
+    f[H2_PHASE_EXACT] += ft;
   }
   for (const Task& tk : P->tasks) {
     if (tk.it >= 0 && tk.is >= 0)
@@ -1365,6 +1454,24 @@ extern "C" h2_status h2_batch_set_timing(h2_batch* P, int on) {
       for (cudaEvent_t& e : P->ev) H2_CUDA(cudaEventCreate(&e));
     }
     P->timing = on != 0;
+  });
+}
+
+extern "C" h2_status h2_batch_set_mode(h2_batch* P, int mode) {
+  if (!P || (mode != H2_MODE_AUTO && mode != H2_MODE_EXACT)) return H2_EINVAL;
+  P->mode = mode;
+  return H2_OK;
+}
+
+extern "C" h2_status h2_batch_paths(h2_ctx* ctx, const h2_batch* P, int32_t* exact) {
+  if (!ctx || !P || (P->count > 0 && !exact)) return H2_EINVAL;
+  return guard(ctx, [&] {
+    H2_REQUIRE(P->executed, "h2_batch_paths: batch not executed");
+    DeviceGuard g(ctx->device);
+    if (P->count)
+      H2_CUDA(cudaMemcpyAsync(exact, P->IB.fail, P->count * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    H2_CUDA(cudaStreamSynchronize(ctx->stream));
+    for (int64_t j = 0; j < P->count; ++j) exact[j] = exact[j] != 0;
   });
 }
 
@@ -1417,9 +1524,33 @@ extern "C" h2_status h2_batch_item_tile(h2_ctx* ctx, const h2_batch* P, int64_t 
   return guard(ctx, [&] {
     H2_REQUIRE(P->executed, "h2_batch_item_tile: batch not executed");
     DeviceGuard g(ctx->device);
-    const double* src = (which == 0 ? P->IB.Rq : which == 1 ? P->IB.Bw : P->IB.Rt) + (size_t)item * kSlot;
-    H2_CUDA(cudaMemcpyAsync(out, src, kSlot * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    const Item& it = P->items[item];
+    int32_t exact = 1;
+    if (P->count)
+      H2_CUDA(cudaMemcpyAsync(&exact, P->IB.fail + it.update, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                              ctx->stream));
     H2_CUDA(cudaStreamSynchronize(ctx->stream));
+    // which 0, 1: the certified path stores the Gram matrices themselves, the
+    // exact path R-factors (returned as R^* R)
+    const double* src = which == 2 ? P->IB.Rt
+                        : exact    ? (which == 0 ? P->IB.Rq : P->IB.Bw)
+                                   : (which == 0 ? P->IB.Gv : P->IB.Wg);
+    src += (size_t)item * kSlot;
+    std::vector<double> tile(kSlot);
+    H2_CUDA(cudaMemcpyAsync(tile.data(), src, kSlot * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    H2_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (which == 2 || !exact) {
+      std::copy(tile.begin(), tile.end(), out);
+      return;
+    }
+    const int K = it.k + P->u;
+    for (int j = 0; j < 32; ++j)
+      for (int i = 0; i < 32; ++i) {
+        double g = 0.0;
+        if (i < K && j < K)
+          for (int q = 0; q < 32; ++q) g += tile[q + i * 32] * tile[q + j * 32];
+        out[i + j * 32] = g;
+      }
   });
 }
 

@@ -64,7 +64,9 @@ constexpr size_t kOffLvl = kOffNT + align256((size_t)kNaNorms * sizeof(NormTask)
 constexpr size_t kOffCl = kOffLvl + align256((size_t)kNaItems * 4);
 constexpr size_t kOffCopy = kOffCl + align256(2ull * kNaClusters * 4);
 constexpr size_t kOffNear = kOffCopy + align256((size_t)(2 * kNaItems + kNaTasks) * sizeof(CopyDesc));
-constexpr size_t kScratchBytes = kOffNear + align256((size_t)kNaNear * sizeof(NearDesc));
+constexpr size_t kOffNeed = kOffNear + align256((size_t)kNaNear * sizeof(NearDesc));    // 2 sides
+constexpr size_t kOffFail = kOffNeed + align256(2ull * kNaClusters * 4);
+constexpr size_t kScratchBytes = kOffFail + align256(4);
 static_assert(kScratchBytes <= (48u << 20), "scratch above its stated 48 MiB");
 
 static __device__ __align__(256) unsigned char h2_noalloc_scratch[kScratchBytes];
@@ -157,6 +159,7 @@ h2_status plan_single(const h2_matrix* Z, int32_t b0, int u, int64_t lda, int64_
       if (P.n_items >= kNaItems)
         return fail(H2_EINVAL, "the update touches more than %lld cluster tasks (fixed scratch limit)", kNaItems);
       Item it{};
+      it.update = 0;
       it.side = sd;
       it.cluster = c;
       it.parent = (c == root[sd]) ? -1 : P.item_of[sd][ct.father[c]];
@@ -296,10 +299,18 @@ h2_status run(h2_ctx* ctx, h2_matrix* Z, int32_t b0, int u, const double* A, int
   IB.norms = reinterpret_cast<double*>(base + kOffNorm);
   IB.S_out = reinterpret_cast<double*>(base + kOffS);
   IB.jac = reinterpret_cast<unsigned long long*>(base + kOffJac);
+  // the certified path's Gram matrices are dead before the exact path
+  // writes its R-factors and weights into the same tiles
+  IB.Gv = IB.Rq;
+  IB.Wg = IB.Bw;
+  IB.fail = reinterpret_cast<int32_t*>(base + kOffFail);
   BaseWeights BW{};
   for (int sd = 0; sd < 2; ++sd) {
     BW.G[sd] = reinterpret_cast<double*>(base + kOffG) + (size_t)sd * kNaClusters * kSlot;
     BW.B[sd] = reinterpret_cast<double*>(base + kOffB) + (size_t)sd * kNaClusters * kSlot;
+    BW.Wo[sd] = BW.G[sd];
+    BW.W0[sd] = BW.B[sd];
+    BW.need[sd] = reinterpret_cast<int32_t*>(base + kOffNeed) + (size_t)sd * kNaClusters;
   }
   MatView M;
   for (int sd = 0; sd < 2; ++sd) {
@@ -336,6 +347,10 @@ h2_status run(h2_ctx* ctx, h2_matrix* Z, int32_t b0, int u, const double* A, int
   pp.cl_list = d_cl;
   pp.cl_ptr = P.cl_ptr;
   pp.levels = L;
+  pp.n_updates = 1;
+  pp.ncl[0] = Z->rows.count();
+  pp.ncl[1] = Z->cols.count();
+  pp.exact_only = 0;
   pp.n_tasks = P.n_tasks;
   pp.n_norms = P.n_norms;
   pp.u = u;

@@ -22,6 +22,13 @@ constexpr int kMaxSweeps = 40;
 
 __device__ __forceinline__ void flag(int* err, int code) { atomicOr(err, code); }
 
+// a[side] without dynamic indexing of a kernel-parameter array (which would
+// copy the parameter struct to local memory)
+template <class T>
+__device__ __forceinline__ T pick(T const (&a)[2], int side) {
+  return side ? a[1] : a[0];
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
@@ -284,19 +291,20 @@ __global__ void k_blockweights(MatView M, const int32_t* __restrict__ list, int 
   double* vb = R + 32 * kLdr;
   const int side = list[idx] >> 30;
   const int c = list[idx] & 0x3fffffff;
-  const int k = M.rank[side][c];
+  if (!pick(BW.need, side)[c]) return;
+  const int k = pick(M.rank, side)[c];
   const int kcap = M.kcap;
   if (k > 32) {
     if (lane == 0) flag(err, kErrCols);
     return;
   }
   zero_tile(R, lane);
-  const double st = sqrt((double)M.subtree[side][c]);
+  const double st = sqrt((double)pick(M.subtree, side)[c]);
   double x[kCh];
-  for (int e = BL.ptr[side][c]; e < BL.ptr[side][c + 1]; ++e) {
-    const int slot = BL.adm[side][e];
-    const int o = BL.other[side][slot];
-    const int l = M.rank[1 - side][o];
+  for (int e = pick(BL.ptr, side)[c]; e < pick(BL.ptr, side)[c + 1]; ++e) {
+    const int slot = pick(BL.adm, side)[e];
+    const int o = pick(BL.other, side)[slot];
+    const int l = pick(M.rank, 1 - side)[o];
     const double* S = M.S + (size_t)slot * kcap * kcap;
     // ||S_b||_F
     double part = 0.0;
@@ -318,7 +326,7 @@ __global__ void k_blockweights(MatView M, const int32_t* __restrict__ list, int 
     }
     fold(R, x, l, k, vb, lane);
   }
-  store_tile(BW.G[side] + (size_t)c * kSlot, R, k, lane);
+  store_tile(pick(BW.G, side) + (size_t)c * kSlot, R, k, lane);
 }
 
 __global__ void k_baseweights(MatView M, const int32_t* __restrict__ list, int n, BaseWeights BW, int* err) {
@@ -331,22 +339,23 @@ __global__ void k_baseweights(MatView M, const int32_t* __restrict__ list, int n
   double* vb = R + 32 * kLdr;
   const int side = list[idx] >> 30;
   const int c = list[idx] & 0x3fffffff;
-  const int k = M.rank[side][c];
+  if (!pick(BW.need, side)[c]) return;
+  const int k = pick(M.rank, side)[c];
   const int kcap = M.kcap;
   if (k > 32) {
     if (lane == 0) flag(err, kErrCols);
     return;
   }
   zero_tile(R, lane);
-  const double* G = BW.G[side] + (size_t)c * kSlot;
+  const double* G = pick(BW.G, side) + (size_t)c * kSlot;
   if (lane < k)
     for (int i = 0; i <= lane; ++i) R[i + lane * kLdr] = G[i + lane * 32];
   __syncwarp();
-  const int f = M.father[side][c];
+  const int f = pick(M.father, side)[c];
   if (f >= 0) {
-    const int kf = M.rank[side][f];
-    const double* P = BW.B[side] + (size_t)f * kSlot;
-    const double* E = M.transfer[side] + (size_t)c * kcap * kcap;   // k x kf
+    const int kf = pick(M.rank, side)[f];
+    const double* P = pick(BW.B, side) + (size_t)f * kSlot;
+    const double* E = pick(M.transfer, side) + (size_t)c * kcap * kcap;   // k x kf
     double x[kCh];
 #pragma unroll
     for (int i = 0; i < kCh; ++i) {
@@ -357,7 +366,7 @@ __global__ void k_baseweights(MatView M, const int32_t* __restrict__ list, int n
     }
     fold(R, x, kf, k, vb, lane);
   }
-  store_tile(BW.B[side] + (size_t)c * kSlot, R, k, lane);
+  store_tile(pick(BW.B, side) + (size_t)c * kSlot, R, k, lane);
 }
 
 // ------------------------------------------------------------- step 2
@@ -375,6 +384,7 @@ __global__ void k_rfactor(MatView M, const Item* __restrict__ items, const int32
   double* vb = R + 32 * kLdr;
   const int id = list[idx];
   const Item it = items[id];
+  if (!IB.fail[it.update]) return;
   const int side = it.side;
   const int k = it.k;
   const int K = k + u;
@@ -385,7 +395,7 @@ __global__ void k_rfactor(MatView M, const Item* __restrict__ items, const int32
   zero_tile(R, lane);
   double x[kCh];
   if (it.flags & kItemLeaf) {
-    const double* V = M.leaf[side] + M.leaf_off[side][it.cluster];
+    const double* V = pick(M.leaf, side) + pick(M.leaf_off, side)[it.cluster];
     const double* F = (side == 0 ? A : B) + it.foff;
     const int m = it.size;
     for (int r0 = 0; r0 < m; r0 += kCh) {
@@ -410,7 +420,7 @@ __global__ void k_rfactor(MatView M, const Item* __restrict__ items, const int32
       const int ks = sn.k;
       const int Ks = ks + u;
       const double* Rs = IB.Rq + (size_t)sons[si] * kSlot;
-      const double* E = M.transfer[side] + (size_t)sn.cluster * M.kcap * M.kcap;   // ks x k
+      const double* E = pick(M.transfer, side) + (size_t)sn.cluster * M.kcap * M.kcap;   // ks x k
 #pragma unroll
       for (int i = 0; i < kCh; ++i) {
         double v = 0.0;
@@ -438,6 +448,7 @@ __global__ void k_norms(MatView M, const Item* __restrict__ items, const NormTas
   if (idx >= n) return;
   const NormTask tk = tasks[idx];
   const Item it = items[tk.it];
+  if (!IB.fail[it.update]) return;
   const Item is = items[tk.is];
   const int kt = it.k, ls = is.k;
   const int Kt = kt + u, Ks = ls + u;
@@ -502,6 +513,7 @@ __global__ void k_outside(MatView M, const Item* __restrict__ items, const Entry
   double* vb = R + 32 * kLdr;
   const int id = list[idx];
   const Item it = items[id];
+  if (!IB.fail[it.update]) return;
   const int side = it.side;
   const int k = it.k;
   const int kcap = M.kcap;
@@ -511,13 +523,13 @@ __global__ void k_outside(MatView M, const Item* __restrict__ items, const Entry
   if (lane == 0) IB.own[id] = own ? 1 : 0;
   if (!own) return;
   zero_tile(R, lane);
-  const double st = sqrt((double)M.subtree[side][it.cluster]);
+  const double st = sqrt((double)pick(M.subtree, side)[it.cluster]);
   double x[kCh];
   for (int e = it.ent_begin; e < it.ent_end; ++e) {
     const Entry en = ents[e];
     if (en.other >= 0) continue;
     const double* S = M.S + (size_t)en.slot * kcap * kcap;
-    const int l = M.rank[1 - side][en.other_cluster];
+    const int l = pick(M.rank, 1 - side)[en.other_cluster];
     double part = 0.0;
     if (orth) {
       // ||S_b||_F
@@ -562,16 +574,17 @@ __global__ void k_weights(MatView M, const Item* __restrict__ items, const Entry
   double* vb = R + 32 * kLdr;
   const int id = list[idx];
   const Item it = items[id];
+  if (!IB.fail[it.update]) return;
   const int side = it.side;
   const int k = it.k;
   const int K = k + u;
   const int kcap = M.kcap;
   zero_tile(R, lane);
   double x[kCh];
-  const double st = sqrt((double)M.subtree[side][it.cluster]);
+  const double st = sqrt((double)pick(M.subtree, side)[it.cluster]);
   // outside blocks: their R-factor, padded with zero columns to K
   {
-    const double* G = IB.own[id] ? IB.Bw + (size_t)id * kSlot : BW.G[side] + (size_t)it.cluster * kSlot;
+    const double* G = IB.own[id] ? IB.Bw + (size_t)id * kSlot : pick(BW.G, side) + (size_t)it.cluster * kSlot;
     if (lane < k)
       for (int i = 0; i <= lane; ++i) R[i + lane * kLdr] = G[i + lane * 32];
     __syncwarp();
@@ -608,10 +621,10 @@ __global__ void k_weights(MatView M, const Item* __restrict__ items, const Entry
   // father's part
   if (it.flags & kItemRoot) {
     if (!(it.flags & kItemTreeRoot)) {
-      const int f = M.father[side][it.cluster];
+      const int f = pick(M.father, side)[it.cluster];
       const int kf = it.kf;
-      const double* P = BW.B[side] + (size_t)f * kSlot;
-      const double* E = M.transfer[side] + (size_t)it.cluster * kcap * kcap;   // k x kf
+      const double* P = pick(BW.B, side) + (size_t)f * kSlot;
+      const double* E = pick(M.transfer, side) + (size_t)it.cluster * kcap * kcap;   // k x kf
 #pragma unroll
       for (int i = 0; i < kCh; ++i) {
         double v = 0.0;
@@ -626,7 +639,7 @@ __global__ void k_weights(MatView M, const Item* __restrict__ items, const Entry
     const int kf = pt.k;
     const int Kf = kf + u;
     const double* P = IB.Bw + (size_t)it.parent * kSlot;
-    const double* E = M.transfer[side] + (size_t)it.cluster * kcap * kcap;   // k x kf
+    const double* E = pick(M.transfer, side) + (size_t)it.cluster * kcap * kcap;   // k x kf
 #pragma unroll
     for (int i = 0; i < kCh; ++i) {
       double v = 0.0;
@@ -804,6 +817,7 @@ __global__ void k_truncate(MatView M, const Item* __restrict__ items, const int3
   double* Vs = Qs + MR * kl;
   const int id = list[idx];
   const Item it = items[id];
+  if (!IB.fail[it.update]) return;
   const int side = it.side;
   const int k = it.k;
   const int K = k + u;
@@ -827,7 +841,7 @@ __global__ void k_truncate(MatView M, const Item* __restrict__ items, const int3
   }
   // V^_t into shared memory (ld MR), one column per lane
   if (it.flags & kItemLeaf) {
-    const double* V = M.leaf[side] + M.leaf_off[side][it.cluster];
+    const double* V = pick(M.leaf, side) + pick(M.leaf_off, side)[it.cluster];
     const double* F = (side == 0 ? A : B) + it.foff;
     if (lane < K)
       for (int i = 0; i < rows; ++i)
@@ -840,7 +854,7 @@ __global__ void k_truncate(MatView M, const Item* __restrict__ items, const int3
       const int ks = sn.k;
       const int rs = si == 0 ? r1 : r2;
       const double* Rt = IB.Rt + (size_t)sons[si] * kSlot;
-      const double* E = M.transfer[side] + (size_t)sn.cluster * kcap * kcap;   // ks x k
+      const double* E = pick(M.transfer, side) + (size_t)sn.cluster * kcap * kcap;   // ks x k
       if (lane < K)
         for (int p = 0; p < rs; ++p) {
           double v = 0.0;
@@ -1015,7 +1029,7 @@ __global__ void k_truncate(MatView M, const Item* __restrict__ items, const int3
   if ((it.flags & kItemRoot) && !(it.flags & kItemTreeRoot)) {
     // E_t0 <- R_t0 [E_t0; 0]  (r x kf)
     __syncwarp();
-    const double* E = M.transfer[side] + (size_t)it.cluster * kcap * kcap;   // k x kf
+    const double* E = pick(M.transfer, side) + (size_t)it.cluster * kcap * kcap;   // k x kf
     double* Fo = IB.F + (size_t)id * kSlot;
     if (lane < it.kf)
       for (int p = 0; p < r; ++p) {
@@ -1149,57 +1163,102 @@ static void launch_truncate(const MatView& M, const Item* items, const int32_t* 
 void run_pipeline(const Pipeline& P) {
   cudaStream_t st = P.stream;
   cudaStream_t bs = P.side ? P.side : P.stream;   // stream of the weights of the unchanged matrix
-  int64_t pl[H2_PHASE_COUNT] = {0, 0, 0, 0, 0, 0};
+  int64_t pl[H2_PHASE_COUNT] = {};
   auto start = [&](int ph, cudaStream_t s) {
     if (P.events) H2_CUDA(cudaEventRecord(P.events[2 * ph], s));
   };
   auto stop = [&](int ph, cudaStream_t s) {
     if (P.events) H2_CUDA(cudaEventRecord(P.events[2 * ph + 1], s));
   };
-  const int L = P.levels;
-  if (P.side) {
+  auto fork = [&]() {
+    if (!P.side) return;
     H2_CUDA(cudaEventRecord(P.fork, st));
     H2_CUDA(cudaStreamWaitEvent(P.side, P.fork, 0));
-  }
-  // weights of the unchanged matrix: block R-factors of every cluster in one
-  // launch, then the inherited part top-down, both sides per launch
-  start(H2_PHASE_BASE_WEIGHTS, bs);
+  };
+  const int L = P.levels;
+  const int ni = P.lvl_ptr[L];
   const int ncl = P.cl_ptr[L];
+  const bool gram = !P.exact_only;
+  // per-update path flags and per-cluster marks of the exact path
+  if (P.n_updates > 0) H2_CUDA(cudaMemsetAsync(P.IB.fail, gram ? 0 : 1, (size_t)P.n_updates * 4, st));
+  for (int sd = 0; sd < 2; ++sd)
+    if (P.ncl[sd] > 0) H2_CUDA(cudaMemsetAsync(P.BW.need[sd], gram ? 0 : 1, (size_t)P.ncl[sd] * 4, st));
+  if (gram) {
+    // certified Gram path: weights of the unchanged matrix on the side
+    // stream, overlapping the basis Grams and the norms
+    fork();
+    start(H2_PHASE_BASE_WEIGHTS, bs);
+    if (ncl > 0) {
+      launch_gram_base(P, bs);
+      ++pl[H2_PHASE_BASE_WEIGHTS];
+    }
+    for (int l = 0; l < L; ++l)
+      if (P.cl_ptr[l + 1] > P.cl_ptr[l]) {
+        launch_gram_base_level(P, l, bs);
+        ++pl[H2_PHASE_BASE_WEIGHTS];
+      }
+    stop(H2_PHASE_BASE_WEIGHTS, bs);
+    if (P.side) H2_CUDA(cudaEventRecord(P.join, P.side));
+    start(H2_PHASE_RFACTOR, st);
+    for (int l = L - 1; l >= 0; --l)
+      if (P.lvl_ptr[l + 1] > P.lvl_ptr[l]) {
+        launch_gram_basis(P, l);
+        ++pl[H2_PHASE_RFACTOR];
+      }
+    stop(H2_PHASE_RFACTOR, st);
+    start(H2_PHASE_NORMS, st);
+    if (P.n_norms > 0) {
+      launch_gram_norms(P);
+      ++pl[H2_PHASE_NORMS];
+    }
+    stop(H2_PHASE_NORMS, st);
+    if (P.side) H2_CUDA(cudaStreamWaitEvent(st, P.join, 0));
+    start(H2_PHASE_WEIGHTS, st);
+    for (int l = 0; l < L; ++l)
+      if (P.lvl_ptr[l + 1] > P.lvl_ptr[l]) {
+        launch_gram_weights(P, l);
+        ++pl[H2_PHASE_WEIGHTS];
+      }
+    stop(H2_PHASE_WEIGHTS, st);
+    start(H2_PHASE_TRUNCATE, st);
+    if (ni > 0) {
+      launch_gram_certify(P);
+      launch_gram_outputs(P);
+      pl[H2_PHASE_TRUNCATE] += 2;
+    }
+    stop(H2_PHASE_TRUNCATE, st);
+  }
+  // exact path for the updates whose certificate failed (every kernel returns
+  // at once for the tasks of the other updates and for unmarked clusters):
+  // weights of the unchanged matrix on the side stream, overlapping step 2,
+  // the norms and the outside folds of step 3
+  start(H2_PHASE_EXACT, st);
+  fork();
   if (ncl > 0) {
     k_blockweights<<<blocks_for(ncl), 32 * kWarps, kFoldSmem, bs>>>(P.M, P.cl_list, ncl, P.BL, P.BW, P.err);
-    ++pl[H2_PHASE_BASE_WEIGHTS];
+    ++pl[H2_PHASE_EXACT];
   }
   for (int l = 0; l < L; ++l) {
     const int n = P.cl_ptr[l + 1] - P.cl_ptr[l];
     if (!n) continue;
     k_baseweights<<<blocks_for(n), 32 * kWarps, kFoldSmem, bs>>>(P.M, P.cl_list + P.cl_ptr[l], n, P.BW, P.err);
-    ++pl[H2_PHASE_BASE_WEIGHTS];
+    ++pl[H2_PHASE_EXACT];
   }
-  stop(H2_PHASE_BASE_WEIGHTS, bs);
   if (P.side) H2_CUDA(cudaEventRecord(P.join, P.side));
-  // step 2: basis R-factors, bottom-up
-  start(H2_PHASE_RFACTOR, st);
   for (int l = L - 1; l >= 0; --l) {
     const int n = P.lvl_ptr[l + 1] - P.lvl_ptr[l];
     if (!n) continue;
     k_rfactor<<<blocks_for(n), 32 * kWarps, kFoldSmem, st>>>(P.M, P.items, P.lvl_list + P.lvl_ptr[l], n, P.u,
                                                               P.A, P.B, P.IB, P.err);
-    ++pl[H2_PHASE_RFACTOR];
+    ++pl[H2_PHASE_EXACT];
   }
-  stop(H2_PHASE_RFACTOR, st);
-  start(H2_PHASE_NORMS, st);
   if (P.n_norms > 0) {
     k_norms<<<blocks_for(P.n_norms), 32 * kWarps, 0, st>>>(P.M, P.items, P.norms, P.n_norms, P.u, P.IB);
-    ++pl[H2_PHASE_NORMS];
+    ++pl[H2_PHASE_EXACT];
   }
-  stop(H2_PHASE_NORMS, st);
-  // step 3: outside blocks of the tasks that need their own fold, then
-  // (after the weights of the unchanged matrix) the weights top-down
-  start(H2_PHASE_WEIGHTS, st);
-  const int ni = P.lvl_ptr[L];
   if (ni > 0) {
     k_outside<<<blocks_for(ni), 32 * kWarps, kFoldSmem, st>>>(P.M, P.items, P.ents, P.lvl_list, ni, P.u, P.IB);
-    ++pl[H2_PHASE_WEIGHTS];
+    ++pl[H2_PHASE_EXACT];
   }
   if (P.side) H2_CUDA(cudaStreamWaitEvent(st, P.join, 0));
   for (int l = 0; l < L; ++l) {
@@ -1207,19 +1266,16 @@ void run_pipeline(const Pipeline& P) {
     if (!n) continue;
     k_weights<<<blocks_for(n), 32 * kWarps, kFoldSmem, st>>>(P.M, P.items, P.ents, P.lvl_list + P.lvl_ptr[l], n,
                                                               P.u, P.BW, P.IB, P.err);
-    ++pl[H2_PHASE_WEIGHTS];
+    ++pl[H2_PHASE_EXACT];
   }
-  stop(H2_PHASE_WEIGHTS, st);
-  // step 4: truncation, bottom-up
-  start(H2_PHASE_TRUNCATE, st);
   for (int l = L - 1; l >= 0; --l) {
     const int n = P.lvl_ptr[l + 1] - P.lvl_ptr[l];
     if (!n) continue;
     launch_truncate(P.M, P.items, P.lvl_list + P.lvl_ptr[l], n, P.u, P.kl, P.lvl_rows[l], P.eps, P.A, P.B, P.IB,
                     P.err, st);
-    ++pl[H2_PHASE_TRUNCATE];
+    ++pl[H2_PHASE_EXACT];
   }
-  stop(H2_PHASE_TRUNCATE, st);
+  stop(H2_PHASE_EXACT, st);
   // step 5: reprojection
   start(H2_PHASE_REPROJECT, st);
   if (P.n_tasks > 0) {

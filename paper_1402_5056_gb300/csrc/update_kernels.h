@@ -47,6 +47,9 @@ struct Pipeline {
   const int32_t* cl_list;       // all clusters of both sides sorted by level (side << 30 | id)
   const int32_t* cl_ptr;        // host, levels + 1 entries
   int levels;
+  int n_updates;
+  int ncl[2];                   // clusters per side
+  int exact_only;               // 1: every update takes the exact path
   int n_tasks, n_norms;
   int u, kl;
   double eps;
@@ -64,8 +67,19 @@ struct Pipeline {
 };
 
 // Launch the whole update (weights of the unchanged matrix, steps 2-5) on
-// P.stream.
+// P.stream: the certified Gram path for every update, the exact path for the
+// updates whose certificate failed (all of them when P.exact_only), then the
+// reprojection.
 void run_pipeline(const Pipeline& P);
+
+// Certified Gram path (gram_kernels.cu).
+void launch_gram_base(const Pipeline& P, cudaStream_t st);               // Wo, all clusters
+void launch_gram_base_level(const Pipeline& P, int level, cudaStream_t st);  // W0, one level
+void launch_gram_basis(const Pipeline& P, int level);                    // G_t, one level
+void launch_gram_norms(const Pipeline& P);                               // ||Z~|_b||_F inside
+void launch_gram_weights(const Pipeline& P, int level);                  // W_t, one level
+void launch_gram_certify(const Pipeline& P);                             // certificate, R_t
+void launch_gram_outputs(const Pipeline& P);                             // new bases, marks
 void launch_copy(const CopyDesc* d, int n, cudaStream_t st);
 void launch_near_add(const NearDesc* d, int n, int u, cudaStream_t st);
 

@@ -20,6 +20,7 @@ constexpr int kErrRank = 8;      // inconsistent ranks
 
 // One cluster of one side of one update ("cluster task").
 struct Item {
+  int32_t update;      // index of the update in the batch
   int32_t side;        // 0 row basis V (factor A), 1 column basis W (factor B)
   int32_t cluster;
   int32_t parent;      // item of the father inside the subtree, -1 for the subtree root
@@ -74,6 +75,12 @@ struct MatView {
 struct BaseWeights {
   double* G[2];        // R-factor of the weighted blocks of row(t)/col(s), ld 32
   double* B[2];        // R-factor of the full weight stack B~_t, ld 32
+  // Gram matrices of the same stacks for the certified path (Wo = G^* G,
+  // W0 = B^* B).  They are dead once the certified path has finished and
+  // may share storage with G and B, which only the exact path writes.
+  double* Wo[2];
+  double* W0[2];
+  int32_t* need[2];    // per cluster: 1 if the exact path needs G and B of it
 };
 
 // Per-item workspace and outputs; every matrix slot is 32 x 32, ld 32.
@@ -86,6 +93,12 @@ struct ItemBuffers {
   int32_t* rank;       // new rank
   int32_t* own;        // 1 if the item folds its outside blocks itself (step 3)
   double* norms;       // per NormTask
+  // certified path: Gram matrices G_t = V~_t^* V~_t and W_t = B~_t^* B~_t.
+  // They are dead before the exact path runs and may share storage with Rq
+  // and Bw (the exact path only writes the tasks of updates that failed).
+  double* Gv;
+  double* Wg;
+  int32_t* fail;       // per update: 1 if the exact path computes it
   double* S_out;       // per Task, 32 x 32 slots
   unsigned long long* jac;   // per item: Jacobi pairs checked, rotations applied, 1 if the
                              // full-rank certificate held (no Jacobi), reserved (4 counters)

@@ -1,0 +1,187 @@
+"""The two paths of the CUDA update: certified Gram path and exact path.
+
+* Where the rank rule keeps every extended rank (eps = 1e-8, random
+  factors, admissible blocks) the certificate holds and the certified path
+  computes the update; where it truncates (heavy truncation at eps = 0.5,
+  clusters without weight) the exact path takes over.
+* Both modes (automatic selection, exact only) agree with the oracle on the
+  same batch, entry by entry on the assembled matrices, and with each other.
+* The new leaf bases of certified updates are orthonormal and span the
+  extended bases (V_t, A|_t).
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1402_5056_gb300 import binding as b  # noqa: E402
+
+from gpu_util import applied_delta, concat_factors  # noqa: E402
+from libside import lib_problem, to_oracle  # noqa: E402
+from oracle.tree import BlockTree  # noqa: E402
+from oracle.update import apply_delta, local_update  # noqa: E402
+from problems import draw_updates, oracle_problem  # noqa: E402
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = b.h2_ctx_create(0, torch.cuda.current_stream().cuda_stream)
+    yield c
+    b.h2_ctx_destroy(c)
+
+
+def _batch(ctx, Zl, blocks, A, B, u, eps, mode):
+    P = b.h2_batch_create(ctx, Zl, blocks, u)
+    b.h2_batch_set_mode(P, mode)
+    Acat, Bcat = concat_factors(P, A, B, u)
+    dA = torch.from_numpy(Acat).cuda()
+    dB = torch.from_numpy(Bcat).cuda()
+    torch.cuda.synchronize()
+    b.h2_batch_execute(ctx, P, dA.data_ptr(), dB.data_ptr(), eps)
+    b.h2_ctx_synchronize(ctx)
+    return P, dA, dB
+
+
+def _dense(ctx, Zl, Zo, P, j, dA, dB):
+    C = b.h2_matrix_clone(ctx, Zl)
+    try:
+        b.h2_batch_apply(ctx, P, j, dA.data_ptr(), dB.data_ptr(), C)
+        return to_oracle(ctx, C, Zo).dense()
+    finally:
+        b.h2_matrix_free(C)
+
+
+def _mixed(Zo, st, count, u, seed):
+    blocks, A, B = draw_updates(Zo, st, count, u)
+    bt = Zo.blocks
+    rng = np.random.default_rng(seed)
+    sub = [c for c in range(1, bt.n_blocks) if bt.kind[c] == BlockTree.SUB]
+    for c in (0, sub[len(sub) // 2], bt.inadmissible[len(bt.inadmissible) // 2]):
+        blocks.append(c)
+        A.append(rng.standard_normal((Zo.V.tree.size[bt.row[c]], u)))
+        B.append(rng.standard_normal((Zo.W.tree.size[bt.col[c]], u)))
+    return blocks, A, B
+
+
+def _keeps_extended_ranks(Zo, d, u):
+    return all(r == Zo.V.rank[t] + u for t, r in d["V"]["rank"].items()) and \
+        all(r == Zo.W.rank[t] + u for t, r in d["W"]["rank"].items())
+
+
+@pytest.mark.parametrize("N,leaf,k,u", [(24, 16, 6, 3), (32, 32, 8, 4)])
+def test_certified_path_without_truncation(ctx, N, leaf, k, u):
+    """eps = 1e-8: the updates of admissible blocks keep every extended rank
+    and take the certified path; updates of the root block and of large
+    inadmissible blocks truncate (clusters without admissible blocks have no
+    weight, so the rank rule drops their bases) and take the exact path."""
+    seed = 300 + N
+    Zo, st, _ = oracle_problem(N, k, seed, leaf)
+    blocks, A, B = _mixed(Zo, st, 8, u, seed)
+    Zl, _, _ = lib_problem(ctx, N, k, seed, leaf)
+    try:
+        P, dA, dB = _batch(ctx, Zl, blocks, A, B, u, 1e-8, b.MODE_AUTO)
+        try:
+            exact = b.h2_batch_paths(ctx, P, len(blocks))
+            assert exact[:8].sum() == 0, exact
+            ph = b.h2_batch_phase_stats(ctx, P, b.PHASES.index("truncate"))
+            assert ph["flops"] > 0
+            for j, b0 in enumerate(blocks):
+                d = local_update(Zo, b0, A[j], B[j], 1e-8)
+                full = _keeps_extended_ranks(Zo, d, u)
+                assert exact[j] == (0 if full else 1), (j, b0)
+                ref = apply_delta(Zo, d).dense()
+                got = _dense(ctx, Zl, Zo, P, j, dA, dB)
+                assert np.linalg.norm(got - ref) <= TOL * np.linalg.norm(ref), j
+        finally:
+            b.h2_batch_free(P)
+    finally:
+        b.h2_matrix_free(Zl)
+
+
+def test_truncation_falls_back_to_exact_path(ctx):
+    N, leaf, k, u, eps = 24, 16, 6, 3, 0.5
+    Zo, st, _ = oracle_problem(N, k, 311, leaf)
+    blocks, A, B = _mixed(Zo, st, 8, u, 311)
+    Zl, _, _ = lib_problem(ctx, N, k, 311, leaf)
+    try:
+        P, dA, dB = _batch(ctx, Zl, blocks, A, B, u, eps, b.MODE_AUTO)
+        try:
+            exact = b.h2_batch_paths(ctx, P, len(blocks))
+            truncating = []
+            for j, b0 in enumerate(blocks):
+                d = local_update(Zo, b0, A[j], B[j], eps)
+                full = _keeps_extended_ranks(Zo, d, u)
+                truncating.append(not full)
+                if not full:
+                    # the certificate cannot hold where the rank rule truncates
+                    assert exact[j] == 1, j
+                ref = apply_delta(Zo, d).dense()
+                got = _dense(ctx, Zl, Zo, P, j, dA, dB)
+                assert np.linalg.norm(got - ref) <= TOL * np.linalg.norm(ref), j
+            assert any(truncating)
+            assert b.h2_batch_phase_stats(ctx, P, b.PHASES.index("exact"))["flops"] > 0
+        finally:
+            b.h2_batch_free(P)
+    finally:
+        b.h2_matrix_free(Zl)
+
+
+@pytest.mark.parametrize("eps", [1e-8, 0.5])
+def test_modes_agree_with_oracle_and_each_other(ctx, eps):
+    N, leaf, k, u = 32, 16, 6, 4
+    Zo, st, _ = oracle_problem(N, k, 321, leaf)
+    blocks, A, B = _mixed(Zo, st, 6, u, 321)
+    Zl, _, _ = lib_problem(ctx, N, k, 321, leaf)
+    try:
+        refs = [apply_delta(Zo, local_update(Zo, b0, A[j], B[j], eps)).dense() for j, b0 in enumerate(blocks)]
+        got = {}
+        for mode in (b.MODE_AUTO, b.MODE_EXACT):
+            P, dA, dB = _batch(ctx, Zl, blocks, A, B, u, eps, mode)
+            try:
+                if mode == b.MODE_EXACT:
+                    assert b.h2_batch_paths(ctx, P, len(blocks)).sum() == len(blocks)
+                got[mode] = [_dense(ctx, Zl, Zo, P, j, dA, dB) for j in range(len(blocks))]
+            finally:
+                b.h2_batch_free(P)
+        for j, ref in enumerate(refs):
+            nr = np.linalg.norm(ref)
+            for mode in got:
+                assert np.linalg.norm(got[mode][j] - ref) <= TOL * nr, (mode, j)
+            assert np.linalg.norm(got[b.MODE_AUTO][j] - got[b.MODE_EXACT][j]) <= TOL * nr, j
+    finally:
+        b.h2_matrix_free(Zl)
+
+
+def test_certified_leaf_bases_orthonormal_and_spanning(ctx):
+    N, leaf, k, u = 32, 32, 8, 4
+    Zo, st, _ = oracle_problem(N, k, 331, leaf)
+    blocks, A, B = draw_updates(Zo, st, 6, u)
+    Zl, _, _ = lib_problem(ctx, N, k, 331, leaf)
+    try:
+        P, dA, dB = _batch(ctx, Zl, blocks, A, B, u, 1e-8, b.MODE_AUTO)
+        try:
+            assert b.h2_batch_paths(ctx, P, len(blocks)).sum() == 0
+            for j, b0 in enumerate(blocks):
+                got_m, _, _ = applied_delta(ctx, Zl, P, j, dA, dB, Zo, b0)
+                t0 = Zo.blocks.row[b0]
+                r0 = Zo.V.tree.offset[t0]
+                for t in Zo.V.tree.descendants(t0):
+                    if not Zo.V.tree.is_leaf(t):
+                        continue
+                    Q = got_m.V.leaf[t]
+                    np.testing.assert_allclose(Q.T @ Q, np.eye(Q.shape[1]), atol=1e-13)
+                    off = Zo.V.tree.offset[t] - r0
+                    Vt = np.hstack([Zo.V.leaf[t], A[j][off:off + Zo.V.tree.size[t]]])
+                    # range(Q) = range(V~_t): the residual of projecting V~_t on Q
+                    res = Vt - Q @ (Q.T @ Vt)
+                    assert np.linalg.norm(res) <= 1e-12 * np.linalg.norm(Vt)
+        finally:
+            b.h2_batch_free(P)
+    finally:
+        b.h2_matrix_free(Zl)

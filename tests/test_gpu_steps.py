@@ -5,7 +5,8 @@ compared with the oracle's trace: the Gram matrices R^* R of the basis
 R-factors (step 2), B~^* B~ of the weights (step 3), the new rank and
 R_t^* R_t of the basis-change matrices (step 4).  The check runs along a
 chain of in-place updates with heavy truncation, where ranks differ from
-cluster to cluster and ancestor bases have been changed by earlier commits.
+cluster to cluster and ancestor bases have been changed by earlier commits,
+in both path modes (certified Gram path with exact fallback, exact only).
 """
 import numpy as np
 import pytest
@@ -31,7 +32,11 @@ def ctx():
 
 
 def _gram_close(X, Y, tol, what):
-    G1, G2 = X.T @ X, Y.T @ Y
+    _sym_close(X.T @ X, Y, tol, what)
+
+
+def _sym_close(G1, Y, tol, what):
+    G2 = Y.T @ Y
     scale = max(1.0, float(np.abs(G2).max()))
     err = float(np.abs(G1 - G2).max()) / scale
     assert err <= tol, (what, err)
@@ -46,10 +51,10 @@ def _check_items(ctx, P, Zs, b0, A, B, u, eps):
         c, k = info["cluster"], info["k"]
         K = k + u
         side = "V" if info["side"] == 0 else "W"
-        Rq = b.h2_batch_item_tile(ctx, P, item, 0)[:K, :K]
-        _gram_close(Rq, tr["R" + side][c], 1e-12, ("R-factor", side, c))
-        Bw = b.h2_batch_item_tile(ctx, P, item, 1)[:K, :K]
-        _gram_close(Bw, tr["B" + side][c], 1e-11, ("weights", side, c))
+        Gq = b.h2_batch_item_tile(ctx, P, item, 0)[:K, :K]
+        _sym_close(Gq, tr["R" + side][c], 1e-12, ("R-factor", side, c))
+        Gw = b.h2_batch_item_tile(ctx, P, item, 1)[:K, :K]
+        _sym_close(Gw, tr["B" + side][c], 1e-11, ("weights", side, c))
         r = info["rank"]
         if d["margin"] >= 1e-6:
             assert r == d[side]["rank"][c], ("rank", side, c, r, d[side]["rank"][c])
@@ -59,8 +64,9 @@ def _check_items(ctx, P, Zs, b0, A, B, u, eps):
     return d
 
 
+@pytest.mark.parametrize("mode", [b.MODE_AUTO, b.MODE_EXACT])
 @pytest.mark.parametrize("eps", [0.5, 2.0, 1e-8])
-def test_chain_intermediates_match_oracle(ctx, eps):
+def test_chain_intermediates_match_oracle(ctx, eps, mode):
     N, leaf, k, u = 24, 16, 5, 3
     Zo, st, _ = oracle_problem(N, k, 21, leaf)
     blocks, A, B = draw_updates(Zo, st, 6, u)
@@ -72,6 +78,7 @@ def test_chain_intermediates_match_oracle(ctx, eps):
         for j, b0 in enumerate(blocks):
             Zs = to_oracle(ctx, Zl, Zo)
             P = b.h2_batch_create(ctx, Zl, [b0], u)
+            b.h2_batch_set_mode(P, mode)
             try:
                 dA = torch.from_numpy(np.asfortranarray(A[j]).ravel(order="F")).cuda()
                 dB = torch.from_numpy(np.asfortranarray(B[j]).ravel(order="F")).cuda()
