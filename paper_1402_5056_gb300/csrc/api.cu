@@ -123,6 +123,8 @@ MatView view_of(const h2_matrix* Z) {
   M.father[1] = Z->d_father_c;
   M.subtree[0] = Z->d_subtree_r;
   M.subtree[1] = Z->d_subtree_c;
+  M.size[0] = Z->d_row_size;
+  M.size[1] = Z->d_col_size;
   M.S = Z->d_S;
   M.kcap = Z->kcap;
   return M;
@@ -717,6 +719,8 @@ struct h2_batch {
   cudaEvent_t ev[2 * H2_PHASE_COUNT] = {};   // start and end of every phase
   cudaStream_t side = nullptr;               // stream of the weights of the unchanged matrix
   cudaEvent_t fork = nullptr, join = nullptr;
+  cudaStream_t side2 = nullptr;              // stream of the basis Grams of the unchanged matrix
+  cudaEvent_t join2 = nullptr;
 };
 
 namespace {
@@ -895,6 +899,8 @@ void alloc_batch(h2_ctx* ctx, h2_batch& P) {
   H2_CUDA(cudaStreamCreateWithFlags(&P.side, cudaStreamNonBlocking));
   H2_CUDA(cudaEventCreateWithFlags(&P.fork, cudaEventDisableTiming));
   H2_CUDA(cudaEventCreateWithFlags(&P.join, cudaEventDisableTiming));
+  H2_CUDA(cudaStreamCreateWithFlags(&P.side2, cudaStreamNonBlocking));
+  H2_CUDA(cudaEventCreateWithFlags(&P.join2, cudaEventDisableTiming));
   P.d_items = upload(P.items, st);
   P.d_ents = upload(P.ents, st);
   P.d_tasks = upload(P.tasks, st);
@@ -925,12 +931,19 @@ void alloc_batch(h2_ctx* ctx, h2_batch& P) {
     P.BW.Wo[sd] = P.BW.G[sd];
     P.BW.W0[sd] = P.BW.B[sd];
     P.BW.need[sd] = dalloc<int32_t>(ncl[sd]);
+    P.BW.Vg[sd] = dalloc<double>((size_t)ncl[sd] * kSlot);
+    P.BW.orth[sd] = dalloc<int32_t>(ncl[sd]);
   }
   H2_CUDA(cudaStreamSynchronize(st));
 }
 
 void free_batch_device(h2_batch& P) {
   if (P.side) cudaStreamSynchronize(P.side);
+  if (P.side2) cudaStreamSynchronize(P.side2);
+  if (P.join2) cudaEventDestroy(P.join2);
+  if (P.side2) cudaStreamDestroy(P.side2);
+  P.join2 = nullptr;
+  P.side2 = nullptr;
   if (P.fork) cudaEventDestroy(P.fork);
   if (P.join) cudaEventDestroy(P.join);
   if (P.side) cudaStreamDestroy(P.side);
@@ -946,6 +959,8 @@ void free_batch_device(h2_batch& P) {
     dfree(P.BW.G[sd]);
     dfree(P.BW.B[sd]);
     dfree(P.BW.need[sd]);
+    dfree(P.BW.Vg[sd]);
+    dfree(P.BW.orth[sd]);
     P.BW.Wo[sd] = P.BW.W0[sd] = nullptr;
   }
   dfree(P.IB.Rq);
@@ -1006,6 +1021,8 @@ void execute(h2_ctx* ctx, h2_batch& P, const double* A, const double* B, double 
   pp.side = P.side;
   pp.fork = P.fork;
   pp.join = P.join;
+  pp.side2 = P.side2;
+  pp.join2 = P.join2;
   pp.events = P.timing ? P.ev : nullptr;
   pp.phase_launches = P.phase_launches;
   run_pipeline(pp);
@@ -1272,8 +1289,15 @@ void phase_flops(h2_ctx* ctx, const h2_batch* P, double f[H2_PHASE_COUNT]) {
   if (P->count)
     H2_CUDA(cudaMemcpyAsync(fail.data(), P->IB.fail, P->count * sizeof(int32_t), cudaMemcpyDeviceToHost,
                             ctx->stream));
-  H2_CUDA(cudaStreamSynchronize(ctx->stream));
+  std::vector<int32_t> orth[2];
   const bool gram = P->mode != H2_MODE_EXACT;
+  for (int sd = 0; sd < 2; ++sd) {
+    orth[sd].assign(tree_of(P->Z, sd).count(), 0);
+    if (gram && !orth[sd].empty())
+      H2_CUDA(cudaMemcpyAsync(orth[sd].data(), P->BW.orth[sd], orth[sd].size() * sizeof(int32_t),
+                              cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  H2_CUDA(cudaStreamSynchronize(ctx->stream));
   const double u = P->u;
   auto qr = [](double m, double n) {
     return m >= n ? 2 * m * n * n - 2.0 / 3.0 * n * n * n : 2 * n * m * m - 2.0 / 3.0 * m * m * m;
@@ -1305,6 +1329,17 @@ void phase_flops(h2_ctx* ctx, const h2_batch* P, double f[H2_PHASE_COUNT]) {
     const std::vector<int32_t>& adm = sd == 0 ? Z->blocks.row_adm : Z->blocks.col_adm;
     for (int32_t c = 0; c < ct.count(); ++c) {
       const double k = bs.rank[c];
+      if (gram) {
+        // V_c^* V_c
+        if (ct.leaf(c)) {
+          f[H2_PHASE_BASE_WEIGHTS] += 2 * tri(k) * (double)ct.size[c];
+        } else {
+          for (int32_t sn : {ct.son0[c], ct.son1[c]}) {
+            const double ks = bs.rank[sn];
+            f[H2_PHASE_BASE_WEIGHTS] += 2 * ks * ks * k + 2 * tri(k) * ks;
+          }
+        }
+      }
       for (int32_t e = ptr[c]; e < ptr[c + 1]; ++e) {
         const int32_t blk = Z->blocks.adm[adm[e]];
         const double l = o.rank[sd == 0 ? Z->blocks.col[blk] : Z->blocks.row[blk]];
@@ -1332,24 +1367,24 @@ void phase_flops(h2_ctx* ctx, const h2_batch* P, double f[H2_PHASE_COUNT]) {
     const bool troot = it.flags & kItemTreeRoot;
     const double kf = it.kf;
     if (gram) {
-      // step 2: basis Gram matrices
+      // step 2: C_t and N_t of the basis Gram matrices
       if (leaf) {
-        f[H2_PHASE_RFACTOR] += 2 * tri(K) * it.size;
+        f[H2_PHASE_RFACTOR] += 2 * (k * u + tri(u)) * it.size;
       } else {
         for (int32_t sid : {it.son0, it.son1}) {
           const double ks = P->items[sid].k;
-          f[H2_PHASE_RFACTOR] += 2 * (ks + u) * k * ks + 2 * tri(k) * ks + (tri(K) - tri(k));
+          f[H2_PHASE_RFACTOR] += 2 * k * u * ks + tri(u);
         }
       }
       // step 3: weight Gram matrices (jac[3] = 1: V_t not orthonormal)
-      const bool orth = jac[4 * i + 3] == 0;
+      const bool orth_w = jac[4 * i + 3] == 0;
       for (int32_t e = it.ent_begin; e < it.ent_end; ++e) {
         const Entry& en = P->ents[e];
         const double l = basis_of(Z, 1 - it.side).rank[en.other_cluster];
         if (en.other >= 0) {
-          if (orth) f[H2_PHASE_WEIGHTS] += 2 * k * l + 2 * tri(k) * l + 2 * tri(k);
+          if (orth_w) f[H2_PHASE_WEIGHTS] += 2 * k * l + 2 * tri(k) * l + 2 * tri(k);
           f[H2_PHASE_WEIGHTS] += 2 * k * (l + u) * l + 2 * (k * K - tri(k - 1)) * l + 2 * tri(K);
-        } else if (!orth) {
+        } else if (!orth_w) {
           f[H2_PHASE_WEIGHTS] += 2 * k * k * l + 2 * k * l + 2 * tri(k) * l + 2 * tri(k);
         }
       }
@@ -1358,13 +1393,26 @@ void phase_flops(h2_ctx* ctx, const h2_batch* P, double f[H2_PHASE_COUNT]) {
       } else if (!root) {
         f[H2_PHASE_WEIGHTS] += 2 * k * (kf + u) * kf + 2 * (k * K - tri(k - 1)) * kf;
       }
-      // step 4: certificate (two LDL^*, W L_G, L_G^* (W L_G)) and new bases
-      f[H2_PHASE_TRUNCATE] += 2 * ldl(K) + 2 * K * tri(K) + (K * K * K + 3 * K * K + 2 * K) / 3;
+      // step 4: certificate (LDL^* of G_t, W L, L^* (W L), LDL^* of the
+      // certificate matrix) and new bases; block formulas for an orthonormal V_t
+      const bool ob = orth[it.side][it.cluster] != 0;
+      if (ob) {
+        double c2 = 2 * tri(k) * u;
+        for (double a = 0; a < u; a += 1) c2 += 2 * (k + a + 1) * (u - a);
+        f[H2_PHASE_TRUNCATE] += 2 * tri(u) * k + ldl(u) + 2 * K * k * u + 2 * K * tri(u) + c2 + ldl(K);
+      } else {
+        f[H2_PHASE_TRUNCATE] += 2 * ldl(K) + 2 * K * tri(K) + (K * K * K + 3 * K * K + 2 * K) / 3;
+      }
       if (!fail[it.update]) {
-        if (leaf) f[H2_PHASE_TRUNCATE] += (double)it.size * K * K;
-        if (!troot) {
-          f[H2_PHASE_TRUNCATE] += 2 * tri(k) * kf;
-          if (!root) f[H2_PHASE_TRUNCATE] += K * (kf + u) * (kf + u);
+        if (leaf) f[H2_PHASE_TRUNCATE] += ob ? 2.0 * it.size * (k * u + tri(u)) : (double)it.size * K * K;
+        if (!troot && !(root && ob)) {
+          const bool op = orth[it.side][tree_of(Z, it.side).father[it.cluster]] != 0;
+          if (root)
+            f[H2_PHASE_TRUNCATE] += 2 * tri(k) * kf;
+          else if (ob && op)
+            f[H2_PHASE_TRUNCATE] += 2 * k * kf * u + K * u * u;
+          else
+            f[H2_PHASE_TRUNCATE] += 2 * tri(k) * kf + K * (kf + u) * (kf + u);
         }
       }
     }
@@ -1417,12 +1465,25 @@ void phase_flops(h2_ctx* ctx, const h2_batch* P, double f[H2_PHASE_COUNT]) {
     f[H2_PHASE_EXACT] += ft;
   }
   for (const Task& tk : P->tasks) {
+    const double kt = tk.kt, ls = tk.ls;
+    if (!fail[P->items[tk.it >= 0 ? tk.it : tk.is].update]) {
+      // certified update: R_t = L_t^* upper triangular, products over the
+      // triangle; one-sided blocks of an orthonormal basis are copies
+      if (tk.it >= 0 && tk.is >= 0) {
+        f[H2_PHASE_REPROJECT] += 2.0 * kt * tri(ls) + 2.0 * tri(kt + u) * (ls + u);
+      } else if (tk.it >= 0) {
+        if (!orth[0][P->items[tk.it].cluster]) f[H2_PHASE_REPROJECT] += 2.0 * tri(kt) * ls;
+      } else {
+        if (!orth[1][P->items[tk.is].cluster]) f[H2_PHASE_REPROJECT] += 2.0 * kt * tri(ls);
+      }
+      continue;
+    }
     if (tk.it >= 0 && tk.is >= 0)
-      f[H2_PHASE_REPROJECT] += 2.0 * (tk.kt + u) * tk.ls * rk[tk.is] + 2.0 * rk[tk.it] * (tk.kt + u) * rk[tk.is];
+      f[H2_PHASE_REPROJECT] += 2.0 * (kt + u) * ls * rk[tk.is] + 2.0 * rk[tk.it] * (kt + u) * rk[tk.is];
     else if (tk.it >= 0)
-      f[H2_PHASE_REPROJECT] += 2.0 * rk[tk.it] * tk.kt * tk.ls;
+      f[H2_PHASE_REPROJECT] += 2.0 * rk[tk.it] * kt * ls;
     else
-      f[H2_PHASE_REPROJECT] += 2.0 * tk.kt * tk.ls * rk[tk.is];
+      f[H2_PHASE_REPROJECT] += 2.0 * kt * ls * rk[tk.is];
   }
 }
 
@@ -1539,8 +1600,20 @@ extern "C" h2_status h2_batch_item_tile(h2_ctx* ctx, const h2_batch* P, int64_t 
     std::vector<double> tile(kSlot);
     H2_CUDA(cudaMemcpyAsync(tile.data(), src, kSlot * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     H2_CUDA(cudaStreamSynchronize(ctx->stream));
-    if (which == 2 || !exact) {
+    if (which == 2 || (which == 1 && !exact)) {
       std::copy(tile.begin(), tile.end(), out);
+      return;
+    }
+    if (!exact) {
+      // basis Gram: the V_t^* V_t block comes from the unchanged basis
+      std::vector<double> vg(kSlot);
+      H2_CUDA(cudaMemcpyAsync(vg.data(), P->BW.Vg[it.side] + (size_t)it.cluster * kSlot, kSlot * sizeof(double),
+                              cudaMemcpyDeviceToHost, ctx->stream));
+      H2_CUDA(cudaStreamSynchronize(ctx->stream));
+      const int K = it.k + P->u;
+      for (int j = 0; j < 32; ++j)
+        for (int i = 0; i < 32; ++i)
+          out[i + j * 32] = (i >= K || j >= K) ? 0.0 : (i < it.k && j < it.k) ? vg[i + j * 32] : tile[i + j * 32];
       return;
     }
     const int K = it.k + P->u;

@@ -4,11 +4,12 @@
 // rank K_t = k_t + u -- every singular value of V^_t B~_t^* above the
 // threshold of the rank rule -- the new basis of t spans range(V~_t), and
 // every quantity of steps 2-4 follows from K_t x K_t Gram matrices:
-//   G_t = V~_t^* V~_t = R_t^* R_t  (leaf: Gram of (V_t, A|_t); inner: sum over
-//                                   the sons of E~_s^* G_s E~_s)
+//   G_t = V~_t^* V~_t = R_t^* R_t = [[V_t^* V_t, C_t], [C_t^*, N_t]],
+//         C_t = V_t^* A|_t, N_t = A|_t^* A|_t  (inner clusters: C_t = sum over
+//         the sons of E_s^* C_s, N_t = sum of N_s)
 //   ||Z~|_b||_F^2 = tr(S~_b^* G_t S~_b G_s)
-//   W_t = B~_t^* B~_t             (sum of omega_b^2 S~_b G_s S~_b^* over
-//                                   row(t), plus E~_t W_{t+} E~_t^*)
+//   W_t = B~_t^* B~_t  (sum of omega_b^2 S~_b G_s S~_b^* over row(t), plus
+//                       E~_t W_{t+} E~_t^*)
 //   sigma_i(V^_t B~_t^*)^2 = lambda_i(G_t W_t) = lambda_i(L^* W_t L), G_t = L L^*.
 // The certificate is an LDL^* factorisation of L^* W_t L - (tau + delta) I
 // with positive pivots, tau = (eps/2)^2 the threshold of the rank rule and
@@ -17,11 +18,18 @@
 // range(V~_t) gives the same projection as the singular vectors; the path
 // takes Q_t = V~_t L^{-*} (orthonormal: Q_t^* Q_t = L^{-1} G_t L^{-*} = I),
 // R_t = Q_t^* V~_t = L^*, new transfer matrices L_s^* E~_s L_t^{-*} and the
-// commit E_t0 <- L_t0^* [E_t0; 0].  An update for which any cluster fails the
-// certificate is recomputed by the exact path (Householder R-factors and a
-// one-sided Jacobi SVD).
+// commit E_t0 <- L_t0^* [E_t0; 0].  An update for which any cluster fails
+// the certificate is recomputed by the exact path (Householder R-factors
+// and a one-sided Jacobi SVD).
 //
-// Execution model: one warp per cluster (or block) task, K x K tiles in
+// Orthonormal bases (V_t^* V_t = I, the normal case) make L block
+// triangular: L = [[I, 0], [C_t^*, L_S]] with L_S L_S^* = N_t - C_t^* C_t, so
+// the new basis is (V_t, (A|_t - V_t C_t) L_S^{-*}): the old basis is kept
+// and extended by the orthonormalised new directions, the factorisation of
+// G_t shrinks to u x u, and R_t [S_b; 0] = [S_b; 0] turns the one-sided
+// reprojections into copies.
+//
+// Execution model: one warp per cluster (or block) task, small tiles in
 // shared memory, and every matrix product spread over all 32 lanes (lane
 // takes entries lane, lane + 32, ... of the result), so that float64
 // instructions run with full lanes; symmetric results are computed on their
@@ -37,6 +45,7 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kLd = 33;     // leading dimension of the shared tiles (up to 32 rows)
 constexpr int kNS = 17;     // lower-triangle entries of a 32 x 32 matrix per lane: ceil(528 / 32)
+constexpr double kOrthTol = 1e-13;   // |V_t^* V_t - I| entrywise for an orthonormal basis
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -76,25 +85,46 @@ __device__ __forceinline__ double recip(double d) {
   return fma(y, e, y);
 }
 
-// rows x cols block of a column-major global matrix (ld gld) into a tile.
-__device__ __forceinline__ void load_tile(double* T, const double* g, int gld, int rows, int cols, int lane) {
-  for (int c = 0; c < cols; ++c)
-    for (int r = lane; r < rows; r += 32) T[r + c * kLd] = g[r + (size_t)c * gld];
+// The same with one quadratic step only: relative error below 2^-43, used
+// where the result only decides the certificate (its rounding is inside
+// delta).
+__device__ __forceinline__ double recip_coarse(double d) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(d));
+  const double e = fma(-d, y, 1.0);
+  return fma(y, e, y);
 }
 
-// In-place LDL^* of A - shift I (lower triangle of the n x n tile A): on
-// return the unit lower factor is below the diagonal and D on it.  lv holds
-// 32 doubles of shared scratch.  Returns false (on every lane) as soon as a
-// pivot is not positive.
-__device__ __forceinline__ bool ldl(double* A, int n, double shift, double* lv, int lane) {
-  if (lane < n) A[lane * (kLd + 1)] -= shift;
+// rows x cols block (rows <= 32, lane = row) of a column-major global matrix
+// (ld gld) into a tile (ld ld); eight columns' loads are issued before their
+// stores, so that a column does not wait for the previous one.
+__device__ __forceinline__ void load_tile(double* T, int ld, const double* g, int gld, int rows, int cols,
+                                          int lane) {
+  const bool act = lane < rows;
+  for (int c0 = 0; c0 < cols; c0 += 8) {
+    double v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = (act && c0 + j < cols) ? g[lane + (size_t)(c0 + j) * gld] : 0.0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (act && c0 + j < cols) T[lane + (c0 + j) * ld] = v[j];
+  }
+}
+
+// In-place LDL^* of A - shift I (lower triangle of the n x n tile A, ld ld):
+// on return the unit lower factor is below the diagonal and D on it.  lv
+// holds 32 doubles of shared scratch.  Returns whether every pivot was
+// positive (the same on every lane); the pivots are tested at the end, a
+// failed factorisation only produces values nobody reads.
+template <bool kPrecise>
+__device__ __forceinline__ bool ldl(double* A, int ld, int n, double shift, double* lv, int lane) {
+  if (lane < n) A[lane * (ld + 1)] -= shift;
   __syncwarp();
   for (int j = 0; j < n; ++j) {
-    const double d = A[j + j * kLd];
-    if (!(d > 1e-300)) return false;
-    const double r = recip(d);
+    const double d = A[j + j * ld];
+    const double r = kPrecise ? recip(d) : recip_coarse(d);
     const int m = n - j - 1;
-    if (lane < m) lv[lane] = A[j + 1 + lane + j * kLd] * r;
+    if (lane < m) lv[lane] = A[j + 1 + lane + j * ld] * r;
     __syncwarp();
     // trailing update A[p][q] -= a_pj l_qj for p >= q > j
     const int nt = tri(m);
@@ -102,13 +132,26 @@ __device__ __forceinline__ bool ldl(double* A, int n, double shift, double* lv, 
       int a, b;
       tri_index(e, a, b);
       const int p = j + 1 + a, q = j + 1 + b;
-      A[p + q * kLd] = fma(-A[p + j * kLd], lv[b], A[p + q * kLd]);
+      A[p + q * ld] = fma(-A[p + j * ld], lv[b], A[p + q * ld]);
     }
     __syncwarp();
-    if (lane < m) A[j + 1 + lane + j * kLd] = lv[lane];
+    if (lane < m) A[j + 1 + lane + j * ld] = lv[lane];
     __syncwarp();
   }
-  return true;
+  const bool ok = lane >= n || A[lane * (ld + 1)] > 1e-300;
+  return __all_sync(kFull, ok);
+}
+
+// The factor L D^{1/2} of a successful ldl in place (lower triangle).
+__device__ __forceinline__ void ldl_to_cholesky(double* A, int ld, int n, double* dsq, int lane) {
+  if (lane < n) dsq[lane] = sqrt(A[lane * (ld + 1)]);
+  __syncwarp();
+  for (int e = lane; e < tri(n); e += 32) {
+    int i, j;
+    tri_index(e, i, j);
+    A[i + j * ld] = i == j ? dsq[j] : A[i + j * ld] * dsq[j];
+  }
+  __syncwarp();
 }
 
 // Rows of the outside-block stack of one block: X[r][q] = S_b[q][r] on the
@@ -116,11 +159,17 @@ __device__ __forceinline__ bool ldl(double* A, int n, double shift, double* lv, 
 __device__ __forceinline__ void load_block_rows(double* X, const double* S, int kcap, int side, int l, int k,
                                                 int lane) {
   if (side == 0) {
-    for (int r = 0; r < l; ++r)
-      if (lane < k) X[r + lane * kLd] = S[lane + (size_t)r * kcap];
+    // X = S_b^*: lane q reads row q of S_b, column by column (8 at a time)
+    for (int r0 = 0; r0 < l; r0 += 8) {
+      double v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = (lane < k && r0 + j < l) ? S[lane + (size_t)(r0 + j) * kcap] : 0.0;
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (lane < k && r0 + j < l) X[(r0 + j) + lane * kLd] = v[j];
+    }
   } else {
-    for (int q = 0; q < k; ++q)
-      if (lane < l) X[lane + q * kLd] = S[lane + (size_t)q * kcap];
+    load_tile(X, kLd, S, kcap, l, k, lane);
   }
 }
 
@@ -168,7 +217,111 @@ __device__ __forceinline__ void store_sym(double* G, const double (&acc)[kNS], i
   }
 }
 
-// ------------------------------------------------- weights of the unchanged matrix
+// G_t (K x K) of a cluster task into a tile: the V_t^* V_t block from the
+// unchanged basis (the identity when V_t is orthonormal), C_t and N_t from
+// the task's slot.
+__device__ __forceinline__ void load_gram(double* T, int ld, const double* Gv, const double* Vg, bool orth, int k,
+                                          int K, int lane) {
+  const int r = lane;
+  for (int c0 = 0; c0 < K; c0 += 8) {
+    double v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int c = c0 + j;
+      double x = 0.0;
+      if (r < K && c < K) {
+        if (r < k && c < k)
+          x = orth ? (r == c ? 1.0 : 0.0) : Vg[r + c * 32];
+        else
+          x = Gv[r + c * 32];
+      }
+      v[j] = x;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (r < K && c0 + j < K) T[r + (c0 + j) * ld] = v[j];
+  }
+}
+
+// ------------------------------------------------- the unchanged matrix
+// Vg_c = V_c^* V_c for every cluster of both sides, bottom-up (one launch
+// per level): leaf Gram of V_c, inner sum over the sons of E_s^* Vg_s E_s;
+// orth_c = 1 when Vg_c = I within kOrthTol.
+__global__ void k_vgram(MatView M, const int32_t* __restrict__ list, int n, BaseWeights BW) {
+  extern __shared__ double smem[];
+  const int lane = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5;
+  const int idx = blockIdx.x * (blockDim.x >> 5) + w;
+  if (idx >= n) return;
+  const int kcap = M.kcap;
+  double* T0 = smem + (size_t)w * 3 * kLd * kcap;
+  double* T1 = T0 + kLd * kcap;
+  double* T2 = T1 + kLd * kcap;
+  const int side = list[idx] >> 30;
+  const int c = list[idx] & 0x3fffffff;
+  const int32_t* rank = pick(M.rank, side);
+  const int32_t* subtree = pick(M.subtree, side);
+  const int k = rank[c];
+  if (k > 32) return;
+  const int nt = tri(k);
+  double acc[kNS];
+#pragma unroll
+  for (int s = 0; s < kNS; ++s) acc[s] = 0.0;
+  if (subtree[c] == 1) {
+    const double* V = pick(M.leaf, side) + pick(M.leaf_off, side)[c];
+    const int m = pick(M.size, side)[c];
+    for (int r0 = 0; r0 < m; r0 += 32) {
+      const int ch = min(32, m - r0);
+      load_tile(T0, kLd, V + r0, m, ch, k, lane);
+      __syncwarp();
+      acc_gram(acc, T0, ch, k, 1.0, lane);
+      __syncwarp();
+    }
+  } else {
+    for (int si = 0; si < 2; ++si) {
+      const int s = si == 0 ? c + 1 : c + 1 + subtree[c + 1];
+      const int ks = rank[s];
+      load_tile(T0, kLd, pick(BW.Vg, side) + (size_t)s * kSlot, 32, ks, ks, lane);
+      load_tile(T1, kLd, pick(M.transfer, side) + (size_t)s * kcap * kcap, kcap, ks, k, lane);
+      __syncwarp();
+      // T2 = Vg_s E_s (ks x k)
+      for (int e = lane; e < ks * k; e += 32) {
+        const int i = e % ks, j = e / ks;
+        double v = 0.0;
+        for (int q = 0; q < ks; ++q) v = fma(T0[i + q * kLd], T1[q + j * kLd], v);
+        T2[i + j * kLd] = v;
+      }
+      __syncwarp();
+#pragma unroll
+      for (int s2 = 0; s2 < kNS; ++s2) {
+        if (32 * s2 >= nt) break;
+        const int e = lane + 32 * s2;
+        if (e < nt) {
+          int i, j;
+          tri_index(e, i, j);
+          double v = acc[s2];
+          for (int q = 0; q < ks; ++q) v = fma(T1[q + i * kLd], T2[q + j * kLd], v);
+          acc[s2] = v;
+        }
+      }
+      __syncwarp();
+    }
+  }
+  store_sym(pick(BW.Vg, side) + (size_t)c * kSlot, acc, k, lane);
+  bool orth = true;
+#pragma unroll
+  for (int s = 0; s < kNS; ++s) {
+    const int e = lane + 32 * s;
+    if (e < nt) {
+      int i, j;
+      tri_index(e, i, j);
+      if (!(fabs(acc[s] - (i == j ? 1.0 : 0.0)) <= kOrthTol)) orth = false;
+    }
+  }
+  orth = __all_sync(kFull, orth);
+  if (lane == 0) pick(BW.orth, side)[c] = orth ? 1 : 0;
+}
+
 // Wo_c = sum over b in row(c) of omega_b^2 S_b S_b^* (column side S_b^* S_b),
 // omega_b = sqrt(#T_c) / ||S_b||_F, for every cluster of both sides; the
 // Gram of the stack whose R-factor the exact path folds.
@@ -189,12 +342,15 @@ __global__ void k_bgram(MatView M, const int32_t* __restrict__ list, int n, Bloc
     return;
   }
   const double st = (double)pick(M.subtree, side)[c];
+  const int32_t* orank = pick(M.rank, 1 - side);
+  const int32_t* other = pick(BL.other, side);
+  const int32_t* adm = pick(BL.adm, side);
   double acc[kNS];
 #pragma unroll
   for (int s = 0; s < kNS; ++s) acc[s] = 0.0;
   for (int e = pick(BL.ptr, side)[c]; e < pick(BL.ptr, side)[c + 1]; ++e) {
-    const int slot = pick(BL.adm, side)[e];
-    const int l = pick(M.rank, 1 - side)[pick(BL.other, side)[slot]];
+    const int slot = adm[e];
+    const int l = orank[other[slot]];
     load_block_rows(X, M.S + (size_t)slot * kcap * kcap, kcap, side, l, k, lane);
     __syncwarp();
     const double nrm2 = sum_squares(X, l, k, lane);
@@ -237,8 +393,8 @@ __global__ void k_bgram_down(MatView M, const int32_t* __restrict__ list, int n,
   }
   if (f >= 0) {
     const int kf = pick(M.rank, side)[f];
-    load_tile(T0, pick(BW.W0, side) + (size_t)f * kSlot, 32, kf, kf, lane);
-    load_tile(T1, pick(M.transfer, side) + (size_t)c * kcap * kcap, kcap, k, kf, lane);
+    load_tile(T0, kLd, pick(BW.W0, side) + (size_t)f * kSlot, 32, kf, kf, lane);
+    load_tile(T1, kLd, pick(M.transfer, side) + (size_t)c * kcap * kcap, kcap, k, kf, lane);
     __syncwarp();
     // T2 = E W0_f (k x kf)
     for (int e = lane; e < k * kf; e += 32) {
@@ -265,8 +421,10 @@ __global__ void k_bgram_down(MatView M, const int32_t* __restrict__ list, int n,
 }
 
 // ------------------------------------------------------------- step 2
-// G_t = V~_t^* V~_t bottom-up: leaf Gram of (V_t, A|_t) over chunks of 32
-// rows; inner sum over the sons of E~_s^* G_s E~_s, E~_s = diag(E_s, I_u).
+// C_t = V_t^* A|_t and N_t = A|_t^* A|_t bottom-up: leaves over chunks of 32
+// rows of (V_t, A|_t), inner clusters C_t = sum E_s^* C_s, N_t = sum N_s.
+// Entry e of the per-lane list is C_t[e % k][e / k] for e < k u, then the
+// lower triangle of N_t.  The V_t^* V_t block of G_t comes from k_vgram.
 __global__ void k_fgram(MatView M, const Item* __restrict__ items, const int32_t* __restrict__ list, int n, int u,
                         int tc, const double* __restrict__ A, const double* __restrict__ B, ItemBuffers IB,
                         int* err) {
@@ -275,9 +433,8 @@ __global__ void k_fgram(MatView M, const Item* __restrict__ items, const int32_t
   const int w = threadIdx.x >> 5;
   const int idx = blockIdx.x * (blockDim.x >> 5) + w;
   if (idx >= n) return;
-  double* T0 = smem + (size_t)w * 3 * kLd * tc;
+  double* T0 = smem + (size_t)w * 2 * kLd * tc;
   double* T1 = T0 + kLd * tc;
-  double* T2 = T1 + kLd * tc;
   const int id = list[idx];
   const Item it = items[id];
   const int side = it.side;
@@ -287,7 +444,8 @@ __global__ void k_fgram(MatView M, const Item* __restrict__ items, const int32_t
     if (lane == 0) atomicOr(err, kErrCols);
     return;
   }
-  const int nt = tri(K);
+  const int ncu = k * u;
+  const int nt = ncu + tri(u);
   double acc[kNS];
 #pragma unroll
   for (int s = 0; s < kNS; ++s) acc[s] = 0.0;
@@ -297,12 +455,28 @@ __global__ void k_fgram(MatView M, const Item* __restrict__ items, const int32_t
     const int m = it.size;
     for (int r0 = 0; r0 < m; r0 += 32) {
       const int ch = min(32, m - r0);
-      if (lane < ch) {
-        for (int c = 0; c < k; ++c) T0[lane + c * kLd] = V[(r0 + lane) + (size_t)c * m];
-        for (int c = 0; c < u; ++c) T0[lane + (k + c) * kLd] = F[(it.rowoff + r0 + lane) + (size_t)c * it.ld];
-      }
+      load_tile(T0, kLd, V + r0, m, ch, k, lane);
+      load_tile(T0 + k * kLd, kLd, F + it.rowoff + r0, it.ld, ch, u, lane);
       __syncwarp();
-      acc_gram(acc, T0, ch, K, 1.0, lane);
+#pragma unroll
+      for (int s = 0; s < kNS; ++s) {
+        if (32 * s >= nt) break;
+        const int e = lane + 32 * s;
+        if (e < nt) {
+          int c1, c2;
+          if (e < ncu) {
+            c1 = e % k;
+            c2 = k + e / k;
+          } else {
+            tri_index(e - ncu, c1, c2);
+            c1 += k;
+            c2 += k;
+          }
+          double g = acc[s];
+          for (int r = 0; r < ch; ++r) g = fma(T0[r + c1 * kLd], T0[r + c2 * kLd], g);
+          acc[s] = g;
+        }
+      }
       __syncwarp();
     }
   } else {
@@ -311,36 +485,23 @@ __global__ void k_fgram(MatView M, const Item* __restrict__ items, const int32_t
       const int sid = si == 0 ? it.son0 : it.son1;
       const Item sn = items[sid];
       const int ks = sn.k;
-      const int Ks = ks + u;
-      load_tile(T0, IB.Gv + (size_t)sid * kSlot, 32, Ks, Ks, lane);
-      load_tile(T1, pick(M.transfer, side) + (size_t)sn.cluster * kcap * kcap, kcap, ks, k, lane);
+      const double* Gs = IB.Gv + (size_t)sid * kSlot;
+      load_tile(T0, kLd, Gs + ks * 32, 32, ks, u, lane);   // C_s (ks x u)
+      load_tile(T1, kLd, pick(M.transfer, side) + (size_t)sn.cluster * kcap * kcap, kcap, ks, k, lane);
       __syncwarp();
-      // T2 = G_s E~_s (Ks x K)
-      for (int e = lane; e < Ks * K; e += 32) {
-        const int i = e % Ks, j = e / Ks;
-        double v;
-        if (j < k) {
-          v = 0.0;
-          for (int q = 0; q < ks; ++q) v = fma(T0[i + q * kLd], T1[q + j * kLd], v);
-        } else {
-          v = T0[i + (ks + j - k) * kLd];
-        }
-        T2[i + j * kLd] = v;
-      }
-      __syncwarp();
-      // acc += E~_s^* T2
 #pragma unroll
       for (int s = 0; s < kNS; ++s) {
         if (32 * s >= nt) break;
         const int e = lane + 32 * s;
         if (e < nt) {
-          int i, j;
-          tri_index(e, i, j);
           double v = acc[s];
-          if (i < k) {
-            for (int q = 0; q < ks; ++q) v = fma(T1[q + i * kLd], T2[q + j * kLd], v);
+          if (e < ncu) {
+            const int i = e % k, j = e / k;
+            for (int q = 0; q < ks; ++q) v = fma(T1[q + i * kLd], T0[q + j * kLd], v);
           } else {
-            v += T2[ks + i - k + j * kLd];
+            int a, b;
+            tri_index(e - ncu, a, b);
+            v += Gs[(ks + a) + (ks + b) * 32];
           }
           acc[s] = v;
         }
@@ -348,14 +509,32 @@ __global__ void k_fgram(MatView M, const Item* __restrict__ items, const int32_t
       __syncwarp();
     }
   }
-  store_sym(IB.Gv + (size_t)id * kSlot, acc, K, lane);
+  double* G = IB.Gv + (size_t)id * kSlot;
+#pragma unroll
+  for (int s = 0; s < kNS; ++s) {
+    if (32 * s >= nt) break;
+    const int e = lane + 32 * s;
+    if (e < nt) {
+      int i, j;
+      if (e < ncu) {
+        i = e % k;
+        j = k + e / k;
+      } else {
+        tri_index(e - ncu, i, j);
+        i += k;
+        j += k;
+      }
+      G[i + j * 32] = acc[s];
+      G[j + i * 32] = acc[s];
+    }
+  }
 }
 
 // ||Z~|_b||_F^2 = tr(S~_b^* G_t S~_b G_s) for the blocks inside the update,
 // S~_b = diag(S_b, I_u): entry (i, j) of G_t S~_b times entry (i, j) of
 // S~_b G_s, summed.
 __global__ void k_fnorms(MatView M, const Item* __restrict__ items, const NormTask* __restrict__ tasks, int n,
-                         int u, int tc, ItemBuffers IB) {
+                         int u, int tc, BaseWeights BW, ItemBuffers IB) {
   extern __shared__ double smem[];
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
@@ -365,12 +544,15 @@ __global__ void k_fnorms(MatView M, const Item* __restrict__ items, const NormTa
   double* T1 = T0 + kLd * tc;
   double* T2 = T1 + kLd * tc;
   const NormTask tk = tasks[idx];
-  const int kt = items[tk.it].k, ls = items[tk.is].k;
+  const Item it = items[tk.it], is = items[tk.is];
+  const int kt = it.k, ls = is.k;
   const int Kt = kt + u, Ks = ls + u;
   const int kcap = M.kcap;
-  load_tile(T0, IB.Gv + (size_t)tk.it * kSlot, 32, Kt, Kt, lane);
-  load_tile(T1, IB.Gv + (size_t)tk.is * kSlot, 32, Ks, Ks, lane);
-  load_tile(T2, M.S + (size_t)tk.slot * kcap * kcap, kcap, kt, ls, lane);
+  load_gram(T0, kLd, IB.Gv + (size_t)tk.it * kSlot, BW.Vg[0] + (size_t)it.cluster * kSlot,
+            BW.orth[0][it.cluster] != 0, kt, Kt, lane);
+  load_gram(T1, kLd, IB.Gv + (size_t)tk.is * kSlot, BW.Vg[1] + (size_t)is.cluster * kSlot,
+            BW.orth[1][is.cluster] != 0, ls, Ks, lane);
+  load_tile(T2, kLd, M.S + (size_t)tk.slot * kcap * kcap, kcap, kt, ls, lane);
   __syncwarp();
   double part = 0.0;
   for (int e = lane; e < Kt * Ks; e += 32) {
@@ -421,17 +603,9 @@ __global__ void k_fweights(MatView M, const Item* __restrict__ items, const Entr
   const int nt = tri(K);
   const int ntk = tri(k);
   const double st = (double)pick(M.subtree, side)[it.cluster];
-  const double* Gt = IB.Gv + (size_t)id * kSlot;
-  // V_t orthonormal: |V_t^* V_t - I| within rounding
-  bool orth = true;
-  for (int e = lane; e < ntk; e += 32) {
-    int i, j;
-    tri_index(e, i, j);
-    const double g = Gt[i + j * 32] - (i == j ? 1.0 : 0.0);
-    if (fabs(g) > 256.0 * DBL_EPSILON) orth = false;
-  }
-  orth = __all_sync(kFull, orth);
-  if (lane == 0) IB.jac[4 * (size_t)id + 3] = orth ? 0ull : 1ull;
+  const int32_t* orank = pick(M.rank, 1 - side);
+  const double* Sbase = M.S;
+  const bool orth = pick(BW.orth, side)[it.cluster] != 0;
   double acc[kNS];
 #pragma unroll
   for (int s = 0; s < kNS; ++s) acc[s] = 0.0;
@@ -450,8 +624,8 @@ __global__ void k_fweights(MatView M, const Item* __restrict__ items, const Entr
       for (int e = it.ent_begin; e < it.ent_end; ++e) {
         const Entry en = ents[e];
         if (en.other < 0) continue;
-        const int l = pick(M.rank, 1 - side)[en.other_cluster];
-        load_block_rows(T0, M.S + (size_t)en.slot * kcap * kcap, kcap, side, l, k, lane);
+        const int l = orank[en.other_cluster];
+        load_block_rows(T0, Sbase + (size_t)en.slot * kcap * kcap, kcap, side, l, k, lane);
         __syncwarp();
         const double nrm2 = sum_squares(T0, l, k, lane);
         const double w2 = nrm2 > 1e-300 ? st * recip(nrm2) : 0.0;
@@ -459,12 +633,12 @@ __global__ void k_fweights(MatView M, const Item* __restrict__ items, const Entr
         __syncwarp();
       }
   } else {
-    load_tile(T1, Gt, 32, k, k, lane);
+    load_tile(T1, kLd, pick(BW.Vg, side) + (size_t)it.cluster * kSlot, 32, k, k, lane);
     for (int e = it.ent_begin; e < it.ent_end; ++e) {
       const Entry en = ents[e];
       if (en.other >= 0) continue;
-      const int l = pick(M.rank, 1 - side)[en.other_cluster];
-      load_block_rows(T0, M.S + (size_t)en.slot * kcap * kcap, kcap, side, l, k, lane);
+      const int l = orank[en.other_cluster];
+      load_block_rows(T0, Sbase + (size_t)en.slot * kcap * kcap, kcap, side, l, k, lane);
       __syncwarp();
       // ||R_kk S_b||_F^2 = sum over rows x of X of x G_kk x^*
       double part = 0.0;
@@ -480,20 +654,25 @@ __global__ void k_fweights(MatView M, const Item* __restrict__ items, const Entr
       __syncwarp();
     }
   }
+  if (lane == 0) IB.jac[4 * (size_t)id + 3] = orth ? 0ull : 1ull;
   // blocks inside the update
-  if (it.flags & kItemInside)
+  if (it.flags & kItemInside) {
+    const double* Vgo = pick(BW.Vg, 1 - side);
+    const int32_t* orth_o = pick(BW.orth, 1 - side);
     for (int e = it.ent_begin; e < it.ent_end; ++e) {
       const Entry en = ents[e];
       if (en.other < 0) continue;
-      const int l = items[en.other].k;
+      const Item ot = items[en.other];
+      const int l = ot.k;
       const int Ko = l + u;
       const double nrm = IB.norms[en.norm];
       const double w2 = nrm > 1e-150 ? st * recip(nrm * nrm) : 0.0;
-      load_tile(T1, IB.Gv + (size_t)en.other * kSlot, 32, Ko, Ko, lane);
+      load_gram(T1, kLd, IB.Gv + (size_t)en.other * kSlot, Vgo + (size_t)ot.cluster * kSlot,
+                orth_o[ot.cluster] != 0, l, Ko, lane);
       // T0 = S' (k x l): S_b on the row side, S_b^* on the column side
-      const double* S = M.S + (size_t)en.slot * kcap * kcap;
+      const double* S = Sbase + (size_t)en.slot * kcap * kcap;
       if (side == 0) {
-        load_tile(T0, S, kcap, k, l, lane);
+        load_tile(T0, kLd, S, kcap, k, l, lane);
       } else {
         for (int q = 0; q < l; ++q)
           if (lane < k) T0[lane + q * kLd] = S[q + (size_t)lane * kcap];
@@ -531,13 +710,15 @@ __global__ void k_fweights(MatView M, const Item* __restrict__ items, const Entr
       }
       __syncwarp();
     }
+  }
   // father's part
+  const double* E = pick(M.transfer, side) + (size_t)it.cluster * kcap * kcap;   // k x kf
   if (it.flags & kItemRoot) {
     if (!(it.flags & kItemTreeRoot)) {
       const int f = pick(M.father, side)[it.cluster];
       const int kf = it.kf;
-      load_tile(T1, pick(BW.W0, side) + (size_t)f * kSlot, 32, kf, kf, lane);
-      load_tile(T0, pick(M.transfer, side) + (size_t)it.cluster * kcap * kcap, kcap, k, kf, lane);
+      load_tile(T1, kLd, pick(BW.W0, side) + (size_t)f * kSlot, 32, kf, kf, lane);
+      load_tile(T0, kLd, E, kcap, k, kf, lane);
       __syncwarp();
       for (int e2 = lane; e2 < k * kf; e2 += 32) {
         const int i = e2 % k, j = e2 / k;
@@ -562,22 +743,19 @@ __global__ void k_fweights(MatView M, const Item* __restrict__ items, const Entr
   } else {
     const int kf = items[it.parent].k;
     const int Kf = kf + u;
-    load_tile(T1, IB.Wg + (size_t)it.parent * kSlot, 32, Kf, Kf, lane);
-    load_tile(T0, pick(M.transfer, side) + (size_t)it.cluster * kcap * kcap, kcap, k, kf, lane);
+    load_tile(T1, kLd, IB.Wg + (size_t)it.parent * kSlot, 32, Kf, Kf, lane);
+    load_tile(T0, kLd, E, kcap, k, kf, lane);
     __syncwarp();
-    // T2 = E~_t W_p (K x Kf)
-    for (int e2 = lane; e2 < K * Kf; e2 += 32) {
-      const int i = e2 % K, j = e2 / K;
-      double v;
-      if (i < k) {
-        v = 0.0;
-        for (int q = 0; q < kf; ++q) v = fma(T0[i + q * kLd], T1[q + j * kLd], v);
-      } else {
-        v = T1[kf + i - k + j * kLd];
-      }
+    // T2 = E W11 (k x kf); rows k.. of E~_t W_p are rows kf.. of W_p
+    for (int e2 = lane; e2 < k * kf; e2 += 32) {
+      const int i = e2 % k, j = e2 / k;
+      double v = 0.0;
+      for (int q = 0; q < kf; ++q) v = fma(T0[i + q * kLd], T1[q + j * kLd], v);
       T2[i + j * kLd] = v;
     }
     __syncwarp();
+    // lower triangle of E~_t W_p E~_t^*: (i, j < k) rows of T2 times E^*;
+    // (i >= k, j < k) rows kf + i - k of W_p times E^*; (i, j >= k) W22
 #pragma unroll
     for (int s = 0; s < kNS; ++s) {
       if (32 * s >= nt) break;
@@ -587,9 +765,13 @@ __global__ void k_fweights(MatView M, const Item* __restrict__ items, const Entr
         tri_index(e2, i, j);
         double v = acc[s];
         if (j < k) {
-          for (int q = 0; q < kf; ++q) v = fma(T2[i + q * kLd], T0[j + q * kLd], v);
+          if (i < k) {
+            for (int q = 0; q < kf; ++q) v = fma(T2[i + q * kLd], T0[j + q * kLd], v);
+          } else {
+            for (int q = 0; q < kf; ++q) v = fma(T1[(kf + i - k) + q * kLd], T0[j + q * kLd], v);
+          }
         } else {
-          v += T2[i + (kf + j - k) * kLd];
+          v += T1[(kf + i - k) + (kf + j - k) * kLd];
         }
         acc[s] = v;
       }
@@ -599,73 +781,141 @@ __global__ void k_fweights(MatView M, const Item* __restrict__ items, const Entr
 }
 
 // ------------------------------------------------------------- step 4
-// Certificate and R_t = L^* for every cluster task of the batch (one
-// launch): G_t = L D L^*, L_G = L D^{1/2}, C = L_G^* W_t L_G, LDL^* of
-// C - (tau + delta) I.  delta = 8 (levels + 4) (K + 32) eps_mach tr(G_t)
-// tr(W_t) bounds the rounding of the Gram sums over the levels of the tree
-// and the K-term products and factorisations, with slack (normwise bounds,
-// tr(G_t) tr(W_t) >= ||G_t|| ||W_t||).
-__global__ void k_certify(const Item* __restrict__ items, int n, int u, int tc, int levels, double eps,
-                          ItemBuffers IB) {
+// Certificate and R_t = L^* for every cluster task of the batch: L^* W_t L -
+// (tau + delta) I = L2 D2 L2^* with positive pivots, G_t = L L^*.  delta =
+// 8 (levels + 4) (K + 32) eps_mach tr(G_t) tr(W_t) bounds the rounding of
+// the Gram sums over the levels of the tree, the K-term products and
+// factorisations and the orthonormality tolerance of the unchanged basis,
+// with slack (normwise bounds, tr(G_t) tr(W_t) >= ||G_t|| ||W_t||).  Tiles
+// have leading dimension ld = largest K + 1.  Two launches over all tasks:
+// kGeneral = false takes the tasks whose V_t is orthonormal (block formulas,
+// a K x u tile for C_t and L_S), kGeneral = true the others (factorisation
+// of the whole G_t).
+template <bool kGeneral>
+__global__ void k_certify(const Item* __restrict__ items, int n, int u, int ld, int levels, double eps,
+                          BaseWeights BW, ItemBuffers IB) {
   extern __shared__ double smem[];
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
   const int id = blockIdx.x * (blockDim.x >> 5) + w;
   if (id >= n) return;
-  double* T0 = smem + (size_t)w * (3 * kLd * tc + 64);
-  double* T1 = T0 + kLd * tc;
-  double* T2 = T1 + kLd * tc;
-  double* lv = T2 + kLd * tc;
-  double* dsq = lv + 32;
   const Item it = items[id];
-  const int K = it.k + u;
-  load_tile(T0, IB.Gv + (size_t)id * kSlot, 32, K, K, lane);
-  load_tile(T1, IB.Wg + (size_t)id * kSlot, 32, K, K, lane);
-  __syncwarp();
-  const double trG = warp_sum(lane < K ? T0[lane * (kLd + 1)] : 0.0);
-  const double trW = warp_sum(lane < K ? T1[lane * (kLd + 1)] : 0.0);
-  const double scale = trG * trW;
-  bool ok = K >= 1 && trG > 0.0 && trW > 0.0 && scale < DBL_MAX;
-  if (ok) ok = ldl(T0, K, 0.0, lv, lane);
+  const bool orth = pick(BW.orth, it.side)[it.cluster] != 0;
+  if (orth == kGeneral) return;
+  const int k = it.k;
+  const int K = k + u;
+  const int tile = ld * (ld - 1);
+  // general: T0 = G_t / L (K x K); orthonormal: T0 = [C_t; S or L_S] (K x u)
+  const int t0 = kGeneral ? tile : ld * u;
+  double* T0 = smem + (size_t)w * (2 * tile + t0 + 64);
+  double* T1 = T0 + t0;
+  double* T2 = T1 + tile;
+  double* lv = T2 + tile;
+  double* dsq = lv + 32;
+  const double* Gv = IB.Gv + (size_t)id * kSlot;
+  load_tile(T1, ld, IB.Wg + (size_t)id * kSlot, 32, K, K, lane);
+  const double trW = warp_sum(lane < K ? IB.Wg[(size_t)id * kSlot + lane * 33] : 0.0);
+  double trG;
+  bool ok;
+  if constexpr (!kGeneral) {
+    // C(p, q) = T0[p + q ld] (p < k), S(a, b) = Sb[a + b ld] = T0[k + a + b ld]
+    load_tile(T0, ld, Gv + k * 32, 32, K, u, lane);
+    trG = k + warp_sum(lane < u ? Gv[(k + lane) * 33] : 0.0);
+    __syncwarp();
+    double* Sb = T0 + k;
+    for (int e = lane; e < tri(u); e += 32) {
+      int a, b;
+      tri_index(e, a, b);
+      double v = Sb[a + b * ld];
+      for (int p = 0; p < k; ++p) v = fma(-T0[p + a * ld], T0[p + b * ld], v);
+      Sb[a + b * ld] = v;
+    }
+    __syncwarp();
+    ok = trG > 0.0 && trW > 0.0 && trG * trW < DBL_MAX && ldl<true>(Sb, ld, u, 0.0, lv, lane);
+    if (ok) {
+      ldl_to_cholesky(Sb, ld, u, dsq, lane);
+      // T2 = W L, L = [[I, 0], [C^*, L_S]]
+      for (int e = lane; e < K * K; e += 32) {
+        const int i = e % K, j = e / K;
+        double v;
+        if (j < k) {
+          v = T1[i + j * ld];
+          for (int q = 0; q < u; ++q) v = fma(T1[i + (k + q) * ld], T0[j + q * ld], v);
+        } else {
+          const int b = j - k;
+          v = 0.0;
+          for (int a = b; a < u; ++a) v = fma(T1[i + (k + a) * ld], Sb[a + b * ld], v);
+        }
+        T2[i + j * ld] = v;
+      }
+      __syncwarp();
+      // C2 = L^* T2 (lower triangle) over W
+      for (int e = lane; e < tri(K); e += 32) {
+        int i, j;
+        tri_index(e, i, j);
+        double v;
+        if (i < k) {
+          v = T2[i + j * ld];
+          for (int q = 0; q < u; ++q) v = fma(T0[i + q * ld], T2[(k + q) + j * ld], v);
+        } else {
+          const int a = i - k;
+          v = 0.0;
+          for (int q = a; q < u; ++q) v = fma(Sb[q + a * ld], T2[(k + q) + j * ld], v);
+        }
+        T1[i + j * ld] = v;
+      }
+      __syncwarp();
+    }
+  } else {
+    load_gram(T0, ld, Gv, pick(BW.Vg, it.side) + (size_t)it.cluster * kSlot, false, k, K, lane);
+    __syncwarp();
+    trG = warp_sum(lane < K ? T0[lane * (ld + 1)] : 0.0);
+    ok = K >= 1 && trG > 0.0 && trW > 0.0 && trG * trW < DBL_MAX && ldl<true>(T0, ld, K, 0.0, lv, lane);
+    if (ok) {
+      ldl_to_cholesky(T0, ld, K, dsq, lane);
+      // T2 = W L
+      for (int e = lane; e < K * K; e += 32) {
+        const int i = e % K, j = e / K;
+        double v = 0.0;
+        for (int q = j; q < K; ++q) v = fma(T1[i + q * ld], T0[q + j * ld], v);
+        T2[i + j * ld] = v;
+      }
+      __syncwarp();
+      // C2 = L^* T2 (lower triangle) over W
+      for (int e = lane; e < tri(K); e += 32) {
+        int i, j;
+        tri_index(e, i, j);
+        double v = 0.0;
+        for (int q = i; q < K; ++q) v = fma(T0[q + i * ld], T2[q + j * ld], v);
+        T1[i + j * ld] = v;
+      }
+      __syncwarp();
+    }
+  }
   if (ok) {
-    // L_G = L D^{1/2}
-    if (lane < K) dsq[lane] = sqrt(T0[lane * (kLd + 1)]);
-    __syncwarp();
-    for (int e = lane; e < tri(K); e += 32) {
-      int i, j;
-      tri_index(e, i, j);
-      T0[i + j * kLd] = i == j ? dsq[j] : T0[i + j * kLd] * dsq[j];
-    }
-    __syncwarp();
-    // T2 = W L_G
-    for (int e = lane; e < K * K; e += 32) {
-      const int i = e % K, j = e / K;
-      double v = 0.0;
-      for (int q = j; q < K; ++q) v = fma(T1[i + q * kLd], T0[q + j * kLd], v);
-      T2[i + j * kLd] = v;
-    }
-    __syncwarp();
-    // C = L_G^* T2 (lower triangle) over W
-    for (int e = lane; e < tri(K); e += 32) {
-      int i, j;
-      tri_index(e, i, j);
-      double v = 0.0;
-      for (int q = i; q < K; ++q) v = fma(T0[q + i * kLd], T2[q + j * kLd], v);
-      T1[i + j * kLd] = v;
-    }
-    __syncwarp();
-    const double delta = 8.0 * (levels + 4) * (K + 32) * DBL_EPSILON * scale;
-    ok = ldl(T1, K, 0.25 * eps * eps + delta, lv, lane);
+    const double delta = 8.0 * (levels + 4) * (K + 32) * DBL_EPSILON * trG * trW;
+    ok = ldl<false>(T1, ld, K, 0.25 * eps * eps + delta, lv, lane);
   }
   if (!ok) {
     if (lane == 0) IB.fail[it.update] = 1;
     return;
   }
-  // R_t = L_G^* (K x K upper, rows K..31 zero)
+  // R_t = L^* (K x K upper, rows K..31 zero)
   double* Rt = IB.Rt + (size_t)id * kSlot;
   for (int e = lane; e < 32 * K; e += 32) {
     const int p = e & 31, c = e >> 5;
-    Rt[p + c * 32] = (p <= c) ? T0[c + p * kLd] : 0.0;
+    double v = 0.0;
+    if constexpr (!kGeneral) {
+      if (c < k)
+        v = p == c ? 1.0 : 0.0;
+      else if (p < k)
+        v = T0[p + (c - k) * ld];                         // C_t
+      else if (p <= c)
+        v = T0[c + (p - k) * ld];                         // L_S^*
+    } else {
+      if (p <= c) v = T0[c + p * ld];
+    }
+    Rt[p + c * 32] = v;
   }
   if (lane == 0) IB.rank[id] = K;
 }
@@ -673,8 +923,13 @@ __global__ void k_certify(const Item* __restrict__ items, int n, int u, int tc, 
 // New leaf bases V~_t L_t^{-*}, transfer matrices L_t^* E~_t L_{t+}^{-*} and
 // the commit E_t0 <- L_t0^* [E_t0; 0] for the certified updates (one launch,
 // one warp per cluster task, lane = row, forward substitution with the
-// factor in shared memory).  Tasks of updates whose certificate failed mark
-// their cluster and its ancestors for the exact path instead.
+// factor in shared memory).  With orthonormal bases they reduce to
+// (V_t, (A|_t - V_t C_t) L_S^{-*}), [[E_t, (C_t - E_t C_p) L_Sp^{-*}],
+// [0, L_St^* L_Sp^{-*}]] and [E_t0; 0].  Two launches over all tasks:
+// kGeneral = false does the parts that have the block form and marks, for
+// the tasks of updates whose certificate failed, their cluster and its
+// ancestors for the exact path; kGeneral = true does the other parts.
+template <bool kGeneral, int UMAX>
 __global__ void k_fbasis(MatView M, const Item* __restrict__ items, int n, int u, int tc,
                          const double* __restrict__ A, const double* __restrict__ B, ItemBuffers IB,
                          BaseWeights BW) {
@@ -690,19 +945,30 @@ __global__ void k_fbasis(MatView M, const Item* __restrict__ items, int n, int u
   const Item it = items[id];
   const int side = it.side;
   if (IB.fail[it.update]) {
-    if (lane == 0)
-      for (int c = it.cluster; c >= 0; c = pick(M.father, side)[c]) pick(BW.need, side)[c] = 1;
+    if (!kGeneral && lane == 0) {
+      const int32_t* father = pick(M.father, side);
+      int32_t* need = pick(BW.need, side);
+      for (int c = it.cluster; c >= 0; c = father[c]) need[c] = 1;
+    }
     return;
   }
   const int k = it.k;
   const int K = k + u;
   const int kcap = M.kcap;
-  // L_t (lower) from R_t = L_t^*
-  const double* Rt = IB.Rt + (size_t)id * kSlot;
-  for (int c = 0; c < K; ++c)
-    if (lane <= c) T0[c + lane * kLd] = Rt[lane + c * 32];
+  const int32_t* orthv = pick(BW.orth, side);
+  const bool orth = orthv[it.cluster] != 0;
+  const bool has_transfer = !(it.flags & kItemTreeRoot);
+  const bool root = it.flags & kItemRoot;
+  const bool orth_p = has_transfer && !root && orthv[pick(M.father, side)[it.cluster]] != 0;
+  // which kernel does which part: the block form needs V_t (and, for a
+  // transfer matrix below the subtree root, V_{t+}) orthonormal
+  const bool do_leaf = (it.flags & kItemLeaf) && (orth == !kGeneral);
+  const bool do_transfer = has_transfer && ((root ? orth : orth && orth_p) == !kGeneral);
+  if (!do_leaf && !do_transfer) return;
+  // R_t = L_t^* (upper) into T0, as stored
+  load_tile(T0, kLd, IB.Rt + (size_t)id * kSlot, 32, K, K, lane);   // zero below the diagonal
   __syncwarp();
-  if (it.flags & kItemLeaf) {
+  if (do_leaf) {
     if (lane < K) ri[lane] = recip(T0[lane * (kLd + 1)]);
     __syncwarp();
     const double* V = pick(M.leaf, side) + pick(M.leaf_off, side)[it.cluster];
@@ -712,37 +978,66 @@ __global__ void k_fbasis(MatView M, const Item* __restrict__ items, int n, int u
     for (int r0 = 0; r0 < m; r0 += 32) {
       const int r = r0 + lane;
       const bool act = r < m;
-      double y[32];
+      if constexpr (!kGeneral) {
+        // y = (row of A|_t - row of V_t C_t) L_S^{-*}; V_t is copied (its
+        // rows staged in T1, lane = row)
+        load_tile(T1, kLd, V + r0, m, min(32, m - r0), k, lane);
+        __syncwarp();
+        if (act)
+          for (int c = 0; c < k; ++c) Q[r + (size_t)c * m] = T1[lane + c * kLd];
+        double y[UMAX];
 #pragma unroll
-      for (int c = 0; c < 32; ++c) {
-        if (c < K) {
-          double v = 0.0;
-          if (act) v = c < k ? V[r + (size_t)c * m] : F[(it.rowoff + r) + (size_t)(c - k) * it.ld];
+        for (int q = 0; q < UMAX; ++q)
+          if (q < u) {
+            double a = act ? F[(it.rowoff + r) + (size_t)q * it.ld] : 0.0;
+            for (int p = 0; p < k; ++p) a = fma(-T1[lane + p * kLd], T0[p + (k + q) * kLd], a);
 #pragma unroll
-          for (int p = 0; p < c; ++p) v = fma(-T0[c + p * kLd], y[p], v);
-          y[c] = v * ri[c];
+            for (int p = 0; p < q; ++p) a = fma(-T0[(k + p) + (k + q) * kLd], y[p], a);
+            y[q] = a * ri[k + q];
+          }
+        if (act)
+#pragma unroll
+          for (int q = 0; q < UMAX; ++q)
+            if (q < u) Q[r + (size_t)(k + q) * m] = y[q];
+      } else {
+        double y[32];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          if (c < K) {
+            double v = 0.0;
+            if (act) v = c < k ? V[r + (size_t)c * m] : F[(it.rowoff + r) + (size_t)(c - k) * it.ld];
+#pragma unroll
+            for (int p = 0; p < c; ++p) v = fma(-T0[p + c * kLd], y[p], v);
+            y[c] = v * ri[c];
+          }
         }
-      }
-      if (act)
+        if (act)
 #pragma unroll
-        for (int c = 0; c < 32; ++c)
-          if (c < K) Q[r + (size_t)c * m] = y[c];
+          for (int c = 0; c < 32; ++c)
+            if (c < K) Q[r + (size_t)c * m] = y[c];
+      }
     }
     __syncwarp();
   }
-  if (it.flags & kItemTreeRoot) return;
+  if (!do_transfer) return;
   const int kf = it.kf;
-  load_tile(T2, pick(M.transfer, side) + (size_t)it.cluster * kcap * kcap, kcap, k, kf, lane);
+  load_tile(T2, kLd, pick(M.transfer, side) + (size_t)it.cluster * kcap * kcap, kcap, k, kf, lane);
   double* Fo = IB.F + (size_t)id * kSlot;
-  if (it.flags & kItemRoot) {
-    // commit: E_t0 <- L^* [E_t0; 0] (K x kf), lane = row
-    __syncwarp();
-    const int i = lane;
+  const int i = lane;
+  __syncwarp();
+  if (root) {
+    // commit: E_t0 <- L^* [E_t0; 0] (K x kf), lane = row; [E_t0; 0] when
+    // V_t0 is orthonormal
+    if constexpr (!kGeneral) {
+      if (i < K)
+        for (int j = 0; j < kf; ++j) Fo[i + j * 32] = i < k ? T2[i + j * kLd] : 0.0;
+      return;
+    }
     double z[32];
 #pragma unroll
     for (int j = 0; j < 32; ++j) z[j] = 0.0;
     for (int q = 0; q < k; ++q) {
-      const double lq = (i < K && q >= i) ? T0[q + i * kLd] : 0.0;
+      const double lq = (i < K && q >= i) ? T0[i + q * kLd] : 0.0;
 #pragma unroll
       for (int j = 0; j < 32; ++j)
         if (j < kf) z[j] = fma(lq, T2[q + j * kLd], z[j]);
@@ -753,20 +1048,50 @@ __global__ void k_fbasis(MatView M, const Item* __restrict__ items, int n, int u
         if (j < kf) Fo[i + j * 32] = z[j];
     return;
   }
-  // new transfer matrix: L_t^* E~_t L_p^{-*} (K x Kf), lane = row
+  // new transfer matrix (K x Kf), lane = row
   const int Kf = kf + u;
-  const double* Rp = IB.Rt + (size_t)it.parent * kSlot;
-  for (int c = 0; c < Kf; ++c)
-    if (lane <= c) T1[c + lane * kLd] = Rp[lane + c * 32];
+  load_tile(T1, kLd, IB.Rt + (size_t)it.parent * kSlot, 32, Kf, Kf, lane);   // R_p = L_p^* (upper)
   __syncwarp();
   if (lane < Kf) ri[lane] = recip(T1[lane * (kLd + 1)]);
   __syncwarp();
-  const int i = lane;
+  if constexpr (!kGeneral) {
+    // rows i < k: [E_t, (C_t - E_t C_p) L_Sp^{-*}]; rows k + a: [0, (row a
+    // of L_St^*) L_Sp^{-*}]
+    double x[UMAX];
+#pragma unroll
+    for (int q = 0; q < UMAX; ++q)
+      if (q < u) {
+        double v = 0.0;
+        if (i < k) {
+          v = T0[i + (k + q) * kLd];
+          for (int p = 0; p < kf; ++p) v = fma(-T2[i + p * kLd], T1[p + (kf + q) * kLd], v);
+        } else if (i < K && k + q >= i) {
+          v = T0[i + (k + q) * kLd];
+        }
+        x[q] = v;
+      }
+#pragma unroll
+    for (int q = 0; q < UMAX; ++q)
+      if (q < u) {
+        double v = x[q];
+#pragma unroll
+        for (int p = 0; p < q; ++p) v = fma(-T1[(kf + p) + (kf + q) * kLd], x[p], v);
+        x[q] = v * ri[kf + q];
+      }
+    if (i < K) {
+      for (int j = 0; j < kf; ++j) Fo[i + j * 32] = i < k ? T2[i + j * kLd] : 0.0;
+#pragma unroll
+      for (int q = 0; q < UMAX; ++q)
+        if (q < u) Fo[i + (kf + q) * 32] = x[q];
+    }
+    return;
+  } else {
+  // general: L_t^* E~_t L_p^{-*}
   double z[32];
 #pragma unroll
   for (int j = 0; j < 32; ++j) z[j] = 0.0;
   for (int q = 0; q < k; ++q) {
-    const double lq = (i < K && q >= i) ? T0[q + i * kLd] : 0.0;
+    const double lq = (i < K && q >= i) ? T0[i + q * kLd] : 0.0;
 #pragma unroll
     for (int j = 0; j < 32; ++j)
       if (j < kf) z[j] = fma(lq, T2[q + j * kLd], z[j]);
@@ -776,7 +1101,7 @@ __global__ void k_fbasis(MatView M, const Item* __restrict__ items, int n, int u
   for (int j = 0; j < 32; ++j)
     if (j >= kf && j < Kf) {
       const int q = k + j - kf;
-      z[j] = (i < K && q >= i) ? T0[q + i * kLd] : 0.0;
+      z[j] = (i < K && q >= i) ? T0[i + q * kLd] : 0.0;
     }
   // z <- z L_p^{-*}: forward substitution over the columns
 #pragma unroll
@@ -784,13 +1109,14 @@ __global__ void k_fbasis(MatView M, const Item* __restrict__ items, int n, int u
     if (j < Kf) {
       double v = z[j];
 #pragma unroll
-      for (int q = 0; q < j; ++q) v = fma(-T1[j + q * kLd], z[q], v);
+      for (int q = 0; q < j; ++q) v = fma(-T1[q + j * kLd], z[q], v);
       z[j] = v * ri[j];
     }
   if (i < K)
 #pragma unroll
     for (int j = 0; j < 32; ++j)
       if (j < Kf) Fo[i + j * 32] = z[j];
+  }
 }
 
 constexpr int kWarps = 4;
@@ -811,75 +1137,103 @@ void smem_limit(Kern kern, size_t bytes, unsigned long long& done) {
 // largest rank of the matrix (fathers of the subtree roots).
 int tile_cols(const Pipeline& P) { return P.kl > P.M.kcap ? P.kl : P.M.kcap; }
 
-size_t tiles_bytes(int cols, int extra) { return (size_t)kWarps * (3 * kLd * cols + extra) * sizeof(double); }
+size_t tiles_bytes(int ntiles, int cols, int extra) {
+  return (size_t)kWarps * (ntiles * kLd * cols + extra) * sizeof(double);
+}
 
 }  // namespace
+
+void launch_gram_vbasis_level(const Pipeline& P, int level, cudaStream_t st) {
+  static unsigned long long done = 0;
+  const int n = P.cl_ptr[level + 1] - P.cl_ptr[level];
+  if (n <= 0) return;
+  smem_limit(k_vgram, tiles_bytes(3, 32, 0), done);
+  k_vgram<<<blocks_for(n), 32 * kWarps, tiles_bytes(3, P.M.kcap, 0), st>>>(P.M, P.cl_list + P.cl_ptr[level], n,
+                                                                          P.BW);
+}
 
 void launch_gram_base(const Pipeline& P, cudaStream_t st) {
   static unsigned long long done = 0;
   const int n = P.cl_ptr[P.levels];
   if (n <= 0) return;
-  const size_t sm = (size_t)kWarps * kLd * P.M.kcap * sizeof(double);
-  smem_limit(k_bgram, (size_t)kWarps * kLd * 32 * sizeof(double), done);
-  k_bgram<<<blocks_for(n), 32 * kWarps, sm, st>>>(P.M, P.cl_list, n, P.BL, P.BW, P.err);
+  smem_limit(k_bgram, tiles_bytes(1, 32, 0), done);
+  k_bgram<<<blocks_for(n), 32 * kWarps, tiles_bytes(1, P.M.kcap, 0), st>>>(P.M, P.cl_list, n, P.BL, P.BW, P.err);
 }
 
 void launch_gram_base_level(const Pipeline& P, int level, cudaStream_t st) {
   static unsigned long long done = 0;
   const int n = P.cl_ptr[level + 1] - P.cl_ptr[level];
   if (n <= 0) return;
-  smem_limit(k_bgram_down, tiles_bytes(32, 0), done);
-  k_bgram_down<<<blocks_for(n), 32 * kWarps, tiles_bytes(P.M.kcap, 0), st>>>(P.M, P.cl_list + P.cl_ptr[level], n,
-                                                                            P.BW);
+  smem_limit(k_bgram_down, tiles_bytes(3, 32, 0), done);
+  k_bgram_down<<<blocks_for(n), 32 * kWarps, tiles_bytes(3, P.M.kcap, 0), st>>>(P.M, P.cl_list + P.cl_ptr[level],
+                                                                               n, P.BW);
 }
 
 void launch_gram_basis(const Pipeline& P, int level) {
-  const int tc = tile_cols(P);
   static unsigned long long done = 0;
   const int n = P.lvl_ptr[level + 1] - P.lvl_ptr[level];
   if (n <= 0) return;
-  smem_limit(k_fgram, tiles_bytes(32, 0), done);
-  k_fgram<<<blocks_for(n), 32 * kWarps, tiles_bytes(tc, 0), P.stream>>>(
+  const int tc = tile_cols(P);
+  smem_limit(k_fgram, tiles_bytes(2, 32, 0), done);
+  k_fgram<<<blocks_for(n), 32 * kWarps, tiles_bytes(2, tc, 0), P.stream>>>(
       P.M, P.items, P.lvl_list + P.lvl_ptr[level], n, P.u, tc, P.A, P.B, P.IB, P.err);
 }
 
 void launch_gram_norms(const Pipeline& P) {
-  const int tc = tile_cols(P);
   static unsigned long long done = 0;
   if (P.n_norms <= 0) return;
-  smem_limit(k_fnorms, tiles_bytes(32, 0), done);
-  k_fnorms<<<blocks_for(P.n_norms), 32 * kWarps, tiles_bytes(tc, 0), P.stream>>>(P.M, P.items, P.norms,
-                                                                                   P.n_norms, P.u, tc, P.IB);
+  const int tc = tile_cols(P);
+  smem_limit(k_fnorms, tiles_bytes(3, 32, 0), done);
+  k_fnorms<<<blocks_for(P.n_norms), 32 * kWarps, tiles_bytes(3, tc, 0), P.stream>>>(P.M, P.items, P.norms,
+                                                                                    P.n_norms, P.u, tc, P.BW, P.IB);
 }
 
 void launch_gram_weights(const Pipeline& P, int level) {
-  const int tc = tile_cols(P);
   static unsigned long long done = 0;
   const int n = P.lvl_ptr[level + 1] - P.lvl_ptr[level];
   if (n <= 0) return;
-  smem_limit(k_fweights, tiles_bytes(32, 0), done);
-  k_fweights<<<blocks_for(n), 32 * kWarps, tiles_bytes(tc, 0), P.stream>>>(
+  const int tc = tile_cols(P);
+  smem_limit(k_fweights, tiles_bytes(3, 32, 0), done);
+  k_fweights<<<blocks_for(n), 32 * kWarps, tiles_bytes(3, tc, 0), P.stream>>>(
       P.M, P.items, P.ents, P.lvl_list + P.lvl_ptr[level], n, P.u, tc, P.BW, P.IB);
 }
 
 void launch_gram_certify(const Pipeline& P) {
-  const int tc = tile_cols(P);
-  static unsigned long long done = 0;
+  static unsigned long long done[2] = {0, 0};
   const int n = P.lvl_ptr[P.levels];
   if (n <= 0) return;
-  smem_limit(k_certify, tiles_bytes(32, 64), done);
-  k_certify<<<blocks_for(n), 32 * kWarps, tiles_bytes(tc, 64), P.stream>>>(P.items, n, P.u, tc, P.levels,
-                                                                             P.eps, P.IB);
+  const int ld = P.kl + 1;
+  const auto bytes = [](int l, int t0) { return (size_t)kWarps * (2 * l * (l - 1) + t0 + 64) * sizeof(double); };
+  smem_limit(k_certify<false>, bytes(33, 33 * 32), done[0]);
+  smem_limit(k_certify<true>, bytes(33, 33 * 32), done[1]);
+  k_certify<false><<<blocks_for(n), 32 * kWarps, bytes(ld, ld * P.u), P.stream>>>(P.items, n, P.u, ld, P.levels,
+                                                                                   P.eps, P.BW, P.IB);
+  k_certify<true><<<blocks_for(n), 32 * kWarps, bytes(ld, ld * (ld - 1)), P.stream>>>(P.items, n, P.u, ld,
+                                                                                      P.levels, P.eps, P.BW, P.IB);
+}
+
+template <int UMAX>
+void launch_fbasis_block_form(const Pipeline& P, int n, int tc) {
+  static unsigned long long done = 0;
+  smem_limit(k_fbasis<false, UMAX>, tiles_bytes(3, 32, 32), done);
+  k_fbasis<false, UMAX><<<blocks_for(n), 32 * kWarps, tiles_bytes(3, tc, 32), P.stream>>>(P.M, P.items, n, P.u, tc,
+                                                                                         P.A, P.B, P.IB, P.BW);
 }
 
 void launch_gram_outputs(const Pipeline& P) {
-  const int tc = tile_cols(P);
   static unsigned long long done = 0;
   const int n = P.lvl_ptr[P.levels];
   if (n <= 0) return;
-  smem_limit(k_fbasis, tiles_bytes(32, 32), done);
-  k_fbasis<<<blocks_for(n), 32 * kWarps, tiles_bytes(tc, 32), P.stream>>>(P.M, P.items, n, P.u, tc, P.A, P.B,
-                                                                            P.IB, P.BW);
+  const int tc = tile_cols(P);
+  if (P.u <= 8)
+    launch_fbasis_block_form<8>(P, n, tc);
+  else if (P.u <= 16)
+    launch_fbasis_block_form<16>(P, n, tc);
+  else
+    launch_fbasis_block_form<32>(P, n, tc);
+  smem_limit(k_fbasis<true, 32>, tiles_bytes(3, 32, 32), done);
+  k_fbasis<true, 32><<<blocks_for(n), 32 * kWarps, tiles_bytes(3, tc, 32), P.stream>>>(P.M, P.items, n, P.u, tc,
+                                                                                      P.A, P.B, P.IB, P.BW);
 }
 
 }  // namespace h2

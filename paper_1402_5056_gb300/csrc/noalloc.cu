@@ -66,7 +66,12 @@ constexpr size_t kOffCopy = kOffCl + align256(2ull * kNaClusters * 4);
 constexpr size_t kOffNear = kOffCopy + align256((size_t)(2 * kNaItems + kNaTasks) * sizeof(CopyDesc));
 constexpr size_t kOffNeed = kOffNear + align256((size_t)kNaNear * sizeof(NearDesc));    // 2 sides
 constexpr size_t kOffFail = kOffNeed + align256(2ull * kNaClusters * 4);
-constexpr size_t kScratchBytes = kOffFail + align256(4);
+constexpr size_t kOffOrth = kOffFail + align256(4);                                       // 2 sides
+constexpr size_t kScratchBytes = kOffOrth + align256(2ull * kNaClusters * 4);
+// The Gram matrices V_t^* V_t of the unchanged bases (2 sides x 512 slots)
+// live in the coupling-output region: they are dead before the
+// reprojection writes its results there.
+static_assert(2ull * kNaClusters * kSlot * 8 <= (size_t)kNaTasks * kSlot * 8, "basis Grams exceed their region");
 static_assert(kScratchBytes <= (48u << 20), "scratch above its stated 48 MiB");
 
 static __device__ __align__(256) unsigned char h2_noalloc_scratch[kScratchBytes];
@@ -311,6 +316,8 @@ h2_status run(h2_ctx* ctx, h2_matrix* Z, int32_t b0, int u, const double* A, int
     BW.Wo[sd] = BW.G[sd];
     BW.W0[sd] = BW.B[sd];
     BW.need[sd] = reinterpret_cast<int32_t*>(base + kOffNeed) + (size_t)sd * kNaClusters;
+    BW.Vg[sd] = reinterpret_cast<double*>(base + kOffS) + (size_t)sd * kNaClusters * kSlot;
+    BW.orth[sd] = reinterpret_cast<int32_t*>(base + kOffOrth) + (size_t)sd * kNaClusters;
   }
   MatView M;
   for (int sd = 0; sd < 2; ++sd) {
@@ -324,6 +331,8 @@ h2_status run(h2_ctx* ctx, h2_matrix* Z, int32_t b0, int u, const double* A, int
   M.father[1] = Z->d_father_c;
   M.subtree[0] = Z->d_subtree_r;
   M.subtree[1] = Z->d_subtree_c;
+  M.size[0] = Z->d_row_size;
+  M.size[1] = Z->d_col_size;
   M.S = Z->d_S;
   M.kcap = Z->kcap;
   // the same kernels as the allocating path, on the fixed scratch
@@ -363,6 +372,8 @@ h2_status run(h2_ctx* ctx, h2_matrix* Z, int32_t b0, int u, const double* A, int
   pp.side = nullptr;
   pp.fork = nullptr;
   pp.join = nullptr;
+  pp.side2 = nullptr;
+  pp.join2 = nullptr;
   pp.events = nullptr;
   pp.phase_launches = nullptr;
   run_pipeline(pp);

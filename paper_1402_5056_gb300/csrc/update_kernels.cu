@@ -1042,15 +1042,20 @@ __global__ void k_truncate(MatView M, const Item* __restrict__ items, const int3
 
 // ------------------------------------------------------------- step 5
 // Reprojection S_b <- R_t S~_b R_s^* for every affected admissible block.
-__global__ void k_reproject(MatView M, const Item* __restrict__ items, const Task* __restrict__ tasks,
-                            int n, int u, ItemBuffers IB) {
-  const int lane = threadIdx.x & 31;
-  const int idx = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (idx >= n) return;
-  const Task tk = tasks[idx];
+//
+// Updates of the certified path have R_t = L_t^* upper triangular: the
+// products run over the triangle only, with the 32 lanes spread over the
+// entries of the result so that the lanes of one instruction share the
+// row (left factor) or the column (right factor) and with it the length of
+// the triangular sum.  Operands are staged in shared memory and the result
+// leaves through it in coalesced columns.  Updates of the exact path have a
+// general r_t x K_t factor and use one lane per column.
+constexpr int kRpLd = 33;   // leading dimension of the tiles (up to 32 rows); 3 tiles per warp of tc columns
+
+__device__ __forceinline__ void reproject_general(const MatView& M, const Item* __restrict__ items, const Task& tk,
+                                                  int u, const ItemBuffers& IB, const double* S, double* out,
+                                                  int lane) {
   const int kcap = M.kcap;
-  const double* S = M.S + (size_t)tk.slot * kcap * kcap;
-  double* out = IB.S_out + (size_t)idx * kSlot;
   if (tk.it >= 0 && tk.is >= 0) {
     const int kt = items[tk.it].k, ls = items[tk.is].k;
     const int Kt = kt + u;
@@ -1102,6 +1107,169 @@ __global__ void k_reproject(MatView M, const Item* __restrict__ items, const Tas
   }
 }
 
+__device__ __forceinline__ void reproject_task(const MatView& M, const Item* __restrict__ items, const Task& tk,
+                                               int idx, int u, int tc, const BaseWeights& BW, const ItemBuffers& IB,
+                                               double* smem, int w, int lane) {
+  const int kcap = M.kcap;
+  const double* S = M.S + (size_t)tk.slot * kcap * kcap;
+  double* out = IB.S_out + (size_t)idx * kSlot;
+  const int upd = items[tk.it >= 0 ? tk.it : tk.is].update;
+  if (IB.fail[upd]) {
+    reproject_general(M, items, tk, u, IB, S, out, lane);
+    return;
+  }
+  double* X = smem + (size_t)w * 3 * kRpLd * tc;   // S (k_t x l_s), later T
+  double* R = X + kRpLd * tc;                       // triangular factor
+  double* O = R + kRpLd * tc;                       // result
+  int rows = 0, cols = 0;                    // size of the result
+  if (tk.it >= 0 && tk.is >= 0) {
+    const int kt = items[tk.it].k, ls = items[tk.is].k;
+    const int Kt = kt + u, Ks = ls + u;
+    rows = Kt;
+    cols = Ks;
+    for (int c = 0; c < ls; ++c)
+      if (lane < kt) X[lane + c * kRpLd] = S[lane + c * kcap];
+    const double* Rs = IB.Rt + (size_t)tk.is * kSlot;
+    for (int c = 0; c < Ks; ++c)
+      if (lane <= c) R[lane + c * kRpLd] = Rs[lane + c * 32];
+    __syncwarp();
+    // T = S~ R_s^* (Kt x Ks), column-major over the lanes: rows i < kt sum
+    // S[i][q] R_s[j][q] over q = j..ls-1; rows i >= kt pick R_s[j][ls + i - kt]
+    for (int e = lane; e < Kt * Ks; e += 32) {
+      const int i = e % Kt, j = e / Kt;
+      double v = 0.0;
+      if (i < kt) {
+        for (int q = j; q < ls; ++q) v = fma(X[i + q * kRpLd], R[j + q * kRpLd], v);
+      } else {
+        const int q = ls + i - kt;
+        v = q >= j ? R[j + q * kRpLd] : 0.0;
+      }
+      O[i + j * kRpLd] = v;
+    }
+    __syncwarp();
+    const double* Rt = IB.Rt + (size_t)tk.it * kSlot;
+    for (int c = 0; c < Kt; ++c)
+      if (lane <= c) R[lane + c * kRpLd] = Rt[lane + c * 32];
+    for (int c = 0; c < Ks; ++c)
+      if (lane < Kt) X[lane + c * kRpLd] = O[lane + c * kRpLd];
+    __syncwarp();
+    // out = R_t T, row-major over the lanes: sum over i = p..Kt-1
+    for (int e = lane; e < Kt * Ks; e += 32) {
+      const int p = e / Ks, j = e % Ks;
+      double v = 0.0;
+      for (int i = p; i < Kt; ++i) v = fma(R[p + i * kRpLd], X[i + j * kRpLd], v);
+      O[p + j * kRpLd] = v;
+    }
+  } else if (tk.it >= 0) {
+    // R_t [S_b; 0]: rows p < kt sum over i = p..kt-1, rows kt.. are zero;
+    // R_t = [[I, C_t], [0, L_S^*]] for an orthonormal V_t gives [S_b; 0]
+    const Item it = items[tk.it];
+    const int kt = it.k, ls = tk.ls;
+    rows = kt + u;
+    cols = ls;
+    if (BW.orth[0][it.cluster]) return;   // a copy: k_recopy
+    for (int c = 0; c < ls; ++c)
+      if (lane < kt) X[lane + c * kRpLd] = S[lane + c * kcap];
+    const double* Rt = IB.Rt + (size_t)tk.it * kSlot;
+    for (int c = 0; c < kt; ++c)
+      if (lane <= c) R[lane + c * kRpLd] = Rt[lane + c * 32];
+    __syncwarp();
+    for (int e = lane; e < kt * ls; e += 32) {
+      const int p = e / ls, j = e % ls;
+      double v = 0.0;
+      for (int i = p; i < kt; ++i) v = fma(R[p + i * kRpLd], X[i + j * kRpLd], v);
+      O[p + j * kRpLd] = v;
+    }
+    for (int c = 0; c < ls; ++c)
+      if (lane >= kt && lane < rows) O[lane + c * kRpLd] = 0.0;
+  } else {
+    // [S_b, 0] R_s^*: columns j < ls sum over q = j..ls-1, columns ls.. are
+    // zero; [S_b, 0] for an orthonormal W_s
+    const Item is = items[tk.is];
+    const int kt = tk.kt, ls = is.k;
+    rows = kt;
+    cols = ls + u;
+    if (BW.orth[1][is.cluster]) return;   // a copy: k_recopy
+    for (int c = 0; c < ls; ++c)
+      if (lane < kt) X[lane + c * kRpLd] = S[lane + c * kcap];
+    const double* Rs = IB.Rt + (size_t)tk.is * kSlot;
+    for (int c = 0; c < ls; ++c)
+      if (lane <= c) R[lane + c * kRpLd] = Rs[lane + c * 32];
+    __syncwarp();
+    for (int e = lane; e < kt * ls; e += 32) {
+      const int p = e % kt, j = e / kt;
+      double v = 0.0;
+      for (int q = j; q < ls; ++q) v = fma(X[p + q * kRpLd], R[j + q * kRpLd], v);
+      O[p + j * kRpLd] = v;
+    }
+    for (int c = ls; c < cols; ++c)
+      if (lane < kt) O[lane + c * kRpLd] = 0.0;
+  }
+  __syncwarp();
+  for (int c = 0; c < cols; ++c)
+    if (lane < rows) out[lane + c * 32] = O[lane + c * kRpLd];
+}
+
+// Persistent warps: warp g takes tasks g, g + G, ... (G warps in the grid),
+// so that the launch does not pay for one block per (often trivial) task.
+__global__ void k_reproject(MatView M, const Item* __restrict__ items, const Task* __restrict__ tasks,
+                            int n, int u, int tc, BaseWeights BW, ItemBuffers IB) {
+  extern __shared__ double smem[];
+  const int lane = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5;
+  const int G = gridDim.x * (blockDim.x >> 5);
+  for (int idx = blockIdx.x * (blockDim.x >> 5) + w; idx < n; idx += G) {
+    const Task tk = tasks[idx];
+    reproject_task(M, items, tk, idx, u, tc, BW, IB, smem, w, lane);
+    __syncwarp();
+  }
+}
+
+// The one-sided reprojections of certified updates with an orthonormal basis
+// are copies: R_t [S_b; 0] = [S_b; 0] and [S_b, 0] R_s^* = [S_b, 0], since
+// R_t = [[I, C_t], [0, L_S^*]].  One warp per block, all loads of the block
+// issued before its stores; no shared memory, so that many warps keep loads
+// in flight.
+constexpr int kCopyWarps = 8;
+
+__global__ void k_recopy(MatView M, const Item* __restrict__ items, const Task* __restrict__ tasks, int n, int u,
+                         BaseWeights BW, ItemBuffers IB) {
+  const int lane = threadIdx.x & 31;
+  const int G = gridDim.x * (blockDim.x >> 5);
+  for (int idx = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); idx < n; idx += G) {
+  const Task tk = tasks[idx];
+  if (tk.it >= 0 && tk.is >= 0) continue;
+  const int side = tk.it >= 0 ? 0 : 1;
+  const Item it = items[side == 0 ? tk.it : tk.is];
+  if (IB.fail[it.update] || !pick(BW.orth, side)[it.cluster]) continue;
+  const int kcap = M.kcap;
+  const double* S = M.S + (size_t)tk.slot * kcap * kcap;
+  double* out = IB.S_out + (size_t)idx * kSlot;
+  const int rows = side == 0 ? tk.kt + u : tk.kt;
+  const int cols = side == 0 ? tk.ls : tk.ls + u;
+  const int nel = rows * cols;
+  // chunks of 12 entries per lane (384 per warp), loads before stores
+  for (int base = 0; base < nel; base += 12 * 32) {
+    double v[12];
+#pragma unroll
+    for (int s = 0; s < 12; ++s) {
+      const int e = base + lane + 32 * s;
+      double x = 0.0;
+      if (e < nel) {
+        const int r = e % rows, c = e / rows;
+        if (r < tk.kt && c < tk.ls) x = S[r + (size_t)c * kcap];
+      }
+      v[s] = x;
+    }
+#pragma unroll
+    for (int s = 0; s < 12; ++s) {
+      const int e = base + lane + 32 * s;
+      if (e < nel) out[e % rows + (e / rows) * 32] = v[s];
+    }
+  }
+  }
+}
+
 // Batched copies of column-major matrices (commit of one update).
 __global__ void k_copy(const CopyDesc* __restrict__ d, int n) {
   const int idx = blockIdx.x;
@@ -1133,6 +1301,18 @@ static constexpr int kWarps = 4;
 static constexpr size_t kFoldSmem = (size_t)kWarps * (32 * kLdr + kCh + 1) * sizeof(double);
 
 static int blocks_for(int n) { return (n + kWarps - 1) / kWarps; }
+
+// Blocks of a persistent launch: as many as stay resident on the device at
+// once (at most `need`).
+template <class Kern>
+static int persistent_blocks(Kern kern, int threads, size_t smem, int need) {
+  int dev = 0, sms = 0, per_sm = 0;
+  H2_CUDA(cudaGetDevice(&dev));
+  H2_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  H2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
+  const int nb = sms * (per_sm > 0 ? per_sm : 1);
+  return nb < need ? nb : (need > 0 ? need : 1);
+}
 
 template <int MR>
 static void launch_truncate_mr(const MatView& M, const Item* items, const int32_t* list, int n, int u, int kl,
@@ -1188,6 +1368,17 @@ void run_pipeline(const Pipeline& P) {
     // stream, overlapping the basis Grams and the norms
     fork();
     start(H2_PHASE_BASE_WEIGHTS, bs);
+    cudaStream_t vs = bs;   // stream of the basis Grams
+    if (P.side && P.side2) {
+      vs = P.side2;
+      H2_CUDA(cudaStreamWaitEvent(vs, P.fork, 0));
+    }
+    for (int l = L - 1; l >= 0; --l)
+      if (P.cl_ptr[l + 1] > P.cl_ptr[l]) {
+        launch_gram_vbasis_level(P, l, vs);
+        ++pl[H2_PHASE_BASE_WEIGHTS];
+      }
+    if (vs != bs) H2_CUDA(cudaEventRecord(P.join2, vs));
     if (ncl > 0) {
       launch_gram_base(P, bs);
       ++pl[H2_PHASE_BASE_WEIGHTS];
@@ -1197,6 +1388,7 @@ void run_pipeline(const Pipeline& P) {
         launch_gram_base_level(P, l, bs);
         ++pl[H2_PHASE_BASE_WEIGHTS];
       }
+    if (vs != bs) H2_CUDA(cudaStreamWaitEvent(bs, P.join2, 0));
     stop(H2_PHASE_BASE_WEIGHTS, bs);
     if (P.side) H2_CUDA(cudaEventRecord(P.join, P.side));
     start(H2_PHASE_RFACTOR, st);
@@ -1206,13 +1398,13 @@ void run_pipeline(const Pipeline& P) {
         ++pl[H2_PHASE_RFACTOR];
       }
     stop(H2_PHASE_RFACTOR, st);
+    if (P.side) H2_CUDA(cudaStreamWaitEvent(st, P.join, 0));
     start(H2_PHASE_NORMS, st);
     if (P.n_norms > 0) {
       launch_gram_norms(P);
       ++pl[H2_PHASE_NORMS];
     }
     stop(H2_PHASE_NORMS, st);
-    if (P.side) H2_CUDA(cudaStreamWaitEvent(st, P.join, 0));
     start(H2_PHASE_WEIGHTS, st);
     for (int l = 0; l < L; ++l)
       if (P.lvl_ptr[l + 1] > P.lvl_ptr[l]) {
@@ -1279,8 +1471,25 @@ void run_pipeline(const Pipeline& P) {
   // step 5: reprojection
   start(H2_PHASE_REPROJECT, st);
   if (P.n_tasks > 0) {
-    k_reproject<<<blocks_for(P.n_tasks), 32 * kWarps, 0, st>>>(P.M, P.items, P.tasks, P.n_tasks, P.u, P.IB);
+    const int tc = P.kl > P.M.kcap ? P.kl : P.M.kcap;
+    static unsigned long long attr = 0;
+    int dev = 0;
+    H2_CUDA(cudaGetDevice(&dev));
+    if (dev >= 64 || !((attr >> dev) & 1ull)) {
+      H2_CUDA(cudaFuncSetAttribute(k_reproject, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   kWarps * 3 * kRpLd * 32 * (int)sizeof(double)));
+      if (dev < 64) attr |= 1ull << dev;
+    }
+    const size_t rp_smem = (size_t)kWarps * 3 * kRpLd * tc * sizeof(double);
+    k_reproject<<<persistent_blocks(k_reproject, 32 * kWarps, rp_smem, blocks_for(P.n_tasks)), 32 * kWarps, rp_smem,
+                  st>>>(P.M, P.items, P.tasks, P.n_tasks, P.u, tc, P.BW, P.IB);
     ++pl[H2_PHASE_REPROJECT];
+    if (!P.exact_only) {
+      const int nb = (P.n_tasks + kCopyWarps - 1) / kCopyWarps;
+      k_recopy<<<persistent_blocks(k_recopy, 32 * kCopyWarps, 0, nb), 32 * kCopyWarps, 0, st>>>(
+          P.M, P.items, P.tasks, P.n_tasks, P.u, P.BW, P.IB);
+      ++pl[H2_PHASE_REPROJECT];
+    }
   }
   stop(H2_PHASE_REPROJECT, st);
   H2_CUDA(cudaGetLastError());

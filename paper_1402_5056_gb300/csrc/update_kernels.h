@@ -62,6 +62,10 @@ struct Pipeline {
   // required when side != nullptr
   cudaStream_t side;
   cudaEvent_t fork, join;
+  // optional third stream for the basis Grams V_t^* V_t of the unchanged
+  // matrix, which run beside the weights on `side` (join2 required with it)
+  cudaStream_t side2;
+  cudaEvent_t join2;
   cudaEvent_t* events;          // 2 * H2_PHASE_COUNT events (start, end per phase) or nullptr
   int64_t* phase_launches;      // host, H2_PHASE_COUNT entries or nullptr
 };
@@ -73,6 +77,7 @@ struct Pipeline {
 void run_pipeline(const Pipeline& P);
 
 // Certified Gram path (gram_kernels.cu).
+void launch_gram_vbasis_level(const Pipeline& P, int level, cudaStream_t st);  // V_t^* V_t, one level
 void launch_gram_base(const Pipeline& P, cudaStream_t st);               // Wo, all clusters
 void launch_gram_base_level(const Pipeline& P, int level, cudaStream_t st);  // W0, one level
 void launch_gram_basis(const Pipeline& P, int level);                    // G_t, one level

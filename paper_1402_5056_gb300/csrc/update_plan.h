@@ -66,7 +66,9 @@ struct MatView {
   const int64_t* leaf_off[2];
   const int32_t* rank[2];
   const int32_t* father[2];
-  const int32_t* subtree[2];
+  const int32_t* subtree[2];   // clusters in the subtree (1 for leaves; sons of c: c + 1 and
+                               // c + 1 + subtree[c + 1], clusters being numbered in preorder)
+  const int32_t* size[2];      // #t
   const double* S;
   int kcap;
 };
@@ -81,6 +83,10 @@ struct BaseWeights {
   double* Wo[2];
   double* W0[2];
   int32_t* need[2];    // per cluster: 1 if the exact path needs G and B of it
+  // Gram matrix V_t^* V_t of every cluster basis of the unchanged matrix and
+  // a flag: 1 when it equals the identity within 1e-13 (orthonormal basis)
+  double* Vg[2];
+  int32_t* orth[2];
 };
 
 // Per-item workspace and outputs; every matrix slot is 32 x 32, ld 32.

@@ -185,3 +185,50 @@ def test_certified_leaf_bases_orthonormal_and_spanning(ctx):
             b.h2_batch_free(P)
     finally:
         b.h2_matrix_free(Zl)
+
+
+def test_certified_path_on_non_orthonormal_bases(ctx):
+    """A truncating update leaves the ancestors of its row cluster with
+    non-orthonormal bases (E_t0 <- R_t0 [E_t0; 0]); a later update without
+    truncation on a block above it runs the certified path with the general
+    (non-block) Gram formulas for those clusters and still matches the oracle
+    applied to the library's state."""
+    N, leaf, k, u = 32, 16, 6, 3
+    Zo, st, _ = oracle_problem(N, k, 341, leaf)
+    Zl, _, _ = lib_problem(ctx, N, k, 341, leaf)
+    bt = Zo.blocks
+    tree = Zo.V.tree
+    adm = list(bt.admissible)
+    deep = max(adm, key=lambda c: tree.level[bt.row[c]])
+    anc = set(tree.predecessors(bt.row[deep])[:-1])
+    above = [c for c in adm if bt.row[c] in anc]
+    assert above
+    high = min(above, key=lambda c: tree.level[bt.row[c]])
+    rng = np.random.default_rng(5)
+    try:
+        for b0, eps, want_exact in ((deep, 0.5, 1), (high, 1e-8, 0)):
+            A = rng.standard_normal((tree.size[bt.row[b0]], u))
+            B = rng.standard_normal((Zo.W.tree.size[bt.col[b0]], u))
+            before = to_oracle(ctx, Zl, Zo)
+            d = local_update(before, b0, A, B, eps)
+            ref = apply_delta(before, d).dense()
+            P, dA, dB = _batch(ctx, Zl, [b0], [A], [B], u, eps, b.MODE_AUTO)
+            try:
+                assert b.h2_batch_paths(ctx, P, 1)[0] == want_exact, (b0, eps)
+                if not want_exact:
+                    # some cluster of the update has a non-orthonormal basis
+                    first, last = b.h2_batch_update_items(P, 0)
+                    dev = 0.0
+                    for item in range(first, last):
+                        info = b.h2_batch_item_info(P, item)
+                        kk = info["k"]
+                        G = b.h2_batch_item_tile(ctx, P, item, 0)[:kk, :kk]
+                        dev = max(dev, float(np.abs(G - np.eye(kk)).max()) if kk else 0.0)
+                    assert dev > 1e-10, dev
+                b.h2_batch_apply(ctx, P, 0, dA.data_ptr(), dB.data_ptr(), Zl)
+            finally:
+                b.h2_batch_free(P)
+            got = to_oracle(ctx, Zl, Zo).dense()
+            assert np.linalg.norm(got - ref) <= TOL * np.linalg.norm(ref), (b0, eps)
+    finally:
+        b.h2_matrix_free(Zl)
