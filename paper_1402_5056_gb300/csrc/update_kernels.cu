@@ -1416,7 +1416,7 @@ void run_pipeline(const Pipeline& P) {
     if (ni > 0) {
       launch_gram_certify(P);
       launch_gram_outputs(P);
-      pl[H2_PHASE_TRUNCATE] += 2;
+      pl[H2_PHASE_TRUNCATE] += 4;   // block-form and general variants of both kernels
     }
     stop(H2_PHASE_TRUNCATE, st);
   }
