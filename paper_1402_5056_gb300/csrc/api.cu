@@ -702,6 +702,10 @@ struct h2_batch {
   Entry* d_ents = nullptr;
   Task* d_tasks = nullptr;
   NormTask* d_norms = nullptr;
+  int32_t* d_two = nullptr;      // two-sided coupling tasks
+  int32_t* d_left = nullptr;     // one-sided tasks that need products (device-built)
+  int32_t* d_nleft = nullptr;
+  std::vector<int32_t> two;
   int32_t* d_lvl = nullptr;
   int32_t* d_cl = nullptr;
   ItemBuffers IB{};
@@ -904,6 +908,12 @@ void alloc_batch(h2_ctx* ctx, h2_batch& P) {
   P.d_items = upload(P.items, st);
   P.d_ents = upload(P.ents, st);
   P.d_tasks = upload(P.tasks, st);
+  P.two.clear();
+  for (size_t t = 0; t < P.tasks.size(); ++t)
+    if (P.tasks[t].it >= 0 && P.tasks[t].is >= 0) P.two.push_back((int32_t)t);
+  P.d_two = upload(P.two, st);
+  P.d_left = dalloc<int32_t>(P.tasks.size());
+  P.d_nleft = dalloc<int32_t>(1);
   P.d_norms = upload(P.norms, st);
   P.d_lvl = upload(P.lvl_list, st);
   P.d_cl = upload(P.cl_list, st);
@@ -952,6 +962,9 @@ void free_batch_device(h2_batch& P) {
   dfree(P.d_items);
   dfree(P.d_ents);
   dfree(P.d_tasks);
+  dfree(P.d_two);
+  dfree(P.d_left);
+  dfree(P.d_nleft);
   dfree(P.d_norms);
   dfree(P.d_lvl);
   dfree(P.d_cl);
@@ -1010,6 +1023,10 @@ void execute(h2_ctx* ctx, h2_batch& P, const double* A, const double* B, double 
   pp.ncl[1] = Z->cols.count();
   pp.exact_only = P.mode == H2_MODE_EXACT ? 1 : 0;
   pp.n_tasks = (int)P.tasks.size();
+  pp.two = P.d_two;
+  pp.n_two = (int)P.two.size();
+  pp.left = P.d_left;
+  pp.n_left = P.d_nleft;
   pp.n_norms = (int)P.norms.size();
   pp.u = P.u;
   pp.kl = P.kl;
@@ -1397,9 +1414,11 @@ void phase_flops(h2_ctx* ctx, const h2_batch* P, double f[H2_PHASE_COUNT]) {
       // certificate matrix) and new bases; block formulas for an orthonormal V_t
       const bool ob = orth[it.side][it.cluster] != 0;
       if (ob) {
-        double c2 = 2 * tri(k) * u;
+        // S = N - C^* C, LDL^*(S); Y = W21 + W22 C^*, Z = W22 L_S; C2_11 =
+        // W11 + W12 C^* + C Y, C2_21 = L_S^* Y, C2_22 = L_S^* Z; LDL^*(C2)
+        double c2 = 4 * tri(k) * u;
         for (double a = 0; a < u; a += 1) c2 += 2 * (k + a + 1) * (u - a);
-        f[H2_PHASE_TRUNCATE] += 2 * tri(u) * k + ldl(u) + 2 * K * k * u + 2 * K * tri(u) + c2 + ldl(K);
+        f[H2_PHASE_TRUNCATE] += 2 * tri(u) * k + ldl(u) + 2 * u * k * u + 2 * u * tri(u) + c2 + ldl(K);
       } else {
         f[H2_PHASE_TRUNCATE] += 2 * ldl(K) + 2 * K * tri(K) + (K * K * K + 3 * K * K + 2 * K) / 3;
       }

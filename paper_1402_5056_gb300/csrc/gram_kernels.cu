@@ -834,33 +834,35 @@ __global__ void k_certify(const Item* __restrict__ items, int n, int u, int ld, 
     ok = trG > 0.0 && trW > 0.0 && trG * trW < DBL_MAX && ldl<true>(Sb, ld, u, 0.0, lv, lane);
     if (ok) {
       ldl_to_cholesky(Sb, ld, u, dsq, lane);
-      // T2 = W L, L = [[I, 0], [C^*, L_S]]
-      for (int e = lane; e < K * K; e += 32) {
-        const int i = e % K, j = e / K;
+      // C2 = L^* W L with L = [[I, 0], [C^*, L_S]], blockwise:
+      //   Y = W21 + W22 C^* (u x k), Z = W22 L_S (u x u) into T2, then over W
+      //   C2_11 = W11 + W12 C^* + C Y, C2_21 = L_S^* Y, C2_22 = L_S^* Z
+      for (int e = lane; e < u * K; e += 32) {
+        const int a = e % u, j = e / u;
         double v;
         if (j < k) {
-          v = T1[i + j * ld];
-          for (int q = 0; q < u; ++q) v = fma(T1[i + (k + q) * ld], T0[j + q * ld], v);
+          v = T1[(k + a) + j * ld];
+          for (int q = 0; q < u; ++q) v = fma(T1[(k + a) + (k + q) * ld], T0[j + q * ld], v);
         } else {
           const int b = j - k;
           v = 0.0;
-          for (int a = b; a < u; ++a) v = fma(T1[i + (k + a) * ld], Sb[a + b * ld], v);
+          for (int p = b; p < u; ++p) v = fma(T1[(k + a) + (k + p) * ld], Sb[p + b * ld], v);
         }
-        T2[i + j * ld] = v;
+        T2[a + j * ld] = v;
       }
       __syncwarp();
-      // C2 = L^* T2 (lower triangle) over W
       for (int e = lane; e < tri(K); e += 32) {
         int i, j;
         tri_index(e, i, j);
         double v;
         if (i < k) {
-          v = T2[i + j * ld];
-          for (int q = 0; q < u; ++q) v = fma(T0[i + q * ld], T2[(k + q) + j * ld], v);
+          v = T1[i + j * ld];
+          for (int q = 0; q < u; ++q) v = fma(T1[i + (k + q) * ld], T0[j + q * ld], v);
+          for (int q = 0; q < u; ++q) v = fma(T0[i + q * ld], T2[q + j * ld], v);
         } else {
           const int a = i - k;
           v = 0.0;
-          for (int q = a; q < u; ++q) v = fma(Sb[q + a * ld], T2[(k + q) + j * ld], v);
+          for (int q = a; q < u; ++q) v = fma(Sb[q + a * ld], T2[q + j * ld], v);
         }
         T1[i + j * ld] = v;
       }
@@ -1212,12 +1214,17 @@ void launch_gram_certify(const Pipeline& P) {
                                                                                       P.levels, P.eps, P.BW, P.IB);
 }
 
+// two warps per block: the per-warp tiles, not the block size, limit the
+// warps per SM, and smaller blocks pack the shared memory more tightly
+constexpr int kFbWarps = 2;
+
 template <int UMAX>
 void launch_fbasis_block_form(const Pipeline& P, int n, int tc) {
   static unsigned long long done = 0;
-  smem_limit(k_fbasis<false, UMAX>, tiles_bytes(3, 32, 32), done);
-  k_fbasis<false, UMAX><<<blocks_for(n), 32 * kWarps, tiles_bytes(3, tc, 32), P.stream>>>(P.M, P.items, n, P.u, tc,
-                                                                                         P.A, P.B, P.IB, P.BW);
+  const size_t bytes = (size_t)kFbWarps * (3 * kLd * tc + 32) * sizeof(double);
+  smem_limit(k_fbasis<false, UMAX>, (size_t)kFbWarps * (3 * kLd * 32 + 32) * sizeof(double), done);
+  k_fbasis<false, UMAX><<<(n + kFbWarps - 1) / kFbWarps, 32 * kFbWarps, bytes, P.stream>>>(P.M, P.items, n, P.u,
+                                                                                          tc, P.A, P.B, P.IB, P.BW);
 }
 
 void launch_gram_outputs(const Pipeline& P) {

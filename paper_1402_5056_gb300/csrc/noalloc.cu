@@ -67,7 +67,10 @@ constexpr size_t kOffNear = kOffCopy + align256((size_t)(2 * kNaItems + kNaTasks
 constexpr size_t kOffNeed = kOffNear + align256((size_t)kNaNear * sizeof(NearDesc));    // 2 sides
 constexpr size_t kOffFail = kOffNeed + align256(2ull * kNaClusters * 4);
 constexpr size_t kOffOrth = kOffFail + align256(4);                                       // 2 sides
-constexpr size_t kScratchBytes = kOffOrth + align256(2ull * kNaClusters * 4);
+constexpr size_t kOffTwo = kOffOrth + align256(2ull * kNaClusters * 4);
+constexpr size_t kOffLeft = kOffTwo + align256((size_t)kNaTasks * 4);
+constexpr size_t kOffNLeft = kOffLeft + align256((size_t)kNaTasks * 4);
+constexpr size_t kScratchBytes = kOffNLeft + align256(4);
 // The Gram matrices V_t^* V_t of the unchanged bases (2 sides x 512 slots)
 // live in the coupling-output region: they are dead before the
 // reprojection writes its results there.
@@ -96,6 +99,8 @@ struct HostPlan {
   int32_t sub[2][kNaClusters];
   int32_t nsub[2];
   int32_t rank[kNaItems];
+  int32_t two[kNaTasks];
+  int n_two;
   CopyDesc copies[2 * kNaItems + kNaTasks];
   NearDesc nears[kNaNear];
   int32_t bstack[4 * kNaNear + 64];
@@ -289,6 +294,11 @@ h2_status run(h2_ctx* ctx, h2_matrix* Z, int32_t b0, int u, const double* A, int
   NA_CUDA(cudaMemcpyAsync(d_items, P.items, P.n_items * sizeof(Item), cudaMemcpyHostToDevice, s));
   if (P.n_ents) NA_CUDA(cudaMemcpyAsync(d_ents, P.ents, P.n_ents * sizeof(Entry), cudaMemcpyHostToDevice, s));
   if (P.n_tasks) NA_CUDA(cudaMemcpyAsync(d_tasks, P.tasks, P.n_tasks * sizeof(Task), cudaMemcpyHostToDevice, s));
+  P.n_two = 0;
+  for (int t = 0; t < P.n_tasks; ++t)
+    if (P.tasks[t].it >= 0 && P.tasks[t].is >= 0) P.two[P.n_two++] = t;
+  int32_t* d_two = reinterpret_cast<int32_t*>(base + kOffTwo);
+  if (P.n_two) NA_CUDA(cudaMemcpyAsync(d_two, P.two, P.n_two * sizeof(int32_t), cudaMemcpyHostToDevice, s));
   if (P.n_norms) NA_CUDA(cudaMemcpyAsync(d_nt, P.norms, P.n_norms * sizeof(NormTask), cudaMemcpyHostToDevice, s));
   NA_CUDA(cudaMemcpyAsync(d_lvl, P.lvl_list, P.n_items * sizeof(int32_t), cudaMemcpyHostToDevice, s));
   const int L = std::max(Z->rows.depth, Z->cols.depth) + 1;
@@ -361,6 +371,10 @@ h2_status run(h2_ctx* ctx, h2_matrix* Z, int32_t b0, int u, const double* A, int
   pp.ncl[1] = Z->cols.count();
   pp.exact_only = 0;
   pp.n_tasks = P.n_tasks;
+  pp.two = d_two;
+  pp.n_two = P.n_two;
+  pp.left = reinterpret_cast<int32_t*>(base + kOffLeft);
+  pp.n_left = reinterpret_cast<int32_t*>(base + kOffNLeft);
   pp.n_norms = P.n_norms;
   pp.u = u;
   pp.kl = P.kl;

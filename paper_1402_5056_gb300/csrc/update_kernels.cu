@@ -1167,7 +1167,6 @@ __device__ __forceinline__ void reproject_task(const MatView& M, const Item* __r
     const int kt = it.k, ls = tk.ls;
     rows = kt + u;
     cols = ls;
-    if (BW.orth[0][it.cluster]) return;   // a copy: k_recopy
     for (int c = 0; c < ls; ++c)
       if (lane < kt) X[lane + c * kRpLd] = S[lane + c * kcap];
     const double* Rt = IB.Rt + (size_t)tk.it * kSlot;
@@ -1189,7 +1188,6 @@ __device__ __forceinline__ void reproject_task(const MatView& M, const Item* __r
     const int kt = tk.kt, ls = is.k;
     rows = kt;
     cols = ls + u;
-    if (BW.orth[1][is.cluster]) return;   // a copy: k_recopy
     for (int c = 0; c < ls; ++c)
       if (lane < kt) X[lane + c * kRpLd] = S[lane + c * kcap];
     const double* Rs = IB.Rt + (size_t)tk.is * kSlot;
@@ -1210,15 +1208,19 @@ __device__ __forceinline__ void reproject_task(const MatView& M, const Item* __r
     if (lane < rows) out[lane + c * 32] = O[lane + c * kRpLd];
 }
 
-// Persistent warps: warp g takes tasks g, g + G, ... (G warps in the grid),
-// so that the launch does not pay for one block per (often trivial) task.
+// The two-sided tasks (list from the host) and the one-sided tasks that
+// k_recopy did not copy (list built on the device), with persistent warps:
+// warp g takes entries g, g + G, ... (G warps in the grid).
 __global__ void k_reproject(MatView M, const Item* __restrict__ items, const Task* __restrict__ tasks,
-                            int n, int u, int tc, BaseWeights BW, ItemBuffers IB) {
+                            const int32_t* __restrict__ two, int n_two, const int32_t* __restrict__ left,
+                            const int32_t* __restrict__ n_left, int u, int tc, BaseWeights BW, ItemBuffers IB) {
   extern __shared__ double smem[];
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
   const int G = gridDim.x * (blockDim.x >> 5);
-  for (int idx = blockIdx.x * (blockDim.x >> 5) + w; idx < n; idx += G) {
+  const int n = n_two + *n_left;
+  for (int e = blockIdx.x * (blockDim.x >> 5) + w; e < n; e += G) {
+    const int idx = e < n_two ? two[e] : left[e - n_two];
     const Task tk = tasks[idx];
     reproject_task(M, items, tk, idx, u, tc, BW, IB, smem, w, lane);
     __syncwarp();
@@ -1233,40 +1235,34 @@ __global__ void k_reproject(MatView M, const Item* __restrict__ items, const Tas
 constexpr int kCopyWarps = 8;
 
 __global__ void k_recopy(MatView M, const Item* __restrict__ items, const Task* __restrict__ tasks, int n, int u,
-                         BaseWeights BW, ItemBuffers IB) {
+                         BaseWeights BW, ItemBuffers IB, int32_t* __restrict__ left, int32_t* __restrict__ n_left) {
   const int lane = threadIdx.x & 31;
   const int G = gridDim.x * (blockDim.x >> 5);
-  for (int idx = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); idx < n; idx += G) {
-  const Task tk = tasks[idx];
-  if (tk.it >= 0 && tk.is >= 0) continue;
-  const int side = tk.it >= 0 ? 0 : 1;
-  const Item it = items[side == 0 ? tk.it : tk.is];
-  if (IB.fail[it.update] || !pick(BW.orth, side)[it.cluster]) continue;
   const int kcap = M.kcap;
-  const double* S = M.S + (size_t)tk.slot * kcap * kcap;
-  double* out = IB.S_out + (size_t)idx * kSlot;
-  const int rows = side == 0 ? tk.kt + u : tk.kt;
-  const int cols = side == 0 ? tk.ls : tk.ls + u;
-  const int nel = rows * cols;
-  // chunks of 12 entries per lane (384 per warp), loads before stores
-  for (int base = 0; base < nel; base += 12 * 32) {
-    double v[12];
-#pragma unroll
-    for (int s = 0; s < 12; ++s) {
-      const int e = base + lane + 32 * s;
-      double x = 0.0;
-      if (e < nel) {
-        const int r = e % rows, c = e / rows;
-        if (r < tk.kt && c < tk.ls) x = S[r + (size_t)c * kcap];
-      }
-      v[s] = x;
+  for (int idx = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); idx < n; idx += G) {
+    const Task tk = tasks[idx];
+    if (tk.it >= 0 && tk.is >= 0) continue;
+    const int side = tk.it >= 0 ? 0 : 1;
+    const Item it = items[side == 0 ? tk.it : tk.is];
+    if (IB.fail[it.update] || !pick(BW.orth, side)[it.cluster]) {
+      if (lane == 0) left[atomicAdd(n_left, 1)] = idx;   // k_reproject computes it
+      continue;
     }
+    const double* S = M.S + (size_t)tk.slot * kcap * kcap;
+    double* out = IB.S_out + (size_t)idx * kSlot;
+    // lane = row; [S_b; 0] (rows kt + u) or [S_b, 0] (columns ls + u)
+    const int rows = side == 0 ? tk.kt + u : tk.kt;
+    const int cols = side == 0 ? tk.ls : tk.ls + u;
+    const bool in_s = lane < tk.kt;
+    for (int c0 = 0; c0 < cols; c0 += 8) {
+      double v[8];
 #pragma unroll
-    for (int s = 0; s < 12; ++s) {
-      const int e = base + lane + 32 * s;
-      if (e < nel) out[e % rows + (e / rows) * 32] = v[s];
+      for (int j = 0; j < 8; ++j) v[j] = (in_s && c0 + j < tk.ls) ? S[lane + (size_t)(c0 + j) * kcap] : 0.0;
+      if (lane < rows)
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (c0 + j < cols) out[lane + (c0 + j) * 32] = v[j];
     }
-  }
   }
 }
 
@@ -1361,6 +1357,7 @@ void run_pipeline(const Pipeline& P) {
   const bool gram = !P.exact_only;
   // per-update path flags and per-cluster marks of the exact path
   if (P.n_updates > 0) H2_CUDA(cudaMemsetAsync(P.IB.fail, gram ? 0 : 1, (size_t)P.n_updates * 4, st));
+  H2_CUDA(cudaMemsetAsync(P.n_left, 0, sizeof(int32_t), st));
   for (int sd = 0; sd < 2; ++sd)
     if (P.ncl[sd] > 0) H2_CUDA(cudaMemsetAsync(P.BW.need[sd], gram ? 0 : 1, (size_t)P.ncl[sd] * 4, st));
   if (gram) {
@@ -1480,16 +1477,14 @@ void run_pipeline(const Pipeline& P) {
                                    kWarps * 3 * kRpLd * 32 * (int)sizeof(double)));
       if (dev < 64) attr |= 1ull << dev;
     }
+    // copies first (they also list the one-sided tasks that need products)
+    const int nb = (P.n_tasks + kCopyWarps - 1) / kCopyWarps;
+    k_recopy<<<persistent_blocks(k_recopy, 32 * kCopyWarps, 0, nb), 32 * kCopyWarps, 0, st>>>(
+        P.M, P.items, P.tasks, P.n_tasks, P.u, P.BW, P.IB, P.left, P.n_left);
     const size_t rp_smem = (size_t)kWarps * 3 * kRpLd * tc * sizeof(double);
     k_reproject<<<persistent_blocks(k_reproject, 32 * kWarps, rp_smem, blocks_for(P.n_tasks)), 32 * kWarps, rp_smem,
-                  st>>>(P.M, P.items, P.tasks, P.n_tasks, P.u, tc, P.BW, P.IB);
-    ++pl[H2_PHASE_REPROJECT];
-    if (!P.exact_only) {
-      const int nb = (P.n_tasks + kCopyWarps - 1) / kCopyWarps;
-      k_recopy<<<persistent_blocks(k_recopy, 32 * kCopyWarps, 0, nb), 32 * kCopyWarps, 0, st>>>(
-          P.M, P.items, P.tasks, P.n_tasks, P.u, P.BW, P.IB);
-      ++pl[H2_PHASE_REPROJECT];
-    }
+                  st>>>(P.M, P.items, P.tasks, P.two, P.n_two, P.left, P.n_left, P.u, tc, P.BW, P.IB);
+    pl[H2_PHASE_REPROJECT] += 2;
   }
   stop(H2_PHASE_REPROJECT, st);
   H2_CUDA(cudaGetLastError());

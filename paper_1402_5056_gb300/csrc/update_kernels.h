@@ -51,6 +51,10 @@ struct Pipeline {
   int ncl[2];                   // clusters per side
   int exact_only;               // 1: every update takes the exact path
   int n_tasks, n_norms;
+  const int32_t* two;           // the two-sided coupling tasks (both clusters inside)
+  int n_two;
+  int32_t* left;                // one-sided tasks that are not copies (filled on the device)
+  int32_t* n_left;              // their number (device)
   int u, kl;
   double eps;
   const double* A;
