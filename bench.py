@@ -32,9 +32,16 @@ if ROOT not in sys.path:
 import synth  # noqa: E402
 
 # kernels behind each phase of h2_batch_phase_stats
-PHASE_KERNELS = {"base_weights": "k_bgram+k_bgram_down", "rfactor": "k_fgram", "norms": "k_fnorms",
-                 "weights": "k_fweights", "truncate": "k_certify+k_fbasis", "reproject": "k_reproject",
-                 "exact": "exact path (k_blockweights..k_truncate)"}
+PHASE_KERNELS = {"base_weights": "k_orth_local+k_vgram+k_bgram+k_bgram_down", "rfactor": "k_fgram",
+                 "norms": "k_fnorms", "weights": "k_fweights", "truncate": "k_certify", "bases": "k_fbasis",
+                 "reproject": "k_recopy+k_reproject", "exact": "exact path (k_blockweights..k_truncate)"}
+
+# DRAM bytes (read + write) per cluster task of the kernels on the critical
+# path, from one ncu capture of each on the 1024-update batch of the same
+# matrix (dram__bytes_read.sum + dram__bytes_write.sum of the launch divided
+# by its cluster tasks); the roofline's `traffic` scales them to one launch
+# of the benchmark batch.  Valid for the kernel versions of this commit.
+TRAFFIC_BYTES_PER_TASK = {"k_fweights": 6126, "k_certify": 11391, "k_fbasis": 15607, "k_fgram": 4082}
 
 METRIC = "H²-LR setup s & low-rank updates/s, mixed vs FP64 GPU at equal ε; % roofline"
 UNIT = "updates/s"
@@ -289,12 +296,18 @@ def main():
         phases[name] = {"launches": ps["launches"], "ms": phase_ms[ph] / args.steps,
                         "gflop": ps["flops"] / 1e9,
                         "tflops": (ps["flops"] / (phase_ms[ph] / args.steps * 1e-3) / 1e12) if phase_ms[ph] > 0 else None}
-    dom = max(phases, key=lambda k: phases[k]["ms"])
+    # dominant kernel on the critical path (the weights of the unchanged matrix
+    # run beside it on side streams; the exact path only returns at once here)
+    dom = max((k for k in phases if k not in ("base_weights", "exact")), key=lambda k: phases[k]["ms"])
     ach = phases[dom]["tflops"]
     n_exact = int(b.h2_batch_paths(ctx, P, len(blocks)).sum())
-    roof = {"bound": "alu", "kernel": PHASE_KERNELS[dom], "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+    kern = PHASE_KERNELS[dom]
+    traffic = None
+    if kern in TRAFFIC_BYTES_PER_TASK and phases[dom]["launches"]:
+        traffic = TRAFFIC_BYTES_PER_TASK[kern] * stats["cluster_tasks"] / phases[dom]["launches"]
+    roof = {"bound": "alu", "kernel": kern, "achieved": ach, "peak": FP64_PEAK_TFLOPS,
             "unit": "TFLOP/s",
-            "frac": (ach / FP64_PEAK_TFLOPS) if ach else None, "traffic": None,
+            "frac": (ach / FP64_PEAK_TFLOPS) if ach else None, "traffic": traffic, "traffic_unit": "bytes per launch",
             "peak_source": FP64_PEAK_SOURCE,
             "launch_ms": phases[dom]["ms"] / max(1, phases[dom]["launches"])}
 

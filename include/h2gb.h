@@ -175,9 +175,9 @@ h2_status h2_batch_apply(h2_ctx* ctx, const h2_batch* batch, int64_t j, const do
 h2_status h2_batch_stats(h2_ctx* ctx, const h2_batch* batch, int64_t* n_cluster_tasks,
                          int64_t* n_block_tasks, int64_t* n_launches, double* flops);
 
-/* Phases of an execution, for h2_batch_phase_stats.  Phases 0-4 are the
- * certified Gram path (every update), phase 5 the exact path (the updates
- * whose certificate failed, see h2_batch_set_mode), phase 6 the
+/* Phases of an execution, for h2_batch_phase_stats.  Phases 0-4 and 7 are
+ * the certified Gram path (every update), phase 6 the exact path (the
+ * updates whose certificate failed, see h2_batch_set_mode), phase 5 the
  * reprojection of every update. */
 typedef enum {
   H2_PHASE_BASE_WEIGHTS = 0,  /* Gram matrices of the weights of the unchanged
@@ -185,13 +185,15 @@ typedef enum {
   H2_PHASE_RFACTOR = 1,       /* step 2: basis Gram matrices R_t^* R_t           */
   H2_PHASE_NORMS = 2,         /* ||Z~|_b||_F of the blocks inside the update     */
   H2_PHASE_WEIGHTS = 3,       /* step 3: weight Gram matrices B~_t^* B~_t        */
-  H2_PHASE_TRUNCATE = 4,      /* step 4: full-rank certificate, new bases        */
+  H2_PHASE_TRUNCATE = 4,      /* step 4: full-rank certificate, R_t              */
   H2_PHASE_REPROJECT = 5,     /* step 5: reprojection of the couplings           */
   H2_PHASE_EXACT = 6,         /* steps 2-4 by Householder R-factors and one-sided
                                  Jacobi SVD for the updates the certificate
                                  did not cover (with the weights of the
                                  unchanged matrix they need)                     */
-  H2_PHASE_COUNT = 7
+  H2_PHASE_BASES = 7,         /* step 4: new leaf bases and transfer matrices of
+                                 the certified updates, commit of E_t0           */
+  H2_PHASE_COUNT = 8
 } h2_phase;
 
 /* Path selection of later executions of this batch.

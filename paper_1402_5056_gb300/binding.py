@@ -33,7 +33,7 @@ EXPORTS = [
     "h2_lowrank_update_noalloc",
 ]
 
-PHASES = ("base_weights", "rfactor", "norms", "weights", "truncate", "reproject", "exact")
+PHASES = ("base_weights", "rfactor", "norms", "weights", "truncate", "reproject", "exact", "bases")
 
 MODE_AUTO, MODE_EXACT = 0, 1
 

@@ -1347,13 +1347,16 @@ void phase_flops(h2_ctx* ctx, const h2_batch* P, double f[H2_PHASE_COUNT]) {
     for (int32_t c = 0; c < ct.count(); ++c) {
       const double k = bs.rank[c];
       if (gram) {
-        // V_c^* V_c
+        // local orthonormality test (V_c^* V_c or sum E_s^* E_s), and
+        // V_c^* V_c by the recursion for clusters that are not orthonormal
+        const bool oc = orth[sd][c] != 0;
         if (ct.leaf(c)) {
-          f[H2_PHASE_BASE_WEIGHTS] += 2 * tri(k) * (double)ct.size[c];
+          f[H2_PHASE_BASE_WEIGHTS] += (oc ? 2 : 4) * tri(k) * (double)ct.size[c];
         } else {
           for (int32_t sn : {ct.son0[c], ct.son1[c]}) {
             const double ks = bs.rank[sn];
-            f[H2_PHASE_BASE_WEIGHTS] += 2 * ks * ks * k + 2 * tri(k) * ks;
+            f[H2_PHASE_BASE_WEIGHTS] += 2 * tri(k) * ks;
+            if (!oc) f[H2_PHASE_BASE_WEIGHTS] += orth[sd][sn] ? 2 * tri(k) * ks : 2 * ks * ks * k + 2 * tri(k) * ks;
           }
         }
       }
@@ -1418,20 +1421,24 @@ void phase_flops(h2_ctx* ctx, const h2_batch* P, double f[H2_PHASE_COUNT]) {
         // W11 + W12 C^* + C Y, C2_21 = L_S^* Y, C2_22 = L_S^* Z; LDL^*(C2)
         double c2 = 4 * tri(k) * u;
         for (double a = 0; a < u; a += 1) c2 += 2 * (k + a + 1) * (u - a);
-        f[H2_PHASE_TRUNCATE] += 2 * tri(u) * k + ldl(u) + 2 * u * k * u + 2 * u * tri(u) + c2 + ldl(K);
+        f[H2_PHASE_TRUNCATE] += 2 * tri(u) * k + ldl(u) + 2 * u * k * u + 2 * u * tri(u) + c2;
       } else {
-        f[H2_PHASE_TRUNCATE] += 2 * ldl(K) + 2 * K * tri(K) + (K * K * K + 3 * K * K + 2 * K) / 3;
+        f[H2_PHASE_TRUNCATE] += ldl(K) + 2 * K * tri(K) + (K * K * K + 3 * K * K + 2 * K) / 3;
       }
+      // certificate: float64 shift and scaling of the lower triangle for the
+      // float32 factorisation (float32 flops not counted), plus the float64
+      // factorisation where the float32 one did not prove it (jac[0] = 1)
+      f[H2_PHASE_TRUNCATE] += 2 * tri(K) + (!fail[it.update] && jac[4 * i] ? ldl(K) : 0.0);
       if (!fail[it.update]) {
-        if (leaf) f[H2_PHASE_TRUNCATE] += ob ? 2.0 * it.size * (k * u + tri(u)) : (double)it.size * K * K;
+        if (leaf) f[H2_PHASE_BASES] += ob ? 2.0 * it.size * (k * u + tri(u)) : (double)it.size * K * K;
         if (!troot && !(root && ob)) {
           const bool op = orth[it.side][tree_of(Z, it.side).father[it.cluster]] != 0;
           if (root)
-            f[H2_PHASE_TRUNCATE] += 2 * tri(k) * kf;
+            f[H2_PHASE_BASES] += 2 * tri(k) * kf;
           else if (ob && op)
-            f[H2_PHASE_TRUNCATE] += 2 * k * kf * u + K * u * u;
+            f[H2_PHASE_BASES] += 2 * k * kf * u + K * u * u;
           else
-            f[H2_PHASE_TRUNCATE] += 2 * tri(k) * kf + K * (kf + u) * (kf + u);
+            f[H2_PHASE_BASES] += 2 * tri(k) * kf + K * (kf + u) * (kf + u);
         }
       }
     }
@@ -1624,11 +1631,20 @@ extern "C" h2_status h2_batch_item_tile(h2_ctx* ctx, const h2_batch* P, int64_t 
       return;
     }
     if (!exact) {
-      // basis Gram: the V_t^* V_t block comes from the unchanged basis
-      std::vector<double> vg(kSlot);
-      H2_CUDA(cudaMemcpyAsync(vg.data(), P->BW.Vg[it.side] + (size_t)it.cluster * kSlot, kSlot * sizeof(double),
-                              cudaMemcpyDeviceToHost, ctx->stream));
+      // basis Gram: the V_t^* V_t block comes from the unchanged basis (the
+      // identity where the basis is orthonormal; only the others have a slot)
+      std::vector<double> vg(kSlot, 0.0);
+      int32_t orth = 0;
+      H2_CUDA(cudaMemcpyAsync(&orth, P->BW.orth[it.side] + it.cluster, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                              ctx->stream));
       H2_CUDA(cudaStreamSynchronize(ctx->stream));
+      if (orth) {
+        for (int i = 0; i < 32; ++i) vg[i * 33] = 1.0;
+      } else {
+        H2_CUDA(cudaMemcpyAsync(vg.data(), P->BW.Vg[it.side] + (size_t)it.cluster * kSlot, kSlot * sizeof(double),
+                                cudaMemcpyDeviceToHost, ctx->stream));
+        H2_CUDA(cudaStreamSynchronize(ctx->stream));
+      }
       const int K = it.k + P->u;
       for (int j = 0; j < 32; ++j)
         for (int i = 0; i < 32; ++i)

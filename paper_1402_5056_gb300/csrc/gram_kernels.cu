@@ -142,6 +142,63 @@ __device__ __forceinline__ bool ldl(double* A, int ld, int n, double shift, doub
   return __all_sync(kFull, ok);
 }
 
+// Float32 LDL^* of the n x n lower triangle of F (ld ld), pivots tested at
+// the end (positive and finite): the fast first try of the certificate.
+__device__ __forceinline__ bool ldl_f32(float* F, int ld, int n, float* lv, int lane) {
+  for (int j = 0; j < n; ++j) {
+    const float d = F[j + j * ld];
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
+    const int m = n - j - 1;
+    if (lane < m) lv[lane] = F[j + 1 + lane + j * ld] * r;
+    __syncwarp();
+    const int nt = tri(m);
+    for (int e = lane; e < nt; e += 32) {
+      int a, b;
+      tri_index(e, a, b);
+      const int p = j + 1 + a, q = j + 1 + b;
+      F[p + q * ld] = fmaf(-F[p + j * ld], lv[b], F[p + q * ld]);
+    }
+    __syncwarp();
+    if (lane < m) F[j + 1 + lane + j * ld] = lv[lane];
+    __syncwarp();
+  }
+  const float d = lane < n ? F[lane * (ld + 1)] : 1.0f;
+  const bool ok = d > 1e-30f && d < 1e30f;
+  return __all_sync(kFull, ok);
+}
+
+// Positive definiteness of A - shift I for the n x n lower triangle of the
+// float64 tile A (ld ld), A = L^* W L symmetric positive semidefinite (so
+// |a_ij| <= tr A).  First a float32 LDL^* of (A - (shift + c) I) 2^-e (an
+// exact power-of-two scaling with 2^e ~ tr A) in the scratch tile Fs, with
+// c = 4 (n + 2) 2^-24 tr A: by the verification of positive definiteness
+// through a floating-point Cholesky factorisation of a shifted matrix (Rump,
+// BIT 2006), success proves A - shift I positive definite, c covering the
+// conversion to float32 (n 2^-24 tr A) and the factorisation's backward error
+// (gamma_{n+1} tr A, the approximate reciprocals included) twice over.  When
+// the float32 factorisation fails, the float64 LDL^* of A - shift I decides
+// (its rounding is inside delta).  A is not modified by the first try.
+// Returns 1 (float32 proof), 2 (float64 proof) or 0 (not positive definite).
+__device__ __forceinline__ int certify_pd(double* A, int ld, int n, double shift, float* Fs, double* lv,
+                                          int lane) {
+  const double trA = warp_sum(lane < n ? A[lane * (ld + 1)] : 0.0);
+  if (trA > 0.0 && trA < DBL_MAX) {
+    int ex = 0;
+    frexp(trA, &ex);
+    const double c = shift + 4.0 * (n + 2) * 0x1p-24 * trA;
+    for (int e = lane; e < tri(n); e += 32) {
+      int i, j;
+      tri_index(e, i, j);
+      const double v = i == j ? A[i + j * ld] - c : A[i + j * ld];
+      Fs[i + j * ld] = (float)ldexp(v, -ex);
+    }
+    __syncwarp();
+    if (ldl_f32(Fs, ld, n, reinterpret_cast<float*>(lv), lane)) return 1;
+  }
+  return ldl<false>(A, ld, n, shift, lv, lane) ? 2 : 0;
+}
+
 // The factor L D^{1/2} of a successful ldl in place (lower triangle).
 __device__ __forceinline__ void ldl_to_cholesky(double* A, int ld, int n, double* dsq, int lane) {
   if (lane < n) dsq[lane] = sqrt(A[lane * (ld + 1)]);
@@ -244,21 +301,100 @@ __device__ __forceinline__ void load_gram(double* T, int ld, const double* Gv, c
 }
 
 // ------------------------------------------------- the unchanged matrix
-// Vg_c = V_c^* V_c for every cluster of both sides, bottom-up (one launch
-// per level): leaf Gram of V_c, inner sum over the sons of E_s^* Vg_s E_s;
-// orth_c = 1 when Vg_c = I within kOrthTol.
-__global__ void k_vgram(MatView M, const int32_t* __restrict__ list, int n, BaseWeights BW) {
+// Orthonormal cluster bases.  A nested basis V_t is orthonormal when every
+// cluster below it is locally orthonormal: V_t^* V_t = I for a leaf,
+// sum over the sons of E_s^* E_s = I for an inner cluster (given orthonormal
+// sons).  k_orth_local tests every cluster of both sides in one launch and
+// writes the local verdict into orth; k_orth_mark then clears orth on every
+// ancestor of a cluster that failed, so that orth_c = 1 exactly when the
+// whole subtree of c passed (a sufficient condition; local deviations of
+// kOrthLocalTol add up over at most the tree depth).  k_vgram computes
+// V_t^* V_t level by level for the clusters left with orth_c = 0 only (the
+// others have V_t^* V_t = I and nobody reads their slot).
+constexpr double kOrthLocalTol = 2e-14;
+
+__global__ void k_orth_local(MatView M, const int32_t* __restrict__ list, int n, BaseWeights BW) {
   extern __shared__ double smem[];
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
   const int idx = blockIdx.x * (blockDim.x >> 5) + w;
   if (idx >= n) return;
   const int kcap = M.kcap;
+  double* T0 = smem + (size_t)w * kLd * kcap;
+  const int side = list[idx] >> 30;
+  const int c = list[idx] & 0x3fffffff;
+  const int32_t* rank = pick(M.rank, side);
+  const int32_t* subtree = pick(M.subtree, side);
+  const int k = rank[c];
+  bool ok = k <= 32;
+  if (ok) {
+    const int nt = tri(k);
+    double acc[kNS];
+#pragma unroll
+    for (int s = 0; s < kNS; ++s) acc[s] = 0.0;
+    if (subtree[c] == 1) {
+      const double* V = pick(M.leaf, side) + pick(M.leaf_off, side)[c];
+      const int m = pick(M.size, side)[c];
+      for (int r0 = 0; r0 < m; r0 += 32) {
+        const int ch = min(32, m - r0);
+        load_tile(T0, kLd, V + r0, m, ch, k, lane);
+        __syncwarp();
+        acc_gram(acc, T0, ch, k, 1.0, lane);
+        __syncwarp();
+      }
+    } else {
+      for (int si = 0; si < 2; ++si) {
+        const int s = si == 0 ? c + 1 : c + 1 + subtree[c + 1];
+        load_tile(T0, kLd, pick(M.transfer, side) + (size_t)s * kcap * kcap, kcap, rank[s], k, lane);
+        __syncwarp();
+        acc_gram(acc, T0, rank[s], k, 1.0, lane);
+        __syncwarp();
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < kNS; ++s) {
+      const int e = lane + 32 * s;
+      if (e < nt) {
+        int i, j;
+        tri_index(e, i, j);
+        if (!(fabs(acc[s] - (i == j ? 1.0 : 0.0)) <= kOrthLocalTol)) ok = false;
+      }
+    }
+  }
+  ok = __all_sync(kFull, ok);
+  if (lane == 0) pick(BW.orth, side)[c] = ok ? 1 : 0;
+}
+
+// One thread per cluster of both sides: a cluster that failed clears orth on
+// its ancestors (stores of 0 only, so concurrent walks agree).
+__global__ void k_orth_mark(MatView M, const int32_t* __restrict__ list, int n, BaseWeights BW) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  const int side = list[idx] >> 30;
+  const int c = list[idx] & 0x3fffffff;
+  int32_t* orth = pick(BW.orth, side);
+  if (orth[c]) return;
+  const int32_t* father = pick(M.father, side);
+  for (int f = father[c]; f >= 0; f = father[f]) orth[f] = 0;
+}
+
+// Vg_c = V_c^* V_c, bottom-up (one launch per level), for clusters with
+// orth_c = 0: leaf Gram of V_c, inner sum over the sons of E_s^* Vg_s E_s
+// (Vg_s = I for an orthonormal son).
+__global__ void k_vgram(MatView M, const int32_t* __restrict__ list, int n, BaseWeights BW) {
+  extern __shared__ double smem[];
+  const int lane = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5;
+  const int idx = blockIdx.x * (blockDim.x >> 5) + w;
+  if (idx >= n) return;
+  const int side = list[idx] >> 30;
+  const int c = list[idx] & 0x3fffffff;
+  const int32_t* orth = pick(BW.orth, side);
+  if (orth[c]) return;
+  const int kcap = M.kcap;
   double* T0 = smem + (size_t)w * 3 * kLd * kcap;
   double* T1 = T0 + kLd * kcap;
   double* T2 = T1 + kLd * kcap;
-  const int side = list[idx] >> 30;
-  const int c = list[idx] & 0x3fffffff;
   const int32_t* rank = pick(M.rank, side);
   const int32_t* subtree = pick(M.subtree, side);
   const int k = rank[c];
@@ -281,8 +417,14 @@ __global__ void k_vgram(MatView M, const int32_t* __restrict__ list, int n, Base
     for (int si = 0; si < 2; ++si) {
       const int s = si == 0 ? c + 1 : c + 1 + subtree[c + 1];
       const int ks = rank[s];
-      load_tile(T0, kLd, pick(BW.Vg, side) + (size_t)s * kSlot, 32, ks, ks, lane);
       load_tile(T1, kLd, pick(M.transfer, side) + (size_t)s * kcap * kcap, kcap, ks, k, lane);
+      __syncwarp();
+      if (orth[s]) {
+        acc_gram(acc, T1, ks, k, 1.0, lane);
+        __syncwarp();
+        continue;
+      }
+      load_tile(T0, kLd, pick(BW.Vg, side) + (size_t)s * kSlot, 32, ks, ks, lane);
       __syncwarp();
       // T2 = Vg_s E_s (ks x k)
       for (int e = lane; e < ks * k; e += 32) {
@@ -308,18 +450,6 @@ __global__ void k_vgram(MatView M, const int32_t* __restrict__ list, int n, Base
     }
   }
   store_sym(pick(BW.Vg, side) + (size_t)c * kSlot, acc, k, lane);
-  bool orth = true;
-#pragma unroll
-  for (int s = 0; s < kNS; ++s) {
-    const int e = lane + 32 * s;
-    if (e < nt) {
-      int i, j;
-      tri_index(e, i, j);
-      if (!(fabs(acc[s] - (i == j ? 1.0 : 0.0)) <= kOrthTol)) orth = false;
-    }
-  }
-  orth = __all_sync(kFull, orth);
-  if (lane == 0) pick(BW.orth, side)[c] = orth ? 1 : 0;
 }
 
 // Wo_c = sum over b in row(c) of omega_b^2 S_b S_b^* (column side S_b^* S_b),
@@ -896,7 +1026,9 @@ __global__ void k_certify(const Item* __restrict__ items, int n, int u, int ld, 
   }
   if (ok) {
     const double delta = 8.0 * (levels + 4) * (K + 32) * DBL_EPSILON * trG * trW;
-    ok = ldl<false>(T1, ld, K, 0.25 * eps * eps + delta, lv, lane);
+    const int how = certify_pd(T1, ld, K, 0.25 * eps * eps + delta, reinterpret_cast<float*>(T2), lv, lane);
+    ok = how != 0;
+    if (lane == 0) IB.jac[4 * (size_t)id] = how == 2 ? 1ull : 0ull;   // float64 factorisation ran
   }
   if (!ok) {
     if (lane == 0) IB.fail[it.update] = 1;
@@ -1144,6 +1276,15 @@ size_t tiles_bytes(int ntiles, int cols, int extra) {
 }
 
 }  // namespace
+
+void launch_gram_orth(const Pipeline& P, cudaStream_t st) {
+  static unsigned long long done = 0;
+  const int n = P.cl_ptr[P.levels];
+  if (n <= 0) return;
+  smem_limit(k_orth_local, tiles_bytes(1, 32, 0), done);
+  k_orth_local<<<blocks_for(n), 32 * kWarps, tiles_bytes(1, P.M.kcap, 0), st>>>(P.M, P.cl_list, n, P.BW);
+  k_orth_mark<<<(n + 127) / 128, 128, 0, st>>>(P.M, P.cl_list, n, P.BW);
+}
 
 void launch_gram_vbasis_level(const Pipeline& P, int level, cudaStream_t st) {
   static unsigned long long done = 0;

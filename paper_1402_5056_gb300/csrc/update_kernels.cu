@@ -1370,12 +1370,16 @@ void run_pipeline(const Pipeline& P) {
       vs = P.side2;
       H2_CUDA(cudaStreamWaitEvent(vs, P.fork, 0));
     }
+    if (ncl > 0) {
+      launch_gram_orth(P, vs);
+      pl[H2_PHASE_BASE_WEIGHTS] += 2;
+    }
     for (int l = L - 1; l >= 0; --l)
       if (P.cl_ptr[l + 1] > P.cl_ptr[l]) {
         launch_gram_vbasis_level(P, l, vs);
         ++pl[H2_PHASE_BASE_WEIGHTS];
       }
-    if (vs != bs) H2_CUDA(cudaEventRecord(P.join2, vs));
+    if (vs != bs) H2_CUDA(cudaEventRecord(P.join2, vs));   // flags and V_t^* V_t (needed by the norms)
     if (ncl > 0) {
       launch_gram_base(P, bs);
       ++pl[H2_PHASE_BASE_WEIGHTS];
@@ -1385,7 +1389,7 @@ void run_pipeline(const Pipeline& P) {
         launch_gram_base_level(P, l, bs);
         ++pl[H2_PHASE_BASE_WEIGHTS];
       }
-    if (vs != bs) H2_CUDA(cudaStreamWaitEvent(bs, P.join2, 0));
+    if (vs != bs) H2_CUDA(cudaStreamWaitEvent(bs, P.join2, 0));   // the phase ends with both chains
     stop(H2_PHASE_BASE_WEIGHTS, bs);
     if (P.side) H2_CUDA(cudaEventRecord(P.join, P.side));
     start(H2_PHASE_RFACTOR, st);
@@ -1395,13 +1399,15 @@ void run_pipeline(const Pipeline& P) {
         ++pl[H2_PHASE_RFACTOR];
       }
     stop(H2_PHASE_RFACTOR, st);
-    if (P.side) H2_CUDA(cudaStreamWaitEvent(st, P.join, 0));
+    // the norms need the orthonormality flags only; the weights need all
+    if (P.side) H2_CUDA(cudaStreamWaitEvent(st, vs != bs ? P.join2 : P.join, 0));
     start(H2_PHASE_NORMS, st);
     if (P.n_norms > 0) {
       launch_gram_norms(P);
       ++pl[H2_PHASE_NORMS];
     }
     stop(H2_PHASE_NORMS, st);
+    if (P.side) H2_CUDA(cudaStreamWaitEvent(st, P.join, 0));
     start(H2_PHASE_WEIGHTS, st);
     for (int l = 0; l < L; ++l)
       if (P.lvl_ptr[l + 1] > P.lvl_ptr[l]) {
@@ -1412,10 +1418,15 @@ void run_pipeline(const Pipeline& P) {
     start(H2_PHASE_TRUNCATE, st);
     if (ni > 0) {
       launch_gram_certify(P);
-      launch_gram_outputs(P);
-      pl[H2_PHASE_TRUNCATE] += 4;   // block-form and general variants of both kernels
+      pl[H2_PHASE_TRUNCATE] += 2;   // block-form and general variants
     }
     stop(H2_PHASE_TRUNCATE, st);
+    start(H2_PHASE_BASES, st);
+    if (ni > 0) {
+      launch_gram_outputs(P);
+      pl[H2_PHASE_BASES] += 2;
+    }
+    stop(H2_PHASE_BASES, st);
   }
   // exact path for the updates whose certificate failed (every kernel returns
   // at once for the tasks of the other updates and for unmarked clusters):

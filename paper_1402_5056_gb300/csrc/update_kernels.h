@@ -81,6 +81,7 @@ struct Pipeline {
 void run_pipeline(const Pipeline& P);
 
 // Certified Gram path (gram_kernels.cu).
+void launch_gram_orth(const Pipeline& P, cudaStream_t st);                // orthonormality flags (2 launches)
 void launch_gram_vbasis_level(const Pipeline& P, int level, cudaStream_t st);  // V_t^* V_t, one level
 void launch_gram_base(const Pipeline& P, cudaStream_t st);               // Wo, all clusters
 void launch_gram_base_level(const Pipeline& P, int level, cudaStream_t st);  // W0, one level
