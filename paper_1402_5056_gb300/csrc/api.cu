@@ -725,6 +725,20 @@ struct h2_batch {
   cudaEvent_t fork = nullptr, join = nullptr;
   cudaStream_t side2 = nullptr;              // stream of the basis Grams of the unchanged matrix
   cudaEvent_t join2 = nullptr;
+  // CUDA graph of the launch sequence, captured when the batch is executed
+  // again with the same arguments and replayed while they stay the same
+  cudaGraphExec_t graph = nullptr;
+  const double* g_A = nullptr;
+  const double* g_B = nullptr;
+  double g_eps = -1.0;
+  int g_mode = -1;
+  bool g_timing = false;
+  int g_repeats = 0;
+  bool g_broken = false;                     // capture failed once: stay eager
+  MatView g_view{};                          // the matrix storage the graph reads
+  const h2_ctx* g_ctx = nullptr;
+  cudaStream_t cap = nullptr;                // private stream for the capture (the context's
+                                             // stream may be the legacy default stream)
 };
 
 namespace {
@@ -904,6 +918,7 @@ void alloc_batch(h2_ctx* ctx, h2_batch& P) {
   H2_CUDA(cudaEventCreateWithFlags(&P.fork, cudaEventDisableTiming));
   H2_CUDA(cudaEventCreateWithFlags(&P.join, cudaEventDisableTiming));
   H2_CUDA(cudaStreamCreateWithFlags(&P.side2, cudaStreamNonBlocking));
+  H2_CUDA(cudaStreamCreateWithFlags(&P.cap, cudaStreamNonBlocking));
   H2_CUDA(cudaEventCreateWithFlags(&P.join2, cudaEventDisableTiming));
   P.d_items = upload(P.items, st);
   P.d_ents = upload(P.ents, st);
@@ -948,8 +963,12 @@ void alloc_batch(h2_ctx* ctx, h2_batch& P) {
 }
 
 void free_batch_device(h2_batch& P) {
+  if (P.graph) cudaGraphExecDestroy(P.graph);
+  P.graph = nullptr;
   if (P.side) cudaStreamSynchronize(P.side);
   if (P.side2) cudaStreamSynchronize(P.side2);
+  if (P.cap) cudaStreamDestroy(P.cap);
+  P.cap = nullptr;
   if (P.join2) cudaEventDestroy(P.join2);
   if (P.side2) cudaStreamDestroy(P.side2);
   P.join2 = nullptr;
@@ -994,6 +1013,15 @@ void free_batch_device(h2_batch& P) {
   dfree(P.d_res);
   dfree(P.d_res_task_off);
   dfree(P.d_res_item_off);
+}
+
+bool same_view(const MatView& a, const MatView& b) {
+  for (int sd = 0; sd < 2; ++sd)
+    if (a.leaf[sd] != b.leaf[sd] || a.transfer[sd] != b.transfer[sd] || a.leaf_off[sd] != b.leaf_off[sd] ||
+        a.rank[sd] != b.rank[sd] || a.father[sd] != b.father[sd] || a.subtree[sd] != b.subtree[sd] ||
+        a.size[sd] != b.size[sd])
+      return false;
+  return a.S == b.S && a.kcap == b.kcap;
 }
 
 void execute(h2_ctx* ctx, h2_batch& P, const double* A, const double* B, double eps) {
@@ -1042,7 +1070,58 @@ void execute(h2_ctx* ctx, h2_batch& P, const double* A, const double* B, double 
   pp.join2 = P.join2;
   pp.events = P.timing ? P.ev : nullptr;
   pp.phase_launches = P.phase_launches;
-  run_pipeline(pp);
+  // the first execution with given arguments runs eagerly (it also sets the
+  // kernels' attributes); a repeat is captured once into a graph and the
+  // graph is replayed while the arguments stay the same
+  // (the graph holds the matrix's storage pointers, which change when its
+  // rank capacity grows, and the context's error word)
+  const bool same = A == P.g_A && B == P.g_B && eps == P.g_eps && P.mode == P.g_mode && P.timing == P.g_timing &&
+                    ctx == P.g_ctx && same_view(pp.M, P.g_view);
+  if (!same) {
+    P.g_view = pp.M;
+    P.g_ctx = ctx;
+    if (P.graph) cudaGraphExecDestroy(P.graph);
+    P.graph = nullptr;
+    P.g_A = A;
+    P.g_B = B;
+    P.g_eps = eps;
+    P.g_mode = P.mode;
+    P.g_timing = P.timing;
+    P.g_repeats = 0;
+  } else {
+    ++P.g_repeats;
+  }
+  bool done = false;
+  if (P.g_repeats >= 1 && !P.g_broken && P.side) {
+    if (!P.graph) {
+      cudaGraph_t g = nullptr;
+      Pipeline pc = pp;
+      pc.stream = P.cap;
+      pc.capturing = true;
+      bool ok = cudaStreamBeginCapture(P.cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      if (ok) {
+        try {
+          run_pipeline(pc);
+        } catch (...) {
+          ok = false;
+        }
+        ok = cudaStreamEndCapture(P.cap, &g) == cudaSuccess && ok;
+        ok = ok && cudaGraphInstantiate(&P.graph, g, 0) == cudaSuccess;
+        if (g) cudaGraphDestroy(g);
+      }
+      if (!ok) {
+        (void)cudaGetLastError();
+        if (P.graph) cudaGraphExecDestroy(P.graph);
+        P.graph = nullptr;
+        P.g_broken = true;
+      }
+    }
+    if (P.graph) {
+      H2_CUDA(cudaGraphLaunch(P.graph, ctx->stream));
+      done = true;
+    }
+  }
+  if (!done) run_pipeline(pp);
   int64_t launches = 0;
   for (int ph = 0; ph < H2_PHASE_COUNT; ++ph) launches += P.phase_launches[ph];
   P.launches = launches;

@@ -214,7 +214,7 @@ __device__ __forceinline__ void ldl_to_cholesky(double* A, int ld, int n, double
 // Rows of the outside-block stack of one block: X[r][q] = S_b[q][r] on the
 // row side (rows of S_b^*), S_b[r][q] on the column side; l x k.
 __device__ __forceinline__ void load_block_rows(double* X, const double* S, int kcap, int side, int l, int k,
-                                                int lane) {
+                                                int lane, int ld = kLd) {
   if (side == 0) {
     // X = S_b^*: lane q reads row q of S_b, column by column (8 at a time)
     for (int r0 = 0; r0 < l; r0 += 8) {
@@ -223,16 +223,17 @@ __device__ __forceinline__ void load_block_rows(double* X, const double* S, int 
       for (int j = 0; j < 8; ++j) v[j] = (lane < k && r0 + j < l) ? S[lane + (size_t)(r0 + j) * kcap] : 0.0;
 #pragma unroll
       for (int j = 0; j < 8; ++j)
-        if (lane < k && r0 + j < l) X[(r0 + j) + lane * kLd] = v[j];
+        if (lane < k && r0 + j < l) X[(r0 + j) + lane * ld] = v[j];
     }
   } else {
-    load_tile(X, kLd, S, kcap, l, k, lane);
+    load_tile(X, ld, S, kcap, l, k, lane);
   }
 }
 
 // acc (lower triangle of the k x k block in the per-lane layout) += w X^* X
 // for the l x k tile X.
-__device__ __forceinline__ void acc_gram(double (&acc)[kNS], const double* X, int l, int k, double w, int lane) {
+__device__ __forceinline__ void acc_gram(double (&acc)[kNS], const double* X, int l, int k, double w, int lane,
+                                         int ld = kLd) {
   const int nt = tri(k);
 #pragma unroll
   for (int s = 0; s < kNS; ++s) {
@@ -242,16 +243,16 @@ __device__ __forceinline__ void acc_gram(double (&acc)[kNS], const double* X, in
       int i, j;
       tri_index(e, i, j);
       double g = 0.0;
-      for (int r = 0; r < l; ++r) g = fma(X[r + i * kLd], X[r + j * kLd], g);
+      for (int r = 0; r < l; ++r) g = fma(X[r + i * ld], X[r + j * ld], g);
       acc[s] = fma(w, g, acc[s]);
     }
   }
 }
 
-__device__ __forceinline__ double sum_squares(const double* X, int l, int k, int lane) {
+__device__ __forceinline__ double sum_squares(const double* X, int l, int k, int lane, int ld = kLd) {
   double part = 0.0;
   for (int e = lane; e < l * k; e += 32) {
-    const double v = X[e % l + (e / l) * kLd];
+    const double v = X[e % l + (e / l) * ld];
     part = fma(v, v, part);
   }
   return warp_sum(part);
@@ -721,9 +722,11 @@ __global__ void k_fweights(MatView M, const Item* __restrict__ items, const Entr
   const int w = threadIdx.x >> 5;
   const int idx = blockIdx.x * (blockDim.x >> 5) + w;
   if (idx >= n) return;
-  double* T0 = smem + (size_t)w * 3 * kLd * tc;
-  double* T1 = T0 + kLd * tc;
-  double* T2 = T1 + kLd * tc;
+  // every tile holds at most max(K, kcap) = tc rows: leading dimension tc + 1
+  const int ld = tc + 1;
+  double* T0 = smem + (size_t)w * 3 * ld * tc;
+  double* T1 = T0 + ld * tc;
+  double* T2 = T1 + ld * tc;
   const int id = list[idx];
   const Item it = items[id];
   const int side = it.side;
@@ -755,32 +758,32 @@ __global__ void k_fweights(MatView M, const Item* __restrict__ items, const Entr
         const Entry en = ents[e];
         if (en.other < 0) continue;
         const int l = orank[en.other_cluster];
-        load_block_rows(T0, Sbase + (size_t)en.slot * kcap * kcap, kcap, side, l, k, lane);
+        load_block_rows(T0, Sbase + (size_t)en.slot * kcap * kcap, kcap, side, l, k, lane, ld);
         __syncwarp();
-        const double nrm2 = sum_squares(T0, l, k, lane);
+        const double nrm2 = sum_squares(T0, l, k, lane, ld);
         const double w2 = nrm2 > 1e-300 ? st * recip(nrm2) : 0.0;
-        acc_gram(acc, T0, l, k, -w2, lane);
+        acc_gram(acc, T0, l, k, -w2, lane, ld);
         __syncwarp();
       }
   } else {
-    load_tile(T1, kLd, pick(BW.Vg, side) + (size_t)it.cluster * kSlot, 32, k, k, lane);
+    load_tile(T1, ld, pick(BW.Vg, side) + (size_t)it.cluster * kSlot, 32, k, k, lane);
     for (int e = it.ent_begin; e < it.ent_end; ++e) {
       const Entry en = ents[e];
       if (en.other >= 0) continue;
       const int l = orank[en.other_cluster];
-      load_block_rows(T0, Sbase + (size_t)en.slot * kcap * kcap, kcap, side, l, k, lane);
+      load_block_rows(T0, Sbase + (size_t)en.slot * kcap * kcap, kcap, side, l, k, lane, ld);
       __syncwarp();
       // ||R_kk S_b||_F^2 = sum over rows x of X of x G_kk x^*
       double part = 0.0;
       for (int e2 = lane; e2 < l * k; e2 += 32) {
         const int r = e2 % l, q = e2 / l;
         double y = 0.0;
-        for (int p = 0; p < k; ++p) y = fma(T0[r + p * kLd], T1[p + q * kLd], y);
-        part = fma(y, T0[r + q * kLd], part);
+        for (int p = 0; p < k; ++p) y = fma(T0[r + p * ld], T1[p + q * ld], y);
+        part = fma(y, T0[r + q * ld], part);
       }
       const double nrm2 = warp_sum(part);
       const double w2 = nrm2 > 1e-300 ? st * recip(nrm2) : 0.0;
-      acc_gram(acc, T0, l, k, w2, lane);
+      acc_gram(acc, T0, l, k, w2, lane, ld);
       __syncwarp();
     }
   }
@@ -797,15 +800,15 @@ __global__ void k_fweights(MatView M, const Item* __restrict__ items, const Entr
       const int Ko = l + u;
       const double nrm = IB.norms[en.norm];
       const double w2 = nrm > 1e-150 ? st * recip(nrm * nrm) : 0.0;
-      load_gram(T1, kLd, IB.Gv + (size_t)en.other * kSlot, Vgo + (size_t)ot.cluster * kSlot,
+      load_gram(T1, ld, IB.Gv + (size_t)en.other * kSlot, Vgo + (size_t)ot.cluster * kSlot,
                 orth_o[ot.cluster] != 0, l, Ko, lane);
       // T0 = S' (k x l): S_b on the row side, S_b^* on the column side
       const double* S = Sbase + (size_t)en.slot * kcap * kcap;
       if (side == 0) {
-        load_tile(T0, kLd, S, kcap, k, l, lane);
+        load_tile(T0, ld, S, kcap, k, l, lane);
       } else {
         for (int q = 0; q < l; ++q)
-          if (lane < k) T0[lane + q * kLd] = S[q + (size_t)lane * kcap];
+          if (lane < k) T0[lane + q * ld] = S[q + (size_t)lane * kcap];
       }
       __syncwarp();
       // T2 = P G_o (K x Ko)
@@ -814,11 +817,11 @@ __global__ void k_fweights(MatView M, const Item* __restrict__ items, const Entr
         double v;
         if (i < k) {
           v = 0.0;
-          for (int q = 0; q < l; ++q) v = fma(T0[i + q * kLd], T1[q + j * kLd], v);
+          for (int q = 0; q < l; ++q) v = fma(T0[i + q * ld], T1[q + j * ld], v);
         } else {
-          v = T1[l + i - k + j * kLd];
+          v = T1[l + i - k + j * ld];
         }
-        T2[i + j * kLd] = v;
+        T2[i + j * ld] = v;
       }
       __syncwarp();
 #pragma unroll
@@ -831,9 +834,9 @@ __global__ void k_fweights(MatView M, const Item* __restrict__ items, const Entr
           double v;
           if (j < k) {
             v = 0.0;
-            for (int q = 0; q < l; ++q) v = fma(T2[i + q * kLd], T0[j + q * kLd], v);
+            for (int q = 0; q < l; ++q) v = fma(T2[i + q * ld], T0[j + q * ld], v);
           } else {
-            v = T2[i + (l + j - k) * kLd];
+            v = T2[i + (l + j - k) * ld];
           }
           acc[s] = fma(w2, v, acc[s]);
         }
@@ -847,14 +850,14 @@ __global__ void k_fweights(MatView M, const Item* __restrict__ items, const Entr
     if (!(it.flags & kItemTreeRoot)) {
       const int f = pick(M.father, side)[it.cluster];
       const int kf = it.kf;
-      load_tile(T1, kLd, pick(BW.W0, side) + (size_t)f * kSlot, 32, kf, kf, lane);
-      load_tile(T0, kLd, E, kcap, k, kf, lane);
+      load_tile(T1, ld, pick(BW.W0, side) + (size_t)f * kSlot, 32, kf, kf, lane);
+      load_tile(T0, ld, E, kcap, k, kf, lane);
       __syncwarp();
       for (int e2 = lane; e2 < k * kf; e2 += 32) {
         const int i = e2 % k, j = e2 / k;
         double v = 0.0;
-        for (int q = 0; q < kf; ++q) v = fma(T0[i + q * kLd], T1[q + j * kLd], v);
-        T2[i + j * kLd] = v;
+        for (int q = 0; q < kf; ++q) v = fma(T0[i + q * ld], T1[q + j * ld], v);
+        T2[i + j * ld] = v;
       }
       __syncwarp();
 #pragma unroll
@@ -865,7 +868,7 @@ __global__ void k_fweights(MatView M, const Item* __restrict__ items, const Entr
           int i, j;
           tri_index(e2, i, j);
           double v = acc[s];
-          for (int q = 0; q < kf; ++q) v = fma(T2[i + q * kLd], T0[j + q * kLd], v);
+          for (int q = 0; q < kf; ++q) v = fma(T2[i + q * ld], T0[j + q * ld], v);
           acc[s] = v;
         }
       }
@@ -873,35 +876,45 @@ __global__ void k_fweights(MatView M, const Item* __restrict__ items, const Entr
   } else {
     const int kf = items[it.parent].k;
     const int Kf = kf + u;
-    load_tile(T1, kLd, IB.Wg + (size_t)it.parent * kSlot, 32, Kf, Kf, lane);
-    load_tile(T0, kLd, E, kcap, k, kf, lane);
+    load_tile(T1, ld, IB.Wg + (size_t)it.parent * kSlot, 32, Kf, Kf, lane);
+    load_tile(T0, ld, E, kcap, k, kf, lane);
     __syncwarp();
     // T2 = E W11 (k x kf); rows k.. of E~_t W_p are rows kf.. of W_p
     for (int e2 = lane; e2 < k * kf; e2 += 32) {
       const int i = e2 % k, j = e2 / k;
       double v = 0.0;
-      for (int q = 0; q < kf; ++q) v = fma(T0[i + q * kLd], T1[q + j * kLd], v);
-      T2[i + j * kLd] = v;
+      for (int q = 0; q < kf; ++q) v = fma(T0[i + q * ld], T1[q + j * ld], v);
+      T2[i + j * ld] = v;
     }
     __syncwarp();
-    // lower triangle of E~_t W_p E~_t^*: (i, j < k) rows of T2 times E^*;
-    // (i >= k, j < k) rows kf + i - k of W_p times E^*; (i, j >= k) W22
+    // lower triangle of E~_t W_p E~_t^*, block by block so that one warp
+    // instruction never mixes products with copies: (i, j < k) rows of T2
+    // times E^* (the first tri(k) entries); (i >= k, j < k) rows kf + i - k
+    // of W_p times E^*; (i, j >= k) W22
+#pragma unroll
+    for (int s = 0; s < kNS; ++s) {
+      if (32 * s >= ntk) break;
+      const int e2 = lane + 32 * s;
+      if (e2 < ntk) {
+        int i, j;
+        tri_index(e2, i, j);
+        double v = acc[s];
+        for (int q = 0; q < kf; ++q) v = fma(T2[i + q * ld], T0[j + q * ld], v);
+        acc[s] = v;
+      }
+    }
 #pragma unroll
     for (int s = 0; s < kNS; ++s) {
       if (32 * s >= nt) break;
       const int e2 = lane + 32 * s;
-      if (e2 < nt) {
+      if (e2 >= ntk && e2 < nt) {
         int i, j;
         tri_index(e2, i, j);
         double v = acc[s];
         if (j < k) {
-          if (i < k) {
-            for (int q = 0; q < kf; ++q) v = fma(T2[i + q * kLd], T0[j + q * kLd], v);
-          } else {
-            for (int q = 0; q < kf; ++q) v = fma(T1[(kf + i - k) + q * kLd], T0[j + q * kLd], v);
-          }
+          for (int q = 0; q < kf; ++q) v = fma(T1[(kf + i - k) + q * ld], T0[j + q * ld], v);
         } else {
-          v += T1[(kf + i - k) + (kf + j - k) * kLd];
+          v += T1[(kf + i - k) + (kf + j - k) * ld];
         }
         acc[s] = v;
       }
@@ -921,6 +934,16 @@ __global__ void k_fweights(MatView M, const Item* __restrict__ items, const Entr
 // kGeneral = false takes the tasks whose V_t is orthonormal (block formulas,
 // a K x u tile for C_t and L_S), kGeneral = true the others (factorisation
 // of the whole G_t).
+// Doubles of the third tile of k_certify: the general form keeps W L (K x K);
+// the block form keeps Y and Z (u x K, ld u + 1) and then the float32 copy
+// of the certificate matrix (K x K floats, ld ld).
+__host__ __device__ inline int certify_t2(bool general, int ld, int u) {
+  const int tile = ld * (ld - 1);
+  const int yz = (u + 1) * (ld - 1);
+  const int fs = (tile + 1) / 2;
+  return general ? tile : (yz > fs ? yz : fs);
+}
+
 template <bool kGeneral>
 __global__ void k_certify(const Item* __restrict__ items, int n, int u, int ld, int levels, double eps,
                           BaseWeights BW, ItemBuffers IB) {
@@ -937,10 +960,11 @@ __global__ void k_certify(const Item* __restrict__ items, int n, int u, int ld, 
   const int tile = ld * (ld - 1);
   // general: T0 = G_t / L (K x K); orthonormal: T0 = [C_t; S or L_S] (K x u)
   const int t0 = kGeneral ? tile : ld * u;
-  double* T0 = smem + (size_t)w * (2 * tile + t0 + 64);
+  const int t2 = certify_t2(kGeneral, ld, u);
+  double* T0 = smem + (size_t)w * (tile + t0 + t2 + 64);
   double* T1 = T0 + t0;
   double* T2 = T1 + tile;
-  double* lv = T2 + tile;
+  double* lv = T2 + t2;
   double* dsq = lv + 32;
   const double* Gv = IB.Gv + (size_t)id * kSlot;
   load_tile(T1, ld, IB.Wg + (size_t)id * kSlot, 32, K, K, lane);
@@ -967,6 +991,7 @@ __global__ void k_certify(const Item* __restrict__ items, int n, int u, int ld, 
       // C2 = L^* W L with L = [[I, 0], [C^*, L_S]], blockwise:
       //   Y = W21 + W22 C^* (u x k), Z = W22 L_S (u x u) into T2, then over W
       //   C2_11 = W11 + W12 C^* + C Y, C2_21 = L_S^* Y, C2_22 = L_S^* Z
+      const int ldy = u + 1;
       for (int e = lane; e < u * K; e += 32) {
         const int a = e % u, j = e / u;
         double v;
@@ -978,7 +1003,7 @@ __global__ void k_certify(const Item* __restrict__ items, int n, int u, int ld, 
           v = 0.0;
           for (int p = b; p < u; ++p) v = fma(T1[(k + a) + (k + p) * ld], Sb[p + b * ld], v);
         }
-        T2[a + j * ld] = v;
+        T2[a + j * ldy] = v;
       }
       __syncwarp();
       for (int e = lane; e < tri(K); e += 32) {
@@ -988,11 +1013,11 @@ __global__ void k_certify(const Item* __restrict__ items, int n, int u, int ld, 
         if (i < k) {
           v = T1[i + j * ld];
           for (int q = 0; q < u; ++q) v = fma(T1[i + (k + q) * ld], T0[j + q * ld], v);
-          for (int q = 0; q < u; ++q) v = fma(T0[i + q * ld], T2[q + j * ld], v);
+          for (int q = 0; q < u; ++q) v = fma(T0[i + q * ld], T2[q + j * ldy], v);
         } else {
           const int a = i - k;
           v = 0.0;
-          for (int q = a; q < u; ++q) v = fma(Sb[q + a * ld], T2[q + j * ld], v);
+          for (int q = a; q < u; ++q) v = fma(Sb[q + a * ld], T2[q + j * ldy], v);
         }
         T1[i + j * ld] = v;
       }
@@ -1336,8 +1361,11 @@ void launch_gram_weights(const Pipeline& P, int level) {
   const int n = P.lvl_ptr[level + 1] - P.lvl_ptr[level];
   if (n <= 0) return;
   const int tc = tile_cols(P);
-  smem_limit(k_fweights, tiles_bytes(3, 32, 0), done);
-  k_fweights<<<blocks_for(n), 32 * kWarps, tiles_bytes(3, tc, 0), P.stream>>>(
+  // two warps per block, tiles of (tc + 1) x tc
+  constexpr int warps = 2;
+  const auto bytes = [](int c) { return (size_t)warps * 3 * (c + 1) * c * sizeof(double); };
+  smem_limit(k_fweights, bytes(32), done);
+  k_fweights<<<(n + warps - 1) / warps, 32 * warps, bytes(tc), P.stream>>>(
       P.M, P.items, P.ents, P.lvl_list + P.lvl_ptr[level], n, P.u, tc, P.BW, P.IB);
 }
 
@@ -1346,13 +1374,16 @@ void launch_gram_certify(const Pipeline& P) {
   const int n = P.lvl_ptr[P.levels];
   if (n <= 0) return;
   const int ld = P.kl + 1;
-  const auto bytes = [](int l, int t0) { return (size_t)kWarps * (2 * l * (l - 1) + t0 + 64) * sizeof(double); };
-  smem_limit(k_certify<false>, bytes(33, 33 * 32), done[0]);
-  smem_limit(k_certify<true>, bytes(33, 33 * 32), done[1]);
-  k_certify<false><<<blocks_for(n), 32 * kWarps, bytes(ld, ld * P.u), P.stream>>>(P.items, n, P.u, ld, P.levels,
-                                                                                   P.eps, P.BW, P.IB);
-  k_certify<true><<<blocks_for(n), 32 * kWarps, bytes(ld, ld * (ld - 1)), P.stream>>>(P.items, n, P.u, ld,
-                                                                                      P.levels, P.eps, P.BW, P.IB);
+  const auto bytes = [](bool general, int l, int u) {
+    const int tile = l * (l - 1);
+    return (size_t)kWarps * (tile + (general ? tile : l * u) + certify_t2(general, l, u) + 64) * sizeof(double);
+  };
+  smem_limit(k_certify<false>, bytes(true, 33, 32), done[0]);
+  smem_limit(k_certify<true>, bytes(true, 33, 32), done[1]);
+  k_certify<false><<<blocks_for(n), 32 * kWarps, bytes(false, ld, P.u), P.stream>>>(P.items, n, P.u, ld, P.levels,
+                                                                                     P.eps, P.BW, P.IB);
+  k_certify<true><<<blocks_for(n), 32 * kWarps, bytes(true, ld, P.u), P.stream>>>(P.items, n, P.u, ld, P.levels,
+                                                                                  P.eps, P.BW, P.IB);
 }
 
 // two warps per block: the per-warp tiles, not the block size, limit the

@@ -1340,11 +1340,14 @@ void run_pipeline(const Pipeline& P) {
   cudaStream_t st = P.stream;
   cudaStream_t bs = P.side ? P.side : P.stream;   // stream of the weights of the unchanged matrix
   int64_t pl[H2_PHASE_COUNT] = {};
+  // phase timing events: recorded as external events while the sequence is
+  // captured into a graph, so that they are real records when it runs
+  const unsigned rec = P.capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
   auto start = [&](int ph, cudaStream_t s) {
-    if (P.events) H2_CUDA(cudaEventRecord(P.events[2 * ph], s));
+    if (P.events) H2_CUDA(cudaEventRecordWithFlags(P.events[2 * ph], s, rec));
   };
   auto stop = [&](int ph, cudaStream_t s) {
-    if (P.events) H2_CUDA(cudaEventRecord(P.events[2 * ph + 1], s));
+    if (P.events) H2_CUDA(cudaEventRecordWithFlags(P.events[2 * ph + 1], s, rec));
   };
   auto fork = [&]() {
     if (!P.side) return;

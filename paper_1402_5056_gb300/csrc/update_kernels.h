@@ -72,6 +72,7 @@ struct Pipeline {
   cudaEvent_t join2;
   cudaEvent_t* events;          // 2 * H2_PHASE_COUNT events (start, end per phase) or nullptr
   int64_t* phase_launches;      // host, H2_PHASE_COUNT entries or nullptr
+  bool capturing;               // the launches are being captured into a graph
 };
 
 // Launch the whole update (weights of the unchanged matrix, steps 2-5) on
