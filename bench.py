@@ -41,7 +41,7 @@ PHASE_KERNELS = {"base_weights": "k_orth_local+k_vgram+k_bgram+k_bgram_down", "r
 # matrix (dram__bytes_read.sum + dram__bytes_write.sum of the launch divided
 # by its cluster tasks); the roofline's `traffic` scales them to one launch
 # of the benchmark batch.  Valid for the kernel versions of this commit.
-TRAFFIC_BYTES_PER_TASK = {"k_fweights": 6095, "k_certify": 11019, "k_fbasis": 15607, "k_fgram": 4082}
+TRAFFIC_BYTES_PER_TASK = {"k_certify": 11019, "k_fbasis": 15607, "k_fgram": 4082}
 
 METRIC = "H²-LR setup s & low-rank updates/s, mixed vs FP64 GPU at equal ε; % roofline"
 UNIT = "updates/s"

@@ -1455,7 +1455,12 @@ void phase_flops(h2_ctx* ctx, const h2_batch* P, double f[H2_PHASE_COUNT]) {
   for (const NormTask& nt : P->norms) {
     const double kt = P->items[nt.it].k, ls = P->items[nt.is].k;
     const double Kt = kt + u, Ks = ls + u;
-    if (gram) f[H2_PHASE_NORMS] += 2 * Kt * ls * kt + 2 * kt * Ks * ls + 2 * Kt * Ks;
+    if (gram) {
+      if (orth[0][P->items[nt.it].cluster] && orth[1][P->items[nt.is].cluster])
+        f[H2_PHASE_NORMS] += 2 * kt * ls + 2 * kt * u * ls + 2 * kt * u + 2 * u * u;   // ||S||, <C_t, S C_s>, <N_t, N_s>
+      else
+        f[H2_PHASE_NORMS] += 2 * Kt * ls * kt + 2 * kt * Ks * ls + 2 * Kt * Ks;
+    }
     if (fail[P->items[nt.it].update]) f[H2_PHASE_EXACT] += 2 * kt * ls * Ks + Kt * Kt * Ks + 2 * Kt * Ks;
   }
   for (size_t i = 0; i < ni; ++i) {
@@ -1481,8 +1486,14 @@ void phase_flops(h2_ctx* ctx, const h2_batch* P, double f[H2_PHASE_COUNT]) {
         const Entry& en = P->ents[e];
         const double l = basis_of(Z, 1 - it.side).rank[en.other_cluster];
         if (en.other >= 0) {
-          if (orth_w) f[H2_PHASE_WEIGHTS] += 2 * k * l + 2 * tri(k) * l + 2 * tri(k);
-          f[H2_PHASE_WEIGHTS] += 2 * k * (l + u) * l + 2 * (k * K - tri(k - 1)) * l + 2 * tri(K);
+          if (orth_w) f[H2_PHASE_WEIGHTS] += 2 * k * l;   // ||S_b|| for the base term
+          if (orth[1 - it.side][P->items[en.other].cluster]) {
+            // S' S'^* (shared with the base term), C_o^* S'^*, N_o
+            f[H2_PHASE_WEIGHTS] += 2 * tri(k) * l + 2 * tri(k) + 2 * u * k * l + 2 * tri(u);
+          } else {
+            if (orth_w) f[H2_PHASE_WEIGHTS] += 2 * tri(k) * l + 2 * tri(k);
+            f[H2_PHASE_WEIGHTS] += 2 * k * (l + u) * l + 2 * (k * K - tri(k - 1)) * l + 2 * tri(K);
+          }
         } else if (!orth_w) {
           f[H2_PHASE_WEIGHTS] += 2 * k * k * l + 2 * k * l + 2 * tri(k) * l + 2 * tri(k);
         }

@@ -679,6 +679,32 @@ __global__ void k_fnorms(MatView M, const Item* __restrict__ items, const NormTa
   const int kt = it.k, ls = is.k;
   const int Kt = kt + u, Ks = ls + u;
   const int kcap = M.kcap;
+  const double* Gt = IB.Gv + (size_t)tk.it * kSlot;
+  const double* Gs = IB.Gv + (size_t)tk.is * kSlot;
+  if (BW.orth[0][it.cluster] && BW.orth[1][is.cluster]) {
+    // ||S||^2 + 2 <C_t, S C_s> + <N_t, N_s> (orthonormal V_t, W_s)
+    load_tile(T2, kLd, M.S + (size_t)tk.slot * kcap * kcap, kcap, kt, ls, lane);
+    load_tile(T1, kLd, Gs + ls * 32, 32, ls, u, lane);   // C_s (ls x u)
+    __syncwarp();
+    double part = 0.0;
+    for (int e = lane; e < kt * ls; e += 32) {
+      const double v = T2[e % kt + (e / kt) * kLd];
+      part = fma(v, v, part);
+    }
+    for (int e = lane; e < kt * u; e += 32) {
+      const int i = e % kt, j = e / kt;
+      double v = 0.0;
+      for (int q = 0; q < ls; ++q) v = fma(T2[i + q * kLd], T1[q + j * kLd], v);
+      part = fma(2.0 * Gt[i + (kt + j) * 32], v, part);
+    }
+    for (int e = lane; e < u * u; e += 32) {
+      const int a = e % u, b = e / u;
+      part = fma(Gt[(kt + a) + (kt + b) * 32], Gs[(ls + a) + (ls + b) * 32], part);
+    }
+    const double s2 = warp_sum(part);
+    if (lane == 0) IB.norms[idx] = sqrt(fmax(s2, 0.0));
+    return;
+  }
   load_gram(T0, kLd, IB.Gv + (size_t)tk.it * kSlot, BW.Vg[0] + (size_t)it.cluster * kSlot,
             BW.orth[0][it.cluster] != 0, kt, Kt, lane);
   load_gram(T1, kLd, IB.Gv + (size_t)tk.is * kSlot, BW.Vg[1] + (size_t)is.cluster * kSlot,
@@ -753,18 +779,6 @@ __global__ void k_fweights(MatView M, const Item* __restrict__ items, const Entr
         acc[s] = Wo[i + j * 32];
       }
     }
-    if (it.flags & kItemInside)
-      for (int e = it.ent_begin; e < it.ent_end; ++e) {
-        const Entry en = ents[e];
-        if (en.other < 0) continue;
-        const int l = orank[en.other_cluster];
-        load_block_rows(T0, Sbase + (size_t)en.slot * kcap * kcap, kcap, side, l, k, lane, ld);
-        __syncwarp();
-        const double nrm2 = sum_squares(T0, l, k, lane, ld);
-        const double w2 = nrm2 > 1e-300 ? st * recip(nrm2) : 0.0;
-        acc_gram(acc, T0, l, k, -w2, lane, ld);
-        __syncwarp();
-      }
   } else {
     load_tile(T1, ld, pick(BW.Vg, side) + (size_t)it.cluster * kSlot, 32, k, k, lane);
     for (int e = it.ent_begin; e < it.ent_end; ++e) {
@@ -788,7 +802,11 @@ __global__ void k_fweights(MatView M, const Item* __restrict__ items, const Entr
     }
   }
   if (lane == 0) IB.jac[4 * (size_t)id + 3] = orth ? 0ull : 1ull;
-  // blocks inside the update
+  // blocks inside the update: omega_b^2 P G_o P^*, and, when the outside
+  // part came from Wo_t, minus the block's term in Wo_t (omega0_b^2 S' S'^*,
+  // omega0_b = sqrt(#T_t) / ||S_b||_F).  X = S'^* (l x k) in T0.  For an
+  // orthonormal W_o, G_o = [[I, C_o], [C_o^*, N_o]] and
+  // P G_o P^* = [[S' S'^*, S' C_o], [C_o^* S'^*, N_o]].
   if (it.flags & kItemInside) {
     const double* Vgo = pick(BW.Vg, 1 - side);
     const int32_t* orth_o = pick(BW.orth, 1 - side);
@@ -800,24 +818,48 @@ __global__ void k_fweights(MatView M, const Item* __restrict__ items, const Entr
       const int Ko = l + u;
       const double nrm = IB.norms[en.norm];
       const double w2 = nrm > 1e-150 ? st * recip(nrm * nrm) : 0.0;
-      load_gram(T1, ld, IB.Gv + (size_t)en.other * kSlot, Vgo + (size_t)ot.cluster * kSlot,
-                orth_o[ot.cluster] != 0, l, Ko, lane);
-      // T0 = S' (k x l): S_b on the row side, S_b^* on the column side
-      const double* S = Sbase + (size_t)en.slot * kcap * kcap;
-      if (side == 0) {
-        load_tile(T0, ld, S, kcap, k, l, lane);
-      } else {
-        for (int q = 0; q < l; ++q)
-          if (lane < k) T0[lane + q * ld] = S[q + (size_t)lane * kcap];
-      }
+      const double* Go = IB.Gv + (size_t)en.other * kSlot;
+      load_block_rows(T0, Sbase + (size_t)en.slot * kcap * kcap, kcap, side, l, k, lane, ld);
       __syncwarp();
-      // T2 = P G_o (K x Ko)
+      double w02 = 0.0;
+      if (orth) {
+        const double nrm2 = sum_squares(T0, l, k, lane, ld);
+        w02 = nrm2 > 1e-300 ? st * recip(nrm2) : 0.0;
+      }
+      if (orth_o[ot.cluster]) {
+        load_tile(T1, ld, Go + l * 32, 32, l, u, lane);   // C_o (l x u)
+        __syncwarp();
+        acc_gram(acc, T0, l, k, w2 - w02, lane, ld);
+#pragma unroll
+        for (int s = 0; s < kNS; ++s) {
+          if (32 * s >= nt) break;
+          const int e2 = lane + 32 * s;
+          if (e2 >= ntk && e2 < nt) {
+            int i, j;
+            tri_index(e2, i, j);
+            double v;
+            if (j < k) {
+              v = 0.0;
+              for (int q = 0; q < l; ++q) v = fma(T1[q + (i - k) * ld], T0[q + j * ld], v);
+            } else {
+              v = Go[(l + i - k) + (l + j - k) * 32];
+            }
+            acc[s] = fma(w2, v, acc[s]);
+          }
+        }
+        __syncwarp();
+        continue;
+      }
+      if (orth) acc_gram(acc, T0, l, k, -w02, lane, ld);
+      load_gram(T1, ld, Go, Vgo + (size_t)ot.cluster * kSlot, false, l, Ko, lane);
+      __syncwarp();
+      // T2 = P G_o (K x Ko), S'[i][q] = X[q][i]
       for (int e2 = lane; e2 < K * Ko; e2 += 32) {
         const int i = e2 % K, j = e2 / K;
         double v;
         if (i < k) {
           v = 0.0;
-          for (int q = 0; q < l; ++q) v = fma(T0[i + q * ld], T1[q + j * ld], v);
+          for (int q = 0; q < l; ++q) v = fma(T0[q + i * ld], T1[q + j * ld], v);
         } else {
           v = T1[l + i - k + j * ld];
         }
@@ -834,7 +876,7 @@ __global__ void k_fweights(MatView M, const Item* __restrict__ items, const Entr
           double v;
           if (j < k) {
             v = 0.0;
-            for (int q = 0; q < l; ++q) v = fma(T2[i + q * ld], T0[j + q * ld], v);
+            for (int q = 0; q < l; ++q) v = fma(T2[i + q * ld], T0[q + j * ld], v);
           } else {
             v = T2[i + (l + j - k) * ld];
           }
