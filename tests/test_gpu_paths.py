@@ -232,3 +232,52 @@ def test_certified_path_on_non_orthonormal_bases(ctx):
             assert np.linalg.norm(got - ref) <= TOL * np.linalg.norm(ref), (b0, eps)
     finally:
         b.h2_matrix_free(Zl)
+
+
+@pytest.mark.parametrize("above", [False, True])
+def test_certificate_at_the_rank_threshold(ctx, above):
+    """(eps/2)^2 just below / above lambda_min = sigma_min^2 of the weighted
+    matrix of the cluster closest to the threshold (the oracle's G_t = R^* R,
+    W_t = B~^* B~).  Below: lambda_min - (eps/2)^2 lies between the float64
+    certificate's rounding allowance delta = 8 (levels + 4) (K + 32) u tr(G_t)
+    tr(W_t) and the float32 one, 4 (K + 2) 2^-24 tr(G_t W_t), so only the
+    float64 factorisation can prove that every rank is kept and the update
+    must stay on the certified path.  Above: the rank rule drops a column, the
+    certificate must fail and the exact path must reproduce the truncation."""
+    N, leaf, k, u = 32, 32, 8, 4
+    Zo, st, _ = oracle_problem(N, k, 351, leaf)
+    blocks, A, B = draw_updates(Zo, st, 1, u)
+    b0 = blocks[0]
+    tr = {}
+    local_update(Zo, b0, A[0], B[0], 1e-12, tr)
+    levels = max(max(Zo.V.tree.level), max(Zo.W.tree.level)) + 1
+    cand = []
+    for side in ("V", "W"):
+        for t, R in tr["R" + side].items():
+            G = R.T @ R
+            W = tr["B" + side][t].T @ tr["B" + side][t]
+            lam = float(tr["sig" + side][t][-1]) ** 2
+            K = G.shape[0]
+            delta = 8.0 * (levels + 4) * (K + 32) * np.finfo(float).eps * np.trace(G) * np.trace(W)
+            fp32 = 4.0 * (K + 2) * 2.0 ** -24 * np.trace(G @ W)
+            cand.append((lam, delta, fp32, side, t))
+    cand.sort()
+    lam, delta, fp32, side, t = cand[0]
+    assert delta < 1e-3 * fp32 and cand[1][0] > lam * (1 + 1e-2)
+    tau = lam * (1 + 1e-3) if above else lam - np.sqrt(delta * fp32)
+    eps = 2.0 * np.sqrt(tau)
+    d = local_update(Zo, b0, A[0], B[0], eps)
+    full = _keeps_extended_ranks(Zo, d, u)
+    assert full != above
+    Zl, _, _ = lib_problem(ctx, N, k, 351, leaf)
+    try:
+        P, dA, dB = _batch(ctx, Zl, blocks, A, B, u, eps, b.MODE_AUTO)
+        try:
+            assert b.h2_batch_paths(ctx, P, 1)[0] == (1 if above else 0)
+            ref = apply_delta(Zo, d).dense()
+            got = _dense(ctx, Zl, Zo, P, 0, dA, dB)
+            assert np.linalg.norm(got - ref) <= TOL * np.linalg.norm(ref)
+        finally:
+            b.h2_batch_free(P)
+    finally:
+        b.h2_matrix_free(Zl)
