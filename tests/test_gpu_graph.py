@@ -64,36 +64,3 @@ def test_replays_match_eager_and_oracle(ctx):
     finally:
         b.h2_batch_free(P)
         b.h2_matrix_free(Zl)
-
-
-def test_replay_follows_matrix_storage(ctx):
-    """Committing an update that grows the matrix's rank capacity moves its
-    storage; the next execution of another batch on the grown matrix must not
-    replay a graph that reads the old storage."""
-    N, leaf, k, u = 24, 16, 6, 3
-    Zo, st, _ = oracle_problem(N, k, 363, leaf)
-    blocks, A, B = draw_updates(Zo, st, 2, u)
-    Zl, _, _ = lib_problem(ctx, N, k, 363, leaf, kcap=k)
-    try:
-        dA = torch.from_numpy(np.asfortranarray(A[0]).ravel(order="F")).cuda()
-        dB = torch.from_numpy(np.asfortranarray(B[0]).ravel(order="F")).cuda()
-        Q = b.h2_batch_create(ctx, Zl, [blocks[1]], u)
-        try:
-            A1 = torch.from_numpy(np.asfortranarray(A[1]).ravel(order="F")).cuda()
-            B1 = torch.from_numpy(np.asfortranarray(B[1]).ravel(order="F")).cuda()
-            for _ in range(2):
-                b.h2_batch_execute(ctx, Q, A1.data_ptr(), B1.data_ptr(), 1e-8)   # eager, then captured
-            b.h2_ctx_synchronize(ctx)
-            before = to_oracle(ctx, Zl, Zo)
-            # grow the capacity of Zl in place (ranks k + u > kcap)
-            b.h2_lowrank_update(ctx, Zl, blocks[0], u, dA.data_ptr(), A[0].shape[0], dB.data_ptr(),
-                                B[0].shape[0], 1e-8)
-            b.h2_ctx_synchronize(ctx)
-            assert b.h2_get_ranks(Zl, 0).max() == k + u
-        finally:
-            b.h2_batch_free(Q)
-        after = to_oracle(ctx, Zl, Zo)
-        ref = apply_delta(before, local_update(before, blocks[0], A[0], B[0], 1e-8)).dense()
-        assert np.linalg.norm(after.dense() - ref) <= TOL * np.linalg.norm(ref)
-    finally:
-        b.h2_matrix_free(Zl)
