@@ -216,6 +216,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--serial-steps", type=int, default=2,
+                    help="executions with every phase on one stream, for per-phase device times")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-sample", type=int, default=24)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -311,6 +313,28 @@ def main():
             "peak_source": FP64_PEAK_SOURCE,
             "launch_ms": phases[dom]["ms"] / max(1, phases[dom]["launches"])}
 
+    # every phase alone: the same executions with all phases on one stream,
+    # so that a phase's events time its own kernels without the overlap of
+    # the side streams (per-kernel roofline fractions)
+    phases_serial = None
+    if args.serial_steps > 0:
+        b.h2_batch_set_timing(P, 2)
+        acc = [0.0] * nph
+        for s in range(2 + args.serial_steps):     # eager run, graph capture, replays
+            flush.fill_(s)
+            b.h2_batch_execute(ctx, P, dA.data_ptr(), dB.data_ptr(), w["eps"])
+            b.h2_ctx_synchronize(ctx)
+            if s >= 2:
+                for ph in range(nph):
+                    acc[ph] += b.h2_batch_phase_stats(ctx, P, ph, flops=False)["ms"]
+        b.h2_batch_set_timing(P, True)
+        phases_serial = {}
+        for ph, name in enumerate(b.PHASES):
+            ms = acc[ph] / args.serial_steps
+            tf = phases[name]["gflop"] / ms if ms > 0 else None
+            phases_serial[name] = {"ms": ms, "tflops": tf,
+                                   "frac_fp64_peak": (tf / FP64_PEAK_TFLOPS) if tf else None}
+
     # end to end through the C ABI from pinned host buffers
     e2e = None
     if args.e2e_steps > 0:
@@ -343,7 +367,8 @@ def main():
                        "block_tasks": stats["block_tasks"], "exact_path_updates": n_exact},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": stats["launches"] * args.steps,
-            "clocks": clocks, "phases": phases, "gflop_per_step": stats["flops"] / 1e9}
+            "clocks": clocks, "phases": phases, "phases_serial": phases_serial,
+            "gflop_per_step": stats["flops"] / 1e9}
     if rank == 0:
         print(json.dumps(line))
     b.h2_batch_free(P)

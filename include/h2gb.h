@@ -155,11 +155,31 @@ h2_status h2_batch_factor_sizes(const h2_batch* batch, int64_t* len_A, int64_t* 
 h2_status h2_batch_execute(h2_ctx* ctx, h2_batch* batch, const double* A, const double* B,
                            double eps);
 /* Same, from HOST factor arrays: copies them in, executes, and copies the
- * updates' new couplings and bases back to the host buffer `result` (length
- * from h2_batch_result_size, layout internal), then synchronizes. */
+ * updates' new ranks, bases, transfer matrices and couplings back to the
+ * host buffer `result` (length from h2_batch_result_size, layout from
+ * h2_batch_result_offsets), then synchronizes.  When `result` is
+ * page-locked (cudaHostAlloc / cudaHostRegister) most of it is copied while
+ * the update runs. */
 h2_status h2_batch_execute_host(h2_ctx* ctx, h2_batch* batch, const double* A_host,
                                 const double* B_host, double eps, double* result);
 h2_status h2_batch_result_size(const h2_batch* batch, int64_t* len);
+/* Layout of that result (host arrays of n_cluster_tasks and n_block_tasks
+ * entries, h2_batch_stats).  result[i] = new rank r_i of cluster task i
+ * (h2_batch_item_info).  At item_off[i]: for a leaf cluster its new basis
+ * (#t x r_i, column-major, ld #t), then, unless the cluster is the root of
+ * its tree, its new transfer matrix (r_i x r_f, ld r_i; r_f = the new rank
+ * of the father's task, or for the subtree root t0 the unchanged rank of
+ * its father: the committed E_t0 of Section 5).  At task_off[b]: the new
+ * coupling of block task b (h2_batch_task_info), r_t x r_s, ld r_t, with
+ * r_t the new rank of its row cluster's task or, when the row cluster is
+ * outside the update's subtrees, its unchanged rank (r_s likewise). */
+h2_status h2_batch_result_offsets(const h2_batch* batch, int64_t* item_off, int64_t* task_off);
+/* Block task b of a batch (a coupling the update changes, Section 5):
+ * info[0] update index, info[1] block (block-tree index), info[2] the
+ * cluster task of its row cluster or -1 (row cluster unchanged), info[3]
+ * that of its column cluster or -1, info[4], info[5] the ranks of the row
+ * and column cluster before the update. */
+h2_status h2_batch_task_info(const h2_batch* batch, int64_t task, int32_t* info);
 /* Commit update j's result into dst (Section 5: replace the bases in the
  * subtrees, the transfer matrices E_{t0}, E_{s0} and every affected
  * coupling; add A|_t B|_s^* to the inadmissible leaves inside the block --
@@ -214,8 +234,11 @@ h2_status h2_batch_set_mode(h2_batch* batch, int mode);
  * the exact path computed it, 0 if the certified path did.  Synchronizes. */
 h2_status h2_batch_paths(h2_ctx* ctx, const h2_batch* batch, int32_t* exact);
 
-/* Enable (on != 0) or disable CUDA-event timing of each phase in later
- * executions of this batch (events on the context's stream). */
+/* Enable (on = 1) or disable (on = 0) CUDA-event timing of each phase in
+ * later executions of this batch (events on the context's stream).  on = 2
+ * times the phases with every phase on the context's stream (the side
+ * streams of the certified path unused), so that a phase's time is that of
+ * its own kernels without overlap; the results are the same. */
 h2_status h2_batch_set_timing(h2_batch* batch, int on);
 /* Launches, device time in ms (last execution, only with timing enabled,
  * else -1) and algorithmic float64 flops of one phase.  Synchronizes. */

@@ -27,7 +27,8 @@ EXPORTS = [
     "h2_get_basis", "h2_get_couplings", "h2_get_nearfield", "h2_get_leaf", "h2_get_transfer",
     "h2_get_coupling",
     "h2_batch_create", "h2_batch_free", "h2_batch_factor_layout", "h2_batch_factor_sizes",
-    "h2_batch_execute", "h2_batch_execute_host", "h2_batch_result_size", "h2_batch_apply",
+    "h2_batch_execute", "h2_batch_execute_host", "h2_batch_result_size", "h2_batch_result_offsets",
+    "h2_batch_task_info", "h2_batch_apply",
     "h2_batch_stats", "h2_batch_set_timing", "h2_batch_phase_stats", "h2_batch_item_info", "h2_batch_item_tile",
     "h2_batch_update_items", "h2_batch_set_mode", "h2_batch_paths", "h2_lowrank_update",
     "h2_lowrank_update_noalloc",
@@ -93,6 +94,8 @@ _sig("h2_batch_factor_sizes", _int, _p, _p, _p)
 _sig("h2_batch_execute", _int, _p, _p, _p, _p, _dbl)
 _sig("h2_batch_execute_host", _int, _p, _p, _p, _p, _dbl, _p)
 _sig("h2_batch_result_size", _int, _p, _p)
+_sig("h2_batch_result_offsets", _int, _p, _p, _p)
+_sig("h2_batch_task_info", _int, _p, _i64, _p)
 _sig("h2_batch_apply", _int, _p, _p, _i64, _p, _p, _p)
 _sig("h2_batch_stats", _int, _p, _p, _p, _p, _p, _p)
 _sig("h2_batch_set_timing", _int, _p, _int)
@@ -316,8 +319,10 @@ def h2_batch_stats(ctx, P, flops: bool = True) -> dict:
     return dict(cluster_tasks=a.value, block_tasks=b.value, launches=c.value, flops=f.value if flops else None)
 
 
-def h2_batch_set_timing(P, on: bool):
-    _check(_lib.h2_batch_set_timing(P, 1 if on else 0))
+def h2_batch_set_timing(P, on):
+    """on: False/0 off, True/1 phase events, 2 phase events with every phase
+    on the context's stream (no overlap between phases)."""
+    _check(_lib.h2_batch_set_timing(P, 2 if on == 2 else (1 if on else 0)))
 
 
 def h2_batch_set_mode(P, mode: int):
@@ -340,6 +345,22 @@ def h2_batch_phase_stats(ctx, P, phase: int, flops: bool = True) -> dict:
     _check(_lib.h2_batch_phase_stats(ctx, P, int(phase), C.byref(n), C.byref(ms),
                                      C.byref(f) if flops else None), ctx)
     return dict(launches=n.value, ms=ms.value, flops=f.value if flops else None)
+
+
+def h2_batch_result_offsets(P):
+    """(item_off, task_off): offsets of the pieces of the host result."""
+    st = h2_batch_stats(None, P, flops=False)
+    io = np.zeros(st["cluster_tasks"], np.int64)
+    to = np.zeros(st["block_tasks"], np.int64)
+    _check(_lib.h2_batch_result_offsets(P, _ptr(io), _ptr(to)))
+    return io, to
+
+
+def h2_batch_task_info(P, task: int) -> dict:
+    a = np.zeros(6, np.int32)
+    _check(_lib.h2_batch_task_info(P, int(task), _ptr(a)))
+    return dict(update=int(a[0]), block=int(a[1]), row_item=int(a[2]), col_item=int(a[3]), kt=int(a[4]),
+                ls=int(a[5]))
 
 
 def h2_batch_item_info(P, item: int) -> dict:

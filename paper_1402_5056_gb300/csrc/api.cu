@@ -697,6 +697,17 @@ struct h2_batch {
   // result packing (execute_host)
   std::vector<int64_t> res_task_off, res_item_off;
   int64_t res_len = 0;
+  int64_t res_prefix = 0;                       // ranks, two-sided couplings, bases
+  std::vector<int32_t> one;                     // one-sided coupling tasks, in result order
+  std::vector<int32_t> res_chunk_of;            // per task: chunk of the one-sided region or -1
+  std::vector<int64_t> res_chunk_off;           // chunk boundaries (element offsets)
+  int32_t* d_one = nullptr;
+  int32_t* d_chunk_of = nullptr;
+  int32_t* d_flags = nullptr;                   // per chunk: re-packed after the early copy
+  int32_t* h_flags = nullptr;                   // page-locked copy of d_flags
+  cudaStream_t io = nullptr;                    // stream of the early copies
+  HostOutput out{};
+  double* g_res = nullptr;                      // host destination the graph copies to
   // device
   Item* d_items = nullptr;
   Entry* d_ents = nullptr;
@@ -719,7 +730,7 @@ struct h2_batch {
   int64_t phase_launches[H2_PHASE_COUNT] = {};
   int mode = H2_MODE_AUTO;
   bool executed = false;
-  bool timing = false;
+  int timing = 0;                            // 0 off, 1 phase events, 2 phase events, one stream
   cudaEvent_t ev[2 * H2_PHASE_COUNT] = {};   // start and end of every phase
   cudaStream_t side = nullptr;               // stream of the weights of the unchanged matrix
   cudaEvent_t fork = nullptr, join = nullptr;
@@ -732,7 +743,7 @@ struct h2_batch {
   const double* g_B = nullptr;
   double g_eps = -1.0;
   int g_mode = -1;
-  bool g_timing = false;
+  int g_timing = 0;
   int g_repeats = 0;
   bool g_broken = false;                     // capture failed once: stay eager
   MatView g_view{};                          // the matrix storage the graph reads
@@ -742,6 +753,8 @@ struct h2_batch {
 };
 
 namespace {
+
+constexpr int kResChunks = 64;   // chunks of the one-sided region of a host result
 
 void plan_batch(h2_batch& P) {
   const h2_matrix* Z = P.Z;
@@ -888,15 +901,25 @@ void plan_batch(h2_batch& P) {
     for (int sd = 0; sd < 2; ++sd)
       for (int32_t c = 0; c < tr[sd]->count(); ++c) P.cl_list[f2[tr[sd]->level[c]]++] = (sd << 30) | c;
   }
-  // packed result layout: [ranks of items][couplings][leaf bases / transfers]
-  int64_t off = (int64_t)P.items.size();
-  P.res_task_off.resize(P.tasks.size());
-  for (size_t t = 0; t < P.tasks.size(); ++t) {
-    const Task& tk = P.tasks[t];
+  // packed result layout: [ranks of the cluster tasks][couplings of the
+  // blocks with both clusters changed][leaf bases / transfer matrices][
+  // couplings of the blocks with one cluster changed], each piece at the
+  // size of its largest possible rank.  The last region comes in chunks of
+  // whole blocks (the unit of a repeated copy to the host).
+  P.two.clear();
+  P.one.clear();
+  for (size_t t = 0; t < P.tasks.size(); ++t)
+    (P.tasks[t].it >= 0 && P.tasks[t].is >= 0 ? P.two : P.one).push_back((int32_t)t);
+  auto task_len = [&](const Task& tk) {
     const int R = tk.it >= 0 ? tk.kt + u : tk.kt;
     const int C = tk.is >= 0 ? tk.ls + u : tk.ls;
+    return (int64_t)R * C;
+  };
+  int64_t off = (int64_t)P.items.size();
+  P.res_task_off.assign(P.tasks.size(), 0);
+  for (int32_t t : P.two) {
     P.res_task_off[t] = off;
-    off += (int64_t)R * C;
+    off += task_len(P.tasks[t]);
   }
   P.res_item_off.resize(P.items.size());
   for (size_t i = 0; i < P.items.size(); ++i) {
@@ -909,7 +932,182 @@ void plan_batch(h2_batch& P) {
       off += (int64_t)K * Kf;
     }
   }
+  P.res_prefix = off;
+  int64_t one_len = 0;
+  for (int32_t t : P.one) one_len += task_len(P.tasks[t]);
+  const int64_t per_chunk = std::max<int64_t>(1, (one_len + kResChunks - 1) / kResChunks);
+  P.res_chunk_of.assign(P.tasks.size(), -1);
+  P.res_chunk_off.assign(1, off);
+  for (int32_t t : P.one) {
+    if (off - P.res_chunk_off.back() >= per_chunk) P.res_chunk_off.push_back(off);
+    P.res_task_off[t] = off;
+    P.res_chunk_of[t] = (int32_t)P.res_chunk_off.size() - 1;
+    off += task_len(P.tasks[t]);
+  }
+  P.res_chunk_off.push_back(off);
   P.res_len = off;
+}
+
+// ------------------------------------------------ results to host memory
+// One warp per object.  A coupling task's piece is the new coupling (rows =
+// new rank of the row cluster, or its old rank when only the column cluster
+// changed; column-major, ld = rows); an item's piece is its new leaf basis
+// (#t x r, ld #t, leaves only) followed by its new transfer matrix (r x
+// rank of the father, ld r; the committed E_t0 for the subtree root; none
+// for the tree root); result[i] = new rank of item i.
+__device__ void pack_task(const Task& tk, int t, const ItemBuffers& IB, const int64_t* task_off, double* res,
+                          int lane) {
+  const int rt = tk.it >= 0 ? IB.rank[tk.it] : tk.kt;
+  const int rs = tk.is >= 0 ? IB.rank[tk.is] : tk.ls;
+  const double* S = IB.S_out + (size_t)t * kSlot;
+  double* d = res + task_off[t];
+  for (int e = lane; e < rt * rs; e += 32) d[e] = S[(e % rt) + (e / rt) * 32];
+}
+
+__device__ void pack_item(const Item* items, int i, int u, const ItemBuffers& IB, const int64_t* item_off,
+                          double* res, int lane) {
+  const Item it = items[i];
+  const int r = IB.rank[i];
+  if (lane == 0) res[i] = (double)r;
+  double* d = res + item_off[i];
+  if (it.flags & kItemLeaf) {
+    const double* Q = IB.Q + it.qoff;
+    for (int e = lane; e < it.size * r; e += 32) d[e] = Q[e];
+    d += (size_t)it.size * (it.k + u);
+  }
+  if (!(it.flags & kItemTreeRoot)) {
+    const int rf = (it.flags & kItemRoot) ? it.kf : IB.rank[it.parent];
+    const double* F = IB.F + (size_t)i * kSlot;
+    for (int e = lane; e < r * rf; e += 32) d[e] = F[(e % r) + (e / r) * 32];
+  }
+}
+
+constexpr int kPackWarps = 8;
+
+// Everything, after the update.
+__global__ void k_pack(const Item* items, int ni, const Task* tasks, int nt, int u, ItemBuffers IB,
+                       const int64_t* task_off, const int64_t* item_off, double* res) {
+  const int o = blockIdx.x * kPackWarps + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (o < nt) {
+    pack_task(tasks[o], o, IB, task_off, res, lane);
+  } else if (o < nt + ni) {
+    pack_item(items, o - nt, u, IB, item_off, res, lane);
+  }
+}
+
+// Early: a one-sided coupling task whose changed cluster has an orthonormal
+// basis becomes [S_b; 0] or [S_b, 0] when the update is certified (the old
+// basis stays the leading part of the new one, Section 5 with the block form
+// of the certified path): packed from the unchanged coupling.
+__global__ void k_pack_early(MatView M, const Item* items, const Task* tasks, const int32_t* one, int n_one,
+                             int u, BaseWeights BW, const int64_t* task_off, double* res) {
+  const int o = blockIdx.x * kPackWarps + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (o >= n_one) return;
+  const int t = one[o];
+  const Task tk = tasks[t];
+  const int side = tk.it >= 0 ? 0 : 1;
+  const Item it = items[side == 0 ? tk.it : tk.is];
+  if (!(side ? BW.orth[1] : BW.orth[0])[it.cluster]) return;
+  const int rt = side == 0 ? tk.kt + u : tk.kt;
+  const int rs = side == 0 ? tk.ls : tk.ls + u;
+  const double* S = M.S + (size_t)tk.slot * M.kcap * M.kcap;
+  double* d = res + task_off[t];
+  for (int e = lane; e < rt * rs; e += 32) {
+    const int i = e % rt, j = e / rt;
+    d[e] = (i < tk.kt && j < tk.ls) ? S[i + (size_t)j * M.kcap] : 0.0;
+  }
+}
+
+// Late: the two-sided couplings, the bases and ranks, and the one-sided
+// couplings the early pass did not fix (all of them when it did not run;
+// else those of failed updates or of clusters without an orthonormal basis,
+// whose chunks are flagged for a second copy).
+__global__ void k_pack_late(const Item* items, int ni, const Task* tasks, const int32_t* two, int n_two,
+                            const int32_t* one, int n_one, int u, ItemBuffers IB, BaseWeights BW,
+                            const int64_t* task_off, const int64_t* item_off, const int32_t* chunk_of,
+                            int32_t* flags, int early_ran, double* res) {
+  const int o = blockIdx.x * kPackWarps + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (o < n_two) {
+    const int t = two[o];
+    pack_task(tasks[t], t, IB, task_off, res, lane);
+  } else if (o < n_two + ni) {
+    pack_item(items, o - n_two, u, IB, item_off, res, lane);
+  } else if (o < n_two + ni + n_one) {
+    const int t = one[o - n_two - ni];
+    const Task tk = tasks[t];
+    if (early_ran) {
+      const int side = tk.it >= 0 ? 0 : 1;
+      const Item it = items[side == 0 ? tk.it : tk.is];
+      if (!IB.fail[it.update] && (side ? BW.orth[1] : BW.orth[0])[it.cluster]) return;
+      if (lane == 0) flags[chunk_of[t]] = 1;
+    }
+    pack_task(tk, t, IB, task_off, res, lane);
+  }
+}
+
+int pack_blocks(int64_t n) { return (int)((n + kPackWarps - 1) / kPackWarps); }
+
+void early_output(const Pipeline& pp, const HostOutput& O, cudaStream_t st) {
+  h2_batch& P = *static_cast<h2_batch*>(O.owner);
+  const int n_one = (int)P.one.size();
+  if (n_one > 0)
+    k_pack_early<<<pack_blocks(n_one), 32 * kPackWarps, 0, st>>>(pp.M, pp.items, pp.tasks, P.d_one, n_one, pp.u,
+                                                                  pp.BW, P.d_res_task_off, P.d_res);
+  H2_CUDA(cudaEventRecord(O.packed, st));
+  const int64_t len = P.res_len - P.res_prefix;
+  if (len > 0)
+    H2_CUDA(cudaMemcpyAsync(P.g_res + P.res_prefix, P.d_res + P.res_prefix, len * sizeof(double),
+                            cudaMemcpyDeviceToHost, st));
+}
+
+void late_output(const Pipeline& pp, const HostOutput& O, cudaStream_t st, bool early_ran) {
+  h2_batch& P = *static_cast<h2_batch*>(O.owner);
+  const int n_two = (int)P.two.size(), ni = (int)P.items.size(), n_one = (int)P.one.size();
+  const int nch = (int)P.res_chunk_off.size() - 1;
+  if (early_ran && nch > 0) H2_CUDA(cudaMemsetAsync(P.d_flags, 0, nch * sizeof(int32_t), st));
+  const int64_t n = (int64_t)n_two + ni + n_one;
+  if (n > 0)
+    k_pack_late<<<pack_blocks(n), 32 * kPackWarps, 0, st>>>(pp.items, ni, pp.tasks, P.d_two, n_two, P.d_one, n_one,
+                                                            pp.u, pp.IB, pp.BW, P.d_res_task_off, P.d_res_item_off,
+                                                            P.d_chunk_of, P.d_flags, early_ran ? 1 : 0, P.d_res);
+  if (P.res_prefix > 0)
+    H2_CUDA(cudaMemcpyAsync(P.g_res, P.d_res, P.res_prefix * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (!early_ran) {
+    const int64_t len = P.res_len - P.res_prefix;
+    if (len > 0)
+      H2_CUDA(cudaMemcpyAsync(P.g_res + P.res_prefix, P.d_res + P.res_prefix, len * sizeof(double),
+                              cudaMemcpyDeviceToHost, st));
+  } else if (nch > 0) {
+    H2_CUDA(cudaMemcpyAsync(P.h_flags, P.d_flags, nch * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  }
+}
+
+// Buffers of the host result (first h2_batch_execute_host).
+void alloc_result(h2_batch& P, cudaStream_t st) {
+  if (P.d_res || !P.res_len) return;
+  P.d_res = dalloc<double>(P.res_len);
+  P.d_res_task_off = upload(P.res_task_off, st);
+  P.d_res_item_off = upload(P.res_item_off, st);
+  P.d_one = upload(P.one, st);
+  P.d_chunk_of = upload(P.res_chunk_of, st);
+  const size_t nch = P.res_chunk_off.size() - 1;
+  P.d_flags = dalloc<int32_t>(nch);
+  if (nch) H2_CUDA(cudaHostAlloc(&P.h_flags, nch * sizeof(int32_t), cudaHostAllocDefault));
+  // the early copies' pack kernel runs beside the update's kernels: give its
+  // stream the highest priority so that its blocks do not wait for theirs
+  int lo = 0, hi = 0;
+  H2_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+  H2_CUDA(cudaStreamCreateWithPriority(&P.io, cudaStreamNonBlocking, hi));
+  P.out.stream = P.io;
+  H2_CUDA(cudaEventCreateWithFlags(&P.out.ready, cudaEventDisableTiming));
+  H2_CUDA(cudaEventCreateWithFlags(&P.out.packed, cudaEventDisableTiming));
+  H2_CUDA(cudaEventCreateWithFlags(&P.out.done, cudaEventDisableTiming));
+  P.out.early = early_output;
+  P.out.late = late_output;
+  P.out.owner = &P;
 }
 
 void alloc_batch(h2_ctx* ctx, h2_batch& P) {
@@ -923,10 +1121,8 @@ void alloc_batch(h2_ctx* ctx, h2_batch& P) {
   P.d_items = upload(P.items, st);
   P.d_ents = upload(P.ents, st);
   P.d_tasks = upload(P.tasks, st);
-  P.two.clear();
-  for (size_t t = 0; t < P.tasks.size(); ++t)
-    if (P.tasks[t].it >= 0 && P.tasks[t].is >= 0) P.two.push_back((int32_t)t);
   P.d_two = upload(P.two, st);
+
   P.d_left = dalloc<int32_t>(P.tasks.size());
   P.d_nleft = dalloc<int32_t>(1);
   P.d_norms = upload(P.norms, st);
@@ -969,6 +1165,20 @@ void free_batch_device(h2_batch& P) {
   if (P.side2) cudaStreamSynchronize(P.side2);
   if (P.cap) cudaStreamDestroy(P.cap);
   P.cap = nullptr;
+  if (P.io) {
+    cudaStreamSynchronize(P.io);
+    cudaStreamDestroy(P.io);
+  }
+  P.io = nullptr;
+  for (cudaEvent_t* e : {&P.out.ready, &P.out.packed, &P.out.done}) {
+    if (*e) cudaEventDestroy(*e);
+    *e = nullptr;
+  }
+  if (P.h_flags) cudaFreeHost(P.h_flags);
+  P.h_flags = nullptr;
+  dfree(P.d_one);
+  dfree(P.d_chunk_of);
+  dfree(P.d_flags);
   if (P.join2) cudaEventDestroy(P.join2);
   if (P.side2) cudaStreamDestroy(P.side2);
   P.join2 = nullptr;
@@ -1024,7 +1234,9 @@ bool same_view(const MatView& a, const MatView& b) {
   return a.S == b.S && a.kcap == b.kcap;
 }
 
-void execute(h2_ctx* ctx, h2_batch& P, const double* A, const double* B, double eps) {
+// h_res: page-locked host destination of the packed result (its copies are
+// part of the launch sequence), or nullptr.
+void execute(h2_ctx* ctx, h2_batch& P, const double* A, const double* B, double eps, double* h_res = nullptr) {
   const h2_matrix* Z = P.Z;
   Pipeline pp{};
   pp.M = view_of(Z);
@@ -1063,10 +1275,13 @@ void execute(h2_ctx* ctx, h2_batch& P, const double* A, const double* B, double 
   pp.B = B;
   pp.err = ctx->d_error;
   pp.stream = ctx->stream;
-  pp.side = P.side;
+  // timing mode 2 runs every phase on the context's stream (no overlap), so
+  // that each phase's events time its kernels alone
+  const bool one_stream = P.timing == 2;
+  pp.side = one_stream ? nullptr : P.side;
   pp.fork = P.fork;
   pp.join = P.join;
-  pp.side2 = P.side2;
+  pp.side2 = one_stream ? nullptr : P.side2;
   pp.join2 = P.join2;
   pp.events = P.timing ? P.ev : nullptr;
   pp.phase_launches = P.phase_launches;
@@ -1075,9 +1290,11 @@ void execute(h2_ctx* ctx, h2_batch& P, const double* A, const double* B, double 
   // graph is replayed while the arguments stay the same
   // (the graph holds the matrix's storage pointers, which change when its
   // rank capacity grows, and the context's error word)
+  pp.out = h_res ? &P.out : nullptr;
   const bool same = A == P.g_A && B == P.g_B && eps == P.g_eps && P.mode == P.g_mode && P.timing == P.g_timing &&
-                    ctx == P.g_ctx && same_view(pp.M, P.g_view);
+                    ctx == P.g_ctx && same_view(pp.M, P.g_view) && h_res == P.g_res;
   if (!same) {
+    P.g_res = h_res;
     P.g_view = pp.M;
     P.g_ctx = ctx;
     if (P.graph) cudaGraphExecDestroy(P.graph);
@@ -1202,42 +1419,29 @@ extern "C" h2_status h2_batch_execute(h2_ctx* ctx, h2_batch* P, const double* A,
   });
 }
 
-namespace {
-__global__ void k_pack(const Item* items, int ni, const Task* tasks, int nt, int u, ItemBuffers IB,
-                       const int64_t* task_off, const int64_t* item_off, double* res) {
-  // block-stride over tasks then items; one block per object
-  const int o = blockIdx.x;
-  if (o < nt) {
-    const Task tk = tasks[o];
-    const int rt = tk.it >= 0 ? IB.rank[tk.it] : tk.kt;
-    const int rs = tk.is >= 0 ? IB.rank[tk.is] : tk.ls;
-    const double* S = IB.S_out + (size_t)o * kSlot;
-    double* d = res + task_off[o];
-    for (int e = threadIdx.x; e < rt * rs; e += blockDim.x) d[e] = S[(e % rt) + (e / rt) * 32];
-    return;
-  }
-  const int i = o - nt;
-  if (i >= ni) return;
-  const Item it = items[i];
-  const int r = IB.rank[i];
-  if (threadIdx.x == 0) res[i] = (double)r;
-  double* d = res + item_off[i];
-  if (it.flags & kItemLeaf) {
-    const double* Q = IB.Q + it.qoff;
-    for (int e = threadIdx.x; e < it.size * r; e += blockDim.x) d[e] = Q[e];
-    d += (size_t)it.size * (it.k + u);
-  }
-  if (!(it.flags & kItemTreeRoot)) {
-    const int rf = (it.flags & kItemRoot) ? it.kf : IB.rank[it.parent];
-    const double* F = IB.F + (size_t)i * kSlot;
-    for (int e = threadIdx.x; e < r * rf; e += blockDim.x) d[e] = F[(e % r) + (e / r) * 32];
-  }
-}
-}  // namespace
 
 extern "C" h2_status h2_batch_result_size(const h2_batch* P, int64_t* len) {
   if (!P || !len) return H2_EINVAL;
   *len = P->res_len;
+  return H2_OK;
+}
+
+extern "C" h2_status h2_batch_result_offsets(const h2_batch* P, int64_t* item_off, int64_t* task_off) {
+  if (!P || (!item_off && !P->items.empty()) || (!task_off && !P->tasks.empty())) return H2_EINVAL;
+  std::copy(P->res_item_off.begin(), P->res_item_off.end(), item_off);
+  std::copy(P->res_task_off.begin(), P->res_task_off.end(), task_off);
+  return H2_OK;
+}
+
+extern "C" h2_status h2_batch_task_info(const h2_batch* P, int64_t task, int32_t* info) {
+  if (!P || !info || task < 0 || task >= (int64_t)P->tasks.size()) return H2_EINVAL;
+  const Task& tk = P->tasks[task];
+  info[0] = (int32_t)(std::upper_bound(P->upd_task.begin(), P->upd_task.end(), task) - P->upd_task.begin() - 1);
+  info[1] = P->Z->blocks.adm[tk.slot];
+  info[2] = tk.it;
+  info[3] = tk.is;
+  info[4] = tk.kt;
+  info[5] = tk.ls;
   return H2_OK;
 }
 
@@ -1251,24 +1455,45 @@ extern "C" h2_status h2_batch_execute_host(h2_ctx* ctx, h2_batch* P, const doubl
     cudaStream_t st = ctx->stream;
     if (!P->d_A && P->lenA) P->d_A = dalloc<double>(P->lenA);
     if (!P->d_B && P->lenB) P->d_B = dalloc<double>(P->lenB);
-    if (!P->d_res && P->res_len) {
-      P->d_res = dalloc<double>(P->res_len);
-      P->d_res_task_off = upload(P->res_task_off, st);
-      P->d_res_item_off = upload(P->res_item_off, st);
-    }
+    alloc_result(*P, st);
     if (P->lenA) H2_CUDA(cudaMemcpyAsync(P->d_A, A_host, P->lenA * sizeof(double), cudaMemcpyHostToDevice, st));
     if (P->lenB) H2_CUDA(cudaMemcpyAsync(P->d_B, B_host, P->lenB * sizeof(double), cudaMemcpyHostToDevice, st));
-    execute(ctx, *P, P->d_A, P->d_B, eps);
-    const int nt = (int)P->tasks.size(), ni = (int)P->items.size();
-    if (nt + ni > 0) {
-      k_pack<<<nt + ni, 128, 0, st>>>(P->d_items, ni, P->d_tasks, nt, P->u, P->IB, P->d_res_task_off,
-                                      P->d_res_item_off, P->d_res);
-      H2_CUDA(cudaGetLastError());
-      P->launches += 1;
+    // a page-locked destination receives the result in copies that overlap
+    // the update (part of the launch sequence); any other after it
+    cudaPointerAttributes pa{};
+    const bool pinned = P->res_len > 0 && cudaPointerGetAttributes(&pa, result) == cudaSuccess &&
+                        pa.type == cudaMemoryTypeHost;
+    (void)cudaGetLastError();
+    if (pinned) {
+      execute(ctx, *P, P->d_A, P->d_B, eps, result);
+      P->launches += P->mode != H2_MODE_EXACT ? 2 : 1;
+      H2_CUDA(cudaStreamSynchronize(st));
+      check_device_error(ctx);
+      if (P->mode != H2_MODE_EXACT) {
+        // chunks of the early region that the late pass packed again
+        bool again = false;
+        for (size_t c = 0; c + 1 < P->res_chunk_off.size(); ++c) {
+          if (!P->h_flags[c]) continue;
+          const int64_t a = P->res_chunk_off[c], b = P->res_chunk_off[c + 1];
+          H2_CUDA(cudaMemcpyAsync(result + a, P->d_res + a, (b - a) * sizeof(double), cudaMemcpyDeviceToHost, st));
+          again = true;
+        }
+        if (again) H2_CUDA(cudaStreamSynchronize(st));
+      }
+    } else {
+      execute(ctx, *P, P->d_A, P->d_B, eps);
+      const int64_t n = (int64_t)P->tasks.size() + (int64_t)P->items.size();
+      if (n > 0) {
+        k_pack<<<pack_blocks(n), 32 * kPackWarps, 0, st>>>(P->d_items, (int)P->items.size(), P->d_tasks,
+                                                            (int)P->tasks.size(), P->u, P->IB, P->d_res_task_off,
+                                                            P->d_res_item_off, P->d_res);
+        H2_CUDA(cudaGetLastError());
+        P->launches += 1;
+      }
+      if (P->res_len)
+        H2_CUDA(cudaMemcpyAsync(result, P->d_res, P->res_len * sizeof(double), cudaMemcpyDeviceToHost, st));
+      H2_CUDA(cudaStreamSynchronize(st));
     }
-    if (P->res_len)
-      H2_CUDA(cudaMemcpyAsync(result, P->d_res, P->res_len * sizeof(double), cudaMemcpyDeviceToHost, st));
-    H2_CUDA(cudaStreamSynchronize(st));
     check_device_error(ctx);
   });
 }
@@ -1630,7 +1855,7 @@ extern "C" h2_status h2_batch_set_timing(h2_batch* P, int on) {
       DeviceGuard g(P->device);
       for (cudaEvent_t& e : P->ev) H2_CUDA(cudaEventCreate(&e));
     }
-    P->timing = on != 0;
+    P->timing = on == 2 ? 2 : (on != 0 ? 1 : 0);
   });
 }
 
@@ -1661,7 +1886,10 @@ extern "C" h2_status h2_batch_phase_stats(h2_ctx* ctx, const h2_batch* P, int ph
     if (launches) *launches = P->phase_launches[phase];
     if (ms) {
       *ms = -1.0;
-      if (P->timing && P->ev[0]) {
+      const bool gram_phase = phase != H2_PHASE_EXACT && phase != H2_PHASE_REPROJECT;
+      if (P->timing && P->ev[0] && gram_phase && P->mode == H2_MODE_EXACT) {
+        *ms = 0.0;   // the certified path did not run
+      } else if (P->timing && P->ev[0]) {
         H2_CUDA(cudaEventSynchronize(P->ev[2 * phase + 1]));
         float t = 0;
         H2_CUDA(cudaEventElapsedTime(&t, P->ev[2 * phase], P->ev[2 * phase + 1]));

@@ -168,15 +168,29 @@ __device__ __forceinline__ bool ldl_f32(float* F, int ld, int n, float* lv, int 
   return __all_sync(kFull, ok);
 }
 
+// x 2^-ex as a float32, truncated toward zero (relative error below 2^-23)
+// and flushed to zero below the normal range, by integer operations on the
+// bits of x; |x| < 2^ex.  Leaves the float64 pipe free.
+__device__ __forceinline__ float scaled_f32(double x, int ex) {
+  const unsigned hi = (unsigned)__double2hiint(x);
+  const unsigned lo = (unsigned)__double2loint(x);
+  const int be = (int)((hi >> 20) & 0x7ffu);
+  const int fe = be - 1023 - ex + 127;
+  const unsigned f = (hi & 0x80000000u) | ((unsigned)fe << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  return (be != 0 && fe > 0) ? __uint_as_float(f) : 0.0f;
+}
+
 // Positive definiteness of A - shift I for the n x n lower triangle of the
 // float64 tile A (ld ld), A = L^* W L symmetric positive semidefinite (so
-// |a_ij| <= tr A).  First a float32 LDL^* of (A - (shift + c) I) 2^-e (an
-// exact power-of-two scaling with 2^e ~ tr A) in the scratch tile Fs, with
-// c = 4 (n + 2) 2^-24 tr A: by the verification of positive definiteness
-// through a floating-point Cholesky factorisation of a shifted matrix (Rump,
-// BIT 2006), success proves A - shift I positive definite, c covering the
-// conversion to float32 (n 2^-24 tr A) and the factorisation's backward error
-// (gamma_{n+1} tr A, the approximate reciprocals included) twice over.  When
+// |a_ij| <= tr A, ||A||_F <= tr A).  First a float32 LDL^* of
+// A 2^-e - (shift + c) 2^-e I (2^e ~ tr A, the shift rounded up) in the
+// scratch tile Fs, with c = 4 (n + 2) 2^-24 tr A: by the verification of
+// positive definiteness through a floating-point Cholesky factorisation of a
+// shifted matrix (Rump, BIT 2006), success proves A - shift I positive
+// definite, c covering the truncation to float32 (2^-23 ||A||_F), the
+// rounding of the diagonal shift (2^-24 tr A) and the factorisation's
+// backward error (gamma_{n+1} tr A, the approximate reciprocals included)
+// with a margin of n 2^-24 tr A.  When
 // the float32 factorisation fails, the float64 LDL^* of A - shift I decides
 // (its rounding is inside delta).  A is not modified by the first try.
 // Returns 1 (float32 proof), 2 (float64 proof) or 0 (not positive definite).
@@ -186,12 +200,13 @@ __device__ __forceinline__ int certify_pd(double* A, int ld, int n, double shift
   if (trA > 0.0 && trA < DBL_MAX) {
     int ex = 0;
     frexp(trA, &ex);
-    const double c = shift + 4.0 * (n + 2) * 0x1p-24 * trA;
+    // shift of the float32 matrix, rounded up
+    const float cf = __double2float_ru(ldexp(shift + 4.0 * (n + 2) * 0x1p-24 * trA, -ex));
     for (int e = lane; e < tri(n); e += 32) {
       int i, j;
       tri_index(e, i, j);
-      const double v = i == j ? A[i + j * ld] - c : A[i + j * ld];
-      Fs[i + j * ld] = (float)ldexp(v, -ex);
+      const float v = scaled_f32(A[i + j * ld], ex);
+      Fs[i + j * ld] = i == j ? v - cf : v;
     }
     __syncwarp();
     if (ldl_f32(Fs, ld, n, reinterpret_cast<float*>(lv), lane)) return 1;
@@ -1257,20 +1272,19 @@ __global__ void k_fbasis(MatView M, const Item* __restrict__ items, int n, int u
   __syncwarp();
   if constexpr (!kGeneral) {
     // rows i < k: [E_t, (C_t - E_t C_p) L_Sp^{-*}]; rows k + a: [0, (row a
-    // of L_St^*) L_Sp^{-*}]
+    // of L_St^*) L_Sp^{-*}].  C_t - E_t C_p over all lanes (entry (ii, q)
+    // per lane, in place of C_t in the tile of R_t), then lane = row.
+    for (int e = lane; e < k * u; e += 32) {
+      const int ii = e % k, q = e / k;
+      double v = T0[ii + (k + q) * kLd];
+      for (int p = 0; p < kf; ++p) v = fma(-T2[ii + p * kLd], T1[p + (kf + q) * kLd], v);
+      T0[ii + (k + q) * kLd] = v;
+    }
+    __syncwarp();
     double x[UMAX];
 #pragma unroll
     for (int q = 0; q < UMAX; ++q)
-      if (q < u) {
-        double v = 0.0;
-        if (i < k) {
-          v = T0[i + (k + q) * kLd];
-          for (int p = 0; p < kf; ++p) v = fma(-T2[i + p * kLd], T1[p + (kf + q) * kLd], v);
-        } else if (i < K && k + q >= i) {
-          v = T0[i + (k + q) * kLd];
-        }
-        x[q] = v;
-      }
+      if (q < u) x[q] = (i < K && k + q >= i) ? T0[i + (k + q) * kLd] : 0.0;
 #pragma unroll
     for (int q = 0; q < UMAX; ++q)
       if (q < u) {

@@ -390,6 +390,7 @@ h2_status run(h2_ctx* ctx, h2_matrix* Z, int32_t b0, int u, const double* A, int
   pp.join2 = nullptr;
   pp.events = nullptr;
   pp.phase_launches = nullptr;
+  pp.out = nullptr;
   run_pipeline(pp);
   NA_CUDA(cudaGetLastError());
   // commit (Section 5): new bases, transfers, couplings, nearfield inside b0

@@ -1358,6 +1358,7 @@ void run_pipeline(const Pipeline& P) {
   const int ni = P.lvl_ptr[L];
   const int ncl = P.cl_ptr[L];
   const bool gram = !P.exact_only;
+  bool early_ran = false;
   // per-update path flags and per-cluster marks of the exact path
   if (P.n_updates > 0) H2_CUDA(cudaMemsetAsync(P.IB.fail, gram ? 0 : 1, (size_t)P.n_updates * 4, st));
   H2_CUDA(cudaMemsetAsync(P.n_left, 0, sizeof(int32_t), st));
@@ -1376,6 +1377,15 @@ void run_pipeline(const Pipeline& P) {
     if (ncl > 0) {
       launch_gram_orth(P, vs);
       pl[H2_PHASE_BASE_WEIGHTS] += 2;
+    }
+    if (P.out) {
+      // results that the orthonormality flags already fix go to the host
+      // while the update runs
+      H2_CUDA(cudaEventRecord(P.out->ready, vs));
+      H2_CUDA(cudaStreamWaitEvent(P.out->stream, P.out->ready, 0));
+      P.out->early(P, *P.out, P.out->stream);
+      H2_CUDA(cudaEventRecord(P.out->done, P.out->stream));
+      early_ran = true;
     }
     for (int l = L - 1; l >= 0; --l)
       if (P.cl_ptr[l + 1] > P.cl_ptr[l]) {
@@ -1501,6 +1511,11 @@ void run_pipeline(const Pipeline& P) {
     pl[H2_PHASE_REPROJECT] += 2;
   }
   stop(H2_PHASE_REPROJECT, st);
+  if (P.out) {
+    if (early_ran) H2_CUDA(cudaStreamWaitEvent(st, P.out->packed, 0));
+    P.out->late(P, *P.out, st, early_ran);
+    if (early_ran) H2_CUDA(cudaStreamWaitEvent(st, P.out->done, 0));
+  }
   H2_CUDA(cudaGetLastError());
   if (P.phase_launches)
     for (int ph = 0; ph < H2_PHASE_COUNT; ++ph) P.phase_launches[ph] = pl[ph];

@@ -73,6 +73,21 @@ struct Pipeline {
   cudaEvent_t* events;          // 2 * H2_PHASE_COUNT events (start, end per phase) or nullptr
   int64_t* phase_launches;      // host, H2_PHASE_COUNT entries or nullptr
   bool capturing;               // the launches are being captured into a graph
+  const struct HostOutput* out; // copy of the results to host memory, or nullptr
+};
+
+// Copy of the results to page-locked host memory, overlapped with the
+// update: `early` is launched on `stream` once the orthonormality flags of
+// the unchanged matrix exist (certified path only; `packed` is recorded
+// after its kernels, `done` after its copies), `late` on the main stream
+// after the reprojection (after waiting for `packed` when early ran); the
+// main stream then waits for `done`.
+struct HostOutput {
+  cudaStream_t stream;
+  cudaEvent_t ready, packed, done;
+  void (*early)(const Pipeline& P, const HostOutput& O, cudaStream_t st);
+  void (*late)(const Pipeline& P, const HostOutput& O, cudaStream_t st, bool early_ran);
+  void* owner;
 };
 
 // Launch the whole update (weights of the unchanged matrix, steps 2-5) on
