@@ -185,7 +185,11 @@ h2_status h2_batch_task_info(const h2_batch* batch, int64_t task, int32_t* info)
  * coupling; add A|_t B|_s^* to the inadmissible leaves inside the block --
  * this last part reads A, B again, so pass the same device factors).  dst
  * must have the structure of the planned matrix and, outside the touched
- * subtrees, its ranks; its storage grows if a new rank exceeds capacity. */
+ * subtrees, its ranks; its storage grows if a new rank exceeds capacity.
+ * The couplings that the update keeps ([S_b; 0] and [S_b, 0] of a certified
+ * update whose basis keeps the old one as its leading part) are not stored
+ * by the execution: they are read here from the planned matrix, which must
+ * not have changed since (dst may be that matrix itself). */
 h2_status h2_batch_apply(h2_ctx* ctx, const h2_batch* batch, int64_t j, const double* A,
                          const double* B, h2_matrix* dst);
 /* Statistics of the last execution (host, synchronizes): number of cluster

@@ -690,6 +690,7 @@ struct h2_batch {
   std::vector<int32_t> lvl_list;                // items sorted by level
   std::vector<int32_t> lvl_ptr;                 // per level
   std::vector<int32_t> lvl_maxrows;             // per level: bound on rows of the truncation
+  std::vector<int32_t> lvl_leaves;              // per level: leaves (first in lvl_list)
   std::vector<int32_t> cl_list, cl_ptr;         // clusters of both sides by level (side << 30 | id)
   int depth = 0;
   int kl = 0;                                   // max extended rank
@@ -879,15 +880,20 @@ void plan_batch(h2_batch& P) {
   }
   for (int l = 0; l < L; ++l) P.lvl_ptr[l + 1] += P.lvl_ptr[l];
   P.lvl_list.assign(P.items.size(), 0);
+  P.lvl_leaves.assign(L, 0);
   std::vector<int32_t> fill(P.lvl_ptr.begin(), P.lvl_ptr.end() - 1);
-  for (size_t i = 0; i < P.items.size(); ++i) {
-    const Item& it = P.items[i];
-    const int lev = tr[it.side]->level[it.cluster];
-    P.lvl_list[fill[lev]++] = (int32_t)i;
-    int rows = it.size;
-    if (!(it.flags & kItemLeaf)) rows = P.items[it.son0].k + P.items[it.son1].k + 2 * u;
-    P.lvl_maxrows[lev] = std::max(P.lvl_maxrows[lev], rows);
-  }
+  for (int pass = 0; pass < 2; ++pass)   // leaves first within a level
+    for (size_t i = 0; i < P.items.size(); ++i) {
+      const Item& it = P.items[i];
+      const bool leaf = it.flags & kItemLeaf;
+      if (leaf != (pass == 0)) continue;
+      const int lev = tr[it.side]->level[it.cluster];
+      P.lvl_list[fill[lev]++] = (int32_t)i;
+      if (leaf) ++P.lvl_leaves[lev];
+      int rows = it.size;
+      if (!leaf) rows = P.items[it.son0].k + P.items[it.son1].k + 2 * u;
+      P.lvl_maxrows[lev] = std::max(P.lvl_maxrows[lev], rows);
+    }
   for (int l = 0; l < L; ++l)
     H2_REQUIRE(P.lvl_maxrows[l] <= 64, "h2_batch_create: leaf clusters above 64 indices are not supported");
   // all clusters of both sides by level (weights of the unchanged matrix)
@@ -955,8 +961,24 @@ void plan_batch(h2_batch& P) {
 // (#t x r, ld #t, leaves only) followed by its new transfer matrix (r x
 // rank of the father, ld r; the committed E_t0 for the subtree root; none
 // for the tree root); result[i] = new rank of item i.
-__device__ void pack_task(const Task& tk, int t, const ItemBuffers& IB, const int64_t* task_off, double* res,
-                          int lane) {
+// [S_b; 0] ((k_t + u) x l_s) or [S_b, 0] (k_t x (l_s + u)) from the
+// unchanged coupling.
+__device__ void pack_copy(const MatView& M, const Task& tk, int u, double* d, int lane) {
+  const int rt = tk.it >= 0 ? tk.kt + u : tk.kt;
+  const int rs = tk.it >= 0 ? tk.ls : tk.ls + u;
+  const double* S = M.S + (size_t)tk.slot * M.kcap * M.kcap;
+  for (int e = lane; e < rt * rs; e += 32) {
+    const int i = e % rt, j = e / rt;
+    d[e] = (i < tk.kt && j < tk.ls) ? S[i + (size_t)j * M.kcap] : 0.0;
+  }
+}
+
+__device__ void pack_task(const MatView& M, const Task& tk, int t, int u, const ItemBuffers& IB,
+                          const int64_t* task_off, double* res, int lane) {
+  if (IB.copy[t]) {
+    pack_copy(M, tk, u, res + task_off[t], lane);
+    return;
+  }
   const int rt = tk.it >= 0 ? IB.rank[tk.it] : tk.kt;
   const int rs = tk.is >= 0 ? IB.rank[tk.is] : tk.ls;
   const double* S = IB.S_out + (size_t)t * kSlot;
@@ -985,12 +1007,12 @@ __device__ void pack_item(const Item* items, int i, int u, const ItemBuffers& IB
 constexpr int kPackWarps = 8;
 
 // Everything, after the update.
-__global__ void k_pack(const Item* items, int ni, const Task* tasks, int nt, int u, ItemBuffers IB,
+__global__ void k_pack(MatView M, const Item* items, int ni, const Task* tasks, int nt, int u, ItemBuffers IB,
                        const int64_t* task_off, const int64_t* item_off, double* res) {
   const int o = blockIdx.x * kPackWarps + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (o < nt) {
-    pack_task(tasks[o], o, IB, task_off, res, lane);
+    pack_task(M, tasks[o], o, u, IB, task_off, res, lane);
   } else if (o < nt + ni) {
     pack_item(items, o - nt, u, IB, item_off, res, lane);
   }
@@ -1010,21 +1032,14 @@ __global__ void k_pack_early(MatView M, const Item* items, const Task* tasks, co
   const int side = tk.it >= 0 ? 0 : 1;
   const Item it = items[side == 0 ? tk.it : tk.is];
   if (!(side ? BW.orth[1] : BW.orth[0])[it.cluster]) return;
-  const int rt = side == 0 ? tk.kt + u : tk.kt;
-  const int rs = side == 0 ? tk.ls : tk.ls + u;
-  const double* S = M.S + (size_t)tk.slot * M.kcap * M.kcap;
-  double* d = res + task_off[t];
-  for (int e = lane; e < rt * rs; e += 32) {
-    const int i = e % rt, j = e / rt;
-    d[e] = (i < tk.kt && j < tk.ls) ? S[i + (size_t)j * M.kcap] : 0.0;
-  }
+  pack_copy(M, tk, u, res + task_off[t], lane);
 }
 
 // Late: the two-sided couplings, the bases and ranks, and the one-sided
 // couplings the early pass did not fix (all of them when it did not run;
 // else those of failed updates or of clusters without an orthonormal basis,
 // whose chunks are flagged for a second copy).
-__global__ void k_pack_late(const Item* items, int ni, const Task* tasks, const int32_t* two, int n_two,
+__global__ void k_pack_late(MatView M, const Item* items, int ni, const Task* tasks, const int32_t* two, int n_two,
                             const int32_t* one, int n_one, int u, ItemBuffers IB, BaseWeights BW,
                             const int64_t* task_off, const int64_t* item_off, const int32_t* chunk_of,
                             int32_t* flags, int early_ran, double* res) {
@@ -1032,19 +1047,18 @@ __global__ void k_pack_late(const Item* items, int ni, const Task* tasks, const 
   const int lane = threadIdx.x & 31;
   if (o < n_two) {
     const int t = two[o];
-    pack_task(tasks[t], t, IB, task_off, res, lane);
+    pack_task(M, tasks[t], t, u, IB, task_off, res, lane);
   } else if (o < n_two + ni) {
     pack_item(items, o - n_two, u, IB, item_off, res, lane);
   } else if (o < n_two + ni + n_one) {
     const int t = one[o - n_two - ni];
     const Task tk = tasks[t];
     if (early_ran) {
-      const int side = tk.it >= 0 ? 0 : 1;
-      const Item it = items[side == 0 ? tk.it : tk.is];
-      if (!IB.fail[it.update] && (side ? BW.orth[1] : BW.orth[0])[it.cluster]) return;
+      // the early pass packed exactly the tasks that turned out copies
+      if (IB.copy[t]) return;
       if (lane == 0) flags[chunk_of[t]] = 1;
     }
-    pack_task(tk, t, IB, task_off, res, lane);
+    pack_task(M, tk, t, u, IB, task_off, res, lane);
   }
 }
 
@@ -1070,7 +1084,8 @@ void late_output(const Pipeline& pp, const HostOutput& O, cudaStream_t st, bool 
   if (early_ran && nch > 0) H2_CUDA(cudaMemsetAsync(P.d_flags, 0, nch * sizeof(int32_t), st));
   const int64_t n = (int64_t)n_two + ni + n_one;
   if (n > 0)
-    k_pack_late<<<pack_blocks(n), 32 * kPackWarps, 0, st>>>(pp.items, ni, pp.tasks, P.d_two, n_two, P.d_one, n_one,
+    k_pack_late<<<pack_blocks(n), 32 * kPackWarps, 0, st>>>(pp.M, pp.items, ni, pp.tasks, P.d_two, n_two, P.d_one,
+                                                            n_one,
                                                             pp.u, pp.IB, pp.BW, P.d_res_task_off, P.d_res_item_off,
                                                             P.d_chunk_of, P.d_flags, early_ran ? 1 : 0, P.d_res);
   if (P.res_prefix > 0)
@@ -1141,6 +1156,7 @@ void alloc_batch(h2_ctx* ctx, h2_batch& P) {
   P.IB.own = dalloc<int32_t>(ni);
   P.IB.norms = dalloc<double>(P.norms.size());
   P.IB.S_out = dalloc<double>(P.tasks.size() * kSlot);
+  P.IB.copy = dalloc<int8_t>(P.tasks.size());
   P.IB.jac = dalloc<unsigned long long>(4 * ni);
   if (ni) H2_CUDA(cudaMemsetAsync(P.IB.jac, 0, 4 * ni * sizeof(unsigned long long), st));
   const int32_t ncl[2] = {P.Z->rows.count(), P.Z->cols.count()};
@@ -1217,6 +1233,7 @@ void free_batch_device(h2_batch& P) {
   dfree(P.IB.own);
   dfree(P.IB.norms);
   dfree(P.IB.S_out);
+  dfree(P.IB.copy);
   dfree(P.IB.jac);
   dfree(P.d_A);
   dfree(P.d_B);
@@ -1255,6 +1272,7 @@ void execute(h2_ctx* ctx, h2_batch& P, const double* A, const double* B, double 
   pp.lvl_list = P.d_lvl;
   pp.lvl_ptr = P.lvl_ptr.data();
   pp.lvl_rows = P.lvl_maxrows.data();
+  pp.lvl_leaves = P.lvl_leaves.data();
   pp.cl_list = P.d_cl;
   pp.cl_ptr = P.cl_ptr.data();
   pp.levels = P.depth + 1;
@@ -1484,7 +1502,8 @@ extern "C" h2_status h2_batch_execute_host(h2_ctx* ctx, h2_batch* P, const doubl
       execute(ctx, *P, P->d_A, P->d_B, eps);
       const int64_t n = (int64_t)P->tasks.size() + (int64_t)P->items.size();
       if (n > 0) {
-        k_pack<<<pack_blocks(n), 32 * kPackWarps, 0, st>>>(P->d_items, (int)P->items.size(), P->d_tasks,
+        k_pack<<<pack_blocks(n), 32 * kPackWarps, 0, st>>>(view_of(P->Z), P->d_items, (int)P->items.size(),
+                                                            P->d_tasks,
                                                             (int)P->tasks.size(), P->u, P->IB, P->d_res_task_off,
                                                             P->d_res_item_off, P->d_res);
         H2_CUDA(cudaGetLastError());
@@ -1512,8 +1531,11 @@ extern "C" h2_status h2_batch_apply(h2_ctx* ctx, const h2_batch* P, int64_t j, c
     const int64_t i0 = P->upd_item[j], i1 = P->upd_item[j + 1];
     const int64_t t0 = P->upd_task[j], t1 = P->upd_task[j + 1];
     std::vector<int32_t> rk(i1 - i0);
+    std::vector<int8_t> copy(t1 - t0);
     if (i1 > i0)
       H2_CUDA(cudaMemcpyAsync(rk.data(), P->IB.rank + i0, (i1 - i0) * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    if (t1 > t0)
+      H2_CUDA(cudaMemcpyAsync(copy.data(), P->IB.copy + t0, (t1 - t0) * sizeof(int8_t), cudaMemcpyDeviceToHost, st));
     H2_CUDA(cudaStreamSynchronize(st));
     check_device_error(ctx);
     int kmax = 0;
@@ -1540,8 +1562,20 @@ extern "C" h2_status h2_batch_apply(h2_ctx* ctx, const h2_batch* P, int64_t j, c
       const Task& tk = P->tasks[t];
       const int rt = tk.it >= 0 ? rank_of_item(tk.it) : tk.kt;
       const int rs = tk.is >= 0 ? rank_of_item(tk.is) : tk.ls;
-      if (rt > 0 && rs > 0)
-        cd.push_back({P->IB.S_out + (size_t)t * kSlot, dst->d_S + (size_t)tk.slot * kcap * kcap, rt, rs, 32, kcap});
+      if (rt <= 0 || rs <= 0) continue;
+      double* d = dst->d_S + (size_t)tk.slot * kcap * kcap;
+      if (copy[t - t0]) {
+        // [S_b; 0] or [S_b, 0]: the coupling of the planned matrix (the same
+        // storage when dst is that matrix) and the zero rows or columns
+        if (dst != Z && tk.kt > 0 && tk.ls > 0)
+          cd.push_back({Z->d_S + (size_t)tk.slot * Z->kcap * Z->kcap, d, tk.kt, tk.ls, Z->kcap, kcap});
+        if (tk.it >= 0)
+          cd.push_back({nullptr, d + tk.kt, rt - tk.kt, rs, 0, kcap});
+        else
+          cd.push_back({nullptr, d + (size_t)tk.ls * kcap, rt, rs - tk.ls, 0, kcap});
+        continue;
+      }
+      cd.push_back({P->IB.S_out + (size_t)t * kSlot, d, rt, rs, 32, kcap});
     }
     // nearfield leaves inside the block
     std::vector<NearDesc> nd;

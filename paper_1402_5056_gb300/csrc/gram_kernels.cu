@@ -45,7 +45,6 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kLd = 33;     // leading dimension of the shared tiles (up to 32 rows)
 constexpr int kNS = 17;     // lower-triangle entries of a 32 x 32 matrix per lane: ceil(528 / 32)
-constexpr double kOrthTol = 1e-13;   // |V_t^* V_t - I| entrywise for an orthonormal basis
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -290,6 +289,31 @@ __device__ __forceinline__ void store_sym(double* G, const double (&acc)[kNS], i
   }
 }
 
+// Visit the entries of [begin, end) whose block lies inside the update
+// (other >= 0) or outside it: fetched 32 at a time, one per lane, so that
+// walking a long block row costs one load latency per 32 entries, then
+// broadcast one by one; fn(en) runs on the whole warp.
+template <class Fn>
+__device__ __forceinline__ void for_entries(const Entry* __restrict__ ents, int begin, int end, bool inside,
+                                            int lane, Fn&& fn) {
+  for (int e0 = begin; e0 < end; e0 += 32) {
+    const bool have = e0 + lane < end;
+    Entry mine{0, -1, 0, -1};
+    if (have) mine = ents[e0 + lane];
+    unsigned m = __ballot_sync(kFull, have && ((mine.other >= 0) == inside));
+    while (m) {
+      const int src = __ffs(m) - 1;
+      m &= m - 1;
+      Entry en;
+      en.slot = __shfl_sync(kFull, mine.slot, src);
+      en.other = __shfl_sync(kFull, mine.other, src);
+      en.other_cluster = __shfl_sync(kFull, mine.other_cluster, src);
+      en.norm = __shfl_sync(kFull, mine.norm, src);
+      fn(en);
+    }
+  }
+}
+
 // G_t (K x K) of a cluster task into a tile: the V_t^* V_t block from the
 // unchanged basis (the identity when V_t is orthonormal), C_t and N_t from
 // the task's slot.
@@ -507,68 +531,62 @@ __global__ void k_bgram(MatView M, const int32_t* __restrict__ list, int n, Bloc
   store_sym(pick(BW.Wo, side) + (size_t)c * kSlot, acc, k, lane);
 }
 
-// W0_c = Wo_c + E_c W0_{c+} E_c^* top-down (one launch per level).
+// W0_c = Wo_c + E_c W0_{c+} E_c^* top-down (one launch per level), one
+// block of kDownWarps warps per cluster: the few clusters of the upper levels
+// would otherwise wait on one warp's chain of float64 instructions.
+constexpr int kDownWarps = 4;
+
 __global__ void k_bgram_down(MatView M, const int32_t* __restrict__ list, int n, BaseWeights BW) {
-  extern __shared__ double smem[];
-  const int lane = threadIdx.x & 31;
-  const int w = threadIdx.x >> 5;
-  const int idx = blockIdx.x * (blockDim.x >> 5) + w;
-  if (idx >= n) return;
+  __shared__ double T0[kLd * 32];   // W0_{c+} (kf x kf)
+  __shared__ double T1[kLd * 32];   // E_c (k x kf)
+  __shared__ double T2[kLd * 32];   // E_c W0_{c+} (k x kf)
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int w = tid >> 5;
+  constexpr int nthr = 32 * kDownWarps;
+  if ((int)blockIdx.x >= n) return;
   const int kcap = M.kcap;
-  double* T0 = smem + (size_t)w * 3 * kLd * kcap;
-  double* T1 = T0 + kLd * kcap;
-  double* T2 = T1 + kLd * kcap;
-  const int side = list[idx] >> 30;
-  const int c = list[idx] & 0x3fffffff;
+  const int side = list[blockIdx.x] >> 30;
+  const int c = list[blockIdx.x] & 0x3fffffff;
   const int k = pick(M.rank, side)[c];
-  if (k > 32) return;
+  if (k > 32 || kcap > 32) return;
   const double* Wo = pick(BW.Wo, side) + (size_t)c * kSlot;
+  double* W0 = pick(BW.W0, side) + (size_t)c * kSlot;
   const int f = pick(M.father, side)[c];
   const int nt = tri(k);
-  double acc[kNS];
-#pragma unroll
-  for (int s = 0; s < kNS; ++s) {
-    const int e = lane + 32 * s;
-    double v = 0.0;
-    if (e < nt) {
+  if (f < 0) {
+    for (int e = tid; e < nt; e += nthr) {
       int i, j;
       tri_index(e, i, j);
-      v = Wo[i + j * 32];
+      W0[i + j * 32] = W0[j + i * 32] = Wo[i + j * 32];
     }
-    acc[s] = v;
+    return;
   }
-  if (f >= 0) {
-    const int kf = pick(M.rank, side)[f];
-    load_tile(T0, kLd, pick(BW.W0, side) + (size_t)f * kSlot, 32, kf, kf, lane);
-    load_tile(T1, kLd, pick(M.transfer, side) + (size_t)c * kcap * kcap, kcap, k, kf, lane);
-    __syncwarp();
-    // T2 = E W0_f (k x kf)
-    for (int e = lane; e < k * kf; e += 32) {
-      const int i = e % k, j = e / k;
-      double v = 0.0;
-      for (int q = 0; q < kf; ++q) v = fma(T1[i + q * kLd], T0[q + j * kLd], v);
-      T2[i + j * kLd] = v;
-    }
-    __syncwarp();
-#pragma unroll
-    for (int s = 0; s < kNS; ++s) {
-      if (32 * s >= nt) break;
-      const int e = lane + 32 * s;
-      if (e < nt) {
-        int i, j;
-        tri_index(e, i, j);
-        double v = acc[s];
-        for (int q = 0; q < kf; ++q) v = fma(T2[i + q * kLd], T1[j + q * kLd], v);
-        acc[s] = v;
-      }
-    }
+  const int kf = pick(M.rank, side)[f];
+  if (w == 0) load_tile(T0, kLd, pick(BW.W0, side) + (size_t)f * kSlot, 32, kf, kf, lane);
+  if (w == 1) load_tile(T1, kLd, pick(M.transfer, side) + (size_t)c * kcap * kcap, kcap, k, kf, lane);
+  __syncthreads();
+  for (int e = tid; e < k * kf; e += nthr) {
+    const int i = e % k, j = e / k;
+    double v = 0.0;
+    for (int q = 0; q < kf; ++q) v = fma(T1[i + q * kLd], T0[q + j * kLd], v);
+    T2[i + j * kLd] = v;
   }
-  store_sym(pick(BW.W0, side) + (size_t)c * kSlot, acc, k, lane);
+  __syncthreads();
+  for (int e = tid; e < nt; e += nthr) {
+    int i, j;
+    tri_index(e, i, j);
+    double v = Wo[i + j * 32];
+    for (int q = 0; q < kf; ++q) v = fma(T2[i + q * kLd], T1[j + q * kLd], v);
+    W0[i + j * 32] = W0[j + i * 32] = v;
+  }
 }
 
 // ------------------------------------------------------------- step 2
 // C_t = V_t^* A|_t and N_t = A|_t^* A|_t bottom-up: leaves over chunks of 32
-// rows of (V_t, A|_t), inner clusters C_t = sum E_s^* C_s, N_t = sum N_s.
+// rows of (V_t, A|_t) (k_fgram, one warp per leaf), inner clusters
+// C_t = sum E_s^* C_s, N_t = sum N_s (k_fgram_inner, one block of
+// kInnerWarps warps per cluster: the upper levels have few clusters).
 // Entry e of the per-lane list is C_t[e % k][e / k] for e < k u, then the
 // lower triangle of N_t.  The V_t^* V_t block of G_t comes from k_vgram.
 __global__ void k_fgram(MatView M, const Item* __restrict__ items, const int32_t* __restrict__ list, int n, int u,
@@ -579,8 +597,7 @@ __global__ void k_fgram(MatView M, const Item* __restrict__ items, const int32_t
   const int w = threadIdx.x >> 5;
   const int idx = blockIdx.x * (blockDim.x >> 5) + w;
   if (idx >= n) return;
-  double* T0 = smem + (size_t)w * 2 * kLd * tc;
-  double* T1 = T0 + kLd * tc;
+  double* T0 = smem + (size_t)w * kLd * tc;
   const int id = list[idx];
   const Item it = items[id];
   const int side = it.side;
@@ -595,7 +612,7 @@ __global__ void k_fgram(MatView M, const Item* __restrict__ items, const int32_t
   double acc[kNS];
 #pragma unroll
   for (int s = 0; s < kNS; ++s) acc[s] = 0.0;
-  if (it.flags & kItemLeaf) {
+  {
     const double* V = pick(M.leaf, side) + pick(M.leaf_off, side)[it.cluster];
     const double* F = (side == 0 ? A : B) + it.foff;
     const int m = it.size;
@@ -625,35 +642,6 @@ __global__ void k_fgram(MatView M, const Item* __restrict__ items, const int32_t
       }
       __syncwarp();
     }
-  } else {
-    const int kcap = M.kcap;
-    for (int si = 0; si < 2; ++si) {
-      const int sid = si == 0 ? it.son0 : it.son1;
-      const Item sn = items[sid];
-      const int ks = sn.k;
-      const double* Gs = IB.Gv + (size_t)sid * kSlot;
-      load_tile(T0, kLd, Gs + ks * 32, 32, ks, u, lane);   // C_s (ks x u)
-      load_tile(T1, kLd, pick(M.transfer, side) + (size_t)sn.cluster * kcap * kcap, kcap, ks, k, lane);
-      __syncwarp();
-#pragma unroll
-      for (int s = 0; s < kNS; ++s) {
-        if (32 * s >= nt) break;
-        const int e = lane + 32 * s;
-        if (e < nt) {
-          double v = acc[s];
-          if (e < ncu) {
-            const int i = e % k, j = e / k;
-            for (int q = 0; q < ks; ++q) v = fma(T1[q + i * kLd], T0[q + j * kLd], v);
-          } else {
-            int a, b;
-            tri_index(e - ncu, a, b);
-            v += Gs[(ks + a) + (ks + b) * 32];
-          }
-          acc[s] = v;
-        }
-      }
-      __syncwarp();
-    }
   }
   double* G = IB.Gv + (size_t)id * kSlot;
 #pragma unroll
@@ -673,6 +661,63 @@ __global__ void k_fgram(MatView M, const Item* __restrict__ items, const int32_t
       G[i + j * 32] = acc[s];
       G[j + i * 32] = acc[s];
     }
+  }
+}
+
+constexpr int kInnerWarps = 4;
+
+__global__ void k_fgram_inner(MatView M, const Item* __restrict__ items, const int32_t* __restrict__ list, int n,
+                              int u, ItemBuffers IB, int* err) {
+  __shared__ double Cs[2][kLd * 32];   // C_s (k_s x u) of the two sons
+  __shared__ double Es[2][kLd * 32];   // E_s (k_s x k)
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int w = tid >> 5;
+  if ((int)blockIdx.x >= n) return;
+  const int id = list[blockIdx.x];
+  const Item it = items[id];
+  const int side = it.side;
+  const int k = it.k;
+  const int kcap = M.kcap;
+  if (k + u > 32 || kcap > 32) {
+    if (tid == 0) atomicOr(err, kErrCols);
+    return;
+  }
+  const int sid[2] = {it.son0, it.son1};
+  const int ks0 = items[it.son0].k, ks1 = items[it.son1].k;
+  {
+    const int si = w & 1;
+    const Item sn = items[si ? sid[1] : sid[0]];
+    if (w < 2)
+      load_tile(Cs[si], kLd, IB.Gv + (size_t)(si ? sid[1] : sid[0]) * kSlot + sn.k * 32, 32, sn.k, u, lane);
+    else
+      load_tile(Es[si], kLd, pick(M.transfer, side) + (size_t)sn.cluster * kcap * kcap, kcap, sn.k, k, lane);
+  }
+  __syncthreads();
+  const int ncu = k * u;
+  const int nt = ncu + tri(u);
+  const double* G0 = IB.Gv + (size_t)it.son0 * kSlot;
+  const double* G1 = IB.Gv + (size_t)it.son1 * kSlot;
+  double* G = IB.Gv + (size_t)id * kSlot;
+  for (int e = tid; e < nt; e += 32 * kInnerWarps) {
+    int i, j;
+    double v = 0.0;
+    if (e < ncu) {
+      i = e % k;
+      j = e / k;
+      for (int q = 0; q < ks0; ++q) v = fma(Es[0][q + i * kLd], Cs[0][q + j * kLd], v);
+      for (int q = 0; q < ks1; ++q) v = fma(Es[1][q + i * kLd], Cs[1][q + j * kLd], v);
+      j += k;
+    } else {
+      int a, b;
+      tri_index(e - ncu, a, b);
+      v += G0[(ks0 + a) + (ks0 + b) * 32];
+      v += G1[(ks1 + a) + (ks1 + b) * 32];
+      i = k + a;
+      j = k + b;
+    }
+    G[i + j * 32] = v;
+    G[j + i * 32] = v;
   }
 }
 
@@ -756,19 +801,11 @@ __global__ void k_fnorms(MatView M, const Item* __restrict__ items, const NormTa
 // on the row side, diag(S_b^*, I_u) on the column side), plus the father's
 // part E~_t W_{t+} E~_t^* (subtree root: E_t W0_{t+} E_t^* of the unchanged
 // matrix).
-__global__ void k_fweights(MatView M, const Item* __restrict__ items, const Entry* __restrict__ ents,
-                           const int32_t* __restrict__ list, int n, int u, int tc, BaseWeights BW, ItemBuffers IB) {
-  extern __shared__ double smem[];
-  const int lane = threadIdx.x & 31;
-  const int w = threadIdx.x >> 5;
-  const int idx = blockIdx.x * (blockDim.x >> 5) + w;
-  if (idx >= n) return;
-  // every tile holds at most max(K, kcap) = tc rows: leading dimension tc + 1
-  const int ld = tc + 1;
-  double* T0 = smem + (size_t)w * 3 * ld * tc;
-  double* T1 = T0 + ld * tc;
-  double* T2 = T1 + ld * tc;
-  const int id = list[idx];
+// One warp: cluster task id with its three tiles (leading dimension ld).
+__device__ __forceinline__ void fweights_warp(const MatView& M, const Item* __restrict__ items,
+                                              const Entry* __restrict__ ents, int id, int u, int ld,
+                                              const BaseWeights& BW, const ItemBuffers& IB, double* T0, double* T1,
+                                              double* T2, int lane) {
   const Item it = items[id];
   const int side = it.side;
   const int k = it.k;
@@ -796,9 +833,7 @@ __global__ void k_fweights(MatView M, const Item* __restrict__ items, const Entr
     }
   } else {
     load_tile(T1, ld, pick(BW.Vg, side) + (size_t)it.cluster * kSlot, 32, k, k, lane);
-    for (int e = it.ent_begin; e < it.ent_end; ++e) {
-      const Entry en = ents[e];
-      if (en.other >= 0) continue;
+    for_entries(ents, it.ent_begin, it.ent_end, false, lane, [&](const Entry& en) {
       const int l = orank[en.other_cluster];
       load_block_rows(T0, Sbase + (size_t)en.slot * kcap * kcap, kcap, side, l, k, lane, ld);
       __syncwarp();
@@ -814,7 +849,7 @@ __global__ void k_fweights(MatView M, const Item* __restrict__ items, const Entr
       const double w2 = nrm2 > 1e-300 ? st * recip(nrm2) : 0.0;
       acc_gram(acc, T0, l, k, w2, lane, ld);
       __syncwarp();
-    }
+    });
   }
   if (lane == 0) IB.jac[4 * (size_t)id + 3] = orth ? 0ull : 1ull;
   // blocks inside the update: omega_b^2 P G_o P^*, and, when the outside
@@ -825,9 +860,7 @@ __global__ void k_fweights(MatView M, const Item* __restrict__ items, const Entr
   if (it.flags & kItemInside) {
     const double* Vgo = pick(BW.Vg, 1 - side);
     const int32_t* orth_o = pick(BW.orth, 1 - side);
-    for (int e = it.ent_begin; e < it.ent_end; ++e) {
-      const Entry en = ents[e];
-      if (en.other < 0) continue;
+    for_entries(ents, it.ent_begin, it.ent_end, true, lane, [&](const Entry& en) {
       const Item ot = items[en.other];
       const int l = ot.k;
       const int Ko = l + u;
@@ -863,7 +896,7 @@ __global__ void k_fweights(MatView M, const Item* __restrict__ items, const Entr
           }
         }
         __syncwarp();
-        continue;
+        return;
       }
       if (orth) acc_gram(acc, T0, l, k, -w02, lane, ld);
       load_gram(T1, ld, Go, Vgo + (size_t)ot.cluster * kSlot, false, l, Ko, lane);
@@ -899,7 +932,7 @@ __global__ void k_fweights(MatView M, const Item* __restrict__ items, const Entr
         }
       }
       __syncwarp();
-    }
+    });
   }
   // father's part
   const double* E = pick(M.transfer, side) + (size_t)it.cluster * kcap * kcap;   // k x kf
@@ -978,6 +1011,209 @@ __global__ void k_fweights(MatView M, const Item* __restrict__ items, const Entr
     }
   }
   store_sym(IB.Wg + (size_t)id * kSlot, acc, K, lane);
+}
+
+__global__ void k_fweights(MatView M, const Item* __restrict__ items, const Entry* __restrict__ ents,
+                           const int32_t* __restrict__ list, int n, int u, int tc, BaseWeights BW, ItemBuffers IB) {
+  extern __shared__ double smem[];
+  const int lane = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5;
+  const int idx = blockIdx.x * (blockDim.x >> 5) + w;
+  if (idx >= n) return;
+  // every tile holds at most max(K, kcap) = tc rows: leading dimension tc + 1
+  const int ld = tc + 1;
+  double* T0 = smem + (size_t)w * 3 * ld * tc;
+  fweights_warp(M, items, ents, list[idx], u, ld, BW, IB, T0, T0 + ld * tc, T0 + 2 * ld * tc, lane);
+}
+
+// The same with one block of kWideWarps warps per cluster task, for the
+// levels with few tasks (where one warp's chain of instructions would set
+// the launch's duration): the entries of W_t and of the products are spread
+// over the block, each entry of W_t summed by one thread in the order of
+// k_fweights, so that both kernels give the same bits.  Tasks whose V_t is
+// not orthonormal run the one-warp code on warp 0.
+constexpr int kWideWarps = 4;
+constexpr int kWideMaxTasks = 1024;   // levels with at most this many tasks take k_fweights_wide
+constexpr int kWideThreads = 32 * kWideWarps;
+constexpr int kWS = (kNS * 32 + kWideThreads - 1) / kWideThreads;   // entries of W_t per thread
+
+__global__ void k_fweights_wide(MatView M, const Item* __restrict__ items, const Entry* __restrict__ ents,
+                                const int32_t* __restrict__ list, int n, int u, int tc, BaseWeights BW,
+                                ItemBuffers IB) {
+  extern __shared__ double smem[];
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int w = tid >> 5;
+  if ((int)blockIdx.x >= n) return;
+  const int ld = tc + 1;
+  double* T0 = smem;
+  double* T1 = T0 + ld * tc;
+  double* T2 = T1 + ld * tc;
+  const int id = list[blockIdx.x];
+  const Item it = items[id];
+  const int side = it.side;
+  if (!pick(BW.orth, side)[it.cluster]) {
+    if (w == 0) fweights_warp(M, items, ents, id, u, ld, BW, IB, T0, T1, T2, lane);
+    return;
+  }
+  const int k = it.k;
+  const int K = k + u;
+  const int kcap = M.kcap;
+  const int nt = tri(K);
+  const int ntk = tri(k);
+  const double st = (double)pick(M.subtree, side)[it.cluster];
+  double acc[kWS];
+  int ei[kWS], ej[kWS];
+#pragma unroll
+  for (int s = 0; s < kWS; ++s) {
+    const int e = tid + kWideThreads * s;
+    int i = 0, j = 0;
+    if (e < nt) tri_index(e, i, j);
+    ei[s] = i;
+    ej[s] = j;
+    acc[s] = e < ntk ? pick(BW.Wo, side)[(size_t)it.cluster * kSlot + i + j * 32] : 0.0;
+  }
+  if (tid == 0) IB.jac[4 * (size_t)id + 3] = 0ull;
+  if (it.flags & kItemInside) {
+    const double* Vgo = pick(BW.Vg, 1 - side);
+    const int32_t* orth_o = pick(BW.orth, 1 - side);
+    // every warp walks the same entries, so that all reach the same barriers
+    for_entries(ents, it.ent_begin, it.ent_end, true, lane, [&](const Entry& en) {
+      const Item ot = items[en.other];
+      const int l = ot.k;
+      const int Ko = l + u;
+      const double nrm = IB.norms[en.norm];
+      const double w2 = nrm > 1e-150 ? st * recip(nrm * nrm) : 0.0;
+      const double* Go = IB.Gv + (size_t)en.other * kSlot;
+      const bool oo = orth_o[ot.cluster] != 0;
+      if (w == 0) load_block_rows(T0, M.S + (size_t)en.slot * kcap * kcap, kcap, side, l, k, lane, ld);
+      if (w == 1) {
+        if (oo)
+          load_tile(T1, ld, Go + l * 32, 32, l, u, lane);   // C_o (l x u)
+        else
+          load_gram(T1, ld, Go, Vgo + (size_t)ot.cluster * kSlot, false, l, Ko, lane);
+      }
+      __syncthreads();
+      const double nrm2 = sum_squares(T0, l, k, lane, ld);   // the same in every warp
+      const double w02 = nrm2 > 1e-300 ? st * recip(nrm2) : 0.0;
+      const double wb = oo ? w2 - w02 : -w02;
+#pragma unroll
+      for (int s = 0; s < kWS; ++s) {
+        const int e = tid + kWideThreads * s;
+        if (e < ntk) {
+          double g = 0.0;
+          for (int r = 0; r < l; ++r) g = fma(T0[r + ei[s] * ld], T0[r + ej[s] * ld], g);
+          acc[s] = fma(wb, g, acc[s]);
+        }
+      }
+      if (oo) {
+#pragma unroll
+        for (int s = 0; s < kWS; ++s) {
+          const int e = tid + kWideThreads * s;
+          if (e >= ntk && e < nt) {
+            const int i = ei[s], j = ej[s];
+            double v;
+            if (j < k) {
+              v = 0.0;
+              for (int q = 0; q < l; ++q) v = fma(T1[q + (i - k) * ld], T0[q + j * ld], v);
+            } else {
+              v = Go[(l + i - k) + (l + j - k) * 32];
+            }
+            acc[s] = fma(w2, v, acc[s]);
+          }
+        }
+        __syncthreads();
+        return;
+      }
+      // T2 = P G_o (K x Ko), S'[i][q] = X[q][i]
+      for (int e2 = tid; e2 < K * Ko; e2 += kWideThreads) {
+        const int i = e2 % K, j = e2 / K;
+        double v;
+        if (i < k) {
+          v = 0.0;
+          for (int q = 0; q < l; ++q) v = fma(T0[q + i * ld], T1[q + j * ld], v);
+        } else {
+          v = T1[l + i - k + j * ld];
+        }
+        T2[i + j * ld] = v;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int s = 0; s < kWS; ++s) {
+        const int e = tid + kWideThreads * s;
+        if (e < nt) {
+          const int i = ei[s], j = ej[s];
+          double v;
+          if (j < k) {
+            v = 0.0;
+            for (int q = 0; q < l; ++q) v = fma(T2[i + q * ld], T0[q + j * ld], v);
+          } else {
+            v = T2[i + (l + j - k) * ld];
+          }
+          acc[s] = fma(w2, v, acc[s]);
+        }
+      }
+      __syncthreads();
+    });
+  }
+  // father's part
+  const double* E = pick(M.transfer, side) + (size_t)it.cluster * kcap * kcap;   // k x kf
+  const bool root = it.flags & kItemRoot;
+  if (!root || !(it.flags & kItemTreeRoot)) {
+    const int kf = root ? it.kf : items[it.parent].k;
+    const int Kf = root ? kf : kf + u;
+    if (w == 0) {
+      if (root)
+        load_tile(T1, ld, pick(BW.W0, side) + (size_t)pick(M.father, side)[it.cluster] * kSlot, 32, kf, kf, lane);
+      else
+        load_tile(T1, ld, IB.Wg + (size_t)it.parent * kSlot, 32, Kf, Kf, lane);
+    }
+    if (w == 1) load_tile(T0, ld, E, kcap, k, kf, lane);
+    __syncthreads();
+    // T2 = E W11 (k x kf)
+    for (int e2 = tid; e2 < k * kf; e2 += kWideThreads) {
+      const int i = e2 % k, j = e2 / k;
+      double v = 0.0;
+      for (int q = 0; q < kf; ++q) v = fma(T0[i + q * ld], T1[q + j * ld], v);
+      T2[i + j * ld] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < kWS; ++s) {
+      const int e = tid + kWideThreads * s;
+      if (e < ntk) {
+        double v = acc[s];
+        for (int q = 0; q < kf; ++q) v = fma(T2[ei[s] + q * ld], T0[ej[s] + q * ld], v);
+        acc[s] = v;
+      }
+    }
+    if (!root) {
+      // (i >= k, j < k): rows kf + i - k of W_p times E^*; (i, j >= k): W22
+#pragma unroll
+      for (int s = 0; s < kWS; ++s) {
+        const int e = tid + kWideThreads * s;
+        if (e >= ntk && e < nt) {
+          const int i = ei[s], j = ej[s];
+          double v = acc[s];
+          if (j < k) {
+            for (int q = 0; q < kf; ++q) v = fma(T1[(kf + i - k) + q * ld], T0[j + q * ld], v);
+          } else {
+            v += T1[(kf + i - k) + (kf + j - k) * ld];
+          }
+          acc[s] = v;
+        }
+      }
+    }
+  }
+  double* G = IB.Wg + (size_t)id * kSlot;
+#pragma unroll
+  for (int s = 0; s < kWS; ++s) {
+    const int e = tid + kWideThreads * s;
+    if (e < nt) {
+      G[ei[s] + ej[s] * 32] = acc[s];
+      G[ej[s] + ei[s] * 32] = acc[s];
+    }
+  }
 }
 
 // ------------------------------------------------------------- step 4
@@ -1154,10 +1390,13 @@ __global__ void k_fbasis(MatView M, const Item* __restrict__ items, int n, int u
   const int w = threadIdx.x >> 5;
   const int id = blockIdx.x * (blockDim.x >> 5) + w;
   if (id >= n) return;
-  double* T0 = smem + (size_t)w * (3 * kLd * tc + 32);
-  double* T1 = T0 + kLd * tc;
+  // R_t and E_t tiles with leading dimension tc + 1, the tile of 32 rows of
+  // V_t (or R_{t+}) with kLd
+  const int ldt = tc + 1;
+  double* T0 = smem + (size_t)w * (2 * ldt * tc + kLd * tc + 32);
+  double* T1 = T0 + ldt * tc;
   double* T2 = T1 + kLd * tc;
-  double* ri = T2 + kLd * tc;
+  double* ri = T2 + ldt * tc;
   const Item it = items[id];
   const int side = it.side;
   if (IB.fail[it.update]) {
@@ -1182,10 +1421,10 @@ __global__ void k_fbasis(MatView M, const Item* __restrict__ items, int n, int u
   const bool do_transfer = has_transfer && ((root ? orth : orth && orth_p) == !kGeneral);
   if (!do_leaf && !do_transfer) return;
   // R_t = L_t^* (upper) into T0, as stored
-  load_tile(T0, kLd, IB.Rt + (size_t)id * kSlot, 32, K, K, lane);   // zero below the diagonal
+  load_tile(T0, ldt, IB.Rt + (size_t)id * kSlot, 32, K, K, lane);   // zero below the diagonal
   __syncwarp();
   if (do_leaf) {
-    if (lane < K) ri[lane] = recip(T0[lane * (kLd + 1)]);
+    if (lane < K) ri[lane] = recip(T0[lane * (ldt + 1)]);
     __syncwarp();
     const double* V = pick(M.leaf, side) + pick(M.leaf_off, side)[it.cluster];
     const double* F = (side == 0 ? A : B) + it.foff;
@@ -1206,9 +1445,9 @@ __global__ void k_fbasis(MatView M, const Item* __restrict__ items, int n, int u
         for (int q = 0; q < UMAX; ++q)
           if (q < u) {
             double a = act ? F[(it.rowoff + r) + (size_t)q * it.ld] : 0.0;
-            for (int p = 0; p < k; ++p) a = fma(-T1[lane + p * kLd], T0[p + (k + q) * kLd], a);
+            for (int p = 0; p < k; ++p) a = fma(-T1[lane + p * kLd], T0[p + (k + q) * ldt], a);
 #pragma unroll
-            for (int p = 0; p < q; ++p) a = fma(-T0[(k + p) + (k + q) * kLd], y[p], a);
+            for (int p = 0; p < q; ++p) a = fma(-T0[(k + p) + (k + q) * ldt], y[p], a);
             y[q] = a * ri[k + q];
           }
         if (act)
@@ -1223,7 +1462,7 @@ __global__ void k_fbasis(MatView M, const Item* __restrict__ items, int n, int u
             double v = 0.0;
             if (act) v = c < k ? V[r + (size_t)c * m] : F[(it.rowoff + r) + (size_t)(c - k) * it.ld];
 #pragma unroll
-            for (int p = 0; p < c; ++p) v = fma(-T0[p + c * kLd], y[p], v);
+            for (int p = 0; p < c; ++p) v = fma(-T0[p + c * ldt], y[p], v);
             y[c] = v * ri[c];
           }
         }
@@ -1237,7 +1476,7 @@ __global__ void k_fbasis(MatView M, const Item* __restrict__ items, int n, int u
   }
   if (!do_transfer) return;
   const int kf = it.kf;
-  load_tile(T2, kLd, pick(M.transfer, side) + (size_t)it.cluster * kcap * kcap, kcap, k, kf, lane);
+  load_tile(T2, ldt, pick(M.transfer, side) + (size_t)it.cluster * kcap * kcap, kcap, k, kf, lane);
   double* Fo = IB.F + (size_t)id * kSlot;
   const int i = lane;
   __syncwarp();
@@ -1246,17 +1485,17 @@ __global__ void k_fbasis(MatView M, const Item* __restrict__ items, int n, int u
     // V_t0 is orthonormal
     if constexpr (!kGeneral) {
       if (i < K)
-        for (int j = 0; j < kf; ++j) Fo[i + j * 32] = i < k ? T2[i + j * kLd] : 0.0;
+        for (int j = 0; j < kf; ++j) Fo[i + j * 32] = i < k ? T2[i + j * ldt] : 0.0;
       return;
     }
     double z[32];
 #pragma unroll
     for (int j = 0; j < 32; ++j) z[j] = 0.0;
     for (int q = 0; q < k; ++q) {
-      const double lq = (i < K && q >= i) ? T0[i + q * kLd] : 0.0;
+      const double lq = (i < K && q >= i) ? T0[i + q * ldt] : 0.0;
 #pragma unroll
       for (int j = 0; j < 32; ++j)
-        if (j < kf) z[j] = fma(lq, T2[q + j * kLd], z[j]);
+        if (j < kf) z[j] = fma(lq, T2[q + j * ldt], z[j]);
     }
     if (i < K)
 #pragma unroll
@@ -1276,15 +1515,15 @@ __global__ void k_fbasis(MatView M, const Item* __restrict__ items, int n, int u
     // per lane, in place of C_t in the tile of R_t), then lane = row.
     for (int e = lane; e < k * u; e += 32) {
       const int ii = e % k, q = e / k;
-      double v = T0[ii + (k + q) * kLd];
-      for (int p = 0; p < kf; ++p) v = fma(-T2[ii + p * kLd], T1[p + (kf + q) * kLd], v);
-      T0[ii + (k + q) * kLd] = v;
+      double v = T0[ii + (k + q) * ldt];
+      for (int p = 0; p < kf; ++p) v = fma(-T2[ii + p * ldt], T1[p + (kf + q) * kLd], v);
+      T0[ii + (k + q) * ldt] = v;
     }
     __syncwarp();
     double x[UMAX];
 #pragma unroll
     for (int q = 0; q < UMAX; ++q)
-      if (q < u) x[q] = (i < K && k + q >= i) ? T0[i + (k + q) * kLd] : 0.0;
+      if (q < u) x[q] = (i < K && k + q >= i) ? T0[i + (k + q) * ldt] : 0.0;
 #pragma unroll
     for (int q = 0; q < UMAX; ++q)
       if (q < u) {
@@ -1294,7 +1533,7 @@ __global__ void k_fbasis(MatView M, const Item* __restrict__ items, int n, int u
         x[q] = v * ri[kf + q];
       }
     if (i < K) {
-      for (int j = 0; j < kf; ++j) Fo[i + j * 32] = i < k ? T2[i + j * kLd] : 0.0;
+      for (int j = 0; j < kf; ++j) Fo[i + j * 32] = i < k ? T2[i + j * ldt] : 0.0;
 #pragma unroll
       for (int q = 0; q < UMAX; ++q)
         if (q < u) Fo[i + (kf + q) * 32] = x[q];
@@ -1306,17 +1545,17 @@ __global__ void k_fbasis(MatView M, const Item* __restrict__ items, int n, int u
 #pragma unroll
   for (int j = 0; j < 32; ++j) z[j] = 0.0;
   for (int q = 0; q < k; ++q) {
-    const double lq = (i < K && q >= i) ? T0[i + q * kLd] : 0.0;
+    const double lq = (i < K && q >= i) ? T0[i + q * ldt] : 0.0;
 #pragma unroll
     for (int j = 0; j < 32; ++j)
-      if (j < kf) z[j] = fma(lq, T2[q + j * kLd], z[j]);
+      if (j < kf) z[j] = fma(lq, T2[q + j * ldt], z[j]);
   }
   // identity part of E~_t: column kf + jj picks row k + jj of L_t^*
 #pragma unroll
   for (int j = 0; j < 32; ++j)
     if (j >= kf && j < Kf) {
       const int q = k + j - kf;
-      z[j] = (i < K && q >= i) ? T0[i + q * kLd] : 0.0;
+      z[j] = (i < K && q >= i) ? T0[i + q * ldt] : 0.0;
     }
   // z <- z L_p^{-*}: forward substitution over the columns
 #pragma unroll
@@ -1335,6 +1574,9 @@ __global__ void k_fbasis(MatView M, const Item* __restrict__ items, int n, int u
 }
 
 constexpr int kWarps = 4;
+
+// Shared doubles of one k_fbasis warp (tiles of tc columns).
+constexpr int fbasis_doubles(int tc) { return 2 * (tc + 1) * tc + kLd * tc + 32; }
 
 int blocks_for(int n) { return (n + kWarps - 1) / kWarps; }
 
@@ -1385,22 +1627,30 @@ void launch_gram_base(const Pipeline& P, cudaStream_t st) {
 }
 
 void launch_gram_base_level(const Pipeline& P, int level, cudaStream_t st) {
-  static unsigned long long done = 0;
   const int n = P.cl_ptr[level + 1] - P.cl_ptr[level];
   if (n <= 0) return;
-  smem_limit(k_bgram_down, tiles_bytes(3, 32, 0), done);
-  k_bgram_down<<<blocks_for(n), 32 * kWarps, tiles_bytes(3, P.M.kcap, 0), st>>>(P.M, P.cl_list + P.cl_ptr[level],
-                                                                               n, P.BW);
+  k_bgram_down<<<n, 32 * kDownWarps, 0, st>>>(P.M, P.cl_list + P.cl_ptr[level], n, P.BW);
 }
 
-void launch_gram_basis(const Pipeline& P, int level) {
+int launch_gram_basis(const Pipeline& P, int level) {
   static unsigned long long done = 0;
   const int n = P.lvl_ptr[level + 1] - P.lvl_ptr[level];
-  if (n <= 0) return;
-  const int tc = tile_cols(P);
-  smem_limit(k_fgram, tiles_bytes(2, 32, 0), done);
-  k_fgram<<<blocks_for(n), 32 * kWarps, tiles_bytes(2, tc, 0), P.stream>>>(
-      P.M, P.items, P.lvl_list + P.lvl_ptr[level], n, P.u, tc, P.A, P.B, P.IB, P.err);
+  if (n <= 0) return 0;
+  const int nl = P.lvl_leaves[level];
+  const int32_t* list = P.lvl_list + P.lvl_ptr[level];
+  int launches = 0;
+  if (nl > 0) {
+    const int tc = tile_cols(P);
+    smem_limit(k_fgram, tiles_bytes(1, 32, 0), done);
+    k_fgram<<<blocks_for(nl), 32 * kWarps, tiles_bytes(1, tc, 0), P.stream>>>(P.M, P.items, list, nl, P.u, tc, P.A,
+                                                                            P.B, P.IB, P.err);
+    ++launches;
+  }
+  if (n > nl) {
+    k_fgram_inner<<<n - nl, 32 * kInnerWarps, 0, P.stream>>>(P.M, P.items, list + nl, n - nl, P.u, P.IB, P.err);
+    ++launches;
+  }
+  return launches;
 }
 
 void launch_gram_norms(const Pipeline& P) {
@@ -1417,11 +1667,20 @@ void launch_gram_weights(const Pipeline& P, int level) {
   const int n = P.lvl_ptr[level + 1] - P.lvl_ptr[level];
   if (n <= 0) return;
   const int tc = tile_cols(P);
+  const auto bytes = [](int warps, int c) { return (size_t)warps * 3 * (c + 1) * c * sizeof(double); };
+  if (n <= kWideMaxTasks) {
+    // few tasks: one block of kWideWarps warps per task, one set of tiles
+    static unsigned long long done_wide = 0;
+    smem_limit(k_fweights_wide, bytes(1, 32), done_wide);
+    k_fweights_wide<<<n, kWideThreads, bytes(1, tc), P.stream>>>(P.M, P.items, P.ents,
+                                                                 P.lvl_list + P.lvl_ptr[level], n, P.u, tc, P.BW,
+                                                                 P.IB);
+    return;
+  }
   // two warps per block, tiles of (tc + 1) x tc
   constexpr int warps = 2;
-  const auto bytes = [](int c) { return (size_t)warps * 3 * (c + 1) * c * sizeof(double); };
-  smem_limit(k_fweights, bytes(32), done);
-  k_fweights<<<(n + warps - 1) / warps, 32 * warps, bytes(tc), P.stream>>>(
+  smem_limit(k_fweights, bytes(warps, 32), done);
+  k_fweights<<<(n + warps - 1) / warps, 32 * warps, bytes(warps, tc), P.stream>>>(
       P.M, P.items, P.ents, P.lvl_list + P.lvl_ptr[level], n, P.u, tc, P.BW, P.IB);
 }
 
@@ -1449,8 +1708,8 @@ constexpr int kFbWarps = 2;
 template <int UMAX>
 void launch_fbasis_block_form(const Pipeline& P, int n, int tc) {
   static unsigned long long done = 0;
-  const size_t bytes = (size_t)kFbWarps * (3 * kLd * tc + 32) * sizeof(double);
-  smem_limit(k_fbasis<false, UMAX>, (size_t)kFbWarps * (3 * kLd * 32 + 32) * sizeof(double), done);
+  const size_t bytes = (size_t)kFbWarps * fbasis_doubles(tc) * sizeof(double);
+  smem_limit(k_fbasis<false, UMAX>, (size_t)kFbWarps * fbasis_doubles(32) * sizeof(double), done);
   k_fbasis<false, UMAX><<<(n + kFbWarps - 1) / kFbWarps, 32 * kFbWarps, bytes, P.stream>>>(P.M, P.items, n, P.u,
                                                                                           tc, P.A, P.B, P.IB, P.BW);
 }
@@ -1466,9 +1725,9 @@ void launch_gram_outputs(const Pipeline& P) {
     launch_fbasis_block_form<16>(P, n, tc);
   else
     launch_fbasis_block_form<32>(P, n, tc);
-  smem_limit(k_fbasis<true, 32>, tiles_bytes(3, 32, 32), done);
-  k_fbasis<true, 32><<<blocks_for(n), 32 * kWarps, tiles_bytes(3, tc, 32), P.stream>>>(P.M, P.items, n, P.u, tc,
-                                                                                      P.A, P.B, P.IB, P.BW);
+  smem_limit(k_fbasis<true, 32>, (size_t)kWarps * fbasis_doubles(32) * sizeof(double), done);
+  k_fbasis<true, 32><<<blocks_for(n), 32 * kWarps, (size_t)kWarps * fbasis_doubles(tc) * sizeof(double),
+                       P.stream>>>(P.M, P.items, n, P.u, tc, P.A, P.B, P.IB, P.BW);
 }
 
 }  // namespace h2

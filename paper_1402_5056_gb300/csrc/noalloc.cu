@@ -70,7 +70,8 @@ constexpr size_t kOffOrth = kOffFail + align256(4);                             
 constexpr size_t kOffTwo = kOffOrth + align256(2ull * kNaClusters * 4);
 constexpr size_t kOffLeft = kOffTwo + align256((size_t)kNaTasks * 4);
 constexpr size_t kOffNLeft = kOffLeft + align256((size_t)kNaTasks * 4);
-constexpr size_t kScratchBytes = kOffNLeft + align256(4);
+constexpr size_t kOffCopyFlag = kOffNLeft + align256(4);
+constexpr size_t kScratchBytes = kOffCopyFlag + align256((size_t)kNaTasks);
 // The Gram matrices V_t^* V_t of the unchanged bases (2 sides x 512 slots)
 // live in the coupling-output region: they are dead before the
 // reprojection writes its results there.
@@ -91,6 +92,7 @@ struct HostPlan {
   NormTask norms[kNaNorms];
   int32_t lvl_list[kNaItems];
   int32_t lvl_ptr[kNaLevels + 1];
+  int32_t lvl_leaves[kNaLevels];
   int32_t lvl_rows[kNaLevels];
   int32_t cl_list[2 * kNaClusters];
   int32_t cl_ptr[kNaLevels + 1];
@@ -99,6 +101,7 @@ struct HostPlan {
   int32_t sub[2][kNaClusters];
   int32_t nsub[2];
   int32_t rank[kNaItems];
+  int8_t copy[kNaTasks];
   int32_t two[kNaTasks];
   int n_two;
   CopyDesc copies[2 * kNaItems + kNaTasks];
@@ -251,14 +254,21 @@ h2_status plan_single(const h2_matrix* Z, int32_t b0, int u, int64_t lda, int64_
   }
   for (int l = 0; l < L; ++l) P.lvl_ptr[l + 1] += P.lvl_ptr[l];
   int fill[kNaLevels];
-  for (int l = 0; l < L; ++l) fill[l] = P.lvl_ptr[l];
-  for (int i = 0; i < P.n_items; ++i) {
-    const Item& it = P.items[i];
-    const int lev = tree(Z, it.side).level[it.cluster];
-    P.lvl_list[fill[lev]++] = i;
-    const int rows = (it.flags & kItemLeaf) ? it.size : P.items[it.son0].k + P.items[it.son1].k + 2 * u;
-    P.lvl_rows[lev] = std::max(P.lvl_rows[lev], rows);
+  for (int l = 0; l < L; ++l) {
+    fill[l] = P.lvl_ptr[l];
+    P.lvl_leaves[l] = 0;
   }
+  for (int pass = 0; pass < 2; ++pass)   // leaves first within a level
+    for (int i = 0; i < P.n_items; ++i) {
+      const Item& it = P.items[i];
+      const bool leaf = it.flags & kItemLeaf;
+      if (leaf != (pass == 0)) continue;
+      const int lev = tree(Z, it.side).level[it.cluster];
+      P.lvl_list[fill[lev]++] = i;
+      if (leaf) ++P.lvl_leaves[lev];
+      const int rows = leaf ? it.size : P.items[it.son0].k + P.items[it.son1].k + 2 * u;
+      P.lvl_rows[lev] = std::max(P.lvl_rows[lev], rows);
+    }
   for (int l = 0; l < L; ++l)
     if (P.lvl_rows[l] > 64) return fail(H2_EINVAL, "leaf clusters above 64 indices are not supported");
   // all clusters of both sides by level, for the weights of the unchanged matrix
@@ -313,6 +323,7 @@ h2_status run(h2_ctx* ctx, h2_matrix* Z, int32_t b0, int u, const double* A, int
   IB.own = reinterpret_cast<int32_t*>(base + kOffOwn);
   IB.norms = reinterpret_cast<double*>(base + kOffNorm);
   IB.S_out = reinterpret_cast<double*>(base + kOffS);
+  IB.copy = reinterpret_cast<int8_t*>(base + kOffCopyFlag);
   IB.jac = reinterpret_cast<unsigned long long*>(base + kOffJac);
   // the certified path's Gram matrices are dead before the exact path
   // writes its R-factors and weights into the same tiles
@@ -362,6 +373,7 @@ h2_status run(h2_ctx* ctx, h2_matrix* Z, int32_t b0, int u, const double* A, int
   pp.norms = d_nt;
   pp.lvl_list = d_lvl;
   pp.lvl_ptr = P.lvl_ptr;
+  pp.lvl_leaves = P.lvl_leaves;
   pp.lvl_rows = P.lvl_rows;
   pp.cl_list = d_cl;
   pp.cl_ptr = P.cl_ptr;
@@ -395,6 +407,7 @@ h2_status run(h2_ctx* ctx, h2_matrix* Z, int32_t b0, int u, const double* A, int
   NA_CUDA(cudaGetLastError());
   // commit (Section 5): new bases, transfers, couplings, nearfield inside b0
   NA_CUDA(cudaMemcpyAsync(P.rank, IB.rank, P.n_items * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  if (P.n_tasks) NA_CUDA(cudaMemcpyAsync(P.copy, IB.copy, P.n_tasks * sizeof(int8_t), cudaMemcpyDeviceToHost, s));
   NA_CUDA(cudaStreamSynchronize(s));
   int err = 0;
   NA_CUDA(cudaMemcpy(&err, ctx->d_error, sizeof(int), cudaMemcpyDeviceToHost));
@@ -422,8 +435,17 @@ h2_status run(h2_ctx* ctx, h2_matrix* Z, int32_t b0, int u, const double* A, int
     const Task& tk = P.tasks[t];
     const int rt = tk.it >= 0 ? P.rank[tk.it] : tk.kt;
     const int rs = tk.is >= 0 ? P.rank[tk.is] : tk.ls;
-    if (rt > 0 && rs > 0)
-      P.copies[nc++] = CopyDesc{IB.S_out + (size_t)t * kSlot, Z->d_S + (size_t)tk.slot * kcap * kcap, rt, rs, 32, kcap};
+    if (rt <= 0 || rs <= 0) continue;
+    double* d = Z->d_S + (size_t)tk.slot * kcap * kcap;
+    if (P.copy[t]) {
+      // [S_b; 0] or [S_b, 0] in place: only the zero rows or columns
+      if (tk.it >= 0)
+        P.copies[nc++] = CopyDesc{nullptr, d + tk.kt, rt - tk.kt, rs, 0, kcap};
+      else
+        P.copies[nc++] = CopyDesc{nullptr, d + (size_t)tk.ls * kcap, rt, rs - tk.ls, 0, kcap};
+      continue;
+    }
+    P.copies[nc++] = CopyDesc{IB.S_out + (size_t)t * kSlot, d, rt, rs, 32, kcap};
   }
   const BlockTree& bt = Z->blocks;
   int nn = 0, top = 0;

@@ -1209,7 +1209,7 @@ __device__ __forceinline__ void reproject_task(const MatView& M, const Item* __r
 }
 
 // The two-sided tasks (list from the host) and the one-sided tasks that
-// k_recopy did not copy (list built on the device), with persistent warps:
+// k_onesided did not flag as copies (list built on the device), with persistent warps:
 // warp g takes entries g, g + G, ... (G warps in the grid).
 __global__ void k_reproject(MatView M, const Item* __restrict__ items, const Task* __restrict__ tasks,
                             const int32_t* __restrict__ two, int n_two, const int32_t* __restrict__ left,
@@ -1228,52 +1228,37 @@ __global__ void k_reproject(MatView M, const Item* __restrict__ items, const Tas
 }
 
 // The one-sided reprojections of certified updates with an orthonormal basis
-// are copies: R_t [S_b; 0] = [S_b; 0] and [S_b, 0] R_s^* = [S_b, 0], since
-// R_t = [[I, C_t], [0, L_S^*]].  One warp per block, all loads of the block
-// issued before its stores; no shared memory, so that many warps keep loads
-// in flight.
-constexpr int kCopyWarps = 8;
-
-__global__ void k_recopy(MatView M, const Item* __restrict__ items, const Task* __restrict__ tasks, int n, int u,
-                         BaseWeights BW, ItemBuffers IB, int32_t* __restrict__ left, int32_t* __restrict__ n_left) {
-  const int lane = threadIdx.x & 31;
-  const int G = gridDim.x * (blockDim.x >> 5);
-  const int kcap = M.kcap;
-  for (int idx = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); idx < n; idx += G) {
-    const Task tk = tasks[idx];
-    if (tk.it >= 0 && tk.is >= 0) continue;
+// keep the coupling: R_t [S_b; 0] = [S_b; 0] and [S_b, 0] R_s^* = [S_b, 0],
+// since R_t = [[I, C_t], [0, L_S^*]].  Such a task is flagged (IB.copy) and
+// its coupling stays where it is (the packing of the result and the commit
+// read it from the unchanged matrix); the other one-sided tasks go to a
+// device list for k_reproject.  One thread per task.
+__global__ void k_onesided(const Item* __restrict__ items, const Task* __restrict__ tasks, int n, BaseWeights BW,
+                           ItemBuffers IB, int32_t* __restrict__ left, int32_t* __restrict__ n_left) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  const Task tk = tasks[idx];
+  int8_t copy = 0;
+  if (tk.it < 0 || tk.is < 0) {
     const int side = tk.it >= 0 ? 0 : 1;
     const Item it = items[side == 0 ? tk.it : tk.is];
-    if (IB.fail[it.update] || !pick(BW.orth, side)[it.cluster]) {
-      if (lane == 0) left[atomicAdd(n_left, 1)] = idx;   // k_reproject computes it
-      continue;
-    }
-    const double* S = M.S + (size_t)tk.slot * kcap * kcap;
-    double* out = IB.S_out + (size_t)idx * kSlot;
-    // lane = row; [S_b; 0] (rows kt + u) or [S_b, 0] (columns ls + u)
-    const int rows = side == 0 ? tk.kt + u : tk.kt;
-    const int cols = side == 0 ? tk.ls : tk.ls + u;
-    const bool in_s = lane < tk.kt;
-    for (int c0 = 0; c0 < cols; c0 += 8) {
-      double v[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) v[j] = (in_s && c0 + j < tk.ls) ? S[lane + (size_t)(c0 + j) * kcap] : 0.0;
-      if (lane < rows)
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-          if (c0 + j < cols) out[lane + (c0 + j) * 32] = v[j];
-    }
+    if (IB.fail[it.update] || !pick(BW.orth, side)[it.cluster])
+      left[atomicAdd(n_left, 1)] = idx;   // k_reproject computes it
+    else
+      copy = 1;
   }
+  IB.copy[idx] = copy;
 }
 
-// Batched copies of column-major matrices (commit of one update).
+// Batched copies of column-major matrices (commit of one update); a
+// descriptor without source writes zeros.
 __global__ void k_copy(const CopyDesc* __restrict__ d, int n) {
   const int idx = blockIdx.x;
   if (idx >= n) return;
   const CopyDesc c = d[idx];
   for (int e = threadIdx.x; e < c.rows * c.cols; e += blockDim.x) {
     const int i = e % c.rows, j = e / c.rows;
-    c.dst[i + (size_t)j * c.ldd] = c.src[i + (size_t)j * c.lds];
+    c.dst[i + (size_t)j * c.ldd] = c.src ? c.src[i + (size_t)j * c.lds] : 0.0;
   }
 }
 
@@ -1408,8 +1393,7 @@ void run_pipeline(const Pipeline& P) {
     start(H2_PHASE_RFACTOR, st);
     for (int l = L - 1; l >= 0; --l)
       if (P.lvl_ptr[l + 1] > P.lvl_ptr[l]) {
-        launch_gram_basis(P, l);
-        ++pl[H2_PHASE_RFACTOR];
+        pl[H2_PHASE_RFACTOR] += launch_gram_basis(P, l);
       }
     stop(H2_PHASE_RFACTOR, st);
     // the norms need the orthonormality flags only; the weights need all
@@ -1501,10 +1485,8 @@ void run_pipeline(const Pipeline& P) {
                                    kWarps * 3 * kRpLd * 32 * (int)sizeof(double)));
       if (dev < 64) attr |= 1ull << dev;
     }
-    // copies first (they also list the one-sided tasks that need products)
-    const int nb = (P.n_tasks + kCopyWarps - 1) / kCopyWarps;
-    k_recopy<<<persistent_blocks(k_recopy, 32 * kCopyWarps, 0, nb), 32 * kCopyWarps, 0, st>>>(
-        P.M, P.items, P.tasks, P.n_tasks, P.u, P.BW, P.IB, P.left, P.n_left);
+    // flag the copies, list the one-sided tasks that need products
+    k_onesided<<<(P.n_tasks + 255) / 256, 256, 0, st>>>(P.items, P.tasks, P.n_tasks, P.BW, P.IB, P.left, P.n_left);
     const size_t rp_smem = (size_t)kWarps * 3 * kRpLd * tc * sizeof(double);
     k_reproject<<<persistent_blocks(k_reproject, 32 * kWarps, rp_smem, blocks_for(P.n_tasks)), 32 * kWarps, rp_smem,
                   st>>>(P.M, P.items, P.tasks, P.two, P.n_two, P.left, P.n_left, P.u, tc, P.BW, P.IB);

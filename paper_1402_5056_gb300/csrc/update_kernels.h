@@ -44,6 +44,7 @@ struct Pipeline {
   const int32_t* lvl_list;      // items sorted by level
   const int32_t* lvl_ptr;       // host, levels + 1 entries
   const int32_t* lvl_rows;      // host, per level: bound on the truncation rows
+  const int32_t* lvl_leaves;    // host, per level: number of leaves (they come first in lvl_list)
   const int32_t* cl_list;       // all clusters of both sides sorted by level (side << 30 | id)
   const int32_t* cl_ptr;        // host, levels + 1 entries
   int levels;
@@ -101,7 +102,7 @@ void launch_gram_orth(const Pipeline& P, cudaStream_t st);                // ort
 void launch_gram_vbasis_level(const Pipeline& P, int level, cudaStream_t st);  // V_t^* V_t, one level
 void launch_gram_base(const Pipeline& P, cudaStream_t st);               // Wo, all clusters
 void launch_gram_base_level(const Pipeline& P, int level, cudaStream_t st);  // W0, one level
-void launch_gram_basis(const Pipeline& P, int level);                    // G_t, one level
+int launch_gram_basis(const Pipeline& P, int level);                     // G_t, one level (returns launches)
 void launch_gram_norms(const Pipeline& P);                               // ||Z~|_b||_F inside
 void launch_gram_weights(const Pipeline& P, int level);                  // W_t, one level
 void launch_gram_certify(const Pipeline& P);                             // certificate, R_t

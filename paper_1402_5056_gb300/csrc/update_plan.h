@@ -106,6 +106,8 @@ struct ItemBuffers {
   double* Wg;
   int32_t* fail;       // per update: 1 if the exact path computes it
   double* S_out;       // per Task, 32 x 32 slots
+  int8_t* copy;        // per Task: 1 when the new coupling is the old one padded with zeros
+                       // ([S_b; 0] or [S_b, 0]); S_out is not written then
   unsigned long long* jac;   // per item: Jacobi pairs checked, rotations applied, 1 if the
                              // full-rank certificate held (no Jacobi), reserved (4 counters)
 };
