@@ -246,11 +246,12 @@ __device__ __forceinline__ void load_block_rows(double* X, const double* S, int 
 
 // acc (lower triangle of the k x k block in the per-lane layout) += w X^* X
 // for the l x k tile X.
-__device__ __forceinline__ void acc_gram(double (&acc)[kNS], const double* X, int l, int k, double w, int lane,
+template <int NS>
+__device__ __forceinline__ void acc_gram(double (&acc)[NS], const double* X, int l, int k, double w, int lane,
                                          int ld = kLd) {
   const int nt = tri(k);
 #pragma unroll
-  for (int s = 0; s < kNS; ++s) {
+  for (int s = 0; s < NS; ++s) {
     if (32 * s >= nt) break;
     const int e = lane + 32 * s;
     if (e < nt) {
@@ -274,10 +275,11 @@ __device__ __forceinline__ double sum_squares(const double* X, int l, int k, int
 
 // Store the lower-triangle accumulator as a full symmetric n x n matrix
 // (global slot, ld 32).
-__device__ __forceinline__ void store_sym(double* G, const double (&acc)[kNS], int n, int lane) {
+template <int NS>
+__device__ __forceinline__ void store_sym(double* G, const double (&acc)[NS], int n, int lane) {
   const int nt = tri(n);
 #pragma unroll
-  for (int s = 0; s < kNS; ++s) {
+  for (int s = 0; s < NS; ++s) {
     if (32 * s >= nt) break;
     const int e = lane + 32 * s;
     if (e < nt) {
@@ -495,6 +497,7 @@ __global__ void k_vgram(MatView M, const int32_t* __restrict__ list, int n, Base
 // Wo_c = sum over b in row(c) of omega_b^2 S_b S_b^* (column side S_b^* S_b),
 // omega_b = sqrt(#T_c) / ||S_b||_F, for every cluster of both sides; the
 // Gram of the stack whose R-factor the exact path folds.
+template <int NS>
 __global__ void k_bgram(MatView M, const int32_t* __restrict__ list, int n, BlockLists BL, BaseWeights BW,
                         int* err) {
   extern __shared__ double smem[];
@@ -515,9 +518,9 @@ __global__ void k_bgram(MatView M, const int32_t* __restrict__ list, int n, Bloc
   const int32_t* orank = pick(M.rank, 1 - side);
   const int32_t* other = pick(BL.other, side);
   const int32_t* adm = pick(BL.adm, side);
-  double acc[kNS];
+  double acc[NS];
 #pragma unroll
-  for (int s = 0; s < kNS; ++s) acc[s] = 0.0;
+  for (int s = 0; s < NS; ++s) acc[s] = 0.0;
   for (int e = pick(BL.ptr, side)[c]; e < pick(BL.ptr, side)[c + 1]; ++e) {
     const int slot = adm[e];
     const int l = orank[other[slot]];
@@ -589,6 +592,7 @@ __global__ void k_bgram_down(MatView M, const int32_t* __restrict__ list, int n,
 // kInnerWarps warps per cluster: the upper levels have few clusters).
 // Entry e of the per-lane list is C_t[e % k][e / k] for e < k u, then the
 // lower triangle of N_t.  The V_t^* V_t block of G_t comes from k_vgram.
+template <int NS>
 __global__ void k_fgram(MatView M, const Item* __restrict__ items, const int32_t* __restrict__ list, int n, int u,
                         int tc, const double* __restrict__ A, const double* __restrict__ B, ItemBuffers IB,
                         int* err) {
@@ -609,9 +613,9 @@ __global__ void k_fgram(MatView M, const Item* __restrict__ items, const int32_t
   }
   const int ncu = k * u;
   const int nt = ncu + tri(u);
-  double acc[kNS];
+  double acc[NS];
 #pragma unroll
-  for (int s = 0; s < kNS; ++s) acc[s] = 0.0;
+  for (int s = 0; s < NS; ++s) acc[s] = 0.0;
   {
     const double* V = pick(M.leaf, side) + pick(M.leaf_off, side)[it.cluster];
     const double* F = (side == 0 ? A : B) + it.foff;
@@ -622,7 +626,7 @@ __global__ void k_fgram(MatView M, const Item* __restrict__ items, const int32_t
       load_tile(T0 + k * kLd, kLd, F + it.rowoff + r0, it.ld, ch, u, lane);
       __syncwarp();
 #pragma unroll
-      for (int s = 0; s < kNS; ++s) {
+      for (int s = 0; s < NS; ++s) {
         if (32 * s >= nt) break;
         const int e = lane + 32 * s;
         if (e < nt) {
@@ -645,7 +649,7 @@ __global__ void k_fgram(MatView M, const Item* __restrict__ items, const int32_t
   }
   double* G = IB.Gv + (size_t)id * kSlot;
 #pragma unroll
-  for (int s = 0; s < kNS; ++s) {
+  for (int s = 0; s < NS; ++s) {
     if (32 * s >= nt) break;
     const int e = lane + 32 * s;
     if (e < nt) {
@@ -802,6 +806,7 @@ __global__ void k_fnorms(MatView M, const Item* __restrict__ items, const NormTa
 // part E~_t W_{t+} E~_t^* (subtree root: E_t W0_{t+} E_t^* of the unchanged
 // matrix).
 // One warp: cluster task id with its three tiles (leading dimension ld).
+template <int NS>
 __device__ __forceinline__ void fweights_warp(const MatView& M, const Item* __restrict__ items,
                                               const Entry* __restrict__ ents, int id, int u, int ld,
                                               const BaseWeights& BW, const ItemBuffers& IB, double* T0, double* T1,
@@ -817,13 +822,13 @@ __device__ __forceinline__ void fweights_warp(const MatView& M, const Item* __re
   const int32_t* orank = pick(M.rank, 1 - side);
   const double* Sbase = M.S;
   const bool orth = pick(BW.orth, side)[it.cluster] != 0;
-  double acc[kNS];
+  double acc[NS];
 #pragma unroll
-  for (int s = 0; s < kNS; ++s) acc[s] = 0.0;
+  for (int s = 0; s < NS; ++s) acc[s] = 0.0;
   if (orth) {
     const double* Wo = pick(BW.Wo, side) + (size_t)it.cluster * kSlot;
 #pragma unroll
-    for (int s = 0; s < kNS; ++s) {
+    for (int s = 0; s < NS; ++s) {
       const int e = lane + 32 * s;
       if (e < ntk) {
         int i, j;
@@ -879,7 +884,7 @@ __device__ __forceinline__ void fweights_warp(const MatView& M, const Item* __re
         __syncwarp();
         acc_gram(acc, T0, l, k, w2 - w02, lane, ld);
 #pragma unroll
-        for (int s = 0; s < kNS; ++s) {
+        for (int s = 0; s < NS; ++s) {
           if (32 * s >= nt) break;
           const int e2 = lane + 32 * s;
           if (e2 >= ntk && e2 < nt) {
@@ -915,7 +920,7 @@ __device__ __forceinline__ void fweights_warp(const MatView& M, const Item* __re
       }
       __syncwarp();
 #pragma unroll
-      for (int s = 0; s < kNS; ++s) {
+      for (int s = 0; s < NS; ++s) {
         if (32 * s >= nt) break;
         const int e2 = lane + 32 * s;
         if (e2 < nt) {
@@ -951,7 +956,7 @@ __device__ __forceinline__ void fweights_warp(const MatView& M, const Item* __re
       }
       __syncwarp();
 #pragma unroll
-      for (int s = 0; s < kNS; ++s) {
+      for (int s = 0; s < NS; ++s) {
         if (32 * s >= ntk) break;
         const int e2 = lane + 32 * s;
         if (e2 < ntk) {
@@ -982,7 +987,7 @@ __device__ __forceinline__ void fweights_warp(const MatView& M, const Item* __re
     // times E^* (the first tri(k) entries); (i >= k, j < k) rows kf + i - k
     // of W_p times E^*; (i, j >= k) W22
 #pragma unroll
-    for (int s = 0; s < kNS; ++s) {
+    for (int s = 0; s < NS; ++s) {
       if (32 * s >= ntk) break;
       const int e2 = lane + 32 * s;
       if (e2 < ntk) {
@@ -994,7 +999,7 @@ __device__ __forceinline__ void fweights_warp(const MatView& M, const Item* __re
       }
     }
 #pragma unroll
-    for (int s = 0; s < kNS; ++s) {
+    for (int s = 0; s < NS; ++s) {
       if (32 * s >= nt) break;
       const int e2 = lane + 32 * s;
       if (e2 >= ntk && e2 < nt) {
@@ -1013,6 +1018,7 @@ __device__ __forceinline__ void fweights_warp(const MatView& M, const Item* __re
   store_sym(IB.Wg + (size_t)id * kSlot, acc, K, lane);
 }
 
+template <int NS>
 __global__ void k_fweights(MatView M, const Item* __restrict__ items, const Entry* __restrict__ ents,
                            const int32_t* __restrict__ list, int n, int u, int tc, BaseWeights BW, ItemBuffers IB) {
   extern __shared__ double smem[];
@@ -1023,7 +1029,7 @@ __global__ void k_fweights(MatView M, const Item* __restrict__ items, const Entr
   // every tile holds at most max(K, kcap) = tc rows: leading dimension tc + 1
   const int ld = tc + 1;
   double* T0 = smem + (size_t)w * 3 * ld * tc;
-  fweights_warp(M, items, ents, list[idx], u, ld, BW, IB, T0, T0 + ld * tc, T0 + 2 * ld * tc, lane);
+  fweights_warp<NS>(M, items, ents, list[idx], u, ld, BW, IB, T0, T0 + ld * tc, T0 + 2 * ld * tc, lane);
 }
 
 // The same with one block of kWideWarps warps per cluster task, for the
@@ -1053,7 +1059,7 @@ __global__ void k_fweights_wide(MatView M, const Item* __restrict__ items, const
   const Item it = items[id];
   const int side = it.side;
   if (!pick(BW.orth, side)[it.cluster]) {
-    if (w == 0) fweights_warp(M, items, ents, id, u, ld, BW, IB, T0, T1, T2, lane);
+    if (w == 0) fweights_warp<kNS>(M, items, ents, id, u, ld, BW, IB, T0, T1, T2, lane);
     return;
   }
   const int k = it.k;
@@ -1575,6 +1581,13 @@ __global__ void k_fbasis(MatView M, const Item* __restrict__ items, int n, int u
 
 constexpr int kWarps = 4;
 
+// Per-lane accumulator slots for `entries` lower-triangle entries: 5, 10 or
+// kNS (the fewer, the fewer registers a lane holds).
+int slots_for(int entries) {
+  const int need = (entries + 31) / 32;
+  return need <= 5 ? 5 : need <= 10 ? 10 : kNS;
+}
+
 // Shared doubles of one k_fbasis warp (tiles of tc columns).
 constexpr int fbasis_doubles(int tc) { return 2 * (tc + 1) * tc + kLd * tc + 32; }
 
@@ -1622,8 +1635,17 @@ void launch_gram_base(const Pipeline& P, cudaStream_t st) {
   static unsigned long long done = 0;
   const int n = P.cl_ptr[P.levels];
   if (n <= 0) return;
-  smem_limit(k_bgram, tiles_bytes(1, 32, 0), done);
-  k_bgram<<<blocks_for(n), 32 * kWarps, tiles_bytes(1, P.M.kcap, 0), st>>>(P.M, P.cl_list, n, P.BL, P.BW, P.err);
+  const auto go = [&](auto kern) {
+    smem_limit(kern, tiles_bytes(1, 32, 0), done);
+    kern<<<blocks_for(n), 32 * kWarps, tiles_bytes(1, P.M.kcap, 0), st>>>(P.M, P.cl_list, n, P.BL, P.BW, P.err);
+  };
+  const int ns = slots_for(P.M.kcap * (P.M.kcap + 1) / 2);
+  if (ns == 5)
+    go(k_bgram<5>);
+  else if (ns == 10)
+    go(k_bgram<10>);
+  else
+    go(k_bgram<kNS>);
 }
 
 void launch_gram_base_level(const Pipeline& P, int level, cudaStream_t st) {
@@ -1641,9 +1663,19 @@ int launch_gram_basis(const Pipeline& P, int level) {
   int launches = 0;
   if (nl > 0) {
     const int tc = tile_cols(P);
-    smem_limit(k_fgram, tiles_bytes(1, 32, 0), done);
-    k_fgram<<<blocks_for(nl), 32 * kWarps, tiles_bytes(1, tc, 0), P.stream>>>(P.M, P.items, list, nl, P.u, tc, P.A,
+    const auto go = [&](auto kern) {
+      smem_limit(kern, tiles_bytes(1, 32, 0), done);
+      kern<<<blocks_for(nl), 32 * kWarps, tiles_bytes(1, tc, 0), P.stream>>>(P.M, P.items, list, nl, P.u, tc, P.A,
                                                                             P.B, P.IB, P.err);
+    };
+    const int kk = P.M.kcap;
+    const int ns = slots_for(kk * P.u + P.u * (P.u + 1) / 2);
+    if (ns == 5)
+      go(k_fgram<5>);
+    else if (ns == 10)
+      go(k_fgram<10>);
+    else
+      go(k_fgram<kNS>);
     ++launches;
   }
   if (n > nl) {
@@ -1679,9 +1711,15 @@ void launch_gram_weights(const Pipeline& P, int level) {
   }
   // two warps per block, tiles of (tc + 1) x tc
   constexpr int warps = 2;
-  smem_limit(k_fweights, bytes(warps, 32), done);
-  k_fweights<<<(n + warps - 1) / warps, 32 * warps, bytes(warps, tc), P.stream>>>(
-      P.M, P.items, P.ents, P.lvl_list + P.lvl_ptr[level], n, P.u, tc, P.BW, P.IB);
+  const auto go = [&](auto kern) {
+    smem_limit(kern, bytes(warps, 32), done);
+    kern<<<(n + warps - 1) / warps, 32 * warps, bytes(warps, tc), P.stream>>>(
+        P.M, P.items, P.ents, P.lvl_list + P.lvl_ptr[level], n, P.u, tc, P.BW, P.IB);
+  };
+  if (slots_for(P.kl * (P.kl + 1) / 2) <= 10)
+    go(k_fweights<10>);
+  else
+    go(k_fweights<kNS>);
 }
 
 void launch_gram_certify(const Pipeline& P) {
