@@ -32,16 +32,18 @@ if ROOT not in sys.path:
 import synth  # noqa: E402
 
 # kernels behind each phase of h2_batch_phase_stats
-PHASE_KERNELS = {"base_weights": "k_orth_local+k_vgram+k_bgram+k_bgram_down", "rfactor": "k_fgram",
-                 "norms": "k_fnorms", "weights": "k_fweights", "truncate": "k_certify", "bases": "k_fbasis",
-                 "reproject": "k_recopy+k_reproject", "exact": "exact path (k_blockweights..k_truncate)"}
+PHASE_KERNELS = {"base_weights": "k_orth_local+k_vgram+k_bgram+k_bgram_down", "rfactor": "k_fgram+k_fgram_inner",
+                 "norms": "k_fnorms", "weights": "k_fweights+k_fweights_wide", "truncate": "k_certify",
+                 "bases": "k_fbasis", "reproject": "k_onesided+k_reproject",
+                 "exact": "exact path (k_blockweights..k_truncate)"}
 
-# DRAM bytes (read + write) per cluster task of the kernels on the critical
-# path, from one ncu capture of each on the 1024-update batch of the same
-# matrix (dram__bytes_read.sum + dram__bytes_write.sum of the launch divided
-# by its cluster tasks); the roofline's `traffic` scales them to one launch
-# of the benchmark batch.  Valid for the kernel versions of this commit.
-TRAFFIC_BYTES_PER_TASK = {"k_certify": 11019, "k_fbasis": 15607, "k_fgram": 4082}
+# DRAM bytes (read + write) per cluster task of a phase's kernels, from ncu
+# captures on the 1024-update batch of the same matrix (13,220 cluster
+# tasks): dram__bytes_read.sum + dram__bytes_write.sum summed over the
+# phase's launches of one execution, divided by its cluster tasks; the
+# roofline's `traffic` scales them to one launch of the benchmark batch.
+# Valid for the kernel versions of this commit.
+TRAFFIC_BYTES_PER_TASK = {"k_fweights+k_fweights_wide": 5787, "k_certify": 10972, "k_fbasis": 15560}
 
 METRIC = "H²-LR setup s & low-rank updates/s, mixed vs FP64 GPU at equal ε; % roofline"
 UNIT = "updates/s"
