@@ -804,10 +804,15 @@ __global__ void k_fnorms(MatView M, const Item* __restrict__ items, const NormTa
 // on the row side, diag(S_b^*, I_u) on the column side), plus the father's
 // part E~_t W_{t+} E~_t^* (subtree root: E_t W0_{t+} E_t^* of the unchanged
 // matrix).
-// One warp: cluster task id with its three tiles (leading dimension ld).
+// Shared doubles of the three k_fweights tiles of one warp.
+__host__ __device__ constexpr int fweights_doubles(int tc, int kcap) { return (kcap + 1) * kcap + 2 * (tc + 1) * tc; }
+
+// One warp: cluster task id with its three tiles: T0 (blocks of couplings
+// and E_t, at most kcap x kcap, leading dimension ld0) and T1, T2 (leading
+// dimension ld).
 template <int NS>
 __device__ __forceinline__ void fweights_warp(const MatView& M, const Item* __restrict__ items,
-                                              const Entry* __restrict__ ents, int id, int u, int ld,
+                                              const Entry* __restrict__ ents, int id, int u, int ld, int ld0,
                                               const BaseWeights& BW, const ItemBuffers& IB, double* T0, double* T1,
                                               double* T2, int lane) {
   const Item it = items[id];
@@ -839,19 +844,19 @@ __device__ __forceinline__ void fweights_warp(const MatView& M, const Item* __re
     load_tile(T1, ld, pick(BW.Vg, side) + (size_t)it.cluster * kSlot, 32, k, k, lane);
     for_entries(ents, it.ent_begin, it.ent_end, false, lane, [&](const Entry& en) {
       const int l = orank[en.other_cluster];
-      load_block_rows(T0, Sbase + (size_t)en.slot * kcap * kcap, kcap, side, l, k, lane, ld);
+      load_block_rows(T0, Sbase + (size_t)en.slot * kcap * kcap, kcap, side, l, k, lane, ld0);
       __syncwarp();
       // ||R_kk S_b||_F^2 = sum over rows x of X of x G_kk x^*
       double part = 0.0;
       for (int e2 = lane; e2 < l * k; e2 += 32) {
         const int r = e2 % l, q = e2 / l;
         double y = 0.0;
-        for (int p = 0; p < k; ++p) y = fma(T0[r + p * ld], T1[p + q * ld], y);
-        part = fma(y, T0[r + q * ld], part);
+        for (int p = 0; p < k; ++p) y = fma(T0[r + p * ld0], T1[p + q * ld], y);
+        part = fma(y, T0[r + q * ld0], part);
       }
       const double nrm2 = warp_sum(part);
       const double w2 = nrm2 > 1e-300 ? st * recip(nrm2) : 0.0;
-      acc_gram(acc, T0, l, k, w2, lane, ld);
+      acc_gram(acc, T0, l, k, w2, lane, ld0);
       __syncwarp();
     });
   }
@@ -871,17 +876,17 @@ __device__ __forceinline__ void fweights_warp(const MatView& M, const Item* __re
       const double nrm = IB.norms[en.norm];
       const double w2 = nrm > 1e-150 ? st * recip(nrm * nrm) : 0.0;
       const double* Go = IB.Gv + (size_t)en.other * kSlot;
-      load_block_rows(T0, Sbase + (size_t)en.slot * kcap * kcap, kcap, side, l, k, lane, ld);
+      load_block_rows(T0, Sbase + (size_t)en.slot * kcap * kcap, kcap, side, l, k, lane, ld0);
       __syncwarp();
       double w02 = 0.0;
       if (orth) {
-        const double nrm2 = sum_squares(T0, l, k, lane, ld);
+        const double nrm2 = sum_squares(T0, l, k, lane, ld0);
         w02 = nrm2 > 1e-300 ? st * recip(nrm2) : 0.0;
       }
       if (orth_o[ot.cluster]) {
         load_tile(T1, ld, Go + l * 32, 32, l, u, lane);   // C_o (l x u)
         __syncwarp();
-        acc_gram(acc, T0, l, k, w2 - w02, lane, ld);
+        acc_gram(acc, T0, l, k, w2 - w02, lane, ld0);
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
           if (32 * s >= nt) break;
@@ -892,7 +897,7 @@ __device__ __forceinline__ void fweights_warp(const MatView& M, const Item* __re
             double v;
             if (j < k) {
               v = 0.0;
-              for (int q = 0; q < l; ++q) v = fma(T1[q + (i - k) * ld], T0[q + j * ld], v);
+              for (int q = 0; q < l; ++q) v = fma(T1[q + (i - k) * ld], T0[q + j * ld0], v);
             } else {
               v = Go[(l + i - k) + (l + j - k) * 32];
             }
@@ -902,7 +907,7 @@ __device__ __forceinline__ void fweights_warp(const MatView& M, const Item* __re
         __syncwarp();
         return;
       }
-      if (orth) acc_gram(acc, T0, l, k, -w02, lane, ld);
+      if (orth) acc_gram(acc, T0, l, k, -w02, lane, ld0);
       load_gram(T1, ld, Go, Vgo + (size_t)ot.cluster * kSlot, false, l, Ko, lane);
       __syncwarp();
       // T2 = P G_o (K x Ko), S'[i][q] = X[q][i]
@@ -911,7 +916,7 @@ __device__ __forceinline__ void fweights_warp(const MatView& M, const Item* __re
         double v;
         if (i < k) {
           v = 0.0;
-          for (int q = 0; q < l; ++q) v = fma(T0[q + i * ld], T1[q + j * ld], v);
+          for (int q = 0; q < l; ++q) v = fma(T0[q + i * ld0], T1[q + j * ld], v);
         } else {
           v = T1[l + i - k + j * ld];
         }
@@ -928,7 +933,7 @@ __device__ __forceinline__ void fweights_warp(const MatView& M, const Item* __re
           double v;
           if (j < k) {
             v = 0.0;
-            for (int q = 0; q < l; ++q) v = fma(T2[i + q * ld], T0[q + j * ld], v);
+            for (int q = 0; q < l; ++q) v = fma(T2[i + q * ld], T0[q + j * ld0], v);
           } else {
             v = T2[i + (l + j - k) * ld];
           }
@@ -945,12 +950,12 @@ __device__ __forceinline__ void fweights_warp(const MatView& M, const Item* __re
       const int f = pick(M.father, side)[it.cluster];
       const int kf = it.kf;
       load_tile(T1, ld, pick(BW.W0, side) + (size_t)f * kSlot, 32, kf, kf, lane);
-      load_tile(T0, ld, E, kcap, k, kf, lane);
+      load_tile(T0, ld0, E, kcap, k, kf, lane);
       __syncwarp();
       for (int e2 = lane; e2 < k * kf; e2 += 32) {
         const int i = e2 % k, j = e2 / k;
         double v = 0.0;
-        for (int q = 0; q < kf; ++q) v = fma(T0[i + q * ld], T1[q + j * ld], v);
+        for (int q = 0; q < kf; ++q) v = fma(T0[i + q * ld0], T1[q + j * ld], v);
         T2[i + j * ld] = v;
       }
       __syncwarp();
@@ -962,7 +967,7 @@ __device__ __forceinline__ void fweights_warp(const MatView& M, const Item* __re
           int i, j;
           tri_index(e2, i, j);
           double v = acc[s];
-          for (int q = 0; q < kf; ++q) v = fma(T2[i + q * ld], T0[j + q * ld], v);
+          for (int q = 0; q < kf; ++q) v = fma(T2[i + q * ld], T0[j + q * ld0], v);
           acc[s] = v;
         }
       }
@@ -971,13 +976,13 @@ __device__ __forceinline__ void fweights_warp(const MatView& M, const Item* __re
     const int kf = items[it.parent].k;
     const int Kf = kf + u;
     load_tile(T1, ld, IB.Wg + (size_t)it.parent * kSlot, 32, Kf, Kf, lane);
-    load_tile(T0, ld, E, kcap, k, kf, lane);
+    load_tile(T0, ld0, E, kcap, k, kf, lane);
     __syncwarp();
     // T2 = E W11 (k x kf); rows k.. of E~_t W_p are rows kf.. of W_p
     for (int e2 = lane; e2 < k * kf; e2 += 32) {
       const int i = e2 % k, j = e2 / k;
       double v = 0.0;
-      for (int q = 0; q < kf; ++q) v = fma(T0[i + q * ld], T1[q + j * ld], v);
+      for (int q = 0; q < kf; ++q) v = fma(T0[i + q * ld0], T1[q + j * ld], v);
       T2[i + j * ld] = v;
     }
     __syncwarp();
@@ -993,7 +998,7 @@ __device__ __forceinline__ void fweights_warp(const MatView& M, const Item* __re
         int i, j;
         tri_index(e2, i, j);
         double v = acc[s];
-        for (int q = 0; q < kf; ++q) v = fma(T2[i + q * ld], T0[j + q * ld], v);
+        for (int q = 0; q < kf; ++q) v = fma(T2[i + q * ld], T0[j + q * ld0], v);
         acc[s] = v;
       }
     }
@@ -1006,7 +1011,7 @@ __device__ __forceinline__ void fweights_warp(const MatView& M, const Item* __re
         tri_index(e2, i, j);
         double v = acc[s];
         if (j < k) {
-          for (int q = 0; q < kf; ++q) v = fma(T1[(kf + i - k) + q * ld], T0[j + q * ld], v);
+          for (int q = 0; q < kf; ++q) v = fma(T1[(kf + i - k) + q * ld], T0[j + q * ld0], v);
         } else {
           v += T1[(kf + i - k) + (kf + j - k) * ld];
         }
@@ -1025,10 +1030,13 @@ __global__ void k_fweights(MatView M, const Item* __restrict__ items, const Entr
   const int w = threadIdx.x >> 5;
   const int idx = blockIdx.x * (blockDim.x >> 5) + w;
   if (idx >= n) return;
-  // every tile holds at most max(K, kcap) = tc rows: leading dimension tc + 1
+  // T1, T2 hold at most max(K, kcap) = tc rows (leading dimension tc + 1),
+  // T0 at most kcap (leading dimension kcap + 1)
   const int ld = tc + 1;
-  double* T0 = smem + (size_t)w * 3 * ld * tc;
-  fweights_warp<NS>(M, items, ents, list[idx], u, ld, BW, IB, T0, T0 + ld * tc, T0 + 2 * ld * tc, lane);
+  const int ld0 = M.kcap + 1;
+  double* T0 = smem + (size_t)w * fweights_doubles(tc, M.kcap);
+  double* T1 = T0 + ld0 * M.kcap;
+  fweights_warp<NS>(M, items, ents, list[idx], u, ld, ld0, BW, IB, T0, T1, T1 + ld * tc, lane);
 }
 
 // The same with one block of kWideWarps warps per cluster task, for the
@@ -1051,14 +1059,15 @@ __global__ void k_fweights_wide(MatView M, const Item* __restrict__ items, const
   const int w = tid >> 5;
   if ((int)blockIdx.x >= n) return;
   const int ld = tc + 1;
+  const int ld0 = M.kcap + 1;
   double* T0 = smem;
-  double* T1 = T0 + ld * tc;
+  double* T1 = T0 + ld0 * M.kcap;
   double* T2 = T1 + ld * tc;
   const int id = list[blockIdx.x];
   const Item it = items[id];
   const int side = it.side;
   if (!pick(BW.orth, side)[it.cluster]) {
-    if (w == 0) fweights_warp<kNS>(M, items, ents, id, u, ld, BW, IB, T0, T1, T2, lane);
+    if (w == 0) fweights_warp<kNS>(M, items, ents, id, u, ld, ld0, BW, IB, T0, T1, T2, lane);
     return;
   }
   const int k = it.k;
@@ -1091,7 +1100,7 @@ __global__ void k_fweights_wide(MatView M, const Item* __restrict__ items, const
       const double w2 = nrm > 1e-150 ? st * recip(nrm * nrm) : 0.0;
       const double* Go = IB.Gv + (size_t)en.other * kSlot;
       const bool oo = orth_o[ot.cluster] != 0;
-      if (w == 0) load_block_rows(T0, M.S + (size_t)en.slot * kcap * kcap, kcap, side, l, k, lane, ld);
+      if (w == 0) load_block_rows(T0, M.S + (size_t)en.slot * kcap * kcap, kcap, side, l, k, lane, ld0);
       if (w == 1) {
         if (oo)
           load_tile(T1, ld, Go + l * 32, 32, l, u, lane);   // C_o (l x u)
@@ -1099,7 +1108,7 @@ __global__ void k_fweights_wide(MatView M, const Item* __restrict__ items, const
           load_gram(T1, ld, Go, Vgo + (size_t)ot.cluster * kSlot, false, l, Ko, lane);
       }
       __syncthreads();
-      const double nrm2 = sum_squares(T0, l, k, lane, ld);   // the same in every warp
+      const double nrm2 = sum_squares(T0, l, k, lane, ld0);   // the same in every warp
       const double w02 = nrm2 > 1e-300 ? st * recip(nrm2) : 0.0;
       const double wb = oo ? w2 - w02 : -w02;
 #pragma unroll
@@ -1107,7 +1116,7 @@ __global__ void k_fweights_wide(MatView M, const Item* __restrict__ items, const
         const int e = tid + kWideThreads * s;
         if (e < ntk) {
           double g = 0.0;
-          for (int r = 0; r < l; ++r) g = fma(T0[r + ei[s] * ld], T0[r + ej[s] * ld], g);
+          for (int r = 0; r < l; ++r) g = fma(T0[r + ei[s] * ld0], T0[r + ej[s] * ld0], g);
           acc[s] = fma(wb, g, acc[s]);
         }
       }
@@ -1120,7 +1129,7 @@ __global__ void k_fweights_wide(MatView M, const Item* __restrict__ items, const
             double v;
             if (j < k) {
               v = 0.0;
-              for (int q = 0; q < l; ++q) v = fma(T1[q + (i - k) * ld], T0[q + j * ld], v);
+              for (int q = 0; q < l; ++q) v = fma(T1[q + (i - k) * ld], T0[q + j * ld0], v);
             } else {
               v = Go[(l + i - k) + (l + j - k) * 32];
             }
@@ -1136,7 +1145,7 @@ __global__ void k_fweights_wide(MatView M, const Item* __restrict__ items, const
         double v;
         if (i < k) {
           v = 0.0;
-          for (int q = 0; q < l; ++q) v = fma(T0[q + i * ld], T1[q + j * ld], v);
+          for (int q = 0; q < l; ++q) v = fma(T0[q + i * ld0], T1[q + j * ld], v);
         } else {
           v = T1[l + i - k + j * ld];
         }
@@ -1151,7 +1160,7 @@ __global__ void k_fweights_wide(MatView M, const Item* __restrict__ items, const
           double v;
           if (j < k) {
             v = 0.0;
-            for (int q = 0; q < l; ++q) v = fma(T2[i + q * ld], T0[q + j * ld], v);
+            for (int q = 0; q < l; ++q) v = fma(T2[i + q * ld], T0[q + j * ld0], v);
           } else {
             v = T2[i + (l + j - k) * ld];
           }
@@ -1173,13 +1182,13 @@ __global__ void k_fweights_wide(MatView M, const Item* __restrict__ items, const
       else
         load_tile(T1, ld, IB.Wg + (size_t)it.parent * kSlot, 32, Kf, Kf, lane);
     }
-    if (w == 1) load_tile(T0, ld, E, kcap, k, kf, lane);
+    if (w == 1) load_tile(T0, ld0, E, kcap, k, kf, lane);
     __syncthreads();
     // T2 = E W11 (k x kf)
     for (int e2 = tid; e2 < k * kf; e2 += kWideThreads) {
       const int i = e2 % k, j = e2 / k;
       double v = 0.0;
-      for (int q = 0; q < kf; ++q) v = fma(T0[i + q * ld], T1[q + j * ld], v);
+      for (int q = 0; q < kf; ++q) v = fma(T0[i + q * ld0], T1[q + j * ld], v);
       T2[i + j * ld] = v;
     }
     __syncthreads();
@@ -1188,7 +1197,7 @@ __global__ void k_fweights_wide(MatView M, const Item* __restrict__ items, const
       const int e = tid + kWideThreads * s;
       if (e < ntk) {
         double v = acc[s];
-        for (int q = 0; q < kf; ++q) v = fma(T2[ei[s] + q * ld], T0[ej[s] + q * ld], v);
+        for (int q = 0; q < kf; ++q) v = fma(T2[ei[s] + q * ld], T0[ej[s] + q * ld0], v);
         acc[s] = v;
       }
     }
@@ -1201,7 +1210,7 @@ __global__ void k_fweights_wide(MatView M, const Item* __restrict__ items, const
           const int i = ei[s], j = ej[s];
           double v = acc[s];
           if (j < k) {
-            for (int q = 0; q < kf; ++q) v = fma(T1[(kf + i - k) + q * ld], T0[j + q * ld], v);
+            for (int q = 0; q < kf; ++q) v = fma(T1[(kf + i - k) + q * ld], T0[j + q * ld0], v);
           } else {
             v += T1[(kf + i - k) + (kf + j - k) * ld];
           }
@@ -1377,6 +1386,11 @@ __global__ void k_certify(const Item* __restrict__ items, int n, int u, int ld, 
   if (lane == 0) IB.rank[id] = K;
 }
 
+// Shared doubles of one k_fbasis warp (tiles of tc columns).
+__host__ __device__ constexpr int fbasis_doubles(int tc, bool general) {
+  return (general ? 2 : 1) * (tc + 1) * tc + kLd * tc + 32;
+}
+
 // New leaf bases V~_t L_t^{-*}, transfer matrices L_t^* E~_t L_{t+}^{-*} and
 // the commit E_t0 <- L_t0^* [E_t0; 0] for the certified updates (one launch,
 // one warp per cluster task, lane = row, forward substitution with the
@@ -1386,8 +1400,13 @@ __global__ void k_certify(const Item* __restrict__ items, int n, int u, int ld, 
 // kGeneral = false does the parts that have the block form and marks, for
 // the tasks of updates whose certificate failed, their cluster and its
 // ancestors for the exact path; kGeneral = true does the other parts.
+// Block-form launches use two warps per block and ten blocks per SM (their
+// shared tiles allow ten; the register budget is held to match).
+constexpr int kFbWarps = 2;
+
 template <bool kGeneral, int UMAX>
-__global__ void k_fbasis(MatView M, const Item* __restrict__ items, int n, int u, int tc,
+__global__ void __launch_bounds__(kGeneral ? 128 : 32 * kFbWarps, kGeneral ? 1 : 10)
+k_fbasis(MatView M, const Item* __restrict__ items, int n, int u, int tc,
                          const double* __restrict__ A, const double* __restrict__ B, ItemBuffers IB,
                          BaseWeights BW) {
   extern __shared__ double smem[];
@@ -1397,11 +1416,12 @@ __global__ void k_fbasis(MatView M, const Item* __restrict__ items, int n, int u
   if (id >= n) return;
   // R_t and E_t tiles with leading dimension tc + 1, the tile of 32 rows of
   // V_t (or R_{t+}) with kLd
+  // (the block-form variant reads E_t from global memory and has no third tile)
   const int ldt = tc + 1;
-  double* T0 = smem + (size_t)w * (2 * ldt * tc + kLd * tc + 32);
+  double* T0 = smem + (size_t)w * fbasis_doubles(tc, kGeneral);
   double* T1 = T0 + ldt * tc;
   double* T2 = T1 + kLd * tc;
-  double* ri = T2 + ldt * tc;
+  double* ri = kGeneral ? T2 + ldt * tc : T2;
   const Item it = items[id];
   const int side = it.side;
   if (IB.fail[it.update]) {
@@ -1481,7 +1501,8 @@ __global__ void k_fbasis(MatView M, const Item* __restrict__ items, int n, int u
   }
   if (!do_transfer) return;
   const int kf = it.kf;
-  load_tile(T2, ldt, pick(M.transfer, side) + (size_t)it.cluster * kcap * kcap, kcap, k, kf, lane);
+  const double* Eg = pick(M.transfer, side) + (size_t)it.cluster * kcap * kcap;   // E_t (k x kf, ld kcap)
+  if constexpr (kGeneral) load_tile(T2, ldt, Eg, kcap, k, kf, lane);
   double* Fo = IB.F + (size_t)id * kSlot;
   const int i = lane;
   __syncwarp();
@@ -1490,7 +1511,7 @@ __global__ void k_fbasis(MatView M, const Item* __restrict__ items, int n, int u
     // V_t0 is orthonormal
     if constexpr (!kGeneral) {
       if (i < K)
-        for (int j = 0; j < kf; ++j) Fo[i + j * 32] = i < k ? T2[i + j * ldt] : 0.0;
+        for (int j = 0; j < kf; ++j) Fo[i + j * 32] = i < k ? Eg[i + (size_t)j * kcap] : 0.0;
       return;
     }
     double z[32];
@@ -1521,7 +1542,7 @@ __global__ void k_fbasis(MatView M, const Item* __restrict__ items, int n, int u
     for (int e = lane; e < k * u; e += 32) {
       const int ii = e % k, q = e / k;
       double v = T0[ii + (k + q) * ldt];
-      for (int p = 0; p < kf; ++p) v = fma(-T2[ii + p * ldt], T1[p + (kf + q) * kLd], v);
+      for (int p = 0; p < kf; ++p) v = fma(-Eg[ii + (size_t)p * kcap], T1[p + (kf + q) * kLd], v);
       T0[ii + (k + q) * ldt] = v;
     }
     __syncwarp();
@@ -1538,7 +1559,7 @@ __global__ void k_fbasis(MatView M, const Item* __restrict__ items, int n, int u
         x[q] = v * ri[kf + q];
       }
     if (i < K) {
-      for (int j = 0; j < kf; ++j) Fo[i + j * 32] = i < k ? T2[i + j * ldt] : 0.0;
+      for (int j = 0; j < kf; ++j) Fo[i + j * 32] = i < k ? Eg[i + (size_t)j * kcap] : 0.0;
 #pragma unroll
       for (int q = 0; q < UMAX; ++q)
         if (q < u) Fo[i + (kf + q) * 32] = x[q];
@@ -1587,8 +1608,7 @@ int slots_for(int entries) {
   return need <= 5 ? 5 : need <= 10 ? 10 : kNS;
 }
 
-// Shared doubles of one k_fbasis warp (tiles of tc columns).
-constexpr int fbasis_doubles(int tc) { return 2 * (tc + 1) * tc + kLd * tc + 32; }
+
 
 int blocks_for(int n) { return (n + kWarps - 1) / kWarps; }
 
@@ -1698,12 +1718,12 @@ void launch_gram_weights(const Pipeline& P, int level) {
   const int n = P.lvl_ptr[level + 1] - P.lvl_ptr[level];
   if (n <= 0) return;
   const int tc = tile_cols(P);
-  const auto bytes = [](int warps, int c) { return (size_t)warps * 3 * (c + 1) * c * sizeof(double); };
+  const auto bytes = [](int warps, int c, int kc) { return (size_t)warps * fweights_doubles(c, kc) * sizeof(double); };
   if (n <= kWideMaxTasks) {
     // few tasks: one block of kWideWarps warps per task, one set of tiles
     static unsigned long long done_wide = 0;
-    smem_limit(k_fweights_wide, bytes(1, 32), done_wide);
-    k_fweights_wide<<<n, kWideThreads, bytes(1, tc), P.stream>>>(P.M, P.items, P.ents,
+    smem_limit(k_fweights_wide, bytes(1, 32, 32), done_wide);
+    k_fweights_wide<<<n, kWideThreads, bytes(1, tc, P.M.kcap), P.stream>>>(P.M, P.items, P.ents,
                                                                  P.lvl_list + P.lvl_ptr[level], n, P.u, tc, P.BW,
                                                                  P.IB);
     return;
@@ -1711,8 +1731,8 @@ void launch_gram_weights(const Pipeline& P, int level) {
   // two warps per block, tiles of (tc + 1) x tc
   constexpr int warps = 2;
   const auto go = [&](auto kern) {
-    smem_limit(kern, bytes(warps, 32), done);
-    kern<<<(n + warps - 1) / warps, 32 * warps, bytes(warps, tc), P.stream>>>(
+    smem_limit(kern, bytes(warps, 32, 32), done);
+    kern<<<(n + warps - 1) / warps, 32 * warps, bytes(warps, tc, P.M.kcap), P.stream>>>(
         P.M, P.items, P.ents, P.lvl_list + P.lvl_ptr[level], n, P.u, tc, P.BW, P.IB);
   };
   if (slots_for(P.kl * (P.kl + 1) / 2) <= 10)
@@ -1740,13 +1760,12 @@ void launch_gram_certify(const Pipeline& P) {
 
 // two warps per block: the per-warp tiles, not the block size, limit the
 // warps per SM, and smaller blocks pack the shared memory more tightly
-constexpr int kFbWarps = 2;
 
 template <int UMAX>
 void launch_fbasis_block_form(const Pipeline& P, int n, int tc) {
   static unsigned long long done = 0;
-  const size_t bytes = (size_t)kFbWarps * fbasis_doubles(tc) * sizeof(double);
-  smem_limit(k_fbasis<false, UMAX>, (size_t)kFbWarps * fbasis_doubles(32) * sizeof(double), done);
+  const size_t bytes = (size_t)kFbWarps * fbasis_doubles(tc, false) * sizeof(double);
+  smem_limit(k_fbasis<false, UMAX>, (size_t)kFbWarps * fbasis_doubles(32, false) * sizeof(double), done);
   k_fbasis<false, UMAX><<<(n + kFbWarps - 1) / kFbWarps, 32 * kFbWarps, bytes, P.stream>>>(P.M, P.items, n, P.u,
                                                                                           tc, P.A, P.B, P.IB, P.BW);
 }
@@ -1762,8 +1781,8 @@ void launch_gram_outputs(const Pipeline& P) {
     launch_fbasis_block_form<16>(P, n, tc);
   else
     launch_fbasis_block_form<32>(P, n, tc);
-  smem_limit(k_fbasis<true, 32>, (size_t)kWarps * fbasis_doubles(32) * sizeof(double), done);
-  k_fbasis<true, 32><<<blocks_for(n), 32 * kWarps, (size_t)kWarps * fbasis_doubles(tc) * sizeof(double),
+  smem_limit(k_fbasis<true, 32>, (size_t)kWarps * fbasis_doubles(32, true) * sizeof(double), done);
+  k_fbasis<true, 32><<<blocks_for(n), 32 * kWarps, (size_t)kWarps * fbasis_doubles(tc, true) * sizeof(double),
                        P.stream>>>(P.M, P.items, n, P.u, tc, P.A, P.B, P.IB, P.BW);
 }
 
