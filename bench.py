@@ -218,6 +218,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--mode", choices=("auto", "exact"), default="auto",
+                    help="path of the timed steps: auto (certified path, exact path where it fails) or exact")
+    ap.add_argument("--exact-steps", type=int, default=2,
+                    help="executions with every update on the exact path (reported beside the line)")
     ap.add_argument("--serial-steps", type=int, default=2,
                     help="executions with every phase on one stream, for per-phase device times")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -250,6 +254,8 @@ def main():
     blocks, A, B = blocks[:args.count], A[:args.count], B[:args.count]
     w = WORK
     P = b.h2_batch_create(ctx, Z, blocks, w["u"])
+    if args.mode == "exact":
+        b.h2_batch_set_mode(P, b.MODE_EXACT)   # every update through the exact path
     lenA, lenB = b.h2_batch_factor_sizes(P)
     Acat, Bcat = np.zeros(lenA), np.zeros(lenB)
     for j in range(len(blocks)):
@@ -302,7 +308,10 @@ def main():
                         "tflops": (ps["flops"] / (phase_ms[ph] / args.steps * 1e-3) / 1e12) if phase_ms[ph] > 0 else None}
     # dominant kernel on the critical path (the weights of the unchanged matrix
     # run beside it on side streams; the exact path only returns at once here)
-    dom = max((k for k in phases if k not in ("base_weights", "exact")), key=lambda k: phases[k]["ms"])
+    if args.mode == "exact":
+        dom = "exact"
+    else:
+        dom = max((k for k in phases if k not in ("base_weights", "exact")), key=lambda k: phases[k]["ms"])
     ach = phases[dom]["tflops"]
     n_exact = int(b.h2_batch_paths(ctx, P, len(blocks)).sum())
     kern = PHASE_KERNELS[dom]
@@ -337,6 +346,31 @@ def main():
             phases_serial[name] = {"ms": ms, "tflops": tf,
                                    "frac_fp64_peak": (tf / FP64_PEAK_TFLOPS) if tf else None}
 
+    # the same batch with every update forced through the exact path (the
+    # fallback for updates whose certificate fails: Householder folds and the
+    # truncation SVD), to show what a truncating workload costs
+    exact_mode = None
+    if args.exact_steps > 0 and args.mode == "auto":
+        b.h2_batch_set_mode(P, b.MODE_EXACT)
+        ts = []
+        for s in range(2 + args.exact_steps):
+            flush.fill_(s)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.h2_batch_execute(ctx, P, dA.data_ptr(), dB.data_ptr(), w["eps"])
+            e1.record(stream)
+            e1.synchronize()
+            if s >= 2:
+                ts.append(e0.elapsed_time(e1))
+        ex = b.h2_batch_phase_stats(ctx, P, b.PHASES.index("exact"))
+        ms = sum(ts) / len(ts)
+        gf = b.h2_batch_stats(ctx, P)["flops"] / 1e9
+        exact_mode = {"ms_per_step": ms, "value": len(blocks) / (ms / 1e3), "unit": UNIT,
+                      "gflop": gf, "tflops": gf / ms, "frac_fp64_peak": gf / ms / FP64_PEAK_TFLOPS,
+                      "exact_phase_ms": ex["ms"]}
+        b.h2_batch_set_mode(P, b.MODE_AUTO)
+
     # end to end through the C ABI from pinned host buffers (no phase events:
     # recorded inside the replayed graph they keep its copies from
     # overlapping the kernels)
@@ -368,12 +402,13 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD_NAME, "mode": "isolated (each update reads the same base matrix)",
+                       "path": args.mode,
                        "l2": "512 MB buffer written between timed steps",
                        "updates": len(blocks), "cluster_tasks": stats["cluster_tasks"],
                        "block_tasks": stats["block_tasks"], "exact_path_updates": n_exact},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": stats["launches"] * args.steps,
-            "clocks": clocks, "phases": phases, "phases_serial": phases_serial,
+            "clocks": clocks, "phases": phases, "phases_serial": phases_serial, "exact_mode": exact_mode,
             "gflop_per_step": stats["flops"] / 1e9}
     if rank == 0:
         print(json.dumps(line))
