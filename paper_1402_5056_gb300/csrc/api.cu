@@ -1979,7 +1979,11 @@ extern "C" h2_status h2_batch_item_tile(h2_ctx* ctx, const h2_batch* P, int64_t 
     H2_CUDA(cudaMemcpyAsync(tile.data(), src, kSlot * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     H2_CUDA(cudaStreamSynchronize(ctx->stream));
     if (which == 2 || (which == 1 && !exact)) {
-      std::copy(tile.begin(), tile.end(), out);
+      // only the (k+u) x (k+u) part (R_t: its first k+u columns) is written
+      const int K = it.k + P->u;
+      for (int j = 0; j < 32; ++j)
+        for (int i = 0; i < 32; ++i)
+          out[i + j * 32] = (j >= K || (which == 1 && i >= K)) ? 0.0 : tile[i + j * 32];
       return;
     }
     if (!exact) {

@@ -246,3 +246,55 @@ def test_full_batch_properties(ctx, full):
                     np.testing.assert_allclose(Q.T @ Q, np.eye(Q.shape[1]), atol=1e-13)
     finally:
         b.h2_batch_free(P)
+
+
+def test_update_independent_of_its_batch(ctx, full):
+    """An update computes the same bits whether it runs inside the 4096-update
+    batch (upper levels on k_fweights_wide, the others on k_fweights) or alone
+    (every level on k_fweights_wide): the Gram matrices of steps 2 and 3, the
+    certificate's R_t, the ranks, and the committed couplings."""
+    Zo, Zl, blocks, A, B = full
+    P = b.h2_batch_create(ctx, Zl, blocks, FULL_U)
+    try:
+        Acat, Bcat = concat_factors(P, A, B, FULL_U)
+        dA = torch.from_numpy(Acat).cuda()
+        dB = torch.from_numpy(Bcat).cuda()
+        b.h2_batch_execute(ctx, P, dA.data_ptr(), dB.data_ptr(), FULL_EPS)
+        b.h2_ctx_synchronize(ctx)
+        bt = Zo.blocks
+        rng = np.random.default_rng(11)
+        # updates with large subtrees reach the levels that run one warp per task
+        big = sorted(range(len(blocks)), key=lambda j: -Zo.V.tree.size[bt.row[blocks[j]]])[:2]
+        for j in big + [int(x) for x in rng.choice(len(blocks), 2, replace=False)]:
+            first, last = b.h2_batch_update_items(P, j)
+            Q = b.h2_batch_create(ctx, Zl, [blocks[j]], FULL_U)
+            try:
+                a1, b1 = concat_factors(Q, [A[j]], [B[j]], FULL_U)
+                qa = torch.from_numpy(a1).cuda()
+                qb = torch.from_numpy(b1).cuda()
+                b.h2_batch_execute(ctx, Q, qa.data_ptr(), qb.data_ptr(), FULL_EPS)
+                b.h2_ctx_synchronize(ctx)
+                f1, l1 = b.h2_batch_update_items(Q, 0)
+                assert l1 - f1 == last - first
+                for i in range(last - first):
+                    ia, ib = b.h2_batch_item_info(P, first + i), b.h2_batch_item_info(Q, f1 + i)
+                    assert (ia["side"], ia["cluster"], ia["rank"]) == (ib["side"], ib["cluster"], ib["rank"])
+                    for which in (0, 1, 2):
+                        np.testing.assert_array_equal(b.h2_batch_item_tile(ctx, P, first + i, which),
+                                                      b.h2_batch_item_tile(ctx, Q, f1 + i, which))
+                C1 = b.h2_matrix_clone(ctx, Zl)
+                C2 = b.h2_matrix_clone(ctx, Zl)
+                try:
+                    b.h2_batch_apply(ctx, P, j, dA.data_ptr(), dB.data_ptr(), C1)
+                    b.h2_batch_apply(ctx, Q, 0, qa.data_ptr(), qb.data_ptr(), C2)
+                    np.testing.assert_array_equal(b.h2_get_couplings(ctx, C1), b.h2_get_couplings(ctx, C2))
+                    for sd in (0, 1):
+                        for x, y in zip(b.h2_get_basis(ctx, C1, sd), b.h2_get_basis(ctx, C2, sd)):
+                            np.testing.assert_array_equal(x, y)
+                finally:
+                    b.h2_matrix_free(C1)
+                    b.h2_matrix_free(C2)
+            finally:
+                b.h2_batch_free(Q)
+    finally:
+        b.h2_batch_free(P)
