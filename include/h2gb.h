@@ -262,6 +262,22 @@ h2_status h2_batch_item_tile(h2_ctx* ctx, const h2_batch* batch, int64_t item, i
 /* Cluster tasks of update j occupy items [first, last). */
 h2_status h2_batch_update_items(const h2_batch* batch, int64_t j, int64_t* first, int64_t* last);
 
+/* count updates Z|_{b_j} <- trunc_eps(Z|_{b_j} + A_j B_j^*) applied to Z in
+ * place in the order j = 0, 1, ... (sequential semantics; Section 5 applied
+ * repeatedly): the result is that of calling h2_lowrank_update for each in
+ * turn.  Updates whose footprints do not meet -- what one writes (the bases
+ * of its subtrees T_t0, T_s0, the couplings of blocks with row in T_t0 or
+ * column in T_s0) the other does not read (the bases of its subtrees and
+ * their ancestors, the couplings in their block rows and columns) -- run
+ * together as one isolated batch (a wave); inside a wave every update reads
+ * the matrix as it was before the wave and the commits follow in order.
+ * A, B: DEVICE pointers to the concatenated factors: A_j (#t_j x u,
+ * column-major) starts at element sum_{i<j} #t_i u of A, B_j likewise with
+ * the column clusters.  waves (host, optional): the number of waves.
+ * Synchronizes. */
+h2_status h2_lowrank_update_sequence(h2_ctx* ctx, h2_matrix* Z, int64_t count, const int64_t* blocks,
+                                     int u, const double* A, const double* B, double eps,
+                                     int64_t* waves);
 /* One update applied to Z in place (sequential semantics; Section 5).
  * A (rows of block's row cluster x u, ld lda) and B (rows of column cluster
  * x u, ld ldb) are DEVICE pointers. */

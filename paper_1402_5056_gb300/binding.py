@@ -31,7 +31,7 @@ EXPORTS = [
     "h2_batch_task_info", "h2_batch_apply",
     "h2_batch_stats", "h2_batch_set_timing", "h2_batch_phase_stats", "h2_batch_item_info", "h2_batch_item_tile",
     "h2_batch_update_items", "h2_batch_set_mode", "h2_batch_paths", "h2_lowrank_update",
-    "h2_lowrank_update_noalloc",
+    "h2_lowrank_update_noalloc", "h2_lowrank_update_sequence",
 ]
 
 PHASES = ("base_weights", "rfactor", "norms", "weights", "truncate", "reproject", "exact", "bases")
@@ -94,6 +94,7 @@ _sig("h2_batch_factor_sizes", _int, _p, _p, _p)
 _sig("h2_batch_execute", _int, _p, _p, _p, _p, _dbl)
 _sig("h2_batch_execute_host", _int, _p, _p, _p, _p, _dbl, _p)
 _sig("h2_batch_result_size", _int, _p, _p)
+_sig("h2_lowrank_update_sequence", _int, _p, _p, _i64, _p, _int, _p, _p, _dbl, _p)
 _sig("h2_batch_result_offsets", _int, _p, _p, _p)
 _sig("h2_batch_task_info", _int, _p, _i64, _p)
 _sig("h2_batch_apply", _int, _p, _p, _i64, _p, _p, _p)
@@ -393,3 +394,14 @@ def h2_lowrank_update_noalloc(ctx, Z, block: int, u: int, A_dev: int, lda: int, 
     library-internal scratch; see include/h2gb.h for the limits)."""
     _check(_lib.h2_lowrank_update_noalloc(ctx, Z, int(block), int(u), C.c_void_p(A_dev), int(lda),
                                           C.c_void_p(B_dev), int(ldb), float(eps)), ctx)
+
+
+def h2_lowrank_update_sequence(ctx, Z, blocks, u: int, A_dev: int, B_dev: int, eps: float) -> int:
+    """Updates applied in order (waves of non-conflicting updates); A_dev,
+    B_dev: device pointers to the factors concatenated in order.  Returns
+    the number of waves."""
+    bl = np.ascontiguousarray(blocks, dtype=np.int64)
+    w = C.c_int64()
+    _check(_lib.h2_lowrank_update_sequence(ctx, Z, len(bl), _ptr(bl), int(u), C.c_void_p(A_dev), C.c_void_p(B_dev),
+                                           float(eps), C.byref(w)), ctx)
+    return w.value

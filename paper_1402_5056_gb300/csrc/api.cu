@@ -1365,8 +1365,11 @@ void execute(h2_ctx* ctx, h2_batch& P, const double* A, const double* B, double 
 
 }  // namespace
 
-extern "C" h2_status h2_batch_create(h2_ctx* ctx, const h2_matrix* Z, int64_t count, const int64_t* blocks,
-                                     int u, h2_batch** out) {
+namespace {
+// A batch over `blocks`; the factors of update j start at offA[j], offB[j]
+// of the concatenated arrays when given (else they are packed in order).
+h2_status create_batch(h2_ctx* ctx, const h2_matrix* Z, int64_t count, const int64_t* blocks, int u,
+                       const int64_t* offA, const int64_t* offB, h2_batch** out) {
   if (!Z || !out || count < 0 || (count > 0 && !blocks)) return H2_EINVAL;
   *out = nullptr;
   auto P = std::make_unique<h2_batch>();
@@ -1385,10 +1388,10 @@ extern "C" h2_status h2_batch_create(h2_ctx* ctx, const h2_matrix* Z, int64_t co
       H2_REQUIRE(blocks[j] >= 0 && blocks[j] < bt.count(), "h2_batch_create: block id out of range");
       P->rowsA[j] = Z->rows.size[bt.row[blocks[j]]];
       P->rowsB[j] = Z->cols.size[bt.col[blocks[j]]];
-      P->offA[j] = P->lenA;
-      P->offB[j] = P->lenB;
-      P->lenA += P->rowsA[j] * u;
-      P->lenB += P->rowsB[j] * u;
+      P->offA[j] = offA ? offA[j] : P->lenA;
+      P->offB[j] = offB ? offB[j] : P->lenB;
+      P->lenA = std::max(P->lenA, P->offA[j] + P->rowsA[j] * u);
+      P->lenB = std::max(P->lenB, P->offB[j] + P->rowsB[j] * u);
     }
     plan_batch(*P);
     if (!ctx) return;   // host-only plan
@@ -1399,6 +1402,12 @@ extern "C" h2_status h2_batch_create(h2_ctx* ctx, const h2_matrix* Z, int64_t co
   });
   if (s == H2_OK) *out = P.release();
   return s;
+}
+}  // namespace
+
+extern "C" h2_status h2_batch_create(h2_ctx* ctx, const h2_matrix* Z, int64_t count, const int64_t* blocks,
+                                     int u, h2_batch** out) {
+  return create_batch(ctx, Z, count, blocks, u, nullptr, nullptr, out);
 }
 
 extern "C" void h2_batch_free(h2_batch* P) {
@@ -2059,5 +2068,120 @@ extern "C" h2_status h2_lowrank_update(h2_ctx* ctx, h2_matrix* Z, int64_t block,
     H2_CUDA(cudaStreamSynchronize(st));
     dfree(dA);
     dfree(dB);
+  });
+}
+
+namespace {
+// Waves of a sequence of updates (sequential semantics, Section 5 applied in
+// order).  What update j reads: the bases (leaf matrices, transfer matrices,
+// ranks) of the clusters of T_t0 and of the ancestors of t0, likewise on the
+// column side, and the couplings of every block in the rows of those row
+// clusters and in the columns of those column clusters (the weights of
+// Section 4 over the whole block rows and the ancestor paths, the
+// reprojection).  What it writes: the bases of T_t0 and T_s0 (the commit of
+// E_t0 included) and the couplings of the blocks with row in T_t0 or column
+// in T_s0 (and the nearfield inside b0, which no update reads).  Update j
+// goes into the first wave after every earlier update whose writes it reads,
+// and not before any earlier update that reads what j writes; inside a wave
+// all updates read the matrix as it was before the wave and commit in order.
+int32_t sequence_waves(const h2_matrix* Z, int64_t count, const int64_t* blocks, std::vector<int32_t>& wave) {
+  const BlockTree& bt = Z->blocks;
+  const ClusterTree* tr[2] = {&Z->rows, &Z->cols};
+  const int32_t nc0 = tr[0]->count();
+  const int32_t ncl = nc0 + tr[1]->count();
+  const int32_t nslot = (int32_t)bt.adm.size();
+  std::vector<int32_t> wr_cl(ncl, -1), rd_cl(ncl, -1), wr_s(nslot, -1), rd_s(nslot, -1);
+  std::vector<int32_t> rcl, wcl, rs, ws;
+  int32_t waves = 0;
+  wave.assign(count, 0);
+  for (int64_t j = 0; j < count; ++j) {
+    rcl.clear();
+    wcl.clear();
+    rs.clear();
+    ws.clear();
+    for (int sd = 0; sd < 2; ++sd) {
+      const ClusterTree& ct = *tr[sd];
+      const int32_t c0 = sd == 0 ? bt.row[blocks[j]] : bt.col[blocks[j]];
+      const int32_t base = sd == 0 ? 0 : nc0;
+      const std::vector<int32_t>& ptr = sd == 0 ? bt.row_ptr : bt.col_ptr;
+      const std::vector<int32_t>& adm = sd == 0 ? bt.row_adm : bt.col_adm;
+      auto blocks_of = [&](int32_t c, std::vector<int32_t>& out) {
+        for (int32_t e = ptr[c]; e < ptr[c + 1]; ++e) out.push_back(adm[e]);
+      };
+      for (int32_t c = c0; c < c0 + ct.subtree[c0]; ++c) {   // T_c0 (preorder)
+        wcl.push_back(base + c);
+        rcl.push_back(base + c);
+        blocks_of(c, ws);
+        blocks_of(c, rs);
+      }
+      for (int32_t a = ct.father[c0]; a >= 0; a = ct.father[a]) {
+        rcl.push_back(base + a);
+        blocks_of(a, rs);
+      }
+    }
+    int32_t w = 0;
+    for (int32_t r : rcl) w = std::max(w, wr_cl[r] + 1);
+    for (int32_t r : rs) w = std::max(w, wr_s[r] + 1);
+    for (int32_t r : wcl) w = std::max(w, rd_cl[r]);
+    for (int32_t r : ws) w = std::max(w, rd_s[r]);
+    wave[j] = w;
+    waves = std::max(waves, w + 1);
+    for (int32_t r : wcl) wr_cl[r] = std::max(wr_cl[r], w);
+    for (int32_t r : ws) wr_s[r] = std::max(wr_s[r], w);
+    for (int32_t r : rcl) rd_cl[r] = std::max(rd_cl[r], w);
+    for (int32_t r : rs) rd_s[r] = std::max(rd_s[r], w);
+  }
+  return waves;
+}
+}  // namespace
+
+extern "C" h2_status h2_lowrank_update_sequence(h2_ctx* ctx, h2_matrix* Z, int64_t count, const int64_t* blocks,
+                                                int u, const double* A, const double* B, double eps,
+                                                int64_t* waves_out) {
+  if (!ctx || !Z || count < 0 || (count > 0 && (!blocks || !A || !B))) return H2_EINVAL;
+  return guard(ctx, [&] {
+    H2_REQUIRE(std::isfinite(eps) && eps >= 0, "h2_lowrank_update_sequence: eps must be finite and >= 0");
+    H2_REQUIRE(has_storage(Z), "h2_lowrank_update_sequence: matrix has no device storage");
+    const BlockTree& bt = Z->blocks;
+    std::vector<int64_t> offA(count), offB(count);
+    int64_t la = 0, lb = 0;
+    for (int64_t j = 0; j < count; ++j) {
+      H2_REQUIRE(blocks[j] >= 0 && blocks[j] < bt.count(), "h2_lowrank_update_sequence: block id out of range");
+      offA[j] = la;
+      offB[j] = lb;
+      la += Z->rows.size[bt.row[blocks[j]]] * u;
+      lb += Z->cols.size[bt.col[blocks[j]]] * u;
+    }
+    std::vector<int32_t> wave;
+    const int32_t waves = sequence_waves(Z, count, blocks, wave);
+    DeviceGuard g(ctx->device);
+    std::vector<int64_t> wb, wa, wbo;
+    std::vector<int64_t> members;
+    for (int32_t w = 0; w < waves; ++w) {
+      members.clear();
+      for (int64_t j = 0; j < count; ++j)
+        if (wave[j] == w) members.push_back(j);
+      wb.clear();
+      wa.clear();
+      wbo.clear();
+      for (int64_t j : members) {
+        wb.push_back(blocks[j]);
+        wa.push_back(offA[j]);
+        wbo.push_back(offB[j]);
+      }
+      // the wave as one isolated batch on the current matrix (its factors
+      // addressed in place in the caller's arrays), then its commits in order
+      h2_batch* P = nullptr;
+      h2_status s = create_batch(ctx, Z, (int64_t)wb.size(), wb.data(), u, wa.data(), wbo.data(), &P);
+      if (s != H2_OK) throw Error(s, ctx->last_error);
+      std::unique_ptr<h2_batch, void (*)(h2_batch*)> hold(P, h2_batch_free);
+      execute(ctx, *P, A, B, eps);
+      for (int64_t i = 0; i < (int64_t)wb.size(); ++i) {
+        s = h2_batch_apply(ctx, P, i, A, B, Z);
+        if (s != H2_OK) throw Error(s, ctx->last_error);
+      }
+    }
+    H2_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (waves_out) *waves_out = waves;
   });
 }
