@@ -43,7 +43,7 @@ PHASE_KERNELS = {"base_weights": "k_orth_local+k_vgram+k_bgram+k_bgram_down", "r
 # phase's launches of one execution, divided by its cluster tasks; the
 # roofline's `traffic` scales them to one launch of the benchmark batch.
 # Valid for the kernel versions of this commit.
-TRAFFIC_BYTES_PER_TASK = {"k_fweights+k_fweights_wide": 5787, "k_certify": 10972, "k_fbasis": 15560}
+TRAFFIC_BYTES_PER_TASK = {"k_fweights+k_fweights_wide": 5815, "k_certify": 10972, "k_fbasis": 15438}
 
 METRIC = "H²-LR setup s & low-rank updates/s, mixed vs FP64 GPU at equal ε; % roofline"
 UNIT = "updates/s"
