@@ -49,3 +49,34 @@ def test_pins_catch_mutation(name, tmp_path):
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=str(tmp_path),
                        env=env, timeout=600)
     assert r.returncode != 0, r.stdout[-2000:]
+
+
+MATVEC_MUTATIONS = {
+    "forward transformation without the transfer": (
+        "acc = acc + W.transfer[c].T @ xh[c]", "acc = acc + xh[c][:W.rank[s]]"),
+    "backward transformation transposed": (
+        "yh[c] = yh[c] + V.transfer[c] @ yh[t]", "yh[c] = yh[c] + V.transfer[c].T @ yh[t]"),
+    "coupling transposed": (
+        "yh[bt.row[b]] = yh[bt.row[b]] + Z.S[b] @ xh[bt.col[b]]",
+        "yh[bt.row[b]] = yh[bt.row[b]] + Z.S[b].T @ xh[bt.col[b]]"),
+    "nearfield dropped": ("out[rt.offset[t]:rt.offset[t] + rt.size[t]] += Z.N[b] @", "_ = Z.N[b] @"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MATVEC_MUTATIONS))
+def test_matvec_pins_catch_mutation(name, tmp_path):
+    before, after = MATVEC_MUTATIONS[name]
+    shutil.copytree(os.path.join(ROOT, "oracle"), tmp_path / "oracle")
+    path = tmp_path / "oracle" / "matvec.py"
+    src = path.read_text()
+    assert before in src
+    path.write_text(src.replace(before, after))
+    env = dict(os.environ)
+    env["PYTHONPATH"] = os.pathsep.join([str(tmp_path), ROOT, os.path.join(ROOT, "tests")])
+    code = ("import sys, pytest; sys.path.insert(0, %r); import oracle; "
+            "assert oracle.__file__.startswith(%r); "
+            "sys.exit(pytest.main(['-q', '-x', '-p', 'no:cacheprovider', %r]))"
+            % (str(tmp_path), str(tmp_path), os.path.join(ROOT, "tests", "test_oracle_matvec.py")))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=str(tmp_path),
+                       env=env, timeout=600)
+    assert r.returncode != 0, r.stdout[-2000:]
