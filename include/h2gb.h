@@ -262,6 +262,19 @@ h2_status h2_batch_item_tile(h2_ctx* ctx, const h2_batch* batch, int64_t item, i
 /* Cluster tasks of update j occupy items [first, last). */
 h2_status h2_batch_update_items(const h2_batch* batch, int64_t j, int64_t* first, int64_t* last);
 
+/* Y <- alpha Z X + beta Y for nrhs right-hand sides (Section 2: Eq. (vsw)
+ * on the admissible leaves with the nested bases of Eq. (nested), dense
+ * inadmissible leaves; the product the multiplication of Section 6 applies
+ * in its Case 2).  X (n_cols x nrhs, ld ldx) and Y (n_rows x nrhs, ld ldy)
+ * are column-major DEVICE arrays with rows in TREE order
+ * (h2_tree_permutation); they must not overlap; Y is not read when
+ * beta = 0.  Forward transformation over the column tree, the couplings,
+ * backward transformation over the row tree and the nearfield, each value
+ * of the matrix read once.  Asynchronous on the context's stream (its
+ * workspace is stream-ordered). */
+h2_status h2_matvec(h2_ctx* ctx, const h2_matrix* Z, int64_t nrhs, double alpha, const double* X,
+                    int64_t ldx, double beta, double* Y, int64_t ldy);
+
 /* count updates Z|_{b_j} <- trunc_eps(Z|_{b_j} + A_j B_j^*) applied to Z in
  * place in the order j = 0, 1, ... (sequential semantics; Section 5 applied
  * repeatedly): the result is that of calling h2_lowrank_update for each in

@@ -7,6 +7,7 @@
 #include <unordered_map>
 
 #include "h2_internal.h"
+#include "matvec.h"
 #include "update_kernels.h"
 
 using namespace h2;
@@ -315,6 +316,12 @@ extern "C" void h2_matrix_free(h2_matrix* Z) {
   dfree(Z->d_row_adm);
   dfree(Z->d_col_ptr);
   dfree(Z->d_col_adm);
+  dfree(Z->d_mv_lvl[0]);
+  dfree(Z->d_mv_lvl[1]);
+  dfree(Z->d_mv_leaves);
+  dfree(Z->d_near_ptr);
+  dfree(Z->d_near_col);
+  dfree(Z->d_near_off);
   delete Z;
 }
 
@@ -2183,5 +2190,113 @@ extern "C" h2_status h2_lowrank_update_sequence(h2_ctx* ctx, h2_matrix* Z, int64
     }
     H2_CUDA(cudaStreamSynchronize(ctx->stream));
     if (waves_out) *waves_out = waves;
+  });
+}
+
+namespace {
+void ensure_matvec_plan(h2_matrix* Z, cudaStream_t st) {
+  if (Z->mv_ready) return;
+  const ClusterTree* tr[2] = {&Z->rows, &Z->cols};
+  for (int sd = 0; sd < 2; ++sd) {
+    const ClusterTree& ct = *tr[sd];
+    const int L = ct.depth + 1;
+    std::vector<int32_t>& ptr = Z->mv_lvl_ptr[sd];
+    ptr.assign(L + 1, 0);
+    for (int32_t c = 0; c < ct.count(); ++c) ptr[ct.level[c] + 1]++;
+    for (int l = 0; l < L; ++l) ptr[l + 1] += ptr[l];
+    std::vector<int32_t> list(ct.count()), fill(ptr.begin(), ptr.end() - 1);
+    for (int32_t c = 0; c < ct.count(); ++c) list[fill[ct.level[c]]++] = c;
+    Z->d_mv_lvl[sd] = upload(list, st);
+  }
+  std::vector<int32_t> leaves;
+  for (int32_t c = 0; c < Z->rows.count(); ++c)
+    if (Z->rows.leaf(c)) leaves.push_back(c);
+  Z->mv_n_leaves = (int32_t)leaves.size();
+  Z->d_mv_leaves = upload(leaves, st);
+  const BlockTree& bt = Z->blocks;
+  std::vector<int32_t> nptr(Z->rows.count() + 1, 0), ncol(bt.near.size());
+  std::vector<int64_t> noff(bt.near.size());
+  for (int32_t b : bt.near) nptr[bt.row[b] + 1]++;
+  for (int32_t c = 0; c < Z->rows.count(); ++c) nptr[c + 1] += nptr[c];
+  std::vector<int32_t> nf(nptr.begin(), nptr.end() - 1);
+  for (size_t i = 0; i < bt.near.size(); ++i) {
+    const int32_t b = bt.near[i];
+    const int32_t x = nf[bt.row[b]]++;
+    ncol[x] = bt.col[b];
+    noff[x] = Z->near_off[bt.slot[b]];
+  }
+  Z->d_near_ptr = upload(nptr, st);
+  Z->d_near_col = upload(ncol, st);
+  Z->d_near_off = upload(noff, st);
+  Z->mv_ready = true;
+}
+}  // namespace
+
+extern "C" h2_status h2_matvec(h2_ctx* ctx, const h2_matrix* Zc, int64_t nrhs, double alpha, const double* X,
+                               int64_t ldx, double beta, double* Y, int64_t ldy) {
+  if (!ctx || !Zc || nrhs < 0) return H2_EINVAL;
+  return guard(ctx, [&] {
+    h2_matrix* Z = const_cast<h2_matrix*>(Zc);   // the plan is cached on the matrix
+    H2_REQUIRE(has_storage(Z), "h2_matvec: matrix has no device storage");
+    if (nrhs == 0) return;
+    const int64_t nr = Z->rows.count() ? Z->rows.size[0] : 0;
+    const int64_t nc = Z->cols.count() ? Z->cols.size[0] : 0;
+    H2_REQUIRE(X && Y, "h2_matvec: operands missing");
+    H2_REQUIRE(ldx >= nc && ldy >= nr, "h2_matvec: leading dimension too small");
+    H2_REQUIRE(nrhs <= (int64_t)1 << 20, "h2_matvec: too many right-hand sides");
+    const double* Xe = X + (size_t)(nrhs - 1) * ldx + nc;
+    const double* Ye = Y + (size_t)(nrhs - 1) * ldy + nr;
+    H2_REQUIRE(Xe <= Y || Ye <= X, "h2_matvec: X and Y overlap");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = ctx->stream;
+    ensure_matvec_plan(Z, st);
+    MatvecArgs a{};
+    const int64_t* offs[2] = {Z->d_row_off, Z->d_col_off};
+    const int32_t* sizes[2] = {Z->d_row_size, Z->d_col_size};
+    const int32_t* subs[2] = {Z->d_subtree_r, Z->d_subtree_c};
+    const int32_t* fath[2] = {Z->d_father_r, Z->d_father_c};
+    for (int sd = 0; sd < 2; ++sd) {
+      const DeviceBasis& bs = basis_of(Z, sd);
+      a.off[sd] = offs[sd];
+      a.size[sd] = sizes[sd];
+      a.rank[sd] = bs.d_rank;
+      a.subtree[sd] = subs[sd];
+      a.father[sd] = fath[sd];
+      a.leaf[sd] = bs.d_leaf;
+      a.leaf_off[sd] = bs.d_leaf_off;
+      a.transfer[sd] = bs.d_transfer;
+      a.lvl_ptr[sd] = Z->mv_lvl_ptr[sd].data();
+      a.lvl_list[sd] = Z->d_mv_lvl[sd];
+      a.levels[sd] = (int)Z->mv_lvl_ptr[sd].size() - 1;
+      a.n_clusters[sd] = tree_of(Z, sd).count();
+    }
+    a.S = Z->d_S;
+    a.kcap = Z->kcap;
+    a.row_ptr = Z->d_row_ptr;
+    a.row_adm = Z->d_row_adm;
+    a.blk_col = Z->d_blk_col;
+    a.N = Z->d_N;
+    a.near_ptr = Z->d_near_ptr;
+    a.near_col = Z->d_near_col;
+    a.near_off = Z->d_near_off;
+    a.leaves = Z->d_mv_leaves;
+    a.n_leaves = Z->mv_n_leaves;
+    a.nrhs = (int)nrhs;
+    a.alpha = alpha;
+    a.beta = beta;
+    a.X = X;
+    a.ldx = ldx;
+    a.Y = Y;
+    a.ldy = ldy;
+    // per-cluster workspace, stream-ordered
+    const size_t wx = (size_t)a.n_clusters[1] * Z->kcap * nrhs, wy = (size_t)a.n_clusters[0] * Z->kcap * nrhs;
+    void* w = nullptr;
+    if (wx + wy) H2_CUDA(cudaMallocAsync(&w, (wx + wy) * sizeof(double), st));
+    a.xh = static_cast<double*>(w);
+    a.yh = a.xh ? a.xh + wx : nullptr;
+    launch_matvec(a, st);
+    const cudaError_t e = cudaGetLastError();
+    if (w) H2_CUDA(cudaFreeAsync(w, st));
+    H2_CUDA(e);
   });
 }

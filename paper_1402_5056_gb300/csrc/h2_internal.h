@@ -108,4 +108,15 @@ struct h2_matrix {
   int32_t* d_col_adm = nullptr;
   int32_t* d_father_r = nullptr;
   int32_t* d_father_c = nullptr;
+  // plan of h2_matvec (built on first use; the trees never change): clusters
+  // of each tree by level, the leaves of the row tree, the nearfield blocks
+  // by row cluster (CSR: column cluster, offset in d_N)
+  bool mv_ready = false;
+  std::vector<int32_t> mv_lvl_ptr[2];
+  int32_t* d_mv_lvl[2] = {nullptr, nullptr};
+  int32_t* d_mv_leaves = nullptr;
+  int32_t mv_n_leaves = 0;
+  int32_t* d_near_ptr = nullptr;
+  int32_t* d_near_col = nullptr;
+  int64_t* d_near_off = nullptr;
 };

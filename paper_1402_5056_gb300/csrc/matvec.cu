@@ -1,0 +1,171 @@
+// H^2-matrix times a block of vectors (Section 2: Eq. (vsw) for the
+// admissible leaves, dense inadmissible leaves, nested bases Eq. (nested)),
+// the product the multiplication of Section 6 applies in its Case 2.
+//
+//   forward transformation, bottom-up over the column tree:
+//     xh_s = W_s^* X|_s (leaf), xh_s = sum over sons E_{s'}^* xh_{s'};
+//   coupling, every row cluster at once: yh_t = sum over row(t) S_b xh_s;
+//   backward transformation, top-down over the row tree:
+//     yh_{t'} += E_{t'} yh_t for the sons t' of t;
+//   leaves of the row tree: Y|_t = alpha (V_t yh_t + the rows of t of every
+//     nearfield block N_b X|_s whose row cluster contains t) + beta Y|_t
+//     (a nearfield block pairs a leaf with a cluster that may be larger).
+//
+// One warp per cluster; lanes take the entries (i, r) of the k x nrhs
+// results (entry e = i + k r) or, at the leaves, the rows.  Every value of
+// the matrix is read once per call; the per-level launches follow the tree.
+#include "matvec.h"
+
+namespace h2 {
+namespace {
+
+constexpr int kMvWarps = 4;
+
+__device__ __forceinline__ bool is_leaf(const int32_t* subtree, int c) { return subtree[c] == 1; }
+
+__global__ void k_mv_forward(MatvecArgs a, const int32_t* __restrict__ list, int n) {
+  const int w = blockIdx.x * kMvWarps + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (w >= n) return;
+  const int c = list[w];
+  const int kc = a.rank[1][c];
+  const int kcap = a.kcap;
+  double* out = a.xh + (size_t)c * kcap * a.nrhs;
+  const int ne = kc * a.nrhs;
+  if (is_leaf(a.subtree[1], c)) {
+    const int m = a.size[1][c];
+    const double* Wl = a.leaf[1] + a.leaf_off[1][c];
+    const double* X = a.X + a.off[1][c];
+    for (int e = lane; e < ne; e += 32) {
+      const int i = e % kc, r = e / kc;
+      double v = 0.0;
+      for (int p = 0; p < m; ++p) v = fma(Wl[p + (size_t)i * m], X[p + r * a.ldx], v);
+      out[i + r * kcap] = v;
+    }
+  } else {
+    const int s0 = c + 1;
+    const int s1 = c + 1 + a.subtree[1][c + 1];
+    const int k0 = a.rank[1][s0], k1 = a.rank[1][s1];
+    const double* E0 = a.transfer[1] + (size_t)s0 * kcap * kcap;
+    const double* E1 = a.transfer[1] + (size_t)s1 * kcap * kcap;
+    const double* x0 = a.xh + (size_t)s0 * kcap * a.nrhs;
+    const double* x1 = a.xh + (size_t)s1 * kcap * a.nrhs;
+    for (int e = lane; e < ne; e += 32) {
+      const int i = e % kc, r = e / kc;
+      double v = 0.0;
+      for (int q = 0; q < k0; ++q) v = fma(E0[q + i * kcap], x0[q + r * kcap], v);
+      for (int q = 0; q < k1; ++q) v = fma(E1[q + i * kcap], x1[q + r * kcap], v);
+      out[i + r * kcap] = v;
+    }
+  }
+}
+
+__global__ void k_mv_coupling(MatvecArgs a) {
+  const int t = blockIdx.x * kMvWarps + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (t >= a.n_clusters[0]) return;
+  const int kt = a.rank[0][t];
+  const int kcap = a.kcap;
+  double* out = a.yh + (size_t)t * kcap * a.nrhs;
+  const int ne = kt * a.nrhs;
+  const int e0 = a.row_ptr[t], e1 = a.row_ptr[t + 1];
+  for (int e = lane; e < ne; e += 32) {
+    const int i = e % kt, r = e / kt;
+    double v = 0.0;
+    for (int x = e0; x < e1; ++x) {
+      const int slot = a.row_adm[x];
+      const int s = a.blk_col[slot];
+      const int ls = a.rank[1][s];
+      const double* S = a.S + (size_t)slot * kcap * kcap;
+      const double* xs = a.xh + (size_t)s * kcap * a.nrhs + r * kcap;
+      for (int q = 0; q < ls; ++q) v = fma(S[i + q * kcap], xs[q], v);
+    }
+    out[i + r * kcap] = v;
+  }
+}
+
+__global__ void k_mv_backward(MatvecArgs a, const int32_t* __restrict__ list, int n) {
+  const int w = blockIdx.x * kMvWarps + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (w >= n) return;
+  const int c = list[w];
+  const int f = a.father[0][c];
+  if (f < 0) return;
+  const int kc = a.rank[0][c], kf = a.rank[0][f];
+  const int kcap = a.kcap;
+  const double* E = a.transfer[0] + (size_t)c * kcap * kcap;   // kc x kf
+  const double* yf = a.yh + (size_t)f * kcap * a.nrhs;
+  double* yc = a.yh + (size_t)c * kcap * a.nrhs;
+  const int ne = kc * a.nrhs;
+  for (int e = lane; e < ne; e += 32) {
+    const int i = e % kc, r = e / kc;
+    double v = yc[i + r * kcap];
+    for (int q = 0; q < kf; ++q) v = fma(E[i + q * kcap], yf[q + r * kcap], v);
+    yc[i + r * kcap] = v;
+  }
+}
+
+__global__ void k_mv_leaves(MatvecArgs a) {
+  const int w = blockIdx.x * kMvWarps + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (w >= a.n_leaves) return;
+  const int t = a.leaves[w];
+  const int m = a.size[0][t];
+  const int kt = a.rank[0][t];
+  const int kcap = a.kcap;
+  const double* Vl = a.leaf[0] + a.leaf_off[0][t];
+  const double* yt = a.yh + (size_t)t * kcap * a.nrhs;
+  for (int r = 0; r < a.nrhs; ++r)
+    for (int p = lane; p < m; p += 32) {
+      double v = 0.0;
+      for (int i = 0; i < kt; ++i) v = fma(Vl[p + (size_t)i * m], yt[i + r * kcap], v);
+      // nearfield blocks whose row cluster contains t (the leaf itself, or
+      // an ancestor paired with a leaf of the column tree): their rows of t
+      for (int c = t; c >= 0; c = a.father[0][c]) {
+        const int mc = a.size[0][c];
+        const int64_t row = a.off[0][t] - a.off[0][c] + p;
+        for (int x = a.near_ptr[c]; x < a.near_ptr[c + 1]; ++x) {
+          const int s = a.near_col[x];
+          const int ms = a.size[1][s];
+          const double* Nb = a.N + a.near_off[x] + row;
+          const double* X = a.X + a.off[1][s] + r * a.ldx;
+          for (int q = 0; q < ms; ++q) v = fma(Nb[(size_t)q * mc], X[q], v);
+        }
+      }
+      double* y = a.Y + a.off[0][t] + p + r * a.ldy;
+      *y = a.beta == 0.0 ? a.alpha * v : fma(a.beta, *y, a.alpha * v);
+    }
+}
+
+int blocks_of(int n) { return (n + kMvWarps - 1) / kMvWarps; }
+
+}  // namespace
+
+int launch_matvec(const MatvecArgs& a, cudaStream_t st) {
+  int launches = 0;
+  // forward transformation: deepest level first
+  for (int l = a.levels[1] - 1; l >= 0; --l) {
+    const int n = a.lvl_ptr[1][l + 1] - a.lvl_ptr[1][l];
+    if (n <= 0) continue;
+    k_mv_forward<<<blocks_of(n), 32 * kMvWarps, 0, st>>>(a, a.lvl_list[1] + a.lvl_ptr[1][l], n);
+    ++launches;
+  }
+  if (a.n_clusters[0] > 0) {
+    k_mv_coupling<<<blocks_of(a.n_clusters[0]), 32 * kMvWarps, 0, st>>>(a);
+    ++launches;
+  }
+  // backward transformation: level 1 down (the root has no father)
+  for (int l = 1; l < a.levels[0]; ++l) {
+    const int n = a.lvl_ptr[0][l + 1] - a.lvl_ptr[0][l];
+    if (n <= 0) continue;
+    k_mv_backward<<<blocks_of(n), 32 * kMvWarps, 0, st>>>(a, a.lvl_list[0] + a.lvl_ptr[0][l], n);
+    ++launches;
+  }
+  if (a.n_leaves > 0) {
+    k_mv_leaves<<<blocks_of(a.n_leaves), 32 * kMvWarps, 0, st>>>(a);
+    ++launches;
+  }
+  return launches;
+}
+
+}  // namespace h2
