@@ -55,6 +55,19 @@ WORKLOAD_NAME = ("isolated H2 low-rank updates: 4096 rank-8 updates, 256x256-poi
 # x 152 SMs x 2 flop x 2.070 GHz; the roofline denominator of this
 # ALU-bound path.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+
+
+def _hbm_peak():
+    """Copy bandwidth measured on the GB300s (GB/s), else the
+    fallback figure of an earlier measurement."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+HBM_PEAK_GBS, HBM_PEAK_KIND = _hbm_peak()
 FP64_PEAK_SOURCE = "derived: 152 SM x 2 DFMA/clk x 2 flop x 2070 MHz (DFMA probe: 1.254 TFLOP/s measured)"
 L2_FLUSH_BYTES = 512 << 20
 
@@ -86,6 +99,58 @@ def lib_workload(b, ctx, rank_offset: int = 0):
         b.h2_set_couplings(ctx, Z, S)
         b.h2_set_nearfield(ctx, Z, Nf)
     return Z, blocks, A, B
+
+
+def matvec_work(b, Z):
+    """Algorithmic bytes (nrhs = 1) and flops per right-hand side of one
+    H2 matrix times vector: every coupling, nearfield value, leaf basis and
+    transfer matrix once, x read and y written once."""
+    tc = b.h2_tree_clusters(Z)
+    tb = b.h2_tree_blocks(Z)
+    rv, rw = b.h2_get_ranks(Z, 0).astype(np.int64), b.h2_get_ranks(Z, 1).astype(np.int64)
+    size = np.asarray(tc["size"], dtype=np.int64)
+    father = np.asarray(tc["father"])
+    leaf = np.asarray(tc["son0"]) < 0
+    kind, row, col = np.asarray(tb["kind"]), np.asarray(tb["row"]), np.asarray(tb["col"])
+    adm, near = kind == 1, kind == 2
+    s_vals = int((rv[row[adm]] * rw[col[adm]]).sum())
+    n_vals = int((size[row[near]] * size[col[near]]).sum())
+    leaf_vals = int((size[leaf] * rv[leaf]).sum() + (size[leaf] * rw[leaf]).sum())
+    inner = father >= 0
+    tr_vals = int((rv[inner] * rv[father[inner]]).sum() + (rw[inner] * rw[father[inner]]).sum())
+    n = int(size[0])
+    vals = s_vals + n_vals + leaf_vals + tr_vals
+    return 8 * (vals + 2 * n), 2 * vals
+
+
+def matvec_measure(b, ctx, Z, stream, flush, steps):
+    import torch
+    n = int(b.h2_tree_clusters(Z)["size"][0])
+    nbytes, flops = matvec_work(b, Z)
+    out = {}
+    for nrhs in (1, 16):
+        X = torch.randn(nrhs * n, dtype=torch.float64, device="cuda")
+        Y = torch.zeros(nrhs * n, dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            b.h2_matvec(ctx, Z, nrhs, 1.0, X.data_ptr(), n, 0.0, Y.data_ptr(), n)
+        ts = []
+        for s in range(steps):
+            flush.fill_(s)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.h2_matvec(ctx, Z, nrhs, 1.0, X.data_ptr(), n, 0.0, Y.data_ptr(), n)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = sum(ts) / len(ts)
+        mb = nbytes + 16 * n * (nrhs - 1)
+        gbs = mb / (ms * 1e-3) / 1e9
+        tf = nrhs * flops / (ms * 1e-3) / 1e12
+        out["nrhs_%d" % nrhs] = {"ms": ms, "algorithmic_bytes": mb, "GB/s": gbs, "frac_hbm": gbs / HBM_PEAK_GBS,
+                                 "gflop": nrhs * flops / 1e9, "TFLOP/s": tf, "frac_fp64_peak": tf / FP64_PEAK_TFLOPS}
+    out["peak_source"] = "HBM %.0f GB/s (%s); FP64: %s" % (HBM_PEAK_GBS, HBM_PEAK_KIND, FP64_PEAK_SOURCE)
+    return out
 
 
 class ClockSampler:
@@ -218,6 +283,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--matvec-steps", type=int, default=10, help="timed h2_matvec calls per case (0: none)")
     ap.add_argument("--mode", choices=("auto", "exact"), default="auto",
                     help="path of the timed steps: auto (certified path, exact path where it fails) or exact")
     ap.add_argument("--exact-steps", type=int, default=2,
@@ -392,6 +458,13 @@ def main():
         e2e = {"value": len(blocks) / (sum(ts) / len(ts)), "unit": UNIT,
                "h2d_bytes_per_step": 8 * (lenA + lenB), "d2h_bytes_per_step": 8 * int(res.numel())}
 
+    # H2 matrix times vectors on the same matrix (h2_matvec): one vector
+    # (bound by HBM: every value of the matrix read once) and k = 16 vectors
+    # (the products of the multiplication's Case 2; bound by the FP64 pipe)
+    mv = None
+    if args.matvec_steps > 0:
+        mv = matvec_measure(b, ctx, Z, stream, flush, args.matvec_steps)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         done, wall, cpu_s, _, _ = oracle_sample(args.cpu_seconds)
@@ -409,6 +482,7 @@ def main():
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": stats["launches"] * args.steps,
             "clocks": clocks, "phases": phases, "phases_serial": phases_serial, "exact_mode": exact_mode,
+            "matvec": mv,
             "gflop_per_step": stats["flops"] / 1e9}
     if rank == 0:
         print(json.dumps(line))

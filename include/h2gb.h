@@ -275,6 +275,14 @@ h2_status h2_batch_update_items(const h2_batch* batch, int64_t j, int64_t* first
 h2_status h2_matvec(h2_ctx* ctx, const h2_matrix* Z, int64_t nrhs, double alpha, const double* X,
                     int64_t ldx, double beta, double* Y, int64_t ldy);
 
+/* The dense block Z|_{t x s} of any block-tree node (Section 2: the
+ * admissible leaves V_t S_b W_s^*, the dense inadmissible leaves, and the
+ * sub-blocks of a subdivided node), into the DEVICE array out (#t x #s,
+ * column-major, ld >= #t, rows and columns in tree order).  Computed as the
+ * rows t of Z times the unit columns of s (h2_matvec with #s right-hand
+ * sides): a check and a diagnostic, not a fast path.  Asynchronous. */
+h2_status h2_block_to_dense(h2_ctx* ctx, const h2_matrix* Z, int64_t block, double* out, int64_t ld);
+
 /* count updates Z|_{b_j} <- trunc_eps(Z|_{b_j} + A_j B_j^*) applied to Z in
  * place in the order j = 0, 1, ... (sequential semantics; Section 5 applied
  * repeatedly): the result is that of calling h2_lowrank_update for each in

@@ -2300,3 +2300,51 @@ extern "C" h2_status h2_matvec(h2_ctx* ctx, const h2_matrix* Zc, int64_t nrhs, d
     H2_CUDA(e);
   });
 }
+
+namespace {
+__global__ void k_unit_columns(double* X, int64_t n, int64_t s_off, int64_t ns) {
+  // X (n x ns, ld n) = columns s_off .. s_off + ns - 1 of the identity
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= n * ns) return;
+  const int64_t i = e % n, j = e / n;
+  X[e] = i == s_off + j ? 1.0 : 0.0;
+}
+
+__global__ void k_rows_out(const double* Y, int64_t n, int64_t t_off, int64_t nt, int64_t ns, double* out,
+                           int64_t ld) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= nt * ns) return;
+  const int64_t i = e % nt, j = e / nt;
+  out[i + j * ld] = Y[t_off + i + j * n];
+}
+}  // namespace
+
+extern "C" h2_status h2_block_to_dense(h2_ctx* ctx, const h2_matrix* Z, int64_t block, double* out, int64_t ld) {
+  if (!ctx || !Z || !out) return H2_EINVAL;
+  return guard(ctx, [&] {
+    const BlockTree& bt = Z->blocks;
+    H2_REQUIRE(block >= 0 && block < bt.count(), "h2_block_to_dense: block out of range");
+    H2_REQUIRE(has_storage(Z), "h2_block_to_dense: matrix has no device storage");
+    const int32_t t = bt.row[block], sc = bt.col[block];
+    const int64_t nt = Z->rows.size[t], ns = Z->cols.size[sc];
+    H2_REQUIRE(ld >= nt, "h2_block_to_dense: leading dimension too small");
+    const int64_t n_r = Z->rows.size[0], n_c = Z->cols.size[0];
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = ctx->stream;
+    // Z|_{t x s} = rows t of Z times the unit columns of s (the whole matrix
+    // product h2_matvec with #s right-hand sides)
+    void* w = nullptr;
+    H2_CUDA(cudaMallocAsync(&w, (size_t)(n_c + n_r) * ns * sizeof(double), st));
+    double* X = static_cast<double*>(w);
+    double* Y = X + (size_t)n_c * ns;
+    const int th = 256;
+    k_unit_columns<<<(unsigned)((n_c * ns + th - 1) / th), th, 0, st>>>(X, n_c, Z->cols.off[sc], ns);
+    h2_status s = h2_matvec(ctx, Z, ns, 1.0, X, n_c, 0.0, Y, n_r);
+    if (s == H2_OK && nt * ns > 0)
+      k_rows_out<<<(unsigned)((nt * ns + th - 1) / th), th, 0, st>>>(Y, n_r, Z->rows.off[t], nt, ns, out, ld);
+    const cudaError_t e = cudaGetLastError();
+    H2_CUDA(cudaFreeAsync(w, st));
+    if (s != H2_OK) throw Error(s, ctx->last_error);
+    H2_CUDA(e);
+  });
+}

@@ -60,27 +60,58 @@ __global__ void k_mv_forward(MatvecArgs a, const int32_t* __restrict__ list, int
   }
 }
 
+// Coupling: lane = (row i of yh_t, group g); the groups split the
+// right-hand sides (RB at a time, sharing each S_b load) or, with fewer
+// right-hand sides than groups, the blocks of row(t) (partial sums added by
+// shuffles in a fixed order).
+template <int RB>
 __global__ void k_mv_coupling(MatvecArgs a) {
   const int t = blockIdx.x * kMvWarps + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (t >= a.n_clusters[0]) return;
   const int kt = a.rank[0][t];
+  if (kt == 0) return;
   const int kcap = a.kcap;
+  const int groups = kt <= 32 ? 32 / kt : 1;
+  const int i = lane % kt, g = lane / kt;
+  const bool in = g < groups;
   double* out = a.yh + (size_t)t * kcap * a.nrhs;
-  const int ne = kt * a.nrhs;
   const int e0 = a.row_ptr[t], e1 = a.row_ptr[t + 1];
-  for (int e = lane; e < ne; e += 32) {
-    const int i = e % kt, r = e / kt;
-    double v = 0.0;
-    for (int x = e0; x < e1; ++x) {
-      const int slot = a.row_adm[x];
-      const int s = a.blk_col[slot];
-      const int ls = a.rank[1][s];
-      const double* S = a.S + (size_t)slot * kcap * kcap;
-      const double* xs = a.xh + (size_t)s * kcap * a.nrhs + r * kcap;
-      for (int q = 0; q < ls; ++q) v = fma(S[i + q * kcap], xs[q], v);
+  const int rsteps = (a.nrhs + RB - 1) / RB;
+  const bool split_blocks = rsteps < groups;   // few right-hand sides: the groups share the blocks
+  for (int r0 = (split_blocks ? 0 : g) * RB; r0 < a.nrhs; r0 += (split_blocks ? 1 : groups) * RB) {
+    double acc[RB];
+#pragma unroll
+    for (int j = 0; j < RB; ++j) acc[j] = 0.0;
+    if (in)
+      for (int x = e0 + (split_blocks ? g : 0); x < e1; x += split_blocks ? groups : 1) {
+        const int slot = a.row_adm[x];
+        const int s = a.blk_col[slot];
+        const int ls = a.rank[1][s];
+        const double* S = a.S + (size_t)slot * kcap * kcap + i;
+        const double* xs = a.xh + (size_t)s * kcap * a.nrhs + (size_t)r0 * kcap;
+        for (int q = 0; q < ls; ++q) {
+          const double sv = S[q * kcap];
+#pragma unroll
+          for (int j = 0; j < RB; ++j)
+            if (r0 + j < a.nrhs) acc[j] = fma(sv, xs[q + j * kcap], acc[j]);
+        }
+      }
+    if (split_blocks) {
+      // add the groups' partial sums: group 0 collects g = 1, 2, ... in order
+#pragma unroll
+      for (int j = 0; j < RB; ++j)
+        for (int h = 1; h < groups; ++h) {
+          const double o = __shfl_sync(0xffffffffu, acc[j], (lane + h * kt) & 31);
+          if (g == 0) acc[j] += o;
+        }
+      if (g != 0 || !in) continue;
+    } else if (!in) {
+      continue;
     }
-    out[i + r * kcap] = v;
+#pragma unroll
+    for (int j = 0; j < RB; ++j)
+      if (r0 + j < a.nrhs) out[i + (r0 + j) * kcap] = acc[j];
   }
 }
 
@@ -105,6 +136,9 @@ __global__ void k_mv_backward(MatvecArgs a, const int32_t* __restrict__ list, in
   }
 }
 
+// Leaves: lane = row; RB right-hand sides at a time share every load of the
+// leaf basis and of the nearfield blocks.
+template <int RB>
 __global__ void k_mv_leaves(MatvecArgs a) {
   const int w = blockIdx.x * kMvWarps + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
@@ -115,10 +149,17 @@ __global__ void k_mv_leaves(MatvecArgs a) {
   const int kcap = a.kcap;
   const double* Vl = a.leaf[0] + a.leaf_off[0][t];
   const double* yt = a.yh + (size_t)t * kcap * a.nrhs;
-  for (int r = 0; r < a.nrhs; ++r)
+  for (int r0 = 0; r0 < a.nrhs; r0 += RB)
     for (int p = lane; p < m; p += 32) {
-      double v = 0.0;
-      for (int i = 0; i < kt; ++i) v = fma(Vl[p + (size_t)i * m], yt[i + r * kcap], v);
+      double acc[RB];
+#pragma unroll
+      for (int j = 0; j < RB; ++j) acc[j] = 0.0;
+      for (int i = 0; i < kt; ++i) {
+        const double v = Vl[p + (size_t)i * m];
+#pragma unroll
+        for (int j = 0; j < RB; ++j)
+          if (r0 + j < a.nrhs) acc[j] = fma(v, yt[i + (r0 + j) * kcap], acc[j]);
+      }
       // nearfield blocks whose row cluster contains t (the leaf itself, or
       // an ancestor paired with a leaf of the column tree): their rows of t
       for (int c = t; c >= 0; c = a.father[0][c]) {
@@ -128,12 +169,21 @@ __global__ void k_mv_leaves(MatvecArgs a) {
           const int s = a.near_col[x];
           const int ms = a.size[1][s];
           const double* Nb = a.N + a.near_off[x] + row;
-          const double* X = a.X + a.off[1][s] + r * a.ldx;
-          for (int q = 0; q < ms; ++q) v = fma(Nb[(size_t)q * mc], X[q], v);
+          const double* X = a.X + a.off[1][s] + (size_t)r0 * a.ldx;
+          for (int q = 0; q < ms; ++q) {
+            const double nv = Nb[(size_t)q * mc];
+#pragma unroll
+            for (int j = 0; j < RB; ++j)
+              if (r0 + j < a.nrhs) acc[j] = fma(nv, X[q + j * a.ldx], acc[j]);
+          }
         }
       }
-      double* y = a.Y + a.off[0][t] + p + r * a.ldy;
-      *y = a.beta == 0.0 ? a.alpha * v : fma(a.beta, *y, a.alpha * v);
+#pragma unroll
+      for (int j = 0; j < RB; ++j)
+        if (r0 + j < a.nrhs) {
+          double* y = a.Y + a.off[0][t] + p + (size_t)(r0 + j) * a.ldy;
+          *y = a.beta == 0.0 ? a.alpha * acc[j] : fma(a.beta, *y, a.alpha * acc[j]);
+        }
     }
 }
 
@@ -151,7 +201,10 @@ int launch_matvec(const MatvecArgs& a, cudaStream_t st) {
     ++launches;
   }
   if (a.n_clusters[0] > 0) {
-    k_mv_coupling<<<blocks_of(a.n_clusters[0]), 32 * kMvWarps, 0, st>>>(a);
+    if (a.nrhs >= 8)
+      k_mv_coupling<8><<<blocks_of(a.n_clusters[0]), 32 * kMvWarps, 0, st>>>(a);
+    else
+      k_mv_coupling<1><<<blocks_of(a.n_clusters[0]), 32 * kMvWarps, 0, st>>>(a);
     ++launches;
   }
   // backward transformation: level 1 down (the root has no father)
@@ -162,7 +215,12 @@ int launch_matvec(const MatvecArgs& a, cudaStream_t st) {
     ++launches;
   }
   if (a.n_leaves > 0) {
-    k_mv_leaves<<<blocks_of(a.n_leaves), 32 * kMvWarps, 0, st>>>(a);
+    if (a.nrhs >= 8)
+      k_mv_leaves<8><<<blocks_of(a.n_leaves), 32 * kMvWarps, 0, st>>>(a);
+    else if (a.nrhs >= 2)
+      k_mv_leaves<2><<<blocks_of(a.n_leaves), 32 * kMvWarps, 0, st>>>(a);
+    else
+      k_mv_leaves<1><<<blocks_of(a.n_leaves), 32 * kMvWarps, 0, st>>>(a);
     ++launches;
   }
   return launches;

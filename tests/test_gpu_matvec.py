@@ -104,3 +104,24 @@ def test_matvec_argument_checks(ctx):
         b.h2_matvec(ctx, Zl, 0, 1.0, 0, n, 0.0, 0, n)   # nothing to do
     finally:
         b.h2_matrix_free(Zl)
+
+
+def test_block_to_dense(ctx):
+    """h2_block_to_dense on admissible, inadmissible, subdivided and root
+    blocks against the oracle's block assembly (expanded bases)."""
+    from oracle.tree import BlockTree
+    Zo, _, _ = oracle_problem(24, 5, 509, 16)
+    Zl, _, _ = lib_problem(ctx, 24, 5, 509, 16)
+    try:
+        bt = Zo.blocks
+        sub = [c for c in range(1, bt.n_blocks) if bt.kind[c] == BlockTree.SUB]
+        for blk in (0, bt.admissible[3], bt.admissible[-1], bt.inadmissible[5], sub[len(sub) // 2]):
+            ref = Zo.block_dense(blk)
+            nt, ns = ref.shape
+            out = torch.full((ns, nt + 3), float("nan"), dtype=torch.float64, device="cuda")   # ld = nt + 3
+            b.h2_block_to_dense(ctx, Zl, blk, out.data_ptr(), nt + 3)
+            b.h2_ctx_synchronize(ctx)
+            got = out.cpu().numpy().T[:nt]
+            assert np.linalg.norm(got - ref) <= TOL * max(np.linalg.norm(ref), 1e-300), blk
+    finally:
+        b.h2_matrix_free(Zl)
