@@ -1512,21 +1512,21 @@ k_fbasis(MatView M, const Item* __restrict__ items, int n, int u, int tc,
     if constexpr (!kGeneral) {
       if (i < K)
         for (int j = 0; j < kf; ++j) Fo[i + j * 32] = i < k ? Eg[i + (size_t)j * kcap] : 0.0;
-      return;
+    } else {
+      double z[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) z[j] = 0.0;
+      for (int q = 0; q < k; ++q) {
+        const double lq = (i < K && q >= i) ? T0[i + q * ldt] : 0.0;
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (j < kf) z[j] = fma(lq, T2[q + j * ldt], z[j]);
+      }
+      if (i < K)
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (j < kf) Fo[i + j * 32] = z[j];
     }
-    double z[32];
-#pragma unroll
-    for (int j = 0; j < 32; ++j) z[j] = 0.0;
-    for (int q = 0; q < k; ++q) {
-      const double lq = (i < K && q >= i) ? T0[i + q * ldt] : 0.0;
-#pragma unroll
-      for (int j = 0; j < 32; ++j)
-        if (j < kf) z[j] = fma(lq, T2[q + j * ldt], z[j]);
-    }
-    if (i < K)
-#pragma unroll
-      for (int j = 0; j < 32; ++j)
-        if (j < kf) Fo[i + j * 32] = z[j];
     return;
   }
   // new transfer matrix (K x Kf), lane = row
