@@ -299,6 +299,11 @@ h2_status h2_block_to_dense(h2_ctx* ctx, const h2_matrix* Z, int64_t block, doub
 h2_status h2_lowrank_update_sequence(h2_ctx* ctx, h2_matrix* Z, int64_t count, const int64_t* blocks,
                                      int u, const double* A, const double* B, double eps,
                                      int64_t* waves);
+/* The waves h2_lowrank_update_sequence would use (host only, no device
+ * work): wave[j] (host, count entries) = the wave of update j, n_waves
+ * (optional) = their number. */
+h2_status h2_sequence_waves(const h2_matrix* Z, int64_t count, const int64_t* blocks, int32_t* wave,
+                            int64_t* n_waves);
 /* One update applied to Z in place (sequential semantics; Section 5).
  * A (rows of block's row cluster x u, ld lda) and B (rows of column cluster
  * x u, ld ldb) are DEVICE pointers. */

@@ -32,6 +32,7 @@ EXPORTS = [
     "h2_batch_stats", "h2_batch_set_timing", "h2_batch_phase_stats", "h2_batch_item_info", "h2_batch_item_tile",
     "h2_batch_update_items", "h2_batch_set_mode", "h2_batch_paths", "h2_lowrank_update",
     "h2_lowrank_update_noalloc", "h2_lowrank_update_sequence", "h2_matvec", "h2_block_to_dense",
+    "h2_sequence_waves",
 ]
 
 PHASES = ("base_weights", "rfactor", "norms", "weights", "truncate", "reproject", "exact", "bases")
@@ -94,6 +95,7 @@ _sig("h2_batch_factor_sizes", _int, _p, _p, _p)
 _sig("h2_batch_execute", _int, _p, _p, _p, _p, _dbl)
 _sig("h2_batch_execute_host", _int, _p, _p, _p, _p, _dbl, _p)
 _sig("h2_batch_result_size", _int, _p, _p)
+_sig("h2_sequence_waves", _int, _p, _i64, _p, _p, _p)
 _sig("h2_block_to_dense", _int, _p, _p, _i64, _p, _i64)
 _sig("h2_matvec", _int, _p, _p, _i64, _dbl, _p, _i64, _dbl, _p, _i64)
 _sig("h2_lowrank_update_sequence", _int, _p, _p, _i64, _p, _int, _p, _p, _dbl, _p)
@@ -419,3 +421,12 @@ def h2_matvec(ctx, Z, nrhs: int, alpha: float, X_dev: int, ldx: int, beta: float
 def h2_block_to_dense(ctx, Z, block: int, out_dev: int, ld: int):
     """Z|_{t x s} of a block-tree node into a device array (column-major)."""
     _check(_lib.h2_block_to_dense(ctx, Z, int(block), C.c_void_p(out_dev), int(ld)), ctx)
+
+
+def h2_sequence_waves(Z, blocks):
+    """Waves of h2_lowrank_update_sequence for these blocks (host only)."""
+    bl = np.ascontiguousarray(blocks, dtype=np.int64)
+    wave = np.zeros(len(bl), np.int32)
+    n = C.c_int64()
+    _check(_lib.h2_sequence_waves(Z, len(bl), _ptr(bl), _ptr(wave), C.byref(n)))
+    return wave, n.value

@@ -2142,6 +2142,19 @@ int32_t sequence_waves(const h2_matrix* Z, int64_t count, const int64_t* blocks,
 }
 }  // namespace
 
+extern "C" h2_status h2_sequence_waves(const h2_matrix* Z, int64_t count, const int64_t* blocks, int32_t* wave,
+                                       int64_t* n_waves) {
+  if (!Z || count < 0 || (count > 0 && (!blocks || !wave))) return H2_EINVAL;
+  return guard(nullptr, [&] {
+    for (int64_t j = 0; j < count; ++j)
+      H2_REQUIRE(blocks[j] >= 0 && blocks[j] < Z->blocks.count(), "h2_sequence_waves: block id out of range");
+    std::vector<int32_t> wv;
+    const int32_t waves = sequence_waves(Z, count, blocks, wv);
+    std::copy(wv.begin(), wv.end(), wave);
+    if (n_waves) *n_waves = waves;
+  });
+}
+
 extern "C" h2_status h2_lowrank_update_sequence(h2_ctx* ctx, h2_matrix* Z, int64_t count, const int64_t* blocks,
                                                 int u, const double* A, const double* B, double eps,
                                                 int64_t* waves_out) {
