@@ -592,7 +592,7 @@ __global__ void k_bgram_down(MatView M, const int32_t* __restrict__ list, int n,
 // Entry e of the per-lane list is C_t[e % k][e / k] for e < k u, then the
 // lower triangle of N_t.  The V_t^* V_t block of G_t comes from k_vgram.
 template <int NS>
-__global__ void k_fgram(MatView M, const Item* __restrict__ items, const int32_t* __restrict__ list, int n, int u,
+__global__ void __launch_bounds__(128, 6) k_fgram(MatView M, const Item* __restrict__ items, const int32_t* __restrict__ list, int n, int u,
                         int tc, const double* __restrict__ A, const double* __restrict__ B, ItemBuffers IB,
                         int* err) {
   extern __shared__ double smem[];

@@ -1050,7 +1050,7 @@ __global__ void k_truncate(MatView M, const Item* __restrict__ items, const int3
 // the triangular sum.  Operands are staged in shared memory and the result
 // leaves through it in coalesced columns.  Updates of the exact path have a
 // general r_t x K_t factor and use one lane per column.
-constexpr int kRpLd = 33;   // leading dimension of the tiles (up to 32 rows); 3 tiles per warp of tc columns
+// k_reproject: 3 tiles per warp of tc columns and tc + 1 rows (at most 32 + 1)
 
 __device__ __forceinline__ void reproject_general(const MatView& M, const Item* __restrict__ items, const Task& tk,
                                                   int u, const ItemBuffers& IB, const double* S, double* out,
@@ -1118,9 +1118,10 @@ __device__ __forceinline__ void reproject_task(const MatView& M, const Item* __r
     reproject_general(M, items, tk, u, IB, S, out, lane);
     return;
   }
-  double* X = smem + (size_t)w * 3 * kRpLd * tc;   // S (k_t x l_s), later T
-  double* R = X + kRpLd * tc;                       // triangular factor
-  double* O = R + kRpLd * tc;                       // result
+  const int rld = tc + 1;                          // tiles of at most tc rows
+  double* X = smem + (size_t)w * 3 * rld * tc;      // S (k_t x l_s), later T
+  double* R = X + rld * tc;                         // triangular factor
+  double* O = R + rld * tc;                         // result
   int rows = 0, cols = 0;                    // size of the result
   if (tk.it >= 0 && tk.is >= 0) {
     const int kt = items[tk.it].k, ls = items[tk.is].k;
@@ -1128,10 +1129,10 @@ __device__ __forceinline__ void reproject_task(const MatView& M, const Item* __r
     rows = Kt;
     cols = Ks;
     for (int c = 0; c < ls; ++c)
-      if (lane < kt) X[lane + c * kRpLd] = S[lane + c * kcap];
+      if (lane < kt) X[lane + c * rld] = S[lane + c * kcap];
     const double* Rs = IB.Rt + (size_t)tk.is * kSlot;
     for (int c = 0; c < Ks; ++c)
-      if (lane <= c) R[lane + c * kRpLd] = Rs[lane + c * 32];
+      if (lane <= c) R[lane + c * rld] = Rs[lane + c * 32];
     __syncwarp();
     // T = S~ R_s^* (Kt x Ks), column-major over the lanes: rows i < kt sum
     // S[i][q] R_s[j][q] over q = j..ls-1; rows i >= kt pick R_s[j][ls + i - kt]
@@ -1139,26 +1140,26 @@ __device__ __forceinline__ void reproject_task(const MatView& M, const Item* __r
       const int i = e % Kt, j = e / Kt;
       double v = 0.0;
       if (i < kt) {
-        for (int q = j; q < ls; ++q) v = fma(X[i + q * kRpLd], R[j + q * kRpLd], v);
+        for (int q = j; q < ls; ++q) v = fma(X[i + q * rld], R[j + q * rld], v);
       } else {
         const int q = ls + i - kt;
-        v = q >= j ? R[j + q * kRpLd] : 0.0;
+        v = q >= j ? R[j + q * rld] : 0.0;
       }
-      O[i + j * kRpLd] = v;
+      O[i + j * rld] = v;
     }
     __syncwarp();
     const double* Rt = IB.Rt + (size_t)tk.it * kSlot;
     for (int c = 0; c < Kt; ++c)
-      if (lane <= c) R[lane + c * kRpLd] = Rt[lane + c * 32];
+      if (lane <= c) R[lane + c * rld] = Rt[lane + c * 32];
     for (int c = 0; c < Ks; ++c)
-      if (lane < Kt) X[lane + c * kRpLd] = O[lane + c * kRpLd];
+      if (lane < Kt) X[lane + c * rld] = O[lane + c * rld];
     __syncwarp();
     // out = R_t T, row-major over the lanes: sum over i = p..Kt-1
     for (int e = lane; e < Kt * Ks; e += 32) {
       const int p = e / Ks, j = e % Ks;
       double v = 0.0;
-      for (int i = p; i < Kt; ++i) v = fma(R[p + i * kRpLd], X[i + j * kRpLd], v);
-      O[p + j * kRpLd] = v;
+      for (int i = p; i < Kt; ++i) v = fma(R[p + i * rld], X[i + j * rld], v);
+      O[p + j * rld] = v;
     }
   } else if (tk.it >= 0) {
     // R_t [S_b; 0]: rows p < kt sum over i = p..kt-1, rows kt.. are zero;
@@ -1168,19 +1169,19 @@ __device__ __forceinline__ void reproject_task(const MatView& M, const Item* __r
     rows = kt + u;
     cols = ls;
     for (int c = 0; c < ls; ++c)
-      if (lane < kt) X[lane + c * kRpLd] = S[lane + c * kcap];
+      if (lane < kt) X[lane + c * rld] = S[lane + c * kcap];
     const double* Rt = IB.Rt + (size_t)tk.it * kSlot;
     for (int c = 0; c < kt; ++c)
-      if (lane <= c) R[lane + c * kRpLd] = Rt[lane + c * 32];
+      if (lane <= c) R[lane + c * rld] = Rt[lane + c * 32];
     __syncwarp();
     for (int e = lane; e < kt * ls; e += 32) {
       const int p = e / ls, j = e % ls;
       double v = 0.0;
-      for (int i = p; i < kt; ++i) v = fma(R[p + i * kRpLd], X[i + j * kRpLd], v);
-      O[p + j * kRpLd] = v;
+      for (int i = p; i < kt; ++i) v = fma(R[p + i * rld], X[i + j * rld], v);
+      O[p + j * rld] = v;
     }
     for (int c = 0; c < ls; ++c)
-      if (lane >= kt && lane < rows) O[lane + c * kRpLd] = 0.0;
+      if (lane >= kt && lane < rows) O[lane + c * rld] = 0.0;
   } else {
     // [S_b, 0] R_s^*: columns j < ls sum over q = j..ls-1, columns ls.. are
     // zero; [S_b, 0] for an orthonormal W_s
@@ -1189,23 +1190,23 @@ __device__ __forceinline__ void reproject_task(const MatView& M, const Item* __r
     rows = kt;
     cols = ls + u;
     for (int c = 0; c < ls; ++c)
-      if (lane < kt) X[lane + c * kRpLd] = S[lane + c * kcap];
+      if (lane < kt) X[lane + c * rld] = S[lane + c * kcap];
     const double* Rs = IB.Rt + (size_t)tk.is * kSlot;
     for (int c = 0; c < ls; ++c)
-      if (lane <= c) R[lane + c * kRpLd] = Rs[lane + c * 32];
+      if (lane <= c) R[lane + c * rld] = Rs[lane + c * 32];
     __syncwarp();
     for (int e = lane; e < kt * ls; e += 32) {
       const int p = e % kt, j = e / kt;
       double v = 0.0;
-      for (int q = j; q < ls; ++q) v = fma(X[p + q * kRpLd], R[j + q * kRpLd], v);
-      O[p + j * kRpLd] = v;
+      for (int q = j; q < ls; ++q) v = fma(X[p + q * rld], R[j + q * rld], v);
+      O[p + j * rld] = v;
     }
     for (int c = ls; c < cols; ++c)
-      if (lane < kt) O[lane + c * kRpLd] = 0.0;
+      if (lane < kt) O[lane + c * rld] = 0.0;
   }
   __syncwarp();
   for (int c = 0; c < cols; ++c)
-    if (lane < rows) out[lane + c * 32] = O[lane + c * kRpLd];
+    if (lane < rows) out[lane + c * 32] = O[lane + c * rld];
 }
 
 // The two-sided tasks (list from the host) and the one-sided tasks that
@@ -1482,12 +1483,12 @@ void run_pipeline(const Pipeline& P) {
     H2_CUDA(cudaGetDevice(&dev));
     if (dev >= 64 || !((attr >> dev) & 1ull)) {
       H2_CUDA(cudaFuncSetAttribute(k_reproject, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   kWarps * 3 * kRpLd * 32 * (int)sizeof(double)));
+                                   kWarps * 3 * 33 * 32 * (int)sizeof(double)));
       if (dev < 64) attr |= 1ull << dev;
     }
     // flag the copies, list the one-sided tasks that need products
     k_onesided<<<(P.n_tasks + 255) / 256, 256, 0, st>>>(P.items, P.tasks, P.n_tasks, P.BW, P.IB, P.left, P.n_left);
-    const size_t rp_smem = (size_t)kWarps * 3 * kRpLd * tc * sizeof(double);
+    const size_t rp_smem = (size_t)kWarps * 3 * (tc + 1) * tc * sizeof(double);
     k_reproject<<<persistent_blocks(k_reproject, 32 * kWarps, rp_smem, blocks_for(P.n_tasks)), 32 * kWarps, rp_smem,
                   st>>>(P.M, P.items, P.tasks, P.two, P.n_two, P.left, P.n_left, P.u, tc, P.BW, P.IB);
     pl[H2_PHASE_REPROJECT] += 2;
