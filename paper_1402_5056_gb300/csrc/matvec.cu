@@ -23,11 +23,8 @@ constexpr int kMvWarps = 4;
 
 __device__ __forceinline__ bool is_leaf(const int32_t* subtree, int c) { return subtree[c] == 1; }
 
-__global__ void k_mv_forward(MatvecArgs a, const int32_t* __restrict__ list, int n) {
-  const int w = blockIdx.x * kMvWarps + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (w >= n) return;
-  const int c = list[w];
+// xh_c of one column cluster (one warp)
+__device__ __forceinline__ void forward_cluster(const MatvecArgs& a, int c, int lane) {
   const int kc = a.rank[1][c];
   const int kcap = a.kcap;
   double* out = a.xh + (size_t)c * kcap * a.nrhs;
@@ -58,6 +55,12 @@ __global__ void k_mv_forward(MatvecArgs a, const int32_t* __restrict__ list, int
       out[i + r * kcap] = v;
     }
   }
+}
+
+__global__ void k_mv_forward(MatvecArgs a, const int32_t* __restrict__ list, int n) {
+  const int w = blockIdx.x * kMvWarps + (threadIdx.x >> 5);
+  if (w >= n) return;
+  forward_cluster(a, list[w], threadIdx.x & 31);
 }
 
 // Coupling: lane = (row i of yh_t, group g); the groups split the
@@ -115,11 +118,8 @@ __global__ void k_mv_coupling(MatvecArgs a) {
   }
 }
 
-__global__ void k_mv_backward(MatvecArgs a, const int32_t* __restrict__ list, int n) {
-  const int w = blockIdx.x * kMvWarps + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (w >= n) return;
-  const int c = list[w];
+// yh_c += E_c yh_{c+} for one row cluster (one warp)
+__device__ __forceinline__ void backward_cluster(const MatvecArgs& a, int c, int lane) {
   const int f = a.father[0][c];
   if (f < 0) return;
   const int kc = a.rank[0][c], kf = a.rank[0][f];
@@ -133,6 +133,41 @@ __global__ void k_mv_backward(MatvecArgs a, const int32_t* __restrict__ list, in
     double v = yc[i + r * kcap];
     for (int q = 0; q < kf; ++q) v = fma(E[i + q * kcap], yf[q + r * kcap], v);
     yc[i + r * kcap] = v;
+  }
+}
+
+__global__ void k_mv_backward(MatvecArgs a, const int32_t* __restrict__ list, int n) {
+  const int w = blockIdx.x * kMvWarps + (threadIdx.x >> 5);
+  if (w >= n) return;
+  backward_cluster(a, list[w], threadIdx.x & 31);
+}
+
+// The levels of a tree that hold few clusters, in one block: level after
+// level (the order of `lev`), a barrier between levels.  A launch per level
+// would cost more than their work.
+constexpr int kTopWarps = 32;
+constexpr int kTopMax = 2 * kTopWarps;   // clusters x right-hand sides per level handled this way
+struct TopLevels {
+  int n;             // levels
+  int first[17];     // offsets into the level list, n + 1 entries, in processing order
+  int count[16];
+};
+
+template <bool kForward>
+__global__ void __launch_bounds__(32 * kTopWarps) k_mv_top(MatvecArgs a, const int32_t* __restrict__ list,
+                                                             TopLevels t) {
+  const int w = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  for (int l = 0; l < t.n; ++l) {
+    const int32_t* lv = list + t.first[l];
+    const int n = t.count[l];
+    for (int x = w; x < n; x += kTopWarps) {
+      if constexpr (kForward)
+        forward_cluster(a, lv[x], lane);
+      else
+        backward_cluster(a, lv[x], lane);
+    }
+    __syncthreads();
   }
 }
 
@@ -193,11 +228,32 @@ int blocks_of(int n) { return (n + kMvWarps - 1) / kMvWarps; }
 
 int launch_matvec(const MatvecArgs& a, cudaStream_t st) {
   int launches = 0;
-  // forward transformation: deepest level first
-  for (int l = a.levels[1] - 1; l >= 0; --l) {
+  // levels [0, top) of a tree whose work is small (clusters x right-hand
+  // sides at most kTopMax, at most 16 levels) go into one block
+  const auto top_of = [&](int sd) {
+    int top = 0;
+    while (top < a.levels[sd] && top < 16 &&
+           (int64_t)(a.lvl_ptr[sd][top + 1] - a.lvl_ptr[sd][top]) * a.nrhs <= kTopMax)
+      ++top;
+    return top;
+  };
+  // forward transformation: deepest level first, the upper levels in one block
+  const int top1 = top_of(1);
+  for (int l = a.levels[1] - 1; l >= top1; --l) {
     const int n = a.lvl_ptr[1][l + 1] - a.lvl_ptr[1][l];
     if (n <= 0) continue;
     k_mv_forward<<<blocks_of(n), 32 * kMvWarps, 0, st>>>(a, a.lvl_list[1] + a.lvl_ptr[1][l], n);
+    ++launches;
+  }
+  if (top1 > 0) {
+    TopLevels t{};
+    t.n = top1;
+    for (int i = 0; i < top1; ++i) {   // levels top1 - 1, ..., 0
+      const int l = top1 - 1 - i;
+      t.first[i] = a.lvl_ptr[1][l];
+      t.count[i] = a.lvl_ptr[1][l + 1] - a.lvl_ptr[1][l];
+    }
+    k_mv_top<true><<<1, 32 * kTopWarps, 0, st>>>(a, a.lvl_list[1], t);
     ++launches;
   }
   if (a.n_clusters[0] > 0) {
@@ -207,8 +263,20 @@ int launch_matvec(const MatvecArgs& a, cudaStream_t st) {
       k_mv_coupling<1><<<blocks_of(a.n_clusters[0]), 32 * kMvWarps, 0, st>>>(a);
     ++launches;
   }
-  // backward transformation: level 1 down (the root has no father)
-  for (int l = 1; l < a.levels[0]; ++l) {
+  // backward transformation: level 1 down (the root has no father), the
+  // upper levels in one block
+  const int top0 = top_of(0);
+  if (top0 > 1) {
+    TopLevels t{};
+    t.n = top0 - 1;
+    for (int i = 0; i < top0 - 1; ++i) {   // levels 1, ..., top0 - 1
+      t.first[i] = a.lvl_ptr[0][i + 1];
+      t.count[i] = a.lvl_ptr[0][i + 2] - a.lvl_ptr[0][i + 1];
+    }
+    k_mv_top<false><<<1, 32 * kTopWarps, 0, st>>>(a, a.lvl_list[0], t);
+    ++launches;
+  }
+  for (int l = top0 > 1 ? top0 : 1; l < a.levels[0]; ++l) {
     const int n = a.lvl_ptr[0][l + 1] - a.lvl_ptr[0][l];
     if (n <= 0) continue;
     k_mv_backward<<<blocks_of(n), 32 * kMvWarps, 0, st>>>(a, a.lvl_list[0] + a.lvl_ptr[0][l], n);
