@@ -264,8 +264,8 @@ h2_status h2_batch_update_items(const h2_batch* batch, int64_t j, int64_t* first
 
 /* Y <- alpha Z X + beta Y for nrhs right-hand sides (Section 2: Eq. (vsw)
  * on the admissible leaves with the nested bases of Eq. (nested), dense
- * inadmissible leaves; the product the multiplication of Section 6 applies
- * in its Case 2).  X (n_cols x nrhs, ld ldx) and Y (n_rows x nrhs, ld ldy)
+ * inadmissible leaves; the product the multiplication of Section 3 applies
+ * where a factor block is a leaf, Section 6 Case 2).  X (n_cols x nrhs, ld ldx) and Y (n_rows x nrhs, ld ldy)
  * are column-major DEVICE arrays with rows in TREE order
  * (h2_tree_permutation); they must not overlap; Y is not read when
  * beta = 0.  Forward transformation over the column tree, the couplings,

@@ -14,9 +14,9 @@ cluster:
    for every son t' of t, and Y|_t += V_t yh_t at the leaves;
 4. nearfield: Y|_t += N_b X|_s for the inadmissible leaves b = (t, s).
 
-The multiplication of Section 6 uses this product (its Case 2 forms
-X|_{t x s} V_s by k products with an H^2-matrix).  Plain numpy, cluster by
-cluster; it shares no code with the CUDA library.
+The multiplication (Section 3) uses this product where one factor block is
+a leaf: X|_{t x s} V_s is formed by k such products (Section 6, Case 2).
+Plain numpy, cluster by cluster; it shares no code with the CUDA library.
 """
 from __future__ import annotations
 

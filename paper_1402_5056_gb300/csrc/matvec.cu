@@ -1,6 +1,7 @@
 // H^2-matrix times a block of vectors (Section 2: Eq. (vsw) for the
 // admissible leaves, dense inadmissible leaves, nested bases Eq. (nested)),
-// the product the multiplication of Section 6 applies in its Case 2.
+// the product the multiplication of Section 3 applies where a factor block
+// is a leaf (Section 6, Case 2: X|_{t x s} V_s by k such products).
 //
 //   forward transformation, bottom-up over the column tree:
 //     xh_s = W_s^* X|_s (leaf), xh_s = sum over sons E_{s'}^* xh_{s'};
