@@ -13,6 +13,8 @@ low-rank updates" (arXiv:1402.5056):
   Z|_{t0 x s0} <- trunc_eps(Z|_{t0 x s0} + A B^*) of Section 5, built from
   the recompression of Section 4 (Eq. (tildeZ_h2), the weight matrices,
   Eqs. (Qt_condensed), (Qt_nested), (hatQt_condensed)).
+* ``oracle.matvec`` -- the H^2 matrix times a block of vectors (forward and
+  backward transformations through the nested bases, Section 2).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
 ``--impl reference`` legs of ``bench.py`` may import this package.  It shares
