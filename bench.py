@@ -440,7 +440,7 @@ def main():
     # end to end through the C ABI from pinned host buffers (no phase events:
     # recorded inside the replayed graph they keep its copies from
     # overlapping the kernels)
-    e2e = None
+    e2e = e2e_compact = None
     if args.e2e_steps > 0:
         b.h2_batch_set_timing(P, False)
         pA = torch.from_numpy(Acat).pin_memory()
@@ -455,8 +455,26 @@ def main():
             t0 = time.perf_counter()
             b.h2_batch_execute_host(ctx, P, pA.numpy(), pB.numpy(), w["eps"], res.numpy())
             ts.append(time.perf_counter() - t0)
+        h2d, d2h = b.h2_batch_host_bytes(P)
         e2e = {"value": len(blocks) / (sum(ts) / len(ts)), "unit": UNIT,
-               "h2d_bytes_per_step": 8 * (lenA + lenB), "d2h_bytes_per_step": 8 * int(res.numel())}
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+        # the compact result: couplings the updates keep ([S_b; 0], [S_b, 0]
+        # of the unchanged matrix) are flagged instead of copied
+        copied = np.zeros(stats["block_tasks"], np.int8)
+        for _ in range(3):
+            b.h2_batch_execute_host_compact(ctx, P, pA.numpy(), pB.numpy(), w["eps"], res.numpy(), copied)
+        ts = []
+        for _ in range(args.e2e_steps):
+            flush.fill_(7)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            b.h2_batch_execute_host_compact(ctx, P, pA.numpy(), pB.numpy(), w["eps"], res.numpy(), copied)
+            ts.append(time.perf_counter() - t0)
+        h2d, d2h = b.h2_batch_host_bytes(P)
+        e2e_compact = {"value": len(blocks) / (sum(ts) / len(ts)), "unit": UNIT,
+                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                       "kept_couplings": int(copied.sum()),
+                       "result": "compact: kept couplings flagged, read from the unchanged matrix"}
 
     # H2 matrix times vectors on the same matrix (h2_matvec): one vector
     # (bound by HBM: every value of the matrix read once) and k = 16 vectors
@@ -479,7 +497,7 @@ def main():
                        "l2": "512 MB buffer written between timed steps",
                        "updates": len(blocks), "cluster_tasks": stats["cluster_tasks"],
                        "block_tasks": stats["block_tasks"], "exact_path_updates": n_exact},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "e2e_compact": e2e_compact,
             "gpu_launches": stats["launches"] * args.steps,
             "clocks": clocks, "phases": phases, "phases_serial": phases_serial, "exact_mode": exact_mode,
             "matvec": mv,

@@ -162,6 +162,25 @@ h2_status h2_batch_execute(h2_ctx* ctx, h2_batch* batch, const double* A, const 
  * the update runs. */
 h2_status h2_batch_execute_host(h2_ctx* ctx, h2_batch* batch, const double* A_host,
                                 const double* B_host, double eps, double* result);
+/* Same with a compact result: copied[b] (one byte per block task, host
+ * array of n_block_tasks entries) is set to 1 where the update keeps the
+ * coupling -- the new coupling of block task b is the unchanged S_b of the
+ * planned matrix padded with zero rows ([S_b; 0], row cluster changed) or
+ * zero columns ([S_b, 0]), which happens for the one-sided blocks of a
+ * certified update whose changed cluster keeps its orthonormal basis as the
+ * leading part of the new one (Section 5 with the block form of the Gram
+ * path) -- and to 0 elsewhere.  With a page-locked `result` those pieces are
+ * not copied to the host (their contents in `result` are unspecified; read
+ * S_b from the planned matrix, h2_get_coupling); every other piece is as in
+ * h2_batch_execute_host.  With a pageable `result` every piece is written.
+ * copied may be NULL only for a batch without block tasks. */
+h2_status h2_batch_execute_host_compact(h2_ctx* ctx, h2_batch* batch, const double* A_host,
+                                        const double* B_host, double eps, double* result,
+                                        int8_t* copied);
+/* Bytes the last h2_batch_execute_host(_compact) copied host -> device (the
+ * factors) and device -> host (result pieces, chunk flags, pieces sent
+ * again, copy flags). */
+h2_status h2_batch_host_bytes(const h2_batch* batch, int64_t* h2d, int64_t* d2h);
 h2_status h2_batch_result_size(const h2_batch* batch, int64_t* len);
 /* Layout of that result (host arrays of n_cluster_tasks and n_block_tasks
  * entries, h2_batch_stats).  result[i] = new rank r_i of cluster task i

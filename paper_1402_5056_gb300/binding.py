@@ -27,8 +27,9 @@ EXPORTS = [
     "h2_get_basis", "h2_get_couplings", "h2_get_nearfield", "h2_get_leaf", "h2_get_transfer",
     "h2_get_coupling",
     "h2_batch_create", "h2_batch_free", "h2_batch_factor_layout", "h2_batch_factor_sizes",
-    "h2_batch_execute", "h2_batch_execute_host", "h2_batch_result_size", "h2_batch_result_offsets",
-    "h2_batch_task_info", "h2_batch_apply",
+    "h2_batch_execute", "h2_batch_execute_host", "h2_batch_execute_host_compact", "h2_batch_host_bytes",
+    "h2_batch_result_size",
+    "h2_batch_result_offsets", "h2_batch_task_info", "h2_batch_apply",
     "h2_batch_stats", "h2_batch_set_timing", "h2_batch_phase_stats", "h2_batch_item_info", "h2_batch_item_tile",
     "h2_batch_update_items", "h2_batch_set_mode", "h2_batch_paths", "h2_lowrank_update",
     "h2_lowrank_update_noalloc", "h2_lowrank_update_sequence", "h2_matvec", "h2_block_to_dense",
@@ -94,6 +95,8 @@ _sig("h2_batch_factor_layout", _int, _p, _i64, _p, _p, _p, _p)
 _sig("h2_batch_factor_sizes", _int, _p, _p, _p)
 _sig("h2_batch_execute", _int, _p, _p, _p, _p, _dbl)
 _sig("h2_batch_execute_host", _int, _p, _p, _p, _p, _dbl, _p)
+_sig("h2_batch_execute_host_compact", _int, _p, _p, _p, _p, _dbl, _p, _p)
+_sig("h2_batch_host_bytes", _int, _p, _p, _p)
 _sig("h2_batch_result_size", _int, _p, _p)
 _sig("h2_sequence_waves", _int, _p, _i64, _p, _p, _p)
 _sig("h2_block_to_dense", _int, _p, _p, _i64, _p, _i64)
@@ -311,6 +314,26 @@ def h2_batch_execute_host(ctx, P, A_host, B_host, eps: float, result=None):
     _check(_lib.h2_batch_execute_host(ctx, P, _ptr(_f64(A_host)), _ptr(_f64(B_host)), float(eps),
                                       _ptr(result)), ctx)
     return result
+
+
+def h2_batch_execute_host_compact(ctx, P, A_host, B_host, eps: float, result=None, copied=None):
+    """Compact host result: (result, copied); copied[b] = 1 where block task
+    b keeps its coupling padded with zeros (its piece is then unspecified
+    when `result` is page-locked)."""
+    if result is None:
+        result = np.zeros(h2_batch_result_size(P))
+    if copied is None:
+        copied = np.zeros(h2_batch_stats(None, P, flops=False)["block_tasks"], np.int8)
+    _check(_lib.h2_batch_execute_host_compact(ctx, P, _ptr(_f64(A_host)), _ptr(_f64(B_host)), float(eps),
+                                              _ptr(result), _ptr(copied)), ctx)
+    return result, copied
+
+
+def h2_batch_host_bytes(P):
+    """(h2d, d2h): bytes the last host execution copied each way."""
+    a, c = C.c_int64(), C.c_int64()
+    _check(_lib.h2_batch_host_bytes(P, C.byref(a), C.byref(c)))
+    return a.value, c.value
 
 
 def h2_batch_apply(ctx, P, j: int, A_dev: int, B_dev: int, dst):

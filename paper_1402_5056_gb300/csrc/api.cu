@@ -713,6 +713,9 @@ struct h2_batch {
   int32_t* d_chunk_of = nullptr;
   int32_t* d_flags = nullptr;                   // per chunk: re-packed after the early copy
   int32_t* h_flags = nullptr;                   // page-locked copy of d_flags
+  int8_t* h_copy = nullptr;                     // page-locked copy of the copy flags (compact result)
+  bool compact = false;                         // this execution writes the compact host result
+  int64_t h2d_bytes = 0, d2h_bytes = 0;         // copies of the last host execution
   cudaStream_t io = nullptr;                    // stream of the early copies
   HostOutput out{};
   double* g_res = nullptr;                      // host destination the graph copies to
@@ -752,6 +755,7 @@ struct h2_batch {
   double g_eps = -1.0;
   int g_mode = -1;
   int g_timing = 0;
+  bool g_compact = false;
   int g_repeats = 0;
   bool g_broken = false;                     // capture failed once: stay eager
   MatView g_view{};                          // the matrix storage the graph reads
@@ -1074,6 +1078,11 @@ int pack_blocks(int64_t n) { return (int)((n + kPackWarps - 1) / kPackWarps); }
 void early_output(const Pipeline& pp, const HostOutput& O, cudaStream_t st) {
   h2_batch& P = *static_cast<h2_batch*>(O.owner);
   const int n_one = (int)P.one.size();
+  if (P.compact) {
+    // the couplings that turn out copies stay on the device: nothing to send early
+    H2_CUDA(cudaEventRecord(O.packed, st));
+    return;
+  }
   if (n_one > 0)
     k_pack_early<<<pack_blocks(n_one), 32 * kPackWarps, 0, st>>>(pp.M, pp.items, pp.tasks, P.d_one, n_one, pp.u,
                                                                   pp.BW, P.d_res_task_off, P.d_res);
@@ -1105,6 +1114,8 @@ void late_output(const Pipeline& pp, const HostOutput& O, cudaStream_t st, bool 
   } else if (nch > 0) {
     H2_CUDA(cudaMemcpyAsync(P.h_flags, P.d_flags, nch * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   }
+  if (P.compact && !P.tasks.empty())
+    H2_CUDA(cudaMemcpyAsync(P.h_copy, pp.IB.copy, P.tasks.size() * sizeof(int8_t), cudaMemcpyDeviceToHost, st));
 }
 
 // Buffers of the host result (first h2_batch_execute_host).
@@ -1118,6 +1129,7 @@ void alloc_result(h2_batch& P, cudaStream_t st) {
   const size_t nch = P.res_chunk_off.size() - 1;
   P.d_flags = dalloc<int32_t>(nch);
   if (nch) H2_CUDA(cudaHostAlloc(&P.h_flags, nch * sizeof(int32_t), cudaHostAllocDefault));
+  if (!P.tasks.empty()) H2_CUDA(cudaHostAlloc(&P.h_copy, P.tasks.size() * sizeof(int8_t), cudaHostAllocDefault));
   // the early copies' pack kernel runs beside the update's kernels: give its
   // stream the highest priority so that its blocks do not wait for theirs
   int lo = 0, hi = 0;
@@ -1199,6 +1211,8 @@ void free_batch_device(h2_batch& P) {
   }
   if (P.h_flags) cudaFreeHost(P.h_flags);
   P.h_flags = nullptr;
+  if (P.h_copy) cudaFreeHost(P.h_copy);
+  P.h_copy = nullptr;
   dfree(P.d_one);
   dfree(P.d_chunk_of);
   dfree(P.d_flags);
@@ -1317,7 +1331,8 @@ void execute(h2_ctx* ctx, h2_batch& P, const double* A, const double* B, double 
   // rank capacity grows, and the context's error word)
   pp.out = h_res ? &P.out : nullptr;
   const bool same = A == P.g_A && B == P.g_B && eps == P.g_eps && P.mode == P.g_mode && P.timing == P.g_timing &&
-                    ctx == P.g_ctx && same_view(pp.M, P.g_view) && h_res == P.g_res;
+                    ctx == P.g_ctx && same_view(pp.M, P.g_view) && h_res == P.g_res &&
+                    P.compact == P.g_compact;
   if (!same) {
     P.g_res = h_res;
     P.g_view = pp.M;
@@ -1329,6 +1344,7 @@ void execute(h2_ctx* ctx, h2_batch& P, const double* A, const double* B, double 
     P.g_eps = eps;
     P.g_mode = P.mode;
     P.g_timing = P.timing;
+    P.g_compact = P.compact;
     P.g_repeats = 0;
   } else {
     ++P.g_repeats;
@@ -1449,6 +1465,7 @@ extern "C" h2_status h2_batch_execute(h2_ctx* ctx, h2_batch* P, const double* A,
     H2_REQUIRE((A || P->lenA == 0) && (B || P->lenB == 0), "h2_batch_execute: factors missing");
     H2_REQUIRE(std::isfinite(eps) && eps >= 0, "h2_batch_execute: eps must be finite and >= 0");
     DeviceGuard g(ctx->device);
+    P->compact = false;
     execute(ctx, *P, A, B, eps);
   });
 }
@@ -1479,13 +1496,18 @@ extern "C" h2_status h2_batch_task_info(const h2_batch* P, int64_t task, int32_t
   return H2_OK;
 }
 
-extern "C" h2_status h2_batch_execute_host(h2_ctx* ctx, h2_batch* P, const double* A_host, const double* B_host,
-                                           double eps, double* result) {
+// Both host-result entry points; copied == nullptr: the full result.
+static h2_status execute_host(h2_ctx* ctx, h2_batch* P, const double* A_host, const double* B_host, double eps,
+                              double* result, int8_t* copied) {
   if (!ctx || !P || !result) return H2_EINVAL;
   return guard(ctx, [&] {
     H2_REQUIRE((A_host || P->lenA == 0) && (B_host || P->lenB == 0), "h2_batch_execute_host: factors missing");
     H2_REQUIRE(std::isfinite(eps) && eps >= 0, "h2_batch_execute_host: eps must be finite and >= 0");
     DeviceGuard g(ctx->device);
+    P->compact = copied != nullptr;
+    const int64_t n_tasks = (int64_t)P->tasks.size();
+    P->h2d_bytes = (P->lenA + P->lenB) * (int64_t)sizeof(double);
+    P->d2h_bytes = copied ? n_tasks : 0;
     cudaStream_t st = ctx->stream;
     if (!P->d_A && P->lenA) P->d_A = dalloc<double>(P->lenA);
     if (!P->d_B && P->lenB) P->d_B = dalloc<double>(P->lenB);
@@ -1500,20 +1522,27 @@ extern "C" h2_status h2_batch_execute_host(h2_ctx* ctx, h2_batch* P, const doubl
     (void)cudaGetLastError();
     if (pinned) {
       execute(ctx, *P, P->d_A, P->d_B, eps, result);
-      P->launches += P->mode != H2_MODE_EXACT ? 2 : 1;
+      P->launches += (P->mode != H2_MODE_EXACT && !P->compact) ? 2 : 1;   // the pack kernels
       H2_CUDA(cudaStreamSynchronize(st));
       check_device_error(ctx);
       if (P->mode != H2_MODE_EXACT) {
         // chunks of the early region that the late pass packed again
+        const int64_t nch = (int64_t)P->res_chunk_off.size() - 1;
+        P->d2h_bytes += nch * (int64_t)sizeof(int32_t) +
+                        (P->compact ? P->res_prefix : P->res_len) * (int64_t)sizeof(double);
         bool again = false;
-        for (size_t c = 0; c + 1 < P->res_chunk_off.size(); ++c) {
+        for (int64_t c = 0; c < nch; ++c) {
           if (!P->h_flags[c]) continue;
           const int64_t a = P->res_chunk_off[c], b = P->res_chunk_off[c + 1];
           H2_CUDA(cudaMemcpyAsync(result + a, P->d_res + a, (b - a) * sizeof(double), cudaMemcpyDeviceToHost, st));
+          P->d2h_bytes += (b - a) * (int64_t)sizeof(double);
           again = true;
         }
         if (again) H2_CUDA(cudaStreamSynchronize(st));
+      } else {
+        P->d2h_bytes += P->res_len * (int64_t)sizeof(double);
       }
+      if (copied && !P->tasks.empty()) std::memcpy(copied, P->h_copy, P->tasks.size() * sizeof(int8_t));
     } else {
       execute(ctx, *P, P->d_A, P->d_B, eps);
       const int64_t n = (int64_t)P->tasks.size() + (int64_t)P->items.size();
@@ -1527,10 +1556,34 @@ extern "C" h2_status h2_batch_execute_host(h2_ctx* ctx, h2_batch* P, const doubl
       }
       if (P->res_len)
         H2_CUDA(cudaMemcpyAsync(result, P->d_res, P->res_len * sizeof(double), cudaMemcpyDeviceToHost, st));
+      P->d2h_bytes += P->res_len * (int64_t)sizeof(double);
+      // a pageable destination receives every piece; the flags say which
+      // pieces are copies all the same
+      if (copied && !P->tasks.empty())
+        H2_CUDA(cudaMemcpyAsync(copied, P->IB.copy, P->tasks.size() * sizeof(int8_t), cudaMemcpyDeviceToHost, st));
       H2_CUDA(cudaStreamSynchronize(st));
     }
     check_device_error(ctx);
   });
+}
+
+extern "C" h2_status h2_batch_execute_host(h2_ctx* ctx, h2_batch* P, const double* A_host, const double* B_host,
+                                           double eps, double* result) {
+  return execute_host(ctx, P, A_host, B_host, eps, result, nullptr);
+}
+
+extern "C" h2_status h2_batch_host_bytes(const h2_batch* P, int64_t* h2d, int64_t* d2h) {
+  if (!P || !h2d || !d2h) return H2_EINVAL;
+  *h2d = P->h2d_bytes;
+  *d2h = P->d2h_bytes;
+  return H2_OK;
+}
+
+extern "C" h2_status h2_batch_execute_host_compact(h2_ctx* ctx, h2_batch* P, const double* A_host,
+                                                   const double* B_host, double eps, double* result, int8_t* copied) {
+  if (!copied && P && !P->tasks.empty()) return H2_EINVAL;
+  static int8_t none = 0;   // a batch without coupling tasks needs no flags
+  return execute_host(ctx, P, A_host, B_host, eps, result, copied ? copied : &none);
 }
 
 extern "C" h2_status h2_batch_apply(h2_ctx* ctx, const h2_batch* P, int64_t j, const double* A, const double* B,

@@ -7,6 +7,10 @@ included) and a pageable one give the same bytes.  Cases: certified updates
 (one-sided couplings copied early), truncating updates (their early copies
 are packed again and re-sent), the exact path for everything, and bases that
 are not orthonormal (no early copies for their clusters).
+
+The compact result (h2_batch_execute_host_compact) must flag exactly the
+one-sided couplings that are the unchanged S_b padded with zeros and give
+every other piece the same bytes as the full result.
 """
 import numpy as np
 import pytest
@@ -82,6 +86,25 @@ def _decode_check(ctx, P, Zl, n_updates, res, dA, dB, u):
     return pieces
 
 
+def _check_compact(ctx, P, Zl, u, full, compact, copied):
+    """Pieces outside the flagged couplings: the bytes of the full result;
+    flagged couplings: one-sided, and in the full result the unchanged
+    coupling padded with zeros."""
+    _, to = b.h2_batch_result_offsets(P)
+    keep = np.ones(len(full), bool)
+    for t in np.flatnonzero(copied):
+        ti = b.h2_batch_task_info(P, int(t))
+        assert ti["row_item"] < 0 or ti["col_item"] < 0
+        R = ti["kt"] + (u if ti["row_item"] >= 0 else 0)
+        Cn = ti["ls"] + (u if ti["col_item"] >= 0 else 0)
+        piece = full[int(to[t]):int(to[t]) + R * Cn].reshape((R, Cn), order="F")
+        pad = np.zeros((R, Cn))
+        pad[:ti["kt"], :ti["ls"]] = b.h2_get_coupling(ctx, Zl, ti["block"], ti["kt"], ti["ls"])
+        np.testing.assert_array_equal(piece, pad)
+        keep[int(to[t]):int(to[t]) + R * Cn] = False
+    np.testing.assert_array_equal(compact[keep], full[keep])
+
+
 def _run(ctx, Zl, blocks, A, B, u, eps, mode):
     P = b.h2_batch_create(ctx, Zl, blocks, u)
     try:
@@ -99,13 +122,28 @@ def _run(ctx, Zl, blocks, A, B, u, eps, mode):
         pageable = b.h2_batch_execute_host(ctx, P, Acat, Bcat, eps)
         for r in runs:
             np.testing.assert_array_equal(r, pageable)
+        flags = []
+        for _ in range(3):            # compact: eager, captured, replayed
+            pinned[:] = np.nan
+            _, copied = b.h2_batch_execute_host_compact(ctx, P, pa, pb, eps, pinned)
+            _check_compact(ctx, P, Zl, u, pageable, pinned, copied)
+            flags.append(copied)
+        res_pg, copied_pg = b.h2_batch_execute_host_compact(ctx, P, Acat, Bcat, eps)
+        np.testing.assert_array_equal(res_pg, pageable)
+        for f in flags:
+            np.testing.assert_array_equal(f, copied_pg)
+        pinned[:] = np.nan            # and back to the full result
+        b.h2_batch_execute_host(ctx, P, pa, pb, eps, pinned)
+        np.testing.assert_array_equal(pinned, pageable)
+        if mode == b.MODE_EXACT:
+            assert copied_pg.sum() == 0
         paths = b.h2_batch_paths(ctx, P, len(blocks))
         dA = torch.from_numpy(Acat).cuda()
         dB = torch.from_numpy(Bcat).cuda()
         b.h2_batch_execute(ctx, P, dA.data_ptr(), dB.data_ptr(), eps)
         b.h2_ctx_synchronize(ctx)
         pieces = _decode_check(ctx, P, Zl, len(blocks), pageable, dA, dB, u)
-        return paths, pieces
+        return paths, pieces, int(copied_pg.sum())
     finally:
         b.h2_batch_free(P)
 
@@ -118,11 +156,11 @@ def test_host_result_pieces(ctx, eps, mode, exact):
     Zl, _, _ = lib_problem(ctx, N, k, 401, leaf)
     try:
         blocks, A, B = draw_updates(Zo, st, 6, u)
-        paths, pieces = _run(ctx, Zl, blocks, A, B, u, eps, mode)
+        paths, pieces, n_copied = _run(ctx, Zl, blocks, A, B, u, eps, mode)
         if exact:
             assert paths.sum() >= 1
         else:
-            assert paths.sum() == 0
+            assert paths.sum() == 0 and n_copied > 0
         assert pieces > 6
     finally:
         b.h2_matrix_free(Zl)
@@ -151,7 +189,7 @@ def test_host_result_non_orthonormal_bases(ctx):
         blocks = above[:4]
         A = [rng.standard_normal((tree.size[bt.row[c]], u)) for c in blocks]
         B = [rng.standard_normal((Zo.W.tree.size[bt.col[c]], u)) for c in blocks]
-        paths, pieces = _run(ctx, Zl, blocks, A, B, u, 1e-8, b.MODE_AUTO)
+        paths, pieces, _ = _run(ctx, Zl, blocks, A, B, u, 1e-8, b.MODE_AUTO)
         assert pieces > 4
     finally:
         b.h2_matrix_free(Zl)
