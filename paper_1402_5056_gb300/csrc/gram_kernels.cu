@@ -1612,16 +1612,6 @@ int slots_for(int entries) {
 
 int blocks_for(int n) { return (n + kWarps - 1) / kWarps; }
 
-// Raise the dynamic shared memory limit of a kernel once per device.
-template <class Kern>
-void smem_limit(Kern kern, size_t bytes, unsigned long long& done) {
-  int dev = 0;
-  H2_CUDA(cudaGetDevice(&dev));
-  if (dev < 64 && (done >> dev) & 1ull) return;
-  H2_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-  if (dev < 64) done |= 1ull << dev;
-}
-
 // Columns of the shared tiles: the largest extended rank of the batch or the
 // largest rank of the matrix (fathers of the subtree roots).
 int tile_cols(const Pipeline& P) { return P.kl > P.M.kcap ? P.kl : P.M.kcap; }
@@ -1633,7 +1623,7 @@ size_t tiles_bytes(int ntiles, int cols, int extra) {
 }  // namespace
 
 void launch_gram_orth(const Pipeline& P, cudaStream_t st) {
-  static unsigned long long done = 0;
+  static std::atomic<unsigned long long> done{0};
   const int n = P.cl_ptr[P.levels];
   if (n <= 0) return;
   smem_limit(k_orth_local, tiles_bytes(1, 32, 0), done);
@@ -1642,7 +1632,7 @@ void launch_gram_orth(const Pipeline& P, cudaStream_t st) {
 }
 
 void launch_gram_vbasis_level(const Pipeline& P, int level, cudaStream_t st) {
-  static unsigned long long done = 0;
+  static std::atomic<unsigned long long> done{0};
   const int n = P.cl_ptr[level + 1] - P.cl_ptr[level];
   if (n <= 0) return;
   smem_limit(k_vgram, tiles_bytes(3, 32, 0), done);
@@ -1651,7 +1641,7 @@ void launch_gram_vbasis_level(const Pipeline& P, int level, cudaStream_t st) {
 }
 
 void launch_gram_base(const Pipeline& P, cudaStream_t st) {
-  static unsigned long long done = 0;
+  static std::atomic<unsigned long long> done{0};
   const int n = P.cl_ptr[P.levels];
   if (n <= 0) return;
   const auto go = [&](auto kern) {
@@ -1674,7 +1664,7 @@ void launch_gram_base_level(const Pipeline& P, int level, cudaStream_t st) {
 }
 
 int launch_gram_basis(const Pipeline& P, int level) {
-  static unsigned long long done = 0;
+  static std::atomic<unsigned long long> done{0};
   const int n = P.lvl_ptr[level + 1] - P.lvl_ptr[level];
   if (n <= 0) return 0;
   const int nl = P.lvl_leaves[level];
@@ -1705,7 +1695,7 @@ int launch_gram_basis(const Pipeline& P, int level) {
 }
 
 void launch_gram_norms(const Pipeline& P) {
-  static unsigned long long done = 0;
+  static std::atomic<unsigned long long> done{0};
   if (P.n_norms <= 0) return;
   const int tc = tile_cols(P);
   smem_limit(k_fnorms, tiles_bytes(3, 32, 0), done);
@@ -1714,14 +1704,14 @@ void launch_gram_norms(const Pipeline& P) {
 }
 
 void launch_gram_weights(const Pipeline& P, int level) {
-  static unsigned long long done = 0;
+  static std::atomic<unsigned long long> done{0};
   const int n = P.lvl_ptr[level + 1] - P.lvl_ptr[level];
   if (n <= 0) return;
   const int tc = tile_cols(P);
   const auto bytes = [](int warps, int c, int kc) { return (size_t)warps * fweights_doubles(c, kc) * sizeof(double); };
   if (n <= kWideMaxTasks) {
     // few tasks: one block of kWideWarps warps per task, one set of tiles
-    static unsigned long long done_wide = 0;
+    static std::atomic<unsigned long long> done_wide{0};
     smem_limit(k_fweights_wide, bytes(1, 32, 32), done_wide);
     k_fweights_wide<<<n, kWideThreads, bytes(1, tc, P.M.kcap), P.stream>>>(P.M, P.items, P.ents,
                                                                  P.lvl_list + P.lvl_ptr[level], n, P.u, tc, P.BW,
@@ -1742,7 +1732,7 @@ void launch_gram_weights(const Pipeline& P, int level) {
 }
 
 void launch_gram_certify(const Pipeline& P) {
-  static unsigned long long done[2] = {0, 0};
+  static std::atomic<unsigned long long> done[2] = {{0}, {0}};
   const int n = P.lvl_ptr[P.levels];
   if (n <= 0) return;
   const int ld = P.kl + 1;
@@ -1763,7 +1753,7 @@ void launch_gram_certify(const Pipeline& P) {
 
 template <int UMAX>
 void launch_fbasis_block_form(const Pipeline& P, int n, int tc) {
-  static unsigned long long done = 0;
+  static std::atomic<unsigned long long> done{0};
   const size_t bytes = (size_t)kFbWarps * fbasis_doubles(tc, false) * sizeof(double);
   smem_limit(k_fbasis<false, UMAX>, (size_t)kFbWarps * fbasis_doubles(32, false) * sizeof(double), done);
   k_fbasis<false, UMAX><<<(n + kFbWarps - 1) / kFbWarps, 32 * kFbWarps, bytes, P.stream>>>(P.M, P.items, n, P.u,
@@ -1771,7 +1761,7 @@ void launch_fbasis_block_form(const Pipeline& P, int n, int tc) {
 }
 
 void launch_gram_outputs(const Pipeline& P) {
-  static unsigned long long done = 0;
+  static std::atomic<unsigned long long> done{0};
   const int n = P.lvl_ptr[P.levels];
   if (n <= 0) return;
   const int tc = tile_cols(P);

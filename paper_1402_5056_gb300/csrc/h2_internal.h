@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <stdexcept>
 #include <string>
@@ -31,6 +32,20 @@ struct Error : std::runtime_error {
   do {                        \
     if (!(cond)) throw ::h2::Error(H2_EINVAL, msg); \
   } while (0)
+
+// Raise a kernel's dynamic shared memory limit once per device: `done` holds
+// one bit per device ordinal below 64 (above, the attribute is set on every
+// call).  Host threads with contexts of their own may call it at once; the
+// attribute is idempotent.
+template <class Kern>
+inline void smem_limit(Kern kern, size_t bytes, std::atomic<unsigned long long>& done) {
+  int dev = 0;
+  H2_CUDA(cudaGetDevice(&dev));
+  const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return;
+  H2_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  done.fetch_or(bit, std::memory_order_release);
+}
 
 // ----------------------------------------------------------------- trees
 struct ClusterTree {

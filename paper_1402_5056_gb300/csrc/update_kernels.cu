@@ -1302,12 +1302,8 @@ static void launch_truncate_mr(const MatView& M, const Item* items, const int32_
                                cudaStream_t st) {
   const int warps = 2;
   const size_t sm = (size_t)warps * (2 * MR * kl + 2 * kl * (kl + 1) + kl) * sizeof(double);
-  static bool attr = false;
-  if (!attr) {
-    H2_CUDA(cudaFuncSetAttribute(k_truncate<MR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 warps * (2 * MR * 32 + 2 * 32 * 33 + 32) * (int)sizeof(double)));
-    attr = true;
-  }
+  static std::atomic<unsigned long long> attr{0};
+  smem_limit(k_truncate<MR>, (size_t)warps * (2 * MR * 32 + 2 * 32 * 33 + 32) * sizeof(double), attr);
   k_truncate<MR><<<(n + warps - 1) / warps, 32 * warps, sm, st>>>(M, items, list, n, u, kl, eps, A, B, IB, err);
 }
 
@@ -1478,14 +1474,8 @@ void run_pipeline(const Pipeline& P) {
   start(H2_PHASE_REPROJECT, st);
   if (P.n_tasks > 0) {
     const int tc = P.kl > P.M.kcap ? P.kl : P.M.kcap;
-    static unsigned long long attr = 0;
-    int dev = 0;
-    H2_CUDA(cudaGetDevice(&dev));
-    if (dev >= 64 || !((attr >> dev) & 1ull)) {
-      H2_CUDA(cudaFuncSetAttribute(k_reproject, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   kWarps * 3 * 33 * 32 * (int)sizeof(double)));
-      if (dev < 64) attr |= 1ull << dev;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    smem_limit(k_reproject, (size_t)kWarps * 3 * 33 * 32 * sizeof(double), attr);
     // flag the copies, list the one-sided tasks that need products
     k_onesided<<<(P.n_tasks + 255) / 256, 256, 0, st>>>(P.items, P.tasks, P.n_tasks, P.BW, P.IB, P.left, P.n_left);
     const size_t rp_smem = (size_t)kWarps * 3 * (tc + 1) * tc * sizeof(double);
