@@ -24,6 +24,7 @@ if not torch.cuda.is_available():
 from paper_1402_5056_gb300 import binding as b  # noqa: E402
 
 from gpu_util import concat_factors  # noqa: E402
+from layout import ONE, check_result_layout  # noqa: E402
 from libside import lib_problem  # noqa: E402
 from problems import draw_updates, oracle_problem  # noqa: E402
 
@@ -108,6 +109,7 @@ def _check_compact(ctx, P, Zl, u, full, compact, copied):
 def _run(ctx, Zl, blocks, A, B, u, eps, mode):
     P = b.h2_batch_create(ctx, Zl, blocks, u)
     try:
+        assert ONE in check_result_layout(b, P, Zl, u)
         b.h2_batch_set_mode(P, mode)
         Acat, Bcat = concat_factors(P, A, B, u)
         n = b.h2_batch_result_size(P)

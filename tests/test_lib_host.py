@@ -14,6 +14,7 @@ import numpy as np
 import pytest
 
 import synth
+from layout import check_result_layout
 from oracle.tree import BlockTree, ClusterTree
 
 b = pytest.importorskip("paper_1402_5056_gb300.binding")
@@ -118,4 +119,27 @@ def test_invalid_arguments_rejected():
         with pytest.raises(b.H2Error):
             b.h2_batch_create(None, Z, [0], 32)
     finally:
+        b.h2_matrix_free(Z)
+
+
+
+def test_host_result_layout_tiles_the_buffer():
+    """The host result's layout on a planned batch (no GPU: every rank is 0,
+    so one-sided couplings have empty pieces; the GPU host-result test runs
+    the same check with ranks), the compact entry point's argument check,
+    and the byte counts before any host execution."""
+    pts = synth.grid_points_2d(32)
+    Z = b.h2_matrix_create(None, pts, 16, 2.0, 0.0, 8)
+    tb = b.h2_tree_blocks(Z)
+    rng = np.random.default_rng(5)
+    blocks = [int(x) for x in rng.choice(np.flatnonzero(np.asarray(tb["kind"]) == 1), 6)] + [0]
+    P = b.h2_batch_create(None, Z, blocks, 3)
+    try:
+        regions = check_result_layout(b, P, Z, 3)
+        assert {1, 2} <= regions
+        with pytest.raises(b.H2Error):   # no context
+            b.h2_batch_execute_host_compact(None, P, np.zeros(1), np.zeros(1), 1e-8)
+        assert b.h2_batch_host_bytes(P) == (0, 0)
+    finally:
+        b.h2_batch_free(P)
         b.h2_matrix_free(Z)
