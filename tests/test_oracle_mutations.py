@@ -80,3 +80,42 @@ def test_matvec_pins_catch_mutation(name, tmp_path):
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=str(tmp_path),
                        env=env, timeout=600)
     assert r.returncode != 0, r.stdout[-2000:]
+
+
+TREE_MUTATIONS = {
+    "ties go to the highest axis": ("if ext[a] > ext[axis]:", "if ext[a] >= ext[axis]:"),
+    "points on the midpoint go to the first son": (
+        "first = idx[pts[:, axis] < mid]\n            second = idx[~(pts[:, axis] < mid)]",
+        "first = idx[pts[:, axis] <= mid]\n            second = idx[~(pts[:, axis] <= mid)]"),
+    "admissibility by the smaller diameter": (
+        "max(self.rows.diam(t), self.cols.diam(s))", "min(self.rows.diam(t), self.cols.diam(s))"),
+    "subdivision of a block with one leaf cluster": (
+        "elif self.rows.is_leaf(t) or self.cols.is_leaf(s):",
+        "elif self.rows.is_leaf(t) and self.cols.is_leaf(s):"),
+    "sons of a block in column-major order": (
+        "for t1 in self.rows.sons[t]:\n                for s1 in self.cols.sons[s]:",
+        "for s1 in self.cols.sons[s]:\n                for t1 in self.rows.sons[t]:"),
+    "squared box distance": (
+        "return math.sqrt(float(np.sum(gap ** 2)))", "return float(np.sum(gap ** 2))"),
+    "#T_t without t itself": (
+        "self.subtree_count[t] = 1 + sum(", "self.subtree_count[t] = 0 + sum("),
+}
+
+
+@pytest.mark.parametrize("name", sorted(TREE_MUTATIONS))
+def test_tree_pins_catch_mutation(name, tmp_path):
+    before, after = TREE_MUTATIONS[name]
+    shutil.copytree(os.path.join(ROOT, "oracle"), tmp_path / "oracle")
+    path = tmp_path / "oracle" / "tree.py"
+    src = path.read_text()
+    assert before in src
+    path.write_text(src.replace(before, after))
+    env = dict(os.environ)
+    env["PYTHONPATH"] = os.pathsep.join([str(tmp_path), ROOT, os.path.join(ROOT, "tests")])
+    code = ("import sys, pytest; sys.path.insert(0, %r); import oracle; "
+            "assert oracle.__file__.startswith(%r); "
+            "sys.exit(pytest.main(['-q', '-x', '-p', 'no:cacheprovider', %r]))"
+            % (str(tmp_path), str(tmp_path), os.path.join(ROOT, "tests", "test_oracle_tree.py")))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=str(tmp_path),
+                       env=env, timeout=600)
+    assert r.returncode != 0, r.stdout[-2000:]

@@ -49,9 +49,22 @@ def test_leaf_labels_partition_index_set(N, leaf):
     assert all(ct.father[t] < t for t in range(1, ct.n_clusters))
 
 
-def test_bisection_geometry_brute_force():
-    pts = synth.grid_points_2d(24)
-    ct = ClusterTree(pts, 32)
+def _integer_grid(n):
+    """n x n integer points: box midpoints fall exactly on points."""
+    i, j = np.meshgrid(np.arange(n, dtype=np.float64), np.arange(n, dtype=np.float64))
+    return np.stack([j.ravel(), i.ravel()], axis=1)
+
+
+@pytest.mark.parametrize("case", ["grid24", "integer13", "random3d"])
+def test_bisection_geometry_brute_force(case):
+    if case == "grid24":
+        pts, leaf = synth.grid_points_2d(24), 32
+    elif case == "integer13":
+        pts, leaf = _integer_grid(13), 8
+    else:
+        pts, leaf = np.random.default_rng(8).uniform(size=(700, 3)), 16
+    ct = ClusterTree(pts, leaf)
+    on_mid = 0
     for t in range(ct.n_clusters):
         P = pts[ct.idx[t]]
         lo, hi = _box(P)
@@ -63,8 +76,11 @@ def test_bisection_geometry_brute_force():
         a, b = ct.sons[t]
         assert np.all(pts[ct.idx[a]][:, axis] < mid)
         assert np.all(pts[ct.idx[b]][:, axis] >= mid)
+        on_mid += int(np.sum(pts[ct.idx[t]][:, axis] == mid))
         # stable order inside the sons
         assert np.all(np.diff(np.searchsorted(ct.idx[t], ct.idx[a])) > 0) or len(ct.idx[a]) < 2
+    if case == "integer13":
+        assert on_mid > 0          # the rule for points on the midpoint was exercised
 
 
 def test_power_of_two_grid_is_perfect():
@@ -89,12 +105,19 @@ def _brute_adm(P1, P2, eta):
     return dist > 0 and max(d1, d2) <= eta * dist
 
 
-@pytest.mark.parametrize("N,leaf,eta", [(16, 8, 2.0), (24, 16, 2.0), (32, 32, 1.0)])
+@pytest.mark.parametrize("N,leaf,eta", [(16, 8, 2.0), (24, 16, 2.0), (32, 32, 1.0),
+                                         (-1, 12, 2.0), (-2, 10, 1.5)])
 def test_block_tree_partition_and_admissibility(N, leaf, eta):
-    pts = synth.grid_points_2d(N)
+    if N > 0:
+        pts = synth.grid_points_2d(N)
+    else:   # ragged trees: leaves at several levels pair with larger clusters
+        pts = np.random.default_rng(-N).uniform(size=(600, -N + 1)) ** 2
     ct = ClusterTree(pts, leaf)
     bt = BlockTree(ct, ct, eta)
-    n = N * N
+    n = len(pts)
+    if N < 0:
+        assert any(bt.kind[b] == BlockTree.NEAR and bool(ct.sons[bt.row[b]]) != bool(ct.sons[bt.col[b]])
+                   for b in range(bt.n_blocks))
     cover = np.zeros((n, n), dtype=np.int32)
     for b in range(bt.n_blocks):
         t, s = bt.row[b], bt.col[b]
