@@ -32,23 +32,31 @@ MUTATIONS = {
 }
 
 
-@pytest.mark.parametrize("name", sorted(MUTATIONS))
-def test_pins_catch_mutation(name, tmp_path):
-    before, after = MUTATIONS[name]
+def _pins_fail(tmp_path, module, before, after, test_files):
+    """Plant `after` for `before` in a copy of oracle/<module> and run the
+    pin files against the copy: True when they fail."""
     shutil.copytree(os.path.join(ROOT, "oracle"), tmp_path / "oracle")
-    path = tmp_path / "oracle" / "update.py"
+    path = tmp_path / "oracle" / module
     src = path.read_text()
-    assert before in src
+    assert src.count(before) == 1
     path.write_text(src.replace(before, after))
     env = dict(os.environ)
     env["PYTHONPATH"] = os.pathsep.join([str(tmp_path), ROOT, os.path.join(ROOT, "tests")])
+    files = [os.path.join(ROOT, "tests", f) for f in test_files]
     code = ("import sys, pytest; sys.path.insert(0, %r); import oracle; "
             "assert oracle.__file__.startswith(%r); "
-            "sys.exit(pytest.main(['-q', '-x', '-p', 'no:cacheprovider', %r]))"
-            % (str(tmp_path), str(tmp_path), os.path.join(ROOT, "tests", "test_oracle_update.py")))
+            "sys.exit(pytest.main(['-q', '-x', '-p', 'no:cacheprovider'] + %r))"
+            % (str(tmp_path), str(tmp_path), files))
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=str(tmp_path),
                        env=env, timeout=600)
-    assert r.returncode != 0, r.stdout[-2000:]
+    return r.returncode != 0, r.stdout[-2000:]
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pins_catch_mutation(name, tmp_path):
+    before, after = MUTATIONS[name]
+    failed, out = _pins_fail(tmp_path, "update.py", before, after, ["test_oracle_update.py"])
+    assert failed, out
 
 
 MATVEC_MUTATIONS = {
@@ -66,20 +74,8 @@ MATVEC_MUTATIONS = {
 @pytest.mark.parametrize("name", sorted(MATVEC_MUTATIONS))
 def test_matvec_pins_catch_mutation(name, tmp_path):
     before, after = MATVEC_MUTATIONS[name]
-    shutil.copytree(os.path.join(ROOT, "oracle"), tmp_path / "oracle")
-    path = tmp_path / "oracle" / "matvec.py"
-    src = path.read_text()
-    assert before in src
-    path.write_text(src.replace(before, after))
-    env = dict(os.environ)
-    env["PYTHONPATH"] = os.pathsep.join([str(tmp_path), ROOT, os.path.join(ROOT, "tests")])
-    code = ("import sys, pytest; sys.path.insert(0, %r); import oracle; "
-            "assert oracle.__file__.startswith(%r); "
-            "sys.exit(pytest.main(['-q', '-x', '-p', 'no:cacheprovider', %r]))"
-            % (str(tmp_path), str(tmp_path), os.path.join(ROOT, "tests", "test_oracle_matvec.py")))
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=str(tmp_path),
-                       env=env, timeout=600)
-    assert r.returncode != 0, r.stdout[-2000:]
+    failed, out = _pins_fail(tmp_path, "matvec.py", before, after, ["test_oracle_matvec.py"])
+    assert failed, out
 
 
 TREE_MUTATIONS = {
@@ -105,17 +101,31 @@ TREE_MUTATIONS = {
 @pytest.mark.parametrize("name", sorted(TREE_MUTATIONS))
 def test_tree_pins_catch_mutation(name, tmp_path):
     before, after = TREE_MUTATIONS[name]
-    shutil.copytree(os.path.join(ROOT, "oracle"), tmp_path / "oracle")
-    path = tmp_path / "oracle" / "tree.py"
-    src = path.read_text()
-    assert before in src
-    path.write_text(src.replace(before, after))
-    env = dict(os.environ)
-    env["PYTHONPATH"] = os.pathsep.join([str(tmp_path), ROOT, os.path.join(ROOT, "tests")])
-    code = ("import sys, pytest; sys.path.insert(0, %r); import oracle; "
-            "assert oracle.__file__.startswith(%r); "
-            "sys.exit(pytest.main(['-q', '-x', '-p', 'no:cacheprovider', %r]))"
-            % (str(tmp_path), str(tmp_path), os.path.join(ROOT, "tests", "test_oracle_tree.py")))
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=str(tmp_path),
-                       env=env, timeout=600)
-    assert r.returncode != 0, r.stdout[-2000:]
+    failed, out = _pins_fail(tmp_path, "tree.py", before, after, ["test_oracle_tree.py"])
+    assert failed, out
+
+
+H2_MUTATIONS = {
+    "transfer transposed in the expansion": (
+        "parts = [self.dense(s) @ self.transfer[s] for s in self.tree.sons[t]]",
+        "parts = [self.dense(s) @ self.transfer[s].T for s in self.tree.sons[t]]"),
+    "coupling transposed in the block": (
+        "return self.V.dense(bt.row[b]) @ self.S[b] @ self.W.dense(bt.col[b]).T",
+        "return self.V.dense(bt.row[b]) @ self.S[b].T @ self.W.dense(bt.col[b]).T"),
+    "sons of a subdivided block at its corner": (
+        "r0 = self.V.tree.offset[tc] - t_off", "r0 = 0 * (self.V.tree.offset[tc] - t_off)"),
+    "leaf matrices read row by row": (
+        "cb.leaf[t] = np.array(leaf_data[pos:pos + m * k]).reshape((m, k), order=\"F\")",
+        "cb.leaf[t] = np.array(leaf_data[pos:pos + m * k]).reshape((m, k), order=\"C\")"),
+    "couplings read row by row": (
+        "self.S[b] = np.array(data[pos:pos + k * l]).reshape((k, l), order=\"F\")",
+        "self.S[b] = np.array(data[pos:pos + k * l]).reshape((k, l), order=\"C\")"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(H2_MUTATIONS))
+def test_h2_pins_catch_mutation(name, tmp_path):
+    before, after = H2_MUTATIONS[name]
+    failed, out = _pins_fail(tmp_path, "h2.py", before, after,
+                             ["test_oracle_h2.py", "test_oracle_update.py", "test_oracle_matvec.py"])
+    assert failed, out
