@@ -29,6 +29,24 @@ MUTATIONS = {
     "other side's R-factor ignored": ("rows.append(om * (Ro @ Sx))", "rows.append(om * Sx)"),
     "nearfield not updated": ("N_new[b] = Z.N[b] + At @ Bs.T", "N_new[b] = Z.N[b]"),
     "leaf SVD without weights": ("M = Vh @ Bw[t].T", "M = Vh"),
+    "extended transfer without the identity block": (
+        "Ex[k:, kf:] = np.eye(self.u)", "Ex[k:, kf:] = 0.0 * np.eye(self.u)"),
+    "leaf extension from the first rows of A": (
+        "r0 = tree.offset[t] - off0\n                self.leaf_ext", "r0 = 0\n                self.leaf_ext"),
+    "ancestor weights scaled by the subtree root's count": (
+        "om = math.sqrt(tree.subtree_count[a]) / nrm if nrm > 0 else 0.0",
+        "om = math.sqrt(tree.subtree_count[side.root]) / nrm if nrm > 0 else 0.0"),
+    "weights normalised by the unchanged coupling": (
+        "                nrm = block_norm(b)\n                om = math.sqrt(tree.subtree_count[t])",
+        "                nrm = float(np.linalg.norm(Z.S[b]))\n                om = math.sqrt(tree.subtree_count[t])"),
+    "tail measured in singular values, not their squares": (
+        "while r > 0 and tail + sigma[r - 1] ** 2 <= thr:\n        tail += sigma[r - 1] ** 2",
+        "while r > 0 and tail + sigma[r - 1] <= thr:\n        tail += sigma[r - 1]"),
+    "one-sided coupling padded above instead of below": (
+        "return np.vstack([S, np.zeros((u, l))])", "return np.vstack([np.zeros((u, l)), S])[:k + u]"),
+    "new directions with the wrong sign at the leaves": (
+        "self.leaf_ext[t] = np.hstack([basis.leaf[t], F[r0:r0 + tree.size[t], :]])",
+        "self.leaf_ext[t] = np.hstack([basis.leaf[t], -F[r0:r0 + tree.size[t], :]])"),
 }
 
 
