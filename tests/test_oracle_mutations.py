@@ -86,6 +86,13 @@ MATVEC_MUTATIONS = {
         "yh[bt.row[b]] = yh[bt.row[b]] + Z.S[b] @ xh[bt.col[b]]",
         "yh[bt.row[b]] = yh[bt.row[b]] + Z.S[b].T @ xh[bt.col[b]]"),
     "nearfield dropped": ("out[rt.offset[t]:rt.offset[t] + rt.size[t]] += Z.N[b] @", "_ = Z.N[b] @"),
+    "nearfield applied to the row cluster's entries": (
+        "@ X[ct.offset[s]:ct.offset[s] + ct.size[s]]", "@ X[ct.offset[t]:ct.offset[t] + ct.size[t]]"),
+    "backward transformation sons first": (
+        "    for t in range(rt.n_clusters):\n        for c in rt.sons[t]:",
+        "    for t in reversed(range(rt.n_clusters)):\n        for c in rt.sons[t]:"),
+    "beta term scaled by alpha": (
+        "res = res + beta * (", "res = res + alpha * beta * ("),
 }
 
 
