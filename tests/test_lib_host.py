@@ -143,3 +143,37 @@ def test_host_result_layout_tiles_the_buffer():
     finally:
         b.h2_batch_free(P)
         b.h2_matrix_free(Z)
+
+
+def test_update_work_is_linear_in_the_subtrees():
+    """Section 5: an update touches the clusters of T_t0 and T_s0 and the
+    couplings of their block rows and columns, at most C_sp (#T_t0 + #T_s0)
+    of them (C_sp = the most admissible blocks in one block row or column):
+    the planner's task counts for single updates at every level, with
+    equality for the cluster tasks."""
+    pts = synth.grid_points_2d(64)
+    Z = b.h2_matrix_create(None, pts, 16, 2.0, 0.0, 8)
+    ct = ClusterTree(pts, 16)
+    bt = BlockTree(ct, ct, 2.0)
+    c_sp = max(max(len(r) for r in bt.row_blocks), max(len(c) for c in bt.col_blocks))
+    by_level = {}
+    for blk in bt.admissible + bt.inadmissible + [0]:
+        by_level.setdefault(ct.level[bt.row[blk]], []).append(blk)
+    rng = np.random.default_rng(11)
+    ratios = []
+    try:
+        for lev, blks in sorted(by_level.items()):
+            for blk in rng.choice(blks, min(4, len(blks)), replace=False):
+                blk = int(blk)
+                nt = len(ct.descendants(bt.row[blk])) + len(ct.descendants(bt.col[blk]))
+                P = b.h2_batch_create(None, Z, [blk], 2)
+                try:
+                    st = b.h2_batch_stats(None, P, flops=False)
+                finally:
+                    b.h2_batch_free(P)
+                assert st["cluster_tasks"] == nt
+                assert st["block_tasks"] <= c_sp * nt
+                ratios.append(st["block_tasks"] / nt)
+        assert len(by_level) > 5 and max(ratios) <= c_sp
+    finally:
+        b.h2_matrix_free(Z)
