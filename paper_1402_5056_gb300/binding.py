@@ -308,9 +308,17 @@ def h2_batch_result_size(P) -> int:
     return n.value
 
 
+def _host_buffer(a, n, dtype, what):
+    """A caller's output array: contiguous, of the dtype, at least n long."""
+    if not (isinstance(a, np.ndarray) and a.dtype == dtype and a.flags.c_contiguous and a.size >= n):
+        raise ValueError("%s must be a contiguous %s array of at least %d entries" % (what, np.dtype(dtype), n))
+    return a
+
+
 def h2_batch_execute_host(ctx, P, A_host, B_host, eps: float, result=None):
     if result is None:
         result = np.zeros(h2_batch_result_size(P))
+    _host_buffer(result, h2_batch_result_size(P), np.float64, "result")
     _check(_lib.h2_batch_execute_host(ctx, P, _ptr(_f64(A_host)), _ptr(_f64(B_host)), float(eps),
                                       _ptr(result)), ctx)
     return result
@@ -320,10 +328,13 @@ def h2_batch_execute_host_compact(ctx, P, A_host, B_host, eps: float, result=Non
     """Compact host result: (result, copied); copied[b] = 1 where block task
     b keeps its coupling padded with zeros (its piece is then unspecified
     when `result` is page-locked)."""
+    n_tasks = h2_batch_stats(None, P, flops=False)["block_tasks"]
     if result is None:
         result = np.zeros(h2_batch_result_size(P))
     if copied is None:
-        copied = np.zeros(h2_batch_stats(None, P, flops=False)["block_tasks"], np.int8)
+        copied = np.zeros(n_tasks, np.int8)
+    _host_buffer(result, h2_batch_result_size(P), np.float64, "result")
+    _host_buffer(copied, n_tasks, np.int8, "copied")
     _check(_lib.h2_batch_execute_host_compact(ctx, P, _ptr(_f64(A_host)), _ptr(_f64(B_host)), float(eps),
                                               _ptr(result), _ptr(copied)), ctx)
     return result, copied

@@ -177,3 +177,27 @@ def test_update_work_is_linear_in_the_subtrees():
         assert len(by_level) > 5 and max(ratios) <= c_sp
     finally:
         b.h2_matrix_free(Z)
+
+
+def test_binding_rejects_short_host_buffers():
+    """The binding checks a caller's output arrays before the library
+    writes them (dtype, contiguity, length)."""
+    pts = synth.grid_points_2d(16)
+    Z = b.h2_matrix_create(None, pts, 8, 2.0, 0.0, 4)
+    tb = b.h2_tree_blocks(Z)
+    P = b.h2_batch_create(None, Z, [int(np.flatnonzero(np.asarray(tb["kind"]) == 1)[0])], 2)
+    try:
+        n = b.h2_batch_result_size(P)
+        nt = b.h2_batch_stats(None, P, flops=False)["block_tasks"]
+        for bad in (np.zeros(n - 1), np.zeros(n, np.float32), np.zeros((n, 2))[:, 0]):
+            with pytest.raises(ValueError):
+                b.h2_batch_execute_host(None, P, np.zeros(1), np.zeros(1), 1e-8, bad)
+        with pytest.raises(ValueError):
+            b.h2_batch_execute_host_compact(None, P, np.zeros(1), np.zeros(1), 1e-8, np.zeros(n),
+                                            np.zeros(max(nt - 1, 0), np.int8))
+        with pytest.raises(ValueError):
+            b.h2_batch_execute_host_compact(None, P, np.zeros(1), np.zeros(1), 1e-8, np.zeros(n),
+                                            np.zeros(nt, np.int32))
+    finally:
+        b.h2_batch_free(P)
+        b.h2_matrix_free(Z)
