@@ -101,3 +101,57 @@ def test_nested_transfer_block_form():
         F[:ki, kp:] = np.linalg.solve(LSp, (Ci - Ei @ Cp).T).T
         F[ki:, kp:] = np.linalg.solve(LSp, LSi).T          # L_Si^* L_Sp^{-*}
         np.testing.assert_allclose(Qi @ F, Qp[rows], rtol=0, atol=1e-12)
+
+
+def _f32_certificate(A, shift):
+    """Float32 first try of the certificate, emulated: A 2^-e truncated
+    toward zero to float32 (2^e ~ tr A), the diagonal shifted by
+    (shift + 4 (n + 2) 2^-24 tr A) 2^-e rounded up, then an LDL^* in float32
+    with every pivot required positive and finite."""
+    n = A.shape[0]
+    trA = float(np.trace(A))
+    _, ex = np.frexp(trA)
+    X = A * 2.0 ** (-int(ex))
+    F = X.astype(np.float32)
+    over = np.abs(F.astype(np.float64)) > np.abs(X)
+    F[over] = np.nextafter(F[over], np.float32(0))          # truncation toward zero
+    c = (shift + 4.0 * (n + 2) * 2.0 ** -24 * trA) * 2.0 ** (-int(ex))
+    cf = np.float32(c)
+    if float(cf) < c:
+        cf = np.nextafter(cf, np.float32(np.inf))           # rounded up
+    F = F - cf * np.eye(n, dtype=np.float32)
+    for j in range(n):
+        d = F[j, j]
+        if not (np.isfinite(d) and d > np.float32(1e-30)):
+            return False
+        lv = F[j + 1:, j] / d
+        F[j + 1:, j + 1:] -= np.outer(F[j + 1:, j], lv).astype(np.float32)
+    return True
+
+
+def test_float32_certificate_never_certifies_an_indefinite_shift():
+    """Success of the float32 try proves A - shift I positive definite
+    (Rump, BIT 2006): on matrices whose smallest eigenvalue lies just below
+    the shift it must fail; well above the margin it succeeds."""
+    rng = np.random.default_rng(12)
+    fails_below = succeeds_above = 0
+    for trial in range(120):
+        n = int(rng.integers(4, 25))
+        Q = _orth(rng, n, n)
+        lam = np.sort(10.0 ** rng.uniform(-3, 0, n))[::-1] * float(rng.uniform(0.5, 4.0))
+        trA = lam.sum()
+        margin = 4.0 * (n + 2) * 2.0 ** -24 * trA
+        shift = float(rng.uniform(0.0, 50.0)) * margin
+        below = lam.copy()
+        below[-1] = shift * (1.0 - 10.0 ** rng.uniform(-8, -1)) if shift > 0 else -1e-3 * margin
+        A = (Q * below) @ Q.T
+        A = 0.5 * (A + A.T)
+        if np.linalg.eigvalsh(A)[0] - shift < 0:
+            assert not _f32_certificate(A, shift), trial
+            fails_below += 1
+        above = lam.copy()
+        above[-1] = shift + 100.0 * margin
+        A = (Q * above) @ Q.T
+        A = 0.5 * (A + A.T)
+        succeeds_above += _f32_certificate(A, shift)
+    assert fails_below > 100 and succeeds_above > 100
