@@ -282,7 +282,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--matvec-steps", type=int, default=10, help="timed h2_matvec calls per case (0: none)")
     ap.add_argument("--mode", choices=("auto", "exact"), default="auto",
                     help="path of the timed steps: auto (certified path, exact path where it fails) or exact")
