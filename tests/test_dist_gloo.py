@@ -1,5 +1,7 @@
 """Host-side multi-rank logic of the benchmark harness (gloo, 2 ranks, CPU):
-shard ranges cover a batch exactly once and the timing reductions agree."""
+shard ranges cover a batch exactly once, the timing reductions agree, and an
+isolated batch split over ranks (oracle) equals the serial batch bit for
+bit."""
 import os
 import socket
 
@@ -54,3 +56,55 @@ def test_gloo_two_ranks():
         mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
     assert res[0] == res[1] == (10.0, 2.0)
+
+
+def _fingerprint(delta):
+    """The delta of one update as plain numbers: ranks and every matrix."""
+    out = []
+    for key in ("V", "W"):
+        d = delta[key]
+        out.append(sorted(d["rank"].items()))
+        out.append([(t, d["leaf"][t].tobytes()) for t in sorted(d["leaf"])])
+        out.append([(t, d["transfer"][t].tobytes()) for t in sorted(d["transfer"])])
+    out.append([(b, delta["S"][b].tobytes()) for b in sorted(delta["S"])])
+    out.append([(b, delta["N"][b].tobytes()) for b in sorted(delta["N"])])
+    return out
+
+
+def _batch_problem():
+    from problems import draw_updates, oracle_problem
+    Zo, st, _ = oracle_problem(16, 4, 601, 8)
+    blocks, A, B = draw_updates(Zo, st, 7, 2)
+    return Zo, blocks, A, B
+
+
+def _shard_worker(rank, world, port, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from oracle.update import local_update
+        Zo, blocks, A, B = _batch_problem()
+        b, e = shard_range(len(blocks), rank, world)
+        mine = [_fingerprint(local_update(Zo, blocks[j], A[j], B[j], 1e-6)) for j in range(b, e)]
+        parts = [None] * world
+        dist.all_gather_object(parts, mine)
+        out[rank] = [fp for part in parts for fp in part]
+    finally:
+        dist.destroy_process_group()
+
+
+def test_sharded_isolated_batch_equals_serial():
+    """Isolated updates need no exchange between ranks: a batch split by
+    index over 2 gloo ranks, each rank computing its updates on its own copy
+    of the base matrix (the oracle), gives bit for bit the serial batch."""
+    from oracle.update import isolated_batch
+    world = 2
+    port = _free_port()
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_shard_worker, args=(world, port, out), nprocs=world, join=True)
+        res = dict(out)
+    Zo, blocks, A, B = _batch_problem()
+    serial = [_fingerprint(d) for d in isolated_batch(Zo, blocks, A, B, 1e-6)]
+    assert res[0] == res[1] == serial
