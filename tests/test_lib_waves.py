@@ -11,6 +11,7 @@ and not before an earlier update that reads what j writes; the waves are
 the earliest such.
 """
 import numpy as np
+import pytest
 
 import synth
 from paper_1402_5056_gb300 import binding as b
@@ -81,8 +82,13 @@ def _expected_waves(fps):
     return waves
 
 
-def test_waves_match_the_footprints():
-    pts = synth.grid_points_2d(32)
+@pytest.mark.parametrize("case", ["grid", "ragged2d", "ragged3d"])
+def test_waves_match_the_footprints(case):
+    if case == "grid":
+        pts = synth.grid_points_2d(32)
+    else:   # leaves at several levels
+        dim = 2 if case == "ragged2d" else 3
+        pts = np.random.default_rng(dim).uniform(size=(900, dim)) ** 2
     Z = b.h2_matrix_create(None, pts, 16, 2.0, 0.0, 6)
     try:
         tb = b.h2_tree_blocks(Z)
