@@ -123,12 +123,13 @@ def test_invalid_arguments_rejected():
 
 
 
-def test_host_result_layout_tiles_the_buffer():
+@pytest.mark.parametrize("ragged", [False, True])
+def test_host_result_layout_tiles_the_buffer(ragged):
     """The host result's layout on a planned batch (no GPU: every rank is 0,
     so one-sided couplings have empty pieces; the GPU host-result test runs
     the same check with ranks), the compact entry point's argument check,
     and the byte counts before any host execution."""
-    pts = synth.grid_points_2d(32)
+    pts = np.random.default_rng(2).uniform(size=(900, 3)) ** 2 if ragged else synth.grid_points_2d(32)
     Z = b.h2_matrix_create(None, pts, 16, 2.0, 0.0, 8)
     tb = b.h2_tree_blocks(Z)
     rng = np.random.default_rng(5)
