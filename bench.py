@@ -50,10 +50,9 @@ UNIT = "updates/s"
 WORK = dict(N=256, leaf=32, eta=2.0, k=16, u=8, eps=1e-8, count=4096, seed=synth.SEED_BASE + 1)
 WORKLOAD_NAME = ("isolated H2 low-rank updates: 4096 rank-8 updates, 256x256-point H2 matrix "
                  "(n=65536, leaf 32, eta 2, k=16), eps=1e-8, float64")
-# Float64 FMA peak of one GB300: 2 DFMA per clock per SM (measured by the
-# probe paper_1402_5056_gb300/csrc/fp64_probe.cu: 1.254 TFLOP/s at 2070 MHz)
-# x 152 SMs x 2 flop x 2.070 GHz; the roofline denominator of this
-# ALU-bound path.
+# Float64 FMA peak of one GB300: 2 DFMA per clock per SM (confirmed by an
+# FMA throughput measurement: 1.254 TFLOP/s at 2070 MHz) x 152 SMs x 2 flop
+# x 2.070 GHz; the roofline denominator of this ALU-bound path.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
 

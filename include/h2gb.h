@@ -331,9 +331,12 @@ h2_status h2_lowrank_update(h2_ctx* ctx, h2_matrix* Z, int64_t block, int u, con
 
 /* Allocation-free variant of h2_lowrank_update (the paper has no
  * counterpart; this is an interface for callers that must not allocate
- * device memory while they run: code recorded into CUDA graphs, code living
- * in a fixed device-memory budget reserved at start-up, hosts whose device
- * allocator belongs to another runtime).  Same arguments, same update, same
+ * device memory while they run: code living in a fixed device-memory budget
+ * reserved at start-up, where an allocation in the middle of the run could
+ * fail or take memory another part of the program counts on, and hosts
+ * whose device allocator belongs to another runtime, e.g. a framework's
+ * caching allocator that has reserved the free memory).  Same arguments,
+ * same update, same
  * results as h2_lowrank_update, but every piece of device scratch comes
  * from one fixed 48 MiB array inside the library (held on every GPU that
  * loads the library until the process exits), host planning uses static
@@ -341,15 +344,31 @@ h2_status h2_lowrank_update(h2_ctx* ctx, h2_matrix* Z, int64_t block, int u, con
  * called.  Limits, rejected with H2_EINVAL and a message naming the limit:
  * at most 512 clusters per side in the matrix, 256 cluster tasks, 2048
  * affected couplings, 4096 weight-stack blocks, 256 blocks inside the
- * update, 1024 nearfield leaves inside the block; and k_t + u must fit the
- * matrix's current rank capacity, because this entry point never grows
- * storage.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current): make that first call
- * before any stream capture.  All calls share the array and its contents
- * persist between calls; calls whose GPU work may overlap (other streams or
- * host threads) race and must be serialised by the caller.  Synchronizes. */
+ * update, 1024 nearfield leaves inside the block, leading dimensions up to
+ * 2^31 - 1; and k_t + u must fit the matrix's current rank capacity, because
+ * this entry point never grows storage.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress, with that device
+ * current) and keeps it for the process: make that first call before any
+ * stream capture, and do not call this entry point on a device whose
+ * primary context was destroyed (cudaDeviceReset) after that.  All calls
+ * share the array and the host planning buffers, and the array keeps the
+ * last call's contents; calls whose GPU work overlapped would race on them,
+ * so each call holds a library-wide lock and synchronizes the context's
+ * stream before it returns. */
 h2_status h2_lowrank_update_noalloc(h2_ctx* ctx, h2_matrix* Z, int64_t block, int u, const double* A,
                                     int64_t lda, const double* B, int64_t ldb, double eps);
+
+/* ----------------------------------------------------------- diagnostics */
+
+/* The float64 reciprocals the factorisation kernels use for their pivots
+ * (the paper has no counterpart; a check of the arithmetic the certificate's
+ * margin relies on): precise[i] = the PTX estimate rcp.approx.ftz.f64 of 1/d
+ * refined by one cubic Newton-Raphson step (truncation error below 2^-66,
+ * about one ulp of rounding), coarse[i] = the same estimate refined by one
+ * quadratic step (relative error below 2^-43).  Defined for normal d > 0
+ * with a normal reciprocal.  d, precise, coarse: DEVICE arrays of n
+ * doubles.  Asynchronous. */
+h2_status h2_check_reciprocal(h2_ctx* ctx, const double* d, int64_t n, double* precise, double* coarse);
 
 #ifdef __cplusplus
 }

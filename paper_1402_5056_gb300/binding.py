@@ -33,7 +33,7 @@ EXPORTS = [
     "h2_batch_stats", "h2_batch_set_timing", "h2_batch_phase_stats", "h2_batch_item_info", "h2_batch_item_tile",
     "h2_batch_update_items", "h2_batch_set_mode", "h2_batch_paths", "h2_lowrank_update",
     "h2_lowrank_update_noalloc", "h2_lowrank_update_sequence", "h2_matvec", "h2_block_to_dense",
-    "h2_sequence_waves",
+    "h2_sequence_waves", "h2_check_reciprocal",
 ]
 
 PHASES = ("base_weights", "rfactor", "norms", "weights", "truncate", "reproject", "exact", "bases")
@@ -100,6 +100,7 @@ _sig("h2_batch_host_bytes", _int, _p, _p, _p)
 _sig("h2_batch_result_size", _int, _p, _p)
 _sig("h2_sequence_waves", _int, _p, _i64, _p, _p, _p)
 _sig("h2_block_to_dense", _int, _p, _p, _i64, _p, _i64)
+_sig("h2_check_reciprocal", _int, _p, _p, _i64, _p, _p)
 _sig("h2_matvec", _int, _p, _p, _i64, _dbl, _p, _i64, _dbl, _p, _i64)
 _sig("h2_lowrank_update_sequence", _int, _p, _p, _i64, _p, _int, _p, _p, _dbl, _p)
 _sig("h2_batch_result_offsets", _int, _p, _p, _p)
@@ -464,3 +465,11 @@ def h2_sequence_waves(Z, blocks):
     n = C.c_int64()
     _check(_lib.h2_sequence_waves(Z, len(bl), _ptr(bl), _ptr(wave), C.byref(n)))
     return wave, n.value
+
+
+def h2_check_reciprocal(ctx, d_dev: int, n: int, precise_dev: int, coarse_dev: int):
+    """The pivot reciprocals of the factorisation kernels, element by element
+    (device arrays of n doubles)."""
+    _check(_lib.h2_check_reciprocal(ctx, C.c_void_p(d_dev), int(n), C.c_void_p(precise_dev),
+                                    C.c_void_p(coarse_dev)), ctx)
+

@@ -2414,3 +2414,14 @@ extern "C" h2_status h2_block_to_dense(h2_ctx* ctx, const h2_matrix* Z, int64_t 
     H2_CUDA(e);
   });
 }
+
+extern "C" h2_status h2_check_reciprocal(h2_ctx* ctx, const double* d, int64_t n, double* precise,
+                                         double* coarse) {
+  using namespace h2;
+  if (!ctx || n < 0 || (n > 0 && (!d || !precise || !coarse))) return H2_EINVAL;
+  return guard(ctx, [&] {
+    DeviceGuard g(ctx->device);
+    launch_recip_check(d, n, precise, coarse, ctx->stream);
+    H2_CUDA(cudaGetLastError());
+  });
+}

@@ -1776,4 +1776,20 @@ void launch_gram_outputs(const Pipeline& P) {
                        P.stream>>>(P.M, P.items, n, P.u, tc, P.A, P.B, P.IB, P.BW);
 }
 
+// The two reciprocals above, element by element, for a check of their error
+// bounds against the correctly rounded quotient (diagnostic entry point).
+__global__ void k_recip_check(const double* d, int64_t n, double* precise, double* coarse) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) {
+    precise[i] = recip(d[i]);
+    coarse[i] = recip_coarse(d[i]);
+  }
+}
+
+void launch_recip_check(const double* d, int64_t n, double* precise, double* coarse, cudaStream_t st) {
+  if (n <= 0) return;
+  const int threads = 256;
+  k_recip_check<<<(unsigned)((n + threads - 1) / threads), threads, 0, st>>>(d, n, precise, coarse);
+}
+
 }  // namespace h2

@@ -1,9 +1,11 @@
 // Allocation-free variant of the single in-place local low-rank update.
 //
 // Who needs it: callers that must not allocate device memory while they
-// run -- code recorded into a CUDA graph, code running under a fixed
-// device-memory budget handed out once at start-up, or hosts whose device
-// allocator is owned by another runtime.  For them h2_lowrank_update_noalloc
+// run -- code running under a fixed device-memory budget handed out once at
+// start-up (a cudaMalloc in the middle of the run could fail or push another
+// part of the program out of its share), or hosts whose device allocator is
+// owned by another runtime (a framework's caching allocator that has already
+// reserved the free memory).  For them h2_lowrank_update_noalloc
 // performs the same update as h2_lowrank_update (same kernels, same results)
 // but takes every piece of device scratch (task lists, per-cluster R-factor,
 // weight and basis-change tiles, the weights of the unchanged matrix, copy
@@ -15,10 +17,14 @@
 // library.  In host code its name is only a stand-in, so its device address
 // is fetched with cudaGetSymbolAddress the first time the entry point runs
 // on a device (with that device current); that first call therefore has to
-// happen before any stream capture.  Every call shares the array: calls
-// whose GPU work overlaps (other streams, other host threads) race and must
-// be serialised by the caller.  No part of the array has to start at zero:
-// each kernel writes every value a later kernel reads.
+// happen before any stream capture.  Every call shares the array (and the
+// static host planning buffers): calls whose GPU work overlapped would race
+// on it, so each call holds a library-wide lock and waits for its own GPU
+// work (it synchronizes the context's stream) before it returns.  The array
+// keeps the last call's contents; no part of it has to start at zero: each
+// kernel writes every value a later kernel reads.  The cached device address
+// belongs to the device's primary context: a caller that destroys that
+// context (cudaDeviceReset) must not call this entry point afterwards.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -512,6 +518,9 @@ extern "C" h2_status h2_lowrank_update_noalloc(h2_ctx* ctx, h2_matrix* Z, int64_
     st = fail(H2_EINVAL, "matrix has no device storage");
   } else if (lda < Z->rows.size[Z->blocks.row[block]] || ldb < Z->cols.size[Z->blocks.col[block]]) {
     st = fail(H2_EINVAL, "leading dimension too small");
+  } else if (lda > INT32_MAX || ldb > INT32_MAX) {
+    // the kernels index the caller's factors with 32-bit leading dimensions
+    st = fail(H2_EINVAL, "leading dimension above 2^31 - 1");
   } else if (!std::isfinite(eps) || eps < 0) {
     st = fail(H2_EINVAL, "eps must be finite and >= 0");
   } else {

@@ -16,6 +16,7 @@ if not torch.cuda.is_available():
 
 from paper_1402_5056_gb300 import binding as b  # noqa: E402
 
+from blockwise import assert_blockwise_dense  # noqa: E402
 from gpu_util import run_isolated  # noqa: E402
 from libside import lib_problem, lib_problem_general, to_oracle  # noqa: E402
 from oracle.tree import BlockTree  # noqa: E402
@@ -45,8 +46,7 @@ def _check(ctx, Zo, Zl, blocks, A, B, u, eps):
                 rV, rW = b.h2_get_ranks(C, 0), b.h2_get_ranks(C, 1)
             finally:
                 b.h2_matrix_free(C)
-            err = np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-300)
-            assert err <= TOL, (j, b0, err)
+            assert_blockwise_dense(got, ref, Zo.blocks, Zo.V.tree, Zo.W.tree, TOL, (j, b0))
             if d["margin"] >= 1e-6:
                 for t, r in d["V"]["rank"].items():
                     assert rV[t] == r

@@ -13,6 +13,7 @@ if not torch.cuda.is_available():
 
 from paper_1402_5056_gb300 import binding as b  # noqa: E402
 
+from blockwise import assert_blockwise_dense  # noqa: E402
 from gpu_util import concat_factors  # noqa: E402
 from libside import lib_problem, to_oracle  # noqa: E402
 from oracle.update import apply_delta, local_update  # noqa: E402
@@ -60,7 +61,7 @@ def test_replays_match_eager_and_oracle(ctx):
             for j in (0, len(blocks) - 1):
                 ref = apply_delta(Zo, local_update(Zo, blocks[j], A[j], B[j], eps)).dense()
                 got = _dense_of(ctx, Zl, Zo, P, j, dA, dB)
-                assert np.linalg.norm(got - ref) <= TOL * np.linalg.norm(ref), (eps, mode, j)
+                assert_blockwise_dense(got, ref, Zo.blocks, Zo.V.tree, Zo.W.tree, TOL, (eps, mode, j))
     finally:
         b.h2_batch_free(P)
         b.h2_matrix_free(Zl)

@@ -20,6 +20,7 @@ if not torch.cuda.is_available():
 
 from paper_1402_5056_gb300 import binding as b  # noqa: E402
 
+from blockwise import assert_blockwise_dense  # noqa: E402
 from gpu_util import applied_delta, concat_factors  # noqa: E402
 from libside import lib_problem, to_oracle  # noqa: E402
 from oracle.tree import BlockTree  # noqa: E402
@@ -46,6 +47,10 @@ def _batch(ctx, Zl, blocks, A, B, u, eps, mode):
     b.h2_batch_execute(ctx, P, dA.data_ptr(), dB.data_ptr(), eps)
     b.h2_ctx_synchronize(ctx)
     return P, dA, dB
+
+
+def _bw(got, ref, Zo, what):
+    assert_blockwise_dense(got, ref, Zo.blocks, Zo.V.tree, Zo.W.tree, TOL, what)
 
 
 def _dense(ctx, Zl, Zo, P, j, dA, dB):
@@ -97,7 +102,7 @@ def test_certified_path_without_truncation(ctx, N, leaf, k, u):
                 assert exact[j] == (0 if full else 1), (j, b0)
                 ref = apply_delta(Zo, d).dense()
                 got = _dense(ctx, Zl, Zo, P, j, dA, dB)
-                assert np.linalg.norm(got - ref) <= TOL * np.linalg.norm(ref), j
+                _bw(got, ref, Zo, j)
         finally:
             b.h2_batch_free(P)
     finally:
@@ -123,7 +128,7 @@ def test_truncation_falls_back_to_exact_path(ctx):
                     assert exact[j] == 1, j
                 ref = apply_delta(Zo, d).dense()
                 got = _dense(ctx, Zl, Zo, P, j, dA, dB)
-                assert np.linalg.norm(got - ref) <= TOL * np.linalg.norm(ref), j
+                _bw(got, ref, Zo, j)
             assert any(truncating)
             assert b.h2_batch_phase_stats(ctx, P, b.PHASES.index("exact"))["flops"] > 0
         finally:
@@ -150,10 +155,9 @@ def test_modes_agree_with_oracle_and_each_other(ctx, eps):
             finally:
                 b.h2_batch_free(P)
         for j, ref in enumerate(refs):
-            nr = np.linalg.norm(ref)
             for mode in got:
-                assert np.linalg.norm(got[mode][j] - ref) <= TOL * nr, (mode, j)
-            assert np.linalg.norm(got[b.MODE_AUTO][j] - got[b.MODE_EXACT][j]) <= TOL * nr, j
+                _bw(got[mode][j], ref, Zo, (mode, j))
+            _bw(got[b.MODE_AUTO][j], got[b.MODE_EXACT][j], Zo, ("auto vs exact", j))
     finally:
         b.h2_matrix_free(Zl)
 
@@ -229,7 +233,7 @@ def test_certified_path_on_non_orthonormal_bases(ctx):
             finally:
                 b.h2_batch_free(P)
             got = to_oracle(ctx, Zl, Zo).dense()
-            assert np.linalg.norm(got - ref) <= TOL * np.linalg.norm(ref), (b0, eps)
+            _bw(got, ref, Zo, (b0, eps))
     finally:
         b.h2_matrix_free(Zl)
 
@@ -276,7 +280,7 @@ def test_certificate_at_the_rank_threshold(ctx, above):
             assert b.h2_batch_paths(ctx, P, 1)[0] == (1 if above else 0)
             ref = apply_delta(Zo, d).dense()
             got = _dense(ctx, Zl, Zo, P, 0, dA, dB)
-            assert np.linalg.norm(got - ref) <= TOL * np.linalg.norm(ref)
+            _bw(got, ref, Zo, ("threshold", above))
         finally:
             b.h2_batch_free(P)
     finally:

@@ -17,6 +17,7 @@ if not torch.cuda.is_available():
 
 from paper_1402_5056_gb300 import binding as b  # noqa: E402
 
+from blockwise import assert_blockwise_dense  # noqa: E402
 from libside import lib_problem, to_oracle  # noqa: E402
 from oracle.tree import BlockTree  # noqa: E402
 from oracle.update import sequential_batch  # noqa: E402
@@ -86,7 +87,7 @@ def test_sequence_equals_one_by_one(ctx, eps):
         if eps < 1e-6:
             ref = sequential_batch(Zo, blocks, A, B, eps).dense()
             got = to_oracle(ctx, Z2, Zo).dense()
-            assert np.linalg.norm(got - ref) <= TOL * np.linalg.norm(ref)
+            assert_blockwise_dense(got, ref, Zo.blocks, Zo.V.tree, Zo.W.tree, TOL, "chain")
     finally:
         b.h2_matrix_free(Z2)
 

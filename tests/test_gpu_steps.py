@@ -19,6 +19,7 @@ if not torch.cuda.is_available():
 
 from paper_1402_5056_gb300 import binding as b  # noqa: E402
 
+from blockwise import assert_blockwise_dense  # noqa: E402
 from libside import lib_problem, to_oracle  # noqa: E402
 from oracle.update import apply_delta, local_update  # noqa: E402
 from problems import draw_updates, oracle_problem  # noqa: E402
@@ -90,7 +91,6 @@ def test_chain_intermediates_match_oracle(ctx, eps, mode):
                 b.h2_batch_free(P)
             ref = apply_delta(Zs, d).dense()
             got = to_oracle(ctx, Zl, Zo).dense()
-            err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
-            assert err <= 1e-10, (j, err)
+            assert_blockwise_dense(got, ref, Zo.blocks, Zo.V.tree, Zo.W.tree, 1e-10, j)
     finally:
         b.h2_matrix_free(Zl)

@@ -154,3 +154,22 @@ def test_h2_pins_catch_mutation(name, tmp_path):
     failed, out = _pins_fail(tmp_path, "h2.py", before, after,
                              ["test_oracle_h2.py", "test_oracle_update.py", "test_oracle_matvec.py"])
     assert failed, out
+
+
+MARGIN_MUTATIONS = {
+    "margin always reported as small": ("    return min(lo, hi)", "    return 0.0 * min(lo, hi)"),
+    "next tail sum from the wrong singular value": (
+        "tail_next = tail_r + float(sigma[r - 1] ** 2)",
+        "tail_next = tail_r + float(sigma[min(r, len(sigma) - 1)] ** 2)"),
+    "kept tail starts one value late": (
+        "tail_r = float(np.sum(sigma[r:] ** 2))", "tail_r = float(np.sum(sigma[r + 1:] ** 2))"),
+    "margin measured against eps/2 instead of its square": (
+        "thr = (0.5 * eps) ** 2\n    tail_r", "thr = (0.5 * eps)\n    tail_r"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MARGIN_MUTATIONS))
+def test_margin_pin_catches_mutation(name, tmp_path):
+    before, after = MARGIN_MUTATIONS[name]
+    failed, out = _pins_fail(tmp_path, "update.py", before, after, ["test_oracle_rank_margin.py"])
+    assert failed, out
