@@ -360,15 +360,13 @@ h2_status h2_lowrank_update_noalloc(h2_ctx* ctx, h2_matrix* Z, int64_t block, in
 
 /* ----------------------------------------------------------- diagnostics */
 
-/* The float64 reciprocals the factorisation kernels use for their pivots
+/* The float64 reciprocal the factorisation kernels use for their pivots
  * (the paper has no counterpart; a check of the arithmetic the certificate's
- * margin relies on): precise[i] = the PTX estimate rcp.approx.ftz.f64 of 1/d
- * refined by one cubic Newton-Raphson step (truncation error below 2^-66,
- * about one ulp of rounding), coarse[i] = the same estimate refined by one
- * quadratic step (relative error below 2^-43).  Defined for normal d > 0
- * with a normal reciprocal.  d, precise, coarse: DEVICE arrays of n
- * doubles.  Asynchronous. */
-h2_status h2_check_reciprocal(h2_ctx* ctx, const double* d, int64_t n, double* precise, double* coarse);
+ * margin relies on): out[i] = the PTX estimate rcp.approx.ftz.f64 of 1/d[i]
+ * refined by one cubic Newton-Raphson step, within one ulp of the correctly
+ * rounded quotient.  Defined for normal d > 0 with a normal reciprocal.
+ * d, out: DEVICE arrays of n doubles.  Asynchronous. */
+h2_status h2_check_reciprocal(h2_ctx* ctx, const double* d, int64_t n, double* out);
 
 #ifdef __cplusplus
 }

@@ -100,7 +100,7 @@ _sig("h2_batch_host_bytes", _int, _p, _p, _p)
 _sig("h2_batch_result_size", _int, _p, _p)
 _sig("h2_sequence_waves", _int, _p, _i64, _p, _p, _p)
 _sig("h2_block_to_dense", _int, _p, _p, _i64, _p, _i64)
-_sig("h2_check_reciprocal", _int, _p, _p, _i64, _p, _p)
+_sig("h2_check_reciprocal", _int, _p, _p, _i64, _p)
 _sig("h2_matvec", _int, _p, _p, _i64, _dbl, _p, _i64, _dbl, _p, _i64)
 _sig("h2_lowrank_update_sequence", _int, _p, _p, _i64, _p, _int, _p, _p, _dbl, _p)
 _sig("h2_batch_result_offsets", _int, _p, _p, _p)
@@ -467,9 +467,7 @@ def h2_sequence_waves(Z, blocks):
     return wave, n.value
 
 
-def h2_check_reciprocal(ctx, d_dev: int, n: int, precise_dev: int, coarse_dev: int):
-    """The pivot reciprocals of the factorisation kernels, element by element
+def h2_check_reciprocal(ctx, d_dev: int, n: int, out_dev: int):
+    """The pivot reciprocal of the factorisation kernels, element by element
     (device arrays of n doubles)."""
-    _check(_lib.h2_check_reciprocal(ctx, C.c_void_p(d_dev), int(n), C.c_void_p(precise_dev),
-                                    C.c_void_p(coarse_dev)), ctx)
-
+    _check(_lib.h2_check_reciprocal(ctx, C.c_void_p(d_dev), int(n), C.c_void_p(out_dev)), ctx)

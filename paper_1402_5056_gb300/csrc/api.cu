@@ -2415,13 +2415,12 @@ extern "C" h2_status h2_block_to_dense(h2_ctx* ctx, const h2_matrix* Z, int64_t 
   });
 }
 
-extern "C" h2_status h2_check_reciprocal(h2_ctx* ctx, const double* d, int64_t n, double* precise,
-                                         double* coarse) {
+extern "C" h2_status h2_check_reciprocal(h2_ctx* ctx, const double* d, int64_t n, double* out) {
   using namespace h2;
-  if (!ctx || n < 0 || (n > 0 && (!d || !precise || !coarse))) return H2_EINVAL;
+  if (!ctx || n < 0 || (n > 0 && (!d || !out))) return H2_EINVAL;
   return guard(ctx, [&] {
     DeviceGuard g(ctx->device);
-    launch_recip_check(d, n, precise, coarse, ctx->stream);
+    launch_recip_check(d, n, out, ctx->stream);
     H2_CUDA(cudaGetLastError());
   });
 }

@@ -108,7 +108,7 @@ void launch_gram_weights(const Pipeline& P, int level);                  // W_t,
 void launch_gram_certify(const Pipeline& P);                             // certificate, R_t
 void launch_gram_outputs(const Pipeline& P);                             // new bases, marks
 void launch_copy(const CopyDesc* d, int n, cudaStream_t st);
-void launch_recip_check(const double* d, int64_t n, double* precise, double* coarse, cudaStream_t st);
+void launch_recip_check(const double* d, int64_t n, double* out, cudaStream_t st);
 void launch_near_add(const NearDesc* d, int n, int u, cudaStream_t st);
 
 }  // namespace h2

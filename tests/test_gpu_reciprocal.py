@@ -1,12 +1,9 @@
-"""The float64 pivot reciprocals of the factorisation kernels against CUDA's
+"""The float64 pivot reciprocal of the factorisation kernels against CUDA's
 correctly rounded quotient.
 
 The kernels form 1/d from the PTX estimate rcp.approx.ftz.f64 refined by a
-Newton-Raphson step (cubic for the factorisations, quadratic where the
-result only decides the certificate, whose margin delta covers the error).
-Their stated bounds are checked here over normal d spanning the exponent
-range: the cubic form within one ulp of 1/d, the quadratic form within a
-relative 2^-43.
+cubic Newton-Raphson step.  The stated bound is checked here over normal d
+spanning the exponent range: every result within one ulp of 1/d.
 """
 import numpy as np
 import pytest
@@ -32,18 +29,15 @@ def test_reciprocals_within_their_bounds():
     dd = torch.from_numpy(d).cuda()
     quot = (1.0 / dd).cpu().numpy()                         # CUDA's IEEE division
     pr = torch.empty_like(dd)
-    co = torch.empty_like(dd)
     ctx = b.h2_ctx_create(0, torch.cuda.current_stream().cuda_stream)
     try:
-        b.h2_check_reciprocal(ctx, dd.data_ptr(), len(d), pr.data_ptr(), co.data_ptr())
+        b.h2_check_reciprocal(ctx, dd.data_ptr(), len(d), pr.data_ptr())
         b.h2_ctx_synchronize(ctx)
     finally:
         b.h2_ctx_destroy(ctx)
-    pr, co = pr.cpu().numpy(), co.cpu().numpy()
+    pr = pr.cpu().numpy()
     np.testing.assert_array_equal(quot, 1.0 / d)           # host and device agree on 1/d
     ulp = np.spacing(np.abs(quot))
     assert np.all(np.abs(pr - quot) <= ulp), float(np.max(np.abs(pr - quot) / ulp))
-    rel = np.abs(co - quot) / quot
-    assert np.all(rel <= 2.0 ** -43), float(rel.max())
     # most of the cubic form's results are the correctly rounded quotient
     assert np.mean(pr == quot) > 0.9
