@@ -1,0 +1,74 @@
+// Internal declarations of the H^2-LR factorisation path (lr.cu, lr_kernels.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace h2 {
+
+// One cluster basis seen from a kernel (device pointers; tree order).
+struct BasisView {
+  const int64_t* off;        // cluster offsets
+  const int32_t* size;       // cluster sizes
+  const int32_t* rank;       // ranks
+  const int32_t* subtree;    // #T_c; the sons of c are c + 1 and c + 1 + subtree[c + 1]
+  const double* leaf;        // leaf slots (size_t x kcap, ld size_t)
+  const int64_t* leaf_off;   // per cluster, element offset of its leaf slot
+  const double* transfer;    // kcap x kcap slots per cluster
+};
+
+// Y += alpha op(Z|_b) X for one block b of the block tree, op = identity
+// (trans = 0: X on the columns of b, Y on its rows) or transpose (trans = 1).
+// "in" is the side of X, "out" the side of Y.
+struct BlockProd {
+  BasisView in, out;
+  int kcap;
+  int trans;
+  int64_t in_off0, out_off0;  // tree offsets of b's X-side and Y-side clusters
+  const double* S;            // couplings, kcap x kcap slots
+  const double* N;            // nearfield blocks
+  const int64_t* near_off;    // per nearfield slot
+  int m;                      // columns of X and Y
+  double alpha;
+  const double* X;
+  int64_t ldx;
+  double* Y;
+  int64_t ldy;
+  double* xh;                 // per X-side cluster kcap x m (ld kcap)
+  double* yh;                 // per Y-side cluster kcap x m
+};
+
+// forward transformation: xh_c for the X-side clusters of `list`
+void launch_bp_forward(const BlockProd& a, const int32_t* list, int n, cudaStream_t st);
+// couplings: yh_c = sum_e S_e xh_{in_e} (or S_e^* xh) for the Y-side clusters
+// of `list` with entries ptr[i]..ptr[i+1] (pairs slot, X-side cluster)
+void launch_bp_coupling(const BlockProd& a, const int32_t* list, int n, const int32_t* ptr,
+                        const int32_t* ent, cudaStream_t st);
+// backward transformation: yh_c += E_c yh_father for the clusters of `list`
+void launch_bp_backward(const BlockProd& a, const int32_t* list, const int32_t* fathers, int n,
+                        cudaStream_t st);
+// leaves of the Y side: Y|_l += alpha (V_l yh_l + nearfield rows), near
+// entries ptr[i]..ptr[i+1] of (nearfield slot, X-side cluster, Y-side cluster)
+void launch_bp_leaves(const BlockProd& a, const int32_t* leaves, int n, const int32_t* ptr, const int32_t* ent,
+                      cudaStream_t st);
+// yh_c = identity (k x k, ld kcap), for the expansion of a basis
+void launch_identity(double* yh, int k, int kcap, cudaStream_t st);
+
+// C = alpha op(A) op(B) + beta C (C is m x n; C not read when beta = 0)
+void launch_gemm(int m, int n, int k, double alpha, const double* A, int64_t lda, int ta, const double* B,
+                 int64_t ldb, int tb, double beta, double* C, int64_t ldc, cudaStream_t st);
+// in-place LU without pivoting (Doolittle) of the m x m block A (ld lda);
+// a zero pivot sets bit 8 of *err
+void launch_leaf_lu(double* A, int m, int64_t lda, int* err, cudaStream_t st);
+// triangular solves with the factor F (m x m, ld ldf):
+//   kind 0: X <- L^-1 X  (L unit lower in F, X m x n)
+//   kind 1: X <- R^-1 X  (R upper with the diagonal in F, X m x n)
+//   kind 2: X <- X R^-1  (X n x m)
+void launch_trsm(int kind, const double* F, int m, int64_t ldf, double* X, int n, int64_t ldx, cudaStream_t st);
+// vectors of the conjugate gradients
+void launch_dot(const double* x, const double* y, int64_t n, double* partial, double* out, cudaStream_t st);
+void launch_axpby(int64_t n, double a, const double* x, double b, double* y, cudaStream_t st);
+constexpr int kDotBlocks = 608;
+
+}  // namespace h2

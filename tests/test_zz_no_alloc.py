@@ -80,8 +80,11 @@ def test_noalloc_subdivided_block_and_exact_path(ctx):
     sub = [c for c in range(1, bt.n_blocks) if bt.kind[c] == BlockTree.SUB]
     blocks, A, B = draw_updates(Zo, st, 1, u)
     rng = np.random.default_rng(seed)
-    c = sub[len(sub) // 2]
-    assert any(bt.kind[x] == BlockTree.NEAR for x in bt.descendants(c))
+    # a subdivided block with admissible and nearfield leaves below it
+    def count(c, kind):
+        return sum(bt.kind[x] == kind for x in bt.descendants(c))
+    c = next(c for c in sub if count(c, BlockTree.NEAR) >= 4 and count(c, BlockTree.ADM) >= 4
+             and Zo.V.tree.size[bt.row[c]] <= 72)
     cases = [(c, rng.standard_normal((Zo.V.tree.size[bt.row[c]], u)),
               rng.standard_normal((Zo.W.tree.size[bt.col[c]], u)), 1e-8),
              (blocks[0], A[0], B[0], 0.5)]
