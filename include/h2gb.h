@@ -358,6 +358,87 @@ h2_status h2_lowrank_update(h2_ctx* ctx, h2_matrix* Z, int64_t block, int u, con
 h2_status h2_lowrank_update_noalloc(h2_ctx* ctx, h2_matrix* Z, int64_t block, int u, const double* A,
                                     int64_t lda, const double* B, int64_t ldb, double eps);
 
+/* ------------------------------------------------ H^2-LR (Section 3, 7) */
+
+/* Arithmetic of the factorisation.  H2_FP64: every step in float64. */
+typedef enum { H2_FP64 = 0, H2_MIXED_FP32 = 1 } h2_precision;
+
+/* Options of the FEM matrix and its factorisation.
+ *  eps       block-relative truncation accuracy of every local update
+ *            (Sections 4, 5 and 7; the rank rule of h2_batch_execute) and
+ *            of the temporaries of the product (see h2_lr_factor);
+ *  eta       admissibility parameter, max(diam t, diam s) <= eta dist(t, s);
+ *  leaf_size clusters with more points are split;
+ *  precision h2_precision;
+ *  trunc_norm, weighting, max_rank: 0 (Frobenius norm, block-relative
+ *            weights, no rank cap) -- the only supported values. */
+typedef struct {
+  double eps;
+  double eta;
+  int leaf_size;
+  int precision;
+  int trunc_norm;
+  int weighting;
+  int max_rank;
+} h2_options;
+
+/* The P1 finite-element stiffness matrix of -div(sigma grad u) = f on the
+ * unit square (dim 2) or cube (dim 3) with u = 0 on the boundary (the model
+ * problem of Section 7), as an H^2 matrix.  `cells` cells per side; every
+ * cell split into two triangles along its (i,j)-(i+1,j+1) diagonal (2D) or
+ * into Kuhn's six tetrahedra around its main diagonal (3D); the unknowns
+ * are the interior nodes (i/cells, j/cells[, k/cells]), numbered x fastest
+ * (h2_tree_permutation maps tree positions to these numbers).  sigma (host,
+ * checker^dim positive values, x fastest) is piecewise constant on a
+ * checker x checker (x checker) grid; an element takes the value at its
+ * centroid.  Cluster tree and block tree as in h2_matrix_create with the
+ * points' support boxes (padding 1/cells): every admissible block of the
+ * stiffness matrix is then zero, the bases have rank 0 and the nonzeros
+ * sit in the inadmissible leaves.  Uses opt->leaf_size and opt->eta. */
+h2_status h2_build_fem(h2_ctx* ctx, int dim, int64_t cells, int64_t checker, const double* sigma,
+                       const h2_options* opt, h2_matrix** out);
+
+/* In-place H^2-LR factorisation Z = L R (Section 3): on return the
+ * strictly lower part of Z holds L (unit diagonal implied) and the upper
+ * part R, as one H^2 matrix sharing its cluster bases.  Recursion: a leaf
+ * (t, t) by Gaussian elimination without pivoting; otherwise factorise
+ * (t1, t1), solve L11 R12 = A12 and L21 R11 = A21 by block forward
+ * substitution, A22 <- A22 - L21 R12 by the product recursion (Section 3,
+ * Cases 1 and 2 of Section 6), factorise (t2, t2).  Low-rank terms enter Z
+ * through the local low-rank update with accuracy opt->eps.  Readings of
+ * what the paper leaves open: a product's terms are computed from the
+ * matrix as it is when the product starts; an admissible target of two
+ * subdivided factors receives up to four temporaries, each the stacked
+ * terms below it truncated by SVD (sum of the discarded sigma_i^2 <=
+ * (eps/2)^2 of the total) and added by one update; forward substitution on
+ * an admissible leaf V_t S W_s^* replaces it by (L^-1 V_t S) W_s^* through
+ * an update; updates are applied in column groups of at most 32 - (largest
+ * rank in the two subtrees) columns.  Z must be square with one tree and
+ * its LU without pivoting must exist (SPD matrices).  stats (host, 3
+ * entries, optional): local updates, products, largest rank.
+ * Synchronizes. */
+h2_status h2_lr_factor(h2_ctx* ctx, h2_matrix* Z, const h2_options* opt, int64_t* stats);
+
+/* X <- R^-1 L^-1 X for a factor from h2_lr_factor: block forward and
+ * backward substitution (Section 3).  X: DEVICE n x nrhs, column-major, ld
+ * ldx, rows in TREE order.  Synchronizes. */
+h2_status h2_lr_solve(h2_ctx* ctx, const h2_matrix* LR, int64_t nrhs, double* X, int64_t ldx);
+
+/* Conjugate gradients for A x = b preconditioned by the factor LR (NULL =
+ * none), from x = 0, stopped when ||b - A x||_2 <= tol ||b||_2 (the
+ * recursively updated residual) or after maxit steps (Section 7).  A: the
+ * matrix (not factorised; applied by h2_matvec); b, x: DEVICE vectors in
+ * tree order.  iterations, relres (host, optional): steps taken, final
+ * relative residual.  Synchronizes. */
+h2_status h2_pcg(h2_ctx* ctx, const h2_matrix* A, const h2_matrix* LR, const double* b, double* x, double tol,
+                 int maxit, int* iterations, double* relres);
+
+/* ||I - LR^-1 A||_2 estimated by the power iteration (Section 7, column
+ * Err): iters steps v <- w / ||w||, w = v - LR^-1 A v, from the DEVICE
+ * start vector v (n entries, tree order; overwritten); err (host) = the
+ * last ||w||.  Synchronizes. */
+h2_status h2_lr_error(h2_ctx* ctx, const h2_matrix* A, const h2_matrix* LR, double* v, int iters, double* err);
+
 /* ----------------------------------------------------------- diagnostics */
 
 /* The float64 reciprocal the factorisation kernels use for their pivots

@@ -34,6 +34,7 @@ EXPORTS = [
     "h2_batch_update_items", "h2_batch_set_mode", "h2_batch_paths", "h2_lowrank_update",
     "h2_lowrank_update_noalloc", "h2_lowrank_update_sequence", "h2_matvec", "h2_block_to_dense",
     "h2_sequence_waves", "h2_check_reciprocal",
+    "h2_build_fem", "h2_lr_factor", "h2_lr_solve", "h2_pcg", "h2_lr_error",
 ]
 
 PHASES = ("base_weights", "rfactor", "norms", "weights", "truncate", "reproject", "exact", "bases")
@@ -101,6 +102,21 @@ _sig("h2_batch_result_size", _int, _p, _p)
 _sig("h2_sequence_waves", _int, _p, _i64, _p, _p, _p)
 _sig("h2_block_to_dense", _int, _p, _p, _i64, _p, _i64)
 _sig("h2_check_reciprocal", _int, _p, _p, _i64, _p)
+
+
+class Options(C.Structure):
+    """h2_options of include/h2gb.h."""
+    _fields_ = [("eps", C.c_double), ("eta", C.c_double), ("leaf_size", C.c_int), ("precision", C.c_int),
+                ("trunc_norm", C.c_int), ("weighting", C.c_int), ("max_rank", C.c_int)]
+
+
+FP64, MIXED_FP32 = 0, 1
+
+_sig("h2_build_fem", _int, _p, _int, _i64, _i64, _p, C.POINTER(Options), _pp)
+_sig("h2_lr_factor", _int, _p, _p, C.POINTER(Options), _p)
+_sig("h2_lr_solve", _int, _p, _p, _i64, _p, _i64)
+_sig("h2_pcg", _int, _p, _p, _p, _p, _p, _dbl, _int, _p, _p)
+_sig("h2_lr_error", _int, _p, _p, _p, _p, _int, _p)
 _sig("h2_matvec", _int, _p, _p, _i64, _dbl, _p, _i64, _dbl, _p, _i64)
 _sig("h2_lowrank_update_sequence", _int, _p, _p, _i64, _p, _int, _p, _p, _dbl, _p)
 _sig("h2_batch_result_offsets", _int, _p, _p, _p)
@@ -471,3 +487,44 @@ def h2_check_reciprocal(ctx, d_dev: int, n: int, out_dev: int):
     """The pivot reciprocal of the factorisation kernels, element by element
     (device arrays of n doubles)."""
     _check(_lib.h2_check_reciprocal(ctx, C.c_void_p(d_dev), int(n), C.c_void_p(out_dev)), ctx)
+
+
+def options(eps=1e-4, eta=2.0, leaf_size=32, precision=0):
+    return Options(float(eps), float(eta), int(leaf_size), int(precision), 0, 0, 0)
+
+
+def h2_build_fem(ctx, dim: int, cells: int, checker: int, sigma, opt):
+    """P1 FEM stiffness matrix on the unit square/cube as an H^2 matrix."""
+    sg = np.ascontiguousarray(sigma, dtype=np.float64)
+    assert sg.size == checker ** dim
+    out = C.c_void_p()
+    _check(_lib.h2_build_fem(ctx, int(dim), int(cells), int(checker), sg.ctypes.data, C.byref(opt), C.byref(out)),
+           ctx)
+    return out
+
+
+def h2_lr_factor(ctx, Z, opt):
+    """In-place H^2-LR; returns (updates, products, largest rank)."""
+    st = np.zeros(3, dtype=np.int64)
+    _check(_lib.h2_lr_factor(ctx, Z, C.byref(opt), st.ctypes.data), ctx)
+    return {"updates": int(st[0]), "products": int(st[1]), "max_rank": int(st[2])}
+
+
+def h2_lr_solve(ctx, LR, nrhs: int, X_dev: int, ldx: int):
+    _check(_lib.h2_lr_solve(ctx, LR, int(nrhs), C.c_void_p(X_dev), int(ldx)), ctx)
+
+
+def h2_pcg(ctx, A, LR, b_dev: int, x_dev: int, tol: float, maxit: int):
+    """Preconditioned CG; returns (iterations, relative residual)."""
+    it = C.c_int(0)
+    rr = C.c_double(0.0)
+    _check(_lib.h2_pcg(ctx, A, LR, C.c_void_p(b_dev), C.c_void_p(x_dev), float(tol), int(maxit), C.byref(it),
+                       C.byref(rr)), ctx)
+    return it.value, rr.value
+
+
+def h2_lr_error(ctx, A, LR, v_dev: int, iters: int):
+    err = C.c_double(0.0)
+    _check(_lib.h2_lr_error(ctx, A, LR, C.c_void_p(v_dev), int(iters), C.byref(err)), ctx)
+    return err.value
+

@@ -22,7 +22,8 @@ LIB = os.path.join(HERE, "libh2gb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
           "-Xcompiler", "-fno-strict-aliasing", "-I", os.path.join(HERE, "..", "include")]
-SOURCES = ["tree.cpp", "api.cu", "update_kernels.cu", "gram_kernels.cu", "noalloc.cu", "matvec.cu"]
+SOURCES = ["tree.cpp", "api.cu", "update_kernels.cu", "gram_kernels.cu", "noalloc.cu", "matvec.cu", "lr.cu",
+           "lr_kernels.cu"]
 
 
 def nvcc() -> str:

@@ -218,6 +218,7 @@ static void check_device_error(h2_ctx* ctx) {
     if (e & kErrCols) m += " more than 32 columns (k + u > 32);";
     if (e & kErrJacobi) m += " one-sided Jacobi did not converge;";
     if (e & kErrRank) m += " inconsistent ranks;";
+    if (e & kErrPivot) m += " zero pivot in a leaf LU;";
     throw Error(H2_EDEVICE, m);
   }
 }

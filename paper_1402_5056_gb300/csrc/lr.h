@@ -58,6 +58,10 @@ void launch_identity(double* yh, int k, int kcap, cudaStream_t st);
 // C = alpha op(A) op(B) + beta C (C is m x n; C not read when beta = 0)
 void launch_gemm(int m, int n, int k, double alpha, const double* A, int64_t lda, int ta, const double* B,
                  int64_t ldb, int tb, double beta, double* C, int64_t ldc, cudaStream_t st);
+// B (n x m) = alpha A^* (A m x n); A = identity (n x n)
+void launch_transpose(int m, int n, double alpha, const double* A, int64_t lda, double* B, int64_t ldb,
+                      cudaStream_t st);
+void launch_eye(double* A, int n, int64_t lda, cudaStream_t st);
 // in-place LU without pivoting (Doolittle) of the m x m block A (ld lda);
 // a zero pivot sets bit 8 of *err
 void launch_leaf_lu(double* A, int m, int64_t lda, int* err, cudaStream_t st);
@@ -66,6 +70,12 @@ void launch_leaf_lu(double* A, int m, int64_t lda, int* err, cudaStream_t st);
 //   kind 1: X <- R^-1 X  (R upper with the diagonal in F, X m x n)
 //   kind 2: X <- X R^-1  (X n x m)
 void launch_trsm(int kind, const double* F, int m, int64_t ldf, double* X, int n, int64_t ldx, cudaStream_t st);
+// truncation of a factor pair from its Gram matrices (m <= 256; scratch of
+// 6 m*m doubles): TA, TB (m x m, first *rank columns) with A' = A TA,
+// B' = B TB the truncated pair; *rank written on the device
+void launch_compress(const double* GA, const double* GB, int m, double eps, double* scratch, double* TA,
+                     double* TB, int* rank, cudaStream_t st);
+constexpr int kCompressMax = 256;
 // vectors of the conjugate gradients
 void launch_dot(const double* x, const double* y, int64_t n, double* partial, double* out, cudaStream_t st);
 void launch_axpby(int64_t n, double a, const double* x, double b, double* y, cudaStream_t st);

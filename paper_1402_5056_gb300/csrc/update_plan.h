@@ -17,6 +17,7 @@ constexpr int kErrRows = 1;      // a matrix has more rows than the kernel's reg
 constexpr int kErrCols = 2;      // more than 32 columns
 constexpr int kErrJacobi = 4;    // one-sided Jacobi did not converge in the sweep limit
 constexpr int kErrRank = 8;      // inconsistent ranks
+constexpr int kErrPivot = 256;   // zero pivot in a leaf LU (H^2-LR)
 
 // One cluster of one side of one update ("cluster task").
 struct Item {

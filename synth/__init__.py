@@ -156,3 +156,20 @@ def update_factors(rng: np.random.Generator, row_sizes, col_sizes, u: int):
         A.append(np.asfortranarray(rng.standard_normal((mt, u))))
         B.append(np.asfortranarray(rng.standard_normal((ms, u))))
     return A, B
+
+
+# ------------------------------------------------------------ FEM problems
+# Recipe of the finite-element problems (Section 7's model problem with a
+# variable coefficient): seed = SEED_BASE + config index, the streams of
+# ``streams(seed)``; sigma = 10^U(-2, 2) on an M^dim checkerboard (x
+# fastest) from the "sigma" stream, right-hand sides N(0, 1) from the "rhs"
+# stream in the unknowns' original order (interior nodes, x fastest).
+
+def checker_sigma(rng: np.random.Generator, M: int, dim: int, decades=(-2.0, 2.0)) -> np.ndarray:
+    """Checkerboard coefficients 10^U(lo, hi), M^dim values, x fastest."""
+    return 10.0 ** rng.uniform(decades[0], decades[1], M ** dim)
+
+
+def fem_rhs(rng: np.random.Generator, n: int, nrhs: int = 1) -> np.ndarray:
+    """N(0, 1) right-hand sides, n x nrhs (column-major order of draws)."""
+    return rng.standard_normal((nrhs, n)).T.copy()

@@ -1,0 +1,160 @@
+"""Parity of the CUDA H^2-LR path with the CPU oracle (Sections 3 and 7).
+
+* the FEM matrix: the library's cluster and block trees equal the oracle's,
+  its nearfield leaves equal the oracle's assembly (2D and 3D);
+* the factorisation at eps = 0 equals the oracle's and dense Doolittle LU,
+  per assembled block;
+* the factorisation of the 32 x 32-cell problem (n = 961, sigma on a 4 x 4
+  checkerboard over four decades, leaf 32, eta 2, eps = 1e-4): per-block
+  parity with the oracle's factor at 1e-10, equal ranks, ||A - LR|| small,
+  conjugate-gradient steps to 1e-10 within one of the oracle's, the
+  block substitutions and the power-iteration error against the oracle's.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1402_5056_gb300 import binding as b  # noqa: E402
+
+import synth  # noqa: E402
+from blockwise import assert_blockwise_dense, blockwise_dense  # noqa: E402
+from libside import to_oracle  # noqa: E402
+from oracle.fem import h2_from_sparse, stiffness  # noqa: E402
+from oracle.lr import lr_factor, lr_solve, lu_doolittle, pcg, power_error  # noqa: E402
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = b.h2_ctx_create(0, torch.cuda.current_stream().cuda_stream)
+    yield c
+    b.h2_ctx_destroy(c)
+
+
+def _problem(dim, N, M, seed, leaf, eta=2.0):
+    st = synth.streams(seed)
+    sigma = synth.checker_sigma(st["sigma"], M, dim)
+    K, pts = stiffness(N, dim, sigma, M)
+    Zo = h2_from_sparse(K, pts, leaf, eta, 1.0 / N)
+    return sigma, K, Zo, st
+
+
+def _lib(ctx, dim, N, M, sigma, leaf, eps, eta=2.0):
+    return b.h2_build_fem(ctx, dim, N, M, sigma, b.options(eps=eps, eta=eta, leaf_size=leaf))
+
+
+@pytest.mark.parametrize("dim,N,M,leaf", [(2, 32, 4, 32), (2, 20, 4, 8), (3, 8, 2, 64), (3, 10, 2, 16)])
+def test_fem_matrix_matches_oracle(ctx, dim, N, M, leaf):
+    sigma, K, Zo, _ = _problem(dim, N, M, synth.SEED_BASE + 10 + N, leaf)
+    Z = _lib(ctx, dim, N, M, sigma, leaf, 1e-4)
+    try:
+        tb = b.h2_tree_blocks(Z)
+        assert list(tb["row"]) == Zo.blocks.row and list(tb["col"]) == Zo.blocks.col
+        assert list(tb["kind"]) == Zo.blocks.kind
+        np.testing.assert_array_equal(b.h2_tree_permutation(Z), Zo.V.tree.perm)
+        assert max(b.h2_get_ranks(Z, 0)) == 0 and max(b.h2_get_ranks(Z, 1)) == 0
+        got = to_oracle(ctx, Z, Zo)
+        worst, where = blockwise_dense(got.dense(), Zo.dense(), Zo.blocks, Zo.V.tree, Zo.W.tree)
+        assert worst <= 1e-13, (where, worst)
+    finally:
+        b.h2_matrix_free(Z)
+
+
+def _factor_both(ctx, dim, N, M, leaf, eps, seed):
+    sigma, K, Zo, st = _problem(dim, N, M, seed, leaf)
+    A = Zo.copy()
+    info_o = lr_factor(Zo, eps)
+    Z = _lib(ctx, dim, N, M, sigma, leaf, eps)
+    info = b.h2_lr_factor(ctx, Z, b.options(eps=eps, leaf_size=leaf))
+    return Z, Zo, A, K, info, info_o, st
+
+
+@pytest.mark.parametrize("N,leaf", [(16, 16), (20, 8)])
+def test_lr_without_truncation_is_dense_lu(ctx, N, leaf):
+    Z, Zo, A, K, info, info_o, _ = _factor_both(ctx, 2, N, 4, leaf, 0.0, synth.SEED_BASE + 20 + N)
+    try:
+        got = to_oracle(ctx, Z, Zo).dense()
+        bt, tr = Zo.blocks, Zo.V.tree
+        assert_blockwise_dense(got, Zo.dense(), bt, tr, tr, TOL, "oracle")
+        assert_blockwise_dense(got, lu_doolittle(A.dense()), bt, tr, tr, TOL, "dense LU")
+        assert info["updates"] == info_o["updates"]
+        assert info["max_rank"] == info_o["max_rank"]
+    finally:
+        b.h2_matrix_free(Z)
+
+
+@pytest.fixture(scope="module")
+def config0(ctx):
+    """The 32 x 32-cell problem factorised by both sides at eps = 1e-4."""
+    Z, Zo, A, K, info, info_o, st = _factor_both(ctx, 2, 32, 4, 32, 1e-4, synth.SEED_BASE + 0)
+    Za = _lib(ctx, 2, 32, 4, synth.checker_sigma(synth.streams(synth.SEED_BASE + 0)["sigma"], 4, 2), 32, 1e-4)
+    yield Z, Zo, A, K, info, info_o, st, Za
+    b.h2_matrix_free(Z)
+    b.h2_matrix_free(Za)
+
+
+def test_lr_factor_matches_oracle(ctx, config0):
+    Z, Zo, A, K, info, info_o, _, _ = config0
+    got = to_oracle(ctx, Z, Zo)
+    bt, tr = Zo.blocks, Zo.V.tree
+    assert list(got.V.rank) == list(Zo.V.rank)
+    assert list(got.W.rank) == list(Zo.W.rank)
+    assert info["updates"] == info_o["updates"]
+    assert_blockwise_dense(got.dense(), Zo.dense(), bt, tr, tr, TOL, "factor")
+    # the factor reproduces A to about the truncation accuracy
+    D = got.dense()
+    n = D.shape[0]
+    Lm, Rm = np.tril(D, -1) + np.eye(n), np.triu(D)
+    Ad = A.dense()
+    assert np.linalg.norm(Ad - Lm @ Rm) <= 1e-6 * np.linalg.norm(Ad)
+
+
+def test_lr_solve_matches_oracle(ctx, config0):
+    Z, Zo, A, K, info, info_o, st, _ = config0
+    n = K.shape[0]
+    perm = Zo.V.tree.perm
+    rhs = synth.fem_rhs(np.random.default_rng(5), n, 3)[perm]
+    X = torch.from_numpy(np.asfortranarray(rhs).ravel(order="F")).cuda()
+    b.h2_lr_solve(ctx, Z, 3, X.data_ptr(), n)
+    got = X.cpu().numpy().reshape((n, 3), order="F")
+    want = lr_solve(Zo, rhs)
+    assert np.linalg.norm(got - want) <= TOL * np.linalg.norm(want)
+
+
+def test_pcg_iterations_match_oracle(ctx, config0):
+    Z, Zo, A, K, info, info_o, st, Za = config0
+    n = K.shape[0]
+    perm = Zo.V.tree.perm
+    Kp = K[perm][:, perm].tocsr()
+    rhs = synth.fem_rhs(st["rhs"], n)[:, 0][perm]
+    x_o, it_o = pcg(lambda v: Kp @ v, rhs, lambda r: lr_solve(Zo, r), 1e-10)
+    bd = torch.from_numpy(rhs.copy()).cuda()
+    xd = torch.zeros(n, dtype=torch.float64, device="cuda")
+    it, rr = b.h2_pcg(ctx, Za, Z, bd.data_ptr(), xd.data_ptr(), 1e-10, 200)
+    assert rr <= 1e-10
+    assert abs(it - it_o) <= 1, (it, it_o)
+    x = xd.cpu().numpy()
+    assert np.linalg.norm(Kp @ x - rhs) <= 1e-9 * np.linalg.norm(rhs)
+    # without a preconditioner CG needs many more steps
+    xd.zero_()
+    it0, rr0 = b.h2_pcg(ctx, Za, None, bd.data_ptr(), xd.data_ptr(), 1e-10, 2000)
+    assert it0 > 10 * it and rr0 <= 1e-10
+
+
+def test_power_error_matches_oracle(ctx, config0):
+    Z, Zo, A, K, info, info_o, st, Za = config0
+    n = K.shape[0]
+    perm = Zo.V.tree.perm
+    Kp = K[perm][:, perm].tocsr()
+    want = power_error(lambda v: Kp @ v, lambda r: lr_solve(Zo, r), n, 20, seed=3)
+    v0 = np.random.default_rng(3).standard_normal(n)
+    vd = torch.from_numpy(v0).cuda()
+    got = b.h2_lr_error(ctx, Za, Z, vd.data_ptr(), 20)
+    assert abs(got - want) <= 1e-6 * max(want, 1e-12) + 1e-14, (got, want)
+    assert want < 1e-2
