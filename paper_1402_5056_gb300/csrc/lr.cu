@@ -129,7 +129,9 @@ struct Lr {
   size_t lcap = 0;
   double* dscratch = nullptr;     // compression scratch
   int* drank = nullptr;
+  int64_t* dnear_off = nullptr;   // per nearfield slot, offset in Z->d_N
   ~Lr() {
+    if (dnear_off) cudaFree(dnear_off);
     if (xh) cudaFree(xh);
     if (yh) cudaFree(yh);
     if (dlist) cudaFree(dlist);
@@ -137,6 +139,16 @@ struct Lr {
     if (drank) cudaFree(drank);
   }
 };
+
+// per-slot offsets of the nearfield blocks on the device (once per driver)
+const int64_t* near_offsets(Lr& L) {
+  if (!L.dnear_off && !L.Z->near_off.empty()) {
+    const size_t n = L.Z->near_off.size();
+    H2_CUDA(cudaMalloc(&L.dnear_off, n * sizeof(int64_t)));
+    H2_CUDA(cudaMemcpy(L.dnear_off, L.Z->near_off.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice));
+  }
+  return L.dnear_off;
+}
 
 void ensure_work(Lr& L, int m) {
   const size_t need = (size_t)L.Z->rows.count() * L.Z->kcap * std::max(m, 1);
@@ -223,7 +235,7 @@ void block_prod(Lr& L, int32_t b, int trans, double alpha, const double* X, int6
   }
   if (adm.empty() && near.empty()) return;
   ensure_work(L, m);
-  BlockProd a;
+  BlockProd a{};
   a.in = view(Z, in_side);
   a.out = view(Z, out_side);
   a.kcap = Z->kcap;
@@ -232,6 +244,7 @@ void block_prod(Lr& L, int32_t b, int trans, double alpha, const double* X, int6
   a.out_off0 = tout.off[cout];
   a.S = Z->d_S;
   a.N = Z->d_N;
+  a.near_off = near_offsets(L);
   a.m = m;
   a.alpha = alpha;
   a.X = X;
@@ -325,7 +338,7 @@ void expand(Lr& L, int side, int32_t c, double* out, int64_t ld) {
   const int k = (side == 0 ? Z->V : Z->W).rank[c];
   if (k == 0) return;
   ensure_work(L, k);
-  BlockProd a;
+  BlockProd a{};
   a.in = view(Z, side);
   a.out = view(Z, side);
   a.kcap = Z->kcap;
@@ -333,6 +346,7 @@ void expand(Lr& L, int side, int32_t c, double* out, int64_t ld) {
   a.in_off0 = a.out_off0 = ct.off[c];
   a.S = Z->d_S;
   a.N = Z->d_N;
+  a.near_off = near_offsets(L);
   a.m = k;
   a.alpha = 1.0;
   a.X = nullptr;

@@ -31,8 +31,11 @@ def leaf_blocks(bt):
     return sorted(list(bt.admissible) + list(bt.inadmissible))
 
 
-def blockwise_dense(G: np.ndarray, R: np.ndarray, bt, rt, ct, blocks=None):
-    """Worst per-block relative error and the block where it occurs."""
+def blockwise_dense(G: np.ndarray, R: np.ndarray, bt, rt, ct, blocks=None, floor=0.0):
+    """Worst per-block relative error and the block where it occurs.
+    ``floor`` (absolute) is added to every block's norm: blocks whose
+    reference is at the rounding level of the whole matrix (structural
+    zeros computed as +-1e-30) have no relative scale of their own."""
     total = float(np.linalg.norm(R))
     worst, where = 0.0, -1
     for b in (leaf_blocks(bt) if blocks is None else blocks):
@@ -40,7 +43,7 @@ def blockwise_dense(G: np.ndarray, R: np.ndarray, bt, rt, ct, blocks=None):
         r0, c0 = rt.offset[t], ct.offset[s]
         gb = G[r0:r0 + rt.size[t], c0:c0 + ct.size[s]]
         rb = R[r0:r0 + rt.size[t], c0:c0 + ct.size[s]]
-        den = float(np.linalg.norm(rb))
+        den = float(np.linalg.norm(rb)) + floor
         if den == 0.0:
             den = total if total > 0 else 1.0
         e = float(np.linalg.norm(gb - rb)) / den
@@ -49,8 +52,8 @@ def blockwise_dense(G: np.ndarray, R: np.ndarray, bt, rt, ct, blocks=None):
     return worst, where
 
 
-def assert_blockwise_dense(G, R, bt, rt, ct, tol, what=""):
-    worst, where = blockwise_dense(G, R, bt, rt, ct)
+def assert_blockwise_dense(G, R, bt, rt, ct, tol, what="", floor=0.0):
+    worst, where = blockwise_dense(G, R, bt, rt, ct, floor=floor)
     assert worst <= tol, ("per-block relative error", what, where, worst)
     return worst
 

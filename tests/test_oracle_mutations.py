@@ -173,3 +173,31 @@ def test_margin_pin_catches_mutation(name, tmp_path):
     before, after = MARGIN_MUTATIONS[name]
     failed, out = _pins_fail(tmp_path, "update.py", before, after, ["test_oracle_rank_margin.py"])
     assert failed, out
+
+
+LR_MUTATIONS = {
+    "Schur complement added instead of subtracted": (
+        "_mul(C, -1.0, d21, d12, d22)", "_mul(C, 1.0, d21, d12, d22)"),
+    "forward substitution without L21 X1": (
+        "Y2 = Y[n1:] - Z.block_dense(_son(bt, d, t2, t1)) @ X1", "Y2 = Y[n1:]"),
+    "backward substitution without R12 X2": (
+        "Y1 = Y[:n1] - Z.block_dense(_son(bt, d, t1, t2)) @ X2", "Y1 = Y[:n1]"),
+    "low-rank term with the coupling transposed": (
+        'return ("lr", alpha * (Xt @ Z.S[y]), Z.W.dense(r))', 'return ("lr", alpha * (Xt @ Z.S[y].T), Z.W.dense(r))'),
+    "temporaries dropped": (
+        'out.append(("temp", z, temps.get((t1, r1), [])))', 'out.append(("temp", z, []))'),
+    "leaf LU without the division by the pivot": ("A[k + 1:, k] /= A[k, k]", "A[k + 1:, k] *= 1.0"),
+    "right solve with the unit lower factor": (
+        'return solve_triangular(Z.N[d], Y.T, trans="T", lower=False).T',
+        'return solve_triangular(Z.N[d], Y.T, trans="T", lower=True, unit_diagonal=True).T'),
+    "forward substitution on an admissible leaf keeps the old coupling": (
+        "Ws = Z.W.dense(s)\n        Z.S[x] = np.zeros_like(Z.S[x])", "Ws = Z.W.dense(s)"),
+    "conjugate directions not conjugated": ("p = z + (rz_new / rz) * p", "p = z.copy()"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(LR_MUTATIONS))
+def test_lr_pins_catch_mutation(name, tmp_path):
+    before, after = LR_MUTATIONS[name]
+    failed, out = _pins_fail(tmp_path, "lr.py", before, after, ["test_oracle_lr.py"])
+    assert failed, out
