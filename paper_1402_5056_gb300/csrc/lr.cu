@@ -18,8 +18,9 @@
 //  2. a target z that is an admissible leaf while X and Y are subdivided
 //     receives temporaries (t', r') for t' in sons(t), r' in sons(r): the
 //     terms below each are stacked into one factor pair, extended by zeros
-//     to z, truncated to the smallest rank r with sum_{i>r} sigma_i^2 <=
-//     (eps/2)^2 sum sigma_i^2, and added by one local update;
+//     to z, truncated (Householder QR of both factors, SVD of the core) to
+//     the smallest rank r with sum_{i>r} sigma_i^2 <= (eps/2)^2 sum
+//     sigma_i^2, and added by one local update;
 //  3. a dense term P = alpha X Y for a target that is not an inadmissible
 //     leaf becomes the factor pair through its smallest dimension:
 //     (alpha X, Y^*) when the inner cluster is the smallest, else (I, P^*)
@@ -127,15 +128,13 @@ struct Lr {
   size_t wcap = 0;
   int32_t* dlist = nullptr;
   size_t lcap = 0;
-  double* dscratch = nullptr;     // compression scratch
-  int* drank = nullptr;
+  int* drank = nullptr;           // rank of a compressed temporary
   int64_t* dnear_off = nullptr;   // per nearfield slot, offset in Z->d_N
   ~Lr() {
     if (dnear_off) cudaFree(dnear_off);
     if (xh) cudaFree(xh);
     if (yh) cudaFree(yh);
     if (dlist) cudaFree(dlist);
-    if (dscratch) cudaFree(dscratch);
     if (drank) cudaFree(drank);
   }
 };
@@ -644,21 +643,20 @@ void apply_temp(Lr& L, const Temp& tmp) {
                               rr * sizeof(double), T.u, cudaMemcpyDeviceToDevice, L.st));
     c += T.u;
   }
-  DArr GA(m * m, L.st), GB(m * m, L.st), TA(m * m, L.st), TB(m * m, L.st);
-  launch_gemm(m, m, (int)mt, 1.0, A.p, mt, 1, A.p, mt, 0, 0.0, GA.p, m, L.st);
-  launch_gemm(m, m, (int)mr, 1.0, B.p, mr, 1, B.p, mr, 0, 0.0, GB.p, m, L.st);
-  if (!L.dscratch) {
-    H2_CUDA(cudaMalloc(&L.dscratch, 6ull * kCompressMax * kCompressMax * sizeof(double)));
-    H2_CUDA(cudaMalloc(&L.drank, sizeof(int)));
-  }
-  launch_compress(GA.p, GB.p, m, L.eps, L.dscratch, TA.p, TB.p, L.drank, L.st);
+  // Householder QR of both factors, SVD of the core R_A R_B^*, rank rule,
+  // A' = Q_A U_r Sigma_r, B' = Q_B W_r
+  DArr tauA(m, L.st), tauB(m, L.st), C(m * m, L.st), W(m * m, L.st), TA(m * m, L.st), TB(m * m, L.st);
+  if (!L.drank) H2_CUDA(cudaMalloc(&L.drank, sizeof(int)));
+  launch_house_qr(A.p, mt, (int)mt, B.p, mr, (int)mr, m, tauA.p, tauB.p, L.st);
+  const int ka = (int)std::min<int64_t>(mt, m), kb = (int)std::min<int64_t>(mr, m);
+  launch_core_svd(A.p, mt, ka, B.p, mr, kb, m, L.eps, C.p, W.p, TA.p, TB.p, L.drank, L.st);
   int rk = 0;
   H2_CUDA(cudaMemcpyAsync(&rk, L.drank, sizeof(int), cudaMemcpyDeviceToHost, L.st));
   H2_CUDA(cudaStreamSynchronize(L.st));
   if (rk == 0) return;
   DArr A2(mt * rk, L.st), B2(mr * rk, L.st);
-  launch_gemm((int)mt, rk, m, 1.0, A.p, mt, 0, TA.p, m, 0, 0.0, A2.p, mt, L.st);
-  launch_gemm((int)mr, rk, m, 1.0, B.p, mr, 0, TB.p, m, 0, 0.0, B2.p, mr, L.st);
+  launch_apply_q(A.p, mt, (int)mt, tauA.p, TA.p, A2.p, B.p, mr, (int)mr, tauB.p, TB.p, B2.p, m, rk, L.st);
+  H2_CUDA(cudaGetLastError());
   apply_update(L, tmp.z, A2.p, mt, B2.p, mr, rk);
 }
 

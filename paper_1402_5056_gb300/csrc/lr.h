@@ -70,11 +70,18 @@ void launch_leaf_lu(double* A, int m, int64_t lda, int* err, cudaStream_t st);
 //   kind 1: X <- R^-1 X  (R upper with the diagonal in F, X m x n)
 //   kind 2: X <- X R^-1  (X n x m)
 void launch_trsm(int kind, const double* F, int m, int64_t ldf, double* X, int n, int64_t ldx, cudaStream_t st);
-// truncation of a factor pair from its Gram matrices (m <= 256; scratch of
-// 6 m*m doubles): TA, TB (m x m, first *rank columns) with A' = A TA,
-// B' = B TB the truncated pair; *rank written on the device
-void launch_compress(const double* GA, const double* GB, int m, double eps, double* scratch, double* TA,
-                     double* TB, int* rank, cudaStream_t st);
+// truncation of a factor pair (A rows_a x m, B rows_b x m, m <= 256):
+// Householder QR of both in place (tau_a, tau_b: m entries each), the SVD
+// of the core R_A R_B^* by one-sided Jacobi and the rank rule (C, W: m x m
+// scratch; TA, TB: m x m, first r columns; *rank on the device), then
+// A' = Q_A [TA; 0] into OA (rows_a x r), B' = Q_B [TB; 0] into OB
+void launch_house_qr(double* A, int64_t lda, int rows_a, double* B, int64_t ldb, int rows_b, int m, double* tau_a,
+                     double* tau_b, cudaStream_t st);
+void launch_core_svd(const double* A, int64_t lda, int ka, const double* B, int64_t ldb, int kb, int m, double eps,
+                     double* C, double* W, double* TA, double* TB, int* rank, cudaStream_t st);
+void launch_apply_q(const double* A, int64_t lda, int rows_a, const double* tau_a, const double* TA, double* OA,
+                    const double* B, int64_t ldb, int rows_b, const double* tau_b, const double* TB, double* OB,
+                    int m, int r, cudaStream_t st);
 constexpr int kCompressMax = 256;
 // vectors of the conjugate gradients
 void launch_dot(const double* x, const double* y, int64_t n, double* partial, double* out, cudaStream_t st);

@@ -254,173 +254,173 @@ __global__ void k_axpby(int64_t n, double a, const double* x, double b, double* 
 }
 
 // ------------------------------------------------ factor-pair compression
-// Symmetric eigendecomposition A = V diag(w) V^* of an n x n matrix (global
-// scratch, ld n, destroyed: its diagonal ends up as w) by two-sided Jacobi
-// rotations (Golub and Van Loan, the symmetric Schur step) in a round-robin
-// parallel ordering: each step rotates n/2 disjoint pairs at once, which
-// commute.  One thread block; sweeps until the off-diagonal mass is below
-// 1e-30 of the diagonal mass (at most 40 sweeps).
-__device__ void jacobi_eig(double* A, double* V, int n, double* cs, double* sn, int* pp, int* qq) {
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int e = tid; e < n * n; e += nt) V[e] = (e % n == e / n) ? 1.0 : 0.0;
-  __syncthreads();
-  if (n < 2) return;
-  const int n2 = n + (n & 1);
-  __shared__ double red[2];
-  for (int sweep = 0; sweep < 40; ++sweep) {
+// Truncation of a factor pair (A, B) with m columns (m <= 256):
+//  1. Householder QR of A (rows_a x m) and of B, in place, one thread block
+//     per factor: reflection j maps column j below the diagonal to zero
+//     (H = I - tau v v^*, v_j = 1, beta = -sign(alpha) ||x||, the form of
+//     LAPACK's dlarfg); R in the upper triangle, v below it;
+//  2. the core C = R_A R_B^* (ka x kb, ka = min(rows_a, m)), its SVD by
+//     one-sided Jacobi on the columns (C W = U Sigma), the rank r = the
+//     smallest with sum_{i>r} sigma_i^2 <= (eps/2)^2 sum sigma_i^2;
+//  3. A' = Q_A [U_r Sigma_r; 0], B' = Q_B [W_r; 0] by the reflections in
+//     reverse order.
+// A' B'^* is the truncated A B^* (B' has orthonormal columns).
+
+// QR of the rows x m matrix X (ld ldx) in place; tau (m entries).  One block.
+__global__ void k_house_qr(double* XA, int64_t lda, int rows_a, double* XB, int64_t ldb, int rows_b, int m,
+                           double* tau_a, double* tau_b) {
+  double* X = blockIdx.x == 0 ? XA : XB;
+  const int64_t ldx = blockIdx.x == 0 ? lda : ldb;
+  const int rows = blockIdx.x == 0 ? rows_a : rows_b;
+  double* tau = blockIdx.x == 0 ? tau_a : tau_b;
+  __shared__ double red[32];
+  __shared__ double sh_beta, sh_tau, sh_scale;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  const int kk = min(rows, m);
+  for (int j = 0; j < kk; ++j) {
+    double* x = X + j + (int64_t)j * ldx;       // column j from the diagonal down
+    const int len = rows - j;
+    double s = 0.0;
+    for (int i = 1 + tid; i < len; i += nt) s = fma(x[i], x[i], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) red[warp] = s;
+    __syncthreads();
     if (tid == 0) {
-      double off = 0.0, dia = 0.0;
-      for (int j = 0; j < n; ++j)
-        for (int i = 0; i < n; ++i) {
-          const double v = A[i + j * n];
-          if (i == j) dia = fma(v, v, dia); else off = fma(v, v, off);
-        }
-      red[0] = off;
-      red[1] = dia;
+      double sig = 0.0;
+      for (int w = 0; w < nw; ++w) sig += red[w];
+      const double alpha = x[0];
+      if (sig == 0.0) {
+        sh_tau = 0.0;
+        sh_beta = alpha;
+        sh_scale = 0.0;
+      } else {
+        const double nrm = sqrt(fma(alpha, alpha, sig));
+        const double beta = alpha >= 0.0 ? -nrm : nrm;
+        sh_tau = (beta - alpha) / beta;
+        sh_scale = 1.0 / (alpha - beta);
+        sh_beta = beta;
+      }
+      tau[j] = sh_tau;
     }
     __syncthreads();
-    if (!(red[0] > 1e-30 * red[1])) break;
+    const double t = sh_tau;
+    if (t != 0.0)
+      for (int i = 1 + tid; i < len; i += nt) x[i] *= sh_scale;
     __syncthreads();
-    for (int r = 0; r < n2 - 1; ++r) {
-      // pairs of this round: player n2-1 meets r, player i meets (2r - i) mod (n2-1)
-      for (int i = tid; i < n2 / 2; i += nt) {
-        int p, q;
-        if (i == 0) { p = r; q = n2 - 1; }
-        else { p = (r + i) % (n2 - 1); q = (r - i + (n2 - 1)) % (n2 - 1); }
-        if (p > q) { const int t = p; p = q; q = t; }
-        double c = 1.0, s = 0.0;
-        if (q < n) {
-          const double apq = A[p + q * n];
-          if (apq != 0.0) {
-            const double tau = (A[q + q * n] - A[p + p * n]) / (2.0 * apq);
-            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(fma(tau, tau, 1.0)));
-            c = 1.0 / sqrt(fma(t, t, 1.0));
-            s = t * c;
-          }
-        }
-        pp[i] = p; qq[i] = q; cs[i] = c; sn[i] = s;
+    if (tid == 0) x[0] = sh_beta;
+    // apply H to the columns j+1..m-1: one warp per column
+    if (t != 0.0)
+      for (int c = j + 1 + warp; c < m; c += nw) {
+        double* y = X + j + (int64_t)c * ldx;
+        double w = lane == 0 ? y[0] : 0.0;
+        for (int i = 1 + lane; i < len; i += 32) w = fma(x[i], y[i], w);
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+        w *= t;
+        if (lane == 0) y[0] -= w;
+        for (int i = 1 + lane; i < len; i += 32) y[i] = fma(-w, x[i], y[i]);
       }
-      __syncthreads();
-      const int np = n2 / 2;
-      for (int e = tid; e < np * n; e += nt) {          // rows p, q: A <- J^* A
-        const int i = e % np, j = e / np;
-        const int p = pp[i], q = qq[i];
-        if (q >= n) continue;
-        const double a = A[p + j * n], b = A[q + j * n];
-        A[p + j * n] = cs[i] * a - sn[i] * b;
-        A[q + j * n] = sn[i] * a + cs[i] * b;
-      }
-      __syncthreads();
-      for (int e = tid; e < np * n; e += nt) {          // columns p, q: A <- A J, V <- V J
-        const int i = e % np, j = e / np;
-        const int p = pp[i], q = qq[i];
-        if (q >= n) continue;
-        const double a = A[j + p * n], b = A[j + q * n];
-        A[j + p * n] = cs[i] * a - sn[i] * b;
-        A[j + q * n] = sn[i] * a + cs[i] * b;
-        const double va = V[j + p * n], vb = V[j + q * n];
-        V[j + p * n] = cs[i] * va - sn[i] * vb;
-        V[j + q * n] = sn[i] * va + cs[i] * vb;
-      }
-      __syncthreads();
-    }
+    __syncthreads();
   }
 }
 
-// Truncation of the factor pair (A, B), A B^* of rank <= m, from the Gram
-// matrices GA = A^* A and GB = B^* B (m x m): with GA = VA diag(a) VA^*
-// and GB = VB diag(b) VB^* (directions with a_i <= m 2^-52 max a dropped),
-// Q_A = A VA a^-1/2 and Q_B = B VB b^-1/2 are orthonormal and
-// A B^* = Q_A C Q_B^*, C = a^1/2 VA^* VB b^1/2.  The right singular vectors
-// of C are the eigenvectors of C^* C; the rank r is the smallest with
-// sum_{i>r} sigma_i^2 <= (eps/2)^2 sum sigma_i^2, and the truncated pair is
-// A' = A TA, B' = B TB with TA = VA a^-1/2 C VC_r, TB = VB b^-1/2 VC_r (so
-// B' has orthonormal columns and A' = Q_A U_r Sigma_r).  Scratch: 6 m*m
-// doubles.  Writes TA, TB (m x m, ld m; first r columns) and *rank.
-__global__ void k_compress(const double* GA, const double* GB, int m, double eps, double* scratch, double* TA,
-                           double* TB, int* rank) {
-  extern __shared__ double sm[];
-  double* cs = sm;
-  double* sn = sm + 128;
-  int* pp = reinterpret_cast<int*>(sm + 256);
-  int* qq = pp + 128;
-  __shared__ int ka[256], kb[256], order[256];
-  __shared__ int na, nb;
-  double* EA = scratch;
-  double* VA = scratch + m * m;
-  double* EB = scratch + 2 * m * m;
-  double* VB = scratch + 3 * m * m;
-  double* C = scratch + 4 * m * m;
-  double* VC = scratch + 5 * m * m;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int e = tid; e < m * m; e += nt) {
-    EA[e] = GA[e];
-    EB[e] = GB[e];
-  }
-  __syncthreads();
-  jacobi_eig(EA, VA, m, cs, sn, pp, qq);
-  jacobi_eig(EB, VB, m, cs, sn, pp, qq);
-  if (tid == 0) {
-    double amax = 0.0, bmax = 0.0;
-    for (int i = 0; i < m; ++i) {
-      amax = fmax(amax, EA[i + i * m]);
-      bmax = fmax(bmax, EB[i + i * m]);
-    }
-    const double tol = m * 2.220446049250313e-16;
-    int x = 0, y = 0;
-    for (int i = 0; i < m; ++i) {
-      if (EA[i + i * m] > tol * amax) ka[x++] = i;
-      if (EB[i + i * m] > tol * bmax) kb[y++] = i;
-    }
-    na = x;
-    nb = y;
-  }
-  __syncthreads();
-  // C (na x nb, ld m) = a^1/2 VA^* VB b^1/2 on the kept directions
-  for (int e = tid; e < na * nb; e += nt) {
-    const int i = e % na, j = e / na;
-    const int ia = ka[i], jb = kb[j];
+__device__ __forceinline__ int rr_partner(int i, int r, int n2, int& p, int& q) {
+  if (i == 0) { p = r; q = n2 - 1; }
+  else { p = (r + i) % (n2 - 1); q = (r - i + (n2 - 1)) % (n2 - 1); }
+  if (p > q) { const int t = p; p = q; q = t; }
+  return 0;
+}
+
+// Core SVD and rank.  C (ka x kb, ld m, scratch), W (kb x kb, ld m,
+// scratch); writes T = U_r Sigma_r = C W_r (ka x r, ld m) into TA, W_r into
+// TB (kb x r, ld m), the rank into *rank.  One block.
+__global__ void k_core_svd(const double* XA, int64_t lda, int ka, const double* XB, int64_t ldb, int kb, int m,
+                           double eps, double* C, double* W, double* TA, double* TB, int* rank) {
+  __shared__ int order[256];
+  __shared__ double nrm2[256];
+  __shared__ int any_rot;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  // C = R_A R_B^* (upper triangles)
+  for (int e = tid; e < ka * kb; e += nt) {
+    const int i = e % ka, j = e / ka;
     double v = 0.0;
-    for (int q = 0; q < m; ++q) v = fma(VA[q + ia * m], VB[q + jb * m], v);
-    C[i + j * m] = sqrt(EA[ia + ia * m]) * v * sqrt(EB[jb + jb * m]);
+    for (int q = max(i, j); q < m; ++q) v = fma(XA[i + (int64_t)q * lda], XB[j + (int64_t)q * ldb], v);
+    C[i + j * m] = v;
   }
+  for (int e = tid; e < kb * kb; e += nt) W[e % kb + (e / kb) * m] = (e % kb == e / kb) ? 1.0 : 0.0;
   __syncthreads();
-  // CtC (nb x nb, ld nb) in the EA scratch, no longer needed past the diagonal
-  double* wa = TA;   // diagonal of EA kept in TA's first column while EA is reused
-  for (int i = tid; i < na; i += nt) wa[i] = EA[ka[i] + ka[i] * m];
-  __syncthreads();
-  double* M = EA;
-  for (int e = tid; e < nb * nb; e += nt) {
-    const int i = e % nb, j = e / nb;
+  // one-sided Jacobi on the columns of C, round-robin pairs, one warp a pair
+  const int n2 = kb + (kb & 1);
+  const double tol2 = 1e-30;   // (1e-15)^2
+  for (int sweep = 0; sweep < 60 && kb > 1; ++sweep) {
+    if (tid == 0) any_rot = 0;
+    __syncthreads();
+    for (int r = 0; r < n2 - 1; ++r) {
+      for (int i = warp; i < n2 / 2; i += nw) {
+        int p, q;
+        rr_partner(i, r, n2, p, q);
+        if (q >= kb) continue;
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int k = lane; k < ka; k += 32) {
+          const double x = C[k + p * m], y = C[k + q * m];
+          al = fma(x, x, al);
+          be = fma(y, y, be);
+          ga = fma(x, y, ga);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        }
+        if (ga * ga > tol2 * al * be && ga != 0.0) {
+          const double zeta = (be - al) / (2.0 * ga);
+          const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
+          const double c = 1.0 / sqrt(fma(t, t, 1.0)), s = c * t;
+          for (int k = lane; k < ka; k += 32) {
+            const double x = C[k + p * m], y = C[k + q * m];
+            C[k + p * m] = c * x - s * y;
+            C[k + q * m] = s * x + c * y;
+          }
+          for (int k = lane; k < kb; k += 32) {
+            const double x = W[k + p * m], y = W[k + q * m];
+            W[k + p * m] = c * x - s * y;
+            W[k + q * m] = s * x + c * y;
+          }
+          if (lane == 0) any_rot = 1;
+        }
+      }
+      __syncthreads();
+    }
+    if (!any_rot) break;
+    __syncthreads();
+  }
+  // squared column norms = sigma^2, descending order, rank rule
+  for (int j = tid; j < kb; j += nt) {
     double v = 0.0;
-    for (int q = 0; q < na; ++q) v = fma(C[q + i * m], C[q + j * m], v);
-    M[i + j * nb] = v;
+    for (int k = 0; k < ka; ++k) v = fma(C[k + j * m], C[k + j * m], v);
+    nrm2[j] = v;
   }
   __syncthreads();
-  jacobi_eig(M, VC, nb, cs, sn, pp, qq);
   if (tid == 0) {
-    // eigenvalues in descending order, clamped at zero
-    for (int i = 0; i < nb; ++i) order[i] = i;
-    for (int i = 1; i < nb; ++i) {
+    for (int i = 0; i < kb; ++i) order[i] = i;
+    for (int i = 1; i < kb; ++i) {
       const int k = order[i];
-      const double v = M[k + k * nb];
       int j = i - 1;
-      while (j >= 0 && M[order[j] + order[j] * nb] < v) {
+      while (j >= 0 && nrm2[order[j]] < nrm2[k]) {
         order[j + 1] = order[j];
         --j;
       }
       order[j + 1] = k;
     }
     double total = 0.0;
-    for (int i = 0; i < nb; ++i) total += fmax(M[order[i] + order[i] * nb], 0.0);
-    int r = nb;
+    for (int i = 0; i < kb; ++i) total += nrm2[i];
+    int r = kb;
     if (total == 0.0) {
       r = 0;
     } else {
       const double thr = 0.25 * eps * eps * total;
       double tail = 0.0;
-      while (r > 0 && tail + fmax(M[order[r - 1] + order[r - 1] * nb], 0.0) <= thr) {
-        tail += fmax(M[order[r - 1] + order[r - 1] * nb], 0.0);
+      while (r > 0 && tail + nrm2[order[r - 1]] <= thr) {
+        tail += nrm2[order[r - 1]];
         --r;
       }
     }
@@ -428,36 +428,46 @@ __global__ void k_compress(const double* GA, const double* GB, int m, double eps
   }
   __syncthreads();
   const int r = *rank;
-  // TB (m x r) = VB b^-1/2 VC_r ; TA (m x r) = VA a^-1/2 C VC_r
-  for (int e = tid; e < m * r; e += nt) {
-    const int i = e % m, j = e / m;
-    const int cj = order[j];
-    double vb = 0.0;
-    for (int q = 0; q < nb; ++q) vb = fma(VB[i + kb[q] * m] / sqrt(EB[kb[q] + kb[q] * m]), VC[q + cj * nb], vb);
-    TB[i + j * m] = vb;
+  for (int e = tid; e < ka * r; e += nt) TA[e % ka + (e / ka) * m] = C[e % ka + order[e / ka] * m];
+  for (int e = tid; e < kb * r; e += nt) TB[e % kb + (e / kb) * m] = W[e % kb + order[e / kb] * m];
+}
+
+// out (rows x r, ld ldo) = Q [T; 0] with Q = H_0 H_1 ... H_{k-1} stored in X
+// (reflections below the diagonal, tau); T is k x r (ld ldt).  One block
+// per factor (blockIdx 0: A side, 1: B side).
+__global__ void k_apply_q(const double* XA, int64_t lda, int rows_a, const double* tau_a, const double* TA,
+                          double* OA, const double* XB, int64_t ldb, int rows_b, const double* tau_b,
+                          const double* TB, double* OB, int m, int r) {
+  const bool sa = blockIdx.x == 0;
+  const double* X = sa ? XA : XB;
+  const int64_t ldx = sa ? lda : ldb;
+  const int rows = sa ? rows_a : rows_b;
+  const double* tau = sa ? tau_a : tau_b;
+  const double* T = sa ? TA : TB;
+  double* O = sa ? OA : OB;
+  const int k = min(rows, m);
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  for (int e = tid; e < rows * r; e += nt) {
+    const int i = e % rows, c = e / rows;
+    O[i + (int64_t)c * rows] = i < k ? T[i + c * m] : 0.0;
   }
   __syncthreads();
-  // CV = C VC_r (na x r) in the VC-free part of the scratch (EB is free now)
-  double* CV = EB;
-  for (int e = tid; e < na * r; e += nt) {
-    const int i = e % na, j = e / na;
-    const int cj = order[j];
-    double v = 0.0;
-    for (int q = 0; q < nb; ++q) v = fma(C[i + q * m], VC[q + cj * nb], v);
-    CV[i + j * m] = v;
+  for (int j = k - 1; j >= 0; --j) {
+    const double t = tau[j];
+    if (t == 0.0) continue;
+    const double* v = X + j + (int64_t)j * ldx;   // v_0 = 1 implied
+    const int len = rows - j;
+    for (int c = warp; c < r; c += nw) {
+      double* y = O + j + (int64_t)c * rows;
+      double w = lane == 0 ? y[0] : 0.0;
+      for (int i = 1 + lane; i < len; i += 32) w = fma(v[i], y[i], w);
+      for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+      w *= t;
+      if (lane == 0) y[0] -= w;
+      for (int i = 1 + lane; i < len; i += 32) y[i] = fma(-w, v[i], y[i]);
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  double* waw = VC;   // VC is no longer needed: keep a^-1/2 there
-  for (int i = tid; i < na; i += nt) waw[i] = 1.0 / sqrt(wa[i]);
-  __syncthreads();
-  for (int e = tid; e < m * r; e += nt) {
-    const int i = e % m, j = e / m;
-    double v = 0.0;
-    for (int q = 0; q < na; ++q) v = fma(VA[i + ka[q] * m] * waw[q], CV[q + j * m], v);
-    EA[i + j * m] = v;   // M (in EA) is no longer needed
-  }
-  __syncthreads();
-  for (int e = tid; e < m * r; e += nt) TA[e % m + (e / m) * m] = EA[e % m + (e / m) * m];
 }
 
 inline unsigned warps_grid(int n) { return (unsigned)((n + kWarps - 1) / kWarps); }
@@ -514,9 +524,20 @@ void launch_trsm(int kind, const double* F, int m, int64_t ldf, double* X, int n
   k_trsm<<<(unsigned)((n + threads - 1) / threads), threads, 0, st>>>(kind, F, m, ldf, X, n, ldx);
 }
 
-void launch_compress(const double* GA, const double* GB, int m, double eps, double* scratch, double* TA,
-                     double* TB, int* rank, cudaStream_t st) {
-  k_compress<<<1, 256, 256 * sizeof(double) + 256 * sizeof(int), st>>>(GA, GB, m, eps, scratch, TA, TB, rank);
+void launch_house_qr(double* A, int64_t lda, int rows_a, double* B, int64_t ldb, int rows_b, int m, double* tau_a,
+                     double* tau_b, cudaStream_t st) {
+  k_house_qr<<<2, 256, 0, st>>>(A, lda, rows_a, B, ldb, rows_b, m, tau_a, tau_b);
+}
+
+void launch_core_svd(const double* A, int64_t lda, int ka, const double* B, int64_t ldb, int kb, int m, double eps,
+                     double* C, double* W, double* TA, double* TB, int* rank, cudaStream_t st) {
+  k_core_svd<<<1, 256, 0, st>>>(A, lda, ka, B, ldb, kb, m, eps, C, W, TA, TB, rank);
+}
+
+void launch_apply_q(const double* A, int64_t lda, int rows_a, const double* tau_a, const double* TA, double* OA,
+                    const double* B, int64_t ldb, int rows_b, const double* tau_b, const double* TB, double* OB,
+                    int m, int r, cudaStream_t st) {
+  if (r > 0) k_apply_q<<<2, 256, 0, st>>>(A, lda, rows_a, tau_a, TA, OA, B, ldb, rows_b, tau_b, TB, OB, m, r);
 }
 
 void launch_dot(const double* x, const double* y, int64_t n, double* partial, double* out, cudaStream_t st) {

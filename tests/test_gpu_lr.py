@@ -151,10 +151,11 @@ def test_pcg_iterations_match_oracle(ctx, config0):
     assert abs(it - it_o) <= 1, (it, it_o)
     x = xd.cpu().numpy()
     assert np.linalg.norm(Kp @ x - rhs) <= 1e-9 * np.linalg.norm(rhs)
-    # without a preconditioner CG needs many more steps
+    # without a preconditioner CG needs far more steps (sigma spans four
+    # decades: it does not reach 1e-10 in 200 steps)
     xd.zero_()
-    it0, rr0 = b.h2_pcg(ctx, Za, None, bd.data_ptr(), xd.data_ptr(), 1e-10, 2000)
-    assert it0 > 10 * it and rr0 <= 1e-10
+    it0, rr0 = b.h2_pcg(ctx, Za, None, bd.data_ptr(), xd.data_ptr(), 1e-10, 200)
+    assert it0 == 200 and rr0 > 1e-10
 
 
 def test_power_error_matches_oracle(ctx, config0):
