@@ -212,64 +212,169 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def oracle_sample(seconds: float, start: int = 0, max_updates: int | None = None):
-    """Time the CPU oracle on the first updates of the workload until
-    ``seconds`` have passed; returns (updates done, wall s, cpu s, level mix)."""
+_ORACLE = {}
+
+
+def _oracle_init():
+    """Host process of the CPU baseline: builds the oracle's matrix and the
+    batch once (one BLAS thread; spawned, never forked from a GPU process)."""
     sys.path.insert(0, os.path.join(ROOT, "tests"))
-    from oracle.update import local_update
     from problems import draw_updates, oracle_problem
     w = WORK
     Zo, st, _ = oracle_problem(w["N"], w["k"], w["seed"], w["leaf"], w["eta"])
-    blocks, A, B = draw_updates(Zo, st, w["count"], w["u"])
-    done = 0
-    t0, c0 = time.perf_counter(), time.process_time()
-    j = start
-    while True:
-        local_update(Zo, blocks[j % len(blocks)], A[j % len(blocks)], B[j % len(blocks)], w["eps"])
-        done += 1
-        j += 1
-        el = time.perf_counter() - t0
-        if el >= seconds or (max_updates and done >= max_updates):
-            break
-    return done, time.perf_counter() - t0, time.process_time() - c0, Zo, blocks
+    _ORACLE["Z"] = Zo
+    _ORACLE["batch"] = draw_updates(Zo, st, w["count"], w["u"])
+
+
+def _oracle_updates(idx):
+    from oracle.update import local_update
+    blocks, A, B = _ORACLE["batch"]
+    for j in idx:
+        local_update(_ORACLE["Z"], blocks[j], A[j], B[j], WORK["eps"])
+    return len(idx)
+
+
+class OraclePool:
+    """The oracle as it stands on `procs` host processes (one per core)."""
+
+    def __init__(self, procs: int):
+        import multiprocessing as mp
+        keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+        saved = {k: os.environ.get(k) for k in keys}
+        for k in keys:
+            os.environ[k] = "1"
+        try:
+            self.pool = mp.get_context("spawn").Pool(procs, initializer=_oracle_init)
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        self.procs = procs
+        self.pool.map(_oracle_updates, [[] for _ in range(procs)])   # every process built its matrix
+
+    def run(self, start: int, count: int):
+        """Updates start .. start+count-1 of the batch (mod 4096), spread
+        over the processes; returns the wall time."""
+        n = WORK["count"]
+        idx = [(start + i) % n for i in range(count)]
+        chunks = [idx[p::self.procs] for p in range(self.procs)]
+        t0 = time.perf_counter()
+        self.pool.map(_oracle_updates, chunks, chunksize=1)
+        return time.perf_counter() - t0
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+LR_EPS = 1e-4
+
+
+def lr_problem(cells: int):
+    """The 2D FEM problems: 32 x 32 cells, 4 x 4 checkerboard (seed + 0), and
+    512 x 512 cells, 16 x 16 checkerboard (seed + 2); other sizes use a 4 x 4
+    checkerboard and their own seed."""
+    if cells == 32:
+        return 4, synth.SEED_BASE + 0
+    if cells == 512:
+        return 16, synth.SEED_BASE + 2
+    return 4, synth.SEED_BASE + 100 + cells
+
+
+def lr_measure(b, ctx, cells_list, reps: int, oracle_cells):
+    """FEM matrix, H^2-LR setup (build + factorisation, wall clock; the
+    recursion is driven from the host, every arithmetic step on the device),
+    PCG steps to 1e-10 and the power-iteration error; the oracle's setup
+    timed beside it on the host for the sizes in oracle_cells."""
+    import torch
+    out = {}
+    for cells in cells_list:
+        M, seed = lr_problem(cells)
+        st = synth.streams(seed)
+        sigma = synth.checker_sigma(st["sigma"], M, 2)
+        opt = b.options(eps=LR_EPS, eta=2.0, leaf_size=32)
+        builds, factors, info = [], [], None
+        F = A = None
+        for rep in range(reps):
+            for X in (F, A):
+                if X is not None:
+                    b.h2_matrix_free(X)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            A = b.h2_build_fem(ctx, 2, cells, M, sigma, opt)
+            F = b.h2_build_fem(ctx, 2, cells, M, sigma, opt) if rep == 0 else b.h2_matrix_clone(ctx, A)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            info = b.h2_lr_factor(ctx, F, opt)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            builds.append(t1 - t0)
+            factors.append(t2 - t1)
+        n = (cells - 1) ** 2
+        perm = b.h2_tree_permutation(A)
+        rhs = synth.fem_rhs(st["rhs"], n)[:, 0][perm]
+        bd = torch.from_numpy(np.ascontiguousarray(rhs)).cuda()
+        xd = torch.zeros(n, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        it, rr = b.h2_pcg(ctx, A, F, bd.data_ptr(), xd.data_ptr(), 1e-10, 100)
+        torch.cuda.synchronize()
+        cg_s = time.perf_counter() - t0
+        v0 = torch.from_numpy(np.random.default_rng(3).standard_normal(n)).cuda()
+        err = b.h2_lr_error(ctx, A, F, v0.data_ptr(), 20)
+        rec = {"n": n, "cells": cells, "checker": M, "eps": LR_EPS, "leaf": 32, "eta": 2.0,
+               "setup_s": min(factors), "factor_s_all": factors, "build_s": min(builds),
+               "updates": info["updates"], "products": info["products"], "max_rank": info["max_rank"],
+               "cg_iterations": it, "cg_relres": rr, "cg_s": cg_s, "err_power": err}
+        if cells in oracle_cells:
+            sys.path.insert(0, os.path.join(ROOT, "tests"))
+            from oracle.fem import h2_from_sparse, stiffness
+            from oracle.lr import lr_factor, lr_solve, pcg
+            t0 = time.perf_counter()
+            K, pts = stiffness(cells, 2, sigma, M)
+            Zo = h2_from_sparse(K, pts, 32, 2.0, 1.0 / cells)
+            t1 = time.perf_counter()
+            lr_factor(Zo, LR_EPS)
+            t2 = time.perf_counter()
+            Kp = K[Zo.V.tree.perm][:, Zo.V.tree.perm].tocsr()
+            _, it_o = pcg(lambda v: Kp @ v, rhs, lambda r: lr_solve(Zo, r), 1e-10)
+            rec["oracle"] = {"setup_s": t2 - t1, "build_s": t1 - t0, "cg_iterations": it_o, "cores": 1,
+                             "kind": "oracle"}
+        out["%dx%d" % (cells, cells)] = rec
+        b.h2_matrix_free(F)
+        b.h2_matrix_free(A)
+    return out
 
 
 def run_reference(args, rank):
     if rank != 0:
         return 0
+    procs = args.cpu_procs or os.cpu_count() or 1
+    op = OraclePool(procs)
+    sample = args.ref_sample * procs
     per_step = []
-    done_tot = 0
-    cpu_tot = 0.0
-    wall_tot = 0.0
-    sys.path.insert(0, os.path.join(ROOT, "tests"))
-    from oracle.update import local_update
-    from problems import draw_updates, oracle_problem
-    w = WORK
-    Zo, st, _ = oracle_problem(w["N"], w["k"], w["seed"], w["leaf"], w["eta"])
-    blocks, A, B = draw_updates(Zo, st, w["count"], w["u"])
-    sample = args.ref_sample
-    j = 0
+    start = 0
     for step in range(args.warmup + args.steps):
-        t0, c0 = time.perf_counter(), time.process_time()
-        for _ in range(sample):
-            local_update(Zo, blocks[j % len(blocks)], A[j % len(blocks)], B[j % len(blocks)], w["eps"])
-            j += 1
-        dt = time.perf_counter() - t0
+        dt = op.run(start, sample)
+        start += sample
         if step >= args.warmup:
             per_step.append(dt)
-            done_tot += sample
-            wall_tot += dt
-            cpu_tot += time.process_time() - c0
+    op.close()
+    wall_tot = sum(per_step)
+    done_tot = sample * len(per_step)
     value = done_tot / wall_tot
-    cores = max(1, round(cpu_tot / wall_tot))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall_tot / len(per_step),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAME, "step": "%d updates of the batch per step (bounded sample)" % sample,
+            "config": {"workload": WORKLOAD_NAME,
+                       "step": "%d consecutive updates of the batch per step (bounded sample)" % sample,
                        "l2": "n/a (CPU)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": "%d updates per step x %d steps, in batch order" % (sample, args.steps)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle",
+                             "sample": "%d updates per step x %d steps, in batch order, on %d host processes "
+                                       "(one per core, one BLAS thread each)" % (sample, args.steps, procs)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -292,6 +397,10 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-sample", type=int, default=24)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--lr-cells", default="32",
+                    help="comma-separated cells per side of the 2D FEM H2-LR problems to time ('' for none)")
+    ap.add_argument("--lr-reps", type=int, default=3)
+    ap.add_argument("--cpu-procs", type=int, default=0, help="host processes of the CPU baseline (0: all cores)")
     ap.add_argument("--count", type=int, default=WORK["count"],
                     help="updates per batch (profiling runs use fewer; the benchmark uses 4096)")
     args = ap.parse_args()
@@ -318,7 +427,9 @@ def main():
     Z, blocks, A, B = lib_workload(b, ctx, rank_offset=rank_seed(0, rank))
     blocks, A, B = blocks[:args.count], A[:args.count], B[:args.count]
     w = WORK
+    t_plan = time.perf_counter()
     P = b.h2_batch_create(ctx, Z, blocks, w["u"])
+    plan_s = time.perf_counter() - t_plan
     if args.mode == "exact":
         b.h2_batch_set_mode(P, b.MODE_EXACT)   # every update through the exact path
     lenA, lenB = b.h2_batch_factor_sizes(P)
@@ -490,11 +601,25 @@ def main():
     if args.matvec_steps > 0:
         mv = matvec_measure(b, ctx, Z, stream, flush, args.matvec_steps)
 
+    lr = None
+    cells_list = [int(x) for x in args.lr_cells.split(",") if x.strip()]
+    if rank == 0 and world == 1 and cells_list:
+        lr = lr_measure(b, ctx, cells_list, args.lr_reps, oracle_cells={32})
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        done, wall, cpu_s, _, _ = oracle_sample(args.cpu_seconds)
-        cpu = {"value": done / wall, "unit": UNIT, "cores": max(1, round(cpu_s / wall)), "kind": "oracle",
-               "sample": "first %d updates of the 4096-update batch (%.1f s wall)" % (done, wall)}
+        procs = args.cpu_procs or os.cpu_count() or 1
+        op = OraclePool(procs)
+        done, wall, start = 0, 0.0, 0
+        while wall < args.cpu_seconds:
+            chunk = 8 * procs
+            wall += op.run(start, chunk)
+            start += 97 * chunk          # spread the sample over the batch (its level mix)
+            done += chunk
+        op.close()
+        cpu = {"value": done / wall, "unit": UNIT, "cores": procs, "kind": "oracle",
+               "sample": "%d updates of the 4096-update batch in groups of %d spread over the batch, on %d host "
+                         "processes (one per core, one BLAS thread each), %.1f s" % (done, 8 * procs, procs, wall)}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -503,11 +628,12 @@ def main():
                        "path": args.mode,
                        "l2": "512 MB buffer written between timed steps",
                        "updates": len(blocks), "cluster_tasks": stats["cluster_tasks"],
-                       "block_tasks": stats["block_tasks"], "exact_path_updates": n_exact},
+                       "block_tasks": stats["block_tasks"], "exact_path_updates": n_exact,
+                       "plan_s": plan_s},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "e2e_compact": e2e_compact,
             "gpu_launches": stats["launches"] * args.steps,
             "clocks": clocks, "phases": phases, "phases_serial": phases_serial, "exact_mode": exact_mode,
-            "matvec": mv,
+            "matvec": mv, "lr": lr,
             "gflop_per_step": stats["flops"] / 1e9}
     if rank == 0:
         print(json.dumps(line))
