@@ -2096,6 +2096,192 @@ extern "C" h2_status h2_batch_update_items(const h2_batch* P, int64_t j, int64_t
 }
 
 // ============================================================ single update
+// ========================================== reusable single-update engine
+// In-place local low-rank updates one at a time on persistent device
+// buffers (grown on demand, never shrunk), through the exact path (every
+// update of a factorisation truncates), with the weights of the unchanged
+// matrix computed only for the clusters the update reads: the subtrees
+// T_t0, T_s0 and their ancestors.  The work of one update is then
+// proportional to #T_t0 + #T_s0 plus the depth (Section 5), instead of
+// the whole tree of an isolated batch.  Used by the H^2-LR driver.
+namespace h2 {
+
+struct UpdateEngine {
+  h2_batch* P = nullptr;
+  size_t c_items = 0, c_ents = 0, c_tasks = 0, c_two = 0, c_norms = 0, c_lvl = 0, c_cl = 0, c_q = 0;
+  size_t c_A = 0, c_B = 0;
+  int32_t c_ncl[2] = {0, 0};
+  int64_t updates = 0;
+};
+
+template <typename T>
+static void ensure(T*& p, size_t& cap, size_t need) {
+  if (p && need <= cap) return;
+  if (p) cudaFree(p);
+  p = nullptr;
+  cap = std::max<size_t>(std::max<size_t>(need, 1), cap + cap / 2);
+  p = dalloc<T>(cap);
+}
+
+template <typename T>
+static void put(T* dst, const std::vector<T>& v, cudaStream_t st) {
+  // pageable source: staged before the call returns
+  if (!v.empty()) H2_CUDA(cudaMemcpyAsync(dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+}
+
+
+UpdateEngine* engine_new() { return new UpdateEngine(); }
+
+void engine_delete(UpdateEngine* E) {
+  if (!E) return;
+  if (E->P) h2_batch_free(E->P);
+  delete E;
+}
+
+int64_t engine_updates(const UpdateEngine* E) { return E ? E->updates : 0; }
+
+void engine_update(h2_ctx* ctx, h2_matrix* Z, UpdateEngine* E, int32_t block, int u, const double* A, int64_t lda,
+                   const double* B, int64_t ldb, double eps) {
+  H2_REQUIRE(u >= 1 && u < kMaxCols, "update rank must be in 1..31");
+  cudaStream_t st = ctx->stream;
+  if (!E->P) {
+    E->P = new h2_batch();
+    h2_batch& P = *E->P;
+    P.device = ctx->device;
+    H2_CUDA(cudaStreamCreateWithFlags(&P.side, cudaStreamNonBlocking));
+    H2_CUDA(cudaEventCreateWithFlags(&P.fork, cudaEventDisableTiming));
+    H2_CUDA(cudaEventCreateWithFlags(&P.join, cudaEventDisableTiming));
+    H2_CUDA(cudaStreamCreateWithFlags(&P.side2, cudaStreamNonBlocking));
+    H2_CUDA(cudaStreamCreateWithFlags(&P.cap, cudaStreamNonBlocking));
+    H2_CUDA(cudaEventCreateWithFlags(&P.join2, cudaEventDisableTiming));
+  }
+  h2_batch& P = *E->P;
+  const BlockTree& bt = Z->blocks;
+  const ClusterTree* tr[2] = {&Z->rows, &Z->cols};
+  // host plan of one update (the planner appends to these lists)
+  P.Z = Z;
+  P.u = u;
+  P.count = 1;
+  P.blocks.assign(1, block);
+  P.rowsA.assign(1, Z->rows.size[bt.row[block]]);
+  P.rowsB.assign(1, Z->cols.size[bt.col[block]]);
+  P.offA.assign(1, 0);
+  P.offB.assign(1, 0);
+  P.lenA = P.rowsA[0] * u;
+  P.lenB = P.rowsB[0] * u;
+  P.items.clear();
+  P.ents.clear();
+  P.tasks.clear();
+  P.norms.clear();
+  plan_batch(P);
+  P.mode = H2_MODE_EXACT;
+  // the weights of the unchanged matrix: only the clusters of the subtrees
+  // and their ancestors, by level
+  {
+    const int L = P.depth + 1;
+    std::vector<std::vector<int32_t>> by(L);
+    for (int sd = 0; sd < 2; ++sd) {
+      const ClusterTree& ct = *tr[sd];
+      const int32_t root = sd == 0 ? bt.row[block] : bt.col[block];
+      for (int32_t c = root; c < root + ct.subtree[root]; ++c) by[ct.level[c]].push_back((sd << 30) | c);
+      for (int32_t a = ct.father[root]; a >= 0; a = ct.father[a]) by[ct.level[a]].push_back((sd << 30) | a);
+    }
+    P.cl_ptr.assign(L + 1, 0);
+    P.cl_list.clear();
+    for (int l = 0; l < L; ++l) {
+      P.cl_list.insert(P.cl_list.end(), by[l].begin(), by[l].end());
+      P.cl_ptr[l + 1] = (int32_t)P.cl_list.size();
+    }
+  }
+  // device buffers
+  const size_t ni = P.items.size(), nt = P.tasks.size();
+  const size_t prev_items = E->c_items, prev_tasks = E->c_tasks;
+  ensure(P.d_items, E->c_items, ni);
+  if (E->c_items != prev_items) {   // the per-item buffers follow the item capacity
+    const size_t c = E->c_items;
+    for (double** b : {&P.IB.Rq, &P.IB.Bw, &P.IB.Gv, &P.IB.Wg, &P.IB.Rt, &P.IB.F}) {
+      dfree(*b);
+      *b = dalloc<double>(c * kSlot);
+    }
+    dfree(P.IB.rank);
+    dfree(P.IB.own);
+    dfree(P.IB.jac);
+    P.IB.rank = dalloc<int32_t>(c);
+    P.IB.own = dalloc<int32_t>(c);
+    P.IB.jac = dalloc<unsigned long long>(4 * c);
+  }
+  ensure(P.d_ents, E->c_ents, P.ents.size());
+  ensure(P.d_tasks, E->c_tasks, nt);
+  if (E->c_tasks != prev_tasks) {
+    const size_t c = E->c_tasks;
+    dfree(P.d_left);
+    dfree(P.IB.S_out);
+    dfree(P.IB.copy);
+    P.d_left = dalloc<int32_t>(c);
+    P.IB.S_out = dalloc<double>(c * kSlot);
+    P.IB.copy = dalloc<int8_t>(c);
+  }
+  if (!P.d_nleft) P.d_nleft = dalloc<int32_t>(1);
+  if (!P.IB.fail) P.IB.fail = dalloc<int32_t>(1);
+  ensure(P.d_two, E->c_two, P.two.size());
+  {
+    const size_t prev = E->c_norms;
+    ensure(P.d_norms, E->c_norms, P.norms.size());
+    if (E->c_norms != prev || !P.IB.norms) {
+      dfree(P.IB.norms);
+      P.IB.norms = dalloc<double>(E->c_norms);
+    }
+  }
+  ensure(P.d_lvl, E->c_lvl, P.lvl_list.size());
+  ensure(P.d_cl, E->c_cl, P.cl_list.size());
+  ensure(P.IB.Q, E->c_q, (size_t)P.qlen);
+  for (int sd = 0; sd < 2; ++sd) {
+    const int32_t ncl = tr[sd]->count();
+    if (E->c_ncl[sd] != ncl) {
+      dfree(P.BW.G[sd]);
+      dfree(P.BW.B[sd]);
+      dfree(P.BW.need[sd]);
+      dfree(P.BW.Vg[sd]);
+      dfree(P.BW.orth[sd]);
+      P.BW.G[sd] = dalloc<double>((size_t)ncl * kSlot);
+      P.BW.B[sd] = dalloc<double>((size_t)ncl * kSlot);
+      P.BW.Wo[sd] = P.BW.G[sd];
+      P.BW.W0[sd] = P.BW.B[sd];
+      P.BW.need[sd] = dalloc<int32_t>(ncl);
+      P.BW.Vg[sd] = dalloc<double>((size_t)ncl * kSlot);
+      P.BW.orth[sd] = dalloc<int32_t>(ncl);
+      E->c_ncl[sd] = ncl;
+    }
+  }
+  put(P.d_items, P.items, st);
+  put(P.d_ents, P.ents, st);
+  put(P.d_tasks, P.tasks, st);
+  put(P.d_two, P.two, st);
+  put(P.d_norms, P.norms, st);
+  put(P.d_lvl, P.lvl_list, st);
+  put(P.d_cl, P.cl_list, st);
+  if (ni) H2_CUDA(cudaMemsetAsync(P.IB.jac, 0, 4 * ni * sizeof(unsigned long long), st));
+  // the factors with leading dimension = rows
+  ensure(P.d_A, E->c_A, (size_t)P.lenA);
+  ensure(P.d_B, E->c_B, (size_t)P.lenB);
+  H2_CUDA(cudaMemcpy2DAsync(P.d_A, P.rowsA[0] * sizeof(double), A, lda * sizeof(double), P.rowsA[0] * sizeof(double),
+                            u, cudaMemcpyDeviceToDevice, st));
+  H2_CUDA(cudaMemcpy2DAsync(P.d_B, P.rowsB[0] * sizeof(double), B, ldb * sizeof(double), P.rowsB[0] * sizeof(double),
+                            u, cudaMemcpyDeviceToDevice, st));
+  // a new plan every call: never replay a captured graph
+  if (P.graph) cudaGraphExecDestroy(P.graph);
+  P.graph = nullptr;
+  P.g_A = nullptr;
+  P.g_repeats = 0;
+  execute(ctx, P, P.d_A, P.d_B, eps);
+  h2_status s = h2_batch_apply(ctx, &P, 0, P.d_A, P.d_B, Z);
+  if (s != H2_OK) throw Error(s, ctx->last_error);
+  H2_CUDA(cudaStreamSynchronize(st));
+  ++E->updates;
+}
+
+}  // namespace h2
+
 extern "C" h2_status h2_lowrank_update(h2_ctx* ctx, h2_matrix* Z, int64_t block, int u, const double* A,
                                        int64_t lda, const double* B, int64_t ldb, double eps) {
   if (!ctx || !Z || !A || !B) return H2_EINVAL;

@@ -89,6 +89,18 @@ struct DeviceBasis {
   int64_t* d_leaf_off = nullptr;
 };
 
+// Reusable engine of in-place single updates (api.cu): persistent device
+// buffers, the exact path, base weights only for the clusters an update
+// reads.  Not thread-safe; one per driver.
+struct UpdateEngine;
+UpdateEngine* engine_new();
+void engine_delete(UpdateEngine* E);
+int64_t engine_updates(const UpdateEngine* E);
+// Z|_b <- trunc_eps(Z|_b + A B^*) in place (A: #t x u, ld lda; B: #s x u,
+// ld ldb; device); synchronizes.  Throws h2::Error.
+void engine_update(h2_ctx* ctx, h2_matrix* Z, UpdateEngine* E, int32_t block, int u, const double* A, int64_t lda,
+                   const double* B, int64_t ldb, double eps);
+
 }  // namespace h2
 
 struct h2_ctx {

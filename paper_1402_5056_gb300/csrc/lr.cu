@@ -130,7 +130,9 @@ struct Lr {
   size_t lcap = 0;
   int* drank = nullptr;           // rank of a compressed temporary
   int64_t* dnear_off = nullptr;   // per nearfield slot, offset in Z->d_N
+  UpdateEngine* eng = nullptr;    // persistent workspace of the local updates
   ~Lr() {
+    engine_delete(eng);
     if (dnear_off) cudaFree(dnear_off);
     if (xh) cudaFree(xh);
     if (yh) cudaFree(yh);
@@ -406,8 +408,8 @@ void apply_update(Lr& L, int32_t b, const double* A, int64_t lda, const double* 
     for (int32_t c = t; c < t + Z->rows.subtree[t]; ++c) kmax = std::max(kmax, Z->V.rank[c]);
     for (int32_t c = s; c < s + Z->cols.subtree[s]; ++c) kmax = std::max(kmax, Z->W.rank[c]);
     const int w = std::min(std::max(1, kMaxCols - kmax), u - j);
-    h2_status st = h2_lowrank_update(L.ctx, Z, b, w, A + (size_t)j * lda, lda, B + (size_t)j * ldb, ldb, L.eps);
-    if (st != H2_OK) throw Error(st, L.ctx->last_error);
+    if (!L.eng) L.eng = engine_new();
+    engine_update(L.ctx, Z, L.eng, b, w, A + (size_t)j * lda, lda, B + (size_t)j * ldb, ldb, L.eps);
     ++L.updates;
     j += w;
   }
