@@ -71,8 +71,12 @@ FP64_PEAK_SOURCE = "derived: 152 SM x 2 DFMA/clk x 2 flop x 2070 MHz (DFMA probe
 L2_FLUSH_BYTES = 512 << 20
 
 
-def lib_workload(b, ctx, rank_offset: int = 0):
-    """Library-side H^2 matrix, update blocks and factors of the workload."""
+def lib_workload(b, ctx, total: int = WORK["count"], lo: int = 0, hi: int | None = None):
+    """Library-side H^2 matrix of the workload (the same on every rank) and
+    updates lo..hi-1 of a batch of `total` updates drawn from it (blocks and
+    factors are drawn in update order, so a shard of the batch is the same
+    whichever ranks share it)."""
+    hi = total if hi is None else hi
     w = WORK
     pts = synth.grid_points_2d(w["N"])
     Z = b.h2_matrix_create(ctx, pts, w["leaf"], w["eta"], 0.0, w["k"])
@@ -83,15 +87,18 @@ def lib_workload(b, ctx, rank_offset: int = 0):
     pairs = [(int(tc["son0"][t]), int(tc["son1"][t])) for t in range(nc) if tc["son0"][t] >= 0]
     adm = np.flatnonzero(tb["kind"] == 1)
     near = np.flatnonzero(tb["kind"] == 2)
-    st = synth.streams(w["seed"] + rank_offset)
+    st = synth.streams(w["seed"])
     V = synth.nested_orthonormal_bases(st["bases"], leaves, pairs, nc, w["k"])
     W = synth.nested_orthonormal_bases(st["bases"], leaves, pairs, nc, w["k"])
     S = synth.gaussian_couplings(st["couplings"], len(adm), w["k"], 1.0 / w["k"])
     Nf = synth.gaussian_nearfield(st["couplings"], [(int(tc["size"][tb["row"][c]]), int(tc["size"][tb["col"][c]]))
                                                     for c in near], 1.0 / 16)
-    blocks = [int(x) for x in synth.choose_blocks(st["blocks"], adm, w["count"])]
-    A, B = synth.update_factors(st["ab"], [int(tc["size"][tb["row"][c]]) for c in blocks],
-                                [int(tc["size"][tb["col"][c]]) for c in blocks], w["u"])
+    blocks = [int(x) for x in synth.choose_blocks(st["blocks"], adm, total)]
+    rows = [int(tc["size"][tb["row"][c]]) for c in blocks]
+    cols = [int(tc["size"][tb["col"][c]]) for c in blocks]
+    synth.update_factors(st["ab"], rows[:lo], cols[:lo], w["u"])       # the other ranks' updates
+    A, B = synth.update_factors(st["ab"], rows[lo:hi], cols[lo:hi], w["u"])
+    blocks = blocks[lo:hi]
     if ctx is not None:
         b.h2_set_basis(ctx, Z, 0, *V)
         b.h2_set_basis(ctx, Z, 1, *W)
@@ -327,6 +334,7 @@ def lr_measure(b, ctx, cells_list, reps: int, oracle_cells):
         rec = {"n": n, "cells": cells, "checker": M, "eps": LR_EPS, "leaf": 32, "eta": 2.0,
                "setup_s": min(factors), "factor_s_all": factors, "build_s": min(builds),
                "updates": info["updates"], "products": info["products"], "max_rank": info["max_rank"],
+               "seconds_by_activity": info["seconds"],
                "cg_iterations": it, "cg_relres": rr, "cg_s": cg_s, "err_power": err}
         if cells in oracle_cells:
             sys.path.insert(0, os.path.join(ROOT, "tests"))
@@ -420,12 +428,15 @@ def main():
     else:
         torch.cuda.set_device(0)
     from paper_1402_5056_gb300 import binding as b
-    from paper_1402_5056_gb300.dist import rank_seed, reduce_max
+    from paper_1402_5056_gb300.dist import reduce_max, shard_range
 
     stream = torch.cuda.current_stream()
     ctx = b.h2_ctx_create(torch.cuda.current_device(), stream.cuda_stream)
-    Z, blocks, A, B = lib_workload(b, ctx, rank_offset=rank_seed(0, rank))
-    blocks, A, B = blocks[:args.count], A[:args.count], B[:args.count]
+    # one batch of world x count updates on the same matrix, sharded by index
+    # (isolated updates: no exchange between ranks)
+    total = world * args.count
+    lo, hi = shard_range(total, rank, world)
+    Z, blocks, A, B = lib_workload(b, ctx, total, lo, hi)
     w = WORK
     t_plan = time.perf_counter()
     P = b.h2_batch_create(ctx, Z, blocks, w["u"])

@@ -65,6 +65,17 @@ h2_status lr_guard(h2_ctx* ctx, F&& f) {
   }
 }
 
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct Timer {
+  double& acc;
+  double t0;
+  explicit Timer(double& a) : acc(a), t0(now_s()) {}
+  ~Timer() { acc += now_s() - t0; }
+};
+
 struct DevGuard {
   int prev = -1;
   explicit DevGuard(int dev) {
@@ -122,6 +133,9 @@ struct Lr {
   cudaStream_t st = nullptr;
   int64_t updates = 0;
   int64_t products = 0;
+  // wall time (s) by activity: local updates, product terms, temporaries,
+  // dense solves through diagonal blocks, leaf LU
+  double t_update = 0, t_terms = 0, t_temps = 0, t_solves = 0, t_lu = 0;
   // block-product workspace: per cluster kcap x m slots
   double* xh = nullptr;
   double* yh = nullptr;
@@ -399,6 +413,7 @@ std::pair<int32_t, int32_t> sons_of(const ClusterTree& ct, int32_t c) { return {
 
 // ----------------------------------------------------------- local updates
 void apply_update(Lr& L, int32_t b, const double* A, int64_t lda, const double* B, int64_t ldb, int u) {
+  Timer tm(L.t_update);
   h2_matrix* Z = L.Z;
   const BlockTree& bt = Z->blocks;
   int j = 0;
@@ -622,6 +637,13 @@ void apply_term(Lr& L, const Term& T) {
 
 // the terms of a temporary stacked, extended by zeros to z, truncated (reading 2)
 void apply_temp(Lr& L, const Temp& tmp) {
+  const double t0 = now_s();
+  const double u0 = L.t_update;
+  struct Done {
+    Lr& L;
+    double t0, u0;
+    ~Done() { L.t_temps += (now_s() - t0) - (L.t_update - u0); }
+  } done{L, t0, u0};
   h2_matrix* Z = L.Z;
   const BlockTree& bt = Z->blocks;
   const int32_t t = bt.row[tmp.z], r = bt.col[tmp.z];
@@ -664,7 +686,10 @@ void apply_temp(Lr& L, const Temp& tmp) {
 
 void mul(Lr& L, double alpha, int32_t x, int32_t y, int32_t z) {
   std::vector<Item> items;
-  collect(L, alpha, x, y, z, items);
+  {
+    Timer tm(L.t_terms);
+    collect(L, alpha, x, y, z, items);
+  }
   for (const Item& it : items) {
     if (it.temp) apply_temp(L, it.tmp);
     else apply_term(L, it.term);
@@ -733,6 +758,7 @@ void lsolve(Lr& L, int32_t d, int32_t x) {
   const BlockTree& bt = Z->blocks;
   const int32_t t = bt.row[x], s = bt.col[x];
   if (bt.kind[x] == kNear) {
+    Timer tm(L.t_solves);
     lsolve_dense(L, d, near_ptr(Z, x), csize(Z, t), (int)csize(Z, s));
     return;
   }
@@ -741,10 +767,13 @@ void lsolve(Lr& L, int32_t d, int32_t x) {
     if (ls == 0 || kt == 0) return;        // the block is zero
     const int64_t mt = csize(Z, t), ms = csize(Z, s);
     DArr Vt(mt * kt, L.st), Xh(mt * ls, L.st), Ws(ms * ls, L.st);
-    expand(L, 0, t, Vt.p, mt);
-    launch_gemm((int)mt, ls, kt, 1.0, Vt.p, mt, 0, coupling_ptr(Z, x), Z->kcap, 0, 0.0, Xh.p, mt, L.st);
-    lsolve_dense(L, d, Xh.p, mt, ls);
-    expand(L, 1, s, Ws.p, ms);
+    {
+      Timer tm(L.t_solves);
+      expand(L, 0, t, Vt.p, mt);
+      launch_gemm((int)mt, ls, kt, 1.0, Vt.p, mt, 0, coupling_ptr(Z, x), Z->kcap, 0, 0.0, Xh.p, mt, L.st);
+      lsolve_dense(L, d, Xh.p, mt, ls);
+      expand(L, 1, s, Ws.p, ms);
+    }
     H2_CUDA(cudaMemsetAsync(coupling_ptr(Z, x), 0, (size_t)Z->kcap * Z->kcap * sizeof(double), L.st));
     apply_update(L, x, Xh.p, mt, Ws.p, ms, ls);
     return;
@@ -762,6 +791,7 @@ void rsolve(Lr& L, int32_t d, int32_t x) {
   const int32_t t = bt.row[x], s = bt.col[x];
   if (bt.kind[x] == kNear) {
     const int64_t mt = csize(Z, t), ms = csize(Z, s);
+    Timer tm(L.t_solves);
     // transpose in, solve R^* X^* = Y^*, transpose out
     DArr Yt(ms * mt, L.st);
     launch_transpose((int)mt, (int)ms, 1.0, near_ptr(Z, x), mt, Yt.p, ms, L.st);
@@ -774,10 +804,13 @@ void rsolve(Lr& L, int32_t d, int32_t x) {
     if (ls == 0 || kt == 0) return;
     const int64_t mt = csize(Z, t), ms = csize(Z, s);
     DArr Ws(ms * ls, L.st), Bh(ms * kt, L.st), Vt(mt * kt, L.st);
-    expand(L, 1, s, Ws.p, ms);
-    launch_gemm((int)ms, kt, ls, 1.0, Ws.p, ms, 0, coupling_ptr(Z, x), Z->kcap, 1, 0.0, Bh.p, ms, L.st);
-    rsolve_dense_t(L, d, Bh.p, ms, kt);
-    expand(L, 0, t, Vt.p, mt);
+    {
+      Timer tm(L.t_solves);
+      expand(L, 1, s, Ws.p, ms);
+      launch_gemm((int)ms, kt, ls, 1.0, Ws.p, ms, 0, coupling_ptr(Z, x), Z->kcap, 1, 0.0, Bh.p, ms, L.st);
+      rsolve_dense_t(L, d, Bh.p, ms, kt);
+      expand(L, 0, t, Vt.p, mt);
+    }
     H2_CUDA(cudaMemsetAsync(coupling_ptr(Z, x), 0, (size_t)Z->kcap * Z->kcap * sizeof(double), L.st));
     apply_update(L, x, Vt.p, mt, Bh.p, ms, kt);
     return;
@@ -794,6 +827,7 @@ void lr(Lr& L, int32_t d) {
   const BlockTree& bt = Z->blocks;
   const int32_t t = bt.row[d];
   if (bt.kind[d] == kNear) {
+    Timer tm(L.t_lu);
     launch_leaf_lu(near_ptr(Z, d), (int)csize(Z, t), csize(Z, t), L.ctx->d_error, L.st);
     return;
   }
@@ -1053,6 +1087,12 @@ extern "C" h2_status h2_lr_factor(h2_ctx* ctx, h2_matrix* Z, const h2_options* o
       for (int32_t r : Z->V.rank) kmax = std::max(kmax, r);
       for (int32_t r : Z->W.rank) kmax = std::max(kmax, r);
       stats[2] = kmax;
+      // microseconds of wall time by activity
+      stats[3] = (int64_t)(1e6 * L.t_update);
+      stats[4] = (int64_t)(1e6 * L.t_terms);
+      stats[5] = (int64_t)(1e6 * L.t_temps);
+      stats[6] = (int64_t)(1e6 * L.t_solves);
+      stats[7] = (int64_t)(1e6 * L.t_lu);
     }
   });
 }

@@ -108,3 +108,68 @@ def test_sharded_isolated_batch_equals_serial():
     Zo, blocks, A, B = _batch_problem()
     serial = [_fingerprint(d) for d in isolated_batch(Zo, blocks, A, B, 1e-6)]
     assert res[0] == res[1] == serial
+
+
+def _plan_fingerprint(b, P, first, count):
+    """Cluster tasks and coupling tasks of updates first..first+count-1 of a
+    host-only plan, update by update (update index relative to `first`)."""
+    items, tasks = {}, {}
+    st = b.h2_batch_stats(None, P, flops=False)
+    for i in range(st["cluster_tasks"]):
+        d = b.h2_batch_item_info(P, i)
+        items.setdefault(d["update"] - first, []).append((d["side"], d["cluster"], d["k"], d["flags"]))
+    for t in range(st["block_tasks"]):
+        d = b.h2_batch_task_info(P, t)
+        tasks.setdefault(d["update"] - first, []).append((d["block"], d["kt"], d["ls"],
+                                                          d["row_item"] >= 0, d["col_item"] >= 0))
+    return [(items.get(j, []), tasks.get(j, [])) for j in range(count)]
+
+
+def _lib_batch():
+    import numpy as np
+    import synth
+    from paper_1402_5056_gb300 import binding as b
+    Z = b.h2_matrix_create(None, synth.grid_points_2d(48), 16, 2.0, 0.0, 8)
+    tb = b.h2_tree_blocks(Z)
+    adm = np.flatnonzero(np.asarray(tb["kind"]) == 1)
+    blocks = [int(x) for x in synth.choose_blocks(np.random.default_rng(602), adm, 23)]
+    blocks += [0, int(np.flatnonzero(np.asarray(tb["kind"]) == 0)[3])]   # root and a subdivided block
+    return b, Z, blocks
+
+
+def _plan_worker(rank, world, port, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        b, Z, blocks = _lib_batch()
+        lo, hi = shard_range(len(blocks), rank, world)
+        P = b.h2_batch_create(None, Z, blocks[lo:hi], 3)
+        mine = _plan_fingerprint(b, P, 0, hi - lo)
+        b.h2_batch_free(P)
+        b.h2_matrix_free(Z)
+        parts = [None] * world
+        dist.all_gather_object(parts, mine)
+        out[rank] = [fp for part in parts for fp in part]
+    finally:
+        dist.destroy_process_group()
+
+
+def test_shard_plans_tile_the_batch_plan():
+    """The library's plans of the ranks' slices (host-only, gloo ranks on
+    CPU) hold, update by update, exactly the cluster tasks and coupling
+    tasks of the plan of the whole batch: sharding by index splits the work
+    without changing it."""
+    b, Z, blocks = _lib_batch()
+    P = b.h2_batch_create(None, Z, blocks, 3)
+    full = _plan_fingerprint(b, P, 0, len(blocks))
+    b.h2_batch_free(P)
+    b.h2_matrix_free(Z)
+    for world in (2, 3):
+        port = _free_port()
+        with mp.Manager() as m:
+            out = m.dict()
+            mp.spawn(_plan_worker, args=(world, port, out), nprocs=world, join=True)
+            res = dict(out)
+        for r in range(world):
+            assert res[r] == full, (world, r)
