@@ -1587,109 +1587,155 @@ extern "C" h2_status h2_batch_execute_host_compact(h2_ctx* ctx, h2_batch* P, con
   return execute_host(ctx, P, A_host, B_host, eps, result, copied ? copied : &none);
 }
 
-extern "C" h2_status h2_batch_apply(h2_ctx* ctx, const h2_batch* P, int64_t j, const double* A, const double* B,
-                                    h2_matrix* dst) {
-  if (!ctx || !P || !dst || j < 0 || j >= P->count) return H2_EINVAL;
-  return guard(ctx, [&] {
-    H2_REQUIRE(P->executed, "h2_batch_apply: batch not executed");
-    H2_REQUIRE(has_storage(dst), "h2_batch_apply: destination has no device storage");
-    const h2_matrix* Z = P->Z;
-    H2_REQUIRE(dst->rows.count() == Z->rows.count() && dst->blocks.count() == Z->blocks.count(),
-               "h2_batch_apply: destination has another structure");
-    DeviceGuard g(ctx->device);
-    cudaStream_t st = ctx->stream;
-    const int64_t i0 = P->upd_item[j], i1 = P->upd_item[j + 1];
-    const int64_t t0 = P->upd_task[j], t1 = P->upd_task[j + 1];
-    std::vector<int32_t> rk(i1 - i0);
-    std::vector<int8_t> copy(t1 - t0);
-    if (i1 > i0)
-      H2_CUDA(cudaMemcpyAsync(rk.data(), P->IB.rank + i0, (i1 - i0) * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    if (t1 > t0)
-      H2_CUDA(cudaMemcpyAsync(copy.data(), P->IB.copy + t0, (t1 - t0) * sizeof(int8_t), cudaMemcpyDeviceToHost, st));
+namespace {
+// Persistent device buffers of the commit's copy lists (the update engine);
+// without them the lists are uploaded into fresh allocations.
+struct CommitScratch {
+  CopyDesc* cd = nullptr;
+  size_t c_cd = 0;
+  NearDesc* nd = nullptr;
+  size_t c_nd = 0;
+  int* err = nullptr;     // page-locked copy of the device error word
+};
+
+void commit_update(h2_ctx* ctx, const h2_batch* P, int64_t j, const double* A, const double* B, h2_matrix* dst,
+                   CommitScratch* sc) {
+  H2_REQUIRE(P->executed, "h2_batch_apply: batch not executed");
+  H2_REQUIRE(has_storage(dst), "h2_batch_apply: destination has no device storage");
+  const h2_matrix* Z = P->Z;
+  H2_REQUIRE(dst->rows.count() == Z->rows.count() && dst->blocks.count() == Z->blocks.count(),
+             "h2_batch_apply: destination has another structure");
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = ctx->stream;
+  const int64_t i0 = P->upd_item[j], i1 = P->upd_item[j + 1];
+  const int64_t t0 = P->upd_task[j], t1 = P->upd_task[j + 1];
+  std::vector<int32_t> rk(i1 - i0);
+  std::vector<int8_t> copy(t1 - t0);
+  if (i1 > i0)
+    H2_CUDA(cudaMemcpyAsync(rk.data(), P->IB.rank + i0, (i1 - i0) * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  if (t1 > t0)
+    H2_CUDA(cudaMemcpyAsync(copy.data(), P->IB.copy + t0, (t1 - t0) * sizeof(int8_t), cudaMemcpyDeviceToHost, st));
+  if (sc) {
+    // one synchronisation: the error word comes back with the ranks
+    H2_CUDA(cudaMemcpyAsync(sc->err, ctx->d_error, sizeof(int), cudaMemcpyDeviceToHost, st));
+    H2_CUDA(cudaStreamSynchronize(st));
+    if (*sc->err) check_device_error(ctx);
+  } else {
     H2_CUDA(cudaStreamSynchronize(st));
     check_device_error(ctx);
-    int kmax = 0;
-    for (int32_t r : rk) kmax = std::max(kmax, r);
-    grow_kcap(ctx, dst, kmax);
-    const int kcap = dst->kcap;
-    std::vector<CopyDesc> cd;
-    auto rank_of_item = [&](int32_t id) { return rk[id - i0]; };
-    for (int64_t i = i0; i < i1; ++i) {
-      const Item& it = P->items[i];
-      DeviceBasis& db = basis_of(dst, it.side);
-      const ClusterTree& ct = tree_of(dst, it.side);
-      const int r = rank_of_item((int32_t)i);
-      if ((it.flags & kItemLeaf) && r > 0)
-        cd.push_back({P->IB.Q + it.qoff, db.d_leaf + db.leaf_off[it.cluster], it.size, r, it.size, it.size});
-      if (!(it.flags & kItemTreeRoot)) {
-        const int rf = (it.flags & kItemRoot) ? db.rank[ct.father[it.cluster]] : rank_of_item(it.parent);
-        if (r > 0 && rf > 0)
-          cd.push_back({P->IB.F + (size_t)i * kSlot, db.d_transfer + (size_t)it.cluster * kcap * kcap, r, rf, 32,
-                        kcap});
-      }
+  }
+  int kmax = 0;
+  for (int32_t r : rk) kmax = std::max(kmax, r);
+  grow_kcap(ctx, dst, kmax);
+  const int kcap = dst->kcap;
+  std::vector<CopyDesc> cd;
+  auto rank_of_item = [&](int32_t id) { return rk[id - i0]; };
+  for (int64_t i = i0; i < i1; ++i) {
+    const Item& it = P->items[i];
+    DeviceBasis& db = basis_of(dst, it.side);
+    const ClusterTree& ct = tree_of(dst, it.side);
+    const int r = rank_of_item((int32_t)i);
+    if ((it.flags & kItemLeaf) && r > 0)
+      cd.push_back({P->IB.Q + it.qoff, db.d_leaf + db.leaf_off[it.cluster], it.size, r, it.size, it.size});
+    if (!(it.flags & kItemTreeRoot)) {
+      const int rf = (it.flags & kItemRoot) ? db.rank[ct.father[it.cluster]] : rank_of_item(it.parent);
+      if (r > 0 && rf > 0)
+        cd.push_back({P->IB.F + (size_t)i * kSlot, db.d_transfer + (size_t)it.cluster * kcap * kcap, r, rf, 32,
+                      kcap});
     }
-    for (int64_t t = t0; t < t1; ++t) {
-      const Task& tk = P->tasks[t];
-      const int rt = tk.it >= 0 ? rank_of_item(tk.it) : tk.kt;
-      const int rs = tk.is >= 0 ? rank_of_item(tk.is) : tk.ls;
-      if (rt <= 0 || rs <= 0) continue;
-      double* d = dst->d_S + (size_t)tk.slot * kcap * kcap;
-      if (copy[t - t0]) {
-        // [S_b; 0] or [S_b, 0]: the coupling of the planned matrix (the same
-        // storage when dst is that matrix) and the zero rows or columns
-        if (dst != Z && tk.kt > 0 && tk.ls > 0)
-          cd.push_back({Z->d_S + (size_t)tk.slot * Z->kcap * Z->kcap, d, tk.kt, tk.ls, Z->kcap, kcap});
-        if (tk.it >= 0)
-          cd.push_back({nullptr, d + tk.kt, rt - tk.kt, rs, 0, kcap});
-        else
-          cd.push_back({nullptr, d + (size_t)tk.ls * kcap, rt, rs - tk.ls, 0, kcap});
-        continue;
-      }
-      cd.push_back({P->IB.S_out + (size_t)t * kSlot, d, rt, rs, 32, kcap});
+  }
+  for (int64_t t = t0; t < t1; ++t) {
+    const Task& tk = P->tasks[t];
+    const int rt = tk.it >= 0 ? rank_of_item(tk.it) : tk.kt;
+    const int rs = tk.is >= 0 ? rank_of_item(tk.is) : tk.ls;
+    if (rt <= 0 || rs <= 0) continue;
+    double* d = dst->d_S + (size_t)tk.slot * kcap * kcap;
+    if (copy[t - t0]) {
+      // [S_b; 0] or [S_b, 0]: the coupling of the planned matrix (the same
+      // storage when dst is that matrix) and the zero rows or columns
+      if (dst != Z && tk.kt > 0 && tk.ls > 0)
+        cd.push_back({Z->d_S + (size_t)tk.slot * Z->kcap * Z->kcap, d, tk.kt, tk.ls, Z->kcap, kcap});
+      if (tk.it >= 0)
+        cd.push_back({nullptr, d + tk.kt, rt - tk.kt, rs, 0, kcap});
+      else
+        cd.push_back({nullptr, d + (size_t)tk.ls * kcap, rt, rs - tk.ls, 0, kcap});
+      continue;
     }
-    // nearfield leaves inside the block
-    std::vector<NearDesc> nd;
-    const BlockTree& bt = Z->blocks;
-    const int32_t b0 = (int32_t)P->blocks[j];
-    std::vector<int32_t> stack{b0};
-    while (!stack.empty()) {
-      const int32_t b = stack.back();
-      stack.pop_back();
-      if (bt.kind[b] == kSub) {
-        for (int i = 3; i >= 0; --i)
-          if (bt.son4[4 * b + i] >= 0) stack.push_back(bt.son4[4 * b + i]);
-      } else if (bt.kind[b] == kNear) {
-        const int32_t t = bt.row[b], s = bt.col[b];
-        const int64_t ro = Z->rows.off[t] - Z->rows.off[bt.row[b0]];
-        const int64_t co = Z->cols.off[s] - Z->cols.off[bt.col[b0]];
-        NearDesc d{};
-        d.N = dst->d_N + dst->near_off[bt.slot[b]];
-        d.A = A + P->offA[j] + ro;
-        d.B = B + P->offB[j] + co;
-        d.rows = (int)Z->rows.size[t];
-        d.cols = (int)Z->cols.size[s];
-        d.ldn = d.rows;
-        d.lda = (int)P->rowsA[j];
-        d.ldb = (int)P->rowsB[j];
-        nd.push_back(d);
-      }
+    cd.push_back({P->IB.S_out + (size_t)t * kSlot, d, rt, rs, 32, kcap});
+  }
+  // nearfield leaves inside the block
+  std::vector<NearDesc> nd;
+  const BlockTree& bt = Z->blocks;
+  const int32_t b0 = (int32_t)P->blocks[j];
+  std::vector<int32_t> stack{b0};
+  while (!stack.empty()) {
+    const int32_t b = stack.back();
+    stack.pop_back();
+    if (bt.kind[b] == kSub) {
+      for (int i = 3; i >= 0; --i)
+        if (bt.son4[4 * b + i] >= 0) stack.push_back(bt.son4[4 * b + i]);
+    } else if (bt.kind[b] == kNear) {
+      const int32_t t = bt.row[b], s = bt.col[b];
+      const int64_t ro = Z->rows.off[t] - Z->rows.off[bt.row[b0]];
+      const int64_t co = Z->cols.off[s] - Z->cols.off[bt.col[b0]];
+      NearDesc d{};
+      d.N = dst->d_N + dst->near_off[bt.slot[b]];
+      d.A = A + P->offA[j] + ro;
+      d.B = B + P->offB[j] + co;
+      d.rows = (int)Z->rows.size[t];
+      d.cols = (int)Z->cols.size[s];
+      d.ldn = d.rows;
+      d.lda = (int)P->rowsA[j];
+      d.ldb = (int)P->rowsB[j];
+      nd.push_back(d);
     }
-    H2_REQUIRE(nd.empty() || (A && B), "h2_batch_apply: factors needed for the nearfield part");
-    CopyDesc* dcd = upload(cd, st);
-    NearDesc* dnd = upload(nd, st);
-    launch_copy(dcd, (int)cd.size(), st);
-    launch_near_add(dnd, (int)nd.size(), P->u, st);
-    H2_CUDA(cudaGetLastError());
-    for (int64_t i = i0; i < i1; ++i) {
-      const Item& it = P->items[i];
-      basis_of(dst, it.side).rank[it.cluster] = rank_of_item((int32_t)i);
+  }
+  H2_REQUIRE(nd.empty() || (A && B), "h2_batch_apply: factors needed for the nearfield part");
+  CopyDesc* dcd = nullptr;
+  NearDesc* dnd = nullptr;
+  if (sc) {
+    // persistent lists; pageable sources are staged before the calls return
+    if (cd.size() > sc->c_cd) {
+      dfree(sc->cd);
+      sc->c_cd = std::max(cd.size(), 2 * sc->c_cd);
+      sc->cd = dalloc<CopyDesc>(sc->c_cd);
     }
-    sync_ranks(dst->V, st);
-    sync_ranks(dst->W, st);
+    if (nd.size() > sc->c_nd) {
+      dfree(sc->nd);
+      sc->c_nd = std::max(nd.size(), 2 * sc->c_nd);
+      sc->nd = dalloc<NearDesc>(sc->c_nd);
+    }
+    dcd = sc->cd;
+    dnd = sc->nd;
+    if (!cd.empty())
+      H2_CUDA(cudaMemcpyAsync(dcd, cd.data(), cd.size() * sizeof(CopyDesc), cudaMemcpyHostToDevice, st));
+    if (!nd.empty())
+      H2_CUDA(cudaMemcpyAsync(dnd, nd.data(), nd.size() * sizeof(NearDesc), cudaMemcpyHostToDevice, st));
+  } else {
+    dcd = upload(cd, st);
+    dnd = upload(nd, st);
+  }
+  launch_copy(dcd, (int)cd.size(), st);
+  launch_near_add(dnd, (int)nd.size(), P->u, st);
+  H2_CUDA(cudaGetLastError());
+  for (int64_t i = i0; i < i1; ++i) {
+    const Item& it = P->items[i];
+    basis_of(dst, it.side).rank[it.cluster] = rank_of_item((int32_t)i);
+  }
+  sync_ranks(dst->V, st);
+  sync_ranks(dst->W, st);
+  if (!sc) {
     H2_CUDA(cudaStreamSynchronize(st));
     dfree(dcd);
     dfree(dnd);
-  });
+  }
+}
+}  // namespace
+
+extern "C" h2_status h2_batch_apply(h2_ctx* ctx, const h2_batch* P, int64_t j, const double* A, const double* B,
+                                    h2_matrix* dst) {
+  if (!ctx || !P || !dst || j < 0 || j >= P->count) return H2_EINVAL;
+  return guard(ctx, [&] { commit_update(ctx, P, j, A, B, dst, nullptr); });
 }
 
 namespace {
@@ -2108,6 +2154,7 @@ namespace h2 {
 
 struct UpdateEngine {
   h2_batch* P = nullptr;
+  CommitScratch cs;
   size_t c_items = 0, c_ents = 0, c_tasks = 0, c_two = 0, c_norms = 0, c_lvl = 0, c_cl = 0, c_q = 0;
   size_t c_A = 0, c_B = 0;
   int32_t c_ncl[2] = {0, 0};
@@ -2134,7 +2181,10 @@ UpdateEngine* engine_new() { return new UpdateEngine(); }
 
 void engine_delete(UpdateEngine* E) {
   if (!E) return;
-  if (E->P) h2_batch_free(E->P);
+  if (E->P) h2_batch_free(E->P);   // synchronizes its streams
+  dfree(E->cs.cd);
+  dfree(E->cs.nd);
+  if (E->cs.err) cudaFreeHost(E->cs.err);
   delete E;
 }
 
@@ -2273,10 +2323,11 @@ void engine_update(h2_ctx* ctx, h2_matrix* Z, UpdateEngine* E, int32_t block, in
   P.graph = nullptr;
   P.g_A = nullptr;
   P.g_repeats = 0;
+  if (!E->cs.err) H2_CUDA(cudaMallocHost(&E->cs.err, sizeof(int)));
   execute(ctx, P, P.d_A, P.d_B, eps);
-  h2_status s = h2_batch_apply(ctx, &P, 0, P.d_A, P.d_B, Z);
-  if (s != H2_OK) throw Error(s, ctx->last_error);
-  H2_CUDA(cudaStreamSynchronize(st));
+  // the commit reads the new ranks back (one synchronisation); its copies
+  // stay in flight on the context's stream
+  commit_update(ctx, &P, 0, P.d_A, P.d_B, Z, &E->cs);
   ++E->updates;
 }
 

@@ -97,7 +97,9 @@ UpdateEngine* engine_new();
 void engine_delete(UpdateEngine* E);
 int64_t engine_updates(const UpdateEngine* E);
 // Z|_b <- trunc_eps(Z|_b + A B^*) in place (A: #t x u, ld lda; B: #s x u,
-// ld ldb; device); synchronizes.  Throws h2::Error.
+// ld ldb; device); the new ranks are on the host on return, the device
+// work of the commit may still run on the context's stream.  Throws
+// h2::Error.
 void engine_update(h2_ctx* ctx, h2_matrix* Z, UpdateEngine* E, int32_t block, int u, const double* A, int64_t lda,
                    const double* B, int64_t ldb, double eps);
 

@@ -348,10 +348,26 @@ __global__ void k_core_svd(const double* XA, int64_t lda, int ka, const double* 
   }
   for (int e = tid; e < kb * kb; e += nt) W[e % kb + (e / kb) * m] = (e % kb == e / kb) ? 1.0 : 0.0;
   __syncthreads();
+  // columns whose squared norm is below 1e-28 of the largest are at the
+  // rounding level of the product: they are not rotated (rotating them
+  // need not converge, and they lie far below any truncation threshold)
+  for (int j = tid; j < kb; j += nt) {
+    double v = 0.0;
+    for (int k = 0; k < ka; ++k) v = fma(C[k + j * m], C[k + j * m], v);
+    nrm2[j] = v;
+  }
+  __syncthreads();
+  __shared__ double tiny;
+  if (tid == 0) {
+    double mx = 0.0;
+    for (int j = 0; j < kb; ++j) mx = fmax(mx, nrm2[j]);
+    tiny = 1e-28 * mx;
+  }
+  __syncthreads();
   // one-sided Jacobi on the columns of C, round-robin pairs, one warp a pair
   const int n2 = kb + (kb & 1);
   const double tol2 = 1e-30;   // (1e-15)^2
-  for (int sweep = 0; sweep < 60 && kb > 1; ++sweep) {
+  for (int sweep = 0; sweep < 40 && kb > 1; ++sweep) {
     if (tid == 0) any_rot = 0;
     __syncthreads();
     for (int r = 0; r < n2 - 1; ++r) {
@@ -371,7 +387,7 @@ __global__ void k_core_svd(const double* XA, int64_t lda, int ka, const double* 
           be += __shfl_xor_sync(0xffffffffu, be, o);
           ga += __shfl_xor_sync(0xffffffffu, ga, o);
         }
-        if (ga * ga > tol2 * al * be && ga != 0.0) {
+        if (ga * ga > tol2 * al * be && ga != 0.0 && al > tiny && be > tiny) {
           const double zeta = (be - al) / (2.0 * ga);
           const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
           const double c = 1.0 / sqrt(fma(t, t, 1.0)), s = c * t;
