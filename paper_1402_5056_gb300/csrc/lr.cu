@@ -845,6 +845,7 @@ void lr(Lr& L, int32_t d) {
 void check_square(const h2_matrix* Z) {
   H2_REQUIRE(Z->rows.off == Z->cols.off && Z->rows.son0 == Z->cols.son0, "the matrix must be square with one tree");
   H2_REQUIRE(Z->blocks.kind[0] != kAdm, "the root block must not be admissible");
+  H2_REQUIRE(Z->rows.max_leaf <= 64, "leaf clusters above 64 indices are not supported");
 }
 
 // ---------------------------------------------------------------- the FEM

@@ -176,47 +176,76 @@ __global__ void k_eye(double* A, int n, int64_t lda) {
   }
 }
 
-// Doolittle LU without pivoting of one m x m block, one thread block
+// Doolittle LU without pivoting of one m x m block (m <= 64), one warp:
+// lane i owns rows i and i + 32; step k scales column k below the pivot and
+// updates the trailing rows (the same order of operations as the textbook
+// loop, so the same rounding)
 __global__ void k_leaf_lu(double* A, int m, int64_t lda, int* err) {
+  const int lane = threadIdx.x;
   for (int k = 0; k < m; ++k) {
     const double piv = A[k + k * lda];
-    if (piv == 0.0 && threadIdx.x == 0) atomicOr(err, 256);   // zero pivot
-    __syncthreads();
-    for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) A[i + k * lda] = A[i + k * lda] / piv;
-    __syncthreads();
-    const int mt = m - k - 1;
-    for (int e = threadIdx.x; e < mt * mt; e += blockDim.x) {
-      const int i = k + 1 + e % mt, j = k + 1 + e / mt;
-      A[i + j * lda] = fma(-A[i + k * lda], A[k + j * lda], A[i + j * lda]);
+    if (piv == 0.0 && lane == 0) atomicOr(err, 256);   // zero pivot
+    for (int h = 0; h < 2; ++h) {
+      const int i = lane + 32 * h;
+      if (i > k && i < m) {
+        const double l = A[i + k * lda] / piv;
+        A[i + k * lda] = l;
+        for (int j = k + 1; j < m; ++j) A[i + j * lda] = fma(-l, A[k + j * lda], A[i + j * lda]);
+      }
     }
-    __syncthreads();
+    __syncwarp();
   }
 }
 
+// Triangular solves with an m x m factor (m <= 64), one warp per
+// right-hand side, lane i holding entries i and i + 32; the solved entry of
+// each step is broadcast and the others updated column by column
+//   kind 0: column j of X, L x = y (unit lower)
+//   kind 1: column j of X, R x = y (upper)
+//   kind 2: row j of X, x R = y
 __global__ void k_trsm(int kind, const double* F, int m, int64_t ldf, double* X, int n, int64_t ldx) {
-  for (int j = threadIdx.x + blockIdx.x * blockDim.x; j < n; j += blockDim.x * gridDim.x) {
-    if (kind == 0) {          // column j of X: L x = y, unit lower
-      double* x = X + j * ldx;
-      for (int i = 0; i < m; ++i) {
-        double v = x[i];
-        for (int q = 0; q < i; ++q) v = fma(-F[i + q * ldf], x[q], v);
-        x[i] = v;
-      }
-    } else if (kind == 1) {   // column j of X: R x = y, upper
-      double* x = X + j * ldx;
-      for (int i = m - 1; i >= 0; --i) {
-        double v = x[i];
-        for (int q = i + 1; q < m; ++q) v = fma(-F[i + q * ldf], x[q], v);
-        x[i] = v / F[i + i * ldf];
-      }
-    } else {                  // row j of X: x R = y
-      double* x = X + j;
-      for (int i = 0; i < m; ++i) {
-        double v = x[i * ldx];
-        for (int q = 0; q < i; ++q) v = fma(-x[q * ldx], F[q + i * ldf], v);
-        x[i * ldx] = v / F[i + i * ldf];
+  const int lane = threadIdx.x & 31;
+  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (j >= n) return;
+  const int64_t stride = kind == 2 ? ldx : 1;
+  double* x = kind == 2 ? X + j : X + j * ldx;
+  double r[2];
+  for (int h = 0; h < 2; ++h) {
+    const int i = lane + 32 * h;
+    r[h] = i < m ? x[i * stride] : 0.0;
+  }
+  if (kind == 0) {
+    for (int k = 0; k < m; ++k) {
+      const double xk = __shfl_sync(0xffffffffu, k < 32 ? r[0] : r[1], k & 31);
+      for (int h = 0; h < 2; ++h) {
+        const int i = lane + 32 * h;
+        if (i > k && i < m) r[h] = fma(-F[i + k * ldf], xk, r[h]);
       }
     }
+  } else if (kind == 1) {
+    for (int k = m - 1; k >= 0; --k) {
+      const int hk = k >> 5;
+      if ((k & 31) == lane) r[hk] = r[hk] / F[k + k * ldf];
+      const double xk = __shfl_sync(0xffffffffu, hk ? r[1] : r[0], k & 31);
+      for (int h = 0; h < 2; ++h) {
+        const int i = lane + 32 * h;
+        if (i < k) r[h] = fma(-F[i + k * ldf], xk, r[h]);
+      }
+    }
+  } else {
+    for (int q = 0; q < m; ++q) {
+      const int hq = q >> 5;
+      if ((q & 31) == lane) r[hq] = r[hq] / F[q + q * ldf];
+      const double xq = __shfl_sync(0xffffffffu, hq ? r[1] : r[0], q & 31);
+      for (int h = 0; h < 2; ++h) {
+        const int i = lane + 32 * h;
+        if (i > q && i < m) r[h] = fma(-xq, F[q + i * ldf], r[h]);
+      }
+    }
+  }
+  for (int h = 0; h < 2; ++h) {
+    const int i = lane + 32 * h;
+    if (i < m) x[i * stride] = r[h];
   }
 }
 
@@ -267,7 +296,7 @@ __global__ void k_axpby(int64_t n, double a, const double* x, double b, double* 
 // A' B'^* is the truncated A B^* (B' has orthonormal columns).
 
 // QR of the rows x m matrix X (ld ldx) in place; tau (m entries).  One block.
-__global__ void k_house_qr(double* XA, int64_t lda, int rows_a, double* XB, int64_t ldb, int rows_b, int m,
+__global__ void __launch_bounds__(512) k_house_qr(double* XA, int64_t lda, int rows_a, double* XB, int64_t ldb, int rows_b, int m,
                            double* tau_a, double* tau_b) {
   double* X = blockIdx.x == 0 ? XA : XB;
   const int64_t ldx = blockIdx.x == 0 ? lda : ldb;
@@ -333,7 +362,7 @@ __device__ __forceinline__ int rr_partner(int i, int r, int n2, int& p, int& q) 
 // Core SVD and rank.  C (ka x kb, ld m, scratch), W (kb x kb, ld m,
 // scratch); writes T = U_r Sigma_r = C W_r (ka x r, ld m) into TA, W_r into
 // TB (kb x r, ld m), the rank into *rank.  One block.
-__global__ void k_core_svd(const double* XA, int64_t lda, int ka, const double* XB, int64_t ldb, int kb, int m,
+__global__ void __launch_bounds__(1024) k_core_svd(const double* XA, int64_t lda, int ka, const double* XB, int64_t ldb, int kb, int m,
                            double eps, double* C, double* W, double* TA, double* TB, int* rank) {
   __shared__ int order[256];
   __shared__ double nrm2[256];
@@ -451,7 +480,7 @@ __global__ void k_core_svd(const double* XA, int64_t lda, int ka, const double* 
 // out (rows x r, ld ldo) = Q [T; 0] with Q = H_0 H_1 ... H_{k-1} stored in X
 // (reflections below the diagonal, tau); T is k x r (ld ldt).  One block
 // per factor (blockIdx 0: A side, 1: B side).
-__global__ void k_apply_q(const double* XA, int64_t lda, int rows_a, const double* tau_a, const double* TA,
+__global__ void __launch_bounds__(512) k_apply_q(const double* XA, int64_t lda, int rows_a, const double* tau_a, const double* TA,
                           double* OA, const double* XB, int64_t ldb, int rows_b, const double* tau_b,
                           const double* TB, double* OB, int m, int r) {
   const bool sa = blockIdx.x == 0;
@@ -531,29 +560,29 @@ void launch_eye(double* A, int n, int64_t lda, cudaStream_t st) {
 }
 
 void launch_leaf_lu(double* A, int m, int64_t lda, int* err, cudaStream_t st) {
-  if (m > 0) k_leaf_lu<<<1, 256, 0, st>>>(A, m, lda, err);
+  if (m > 0) k_leaf_lu<<<1, 32, 0, st>>>(A, m, lda, err);
 }
 
 void launch_trsm(int kind, const double* F, int m, int64_t ldf, double* X, int n, int64_t ldx, cudaStream_t st) {
   if (m <= 0 || n <= 0) return;
-  const int threads = 64;
-  k_trsm<<<(unsigned)((n + threads - 1) / threads), threads, 0, st>>>(kind, F, m, ldf, X, n, ldx);
+  const int warps = 4;
+  k_trsm<<<(unsigned)((n + warps - 1) / warps), 32 * warps, 0, st>>>(kind, F, m, ldf, X, n, ldx);
 }
 
 void launch_house_qr(double* A, int64_t lda, int rows_a, double* B, int64_t ldb, int rows_b, int m, double* tau_a,
                      double* tau_b, cudaStream_t st) {
-  k_house_qr<<<2, 256, 0, st>>>(A, lda, rows_a, B, ldb, rows_b, m, tau_a, tau_b);
+  k_house_qr<<<2, 512, 0, st>>>(A, lda, rows_a, B, ldb, rows_b, m, tau_a, tau_b);
 }
 
 void launch_core_svd(const double* A, int64_t lda, int ka, const double* B, int64_t ldb, int kb, int m, double eps,
                      double* C, double* W, double* TA, double* TB, int* rank, cudaStream_t st) {
-  k_core_svd<<<1, 256, 0, st>>>(A, lda, ka, B, ldb, kb, m, eps, C, W, TA, TB, rank);
+  k_core_svd<<<1, 1024, 0, st>>>(A, lda, ka, B, ldb, kb, m, eps, C, W, TA, TB, rank);
 }
 
 void launch_apply_q(const double* A, int64_t lda, int rows_a, const double* tau_a, const double* TA, double* OA,
                     const double* B, int64_t ldb, int rows_b, const double* tau_b, const double* TB, double* OB,
                     int m, int r, cudaStream_t st) {
-  if (r > 0) k_apply_q<<<2, 256, 0, st>>>(A, lda, rows_a, tau_a, TA, OA, B, ldb, rows_b, tau_b, TB, OB, m, r);
+  if (r > 0) k_apply_q<<<2, 512, 0, st>>>(A, lda, rows_a, tau_a, TA, OA, B, ldb, rows_b, tau_b, TB, OB, m, r);
 }
 
 void launch_dot(const double* x, const double* y, int64_t n, double* partial, double* out, cudaStream_t st) {
