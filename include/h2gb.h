@@ -414,11 +414,15 @@ h2_status h2_build_fem(h2_ctx* ctx, int dim, int64_t cells, int64_t checker, con
  * an admissible leaf V_t S W_s^* replaces it by (L^-1 V_t S) W_s^* through
  * an update; updates are applied in column groups of at most 32 - (largest
  * rank in the two subtrees) columns.  Z must be square with one tree and
- * its LU without pivoting must exist (SPD matrices).  stats (host, 8
+ * its LU without pivoting must exist (SPD matrices).  stats (host, 15
  * entries, optional): local updates, product terms, largest rank, then the
  * wall time in microseconds spent on the local updates, on computing the
  * product terms, on the temporaries (truncation), on the dense solves
- * through diagonal blocks, and on the leaf LU launches.  Synchronizes. */
+ * through diagonal blocks, on the leaf LU launches, and, within the local
+ * updates, on host planning, on enqueueing their kernels, on waiting for
+ * the GPU before each commit, and in total; then the microseconds spent
+ * waiting for the truncation rank of the temporaries, their number and
+ * their stacked columns.  Synchronizes. */
 h2_status h2_lr_factor(h2_ctx* ctx, h2_matrix* Z, const h2_options* opt, int64_t* stats);
 
 /* X <- R^-1 L^-1 X for a factor from h2_lr_factor: block forward and

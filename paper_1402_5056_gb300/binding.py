@@ -505,11 +505,14 @@ def h2_build_fem(ctx, dim: int, cells: int, checker: int, sigma, opt):
 
 def h2_lr_factor(ctx, Z, opt):
     """In-place H^2-LR; returns counts, the largest rank and the wall time by activity."""
-    st = np.zeros(8, dtype=np.int64)
+    st = np.zeros(15, dtype=np.int64)
     _check(_lib.h2_lr_factor(ctx, Z, C.byref(opt), st.ctypes.data), ctx)
     return {"updates": int(st[0]), "products": int(st[1]), "max_rank": int(st[2]),
             "seconds": {"updates": st[3] / 1e6, "terms": st[4] / 1e6, "temporaries": st[5] / 1e6,
-                        "solves": st[6] / 1e6, "leaf_lu": st[7] / 1e6}}
+                        "solves": st[6] / 1e6, "leaf_lu": st[7] / 1e6},
+            "update_seconds": {"plan": st[8] / 1e6, "enqueue": st[9] / 1e6, "wait": st[10] / 1e6,
+                               "total": st[11] / 1e6},
+            "temporaries": {"count": int(st[13]), "columns": int(st[14]), "wait_seconds": st[12] / 1e6}}
 
 
 def h2_lr_solve(ctx, LR, nrhs: int, X_dev: int, ldx: int):

@@ -1,6 +1,7 @@
 // C ABI of libh2gb: contexts, H^2 storage, the batch planner and the
 // execution of local low-rank updates (Sections 2, 4 and 5).
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <memory>
@@ -1591,6 +1592,7 @@ namespace {
 // Persistent device buffers of the commit's copy lists (the update engine);
 // without them the lists are uploaded into fresh allocations.
 struct CommitScratch {
+  double wait_s = 0.0;    // time spent waiting for the ranks (the GPU work before them)
   CopyDesc* cd = nullptr;
   size_t c_cd = 0;
   NearDesc* nd = nullptr;
@@ -1618,7 +1620,9 @@ void commit_update(h2_ctx* ctx, const h2_batch* P, int64_t j, const double* A, c
   if (sc) {
     // one synchronisation: the error word comes back with the ranks
     H2_CUDA(cudaMemcpyAsync(sc->err, ctx->d_error, sizeof(int), cudaMemcpyDeviceToHost, st));
+    const auto w0 = std::chrono::steady_clock::now();
     H2_CUDA(cudaStreamSynchronize(st));
+    sc->wait_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - w0).count();
     if (*sc->err) check_device_error(ctx);
   } else {
     H2_CUDA(cudaStreamSynchronize(st));
@@ -2159,6 +2163,7 @@ struct UpdateEngine {
   size_t c_A = 0, c_B = 0;
   int32_t c_ncl[2] = {0, 0};
   int64_t updates = 0;
+  double plan_s = 0.0, launch_s = 0.0, total_s = 0.0;   // host planning, enqueue of the kernels, whole call
 };
 
 template <typename T>
@@ -2190,9 +2195,18 @@ void engine_delete(UpdateEngine* E) {
 
 int64_t engine_updates(const UpdateEngine* E) { return E ? E->updates : 0; }
 
+void engine_times(const UpdateEngine* E, double* plan, double* launch, double* wait, double* total) {
+  *plan = E ? E->plan_s : 0.0;
+  *launch = E ? E->launch_s : 0.0;
+  *wait = E ? E->cs.wait_s : 0.0;
+  *total = E ? E->total_s : 0.0;
+}
+
 void engine_update(h2_ctx* ctx, h2_matrix* Z, UpdateEngine* E, int32_t block, int u, const double* A, int64_t lda,
                    const double* B, int64_t ldb, double eps) {
   H2_REQUIRE(u >= 1 && u < kMaxCols, "update rank must be in 1..31");
+  using clk = std::chrono::steady_clock;
+  const auto c0 = clk::now();
   cudaStream_t st = ctx->stream;
   if (!E->P) {
     E->P = new h2_batch();
@@ -2225,6 +2239,8 @@ void engine_update(h2_ctx* ctx, h2_matrix* Z, UpdateEngine* E, int32_t block, in
   P.norms.clear();
   plan_batch(P);
   P.mode = H2_MODE_EXACT;
+  const auto c1 = clk::now();
+  E->plan_s += std::chrono::duration<double>(c1 - c0).count();
   // the weights of the unchanged matrix: only the clusters of the subtrees
   // and their ancestors, by level
   {
@@ -2324,11 +2340,14 @@ void engine_update(h2_ctx* ctx, h2_matrix* Z, UpdateEngine* E, int32_t block, in
   P.g_A = nullptr;
   P.g_repeats = 0;
   if (!E->cs.err) H2_CUDA(cudaMallocHost(&E->cs.err, sizeof(int)));
+  const auto c2 = clk::now();
   execute(ctx, P, P.d_A, P.d_B, eps);
+  E->launch_s += std::chrono::duration<double>(clk::now() - c2).count();
   // the commit reads the new ranks back (one synchronisation); its copies
   // stay in flight on the context's stream
   commit_update(ctx, &P, 0, P.d_A, P.d_B, Z, &E->cs);
   ++E->updates;
+  E->total_s += std::chrono::duration<double>(clk::now() - c0).count();
 }
 
 }  // namespace h2

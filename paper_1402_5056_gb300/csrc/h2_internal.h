@@ -96,6 +96,9 @@ struct UpdateEngine;
 UpdateEngine* engine_new();
 void engine_delete(UpdateEngine* E);
 int64_t engine_updates(const UpdateEngine* E);
+// seconds spent planning on the host, enqueueing the kernels, waiting for
+// the GPU before the commit, and in the whole calls
+void engine_times(const UpdateEngine* E, double* plan, double* launch, double* wait, double* total);
 // Z|_b <- trunc_eps(Z|_b + A B^*) in place (A: #t x u, ld lda; B: #s x u,
 // ld ldb; device); the new ranks are on the host on return, the device
 // work of the commit may still run on the context's stream.  Throws

@@ -136,6 +136,8 @@ struct Lr {
   // wall time (s) by activity: local updates, product terms, temporaries,
   // dense solves through diagonal blocks, leaf LU
   double t_update = 0, t_terms = 0, t_temps = 0, t_solves = 0, t_lu = 0;
+  double t_temp_wait = 0;   // of t_temps: waiting for the rank of the truncation
+  int64_t n_temps = 0, temp_cols = 0;
   // block-product workspace: per cluster kcap x m slots
   double* xh = nullptr;
   double* yh = nullptr;
@@ -676,7 +678,12 @@ void apply_temp(Lr& L, const Temp& tmp) {
   launch_core_svd(A.p, mt, ka, B.p, mr, kb, m, L.eps, C.p, W.p, TA.p, TB.p, L.drank, L.st);
   int rk = 0;
   H2_CUDA(cudaMemcpyAsync(&rk, L.drank, sizeof(int), cudaMemcpyDeviceToHost, L.st));
-  H2_CUDA(cudaStreamSynchronize(L.st));
+  {
+    Timer tw(L.t_temp_wait);
+    H2_CUDA(cudaStreamSynchronize(L.st));
+  }
+  ++L.n_temps;
+  L.temp_cols += m;
   if (rk == 0) return;
   DArr A2(mt * rk, L.st), B2(mr * rk, L.st);
   launch_apply_q(A.p, mt, (int)mt, tauA.p, TA.p, A2.p, B.p, mr, (int)mr, tauB.p, TB.p, B2.p, m, rk, L.st);
@@ -1094,6 +1101,15 @@ extern "C" h2_status h2_lr_factor(h2_ctx* ctx, h2_matrix* Z, const h2_options* o
       stats[5] = (int64_t)(1e6 * L.t_temps);
       stats[6] = (int64_t)(1e6 * L.t_solves);
       stats[7] = (int64_t)(1e6 * L.t_lu);
+      double pl, la, wa, to;
+      engine_times(L.eng, &pl, &la, &wa, &to);
+      stats[8] = (int64_t)(1e6 * pl);
+      stats[9] = (int64_t)(1e6 * la);
+      stats[10] = (int64_t)(1e6 * wa);
+      stats[11] = (int64_t)(1e6 * to);
+      stats[12] = (int64_t)(1e6 * L.t_temp_wait);
+      stats[13] = L.n_temps;
+      stats[14] = L.temp_cols;
     }
   });
 }
