@@ -124,23 +124,25 @@ def _factor_pair(P, x_cols=None, y_rows=None):
 
 
 # ----------------------------------------------------- product (Section 3)
-def _case2(Z, alpha, x, y):
+def _case2(ZX, ZY, alpha, x, y):
     """Term alpha X|_x Y|_y when x or y is a leaf (Section 6, Case 2), as
-    ('lr', A, B) or ('dense', P, X, Y) with P = alpha X Y."""
-    bt = Z.blocks
+    ('lr', A, B) or ('dense', P, X, Y) with P = alpha X Y; X = ZX, Y = ZY
+    (the same matrix in the factorisation)."""
+    bt = ZX.blocks
     t, s, r = bt.row[x], bt.col[x], bt.col[y]
     if bt.kind[y] == BlockTree.ADM:
-        Xt = Z.block_dense(x) @ Z.V.dense(s)                 # X|_{t x s} V_s
-        return ("lr", alpha * (Xt @ Z.S[y]), Z.W.dense(r))
+        Xt = ZX.block_dense(x) @ ZY.V.dense(s)               # X|_{t x s} V_s
+        return ("lr", alpha * (Xt @ ZY.S[y]), ZY.W.dense(r))
     if bt.kind[x] == BlockTree.ADM:
-        Yt = Z.block_dense(y).T @ Z.W.dense(s)               # Y|_{s x r}^* W_s
-        return ("lr", Z.V.dense(t), alpha * (Yt @ Z.S[x].T))
-    X, Y = Z.block_dense(x), Z.block_dense(y)
+        Yt = ZY.block_dense(y).T @ ZX.W.dense(s)             # Y|_{s x r}^* W_s
+        return ("lr", ZX.V.dense(t), alpha * (Yt @ ZX.S[x].T))
+    X, Y = ZX.block_dense(x), ZY.block_dense(y)
     return ("dense", alpha * (X @ Y), alpha * X, Y.T)
 
 
-def _collect(Z, alpha, x, y, z, out):
+def _collect(ZX, ZY, alpha, x, y, z, out):
     """Terms of Z|_z += alpha X|_x Y|_y in the order of the recursion."""
+    Z = ZX
     bt = Z.blocks
     if bt.kind[x] == BlockTree.SUB and bt.kind[y] == BlockTree.SUB:
         t, s, r = bt.row[x], bt.col[x], bt.col[y]
@@ -149,23 +151,25 @@ def _collect(Z, alpha, x, y, z, out):
             for s1 in tree.sons[s]:
                 for t1 in tree.sons[t]:
                     for r1 in tree.sons[r]:
-                        _collect(Z, alpha, _son(bt, x, t1, s1), _son(bt, y, s1, r1), _son(bt, z, t1, r1), out)
+                        _collect(ZX, ZY, alpha, _son(bt, x, t1, s1), _son(bt, y, s1, r1), _son(bt, z, t1, r1),
+                                 out)
             return
         assert bt.kind[z] == BlockTree.ADM, "inadmissible target of subdivided factors"
         temps = {}
         for s1 in tree.sons[s]:
             for t1 in tree.sons[t]:
                 for r1 in tree.sons[r]:
-                    _collect_virtual(Z, alpha, _son(bt, x, t1, s1), _son(bt, y, s1, r1),
+                    _collect_virtual(ZX, ZY, alpha, _son(bt, x, t1, s1), _son(bt, y, s1, r1),
                                      temps.setdefault((t1, r1), []))
         for t1 in tree.sons[t]:
             for r1 in tree.sons[r]:
                 out.append(("temp", z, temps.get((t1, r1), [])))
         return
-    out.append(("term", z, (bt.row[x], bt.col[y]), _case2(Z, alpha, x, y)))
+    out.append(("term", z, (bt.row[x], bt.col[y]), _case2(ZX, ZY, alpha, x, y)))
 
 
-def _collect_virtual(Z, alpha, x, y, bucket):
+def _collect_virtual(ZX, ZY, alpha, x, y, bucket):
+    Z = ZX
     bt = Z.blocks
     if bt.kind[x] == BlockTree.SUB and bt.kind[y] == BlockTree.SUB:
         t, s, r = bt.row[x], bt.col[x], bt.col[y]
@@ -173,9 +177,9 @@ def _collect_virtual(Z, alpha, x, y, bucket):
         for s1 in tree.sons[s]:
             for t1 in tree.sons[t]:
                 for r1 in tree.sons[r]:
-                    _collect_virtual(Z, alpha, _son(bt, x, t1, s1), _son(bt, y, s1, r1), bucket)
+                    _collect_virtual(ZX, ZY, alpha, _son(bt, x, t1, s1), _son(bt, y, s1, r1), bucket)
         return
-    bucket.append(((bt.row[x], bt.col[y]), _case2(Z, alpha, x, y)))
+    bucket.append(((bt.row[x], bt.col[y]), _case2(ZX, ZY, alpha, x, y)))
 
 
 def _place(Z, z, cl, A, B):
@@ -229,10 +233,11 @@ def _apply_term(C: _Ctx, z, term):
             _apply_update(C, z, A, B)
 
 
-def _mul(C: _Ctx, alpha, x, y, z):
-    """Z|_z += alpha X|_x Y|_y (reading 1: terms from the matrix at the start)."""
+def _mul(C: _Ctx, alpha, x, y, z, ZX=None, ZY=None):
+    """Z|_z += alpha X|_x Y|_y (reading 1: terms from the matrices at the
+    start); X, Y default to Z itself (the factorisation in place)."""
     out = []
-    _collect(C.Z, alpha, x, y, z, out)
+    _collect(C.Z if ZX is None else ZX, C.Z if ZY is None else ZY, alpha, x, y, z, out)
     for item in out:
         if item[0] == "term":
             _apply_term(C, item[1], item[3])
@@ -420,3 +425,15 @@ def power_error(apply_A, precond, n, iters=50, seed=0):
             return 0.0
         v = w / lam
     return lam
+
+
+def mul(Z, X, Y, alpha: float, x: int, y: int, z: int, eps: float, cap=32):
+    """The product of Section 3, Z|_z <- Z|_z + alpha X|_x Y|_y, for blocks
+    x = (t, s), y = (s, r), z = (t, r) of the block tree the three H^2
+    matrices share (X or Y may be Z itself); low-rank terms enter Z through
+    local updates with accuracy eps.  Z is modified in place; returns the
+    number of updates."""
+    C = _Ctx(Z, eps, cap)
+    _mul(C, alpha, x, y, z, X, Y)
+    return C.updates
+

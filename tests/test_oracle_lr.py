@@ -23,7 +23,7 @@ import scipy.linalg as la
 
 import synth
 from oracle.fem import h2_from_sparse, stiffness
-from oracle.lr import (_Ctx, _mul, lr_factor, lr_solve, lsolve_dense, lu_doolittle, pcg, power_error,
+from oracle.lr import (_Ctx, _mul, lr_factor, lr_solve, lsolve_dense, lu_doolittle, mul, pcg, power_error,
                        rsolve_dense, usolve_dense)
 from oracle.tree import BlockTree
 from problems import oracle_problem
@@ -124,6 +124,29 @@ def test_product_is_exact_without_truncation():
         want[ct.offset[t]:ct.offset[t] + ct.size[t], ct.offset[r]:ct.offset[r] + ct.size[r]] += -0.75 * X @ Y
         got = Z.dense()
         assert np.linalg.norm(got - want) <= 1e-12 * np.linalg.norm(want), key
+
+
+def test_product_of_three_matrices_is_exact_without_truncation():
+    """Z|_z += alpha X|_x Y|_y with three different H^2 matrices on one tree
+    (different bases and couplings): at eps = 0 exactly the dense product is
+    added to the target block, for every combination of block kinds."""
+    X, _, _ = oracle_problem(16, 3, 81, 8)
+    Y, _, _ = oracle_problem(16, 4, 82, 8)
+    Z0, _, _ = oracle_problem(16, 2, 83, 8)
+    bt, ct = Z0.blocks, Z0.V.tree
+    triples = _triples(bt, ct)
+    for key, (x, y, z) in triples.items():
+        Z = Z0.copy()
+        before = Z.dense()
+        Xb, Yb = X.block_dense(x), Y.block_dense(y)
+        mul(Z, X, Y, 0.5, x, y, z, 0.0, cap=None)
+        want = before.copy()
+        t, r = bt.row[z], bt.col[z]
+        want[ct.offset[t]:ct.offset[t] + ct.size[t], ct.offset[r]:ct.offset[r] + ct.size[r]] += 0.5 * Xb @ Yb
+        got = Z.dense()
+        assert np.linalg.norm(got - want) <= 1e-12 * np.linalg.norm(want), key
+        # X and Y are read only
+        assert np.array_equal(X.block_dense(x), Xb) and np.array_equal(Y.block_dense(y), Yb)
 
 
 def test_cg_step_counts():

@@ -183,7 +183,9 @@ LR_MUTATIONS = {
     "backward substitution without R12 X2": (
         "Y1 = Y[:n1] - Z.block_dense(_son(bt, d, t1, t2)) @ X2", "Y1 = Y[:n1]"),
     "low-rank term with the coupling transposed": (
-        'return ("lr", alpha * (Xt @ Z.S[y]), Z.W.dense(r))', 'return ("lr", alpha * (Xt @ Z.S[y].T), Z.W.dense(r))'),
+        'return ("lr", alpha * (Xt @ ZY.S[y]), ZY.W.dense(r))', 'return ("lr", alpha * (Xt @ ZY.S[y].T), ZY.W.dense(r))'),
+    "low-rank term from the wrong factor's basis": (
+        "Xt = ZX.block_dense(x) @ ZY.V.dense(s)", "Xt = ZX.block_dense(x) @ ZX.V.dense(s)"),
     "temporaries dropped": (
         'out.append(("temp", z, temps.get((t1, r1), [])))', 'out.append(("temp", z, []))'),
     "leaf LU without the division by the pivot": ("A[k + 1:, k] /= A[k, k]", "A[k + 1:, k] *= 1.0"),
