@@ -425,6 +425,21 @@ h2_status h2_build_fem(h2_ctx* ctx, int dim, int64_t cells, int64_t checker, con
  * their stacked columns.  Synchronizes. */
 h2_status h2_lr_factor(h2_ctx* ctx, h2_matrix* Z, const h2_options* opt, int64_t* stats);
 
+/* The product of Section 3, Z|_{t x r} <- Z|_{t x r} + alpha X|_{t x s}
+ * Y|_{s x r}, for blocks bx = (t, s), by = (s, r), bz = (t, r) of the block
+ * tree X, Y and Z share (same points, leaf size and eta; X or Y may be Z
+ * itself).  The recursion of Section 3 over the sons (the eight
+ * sub-products, Case 1 of Section 6); where X or Y is a leaf the term is
+ * low rank, (X|_{t x s} V_s) S W_r^* or V_t S (Y|_{s x r}^* W_s)^* (Case 2),
+ * or dense; low-rank terms enter Z through the local low-rank update with
+ * accuracy eps, dense ones are added to inadmissible leaves; a target that
+ * is an admissible leaf of two subdivided factors receives up to four
+ * truncated temporaries.  Every term is computed from the matrices as they
+ * are when the call starts.  X and Y are not modified (unless one is Z).
+ * updates (host, optional): local updates made.  Synchronizes. */
+h2_status h2_mul(h2_ctx* ctx, double alpha, const h2_matrix* X, int64_t bx, const h2_matrix* Y, int64_t by,
+                 h2_matrix* Z, int64_t bz, double eps, int64_t* updates);
+
 /* X <- R^-1 L^-1 X for a factor from h2_lr_factor: block forward and
  * backward substitution (Section 3).  X: DEVICE n x nrhs, column-major, ld
  * ldx, rows in TREE order.  Synchronizes. */

@@ -34,7 +34,7 @@ EXPORTS = [
     "h2_batch_update_items", "h2_batch_set_mode", "h2_batch_paths", "h2_lowrank_update",
     "h2_lowrank_update_noalloc", "h2_lowrank_update_sequence", "h2_matvec", "h2_block_to_dense",
     "h2_sequence_waves", "h2_check_reciprocal",
-    "h2_build_fem", "h2_lr_factor", "h2_lr_solve", "h2_pcg", "h2_lr_error",
+    "h2_build_fem", "h2_lr_factor", "h2_lr_solve", "h2_pcg", "h2_lr_error", "h2_mul",
 ]
 
 PHASES = ("base_weights", "rfactor", "norms", "weights", "truncate", "reproject", "exact", "bases")
@@ -117,6 +117,7 @@ _sig("h2_lr_factor", _int, _p, _p, C.POINTER(Options), _p)
 _sig("h2_lr_solve", _int, _p, _p, _i64, _p, _i64)
 _sig("h2_pcg", _int, _p, _p, _p, _p, _p, _dbl, _int, _p, _p)
 _sig("h2_lr_error", _int, _p, _p, _p, _p, _int, _p)
+_sig("h2_mul", _int, _p, _dbl, _p, _i64, _p, _i64, _p, _i64, _dbl, _p)
 _sig("h2_matvec", _int, _p, _p, _i64, _dbl, _p, _i64, _dbl, _p, _i64)
 _sig("h2_lowrank_update_sequence", _int, _p, _p, _i64, _p, _int, _p, _p, _dbl, _p)
 _sig("h2_batch_result_offsets", _int, _p, _p, _p)
@@ -532,4 +533,12 @@ def h2_lr_error(ctx, A, LR, v_dev: int, iters: int):
     err = C.c_double(0.0)
     _check(_lib.h2_lr_error(ctx, A, LR, C.c_void_p(v_dev), int(iters), C.byref(err)), ctx)
     return err.value
+
+
+def h2_mul(ctx, alpha: float, X, bx: int, Y, by: int, Z, bz: int, eps: float) -> int:
+    """Z|_bz += alpha X|_bx Y|_by (three matrices on one block tree); returns
+    the number of local updates."""
+    n = C.c_int64(0)
+    _check(_lib.h2_mul(ctx, float(alpha), X, int(bx), Y, int(by), Z, int(bz), float(eps), C.byref(n)), ctx)
+    return n.value
 

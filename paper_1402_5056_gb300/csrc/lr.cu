@@ -129,6 +129,8 @@ void zero(double* p, size_t n, cudaStream_t st) {
 struct Lr {
   h2_ctx* ctx = nullptr;
   h2_matrix* Z = nullptr;
+  const h2_matrix* X = nullptr;   // factors of the current product (nullptr: Z itself)
+  const h2_matrix* Y = nullptr;
   double eps = 0.0;
   cudaStream_t st = nullptr;
   int64_t updates = 0;
@@ -167,8 +169,8 @@ const int64_t* near_offsets(Lr& L) {
   return L.dnear_off;
 }
 
-void ensure_work(Lr& L, int m) {
-  const size_t need = (size_t)L.Z->rows.count() * L.Z->kcap * std::max(m, 1);
+void ensure_work(Lr& L, int m, int kcap) {
+  const size_t need = (size_t)L.Z->rows.count() * kcap * std::max(m, 1);
   if (need <= L.wcap) return;
   H2_CUDA(cudaStreamSynchronize(L.st));
   if (L.xh) cudaFree(L.xh);
@@ -229,10 +231,10 @@ void level_runs(const ClusterTree& ct, int32_t c, bool bottom_up, bool skip_root
 }
 
 // Y (Y-side rows of b x m) += alpha op(Z|_b) X (X-side rows x m)
-void block_prod(Lr& L, int32_t b, int trans, double alpha, const double* X, int64_t ldx, double* Y, int64_t ldy,
-                int m) {
+void block_prod(Lr& L, const h2_matrix* Zb, int32_t b, int trans, double alpha, const double* X, int64_t ldx,
+                double* Y, int64_t ldy, int m) {
   if (m <= 0) return;
-  h2_matrix* Z = L.Z;
+  const h2_matrix* Z = Zb;
   const BlockTree& bt = Z->blocks;
   const int in_side = trans ? 0 : 1, out_side = trans ? 1 : 0;
   const ClusterTree& tin = tree(Z, in_side);
@@ -251,7 +253,7 @@ void block_prod(Lr& L, int32_t b, int trans, double alpha, const double* X, int6
         if (bt.son4[4 * x + k] >= 0) stack.push_back(bt.son4[4 * x + k]);
   }
   if (adm.empty() && near.empty()) return;
-  ensure_work(L, m);
+  ensure_work(L, m, Z->kcap);
   BlockProd a{};
   a.in = view(Z, in_side);
   a.out = view(Z, out_side);
@@ -349,12 +351,11 @@ void block_prod(Lr& L, int32_t b, int trans, double alpha, const double* X, int6
 }
 
 // out (#c x k_c, ld) = the basis of cluster c of one side (Eq. (nested))
-void expand(Lr& L, int side, int32_t c, double* out, int64_t ld) {
-  h2_matrix* Z = L.Z;
+void expand(Lr& L, const h2_matrix* Z, int side, int32_t c, double* out, int64_t ld) {
   const ClusterTree& ct = tree(Z, side);
   const int k = (side == 0 ? Z->V : Z->W).rank[c];
   if (k == 0) return;
-  ensure_work(L, k);
+  ensure_work(L, k, Z->kcap);
   BlockProd a{};
   a.in = view(Z, side);
   a.out = view(Z, side);
@@ -460,48 +461,49 @@ DArr identity(Lr& L, int64_t n) {
 
 // the term alpha X|_x Y|_y when x or y is a leaf (Section 6, Case 2)
 Term case2(Lr& L, double alpha, int32_t x, int32_t y, bool near_target) {
-  h2_matrix* Z = L.Z;
+  const h2_matrix* Z = L.Z;
+  const h2_matrix* MX = L.X ? L.X : L.Z;   // the factors (the product's X and Y)
+  const h2_matrix* MY = L.Y ? L.Y : L.Z;
   const BlockTree& bt = Z->blocks;
   const int32_t t = bt.row[x], s = bt.col[x], r = bt.col[y];
   const int64_t mt = csize(Z, t), ms = csize(Z, s), mr = csize(Z, r);
   Term T;
   T.tc = t;
   T.rc = r;
-  const int kcap = Z->kcap;
   if (bt.kind[y] == kAdm) {
     // (X|_x V_s) S_y, W_r
-    const int ks = rank_of(Z, 0, s), lr = rank_of(Z, 1, r);
+    const int ks = rank_of(MY, 0, s), lr = rank_of(MY, 1, r);
     T.u = lr;
     if (lr == 0) return T;
     DArr Vs(ms * std::max(ks, 1), L.st), Xt(mt * std::max(ks, 1), L.st);
     T.A = DArr(mt * lr, L.st);
     T.B = DArr(mr * lr, L.st);
     if (ks > 0) {
-      expand(L, 0, s, Vs.p, ms);
+      expand(L, MY, 0, s, Vs.p, ms);
       zero(Xt.p, mt * ks, L.st);
-      block_prod(L, x, 0, 1.0, Vs.p, ms, Xt.p, mt, ks);
-      launch_gemm((int)mt, lr, ks, alpha, Xt.p, mt, 0, coupling_ptr(Z, y), kcap, 0, 0.0, T.A.p, mt, L.st);
+      block_prod(L, MX, x, 0, 1.0, Vs.p, ms, Xt.p, mt, ks);
+      launch_gemm((int)mt, lr, ks, alpha, Xt.p, mt, 0, coupling_ptr(MY, y), MY->kcap, 0, 0.0, T.A.p, mt, L.st);
     } else {
       zero(T.A.p, mt * lr, L.st);
     }
-    expand(L, 1, r, T.B.p, mr);
+    expand(L, MY, 1, r, T.B.p, mr);
     ++L.products;
     return T;
   }
   if (bt.kind[x] == kAdm) {
     // V_t, (Y|_y^* W_s) S_x^*
-    const int kt = rank_of(Z, 0, t), ls = rank_of(Z, 1, s);
+    const int kt = rank_of(MX, 0, t), ls = rank_of(MX, 1, s);
     T.u = kt;
     if (kt == 0) return T;
     DArr Ws(ms * std::max(ls, 1), L.st), Yt(mr * std::max(ls, 1), L.st);
     T.A = DArr(mt * kt, L.st);
     T.B = DArr(mr * kt, L.st);
-    expand(L, 0, t, T.A.p, mt);
+    expand(L, MX, 0, t, T.A.p, mt);
     if (ls > 0) {
-      expand(L, 1, s, Ws.p, ms);
+      expand(L, MX, 1, s, Ws.p, ms);
       zero(Yt.p, mr * ls, L.st);
-      block_prod(L, y, 1, 1.0, Ws.p, ms, Yt.p, mr, ls);
-      launch_gemm((int)mr, kt, ls, alpha, Yt.p, mr, 0, coupling_ptr(Z, x), kcap, 1, 0.0, T.B.p, mr, L.st);
+      block_prod(L, MY, y, 1, 1.0, Ws.p, ms, Yt.p, mr, ls);
+      launch_gemm((int)mr, kt, ls, alpha, Yt.p, mr, 0, coupling_ptr(MX, x), MX->kcap, 1, 0.0, T.B.p, mr, L.st);
     } else {
       zero(T.B.p, mr * kt, L.st);
     }
@@ -517,15 +519,15 @@ Term case2(Lr& L, double alpha, int32_t x, int32_t y, bool near_target) {
     T.A = DArr(mt * mr, L.st);
     zero(T.A.p, mt * mr, L.st);
     if (xn && yn) {
-      launch_gemm((int)mt, (int)mr, (int)ms, alpha, near_ptr(Z, x), mt, 0, near_ptr(Z, y), ms, 0, 0.0, T.A.p, mt,
+      launch_gemm((int)mt, (int)mr, (int)ms, alpha, near_ptr(MX, x), mt, 0, near_ptr(MY, y), ms, 0, 0.0, T.A.p, mt,
                   L.st);
     } else if (yn) {   // X subdivided: X Y by the block product with Y's columns
-      block_prod(L, x, 0, alpha, near_ptr(Z, y), ms, T.A.p, mt, (int)mr);
+      block_prod(L, MX, x, 0, alpha, near_ptr(MY, y), ms, T.A.p, mt, (int)mr);
     } else {           // Y subdivided: P^* = Y^* (alpha X^*) by the transposed block product
       DArr Xt(ms * mt, L.st), Pt(mr * mt, L.st);
-      launch_transpose((int)mt, (int)ms, alpha, near_ptr(Z, x), mt, Xt.p, ms, L.st);
+      launch_transpose((int)mt, (int)ms, alpha, near_ptr(MX, x), mt, Xt.p, ms, L.st);
       zero(Pt.p, mr * mt, L.st);
-      block_prod(L, y, 1, 1.0, Xt.p, ms, Pt.p, mr, (int)mt);
+      block_prod(L, MY, y, 1, 1.0, Xt.p, ms, Pt.p, mr, (int)mt);
       launch_transpose((int)mr, (int)mt, 1.0, Pt.p, mr, T.A.p, mt, L.st);
     }
     return T;
@@ -536,8 +538,8 @@ Term case2(Lr& L, double alpha, int32_t x, int32_t y, bool near_target) {
     T.u = (int)ms;
     T.A = DArr(mt * ms, L.st);
     T.B = DArr(mr * ms, L.st);
-    launch_axpby(mt * ms, alpha, near_ptr(Z, x), 0.0, T.A.p, L.st);
-    launch_transpose((int)ms, (int)mr, 1.0, near_ptr(Z, y), ms, T.B.p, mr, L.st);
+    launch_axpby(mt * ms, alpha, near_ptr(MX, x), 0.0, T.A.p, L.st);
+    launch_transpose((int)ms, (int)mr, 1.0, near_ptr(MY, y), ms, T.B.p, mr, L.st);
     return T;
   }
   if (mt <= mr) {
@@ -547,12 +549,12 @@ Term case2(Lr& L, double alpha, int32_t x, int32_t y, bool near_target) {
     T.B = DArr(mr * mt, L.st);
     zero(T.B.p, mr * mt, L.st);
     if (xn && yn) {
-      launch_gemm((int)mr, (int)mt, (int)ms, alpha, near_ptr(Z, y), ms, 1, near_ptr(Z, x), mt, 1, 0.0, T.B.p, mr,
+      launch_gemm((int)mr, (int)mt, (int)ms, alpha, near_ptr(MY, y), ms, 1, near_ptr(MX, x), mt, 1, 0.0, T.B.p, mr,
                   L.st);
     } else if (xn) {   // Y subdivided: Y^* (alpha X^*) by the transposed block product
       DArr Xt(ms * mt, L.st);
-      launch_transpose((int)mt, (int)ms, alpha, near_ptr(Z, x), mt, Xt.p, ms, L.st);
-      block_prod(L, y, 1, 1.0, Xt.p, ms, T.B.p, mr, (int)mt);
+      launch_transpose((int)mt, (int)ms, alpha, near_ptr(MX, x), mt, Xt.p, ms, L.st);
+      block_prod(L, MY, y, 1, 1.0, Xt.p, ms, T.B.p, mr, (int)mt);
     } else {
       throw Error(H2_EINTERNAL, "dense term: unexpected block kinds");
     }
@@ -564,10 +566,10 @@ Term case2(Lr& L, double alpha, int32_t x, int32_t y, bool near_target) {
   T.B = identity(L, mr);
   zero(T.A.p, mt * mr, L.st);
   if (xn && yn) {
-    launch_gemm((int)mt, (int)mr, (int)ms, alpha, near_ptr(Z, x), mt, 0, near_ptr(Z, y), ms, 0, 0.0, T.A.p, mt,
+    launch_gemm((int)mt, (int)mr, (int)ms, alpha, near_ptr(MX, x), mt, 0, near_ptr(MY, y), ms, 0, 0.0, T.A.p, mt,
                 L.st);
   } else if (yn) {
-    block_prod(L, x, 0, alpha, near_ptr(Z, y), ms, T.A.p, mt, (int)mr);
+    block_prod(L, MX, x, 0, alpha, near_ptr(MY, y), ms, T.A.p, mt, (int)mr);
   } else {
     throw Error(H2_EINTERNAL, "dense term: unexpected block kinds");
   }
@@ -716,7 +718,7 @@ void lsolve_dense(Lr& L, int32_t d, double* Y, int64_t ldy, int m) {
   const int32_t t1 = Z->rows.son0[t], t2 = Z->rows.son1[t];
   const int64_t n1 = csize(Z, t1);
   lsolve_dense(L, son(bt, d, t1, t1), Y, ldy, m);
-  block_prod(L, son(bt, d, t2, t1), 0, -1.0, Y, ldy, Y + n1, ldy, m);
+  block_prod(L, L.Z, son(bt, d, t2, t1), 0, -1.0, Y, ldy, Y + n1, ldy, m);
   lsolve_dense(L, son(bt, d, t2, t2), Y + n1, ldy, m);
 }
 
@@ -732,7 +734,7 @@ void usolve_dense(Lr& L, int32_t d, double* Y, int64_t ldy, int m) {
   const int32_t t1 = Z->rows.son0[t], t2 = Z->rows.son1[t];
   const int64_t n1 = csize(Z, t1);
   usolve_dense(L, son(bt, d, t2, t2), Y + n1, ldy, m);
-  block_prod(L, son(bt, d, t1, t2), 0, -1.0, Y + n1, ldy, Y, ldy, m);
+  block_prod(L, L.Z, son(bt, d, t1, t2), 0, -1.0, Y + n1, ldy, Y, ldy, m);
   usolve_dense(L, son(bt, d, t1, t1), Y, ldy, m);
 }
 
@@ -753,7 +755,7 @@ void rsolve_dense_t(Lr& L, int32_t d, double* Yt, int64_t ldy, int m) {
   const int32_t s1 = Z->rows.son0[s], s2 = Z->rows.son1[s];
   const int64_t n1 = csize(Z, s1);
   rsolve_dense_t(L, son(bt, d, s1, s1), Yt, ldy, m);
-  block_prod(L, son(bt, d, s1, s2), 1, -1.0, Yt, ldy, Yt + n1, ldy, m);
+  block_prod(L, L.Z, son(bt, d, s1, s2), 1, -1.0, Yt, ldy, Yt + n1, ldy, m);
   rsolve_dense_t(L, son(bt, d, s2, s2), Yt + n1, ldy, m);
 }
 
@@ -776,10 +778,10 @@ void lsolve(Lr& L, int32_t d, int32_t x) {
     DArr Vt(mt * kt, L.st), Xh(mt * ls, L.st), Ws(ms * ls, L.st);
     {
       Timer tm(L.t_solves);
-      expand(L, 0, t, Vt.p, mt);
+      expand(L, L.Z, 0, t, Vt.p, mt);
       launch_gemm((int)mt, ls, kt, 1.0, Vt.p, mt, 0, coupling_ptr(Z, x), Z->kcap, 0, 0.0, Xh.p, mt, L.st);
       lsolve_dense(L, d, Xh.p, mt, ls);
-      expand(L, 1, s, Ws.p, ms);
+      expand(L, L.Z, 1, s, Ws.p, ms);
     }
     H2_CUDA(cudaMemsetAsync(coupling_ptr(Z, x), 0, (size_t)Z->kcap * Z->kcap * sizeof(double), L.st));
     apply_update(L, x, Xh.p, mt, Ws.p, ms, ls);
@@ -813,10 +815,10 @@ void rsolve(Lr& L, int32_t d, int32_t x) {
     DArr Ws(ms * ls, L.st), Bh(ms * kt, L.st), Vt(mt * kt, L.st);
     {
       Timer tm(L.t_solves);
-      expand(L, 1, s, Ws.p, ms);
+      expand(L, L.Z, 1, s, Ws.p, ms);
       launch_gemm((int)ms, kt, ls, 1.0, Ws.p, ms, 0, coupling_ptr(Z, x), Z->kcap, 1, 0.0, Bh.p, ms, L.st);
       rsolve_dense_t(L, d, Bh.p, ms, kt);
-      expand(L, 0, t, Vt.p, mt);
+      expand(L, L.Z, 0, t, Vt.p, mt);
     }
     H2_CUDA(cudaMemsetAsync(coupling_ptr(Z, x), 0, (size_t)Z->kcap * Z->kcap * sizeof(double), L.st));
     apply_update(L, x, Vt.p, mt, Bh.p, ms, kt);
@@ -1216,5 +1218,37 @@ extern "C" h2_status h2_lr_error(h2_ctx* ctx, const h2_matrix* A, const h2_matri
     }
     H2_CUDA(cudaStreamSynchronize(st));
     *err = lam;
+  });
+}
+
+extern "C" h2_status h2_mul(h2_ctx* ctx, double alpha, const h2_matrix* X, int64_t bx, const h2_matrix* Y,
+                            int64_t by, h2_matrix* Z, int64_t bz, double eps, int64_t* updates) {
+  if (!ctx || !X || !Y || !Z) return H2_EINVAL;
+  return lr_guard(ctx, [&] {
+    H2_REQUIRE(std::isfinite(eps) && eps >= 0 && std::isfinite(alpha), "h2_mul: eps and alpha must be finite");
+    check_square(Z);
+    const BlockTree& bt = Z->blocks;
+    for (const h2_matrix* M : {X, Y})
+      H2_REQUIRE(M->rows.off == Z->rows.off && M->rows.son0 == Z->rows.son0 && M->blocks.row == bt.row &&
+                     M->blocks.col == bt.col && M->blocks.kind == bt.kind && M->device == Z->device &&
+                     M->d_row_off != nullptr,
+                 "h2_mul: X and Y must have Z's cluster tree, block tree and device");
+    const int64_t nb = bt.count();
+    H2_REQUIRE(bx >= 0 && bx < nb && by >= 0 && by < nb && bz >= 0 && bz < nb, "h2_mul: block out of range");
+    H2_REQUIRE(bt.row[bx] == bt.row[bz] && bt.col[bx] == bt.row[by] && bt.col[by] == bt.col[bz],
+               "h2_mul: blocks must be (t,s), (s,r), (t,r)");
+    DevGuard g(ctx->device);
+    Lr L;
+    L.ctx = ctx;
+    L.Z = Z;
+    L.X = X == Z ? nullptr : X;
+    L.Y = Y == Z ? nullptr : Y;
+    L.eps = eps;
+    L.st = ctx->stream;
+    mul(L, alpha, (int32_t)bx, (int32_t)by, (int32_t)bz);
+    H2_CUDA(cudaStreamSynchronize(L.st));
+    h2_status s = h2_ctx_synchronize(ctx);
+    if (s != H2_OK) throw Error(s, ctx->last_error);
+    if (updates) *updates = L.updates;
   });
 }

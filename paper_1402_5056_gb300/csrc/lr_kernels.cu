@@ -395,7 +395,10 @@ __global__ void __launch_bounds__(1024) k_core_svd(const double* XA, int64_t lda
   __syncthreads();
   // one-sided Jacobi on the columns of C, round-robin pairs, one warp a pair
   const int n2 = kb + (kb & 1);
-  const double tol2 = 1e-30;   // (1e-15)^2
+  // rotate while |gamma| > 64 u sqrt(alpha beta): a smaller threshold lies
+  // below the rounding of the dot products (up to 256 terms) and the sweeps
+  // would not end
+  const double tol2 = (64.0 * 2.220446049250313e-16) * (64.0 * 2.220446049250313e-16);
   for (int sweep = 0; sweep < 40 && kb > 1; ++sweep) {
     if (tid == 0) any_rot = 0;
     __syncthreads();

@@ -103,3 +103,23 @@ def oracle_problem_general(points, k, seed, leaf, eta=2.0):
     Z.set_couplings(d["S"])
     Z.set_nearfield(d["N"])
     return Z, d["streams"], pts
+
+
+def block_triples(bt, ct):
+    """(x, y, z) = ((t,s), (s,r), (t,r)) all blocks of the tree, one per
+    combination of kinds."""
+    where = {(bt.row[b], bt.col[b]): b for b in range(bt.n_blocks)}
+    seen = {}
+    for x in range(bt.n_blocks):
+        t, s = bt.row[x], bt.col[x]
+        for y in range(bt.n_blocks):
+            if bt.row[y] != s:
+                continue
+            r = bt.col[y]
+            z = where.get((t, r))
+            if z is None:
+                continue
+            key = (bt.kind[x], bt.kind[y], bt.kind[z])
+            if key not in seen and ct.size[t] <= 200 and ct.size[r] <= 200:
+                seen[key] = (x, y, z)
+    return seen

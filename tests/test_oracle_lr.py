@@ -26,7 +26,7 @@ from oracle.fem import h2_from_sparse, stiffness
 from oracle.lr import (_Ctx, _mul, lr_factor, lr_solve, lsolve_dense, lu_doolittle, mul, pcg, power_error,
                        rsolve_dense, usolve_dense)
 from oracle.tree import BlockTree
-from problems import oracle_problem
+from problems import block_triples as _triples, oracle_problem
 
 
 def _fem(N, leaf, seed=0, M=4):
@@ -85,26 +85,6 @@ def test_substitutions_are_dense_triangular_solves():
     Yr = Y.T.copy()
     assert np.allclose(rsolve_dense(Z, 0, Yr), la.solve_triangular(Rm.T, Yr.T, lower=True).T, rtol=0, atol=1e-10)
     assert np.allclose(lr_solve(Z, Y), np.linalg.solve(A, Y), rtol=0, atol=1e-9)
-
-
-def _triples(bt, ct):
-    """(x, y, z) = ((t,s), (s,r), (t,r)) all blocks of the tree, one per
-    combination of kinds."""
-    where = {(bt.row[b], bt.col[b]): b for b in range(bt.n_blocks)}
-    seen = {}
-    for x in range(bt.n_blocks):
-        t, s = bt.row[x], bt.col[x]
-        for y in range(bt.n_blocks):
-            if bt.row[y] != s:
-                continue
-            r = bt.col[y]
-            z = where.get((t, r))
-            if z is None:
-                continue
-            key = (bt.kind[x], bt.kind[y], bt.kind[z])
-            if key not in seen and ct.size[t] <= 200 and ct.size[r] <= 200:
-                seen[key] = (x, y, z)
-    return seen
 
 
 def test_product_is_exact_without_truncation():
