@@ -674,10 +674,10 @@ void apply_temp(Lr& L, const Temp& tmp) {
   // Householder QR of both factors, SVD of the core R_A R_B^*, rank rule,
   // A' = Q_A U_r Sigma_r, B' = Q_B W_r
   DArr tauA(m, L.st), tauB(m, L.st), C(m * m, L.st), W(m * m, L.st), TA(m * m, L.st), TB(m * m, L.st);
-  if (!L.drank) H2_CUDA(cudaMalloc(&L.drank, sizeof(int)));
-  launch_house_qr(A.p, mt, (int)mt, B.p, mr, (int)mr, m, tauA.p, tauB.p, L.st);
+  if (!L.drank) H2_CUDA(cudaMalloc(&L.drank, 3 * sizeof(int)));   // rank, nonzero flags of A and B
+  launch_house_qr(A.p, mt, (int)mt, B.p, mr, (int)mr, m, tauA.p, tauB.p, L.drank + 1, L.st);
   const int ka = (int)std::min<int64_t>(mt, m), kb = (int)std::min<int64_t>(mr, m);
-  launch_core_svd(A.p, mt, ka, B.p, mr, kb, m, L.eps, C.p, W.p, TA.p, TB.p, L.drank, L.st);
+  launch_core_svd(A.p, mt, ka, B.p, mr, kb, m, L.eps, L.drank + 1, C.p, W.p, TA.p, TB.p, L.drank, L.st);
   int rk = 0;
   H2_CUDA(cudaMemcpyAsync(&rk, L.drank, sizeof(int), cudaMemcpyDeviceToHost, L.st));
   {

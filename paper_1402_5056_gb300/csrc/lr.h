@@ -75,10 +75,12 @@ void launch_trsm(int kind, const double* F, int m, int64_t ldf, double* X, int n
 // of the core R_A R_B^* by one-sided Jacobi and the rank rule (C, W: m x m
 // scratch; TA, TB: m x m, first r columns; *rank on the device), then
 // A' = Q_A [TA; 0] into OA (rows_a x r), B' = Q_B [TB; 0] into OB
+// nonzero (2 ints, device): whether A and B have a nonzero entry (written
+// by the QR; the core SVD returns rank 0 at once for a zero product)
 void launch_house_qr(double* A, int64_t lda, int rows_a, double* B, int64_t ldb, int rows_b, int m, double* tau_a,
-                     double* tau_b, cudaStream_t st);
+                     double* tau_b, int* nonzero, cudaStream_t st);
 void launch_core_svd(const double* A, int64_t lda, int ka, const double* B, int64_t ldb, int kb, int m, double eps,
-                     double* C, double* W, double* TA, double* TB, int* rank, cudaStream_t st);
+                     const int* nonzero, double* C, double* W, double* TA, double* TB, int* rank, cudaStream_t st);
 void launch_apply_q(const double* A, int64_t lda, int rows_a, const double* tau_a, const double* TA, double* OA,
                     const double* B, int64_t ldb, int rows_b, const double* tau_b, const double* TB, double* OB,
                     int m, int r, cudaStream_t st);

@@ -297,14 +297,29 @@ __global__ void k_axpby(int64_t n, double a, const double* x, double b, double* 
 
 // QR of the rows x m matrix X (ld ldx) in place; tau (m entries).  One block.
 __global__ void __launch_bounds__(512) k_house_qr(double* XA, int64_t lda, int rows_a, double* XB, int64_t ldb, int rows_b, int m,
-                           double* tau_a, double* tau_b) {
+                           double* tau_a, double* tau_b, int* nonzero) {
   double* X = blockIdx.x == 0 ? XA : XB;
   const int64_t ldx = blockIdx.x == 0 ? lda : ldb;
   const int rows = blockIdx.x == 0 ? rows_a : rows_b;
   double* tau = blockIdx.x == 0 ? tau_a : tau_b;
   __shared__ double red[32];
   __shared__ double sh_beta, sh_tau, sh_scale;
+  __shared__ int any;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  // an all-zero factor (most temporaries of the factorisation have one):
+  // the product is zero and the core SVD returns rank 0 at once
+  if (tid == 0) any = 0;
+  __syncthreads();
+  int mine = 0;
+  for (int64_t e = tid; e < (int64_t)rows * m; e += nt)
+    if (X[e % rows + (e / rows) * ldx] != 0.0) mine = 1;
+  if (__any_sync(0xffffffffu, mine) && lane == 0) any = 1;
+  __syncthreads();
+  if (tid == 0) nonzero[blockIdx.x] = any;
+  if (!any) {
+    for (int j = tid; j < m; j += nt) tau[j] = 0.0;
+    return;
+  }
   const int kk = min(rows, m);
   for (int j = 0; j < kk; ++j) {
     double* x = X + j + (int64_t)j * ldx;       // column j from the diagonal down
@@ -363,11 +378,15 @@ __device__ __forceinline__ int rr_partner(int i, int r, int n2, int& p, int& q) 
 // scratch); writes T = U_r Sigma_r = C W_r (ka x r, ld m) into TA, W_r into
 // TB (kb x r, ld m), the rank into *rank.  One block.
 __global__ void __launch_bounds__(1024) k_core_svd(const double* XA, int64_t lda, int ka, const double* XB, int64_t ldb, int kb, int m,
-                           double eps, double* C, double* W, double* TA, double* TB, int* rank) {
+                           double eps, const int* nonzero, double* C, double* W, double* TA, double* TB, int* rank) {
   __shared__ int order[256];
   __shared__ double nrm2[256];
   __shared__ int any_rot;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  if (!nonzero[0] || !nonzero[1]) {   // A B^* = 0
+    if (tid == 0) *rank = 0;
+    return;
+  }
   // C = R_A R_B^* (upper triangles)
   for (int e = tid; e < ka * kb; e += nt) {
     const int i = e % ka, j = e / ka;
@@ -573,13 +592,13 @@ void launch_trsm(int kind, const double* F, int m, int64_t ldf, double* X, int n
 }
 
 void launch_house_qr(double* A, int64_t lda, int rows_a, double* B, int64_t ldb, int rows_b, int m, double* tau_a,
-                     double* tau_b, cudaStream_t st) {
-  k_house_qr<<<2, 512, 0, st>>>(A, lda, rows_a, B, ldb, rows_b, m, tau_a, tau_b);
+                     double* tau_b, int* nonzero, cudaStream_t st) {
+  k_house_qr<<<2, 512, 0, st>>>(A, lda, rows_a, B, ldb, rows_b, m, tau_a, tau_b, nonzero);
 }
 
 void launch_core_svd(const double* A, int64_t lda, int ka, const double* B, int64_t ldb, int kb, int m, double eps,
-                     double* C, double* W, double* TA, double* TB, int* rank, cudaStream_t st) {
-  k_core_svd<<<1, 1024, 0, st>>>(A, lda, ka, B, ldb, kb, m, eps, C, W, TA, TB, rank);
+                     const int* nonzero, double* C, double* W, double* TA, double* TB, int* rank, cudaStream_t st) {
+  k_core_svd<<<1, 1024, 0, st>>>(A, lda, ka, B, ldb, kb, m, eps, nonzero, C, W, TA, TB, rank);
 }
 
 void launch_apply_q(const double* A, int64_t lda, int rows_a, const double* tau_a, const double* TA, double* OA,
