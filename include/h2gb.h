@@ -470,6 +470,19 @@ h2_status h2_lr_error(h2_ctx* ctx, const h2_matrix* A, const h2_matrix* LR, doub
  * d, out: DEVICE arrays of n doubles.  Asynchronous. */
 h2_status h2_check_reciprocal(h2_ctx* ctx, const double* d, int64_t n, double* out);
 
+/* Test hook for the error paths (no counterpart in the paper): the n-th
+ * device allocation the library makes from now on, in any context and
+ * thread, fails as if the device were out of memory, so that the call making
+ * it returns H2_ENOMEM; n = 0 switches the hook off, and it is off again
+ * once it has fired.  A local update allocates everything it needs before
+ * its first write to the matrix, so an H2_ENOMEM from h2_lowrank_update or
+ * h2_batch_apply leaves the matrix unchanged (its rank capacity may have
+ * grown) and frees what the call allocated; after one from
+ * h2_lowrank_update_sequence every update of the sequence is either applied
+ * whole or not at all.  h2_lr_factor and h2_mul may have changed the matrix
+ * when they fail.  Returns H2_EINVAL for n < 0. */
+h2_status h2_debug_fail_allocation(int64_t n);
+
 #ifdef __cplusplus
 }
 #endif

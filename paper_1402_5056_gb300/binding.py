@@ -33,7 +33,7 @@ EXPORTS = [
     "h2_batch_stats", "h2_batch_set_timing", "h2_batch_phase_stats", "h2_batch_item_info", "h2_batch_item_tile",
     "h2_batch_update_items", "h2_batch_set_mode", "h2_batch_paths", "h2_lowrank_update",
     "h2_lowrank_update_noalloc", "h2_lowrank_update_sequence", "h2_matvec", "h2_block_to_dense",
-    "h2_sequence_waves", "h2_check_reciprocal",
+    "h2_sequence_waves", "h2_check_reciprocal", "h2_debug_fail_allocation",
     "h2_build_fem", "h2_lr_factor", "h2_lr_solve", "h2_pcg", "h2_lr_error", "h2_mul",
 ]
 
@@ -102,6 +102,7 @@ _sig("h2_batch_result_size", _int, _p, _p)
 _sig("h2_sequence_waves", _int, _p, _i64, _p, _p, _p)
 _sig("h2_block_to_dense", _int, _p, _p, _i64, _p, _i64)
 _sig("h2_check_reciprocal", _int, _p, _p, _i64, _p)
+_sig("h2_debug_fail_allocation", _int, _i64)
 
 
 class Options(C.Structure):
@@ -488,6 +489,12 @@ def h2_check_reciprocal(ctx, d_dev: int, n: int, out_dev: int):
     """The pivot reciprocal of the factorisation kernels, element by element
     (device arrays of n doubles)."""
     _check(_lib.h2_check_reciprocal(ctx, C.c_void_p(d_dev), int(n), C.c_void_p(out_dev)), ctx)
+
+
+def h2_debug_fail_allocation(n: int):
+    """Make the n-th device allocation of the library from now on fail with
+    H2_ENOMEM (n = 0: off).  A test hook for the error paths."""
+    _check(_lib.h2_debug_fail_allocation(int(n)))
 
 
 def options(eps=1e-4, eta=2.0, leaf_size=32, precision=0):

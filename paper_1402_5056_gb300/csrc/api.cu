@@ -15,19 +15,55 @@ using namespace h2;
 
 // ===================================================================== misc
 namespace {
+// allocations left before the hook fails one (0: the hook is off)
+std::atomic<int64_t> g_fail_countdown{0};
+
+bool hook_fires() {
+  int64_t c = g_fail_countdown.load(std::memory_order_relaxed);
+  while (c > 0)
+    if (g_fail_countdown.compare_exchange_weak(c, c - 1, std::memory_order_relaxed)) return c == 1;
+  return false;
+}
+}  // namespace
+
+void* h2::device_alloc(size_t bytes) {
+  if (bytes == 0) return nullptr;
+  if (hook_fires()) throw Error(H2_ENOMEM, "device allocation failed (failure hook)");
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    throw Error(H2_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  return p;
+}
+
+void* h2::device_alloc_async(size_t bytes, cudaStream_t st) {
+  if (bytes == 0) return nullptr;
+  if (hook_fires()) throw Error(H2_ENOMEM, "device allocation failed (failure hook)");
+  void* p = nullptr;
+  cudaError_t e = cudaMallocAsync(&p, bytes, st);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    throw Error(H2_ENOMEM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
+  }
+  return p;
+}
+
+extern "C" h2_status h2_debug_fail_allocation(int64_t n) {
+  if (n < 0) return H2_EINVAL;
+  g_fail_countdown.store(n, std::memory_order_relaxed);
+  return H2_OK;
+}
+
+namespace {
 
 thread_local std::string g_null_ctx_error;
 
 template <typename T>
 T* dalloc(size_t count) {
   if (count == 0) return nullptr;
-  void* p = nullptr;
-  cudaError_t e = cudaMalloc(&p, count * sizeof(T));
-  if (e != cudaSuccess) {
-    (void)cudaGetLastError();
-    throw Error(H2_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
-  }
-  return static_cast<T*>(p);
+  return static_cast<T*>(device_alloc(count * sizeof(T)));
 }
 
 template <typename T>
@@ -40,8 +76,12 @@ template <typename T>
 T* upload(const std::vector<T>& v, cudaStream_t st) {
   T* d = dalloc<T>(v.size());
   if (!v.empty()) {
-    H2_CUDA(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
-    H2_CUDA(cudaStreamSynchronize(st));
+    cudaError_t e = cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      dfree(d);
+      H2_CUDA(e);
+    }
   }
   return d;
 }
@@ -139,6 +179,9 @@ void grow_kcap(h2_ctx* ctx, h2_matrix* Z, int kcap) {
   cudaStream_t st = ctx->stream;
   std::vector<CopyDesc> cd;
   DeviceBasis nb[2];
+  double* nS = nullptr;
+  CopyDesc* dcd = nullptr;
+  try {
   for (int s = 0; s < 2; ++s) {
     const ClusterTree& ct = tree_of(Z, s);
     DeviceBasis& ob = basis_of(Z, s);
@@ -155,7 +198,7 @@ void grow_kcap(h2_ctx* ctx, h2_matrix* Z, int kcap) {
     }
   }
   const size_t nadm = Z->blocks.adm.size();
-  double* nS = dalloc<double>(nadm * kcap * kcap);
+  nS = dalloc<double>(nadm * kcap * kcap);
   H2_CUDA(cudaMemsetAsync(nS, 0, nadm * kcap * kcap * sizeof(double), st));
   for (size_t a = 0; a < nadm; ++a) {
     const int32_t b = Z->blocks.adm[a];
@@ -163,10 +206,19 @@ void grow_kcap(h2_ctx* ctx, h2_matrix* Z, int kcap) {
     if (kt > 0 && ls > 0)
       cd.push_back({Z->d_S + a * Z->kcap * Z->kcap, nS + a * kcap * kcap, kt, ls, Z->kcap, kcap});
   }
-  CopyDesc* dcd = upload(cd, st);
+  dcd = upload(cd, st);
   launch_copy(dcd, (int)cd.size(), st);
   H2_CUDA(cudaGetLastError());
   H2_CUDA(cudaStreamSynchronize(st));
+  } catch (...) {
+    // Z keeps its storage; nothing of the new layout survives
+    (void)cudaStreamSynchronize(st);
+    free_basis(nb[0]);
+    free_basis(nb[1]);
+    dfree(nS);
+    dfree(dcd);
+    throw;
+  }
   dfree(dcd);
   for (int s = 0; s < 2; ++s) {
     free_basis(basis_of(Z, s));
@@ -1426,6 +1478,7 @@ h2_status create_batch(h2_ctx* ctx, const h2_matrix* Z, int64_t count, const int
     alloc_batch(ctx, *P);
   });
   if (s == H2_OK) *out = P.release();
+  else if (ctx) free_batch_device(*P);   // partial allocations
   return s;
 }
 }  // namespace
@@ -1717,7 +1770,12 @@ void commit_update(h2_ctx* ctx, const h2_batch* P, int64_t j, const double* A, c
       H2_CUDA(cudaMemcpyAsync(dnd, nd.data(), nd.size() * sizeof(NearDesc), cudaMemcpyHostToDevice, st));
   } else {
     dcd = upload(cd, st);
-    dnd = upload(nd, st);
+    try {
+      dnd = upload(nd, st);
+    } catch (...) {
+      dfree(dcd);
+      throw;
+    }
   }
   launch_copy(dcd, (int)cd.size(), st);
   launch_near_add(dnd, (int)nd.size(), P->u, st);
@@ -2366,13 +2424,15 @@ extern "C" h2_status h2_lowrank_update(h2_ctx* ctx, h2_matrix* Z, int64_t block,
     h2_status s = h2_batch_create(ctx, Z, 1, &block, u, &P);
     if (s != H2_OK) throw Error(s, ctx->last_error);
     std::unique_ptr<h2_batch, void (*)(h2_batch*)> hold(P, h2_batch_free);
-    double* dA = dalloc<double>(rows * u);
-    double* dB = dalloc<double>(cols * u);
-    H2_CUDA(cudaMemcpy2DAsync(dA, rows * sizeof(double), A, lda * sizeof(double), rows * sizeof(double), u,
-                              cudaMemcpyDeviceToDevice, st));
-    H2_CUDA(cudaMemcpy2DAsync(dB, cols * sizeof(double), B, ldb * sizeof(double), cols * sizeof(double), u,
-                              cudaMemcpyDeviceToDevice, st));
+    double* dA = nullptr;
+    double* dB = nullptr;
     try {
+      dA = dalloc<double>(rows * u);
+      dB = dalloc<double>(cols * u);
+      H2_CUDA(cudaMemcpy2DAsync(dA, rows * sizeof(double), A, lda * sizeof(double), rows * sizeof(double), u,
+                                cudaMemcpyDeviceToDevice, st));
+      H2_CUDA(cudaMemcpy2DAsync(dB, cols * sizeof(double), B, ldb * sizeof(double), cols * sizeof(double), u,
+                                cudaMemcpyDeviceToDevice, st));
       execute(ctx, *P, dA, dB, eps);
       s = h2_batch_apply(ctx, P, 0, dA, dB, Z);
       if (s != H2_OK) throw Error(s, ctx->last_error);
@@ -2529,12 +2589,14 @@ void ensure_matvec_plan(h2_matrix* Z, cudaStream_t st) {
     for (int l = 0; l < L; ++l) ptr[l + 1] += ptr[l];
     std::vector<int32_t> list(ct.count()), fill(ptr.begin(), ptr.end() - 1);
     for (int32_t c = 0; c < ct.count(); ++c) list[fill[ct.level[c]]++] = c;
+    dfree(Z->d_mv_lvl[sd]);   // a retry after a failed allocation
     Z->d_mv_lvl[sd] = upload(list, st);
   }
   std::vector<int32_t> leaves;
   for (int32_t c = 0; c < Z->rows.count(); ++c)
     if (Z->rows.leaf(c)) leaves.push_back(c);
   Z->mv_n_leaves = (int32_t)leaves.size();
+  dfree(Z->d_mv_leaves);
   Z->d_mv_leaves = upload(leaves, st);
   const BlockTree& bt = Z->blocks;
   std::vector<int32_t> nptr(Z->rows.count() + 1, 0), ncol(bt.near.size());
@@ -2548,6 +2610,9 @@ void ensure_matvec_plan(h2_matrix* Z, cudaStream_t st) {
     ncol[x] = bt.col[b];
     noff[x] = Z->near_off[bt.slot[b]];
   }
+  dfree(Z->d_near_ptr);
+  dfree(Z->d_near_col);
+  dfree(Z->d_near_off);
   Z->d_near_ptr = upload(nptr, st);
   Z->d_near_col = upload(ncol, st);
   Z->d_near_off = upload(noff, st);
@@ -2613,8 +2678,7 @@ extern "C" h2_status h2_matvec(h2_ctx* ctx, const h2_matrix* Zc, int64_t nrhs, d
     a.ldy = ldy;
     // per-cluster workspace, stream-ordered
     const size_t wx = (size_t)a.n_clusters[1] * Z->kcap * nrhs, wy = (size_t)a.n_clusters[0] * Z->kcap * nrhs;
-    void* w = nullptr;
-    if (wx + wy) H2_CUDA(cudaMallocAsync(&w, (wx + wy) * sizeof(double), st));
+    void* w = device_alloc_async((wx + wy) * sizeof(double), st);
     a.xh = static_cast<double*>(w);
     a.yh = a.xh ? a.xh + wx : nullptr;
     launch_matvec(a, st);
@@ -2656,8 +2720,7 @@ extern "C" h2_status h2_block_to_dense(h2_ctx* ctx, const h2_matrix* Z, int64_t 
     cudaStream_t st = ctx->stream;
     // Z|_{t x s} = rows t of Z times the unit columns of s (the whole matrix
     // product h2_matvec with #s right-hand sides)
-    void* w = nullptr;
-    H2_CUDA(cudaMallocAsync(&w, (size_t)(n_c + n_r) * ns * sizeof(double), st));
+    void* w = device_alloc_async((size_t)(n_c + n_r) * ns * sizeof(double), st);
     double* X = static_cast<double*>(w);
     double* Y = X + (size_t)n_c * ns;
     const int th = 256;

@@ -33,6 +33,13 @@ struct Error : std::runtime_error {
     if (!(cond)) throw ::h2::Error(H2_EINVAL, msg); \
   } while (0)
 
+// Every device allocation of the library goes through these two calls.
+// They throw Error(H2_ENOMEM) when the allocation fails, or when the
+// failure hook (h2_debug_fail_allocation) says this allocation is the one
+// to fail.
+void* device_alloc(size_t bytes);
+void* device_alloc_async(size_t bytes, cudaStream_t st);
+
 // Raise a kernel's dynamic shared memory limit once per device: `done` holds
 // one bit per device ordinal below 64 (above, the attribute is set on every
 // call).  Host threads with contexts of their own may call it at once; the

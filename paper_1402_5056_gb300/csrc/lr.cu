@@ -93,14 +93,7 @@ struct DArr {
   cudaStream_t st = nullptr;
   DArr() = default;
   DArr(size_t n, cudaStream_t s) : st(s) {
-    if (n == 0) return;
-    void* q = nullptr;
-    cudaError_t e = cudaMallocAsync(&q, n * sizeof(double), s);
-    if (e != cudaSuccess) {
-      (void)cudaGetLastError();
-      throw Error(H2_ENOMEM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
-    }
-    p = static_cast<double*>(q);
+    p = static_cast<double*>(device_alloc_async(n * sizeof(double), s));
   }
   DArr(const DArr&) = delete;
   DArr& operator=(const DArr&) = delete;
@@ -163,7 +156,7 @@ struct Lr {
 const int64_t* near_offsets(Lr& L) {
   if (!L.dnear_off && !L.Z->near_off.empty()) {
     const size_t n = L.Z->near_off.size();
-    H2_CUDA(cudaMalloc(&L.dnear_off, n * sizeof(int64_t)));
+    L.dnear_off = static_cast<int64_t*>(device_alloc(n * sizeof(int64_t)));
     H2_CUDA(cudaMemcpy(L.dnear_off, L.Z->near_off.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice));
   }
   return L.dnear_off;
@@ -177,8 +170,8 @@ void ensure_work(Lr& L, int m, int kcap) {
   if (L.yh) cudaFree(L.yh);
   L.xh = L.yh = nullptr;
   L.wcap = 0;
-  H2_CUDA(cudaMalloc(&L.xh, need * sizeof(double)));
-  H2_CUDA(cudaMalloc(&L.yh, need * sizeof(double)));
+  L.xh = static_cast<double*>(device_alloc(need * sizeof(double)));
+  L.yh = static_cast<double*>(device_alloc(need * sizeof(double)));
   L.wcap = need;
 }
 
@@ -187,8 +180,10 @@ int32_t* upload_list(Lr& L, const std::vector<int32_t>& v) {
     H2_CUDA(cudaStreamSynchronize(L.st));
     if (L.dlist) cudaFree(L.dlist);
     L.dlist = nullptr;
-    L.lcap = std::max<size_t>(v.size(), 2 * L.lcap);
-    H2_CUDA(cudaMalloc(&L.dlist, L.lcap * sizeof(int32_t)));
+    const size_t cap = std::max<size_t>(v.size(), 2 * L.lcap);
+    L.lcap = 0;
+    L.dlist = static_cast<int32_t*>(device_alloc(cap * sizeof(int32_t)));
+    L.lcap = cap;
   }
   // pageable source: the copy is staged before the call returns, and the
   // previous user of the device list ran earlier on the same stream
@@ -674,7 +669,7 @@ void apply_temp(Lr& L, const Temp& tmp) {
   // Householder QR of both factors, SVD of the core R_A R_B^*, rank rule,
   // A' = Q_A U_r Sigma_r, B' = Q_B W_r
   DArr tauA(m, L.st), tauB(m, L.st), C(m * m, L.st), W(m * m, L.st), TA(m * m, L.st), TB(m * m, L.st);
-  if (!L.drank) H2_CUDA(cudaMalloc(&L.drank, 3 * sizeof(int)));   // rank, nonzero flags of A and B
+  if (!L.drank) L.drank = static_cast<int*>(device_alloc(3 * sizeof(int)));   // rank, nonzero flags of A and B
   launch_house_qr(A.p, mt, (int)mt, B.p, mr, (int)mr, m, tauA.p, tauB.p, L.drank + 1, L.st);
   const int ka = (int)std::min<int64_t>(mt, m), kb = (int)std::min<int64_t>(mr, m);
   launch_core_svd(A.p, mt, ka, B.p, mr, kb, m, L.eps, L.drank + 1, C.p, W.p, TA.p, TB.p, L.drank, L.st);
