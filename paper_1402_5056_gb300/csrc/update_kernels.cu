@@ -103,174 +103,6 @@ __device__ __forceinline__ int jacobi_partner(int lane, int r, int n2) {
   return p < 0 ? p + nr : p;
 }
 
-// One-sided (Hestenes) Jacobi on the columns held by the lanes (a[] rows
-// valid, zero below): on return the columns are U * Sigma with mutually
-// orthogonal columns.  The two lanes of a pair split the dot products (the
-// first lane takes the even rows, the second the odd rows, one row each per
-// instruction) and add the partial sums in the same order, so both take the
-// same rotation.
-template <int MR>
-__device__ __forceinline__ void jacobi(double (&a)[MR], int rows, int ncol, int lane, unsigned long long* cnt,
-                       int* err) {
-  const int n2 = ncol + (ncol & 1);
-  const int nr = n2 - 1;
-  const double tol2 = (16.0 * DBL_EPSILON) * (16.0 * DBL_EPSILON);
-  unsigned long long pairs = 0, rots = 0, sweeps = 0;
-  bool converged = (ncol < 2);
-  for (int sweep = 0; sweep < kMaxSweeps && !converged; ++sweep) {
-    int any = 0;
-    ++sweeps;
-    for (int r = 0; r < nr; ++r) {
-      const int p = jacobi_partner(lane, r, n2);
-      const bool lo = lane < p;
-      double al = 0.0, be = 0.0, ga = 0.0;
-#pragma unroll
-      for (int h = 0; h < MR / 2; ++h)
-        if (2 * h < rows) {
-          const double r0 = a[2 * h], r1 = a[2 * h + 1];
-          const double got = __shfl_sync(kFull, lo ? r1 : r0, p);
-          const double xx = lo ? r0 : got;
-          const double yy = lo ? got : r1;
-          al = fma(xx, xx, al);
-          be = fma(yy, yy, be);
-          ga = fma(xx, yy, ga);
-        }
-      al += __shfl_sync(kFull, al, p);
-      be += __shfl_sync(kFull, be, p);
-      ga += __shfl_sync(kFull, ga, p);
-      const bool active = lane < n2 && p != lane;
-      // rotate when |gamma| > tol sqrt(alpha beta); the columns are scaled
-      // to max |entry| < 1, so the squares neither overflow nor matter when
-      // they underflow
-      const bool rot = active && ga * ga > tol2 * (al * be);
-      double c = 1.0, s = 0.0;
-      if (rot) {
-        // t = tan(theta) of the rotation that makes the pair orthogonal:
-        // t = gamma / (d + sign(d) sqrt(d^2 + gamma^2)), d = (beta - alpha) / 2
-        const double d = 0.5 * (be - al);
-        const double t = ga / (d + copysign(sqrt(fma(d, d, ga * ga)), d));
-        c = rsqrt(fma(t, t, 1.0));
-        s = c * t;
-      }
-      if (__any_sync(kFull, rot)) {
-#pragma unroll
-        for (int i = 0; i < MR; ++i)
-          if (i < rows) {
-            const double o = __shfl_sync(kFull, a[i], p);
-            if (rot) a[i] = lo ? fma(c, a[i], -s * o) : fma(s, o, c * a[i]);
-          }
-      }
-      if (active && lo) {
-        pairs += 1;
-        rots += rot ? 1 : 0;
-      }
-      any |= rot ? 1 : 0;
-    }
-    converged = !__any_sync(kFull, any);
-  }
-  if (!converged && lane == 0) flag(err, kErrJacobi);
-  // per-item counters (pairs checked, rotations) for the flop statistics
-  unsigned long long ps = pairs, rs = rots;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    ps += __shfl_xor_sync(kFull, ps, o);
-    rs += __shfl_xor_sync(kFull, rs, o);
-  }
-  if (lane == 0 && cnt) {
-    cnt[0] = ps;
-    cnt[1] = rs;
-  }
-}
-
-// Float32 one-sided Jacobi used as a preconditioner: rotates the float copy
-// af of the columns until they are orthogonal to float accuracy and
-// accumulates the rotations in vf (lane c holds column c of V, ncol
-// entries), so that M V has nearly orthogonal columns.
-template <int MR>
-__device__ __forceinline__ void jacobi32(float (&af)[MR], float (&vf)[32], int rows, int ncol, int lane) {
-  const int n2 = ncol + (ncol & 1);
-  const int nr = n2 - 1;
-  const float tol = 1.0e-6f;
-  if (ncol < 2) return;
-  for (int sweep = 0; sweep < 12; ++sweep) {
-    int any = 0;
-    for (int r = 0; r < nr; ++r) {
-      const int p = jacobi_partner(lane, r, n2);
-      const bool lo = lane < p;
-      float al = 0.f, be = 0.f, ga = 0.f;
-#pragma unroll
-      for (int i = 0; i < MR; ++i)
-        if (i < rows) {
-          const float o = __shfl_sync(kFull, af[i], p);
-          const float xx = lo ? af[i] : o;
-          const float yy = lo ? o : af[i];
-          al = fmaf(xx, xx, al);
-          be = fmaf(yy, yy, be);
-          ga = fmaf(xx, yy, ga);
-        }
-      const bool active = lane < n2 && p != lane;
-      const bool rot = active && al > 0.f && be > 0.f && fabsf(ga) > tol * sqrtf(al) * sqrtf(be);
-      float c = 1.f, s = 0.f;
-      if (rot) {
-        const float zeta = (be - al) / (2.f * ga);
-        const float t = copysignf(1.f, zeta) / (fabsf(zeta) + hypotf(1.f, zeta));
-        c = rsqrtf(fmaf(t, t, 1.f));
-        s = c * t;
-      }
-      if (__any_sync(kFull, rot)) {
-#pragma unroll
-        for (int i = 0; i < MR; ++i)
-          if (i < rows) {
-            const float o = __shfl_sync(kFull, af[i], p);
-            if (rot) af[i] = lo ? fmaf(c, af[i], -s * o) : fmaf(s, o, c * af[i]);
-          }
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-          if (j < ncol) {
-            const float o = __shfl_sync(kFull, vf[j], p);
-            if (rot) vf[j] = lo ? fmaf(c, vf[j], -s * o) : fmaf(s, o, c * vf[j]);
-          }
-      }
-      any |= rot ? 1 : 0;
-    }
-    if (!__any_sync(kFull, any)) break;
-  }
-}
-
-// Two Newton-Schulz steps V <- V (3I - V^* V) / 2 in float64 on the columns
-// v (lane c holds column c, ncol entries) with V staged in Vs (ld 33):
-// turns the float32-accurate rotation product into an orthogonal matrix to
-// float64 accuracy.
-__device__ __forceinline__ void orthonormalize(double (&v)[32], double* Vs, int ncol, int ldg, int lane) {
-  for (int step = 0; step < 2; ++step) {
-    if (lane < ncol)
-#pragma unroll
-      for (int j = 0; j < 32; ++j)
-        if (j < ncol) Vs[j + lane * ldg] = v[j];
-    __syncwarp();
-    double g[32];
-#pragma unroll
-    for (int i = 0; i < 32; ++i) {
-      double x = 0.0;
-      if (i < ncol && lane < ncol)
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-          if (j < ncol) x = fma(Vs[j + i * ldg], v[j], x);
-      g[i] = x;
-    }
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      double x = 0.0;
-      if (j < ncol && lane < ncol)
-#pragma unroll
-        for (int i = 0; i < 32; ++i)
-          if (i < ncol) x = fma(Vs[j + i * ldg], g[i], x);
-      v[j] = fma(1.5, v[j], -0.5 * x);
-    }
-    __syncwarp();
-  }
-}
-
 // --------------------------------------------------------------- prepass
 // Weights of the unchanged matrix (Section 4, the recursive construction of
 // the weight matrices), for both sides:
@@ -658,6 +490,252 @@ __global__ void k_weights(MatView M, const Item* __restrict__ items, const Entry
   (void)err;
 }
 
+// ------------------------------------------------------------- step 4
+// Truncation bottom-up: SVD of M = V^_t B~_t^* (leaf: V^_t = V~_t),
+// rank by the block-relative rule sum_{i>r} sigma_i^2 <= (eps/2)^2, Q^_t
+// from the leading left singular vectors, R_t = Q^_t^* V^_t; the rows of
+// Q^_t become the sons' new transfer matrices (Eq. (Qt_nested)), and the
+// subtree root commits E_t0 <- R_t0 [E_t0; 0] (Eqs. (Qt_condensed),
+// (hatQt_condensed)).
+//
+// One block of four warps per task.  A warp issues its float64
+// instructions to one sub-partition of the SM, at a quarter of the SM's
+// float64 rate, so a task spread over four warps finishes up to four times
+// sooner; the factorisation runs updates one by one, with far fewer tasks
+// per launch than the GPU has sub-partitions.  Lane c owns column c.  Warp
+// w owns the rows i of the tall matrices with (i / 2) mod 4 = w (two of
+// every eight, see trow) and every fourth row (or output row) of the K x K
+// ones.  A sum over rows is formed per warp and the four partial sums are
+// added in warp order by every thread, so that all warps take the same
+// rotations, certificate and rank.
+constexpr int kTW = 4;   // warps per truncation task
+
+// row of the tall matrices held in slot h of warp w
+__device__ __forceinline__ int trow(int h, int w) { return 8 * (h >> 1) + 2 * w + (h & 1); }
+
+// Per-lane sums (maxima) over the four warps, combined in warp order; two
+// alternating buffers of 3 x 128 doubles, so one barrier per call suffices
+// (a buffer is written again only after every thread passed the barrier of
+// the call in between).  Every thread of the block must make the same
+// calls.
+struct CtaSum {
+  double* buf;
+  int ph;
+  __device__ __forceinline__ double* next() {
+    double* b = buf + ph * 384;
+    ph ^= 1;
+    return b;
+  }
+  __device__ __forceinline__ static double add4(const double* b, int lane) {
+    return (b[lane] + b[32 + lane]) + (b[64 + lane] + b[96 + lane]);
+  }
+  __device__ __forceinline__ static float add4f(const double* b, int lane) {
+    return ((float)b[lane] + (float)b[32 + lane]) + ((float)b[64 + lane] + (float)b[96 + lane]);
+  }
+  __device__ __forceinline__ void sum3(double& x, double& y, double& z, int w, int lane) {
+    double* b = next();
+    b[w * 32 + lane] = x;
+    b[128 + w * 32 + lane] = y;
+    b[256 + w * 32 + lane] = z;
+    __syncthreads();
+    x = add4(b, lane);
+    y = add4(b + 128, lane);
+    z = add4(b + 256, lane);
+  }
+  __device__ __forceinline__ void sum3f(float& x, float& y, float& z, int w, int lane) {
+    double* b = next();
+    b[w * 32 + lane] = x;
+    b[128 + w * 32 + lane] = y;
+    b[256 + w * 32 + lane] = z;
+    __syncthreads();
+    x = add4f(b, lane);
+    y = add4f(b + 128, lane);
+    z = add4f(b + 256, lane);
+  }
+  __device__ __forceinline__ double sum1(double x, int w, int lane) {
+    double* b = next();
+    b[w * 32 + lane] = x;
+    __syncthreads();
+    return add4(b, lane);
+  }
+  __device__ __forceinline__ double max1(double x, int w, int lane) {
+    double* b = next();
+    b[w * 32 + lane] = x;
+    __syncthreads();
+    return fmax(fmax(b[lane], b[32 + lane]), fmax(b[64 + lane], b[96 + lane]));
+  }
+};
+
+// One-sided (Hestenes) Jacobi on the K columns (a[]: this warp's rows,
+// zero beyond `rows`): on return the columns are U Sigma, mutually
+// orthogonal.  Round-robin pairs; the two lanes of a pair split the warp's
+// rows (the lower lane the even slots, the upper the odd ones) and add
+// their partial sums; the warps' sums are added in warp order, so all
+// threads take the same rotation.
+template <int RW>
+__device__ __forceinline__ void jacobi_cta(double (&a)[RW], int rows, int ncol, CtaSum& cs, int w, int lane,
+                                           unsigned long long* cnt, int* err) {
+  const int n2 = ncol + (ncol & 1);
+  const int nr = n2 - 1;
+  const double tol2 = (16.0 * DBL_EPSILON) * (16.0 * DBL_EPSILON);
+  unsigned long long pairs = 0, rots = 0;
+  bool converged = (ncol < 2);
+  for (int sweep = 0; sweep < kMaxSweeps && !converged; ++sweep) {
+    int any = 0;
+    for (int r = 0; r < nr; ++r) {
+      const int p = jacobi_partner(lane, r, n2);
+      const bool lo = lane < p;
+      double al = 0.0, be = 0.0, ga = 0.0;
+#pragma unroll
+      for (int h = 0; h < RW / 2; ++h)
+        if (8 * h + 2 * w < rows) {
+          const double r0 = a[2 * h], r1 = a[2 * h + 1];
+          const double got = __shfl_sync(kFull, lo ? r1 : r0, p);
+          const double xx = lo ? r0 : got;
+          const double yy = lo ? got : r1;
+          al = fma(xx, xx, al);
+          be = fma(yy, yy, be);
+          ga = fma(xx, yy, ga);
+        }
+      al += __shfl_sync(kFull, al, p);
+      be += __shfl_sync(kFull, be, p);
+      ga += __shfl_sync(kFull, ga, p);
+      cs.sum3(al, be, ga, w, lane);
+      const bool active = lane < n2 && p != lane;
+      // rotate when |gamma| > tol sqrt(alpha beta); the columns are scaled
+      // to max |entry| < 1, so the squares neither overflow nor matter when
+      // they underflow
+      const bool rot = active && ga * ga > tol2 * (al * be);
+      double c = 1.0, s = 0.0;
+      if (rot) {
+        // t = tan(theta) of the rotation that makes the pair orthogonal:
+        // t = gamma / (d + sign(d) sqrt(d^2 + gamma^2)), d = (beta - alpha) / 2
+        const double d = 0.5 * (be - al);
+        const double t = ga / (d + copysign(sqrt(fma(d, d, ga * ga)), d));
+        c = rsqrt(fma(t, t, 1.0));
+        s = c * t;
+      }
+      if (__any_sync(kFull, rot)) {
+#pragma unroll
+        for (int h = 0; h < RW; ++h)
+          if (trow(h, w) < rows) {
+            const double o = __shfl_sync(kFull, a[h], p);
+            if (rot) a[h] = lo ? fma(c, a[h], -s * o) : fma(s, o, c * a[h]);
+          }
+      }
+      if (active && lo) {
+        pairs += 1;
+        rots += rot ? 1 : 0;
+      }
+      any |= rot ? 1 : 0;
+    }
+    converged = !__any_sync(kFull, any);
+  }
+  if (!converged && threadIdx.x == 0) flag(err, kErrJacobi);
+  // per-item counters (pairs checked, rotations) for the flop statistics
+  if (w == 0) {
+    unsigned long long ps = pairs, rs = rots;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      ps += __shfl_xor_sync(kFull, ps, o);
+      rs += __shfl_xor_sync(kFull, rs, o);
+    }
+    if (lane == 0 && cnt) {
+      cnt[0] = ps;
+      cnt[1] = rs;
+    }
+  }
+}
+
+// Float32 one-sided Jacobi used as a preconditioner: rotates the float copy
+// af of the columns until they are orthogonal to float accuracy and
+// accumulates the rotations in V (vf[jj] = V[4 jj + w][lane]), so that
+// M V has nearly orthogonal columns.
+template <int RW>
+__device__ __forceinline__ void jacobi32_cta(float (&af)[RW], float (&vf)[8], int rows, int ncol, CtaSum& cs, int w,
+                                             int lane) {
+  const int n2 = ncol + (ncol & 1);
+  const int nr = n2 - 1;
+  const float tol = 1.0e-6f;
+  if (ncol < 2) return;
+  for (int sweep = 0; sweep < 12; ++sweep) {
+    int any = 0;
+    for (int r = 0; r < nr; ++r) {
+      const int p = jacobi_partner(lane, r, n2);
+      const bool lo = lane < p;
+      float al = 0.f, be = 0.f, ga = 0.f;
+#pragma unroll
+      for (int h = 0; h < RW; ++h)
+        if (trow(h, w) < rows) {
+          const float o = __shfl_sync(kFull, af[h], p);
+          const float xx = lo ? af[h] : o;
+          const float yy = lo ? o : af[h];
+          al = fmaf(xx, xx, al);
+          be = fmaf(yy, yy, be);
+          ga = fmaf(xx, yy, ga);
+        }
+      cs.sum3f(al, be, ga, w, lane);
+      const bool active = lane < n2 && p != lane;
+      const bool rot = active && al > 0.f && be > 0.f && fabsf(ga) > tol * sqrtf(al) * sqrtf(be);
+      float c = 1.f, s = 0.f;
+      if (rot) {
+        const float zeta = (be - al) / (2.f * ga);
+        const float t = copysignf(1.f, zeta) / (fabsf(zeta) + hypotf(1.f, zeta));
+        c = rsqrtf(fmaf(t, t, 1.f));
+        s = c * t;
+      }
+      if (__any_sync(kFull, rot)) {
+#pragma unroll
+        for (int h = 0; h < RW; ++h)
+          if (trow(h, w) < rows) {
+            const float o = __shfl_sync(kFull, af[h], p);
+            if (rot) af[h] = lo ? fmaf(c, af[h], -s * o) : fmaf(s, o, c * af[h]);
+          }
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj)
+          if (4 * jj + w < ncol) {
+            const float o = __shfl_sync(kFull, vf[jj], p);
+            if (rot) vf[jj] = lo ? fmaf(c, vf[jj], -s * o) : fmaf(s, o, c * vf[jj]);
+          }
+      }
+      any |= rot ? 1 : 0;
+    }
+    if (!__any_sync(kFull, any)) break;
+  }
+}
+
+// Two Newton-Schulz steps V <- V (3I - V^* V) / 2 in float64 on V (ncol x
+// ncol in Vs, ld ldg), with G = V^* V in Gs: turns the float32-accurate
+// rotation product into an orthogonal matrix to float64 accuracy.  Warp w
+// forms the rows i = w, w + 4, ... of G and of the new V.
+__device__ __forceinline__ void orthonormalize_cta(double* Vs, double* Gs, int ncol, int ldg, int w, int lane) {
+  for (int step = 0; step < 2; ++step) {
+    if (lane < ncol)
+      for (int i = w; i < ncol; i += kTW) {
+        double x = 0.0;
+        for (int j = 0; j < ncol; ++j) x = fma(Vs[j + i * ldg], Vs[j + lane * ldg], x);
+        Gs[i + lane * ldg] = x;
+      }
+    __syncthreads();
+    double nv[8];
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) {
+      const int j = 4 * jj + w;
+      double x = 0.0;
+      if (j < ncol && lane < ncol)
+        for (int i = 0; i < ncol; ++i) x = fma(Vs[j + i * ldg], Gs[i + lane * ldg], x);
+      nv[jj] = (j < ncol && lane < ncol) ? fma(1.5, Vs[j + lane * ldg], -0.5 * x) : 0.0;
+    }
+    __syncthreads();   // every read of V is done
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) {
+      const int j = 4 * jj + w;
+      if (j < ncol && lane < ncol) Vs[j + lane * ldg] = nv[jj];
+    }
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------- certified full-rank path
 // When every singular value of the weighted matrix M exceeds the
 // truncation threshold, the rank rule keeps all of range(M) and any
@@ -665,112 +743,121 @@ __global__ void k_weights(MatView M, const Item* __restrict__ items, const Entry
 // singular vectors (Eq. (Qt_condensed)).  The certificate is the Cholesky
 // factorisation of M^* M - (tau + delta) I succeeding, tau = (eps/2)^2 and
 // delta a bound on the rounding of the Gram matrix and of the
-// factorisation; the basis then comes from two Cholesky-QR passes.  All of
-// it is float64 matrix-matrix work with every lane busy.
+// factorisation; the basis then comes from Cholesky-QR passes.  The
+// helpers below run on the four warps of a truncation task; X is the tall
+// matrix in shared memory (ld ldx), xr[] this warp's rows of column lane.
 
-// Gram G = X^* X of the K columns of X (smem, ld ldx); lane c holds column
-// c of X in xc[].  G goes to Gs (ld ldg).
-template <int MR>
-__device__ __forceinline__ void gram(const double* X, int ldx, const double (&xc)[MR], int rows, int K, double* Gs,
-                                     int ldg, int lane) {
+// G = X^* X (K x K, ld ldg): warp w forms the rows j = w, w + 4, ... of G,
+// each entry one sum over the rows in order.
+__device__ __forceinline__ void gram_cta(const double* X, int ldx, int rows, int K, double* Gs, int ldg, int w,
+                                         int lane) {
   if (lane < K)
-    for (int j = 0; j < K; ++j) {
+    for (int j = w; j < K; j += kTW) {
       double g = 0.0;
-#pragma unroll
-      for (int i = 0; i < MR; ++i)
-        if (i < rows) g = fma(X[i + j * ldx], xc[i], g);
+      for (int i = 0; i < rows; ++i) g = fma(X[i + j * ldx], X[i + lane * ldx], g);
       Gs[j + lane * ldg] = g;
     }
-  __syncwarp();
+  __syncthreads();
 }
 
-// In-place Cholesky G - shift I = L L^* of the lower triangle of Gs (ld
-// ldg); lane i owns row i.  Returns false (on every lane alike) when a pivot
-// is not positive.
-__device__ __forceinline__ bool chol(double* Gs, int K, double shift, int ldg, int lane) {
-  if (lane < K) Gs[lane + lane * ldg] -= shift;
-  __syncwarp();
+// In-place Cholesky factorisation G - shift I = L L^* of the lower
+// triangle of Gs (ld ldg): lane i owns row i, the trailing update of column
+// k goes to warp k mod 4.  Returns false (on every thread alike) when a
+// pivot is not positive.
+__device__ __forceinline__ bool chol_cta(double* Gs, int K, double shift, int ldg, int w, int lane) {
+  if (w == 0 && lane < K) Gs[lane + lane * ldg] -= shift;
+  __syncthreads();
   for (int j = 0; j < K; ++j) {
     const double d = Gs[j + j * ldg];
     if (!(d > 0.0)) return false;
     const double ljj = sqrt(d);
     const double inv = 1.0 / ljj;
-    __syncwarp();
-    if (lane == j) Gs[j + j * ldg] = ljj;
-    if (lane > j && lane < K) Gs[lane + j * ldg] *= inv;
-    __syncwarp();
+    __syncthreads();   // every thread has read the pivot
+    if (w == 0) {
+      if (lane == j) Gs[j + j * ldg] = ljj;
+      if (lane > j && lane < K) Gs[lane + j * ldg] *= inv;
+    }
+    __syncthreads();
     if (lane > j && lane < K) {
       const double lij = Gs[lane + j * ldg];
-      for (int k = j + 1; k <= lane; ++k) Gs[lane + k * ldg] = fma(-lij, Gs[k + j * ldg], Gs[lane + k * ldg]);
+      for (int k = j + 1 + ((w - j - 1) & 3); k <= lane; k += kTW)
+        Gs[lane + k * ldg] = fma(-lij, Gs[k + j * ldg], Gs[lane + k * ldg]);
     }
-    __syncwarp();
+    __syncthreads();
   }
   return true;
 }
 
-// Xs = L^{-1} (lower triangular, ld 33) for the Cholesky factor in Ls;
-// lane c computes column c.  dinv (K entries of shared memory) receives
-// the reciprocal diagonal.
-__device__ __forceinline__ void trinv(const double* Ls, double* Xs, double* dinv, int K, int ldg, int lane) {
-  if (lane < K) dinv[lane] = 1.0 / Ls[lane + lane * ldg];
-  __syncwarp();
-  if (lane < K) {
-    const int c = lane;
-    Xs[c + c * ldg] = dinv[c];
-    for (int i = c + 1; i < K; ++i) {
-      double t = 0.0;
-      for (int p = c; p < i; ++p) t = fma(Ls[i + p * ldg], Xs[p + c * ldg], t);
-      Xs[i + c * ldg] = -t * dinv[i];
-    }
+// Xs = L^{-1} (lower triangular, ld ldg) for the Cholesky factor in Ls, one
+// row after the other: X[i][c] = -(sum_{c<=p<i} L[i][p] X[p][c]) / L[i][i],
+// lane c, the sum split over the warps by p mod 4.  dinv receives the
+// reciprocal diagonal.
+__device__ __forceinline__ void trinv_cta(const double* Ls, double* Xs, double* dinv, int K, int ldg, CtaSum& cs,
+                                          int w, int lane) {
+  if (w == 0 && lane < K) {
+    const double di = 1.0 / Ls[lane + lane * ldg];
+    dinv[lane] = di;
+    Xs[lane + lane * ldg] = di;
   }
-  __syncwarp();
+  __syncthreads();
+  for (int i = 1; i < K; ++i) {
+    double t = 0.0;
+    if (lane < i)
+      for (int p = lane + ((w - lane) & 3); p < i; p += kTW) t = fma(Ls[i + p * ldg], Xs[p + lane * ldg], t);
+    t = cs.sum1(t, w, lane);
+    if (w == 0 && lane < i) Xs[i + lane * ldg] = -t * dinv[i];
+    __syncthreads();
+  }
 }
 
-// One Cholesky-QR pass on the K columns of X (smem, ld ldx; lane c holds
-// column c in xc[]): G = X^* X = L L^*, X <- X L^{-*}.  Uses Gs, Xs, dinv;
-// returns false if the factorisation breaks down.  xc[] receives the new
-// column.
-// X <- X L^{-*} for the Cholesky factor L in Gs (lower, ld 33).
-template <int MR>
-__device__ __forceinline__ void apply_inverse_factor(double* X, int ldx, double (&xc)[MR], int rows, int K,
-                                                     const double* Gs, double* Xs, double* dinv, int ldg,
-                                                     int lane) {
-  trinv(Gs, Xs, dinv, K, ldg, lane);
+// X <- X L^{-*} for the Cholesky factor L in Gs; xr[] receives the new
+// rows of this warp.
+template <int RW>
+__device__ __forceinline__ void apply_inverse_cta(double* X, int ldx, double (&xr)[RW], int rows, int K,
+                                                  const double* Gs, double* Xs, double* dinv, int ldg, CtaSum& cs,
+                                                  int w, int lane) {
+  trinv_cta(Gs, Xs, dinv, K, ldg, cs, w, lane);
 #pragma unroll
-  for (int i = 0; i < MR; ++i) xc[i] = 0.0;
+  for (int h = 0; h < RW; ++h) xr[h] = 0.0;
   if (lane < K)
     for (int j = 0; j <= lane; ++j) {
       const double x = Xs[lane + j * ldg];
 #pragma unroll
-      for (int i = 0; i < MR; ++i)
-        if (i < rows) xc[i] = fma(X[i + j * ldx], x, xc[i]);
+      for (int h = 0; h < RW; ++h) {
+        const int i = trow(h, w);
+        if (i < rows) xr[h] = fma(X[i + j * ldx], x, xr[h]);
+      }
     }
-  __syncwarp();
+  __syncwarp();   // the warp's rows are read before they are written
   if (lane < K)
 #pragma unroll
-    for (int i = 0; i < MR; ++i)
-      if (i < rows) X[i + lane * ldx] = xc[i];
-  __syncwarp();
+    for (int h = 0; h < RW; ++h) {
+      const int i = trow(h, w);
+      if (i < rows) X[i + lane * ldx] = xr[h];
+    }
+  __syncthreads();
 }
 
-template <int MR>
-__device__ __forceinline__ bool cholqr_pass(double* X, int ldx, double (&xc)[MR], int rows, int K, double* Gs,
-                                            double* Xs, double* dinv, int ldg, int lane) {
-  gram<MR>(X, ldx, xc, rows, K, Gs, ldg, lane);
-  if (!chol(Gs, K, 0.0, ldg, lane)) return false;
-  apply_inverse_factor<MR>(X, ldx, xc, rows, K, Gs, Xs, dinv, ldg, lane);
+// One Cholesky-QR pass: G = X^* X = L L^*, X <- X L^{-*}.  False if the
+// factorisation breaks down.
+template <int RW>
+__device__ __forceinline__ bool cholqr_cta(double* X, int ldx, double (&xr)[RW], int rows, int K, double* Gs,
+                                           double* Xs, double* dinv, int ldg, CtaSum& cs, int w, int lane) {
+  gram_cta(X, ldx, rows, K, Gs, ldg, w, lane);
+  if (!chol_cta(Gs, K, 0.0, ldg, w, lane)) return false;
+  apply_inverse_cta<RW>(X, ldx, xr, rows, K, Gs, Xs, dinv, ldg, cs, w, lane);
   return true;
 }
 
-// Second orthogonalisation of X (smem, ld ldx; lane c holds column c in
-// xc[]) when it is already orthonormal to within 1e-7: with G = X^* X,
-// X <- X (3I - G) / 2 leaves an orthogonality error of order |G - I|^2.
-// Returns false, leaving X unchanged, when |G - I| is larger.
-template <int MR>
-__device__ __forceinline__ bool polish(double* X, int ldx, double (&xc)[MR], int rows, int K, double* Gs, int ldg,
-                                       int lane) {
-  gram<MR>(X, ldx, xc, rows, K, Gs, ldg, lane);
-  double dev = 0.0;
+// Second orthogonalisation of X when it is already orthonormal to within
+// 1e-7: with G = X^* X, X <- X (3I - G) / 2 leaves an orthogonality error of
+// order |G - I|^2.  Returns false, leaving X unchanged, when |G - I| is
+// larger.
+template <int RW>
+__device__ __forceinline__ bool polish_cta(double* X, int ldx, double (&xr)[RW], int rows, int K, double* Gs,
+                                           int ldg, int w, int lane) {
+  gram_cta(X, ldx, rows, K, Gs, ldg, w, lane);
+  double dev = 0.0;   // every warp reads all of G: the same maximum everywhere
   if (lane < K)
     for (int j = 0; j < K; ++j) dev = fmax(dev, fabs(Gs[j + lane * ldg] - (j == lane ? 1.0 : 0.0)));
 #pragma unroll
@@ -779,42 +866,54 @@ __device__ __forceinline__ bool polish(double* X, int ldx, double (&xc)[MR], int
   // column c: 1.5 x_c - 0.5 sum_j x_j G[j][c]
   if (lane < K) {
 #pragma unroll
-    for (int i = 0; i < MR; ++i) xc[i] *= 1.5;
+    for (int h = 0; h < RW; ++h) xr[h] *= 1.5;
     for (int j = 0; j < K; ++j) {
       const double g = -0.5 * Gs[j + lane * ldg];
 #pragma unroll
-      for (int i = 0; i < MR; ++i)
-        if (i < rows) xc[i] = fma(X[i + j * ldx], g, xc[i]);
+      for (int h = 0; h < RW; ++h) {
+        const int i = trow(h, w);
+        if (i < rows) xr[h] = fma(X[i + j * ldx], g, xr[h]);
+      }
     }
   }
   __syncwarp();
   if (lane < K)
 #pragma unroll
-    for (int i = 0; i < MR; ++i)
-      if (i < rows) X[i + lane * ldx] = xc[i];
-  __syncwarp();
+    for (int h = 0; h < RW; ++h) {
+      const int i = trow(h, w);
+      if (i < rows) X[i + lane * ldx] = xr[h];
+    }
+  __syncthreads();
   return true;
 }
 
-// ------------------------------------------------------------- step 4
-// Truncation bottom-up: SVD of V^_t B~_t^* (leaf: V^_t = V~_t) by one-sided
-// Jacobi, rank by the block-relative rule sum_{i>r} sigma_i^2 <= (eps/2)^2,
-// Q^_t from the leading left singular vectors, R_t = Q^_t^* V^_t; the rows
-// of Q^_t become the sons' new transfer matrices (Eq. (Qt_nested)), and the
-// subtree root commits E_t0 <- R_t0 [E_t0; 0].
+// Shared memory of one truncation task (doubles): V^ and Q (ld MR + 1,
+// kl columns each), two K x K tiles (ld ldg), 32 reciprocal pivots and the
+// warp-sum buffers.
+__host__ __device__ constexpr int trunc_ldg(int kl) { return (kl + 1) | 1; }
+__host__ __device__ constexpr size_t trunc_smem_doubles(int mr, int kl) {
+  return 2 * (size_t)(mr + 1) * kl + 2 * (size_t)kl * trunc_ldg(kl) + 32 + 768;
+}
+
 template <int MR>
-__global__ void k_truncate(MatView M, const Item* __restrict__ items, const int32_t* __restrict__ list,
-                           int n, int u, int kl, double eps, const double* __restrict__ A,
-                           const double* __restrict__ B, ItemBuffers IB, int* err) {
+__global__ void __launch_bounds__(32 * kTW) k_truncate(MatView M, const Item* __restrict__ items,
+                                                       const int32_t* __restrict__ list, int n, int u, int kl,
+                                                       double eps, const double* __restrict__ A,
+                                                       const double* __restrict__ B, ItemBuffers IB, int* err) {
+  constexpr int RW = MR / kTW;   // rows per warp
+  constexpr int LQ = MR + 1;     // leading dimension of V^ and Q in shared memory
   extern __shared__ double smem[];
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
-  const int idx = blockIdx.x * (blockDim.x >> 5) + w;
+  const int idx = blockIdx.x;
   if (idx >= n) return;
-  const int ldg = kl + 1;   // leading dimension of the K x K tiles
-  double* Vh = smem + (size_t)w * (2 * MR * kl + 2 * kl * ldg + kl);
-  double* Qs = Vh + MR * kl;
-  double* Vs = Qs + MR * kl;
+  const int ldg = trunc_ldg(kl);
+  double* Vh = smem;
+  double* Qs = Vh + LQ * kl;
+  double* Gs = Qs + LQ * kl;      // K x K Gram / Cholesky factor
+  double* Xs = Gs + kl * ldg;     // K x K inverse factor / rotations V
+  double* dinv = Xs + kl * ldg;   // 32 reciprocal pivots
+  CtaSum cs{dinv + 32, 0};
   const int id = list[idx];
   const Item it = items[id];
   if (!IB.fail[it.update]) return;
@@ -823,7 +922,7 @@ __global__ void k_truncate(MatView M, const Item* __restrict__ items, const int3
   const int K = k + u;
   const int kcap = M.kcap;
   if (K > kl) {
-    if (lane == 0) flag(err, kErrCols);
+    if (threadIdx.x == 0) flag(err, kErrCols);
     return;
   }
   int rows = 0;
@@ -836,16 +935,16 @@ __global__ void k_truncate(MatView M, const Item* __restrict__ items, const int3
     rows = r1 + r2;
   }
   if (rows > MR) {
-    if (lane == 0) flag(err, kErrRows);
+    if (threadIdx.x == 0) flag(err, kErrRows);
     return;
   }
-  // V^_t into shared memory (ld MR), one column per lane
+  // V^_t into shared memory, one column per lane
   if (it.flags & kItemLeaf) {
     const double* V = pick(M.leaf, side) + pick(M.leaf_off, side)[it.cluster];
     const double* F = (side == 0 ? A : B) + it.foff;
     if (lane < K)
-      for (int i = 0; i < rows; ++i)
-        Vh[i + lane * MR] = lane < k ? V[i + lane * rows] : F[(it.rowoff + i) + (size_t)(lane - k) * it.ld];
+      for (int i = w; i < rows; i += kTW)
+        Vh[i + lane * LQ] = lane < k ? V[i + lane * rows] : F[(it.rowoff + i) + (size_t)(lane - k) * it.ld];
   } else {
     const int sons[2] = {it.son0, it.son1};
     int row0 = 0;
@@ -856,82 +955,86 @@ __global__ void k_truncate(MatView M, const Item* __restrict__ items, const int3
       const double* Rt = IB.Rt + (size_t)sons[si] * kSlot;
       const double* E = pick(M.transfer, side) + (size_t)sn.cluster * kcap * kcap;   // ks x k
       if (lane < K)
-        for (int p = 0; p < rs; ++p) {
+        for (int p = w; p < rs; p += kTW) {
           double v = 0.0;
           if (lane < k) {
             for (int q = 0; q < ks; ++q) v = fma(Rt[p + q * 32], E[q + lane * kcap], v);
           } else {
             v = Rt[p + (ks + lane - k) * 32];
           }
-          Vh[row0 + p + lane * MR] = v;
+          Vh[row0 + p + lane * LQ] = v;
         }
       row0 += rs;
     }
   }
-  __syncwarp();
+  __syncthreads();
   // M = V^ B~^*, column `lane` = V^ * row `lane` of B~, scaled by a power
   // of two (exact) so that max |M| lies in [1/2, 1): the squared sums of
   // the Jacobi test cannot overflow and the float copy keeps its range;
   // singular values are unscaled exactly below.
   const double* Bw = IB.Bw + (size_t)id * kSlot;
-  double a[MR];
+  double a[RW];
   int ex = 0;
   auto form_m = [&]() {
 #pragma unroll
-    for (int i = 0; i < MR; ++i) a[i] = 0.0;
+    for (int h = 0; h < RW; ++h) a[h] = 0.0;
     if (lane < K)
       for (int q = lane; q < K; ++q) {   // B~ is upper triangular: B~[lane, q] = 0 for q < lane
         const double b = Bw[lane + q * 32];
 #pragma unroll
-        for (int i = 0; i < MR; ++i)
-          if (i < rows) a[i] = fma(Vh[i + q * MR], b, a[i]);
+        for (int h = 0; h < RW; ++h) {
+          const int i = trow(h, w);
+          if (i < rows) a[h] = fma(Vh[i + q * LQ], b, a[h]);
+        }
       }
     double mx = 0.0;
 #pragma unroll
-    for (int i = 0; i < MR; ++i)
-      if (i < rows) mx = fmax(mx, fabs(a[i]));
+    for (int h = 0; h < RW; ++h) mx = fmax(mx, fabs(a[h]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(kFull, mx, o));
+    mx = cs.max1(mx, w, lane);
     ex = 0;
     if (mx > 0.0) frexp(mx, &ex);
 #pragma unroll
-    for (int i = 0; i < MR; ++i) a[i] = ldexp(a[i], -ex);
+    for (int h = 0; h < RW; ++h) a[h] = ldexp(a[h], -ex);
+  };
+  auto store_rows = [&]() {
+    if (lane < K)
+#pragma unroll
+      for (int h = 0; h < RW; ++h) {
+        const int i = trow(h, w);
+        if (i < rows) Qs[i + lane * LQ] = a[h];
+      }
+    __syncthreads();
   };
   form_m();
-  double* Gs = Vs;                 // K x K Gram / Cholesky factor (ld ldg)
-  double* Xs = Vs + kl * ldg;      // K x K inverse factor (ld ldg)
-  double* dinv = Xs + kl * ldg;    // K reciprocal pivots
   const double thr = 0.25 * eps * eps;
   unsigned long long* cnt = IB.jac + 4 * (size_t)id;
   // certified full-rank path: M^* M - (tau + delta) I positive definite
   bool certified = false;
-  if (rows >= K && K >= 1 && lane < 32) {
-    if (lane < K)
-#pragma unroll
-      for (int i = 0; i < MR; ++i)
-        if (i < rows) Qs[i + lane * MR] = a[i];
-    __syncwarp();
-    gram<MR>(Qs, MR, a, rows, K, Gs, ldg, lane);
+  if (rows >= K && K >= 1) {
+    store_rows();
+    gram_cta(Qs, LQ, rows, K, Gs, ldg, w, lane);
     double trace = 0.0;
     for (int j = 0; j < K; ++j) trace += Gs[j + j * ldg];
     const double tau = ldexp(thr, -2 * ex);
     const double delta = 4.0 * (double)(rows + K * K) * DBL_EPSILON * trace;
-    if (chol(Gs, K, tau + delta, ldg, lane)) {
+    if (chol_cta(Gs, K, tau + delta, ldg, w, lane)) {
       // The certificate's factor L (L L^* = M^* M - (tau + delta) I) is the
       // first Cholesky-QR pass: M L^{-*} deviates from orthonormality only
       // by (tau + delta) |(L L^*)^{-1}|; a polish (or a second full pass)
       // removes the rest.
-      apply_inverse_factor<MR>(Qs, MR, a, rows, K, Gs, Xs, dinv, ldg, lane);
-      certified = polish<MR>(Qs, MR, a, rows, K, Gs, ldg, lane) ||
-                  (cholqr_pass<MR>(Qs, MR, a, rows, K, Gs, Xs, dinv, ldg, lane) &&
-                   polish<MR>(Qs, MR, a, rows, K, Gs, ldg, lane));
+      apply_inverse_cta<RW>(Qs, LQ, a, rows, K, Gs, Xs, dinv, ldg, cs, w, lane);
+      certified = polish_cta<RW>(Qs, LQ, a, rows, K, Gs, ldg, w, lane) ||
+                  (cholqr_cta<RW>(Qs, LQ, a, rows, K, Gs, Xs, dinv, ldg, cs, w, lane) &&
+                   polish_cta<RW>(Qs, LQ, a, rows, K, Gs, ldg, w, lane));
       if (!certified) form_m();   // a factorisation broke down after the certificate
     }
   }
   int r = 0;
   if (certified) {
     r = K;   // Qs holds an orthonormal basis of range(M)
-    if (lane == 0 && cnt) {
+    if (threadIdx.x == 0 && cnt) {
       cnt[0] = 0;
       cnt[1] = 0;
       cnt[2] = 1;
@@ -942,46 +1045,43 @@ __global__ void k_truncate(MatView M, const Item* __restrict__ items, const int3
     // M <- M V, which leaves the left singular vectors and singular values
     // of M unchanged and hands the float64 Jacobi nearly orthogonal columns.
     if (K >= 2 && rows > 0) {
+      store_rows();
+      float af[RW];
+      float vf[8];
+#pragma unroll
+      for (int h = 0; h < RW; ++h) af[h] = (float)a[h];
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) vf[jj] = (4 * jj + w == lane) ? 1.f : 0.f;
+      jacobi32_cta<RW>(af, vf, rows, K, cs, w, lane);
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) {
+        const int j = 4 * jj + w;
+        if (j < K && lane < K) Xs[j + lane * ldg] = (double)vf[jj];
+      }
+      __syncthreads();
+      orthonormalize_cta(Xs, Gs, K, ldg, w, lane);
+#pragma unroll
+      for (int h = 0; h < RW; ++h) a[h] = 0.0;
       if (lane < K)
+        for (int j = 0; j < K; ++j) {
+          const double vj = Xs[j + lane * ldg];
 #pragma unroll
-        for (int i = 0; i < MR; ++i)
-          if (i < rows) Qs[i + lane * MR] = a[i];
-      float af[MR];
-      float vf[32];
-#pragma unroll
-      for (int i = 0; i < MR; ++i) af[i] = (float)a[i];
-#pragma unroll
-      for (int j = 0; j < 32; ++j) vf[j] = (j == lane) ? 1.f : 0.f;
-      jacobi32<MR>(af, vf, rows, K, lane);
-      double v[32];
-#pragma unroll
-      for (int j = 0; j < 32; ++j) v[j] = (lane < K && j < K) ? (double)vf[j] : 0.0;
-      orthonormalize(v, Vs, K, ldg, lane);
-      __syncwarp();
-#pragma unroll
-      for (int i = 0; i < MR; ++i) a[i] = 0.0;
-      if (lane < K)
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-          if (j < K) {
-            const double vj = v[j];
-#pragma unroll
-            for (int i = 0; i < MR; ++i)
-              if (i < rows) a[i] = fma(Qs[i + j * MR], vj, a[i]);
+          for (int h = 0; h < RW; ++h) {
+            const int i = trow(h, w);
+            if (i < rows) a[h] = fma(Qs[i + j * LQ], vj, a[h]);
           }
-      __syncwarp();
+        }
     }
-    jacobi<MR>(a, rows, K, lane, cnt, err);
-    if (lane == 0 && cnt) cnt[2] = 0;
+    jacobi_cta<RW>(a, rows, K, cs, w, lane, w == 0 ? cnt : nullptr, err);
+    if (threadIdx.x == 0 && cnt) cnt[2] = 0;
     // singular values, order, rank
-    double s2 = -1.0;   // squared singular value of this lane's column (unscaled)
-    double s2c = 0.0;   // the same for the scaled column
-    if (lane < K) {
+    double s2c = 0.0;   // squared norm of this lane's scaled column
+    if (lane < K)
 #pragma unroll
-      for (int i = 0; i < MR; ++i)
-        if (i < rows) s2c = fma(a[i], a[i], s2c);
-      s2 = ldexp(s2c, 2 * ex);
-    }
+      for (int h = 0; h < RW; ++h)
+        if (trow(h, w) < rows) s2c = fma(a[h], a[h], s2c);
+    s2c = cs.sum1(s2c, w, lane);
+    const double s2 = lane < K ? ldexp(s2c, 2 * ex) : -1.0;   // unscaled
     int pos = 0;
     for (int d = 0; d < 32; ++d) {
       const double o = __shfl_sync(kFull, s2, d);
@@ -995,44 +1095,47 @@ __global__ void k_truncate(MatView M, const Item* __restrict__ items, const int3
     }
     const bool keep = lane < K && rows > 0 && tail > thr;
     r = __popc(__ballot_sync(kFull, keep));
+    __syncwarp();   // the warp's rows of M are read before Q overwrites them
     if (keep) {
       const double inv = 1.0 / sqrt(s2c);
 #pragma unroll
-      for (int i = 0; i < MR; ++i)
-        if (i < rows) Qs[i + pos * MR] = a[i] * inv;
+      for (int h = 0; h < RW; ++h) {
+        const int i = trow(h, w);
+        if (i < rows) Qs[i + pos * LQ] = a[h] * inv;
+      }
     }
+    __syncthreads();
   }
-  __syncwarp();
-  // R_t = Q^* V^ (r x K)
+  // R_t = Q^* V^ (r x K): warp w forms the rows p = w, w + 4, ...
   double* Rt = IB.Rt + (size_t)id * kSlot;
   if (lane < K)
-    for (int p = 0; p < 32; ++p) {
+    for (int p = w; p < 32; p += kTW) {
       double v = 0.0;
       if (p < r)
-        for (int i = 0; i < rows; ++i) v = fma(Qs[i + p * MR], Vh[i + lane * MR], v);
+        for (int i = 0; i < rows; ++i) v = fma(Qs[i + p * LQ], Vh[i + lane * LQ], v);
       Rt[p + lane * 32] = v;
     }
-  if (lane == 0) IB.rank[id] = r;
+  if (threadIdx.x == 0) IB.rank[id] = r;
   // outputs: leaf basis or the sons' transfer matrices
   if (it.flags & kItemLeaf) {
     double* Q = IB.Q + it.qoff;
     if (lane < r)
-      for (int i = 0; i < rows; ++i) Q[i + (size_t)lane * rows] = Qs[i + lane * MR];
+      for (int i = w; i < rows; i += kTW) Q[i + (size_t)lane * rows] = Qs[i + lane * LQ];
   } else {
     double* F1 = IB.F + (size_t)it.son0 * kSlot;
     double* F2 = IB.F + (size_t)it.son1 * kSlot;
     if (lane < r) {
-      for (int p = 0; p < r1; ++p) F1[p + lane * 32] = Qs[p + lane * MR];
-      for (int p = 0; p < r2; ++p) F2[p + lane * 32] = Qs[r1 + p + lane * MR];
+      for (int p = w; p < r1; p += kTW) F1[p + lane * 32] = Qs[p + lane * LQ];
+      for (int p = w; p < r2; p += kTW) F2[p + lane * 32] = Qs[r1 + p + lane * LQ];
     }
   }
   if ((it.flags & kItemRoot) && !(it.flags & kItemTreeRoot)) {
     // E_t0 <- R_t0 [E_t0; 0]  (r x kf)
-    __syncwarp();
+    __syncthreads();   // R_t of every warp is written
     const double* E = pick(M.transfer, side) + (size_t)it.cluster * kcap * kcap;   // k x kf
     double* Fo = IB.F + (size_t)id * kSlot;
     if (lane < it.kf)
-      for (int p = 0; p < r; ++p) {
+      for (int p = w; p < r; p += kTW) {
         double v = 0.0;
         for (int q = 0; q < k; ++q) v = fma(Rt[p + q * 32], E[q + lane * kcap], v);
         Fo[p + lane * 32] = v;
@@ -1300,11 +1403,11 @@ template <int MR>
 static void launch_truncate_mr(const MatView& M, const Item* items, const int32_t* list, int n, int u, int kl,
                                double eps, const double* A, const double* B, const ItemBuffers& IB, int* err,
                                cudaStream_t st) {
-  const int warps = 2;
-  const size_t sm = (size_t)warps * (2 * MR * kl + 2 * kl * (kl + 1) + kl) * sizeof(double);
+  // one block of kTW warps per task
+  const size_t sm = trunc_smem_doubles(MR, kl) * sizeof(double);
   static std::atomic<unsigned long long> attr{0};
-  smem_limit(k_truncate<MR>, (size_t)warps * (2 * MR * 32 + 2 * 32 * 33 + 32) * sizeof(double), attr);
-  k_truncate<MR><<<(n + warps - 1) / warps, 32 * warps, sm, st>>>(M, items, list, n, u, kl, eps, A, B, IB, err);
+  smem_limit(k_truncate<MR>, trunc_smem_doubles(MR, kMaxCols) * sizeof(double), attr);
+  k_truncate<MR><<<n, 32 * kTW, sm, st>>>(M, items, list, n, u, kl, eps, A, B, IB, err);
 }
 
 static void launch_truncate(const MatView& M, const Item* items, const int32_t* list, int n, int u, int kl,
