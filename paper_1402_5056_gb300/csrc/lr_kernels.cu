@@ -12,6 +12,7 @@
 // launch per tree level, as in the whole-matrix product.
 #include <algorithm>
 
+#include "h2_internal.h"
 #include "lr.h"
 
 namespace h2 {
@@ -376,9 +377,13 @@ __device__ __forceinline__ int rr_partner(int i, int r, int n2, int& p, int& q) 
 
 // Core SVD and rank.  C (ka x kb, ld m, scratch), W (kb x kb, ld m,
 // scratch); writes T = U_r Sigma_r = C W_r (ka x r, ld m) into TA, W_r into
-// TB (kb x r, ld m), the rank into *rank.  One block.
+// TB (kb x r, ld m), the rank into *rank.  One block.  With in_smem, C and W
+// live in dynamic shared memory instead (ld ka and kb): the same
+// arithmetic, without a round trip through the caches for every rotation.
 __global__ void __launch_bounds__(1024) k_core_svd(const double* XA, int64_t lda, int ka, const double* XB, int64_t ldb, int kb, int m,
-                           double eps, const int* nonzero, double* C, double* W, double* TA, double* TB, int* rank) {
+                           double eps, const int* nonzero, double* Cg, double* Wg, double* TA, double* TB, int* rank,
+                           int in_smem) {
+  extern __shared__ double csm[];
   __shared__ int order[256];
   __shared__ double nrm2[256];
   __shared__ int any_rot;
@@ -387,21 +392,25 @@ __global__ void __launch_bounds__(1024) k_core_svd(const double* XA, int64_t lda
     if (tid == 0) *rank = 0;
     return;
   }
+  double* C = in_smem ? csm : Cg;
+  double* W = in_smem ? csm + ka * kb : Wg;
+  const int lc = in_smem ? ka : m;   // leading dimensions of C and W
+  const int lw = in_smem ? kb : m;
   // C = R_A R_B^* (upper triangles)
   for (int e = tid; e < ka * kb; e += nt) {
     const int i = e % ka, j = e / ka;
     double v = 0.0;
     for (int q = max(i, j); q < m; ++q) v = fma(XA[i + (int64_t)q * lda], XB[j + (int64_t)q * ldb], v);
-    C[i + j * m] = v;
+    C[i + j * lc] = v;
   }
-  for (int e = tid; e < kb * kb; e += nt) W[e % kb + (e / kb) * m] = (e % kb == e / kb) ? 1.0 : 0.0;
+  for (int e = tid; e < kb * kb; e += nt) W[e % kb + (e / kb) * lw] = (e % kb == e / kb) ? 1.0 : 0.0;
   __syncthreads();
   // columns whose squared norm is below 1e-28 of the largest are at the
   // rounding level of the product: they are not rotated (rotating them
   // need not converge, and they lie far below any truncation threshold)
   for (int j = tid; j < kb; j += nt) {
     double v = 0.0;
-    for (int k = 0; k < ka; ++k) v = fma(C[k + j * m], C[k + j * m], v);
+    for (int k = 0; k < ka; ++k) v = fma(C[k + j * lc], C[k + j * lc], v);
     nrm2[j] = v;
   }
   __syncthreads();
@@ -428,7 +437,7 @@ __global__ void __launch_bounds__(1024) k_core_svd(const double* XA, int64_t lda
         if (q >= kb) continue;
         double al = 0.0, be = 0.0, ga = 0.0;
         for (int k = lane; k < ka; k += 32) {
-          const double x = C[k + p * m], y = C[k + q * m];
+          const double x = C[k + p * lc], y = C[k + q * lc];
           al = fma(x, x, al);
           be = fma(y, y, be);
           ga = fma(x, y, ga);
@@ -443,14 +452,14 @@ __global__ void __launch_bounds__(1024) k_core_svd(const double* XA, int64_t lda
           const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
           const double c = 1.0 / sqrt(fma(t, t, 1.0)), s = c * t;
           for (int k = lane; k < ka; k += 32) {
-            const double x = C[k + p * m], y = C[k + q * m];
-            C[k + p * m] = c * x - s * y;
-            C[k + q * m] = s * x + c * y;
+            const double x = C[k + p * lc], y = C[k + q * lc];
+            C[k + p * lc] = c * x - s * y;
+            C[k + q * lc] = s * x + c * y;
           }
           for (int k = lane; k < kb; k += 32) {
-            const double x = W[k + p * m], y = W[k + q * m];
-            W[k + p * m] = c * x - s * y;
-            W[k + q * m] = s * x + c * y;
+            const double x = W[k + p * lw], y = W[k + q * lw];
+            W[k + p * lw] = c * x - s * y;
+            W[k + q * lw] = s * x + c * y;
           }
           if (lane == 0) any_rot = 1;
         }
@@ -463,7 +472,7 @@ __global__ void __launch_bounds__(1024) k_core_svd(const double* XA, int64_t lda
   // squared column norms = sigma^2, descending order, rank rule
   for (int j = tid; j < kb; j += nt) {
     double v = 0.0;
-    for (int k = 0; k < ka; ++k) v = fma(C[k + j * m], C[k + j * m], v);
+    for (int k = 0; k < ka; ++k) v = fma(C[k + j * lc], C[k + j * lc], v);
     nrm2[j] = v;
   }
   __syncthreads();
@@ -495,8 +504,8 @@ __global__ void __launch_bounds__(1024) k_core_svd(const double* XA, int64_t lda
   }
   __syncthreads();
   const int r = *rank;
-  for (int e = tid; e < ka * r; e += nt) TA[e % ka + (e / ka) * m] = C[e % ka + order[e / ka] * m];
-  for (int e = tid; e < kb * r; e += nt) TB[e % kb + (e / kb) * m] = W[e % kb + order[e / kb] * m];
+  for (int e = tid; e < ka * r; e += nt) TA[e % ka + (e / ka) * m] = C[e % ka + order[e / ka] * lc];
+  for (int e = tid; e < kb * r; e += nt) TB[e % kb + (e / kb) * m] = W[e % kb + order[e / kb] * lw];
 }
 
 // out (rows x r, ld ldo) = Q [T; 0] with Q = H_0 H_1 ... H_{k-1} stored in X
@@ -598,7 +607,14 @@ void launch_house_qr(double* A, int64_t lda, int rows_a, double* B, int64_t ldb,
 
 void launch_core_svd(const double* A, int64_t lda, int ka, const double* B, int64_t ldb, int kb, int m, double eps,
                      const int* nonzero, double* C, double* W, double* TA, double* TB, int* rank, cudaStream_t st) {
-  k_core_svd<<<1, 1024, 0, st>>>(A, lda, ka, B, ldb, kb, m, eps, nonzero, C, W, TA, TB, rank);
+  // C and W in shared memory when they fit (most temporaries)
+  constexpr size_t kMax = 160 * 1024;
+  static std::atomic<unsigned long long> attr{0};
+  const size_t bytes = ((size_t)ka * kb + (size_t)kb * kb) * sizeof(double);
+  const int in_smem = bytes <= kMax ? 1 : 0;
+  if (in_smem) smem_limit(k_core_svd, kMax, attr);
+  k_core_svd<<<1, 1024, in_smem ? bytes : 0, st>>>(A, lda, ka, B, ldb, kb, m, eps, nonzero, C, W, TA, TB, rank,
+                                                   in_smem);
 }
 
 void launch_apply_q(const double* A, int64_t lda, int rows_a, const double* tau_a, const double* TA, double* OA,

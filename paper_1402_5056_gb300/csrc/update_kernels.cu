@@ -35,61 +35,198 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// ---------------------------------------------------------------- teams
+// A cluster task runs on a team of NW warps.  A warp issues its float64
+// instructions to one sub-partition of the SM, which runs them at a
+// quarter of the SM's float64 rate; a launch with few tasks (the
+// factorisation applies its updates one at a time) therefore gives every
+// task a block of kTW = 4 warps, one per sub-partition, and a launch with
+// many tasks (a batch) runs one warp per task without block barriers.  The
+// arithmetic is the same in both forms: the rows of a task are dealt to kTW
+// virtual warps, each forms its partial sums in row order, and the kTW
+// partial sums are added as (p0 + p1) + (p2 + p3) -- one warp plays all
+// four virtual warps when NW = 1.  An update gives the same bits whichever
+// form its launches take.
+constexpr int kTW = 4;               // virtual warps of a task
+constexpr int kRW = kCh / kTW;       // rows of a 32-row chunk per virtual warp
+
+template <int NW>
+struct Team {
+  static_assert(NW == 1 || NW == kTW, "a task runs on one warp or on kTW warps");
+  static constexpr int VW = kTW / NW;   // virtual warps per warp
+  int wp;        // warp of the task (0 when NW = 1)
+  int lane;
+  double* buf;   // NW > 1: two buffers of 3 x 128 doubles for the sums
+  int ph;
+  __device__ __forceinline__ int vw(int v) const { return wp * VW + v; }
+  __device__ __forceinline__ bool lead() const { return wp == 0; }
+  __device__ __forceinline__ void sync() const {
+    if constexpr (NW > 1) __syncthreads();
+    else __syncwarp();
+  }
+  // Per-lane sums over the kTW virtual warps of x[v], added in warp order.
+  // NW > 1: one barrier per call; the two buffers alternate, so a buffer is
+  // written again only after every thread passed the barrier of the call in
+  // between.  Every thread of the team makes the same calls.
+  template <class T>
+  __device__ __forceinline__ void sum3(const T (&x)[VW], const T (&y)[VW], const T (&z)[VW], T& sx, T& sy, T& sz) {
+    if constexpr (NW == 1) {
+      sx = (x[0] + x[1]) + (x[2] + x[3]);
+      sy = (y[0] + y[1]) + (y[2] + y[3]);
+      sz = (z[0] + z[1]) + (z[2] + z[3]);
+    } else {
+      double* b = buf + ph * 384;
+      ph ^= 1;
+      b[wp * 32 + lane] = x[0];
+      b[128 + wp * 32 + lane] = y[0];
+      b[256 + wp * 32 + lane] = z[0];
+      __syncthreads();
+      sx = ((T)b[lane] + (T)b[32 + lane]) + ((T)b[64 + lane] + (T)b[96 + lane]);
+      sy = ((T)b[128 + lane] + (T)b[160 + lane]) + ((T)b[192 + lane] + (T)b[224 + lane]);
+      sz = ((T)b[256 + lane] + (T)b[288 + lane]) + ((T)b[320 + lane] + (T)b[352 + lane]);
+    }
+  }
+  __device__ __forceinline__ double sum1(const double (&x)[VW]) {
+    if constexpr (NW == 1) {
+      return (x[0] + x[1]) + (x[2] + x[3]);
+    } else {
+      double* b = buf + ph * 384;
+      ph ^= 1;
+      b[wp * 32 + lane] = x[0];
+      __syncthreads();
+      return (b[lane] + b[32 + lane]) + (b[64 + lane] + b[96 + lane]);
+    }
+  }
+  // maximum over the warps of a value (exact in any order)
+  __device__ __forceinline__ double max1(double x) {
+    if constexpr (NW == 1) {
+      return x;
+    } else {
+      double* b = buf + ph * 384;
+      ph ^= 1;
+      b[wp * 32 + lane] = x;
+      __syncthreads();
+      return fmax(fmax(b[lane], b[32 + lane]), fmax(b[64 + lane], b[96 + lane]));
+    }
+  }
+};
+
 // R (ncol x ncol, upper triangular, shared, ld kLdr) <- R-factor of [R; X].
-// X has `ch` rows; lane c < ncol holds column c of X in x[].  One
+// X has `ch` rows; slot (v, ii) of the team's registers holds row
+// kTW ii + vw(v), x[v][ii] = X[kTW ii + vw(v)][lane] (lane = column).  One
 // Householder reflection H = I - tau u u^* per column j, u = [R_jj - beta;
-// X[:, j]], beta = -sign(R_jj) ||[R_jj; X[:, j]]||, tau = -1 / (beta u_0).
-// The pivot column is spread over the lanes (lane i takes row i) so that
-// its norm is a warp reduction and every float64 instruction of the step
-// works on all lanes; R keeps ncol rows (rows beyond the rank stay zero).
-__device__ __forceinline__ void fold(double* R, double (&x)[kCh], int ch, int ncol, double* vb, int lane) {
+// X[:, j]], beta = -sign(R_jj) ||[R_jj; X[:, j]]||, tau = -1 / (beta u_0):
+// column j goes to vb (shared, by row), the two sums over the rows a column
+// needs (its norm and its products with the trailing columns) come from one
+// warp-order reduction, and the lead warp writes R.  R keeps ncol rows
+// (rows beyond the rank stay zero).  R is complete on return.
+template <int NW>
+__device__ __forceinline__ void fold_t(double* R, double* vb, double (&x)[Team<NW>::VW][kRW], int ch, int ncol,
+                                       Team<NW>& tm) {
+  constexpr int VW = Team<NW>::VW;
+  const int lane = tm.lane;
   for (int j = 0; j < ncol; ++j) {
+    __syncwarp();   // the warp's reads of vb for the previous column are done
     double xi = 0.0;
 #pragma unroll
-    for (int i = 0; i < kCh; ++i)
-      if (i < ch) {
-        const double t = __shfl_sync(kFull, x[i], j);
-        if (lane == i) xi = t;
-      }
-    const double s2 = warp_sum(xi * xi);
-    if (s2 == 0.0) continue;   // nothing below the diagonal: H = I
-    const double alpha = R[j + j * kLdr];
-    const double nrm = sqrt(fma(alpha, alpha, s2));
+    for (int v = 0; v < VW; ++v)
+#pragma unroll
+      for (int ii = 0; ii < kRW; ++ii)
+        if (kTW * ii + tm.vw(v) < ch) {
+          const double t = __shfl_sync(kFull, x[v][ii], j);
+          if (lane == ii * VW + v) xi = t;
+        }
+    if (lane < kRW * VW) {
+      const int i = kTW * (lane / VW) + tm.vw(lane % VW);
+      if (i < ch) vb[i] = xi;
+    }
+    __syncwarp();
+    // squared norm of the virtual warps' parts of column j: a butterfly over
+    // the lanes that hold them (lane ii VW + v), the same tree in both forms
+    double q = __dmul_rn(xi, xi);   // rounded here: never fused into the first sum
+#pragma unroll
+    for (int o = VW; o < kRW * VW; o <<= 1) q += __shfl_xor_sync(kFull, q, o);
+    const bool trail = lane > j && lane < ncol;
+    double s2[VW], dot[VW], none[VW];
+#pragma unroll
+    for (int v = 0; v < VW; ++v) {
+      s2[v] = __shfl_sync(kFull, q, v);
+      dot[v] = 0.0;
+      none[v] = 0.0;
+      if (trail)
+#pragma unroll
+        for (int ii = 0; ii < kRW; ++ii) {
+          const int i = kTW * ii + tm.vw(v);
+          if (i < ch) dot[v] = fma(vb[i], x[v][ii], dot[v]);
+        }
+    }
+    const double alpha = R[j + j * kLdr];   // read before the lead warp writes R below
+    const double rjc = trail ? R[j + lane * kLdr] : 0.0;
+    double S2, DOT, NONE;
+    tm.sum3(s2, dot, none, S2, DOT, NONE);
+    if (S2 == 0.0) continue;   // nothing below the diagonal: H = I
+    const double nrm = sqrt(fma(alpha, alpha, S2));
     const double beta = alpha >= 0.0 ? -nrm : nrm;
     const double u0 = alpha - beta;
     const double tau = -1.0 / (beta * u0);
-    if (lane < ch) vb[lane] = xi;
-    __syncwarp();
     if (lane == j) {
-      R[j + j * kLdr] = beta;
+      if (tm.lead()) R[j + j * kLdr] = beta;
 #pragma unroll
-      for (int i = 0; i < kCh; ++i) x[i] = 0.0;
-    } else if (lane > j && lane < ncol) {
-      double w = u0 * R[j + lane * kLdr];
+      for (int v = 0; v < VW; ++v)
 #pragma unroll
-      for (int i = 0; i < kCh; ++i)
-        if (i < ch) w = fma(vb[i], x[i], w);
-      w *= tau;
-      R[j + lane * kLdr] = fma(-w, u0, R[j + lane * kLdr]);
+        for (int ii = 0; ii < kRW; ++ii) x[v][ii] = 0.0;
+    } else if (trail) {
+      const double wc = tau * fma(u0, rjc, DOT);
+      if (tm.lead()) R[j + lane * kLdr] = fma(-wc, u0, rjc);
 #pragma unroll
-      for (int i = 0; i < kCh; ++i)
-        if (i < ch) x[i] = fma(-w, vb[i], x[i]);
+      for (int v = 0; v < VW; ++v)
+#pragma unroll
+        for (int ii = 0; ii < kRW; ++ii) {
+          const int i = kTW * ii + tm.vw(v);
+          if (i < ch) x[v][ii] = fma(-wc, vb[i], x[v][ii]);
+        }
     }
-    __syncwarp();
   }
+  tm.sync();
 }
 
-__device__ __forceinline__ void zero_tile(double* R, int lane) {
-  for (int c = 0; c < 32; ++c) R[lane + c * kLdr] = 0.0;
-  __syncwarp();
+template <int NW>
+__device__ __forceinline__ void zero_tile_t(double* R, const Team<NW>& tm) {
+  for (int c = tm.wp; c < 32; c += NW) R[tm.lane + c * kLdr] = 0.0;
+  tm.sync();
 }
 
-// Copy the ncol x ncol upper part of a shared R tile to a global 32x32 slot.
-__device__ __forceinline__ void store_tile(double* dst, const double* R, int ncol, int lane) {
-  __syncwarp();
-  if (lane < ncol)
-    for (int i = 0; i < 32; ++i) dst[i + lane * 32] = (i < ncol) ? R[i + lane * kLdr] : 0.0;
-  __syncwarp();
+// Copy the ncol x ncol upper part of a shared R tile to a global 32x32
+// slot (columns beyond ncol are not written).
+template <int NW>
+__device__ __forceinline__ void store_tile_t(double* dst, const double* R, int ncol, const Team<NW>& tm) {
+  tm.sync();
+  for (int c = tm.wp; c < ncol; c += NW) dst[tm.lane + c * 32] = tm.lane < ncol ? R[tm.lane + c * kLdr] : 0.0;
+}
+
+// Shared memory of one task of the fold kernels (doubles): the R tile, the
+// pivot column and, for four-warp teams, the sum buffers.
+__host__ __device__ constexpr int fold_doubles(int nw) { return 32 * kLdr + 32 + (nw > 1 ? 768 : 0); }
+
+// Task index, team and shared memory of a task of a kernel launched with
+// one block of kTW warps per task (NW = kTW) or one warp per task (NW = 1);
+// `per` doubles of dynamic shared memory per task.
+template <int NW>
+__device__ __forceinline__ int team_task(Team<NW>& tm, double*& base, double* smem, int per, int sums_off) {
+  const int w = threadIdx.x >> 5;
+  tm.lane = threadIdx.x & 31;
+  tm.ph = 0;
+  if constexpr (NW > 1) {
+    tm.wp = w;
+    base = smem;
+    tm.buf = smem + sums_off;
+    return blockIdx.x;
+  } else {
+    tm.wp = 0;
+    base = smem + (size_t)w * per;
+    tm.buf = nullptr;
+    return blockIdx.x * (blockDim.x >> 5) + w;
+  }
 }
 
 __device__ __forceinline__ int jacobi_partner(int lane, int r, int n2) {
@@ -112,33 +249,35 @@ __device__ __forceinline__ int jacobi_partner(int lane, int r, int n2) {
 //          launch per level, top-down)
 // omega_b = sqrt(#T_t) / ||S_b||_F (block-relative reading).  Column side:
 // S_b instead of S_b^* and col(s).  Cluster lists encode side << 30 | id.
-__global__ void k_blockweights(MatView M, const int32_t* __restrict__ list, int n, BlockLists BL,
-                               BaseWeights BW, int* err) {
+template <int NW>
+__global__ void __launch_bounds__(128) k_blockweights(MatView M, const int32_t* __restrict__ list, int n,
+                                                     BlockLists BL, BaseWeights BW, int* err) {
   extern __shared__ double smem[];
-  const int lane = threadIdx.x & 31;
-  const int w = threadIdx.x >> 5;
-  const int idx = blockIdx.x * (blockDim.x >> 5) + w;
+  Team<NW> tm;
+  double* R;
+  const int idx = team_task<NW>(tm, R, smem, fold_doubles(1), fold_doubles(1));
   if (idx >= n) return;
-  double* R = smem + w * (32 * kLdr + kCh + 1);
   double* vb = R + 32 * kLdr;
+  const int lane = tm.lane;
+  constexpr int VW = Team<NW>::VW;
   const int side = list[idx] >> 30;
   const int c = list[idx] & 0x3fffffff;
   if (!pick(BW.need, side)[c]) return;
   const int k = pick(M.rank, side)[c];
   const int kcap = M.kcap;
   if (k > 32) {
-    if (lane == 0) flag(err, kErrCols);
+    if (tm.lead() && lane == 0) flag(err, kErrCols);
     return;
   }
-  zero_tile(R, lane);
+  zero_tile_t(R, tm);
   const double st = sqrt((double)pick(M.subtree, side)[c]);
-  double x[kCh];
+  double x[VW][kRW];
   for (int e = pick(BL.ptr, side)[c]; e < pick(BL.ptr, side)[c + 1]; ++e) {
     const int slot = pick(BL.adm, side)[e];
     const int o = pick(BL.other, side)[slot];
     const int l = pick(M.rank, 1 - side)[o];
     const double* S = M.S + (size_t)slot * kcap * kcap;
-    // ||S_b||_F
+    // ||S_b||_F (every warp of the team alike)
     double part = 0.0;
     const int scols = side == 0 ? l : k;
     const int srows = side == 0 ? k : l;
@@ -151,69 +290,81 @@ __global__ void k_blockweights(MatView M, const int32_t* __restrict__ list, int 
     const double om = nrm > 0.0 ? st / nrm : 0.0;
     // rows of the stack: side 0 -> S^* (l x k), side 1 -> S (l x k); l = other side's rank
 #pragma unroll
-    for (int i = 0; i < kCh; ++i) {
-      double v = 0.0;
-      if (i < l && lane < k) v = side == 0 ? S[lane + i * kcap] : S[i + lane * kcap];
-      x[i] = om * v;
-    }
-    fold(R, x, l, k, vb, lane);
+    for (int v = 0; v < VW; ++v)
+#pragma unroll
+      for (int ii = 0; ii < kRW; ++ii) {
+        const int i = kTW * ii + tm.vw(v);
+        double y = 0.0;
+        if (i < l && lane < k) y = side == 0 ? S[lane + i * kcap] : S[i + lane * kcap];
+        x[v][ii] = om * y;
+      }
+    fold_t(R, vb, x, l, k, tm);
   }
-  store_tile(pick(BW.G, side) + (size_t)c * kSlot, R, k, lane);
+  store_tile_t(pick(BW.G, side) + (size_t)c * kSlot, R, k, tm);
 }
 
-__global__ void k_baseweights(MatView M, const int32_t* __restrict__ list, int n, BaseWeights BW, int* err) {
+template <int NW>
+__global__ void __launch_bounds__(128) k_baseweights(MatView M, const int32_t* __restrict__ list, int n,
+                                                    BaseWeights BW, int* err) {
   extern __shared__ double smem[];
-  const int lane = threadIdx.x & 31;
-  const int w = threadIdx.x >> 5;
-  const int idx = blockIdx.x * (blockDim.x >> 5) + w;
+  Team<NW> tm;
+  double* R;
+  const int idx = team_task<NW>(tm, R, smem, fold_doubles(1), fold_doubles(1));
   if (idx >= n) return;
-  double* R = smem + w * (32 * kLdr + kCh + 1);
   double* vb = R + 32 * kLdr;
+  const int lane = tm.lane;
+  constexpr int VW = Team<NW>::VW;
   const int side = list[idx] >> 30;
   const int c = list[idx] & 0x3fffffff;
   if (!pick(BW.need, side)[c]) return;
   const int k = pick(M.rank, side)[c];
   const int kcap = M.kcap;
   if (k > 32) {
-    if (lane == 0) flag(err, kErrCols);
+    if (tm.lead() && lane == 0) flag(err, kErrCols);
     return;
   }
-  zero_tile(R, lane);
+  zero_tile_t(R, tm);
   const double* G = pick(BW.G, side) + (size_t)c * kSlot;
-  if (lane < k)
+  if (tm.lead() && lane < k)
     for (int i = 0; i <= lane; ++i) R[i + lane * kLdr] = G[i + lane * 32];
-  __syncwarp();
+  tm.sync();
   const int f = pick(M.father, side)[c];
   if (f >= 0) {
     const int kf = pick(M.rank, side)[f];
     const double* P = pick(BW.B, side) + (size_t)f * kSlot;
     const double* E = pick(M.transfer, side) + (size_t)c * kcap * kcap;   // k x kf
-    double x[kCh];
+    double x[VW][kRW];
 #pragma unroll
-    for (int i = 0; i < kCh; ++i) {
-      double v = 0.0;
-      if (i < kf && lane < k)
-        for (int q = i; q < kf; ++q) v = fma(P[i + q * 32], E[lane + q * kcap], v);
-      x[i] = v;
-    }
-    fold(R, x, kf, k, vb, lane);
+    for (int v = 0; v < VW; ++v)
+#pragma unroll
+      for (int ii = 0; ii < kRW; ++ii) {
+        const int i = kTW * ii + tm.vw(v);
+        double y = 0.0;
+        if (i < kf && lane < k)
+          for (int q = i; q < kf; ++q) y = fma(P[i + q * 32], E[lane + q * kcap], y);
+        x[v][ii] = y;
+      }
+    fold_t(R, vb, x, kf, k, tm);
   }
-  store_tile(pick(BW.B, side) + (size_t)c * kSlot, R, k, lane);
+  store_tile_t(pick(BW.B, side) + (size_t)c * kSlot, R, k, tm);
 }
 
 // ------------------------------------------------------------- step 2
 // Basis R-factors bottom-up: leaf qr_R((V_t, F|_t)); inner
 // qr_R([R_{t1} E~_{t1}; R_{t2} E~_{t2}]) with E~ = diag(E, I_u).
-__global__ void k_rfactor(MatView M, const Item* __restrict__ items, const int32_t* __restrict__ list,
-                          int n, int u, const double* __restrict__ A, const double* __restrict__ B,
-                          ItemBuffers IB, int* err) {
+template <int NW>
+__global__ void __launch_bounds__(128) k_rfactor(MatView M, const Item* __restrict__ items,
+                                                const int32_t* __restrict__ list, int n, int u,
+                                                const double* __restrict__ A, const double* __restrict__ B,
+                                                ItemBuffers IB, int* err) {
   extern __shared__ double smem[];
-  const int lane = threadIdx.x & 31;
-  const int w = threadIdx.x >> 5;
-  const int idx = blockIdx.x * (blockDim.x >> 5) + w;
+  Team<NW> tm;
+  double* R;
+  const int idx = team_task<NW>(tm, R, smem, fold_doubles(1), fold_doubles(1));
   if (idx >= n) return;
-  double* R = smem + w * (32 * kLdr + kCh + 1);
   double* vb = R + 32 * kLdr;
+  const int lane = tm.lane;
+  constexpr int VW = Team<NW>::VW;
   const int id = list[idx];
   const Item it = items[id];
   if (!IB.fail[it.update]) return;
@@ -221,11 +372,11 @@ __global__ void k_rfactor(MatView M, const Item* __restrict__ items, const int32
   const int k = it.k;
   const int K = k + u;
   if (K > 32) {
-    if (lane == 0) flag(err, kErrCols);
+    if (tm.lead() && lane == 0) flag(err, kErrCols);
     return;
   }
-  zero_tile(R, lane);
-  double x[kCh];
+  zero_tile_t(R, tm);
+  double x[VW][kRW];
   if (it.flags & kItemLeaf) {
     const double* V = pick(M.leaf, side) + pick(M.leaf_off, side)[it.cluster];
     const double* F = (side == 0 ? A : B) + it.foff;
@@ -233,17 +384,20 @@ __global__ void k_rfactor(MatView M, const Item* __restrict__ items, const int32
     for (int r0 = 0; r0 < m; r0 += kCh) {
       const int ch = min(kCh, m - r0);
 #pragma unroll
-      for (int i = 0; i < kCh; ++i) {
-        double v = 0.0;
-        if (i < ch) {
-          if (lane < k)
-            v = V[(r0 + i) + lane * m];
-          else if (lane < K)
-            v = F[(it.rowoff + r0 + i) + (size_t)(lane - k) * it.ld];
+      for (int v = 0; v < VW; ++v)
+#pragma unroll
+        for (int ii = 0; ii < kRW; ++ii) {
+          const int i = kTW * ii + tm.vw(v);
+          double y = 0.0;
+          if (i < ch) {
+            if (lane < k)
+              y = V[(r0 + i) + lane * m];
+            else if (lane < K)
+              y = F[(it.rowoff + r0 + i) + (size_t)(lane - k) * it.ld];
+          }
+          x[v][ii] = y;
         }
-        x[i] = v;
-      }
-      fold(R, x, ch, K, vb, lane);
+      fold_t(R, vb, x, ch, K, tm);
     }
   } else {
     const int sons[2] = {it.son0, it.son1};
@@ -254,21 +408,24 @@ __global__ void k_rfactor(MatView M, const Item* __restrict__ items, const int32
       const double* Rs = IB.Rq + (size_t)sons[si] * kSlot;
       const double* E = pick(M.transfer, side) + (size_t)sn.cluster * M.kcap * M.kcap;   // ks x k
 #pragma unroll
-      for (int i = 0; i < kCh; ++i) {
-        double v = 0.0;
-        if (i < Ks) {
-          if (lane < k) {
-            for (int q = 0; q < ks; ++q) v = fma(Rs[i + q * 32], E[q + lane * M.kcap], v);
-          } else if (lane < K) {
-            v = Rs[i + (ks + lane - k) * 32];
+      for (int v = 0; v < VW; ++v)
+#pragma unroll
+        for (int ii = 0; ii < kRW; ++ii) {
+          const int i = kTW * ii + tm.vw(v);
+          double y = 0.0;
+          if (i < Ks) {
+            if (lane < k) {
+              for (int q = 0; q < ks; ++q) y = fma(Rs[i + q * 32], E[q + lane * M.kcap], y);
+            } else if (lane < K) {
+              y = Rs[i + (ks + lane - k) * 32];
+            }
           }
+          x[v][ii] = y;
         }
-        x[i] = v;
-      }
-      fold(R, x, Ks, K, vb, lane);
+      fold_t(R, vb, x, Ks, K, tm);
     }
   }
-  store_tile(IB.Rq + (size_t)id * kSlot, R, K, lane);
+  store_tile_t(IB.Rq + (size_t)id * kSlot, R, K, tm);
 }
 
 // Norms ||R_t S~_b R_s^*||_F of the blocks inside the update (both sides
@@ -334,15 +491,18 @@ __device__ __forceinline__ bool basis_orthonormal(const double* Rown, int k, int
   return __all_sync(kFull, orth);
 }
 
-__global__ void k_outside(MatView M, const Item* __restrict__ items, const Entry* __restrict__ ents,
-                          const int32_t* __restrict__ list, int n, int u, ItemBuffers IB) {
+template <int NW>
+__global__ void __launch_bounds__(128) k_outside(MatView M, const Item* __restrict__ items,
+                                                const Entry* __restrict__ ents, const int32_t* __restrict__ list,
+                                                int n, int u, ItemBuffers IB) {
   extern __shared__ double smem[];
-  const int lane = threadIdx.x & 31;
-  const int w = threadIdx.x >> 5;
-  const int idx = blockIdx.x * (blockDim.x >> 5) + w;
+  Team<NW> tm;
+  double* R;
+  const int idx = team_task<NW>(tm, R, smem, fold_doubles(1), fold_doubles(1));
   if (idx >= n) return;
-  double* R = smem + w * (32 * kLdr + kCh + 1);
   double* vb = R + 32 * kLdr;
+  const int lane = tm.lane;
+  constexpr int VW = Team<NW>::VW;
   const int id = list[idx];
   const Item it = items[id];
   if (!IB.fail[it.update]) return;
@@ -350,13 +510,13 @@ __global__ void k_outside(MatView M, const Item* __restrict__ items, const Entry
   const int k = it.k;
   const int kcap = M.kcap;
   const double* Rown = IB.Rq + (size_t)id * kSlot;
-  const bool orth = basis_orthonormal(Rown, k, lane);
+  const bool orth = basis_orthonormal(Rown, k, lane);   // every warp of the team alike
   const bool own = (it.flags & kItemInside) || !orth;
-  if (lane == 0) IB.own[id] = own ? 1 : 0;
+  if (tm.lead() && lane == 0) IB.own[id] = own ? 1 : 0;
   if (!own) return;
-  zero_tile(R, lane);
+  zero_tile_t(R, tm);
   const double st = sqrt((double)pick(M.subtree, side)[it.cluster]);
-  double x[kCh];
+  double x[VW][kRW];
   for (int e = it.ent_begin; e < it.ent_end; ++e) {
     const Entry en = ents[e];
     if (en.other >= 0) continue;
@@ -369,8 +529,8 @@ __global__ void k_outside(MatView M, const Item* __restrict__ items, const Entry
       const int srows = side == 0 ? k : l;
       if (lane < scols)
         for (int i = 0; i < srows; ++i) {
-          const double v = S[i + lane * kcap];
-          part = fma(v, v, part);
+          const double y = S[i + lane * kcap];
+          part = fma(y, y, part);
         }
     } else if (lane < l) {
       // ||R_kk S_b||_F (side 0, S is k x l) or ||S_b R_kk^*||_F (side 1, S is l x k)
@@ -384,26 +544,31 @@ __global__ void k_outside(MatView M, const Item* __restrict__ items, const Entry
     const double nrm = sqrt(warp_sum(part));
     const double om = nrm > 0.0 ? st / nrm : 0.0;
 #pragma unroll
-    for (int i = 0; i < kCh; ++i) {
-      double v = 0.0;
-      if (i < l && lane < k) v = side == 0 ? S[lane + i * kcap] : S[i + lane * kcap];
-      x[i] = om * v;
-    }
-    fold(R, x, l, k, vb, lane);
+    for (int v = 0; v < VW; ++v)
+#pragma unroll
+      for (int ii = 0; ii < kRW; ++ii) {
+        const int i = kTW * ii + tm.vw(v);
+        double y = 0.0;
+        if (i < l && lane < k) y = side == 0 ? S[lane + i * kcap] : S[i + lane * kcap];
+        x[v][ii] = om * y;
+      }
+    fold_t(R, vb, x, l, k, tm);
   }
-  store_tile(IB.Bw + (size_t)id * kSlot, R, k, lane);
+  store_tile_t(IB.Bw + (size_t)id * kSlot, R, k, tm);
 }
 
-__global__ void k_weights(MatView M, const Item* __restrict__ items, const Entry* __restrict__ ents,
-                          const int32_t* __restrict__ list, int n, int u, BaseWeights BW,
-                          ItemBuffers IB, int* err) {
+template <int NW>
+__global__ void __launch_bounds__(128) k_weights(MatView M, const Item* __restrict__ items,
+                                                const Entry* __restrict__ ents, const int32_t* __restrict__ list,
+                                                int n, int u, BaseWeights BW, ItemBuffers IB, int* err) {
   extern __shared__ double smem[];
-  const int lane = threadIdx.x & 31;
-  const int w = threadIdx.x >> 5;
-  const int idx = blockIdx.x * (blockDim.x >> 5) + w;
+  Team<NW> tm;
+  double* R;
+  const int idx = team_task<NW>(tm, R, smem, fold_doubles(1), fold_doubles(1));
   if (idx >= n) return;
-  double* R = smem + w * (32 * kLdr + kCh + 1);
   double* vb = R + 32 * kLdr;
+  const int lane = tm.lane;
+  constexpr int VW = Team<NW>::VW;
   const int id = list[idx];
   const Item it = items[id];
   if (!IB.fail[it.update]) return;
@@ -411,15 +576,15 @@ __global__ void k_weights(MatView M, const Item* __restrict__ items, const Entry
   const int k = it.k;
   const int K = k + u;
   const int kcap = M.kcap;
-  zero_tile(R, lane);
-  double x[kCh];
+  zero_tile_t(R, tm);
+  double x[VW][kRW];
   const double st = sqrt((double)pick(M.subtree, side)[it.cluster]);
   // outside blocks: their R-factor, padded with zero columns to K
   {
     const double* G = IB.own[id] ? IB.Bw + (size_t)id * kSlot : pick(BW.G, side) + (size_t)it.cluster * kSlot;
-    if (lane < k)
+    if (tm.lead() && lane < k)
       for (int i = 0; i <= lane; ++i) R[i + lane * kLdr] = G[i + lane * 32];
-    __syncwarp();
+    tm.sync();
   }
   // blocks inside the update: omega_b R_{W,s} S~_b^* (K_s x K_t)
   if (it.flags & kItemInside)
@@ -434,21 +599,24 @@ __global__ void k_weights(MatView M, const Item* __restrict__ items, const Entry
       const double om = nrm > 0.0 ? st / nrm : 0.0;
       const double* Ro = IB.Rq + (size_t)en.other * kSlot;
 #pragma unroll
-      for (int i = 0; i < kCh; ++i) {
-        double v = 0.0;
-        if (i < Ko) {
-          if (lane < k) {
-            // side 0: (R_W,s S~^*)[i, lane] = sum_q R[i,q] S[lane,q]
-            // side 1: (R_V,t S~)[i, lane]   = sum_q R[i,q] S[q,lane]
-            for (int q = i; q < l; ++q)
-              v = fma(Ro[i + q * 32], side == 0 ? S[lane + q * kcap] : S[q + lane * kcap], v);
-          } else if (lane < K) {
-            v = Ro[i + (l + lane - k) * 32];
+      for (int v = 0; v < VW; ++v)
+#pragma unroll
+        for (int ii = 0; ii < kRW; ++ii) {
+          const int i = kTW * ii + tm.vw(v);
+          double y = 0.0;
+          if (i < Ko) {
+            if (lane < k) {
+              // side 0: (R_W,s S~^*)[i, lane] = sum_q R[i,q] S[lane,q]
+              // side 1: (R_V,t S~)[i, lane]   = sum_q R[i,q] S[q,lane]
+              for (int q = i; q < l; ++q)
+                y = fma(Ro[i + q * 32], side == 0 ? S[lane + q * kcap] : S[q + lane * kcap], y);
+            } else if (lane < K) {
+              y = Ro[i + (l + lane - k) * 32];
+            }
           }
+          x[v][ii] = om * y;
         }
-        x[i] = om * v;
-      }
-      fold(R, x, Ko, K, vb, lane);
+      fold_t(R, vb, x, Ko, K, tm);
     }
   // father's part
   if (it.flags & kItemRoot) {
@@ -458,13 +626,16 @@ __global__ void k_weights(MatView M, const Item* __restrict__ items, const Entry
       const double* P = pick(BW.B, side) + (size_t)f * kSlot;
       const double* E = pick(M.transfer, side) + (size_t)it.cluster * kcap * kcap;   // k x kf
 #pragma unroll
-      for (int i = 0; i < kCh; ++i) {
-        double v = 0.0;
-        if (i < kf && lane < k)
-          for (int q = i; q < kf; ++q) v = fma(P[i + q * 32], E[lane + q * kcap], v);
-        x[i] = v;
-      }
-      fold(R, x, kf, K, vb, lane);
+      for (int v = 0; v < VW; ++v)
+#pragma unroll
+        for (int ii = 0; ii < kRW; ++ii) {
+          const int i = kTW * ii + tm.vw(v);
+          double y = 0.0;
+          if (i < kf && lane < k)
+            for (int q = i; q < kf; ++q) y = fma(P[i + q * 32], E[lane + q * kcap], y);
+          x[v][ii] = y;
+        }
+      fold_t(R, vb, x, kf, K, tm);
     }
   } else {
     const Item pt = items[it.parent];
@@ -473,20 +644,23 @@ __global__ void k_weights(MatView M, const Item* __restrict__ items, const Entry
     const double* P = IB.Bw + (size_t)it.parent * kSlot;
     const double* E = pick(M.transfer, side) + (size_t)it.cluster * kcap * kcap;   // k x kf
 #pragma unroll
-    for (int i = 0; i < kCh; ++i) {
-      double v = 0.0;
-      if (i < Kf) {
-        if (lane < k) {
-          for (int q = i; q < kf; ++q) v = fma(P[i + q * 32], E[lane + q * kcap], v);
-        } else if (lane < K) {
-          v = P[i + (kf + lane - k) * 32];
+    for (int v = 0; v < VW; ++v)
+#pragma unroll
+      for (int ii = 0; ii < kRW; ++ii) {
+        const int i = kTW * ii + tm.vw(v);
+        double y = 0.0;
+        if (i < Kf) {
+          if (lane < k) {
+            for (int q = i; q < kf; ++q) y = fma(P[i + q * 32], E[lane + q * kcap], y);
+          } else if (lane < K) {
+            y = P[i + (kf + lane - k) * 32];
+          }
         }
+        x[v][ii] = y;
       }
-      x[i] = v;
-    }
-    fold(R, x, Kf, K, vb, lane);
+    fold_t(R, vb, x, Kf, K, tm);
   }
-  store_tile(IB.Bw + (size_t)id * kSlot, R, K, lane);
+  store_tile_t(IB.Bw + (size_t)id * kSlot, R, K, tm);
   (void)err;
 }
 
@@ -498,83 +672,26 @@ __global__ void k_weights(MatView M, const Item* __restrict__ items, const Entry
 // subtree root commits E_t0 <- R_t0 [E_t0; 0] (Eqs. (Qt_condensed),
 // (hatQt_condensed)).
 //
-// One block of four warps per task.  A warp issues its float64
-// instructions to one sub-partition of the SM, at a quarter of the SM's
-// float64 rate, so a task spread over four warps finishes up to four times
-// sooner; the factorisation runs updates one by one, with far fewer tasks
-// per launch than the GPU has sub-partitions.  Lane c owns column c.  Warp
-// w owns the rows i of the tall matrices with (i / 2) mod 4 = w (two of
-// every eight, see trow) and every fourth row (or output row) of the K x K
-// ones.  A sum over rows is formed per warp and the four partial sums are
-// added in warp order by every thread, so that all warps take the same
-// rotations, certificate and rank.
-constexpr int kTW = 4;   // warps per truncation task
+// A task runs on a team (one warp, or a block of four).  Lane c owns column
+// c.  Virtual warp w owns the rows i of the tall matrices with
+// (i / 2) mod 4 = w (two of every eight, see trow), register slot (v, h) of
+// a warp holding row trow(h, vw(v)); the K x K products are split by their
+// output rows over the warps of the team.
 
-// row of the tall matrices held in slot h of warp w
+// row of the tall matrices held in slot h of virtual warp w
 __device__ __forceinline__ int trow(int h, int w) { return 8 * (h >> 1) + 2 * w + (h & 1); }
 
-// Per-lane sums (maxima) over the four warps, combined in warp order; two
-// alternating buffers of 3 x 128 doubles, so one barrier per call suffices
-// (a buffer is written again only after every thread passed the barrier of
-// the call in between).  Every thread of the block must make the same
-// calls.
-struct CtaSum {
-  double* buf;
-  int ph;
-  __device__ __forceinline__ double* next() {
-    double* b = buf + ph * 384;
-    ph ^= 1;
-    return b;
-  }
-  __device__ __forceinline__ static double add4(const double* b, int lane) {
-    return (b[lane] + b[32 + lane]) + (b[64 + lane] + b[96 + lane]);
-  }
-  __device__ __forceinline__ static float add4f(const double* b, int lane) {
-    return ((float)b[lane] + (float)b[32 + lane]) + ((float)b[64 + lane] + (float)b[96 + lane]);
-  }
-  __device__ __forceinline__ void sum3(double& x, double& y, double& z, int w, int lane) {
-    double* b = next();
-    b[w * 32 + lane] = x;
-    b[128 + w * 32 + lane] = y;
-    b[256 + w * 32 + lane] = z;
-    __syncthreads();
-    x = add4(b, lane);
-    y = add4(b + 128, lane);
-    z = add4(b + 256, lane);
-  }
-  __device__ __forceinline__ void sum3f(float& x, float& y, float& z, int w, int lane) {
-    double* b = next();
-    b[w * 32 + lane] = x;
-    b[128 + w * 32 + lane] = y;
-    b[256 + w * 32 + lane] = z;
-    __syncthreads();
-    x = add4f(b, lane);
-    y = add4f(b + 128, lane);
-    z = add4f(b + 256, lane);
-  }
-  __device__ __forceinline__ double sum1(double x, int w, int lane) {
-    double* b = next();
-    b[w * 32 + lane] = x;
-    __syncthreads();
-    return add4(b, lane);
-  }
-  __device__ __forceinline__ double max1(double x, int w, int lane) {
-    double* b = next();
-    b[w * 32 + lane] = x;
-    __syncthreads();
-    return fmax(fmax(b[lane], b[32 + lane]), fmax(b[64 + lane], b[96 + lane]));
-  }
-};
-
-// One-sided (Hestenes) Jacobi on the K columns (a[]: this warp's rows,
+// One-sided (Hestenes) Jacobi on the K columns (a[v][h]: the team's rows,
 // zero beyond `rows`): on return the columns are U Sigma, mutually
-// orthogonal.  Round-robin pairs; the two lanes of a pair split the warp's
-// rows (the lower lane the even slots, the upper the odd ones) and add
-// their partial sums; the warps' sums are added in warp order, so all
-// threads take the same rotation.
-template <int RW>
-__device__ __forceinline__ void jacobi_cta(double (&a)[RW], int rows, int ncol, CtaSum& cs, int w, int lane,
-                                           unsigned long long* cnt, int* err) {
+// orthogonal.  Round-robin pairs; within a virtual warp the two lanes of a
+// pair split the rows (the lower lane the even slots, the upper the odd
+// ones) and add their partial sums, and the virtual warps' sums are added
+// in warp order, so every thread takes the same rotation.
+template <int RW, int NW>
+__device__ __forceinline__ void jacobi_t(double (&a)[Team<NW>::VW][RW], int rows, int ncol, Team<NW>& tm,
+                                         unsigned long long* cnt, int* err) {
+  constexpr int VW = Team<NW>::VW;
+  const int lane = tm.lane;
   const int n2 = ncol + (ncol & 1);
   const int nr = n2 - 1;
   const double tol2 = (16.0 * DBL_EPSILON) * (16.0 * DBL_EPSILON);
@@ -585,43 +702,54 @@ __device__ __forceinline__ void jacobi_cta(double (&a)[RW], int rows, int ncol, 
     for (int r = 0; r < nr; ++r) {
       const int p = jacobi_partner(lane, r, n2);
       const bool lo = lane < p;
-      double al = 0.0, be = 0.0, ga = 0.0;
+      double al[VW], be[VW], ga[VW];
 #pragma unroll
-      for (int h = 0; h < RW / 2; ++h)
-        if (8 * h + 2 * w < rows) {
-          const double r0 = a[2 * h], r1 = a[2 * h + 1];
-          const double got = __shfl_sync(kFull, lo ? r1 : r0, p);
-          const double xx = lo ? r0 : got;
-          const double yy = lo ? got : r1;
-          al = fma(xx, xx, al);
-          be = fma(yy, yy, be);
-          ga = fma(xx, yy, ga);
-        }
-      al += __shfl_sync(kFull, al, p);
-      be += __shfl_sync(kFull, be, p);
-      ga += __shfl_sync(kFull, ga, p);
-      cs.sum3(al, be, ga, w, lane);
+      for (int v = 0; v < VW; ++v) {
+        const int w = tm.vw(v);
+        double x1 = 0.0, y1 = 0.0, g1 = 0.0;
+#pragma unroll
+        for (int h = 0; h < RW / 2; ++h)
+          if (8 * h + 2 * w < rows) {
+            const double r0 = a[v][2 * h], r1 = a[v][2 * h + 1];
+            const double got = __shfl_sync(kFull, lo ? r1 : r0, p);
+            const double xx = lo ? r0 : got;
+            const double yy = lo ? got : r1;
+            x1 = fma(xx, xx, x1);
+            y1 = fma(yy, yy, y1);
+            g1 = fma(xx, yy, g1);
+          }
+        x1 += __shfl_sync(kFull, x1, p);
+        y1 += __shfl_sync(kFull, y1, p);
+        g1 += __shfl_sync(kFull, g1, p);
+        al[v] = x1;
+        be[v] = y1;
+        ga[v] = g1;
+      }
+      double AL, BE, GA;
+      tm.sum3(al, be, ga, AL, BE, GA);
       const bool active = lane < n2 && p != lane;
       // rotate when |gamma| > tol sqrt(alpha beta); the columns are scaled
       // to max |entry| < 1, so the squares neither overflow nor matter when
       // they underflow
-      const bool rot = active && ga * ga > tol2 * (al * be);
+      const bool rot = active && GA * GA > tol2 * (AL * BE);
       double c = 1.0, s = 0.0;
       if (rot) {
         // t = tan(theta) of the rotation that makes the pair orthogonal:
         // t = gamma / (d + sign(d) sqrt(d^2 + gamma^2)), d = (beta - alpha) / 2
-        const double d = 0.5 * (be - al);
-        const double t = ga / (d + copysign(sqrt(fma(d, d, ga * ga)), d));
+        const double d = 0.5 * (BE - AL);
+        const double t = GA / (d + copysign(sqrt(fma(d, d, GA * GA)), d));
         c = rsqrt(fma(t, t, 1.0));
         s = c * t;
       }
       if (__any_sync(kFull, rot)) {
 #pragma unroll
-        for (int h = 0; h < RW; ++h)
-          if (trow(h, w) < rows) {
-            const double o = __shfl_sync(kFull, a[h], p);
-            if (rot) a[h] = lo ? fma(c, a[h], -s * o) : fma(s, o, c * a[h]);
-          }
+        for (int v = 0; v < VW; ++v)
+#pragma unroll
+          for (int h = 0; h < RW; ++h)
+            if (trow(h, tm.vw(v)) < rows) {
+              const double o = __shfl_sync(kFull, a[v][h], p);
+              if (rot) a[v][h] = lo ? fma(c, a[v][h], -s * o) : fma(s, o, c * a[v][h]);
+            }
       }
       if (active && lo) {
         pairs += 1;
@@ -631,9 +759,9 @@ __device__ __forceinline__ void jacobi_cta(double (&a)[RW], int rows, int ncol, 
     }
     converged = !__any_sync(kFull, any);
   }
-  if (!converged && threadIdx.x == 0) flag(err, kErrJacobi);
+  if (!converged && tm.lead() && lane == 0) flag(err, kErrJacobi);
   // per-item counters (pairs checked, rotations) for the flop statistics
-  if (w == 0) {
+  if (tm.lead()) {
     unsigned long long ps = pairs, rs = rots;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -649,11 +777,13 @@ __device__ __forceinline__ void jacobi_cta(double (&a)[RW], int rows, int ncol, 
 
 // Float32 one-sided Jacobi used as a preconditioner: rotates the float copy
 // af of the columns until they are orthogonal to float accuracy and
-// accumulates the rotations in V (vf[jj] = V[4 jj + w][lane]), so that
-// M V has nearly orthogonal columns.
-template <int RW>
-__device__ __forceinline__ void jacobi32_cta(float (&af)[RW], float (&vf)[8], int rows, int ncol, CtaSum& cs, int w,
-                                             int lane) {
+// accumulates the rotations in V (vf[v][jj] = V[4 jj + vw(v)][lane]), so
+// that M V has nearly orthogonal columns.
+template <int RW, int NW>
+__device__ __forceinline__ void jacobi32_t(float (&af)[Team<NW>::VW][RW], float (&vf)[Team<NW>::VW][8], int rows,
+                                           int ncol, Team<NW>& tm) {
+  constexpr int VW = Team<NW>::VW;
+  const int lane = tm.lane;
   const int n2 = ncol + (ncol & 1);
   const int nr = n2 - 1;
   const float tol = 1.0e-6f;
@@ -663,40 +793,51 @@ __device__ __forceinline__ void jacobi32_cta(float (&af)[RW], float (&vf)[8], in
     for (int r = 0; r < nr; ++r) {
       const int p = jacobi_partner(lane, r, n2);
       const bool lo = lane < p;
-      float al = 0.f, be = 0.f, ga = 0.f;
+      float al[VW], be[VW], ga[VW];
 #pragma unroll
-      for (int h = 0; h < RW; ++h)
-        if (trow(h, w) < rows) {
-          const float o = __shfl_sync(kFull, af[h], p);
-          const float xx = lo ? af[h] : o;
-          const float yy = lo ? o : af[h];
-          al = fmaf(xx, xx, al);
-          be = fmaf(yy, yy, be);
-          ga = fmaf(xx, yy, ga);
-        }
-      cs.sum3f(al, be, ga, w, lane);
+      for (int v = 0; v < VW; ++v) {
+        float x1 = 0.f, y1 = 0.f, g1 = 0.f;
+#pragma unroll
+        for (int h = 0; h < RW; ++h)
+          if (trow(h, tm.vw(v)) < rows) {
+            const float o = __shfl_sync(kFull, af[v][h], p);
+            const float xx = lo ? af[v][h] : o;
+            const float yy = lo ? o : af[v][h];
+            x1 = fmaf(xx, xx, x1);
+            y1 = fmaf(yy, yy, y1);
+            g1 = fmaf(xx, yy, g1);
+          }
+        al[v] = x1;
+        be[v] = y1;
+        ga[v] = g1;
+      }
+      float AL, BE, GA;
+      tm.sum3(al, be, ga, AL, BE, GA);
       const bool active = lane < n2 && p != lane;
-      const bool rot = active && al > 0.f && be > 0.f && fabsf(ga) > tol * sqrtf(al) * sqrtf(be);
+      const bool rot = active && AL > 0.f && BE > 0.f && fabsf(GA) > tol * sqrtf(AL) * sqrtf(BE);
       float c = 1.f, s = 0.f;
       if (rot) {
-        const float zeta = (be - al) / (2.f * ga);
+        const float zeta = (BE - AL) / (2.f * GA);
         const float t = copysignf(1.f, zeta) / (fabsf(zeta) + hypotf(1.f, zeta));
         c = rsqrtf(fmaf(t, t, 1.f));
         s = c * t;
       }
       if (__any_sync(kFull, rot)) {
 #pragma unroll
-        for (int h = 0; h < RW; ++h)
-          if (trow(h, w) < rows) {
-            const float o = __shfl_sync(kFull, af[h], p);
-            if (rot) af[h] = lo ? fmaf(c, af[h], -s * o) : fmaf(s, o, c * af[h]);
-          }
+        for (int v = 0; v < VW; ++v) {
 #pragma unroll
-        for (int jj = 0; jj < 8; ++jj)
-          if (4 * jj + w < ncol) {
-            const float o = __shfl_sync(kFull, vf[jj], p);
-            if (rot) vf[jj] = lo ? fmaf(c, vf[jj], -s * o) : fmaf(s, o, c * vf[jj]);
-          }
+          for (int h = 0; h < RW; ++h)
+            if (trow(h, tm.vw(v)) < rows) {
+              const float o = __shfl_sync(kFull, af[v][h], p);
+              if (rot) af[v][h] = lo ? fmaf(c, af[v][h], -s * o) : fmaf(s, o, c * af[v][h]);
+            }
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj)
+            if (4 * jj + tm.vw(v) < ncol) {
+              const float o = __shfl_sync(kFull, vf[v][jj], p);
+              if (rot) vf[v][jj] = lo ? fmaf(c, vf[v][jj], -s * o) : fmaf(s, o, c * vf[v][jj]);
+            }
+        }
       }
       any |= rot ? 1 : 0;
     }
@@ -706,33 +847,35 @@ __device__ __forceinline__ void jacobi32_cta(float (&af)[RW], float (&vf)[8], in
 
 // Two Newton-Schulz steps V <- V (3I - V^* V) / 2 in float64 on V (ncol x
 // ncol in Vs, ld ldg), with G = V^* V in Gs: turns the float32-accurate
-// rotation product into an orthogonal matrix to float64 accuracy.  Warp w
-// forms the rows i = w, w + 4, ... of G and of the new V.
-__device__ __forceinline__ void orthonormalize_cta(double* Vs, double* Gs, int ncol, int ldg, int w, int lane) {
+// rotation product into an orthogonal matrix to float64 accuracy.  The
+// warps of the team split the rows of G and of the new V.
+template <int NW>
+__device__ __forceinline__ void orthonormalize_t(double* Vs, double* Gs, int ncol, int ldg, const Team<NW>& tm) {
+  const int lane = tm.lane;
   for (int step = 0; step < 2; ++step) {
     if (lane < ncol)
-      for (int i = w; i < ncol; i += kTW) {
+      for (int i = tm.wp; i < ncol; i += NW) {
         double x = 0.0;
         for (int j = 0; j < ncol; ++j) x = fma(Vs[j + i * ldg], Vs[j + lane * ldg], x);
         Gs[i + lane * ldg] = x;
       }
-    __syncthreads();
-    double nv[8];
+    tm.sync();
+    double nv[32 / NW];
 #pragma unroll
-    for (int jj = 0; jj < 8; ++jj) {
-      const int j = 4 * jj + w;
+    for (int jj = 0; jj < 32 / NW; ++jj) {
+      const int j = jj * NW + tm.wp;
       double x = 0.0;
       if (j < ncol && lane < ncol)
         for (int i = 0; i < ncol; ++i) x = fma(Vs[j + i * ldg], Gs[i + lane * ldg], x);
       nv[jj] = (j < ncol && lane < ncol) ? fma(1.5, Vs[j + lane * ldg], -0.5 * x) : 0.0;
     }
-    __syncthreads();   // every read of V is done
+    tm.sync();   // every read of V is done
 #pragma unroll
-    for (int jj = 0; jj < 8; ++jj) {
-      const int j = 4 * jj + w;
+    for (int jj = 0; jj < 32 / NW; ++jj) {
+      const int j = jj * NW + tm.wp;
       if (j < ncol && lane < ncol) Vs[j + lane * ldg] = nv[jj];
     }
-    __syncthreads();
+    tm.sync();
   }
 }
 
@@ -743,109 +886,128 @@ __device__ __forceinline__ void orthonormalize_cta(double* Vs, double* Gs, int n
 // singular vectors (Eq. (Qt_condensed)).  The certificate is the Cholesky
 // factorisation of M^* M - (tau + delta) I succeeding, tau = (eps/2)^2 and
 // delta a bound on the rounding of the Gram matrix and of the
-// factorisation; the basis then comes from Cholesky-QR passes.  The
-// helpers below run on the four warps of a truncation task; X is the tall
-// matrix in shared memory (ld ldx), xr[] this warp's rows of column lane.
+// factorisation; the basis then comes from Cholesky-QR passes.  X is the
+// tall matrix in shared memory (ld ldx), xr[v][h] the team's rows of column
+// lane.
 
-// G = X^* X (K x K, ld ldg): warp w forms the rows j = w, w + 4, ... of G,
-// each entry one sum over the rows in order.
-__device__ __forceinline__ void gram_cta(const double* X, int ldx, int rows, int K, double* Gs, int ldg, int w,
-                                         int lane) {
+// G = X^* X (K x K, ld ldg): the warps split the rows j of G, each entry one
+// sum over the rows in order.
+template <int NW>
+__device__ __forceinline__ void gram_t(const double* X, int ldx, int rows, int K, double* Gs, int ldg,
+                                       const Team<NW>& tm) {
+  const int lane = tm.lane;
   if (lane < K)
-    for (int j = w; j < K; j += kTW) {
+    for (int j = tm.wp; j < K; j += NW) {
       double g = 0.0;
       for (int i = 0; i < rows; ++i) g = fma(X[i + j * ldx], X[i + lane * ldx], g);
       Gs[j + lane * ldg] = g;
     }
-  __syncthreads();
+  tm.sync();
 }
 
-// In-place Cholesky factorisation G - shift I = L L^* of the lower
-// triangle of Gs (ld ldg): lane i owns row i, the trailing update of column
-// k goes to warp k mod 4.  Returns false (on every thread alike) when a
-// pivot is not positive.
-__device__ __forceinline__ bool chol_cta(double* Gs, int K, double shift, int ldg, int w, int lane) {
-  if (w == 0 && lane < K) Gs[lane + lane * ldg] -= shift;
-  __syncthreads();
+// In-place Cholesky factorisation G - shift I = L L^* of the lower triangle
+// of Gs (ld ldg): lane i owns row i, the warps split the columns of the
+// trailing update.  Returns false (on every thread alike) when a pivot is
+// not positive.
+template <int NW>
+__device__ __forceinline__ bool chol_t(double* Gs, int K, double shift, int ldg, const Team<NW>& tm) {
+  const int lane = tm.lane;
+  if (tm.lead() && lane < K) Gs[lane + lane * ldg] -= shift;
+  tm.sync();
   for (int j = 0; j < K; ++j) {
     const double d = Gs[j + j * ldg];
     if (!(d > 0.0)) return false;
     const double ljj = sqrt(d);
     const double inv = 1.0 / ljj;
-    __syncthreads();   // every thread has read the pivot
-    if (w == 0) {
+    tm.sync();   // every thread has read the pivot
+    if (tm.lead()) {
       if (lane == j) Gs[j + j * ldg] = ljj;
       if (lane > j && lane < K) Gs[lane + j * ldg] *= inv;
     }
-    __syncthreads();
+    tm.sync();
     if (lane > j && lane < K) {
       const double lij = Gs[lane + j * ldg];
-      for (int k = j + 1 + ((w - j - 1) & 3); k <= lane; k += kTW)
+      for (int k = j + 1 + ((tm.wp - j - 1) & (NW - 1)); k <= lane; k += NW)
         Gs[lane + k * ldg] = fma(-lij, Gs[k + j * ldg], Gs[lane + k * ldg]);
     }
-    __syncthreads();
+    tm.sync();
   }
   return true;
 }
 
 // Xs = L^{-1} (lower triangular, ld ldg) for the Cholesky factor in Ls, one
 // row after the other: X[i][c] = -(sum_{c<=p<i} L[i][p] X[p][c]) / L[i][i],
-// lane c, the sum split over the warps by p mod 4.  dinv receives the
-// reciprocal diagonal.
-__device__ __forceinline__ void trinv_cta(const double* Ls, double* Xs, double* dinv, int K, int ldg, CtaSum& cs,
-                                          int w, int lane) {
-  if (w == 0 && lane < K) {
+// lane c, the sum split over the virtual warps by p mod 4.  dinv receives
+// the reciprocal diagonal.
+template <int NW>
+__device__ __forceinline__ void trinv_t(const double* Ls, double* Xs, double* dinv, int K, int ldg, Team<NW>& tm) {
+  constexpr int VW = Team<NW>::VW;
+  const int lane = tm.lane;
+  if (tm.lead() && lane < K) {
     const double di = 1.0 / Ls[lane + lane * ldg];
     dinv[lane] = di;
     Xs[lane + lane * ldg] = di;
   }
-  __syncthreads();
+  tm.sync();
   for (int i = 1; i < K; ++i) {
-    double t = 0.0;
-    if (lane < i)
-      for (int p = lane + ((w - lane) & 3); p < i; p += kTW) t = fma(Ls[i + p * ldg], Xs[p + lane * ldg], t);
-    t = cs.sum1(t, w, lane);
-    if (w == 0 && lane < i) Xs[i + lane * ldg] = -t * dinv[i];
-    __syncthreads();
+    double t[VW];
+#pragma unroll
+    for (int v = 0; v < VW; ++v) {
+      const int w = tm.vw(v);
+      double x = 0.0;
+      if (lane < i)
+        for (int p = lane + ((w - lane) & (kTW - 1)); p < i; p += kTW) x = fma(Ls[i + p * ldg], Xs[p + lane * ldg], x);
+      t[v] = x;
+    }
+    const double ts = tm.sum1(t);
+    if (tm.lead() && lane < i) Xs[i + lane * ldg] = -ts * dinv[i];
+    tm.sync();
   }
 }
 
-// X <- X L^{-*} for the Cholesky factor L in Gs; xr[] receives the new
-// rows of this warp.
-template <int RW>
-__device__ __forceinline__ void apply_inverse_cta(double* X, int ldx, double (&xr)[RW], int rows, int K,
-                                                  const double* Gs, double* Xs, double* dinv, int ldg, CtaSum& cs,
-                                                  int w, int lane) {
-  trinv_cta(Gs, Xs, dinv, K, ldg, cs, w, lane);
+// X <- X L^{-*} for the Cholesky factor L in Gs; xr receives the new rows
+// of the team.
+template <int RW, int NW>
+__device__ __forceinline__ void apply_inverse_t(double* X, int ldx, double (&xr)[Team<NW>::VW][RW], int rows, int K,
+                                                const double* Gs, double* Xs, double* dinv, int ldg, Team<NW>& tm) {
+  constexpr int VW = Team<NW>::VW;
+  const int lane = tm.lane;
+  trinv_t(Gs, Xs, dinv, K, ldg, tm);
 #pragma unroll
-  for (int h = 0; h < RW; ++h) xr[h] = 0.0;
+  for (int v = 0; v < VW; ++v)
+#pragma unroll
+    for (int h = 0; h < RW; ++h) xr[v][h] = 0.0;
   if (lane < K)
     for (int j = 0; j <= lane; ++j) {
       const double x = Xs[lane + j * ldg];
 #pragma unroll
-      for (int h = 0; h < RW; ++h) {
-        const int i = trow(h, w);
-        if (i < rows) xr[h] = fma(X[i + j * ldx], x, xr[h]);
-      }
+      for (int v = 0; v < VW; ++v)
+#pragma unroll
+        for (int h = 0; h < RW; ++h) {
+          const int i = trow(h, tm.vw(v));
+          if (i < rows) xr[v][h] = fma(X[i + j * ldx], x, xr[v][h]);
+        }
     }
   __syncwarp();   // the warp's rows are read before they are written
   if (lane < K)
 #pragma unroll
-    for (int h = 0; h < RW; ++h) {
-      const int i = trow(h, w);
-      if (i < rows) X[i + lane * ldx] = xr[h];
-    }
-  __syncthreads();
+    for (int v = 0; v < VW; ++v)
+#pragma unroll
+      for (int h = 0; h < RW; ++h) {
+        const int i = trow(h, tm.vw(v));
+        if (i < rows) X[i + lane * ldx] = xr[v][h];
+      }
+  tm.sync();
 }
 
 // One Cholesky-QR pass: G = X^* X = L L^*, X <- X L^{-*}.  False if the
 // factorisation breaks down.
-template <int RW>
-__device__ __forceinline__ bool cholqr_cta(double* X, int ldx, double (&xr)[RW], int rows, int K, double* Gs,
-                                           double* Xs, double* dinv, int ldg, CtaSum& cs, int w, int lane) {
-  gram_cta(X, ldx, rows, K, Gs, ldg, w, lane);
-  if (!chol_cta(Gs, K, 0.0, ldg, w, lane)) return false;
-  apply_inverse_cta<RW>(X, ldx, xr, rows, K, Gs, Xs, dinv, ldg, cs, w, lane);
+template <int RW, int NW>
+__device__ __forceinline__ bool cholqr_t(double* X, int ldx, double (&xr)[Team<NW>::VW][RW], int rows, int K,
+                                         double* Gs, double* Xs, double* dinv, int ldg, Team<NW>& tm) {
+  gram_t(X, ldx, rows, K, Gs, ldg, tm);
+  if (!chol_t(Gs, K, 0.0, ldg, tm)) return false;
+  apply_inverse_t<RW, NW>(X, ldx, xr, rows, K, Gs, Xs, dinv, ldg, tm);
   return true;
 }
 
@@ -853,10 +1015,12 @@ __device__ __forceinline__ bool cholqr_cta(double* X, int ldx, double (&xr)[RW],
 // 1e-7: with G = X^* X, X <- X (3I - G) / 2 leaves an orthogonality error of
 // order |G - I|^2.  Returns false, leaving X unchanged, when |G - I| is
 // larger.
-template <int RW>
-__device__ __forceinline__ bool polish_cta(double* X, int ldx, double (&xr)[RW], int rows, int K, double* Gs,
-                                           int ldg, int w, int lane) {
-  gram_cta(X, ldx, rows, K, Gs, ldg, w, lane);
+template <int RW, int NW>
+__device__ __forceinline__ bool polish_t(double* X, int ldx, double (&xr)[Team<NW>::VW][RW], int rows, int K,
+                                         double* Gs, int ldg, const Team<NW>& tm) {
+  constexpr int VW = Team<NW>::VW;
+  const int lane = tm.lane;
+  gram_t(X, ldx, rows, K, Gs, ldg, tm);
   double dev = 0.0;   // every warp reads all of G: the same maximum everywhere
   if (lane < K)
     for (int j = 0; j < K; ++j) dev = fmax(dev, fabs(Gs[j + lane * ldg] - (j == lane ? 1.0 : 0.0)));
@@ -866,54 +1030,61 @@ __device__ __forceinline__ bool polish_cta(double* X, int ldx, double (&xr)[RW],
   // column c: 1.5 x_c - 0.5 sum_j x_j G[j][c]
   if (lane < K) {
 #pragma unroll
-    for (int h = 0; h < RW; ++h) xr[h] *= 1.5;
+    for (int v = 0; v < VW; ++v)
+#pragma unroll
+      for (int h = 0; h < RW; ++h) xr[v][h] *= 1.5;
     for (int j = 0; j < K; ++j) {
       const double g = -0.5 * Gs[j + lane * ldg];
 #pragma unroll
-      for (int h = 0; h < RW; ++h) {
-        const int i = trow(h, w);
-        if (i < rows) xr[h] = fma(X[i + j * ldx], g, xr[h]);
-      }
+      for (int v = 0; v < VW; ++v)
+#pragma unroll
+        for (int h = 0; h < RW; ++h) {
+          const int i = trow(h, tm.vw(v));
+          if (i < rows) xr[v][h] = fma(X[i + j * ldx], g, xr[v][h]);
+        }
     }
   }
   __syncwarp();
   if (lane < K)
 #pragma unroll
-    for (int h = 0; h < RW; ++h) {
-      const int i = trow(h, w);
-      if (i < rows) X[i + lane * ldx] = xr[h];
-    }
-  __syncthreads();
+    for (int v = 0; v < VW; ++v)
+#pragma unroll
+      for (int h = 0; h < RW; ++h) {
+        const int i = trow(h, tm.vw(v));
+        if (i < rows) X[i + lane * ldx] = xr[v][h];
+      }
+  tm.sync();
   return true;
 }
 
-// Shared memory of one truncation task (doubles): V^ and Q (ld MR + 1,
-// kl columns each), two K x K tiles (ld ldg), 32 reciprocal pivots and the
-// warp-sum buffers.
+// Shared memory of one truncation task (doubles): V^ and Q (ld MR + 1, kl
+// columns each), two K x K tiles (ld ldg), 32 reciprocal pivots and, for a
+// four-warp team, the sum buffers.
 __host__ __device__ constexpr int trunc_ldg(int kl) { return (kl + 1) | 1; }
-__host__ __device__ constexpr size_t trunc_smem_doubles(int mr, int kl) {
-  return 2 * (size_t)(mr + 1) * kl + 2 * (size_t)kl * trunc_ldg(kl) + 32 + 768;
+__host__ __device__ constexpr size_t trunc_doubles(int mr, int kl, int nw) {
+  return 2 * (size_t)(mr + 1) * kl + 2 * (size_t)kl * trunc_ldg(kl) + 32 + (nw > 1 ? 768 : 0);
 }
 
-template <int MR>
-__global__ void __launch_bounds__(32 * kTW) k_truncate(MatView M, const Item* __restrict__ items,
-                                                       const int32_t* __restrict__ list, int n, int u, int kl,
-                                                       double eps, const double* __restrict__ A,
-                                                       const double* __restrict__ B, ItemBuffers IB, int* err) {
-  constexpr int RW = MR / kTW;   // rows per warp
+template <int MR, int NW>
+__global__ void __launch_bounds__(128) k_truncate(MatView M, const Item* __restrict__ items,
+                                                 const int32_t* __restrict__ list, int n, int u, int kl, double eps,
+                                                 const double* __restrict__ A, const double* __restrict__ B,
+                                                 ItemBuffers IB, int* err) {
+  constexpr int RW = MR / kTW;   // rows per virtual warp
   constexpr int LQ = MR + 1;     // leading dimension of V^ and Q in shared memory
+  constexpr int VW = Team<NW>::VW;
   extern __shared__ double smem[];
-  const int lane = threadIdx.x & 31;
-  const int w = threadIdx.x >> 5;
-  const int idx = blockIdx.x;
-  if (idx >= n) return;
   const int ldg = trunc_ldg(kl);
-  double* Vh = smem;
+  const int per = (int)trunc_doubles(MR, kl, 1);
+  Team<NW> tm;
+  double* Vh;
+  const int idx = team_task<NW>(tm, Vh, smem, per, per);
+  if (idx >= n) return;
+  const int lane = tm.lane;
   double* Qs = Vh + LQ * kl;
   double* Gs = Qs + LQ * kl;      // K x K Gram / Cholesky factor
   double* Xs = Gs + kl * ldg;     // K x K inverse factor / rotations V
   double* dinv = Xs + kl * ldg;   // 32 reciprocal pivots
-  CtaSum cs{dinv + 32, 0};
   const int id = list[idx];
   const Item it = items[id];
   if (!IB.fail[it.update]) return;
@@ -922,7 +1093,7 @@ __global__ void __launch_bounds__(32 * kTW) k_truncate(MatView M, const Item* __
   const int K = k + u;
   const int kcap = M.kcap;
   if (K > kl) {
-    if (threadIdx.x == 0) flag(err, kErrCols);
+    if (tm.lead() && lane == 0) flag(err, kErrCols);
     return;
   }
   int rows = 0;
@@ -935,7 +1106,7 @@ __global__ void __launch_bounds__(32 * kTW) k_truncate(MatView M, const Item* __
     rows = r1 + r2;
   }
   if (rows > MR) {
-    if (threadIdx.x == 0) flag(err, kErrRows);
+    if (tm.lead() && lane == 0) flag(err, kErrRows);
     return;
   }
   // V^_t into shared memory, one column per lane
@@ -943,69 +1114,78 @@ __global__ void __launch_bounds__(32 * kTW) k_truncate(MatView M, const Item* __
     const double* V = pick(M.leaf, side) + pick(M.leaf_off, side)[it.cluster];
     const double* F = (side == 0 ? A : B) + it.foff;
     if (lane < K)
-      for (int i = w; i < rows; i += kTW)
+      for (int i = tm.wp; i < rows; i += NW)
         Vh[i + lane * LQ] = lane < k ? V[i + lane * rows] : F[(it.rowoff + i) + (size_t)(lane - k) * it.ld];
   } else {
-    const int sons[2] = {it.son0, it.son1};
-    int row0 = 0;
     for (int si = 0; si < 2; ++si) {
-      const Item sn = items[sons[si]];
+      const int sid = si == 0 ? it.son0 : it.son1;
+      const Item sn = items[sid];
       const int ks = sn.k;
       const int rs = si == 0 ? r1 : r2;
-      const double* Rt = IB.Rt + (size_t)sons[si] * kSlot;
+      const int row0 = si == 0 ? 0 : r1;
+      const double* Rt = IB.Rt + (size_t)sid * kSlot;
       const double* E = pick(M.transfer, side) + (size_t)sn.cluster * kcap * kcap;   // ks x k
       if (lane < K)
-        for (int p = w; p < rs; p += kTW) {
-          double v = 0.0;
+        for (int p = tm.wp; p < rs; p += NW) {
+          double y = 0.0;
           if (lane < k) {
-            for (int q = 0; q < ks; ++q) v = fma(Rt[p + q * 32], E[q + lane * kcap], v);
+            for (int q = 0; q < ks; ++q) y = fma(Rt[p + q * 32], E[q + lane * kcap], y);
           } else {
-            v = Rt[p + (ks + lane - k) * 32];
+            y = Rt[p + (ks + lane - k) * 32];
           }
-          Vh[row0 + p + lane * LQ] = v;
+          Vh[row0 + p + lane * LQ] = y;
         }
-      row0 += rs;
     }
   }
-  __syncthreads();
+  tm.sync();
   // M = V^ B~^*, column `lane` = V^ * row `lane` of B~, scaled by a power
   // of two (exact) so that max |M| lies in [1/2, 1): the squared sums of
   // the Jacobi test cannot overflow and the float copy keeps its range;
   // singular values are unscaled exactly below.
   const double* Bw = IB.Bw + (size_t)id * kSlot;
-  double a[RW];
+  double a[VW][RW];
   int ex = 0;
   auto form_m = [&]() {
 #pragma unroll
-    for (int h = 0; h < RW; ++h) a[h] = 0.0;
+    for (int v = 0; v < VW; ++v)
+#pragma unroll
+      for (int h = 0; h < RW; ++h) a[v][h] = 0.0;
     if (lane < K)
       for (int q = lane; q < K; ++q) {   // B~ is upper triangular: B~[lane, q] = 0 for q < lane
-        const double b = Bw[lane + q * 32];
+        const double bq = Bw[lane + q * 32];
 #pragma unroll
-        for (int h = 0; h < RW; ++h) {
-          const int i = trow(h, w);
-          if (i < rows) a[h] = fma(Vh[i + q * LQ], b, a[h]);
-        }
+        for (int v = 0; v < VW; ++v)
+#pragma unroll
+          for (int h = 0; h < RW; ++h) {
+            const int i = trow(h, tm.vw(v));
+            if (i < rows) a[v][h] = fma(Vh[i + q * LQ], bq, a[v][h]);
+          }
       }
     double mx = 0.0;
 #pragma unroll
-    for (int h = 0; h < RW; ++h) mx = fmax(mx, fabs(a[h]));
+    for (int v = 0; v < VW; ++v)
+#pragma unroll
+      for (int h = 0; h < RW; ++h) mx = fmax(mx, fabs(a[v][h]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(kFull, mx, o));
-    mx = cs.max1(mx, w, lane);
+    mx = tm.max1(mx);
     ex = 0;
     if (mx > 0.0) frexp(mx, &ex);
 #pragma unroll
-    for (int h = 0; h < RW; ++h) a[h] = ldexp(a[h], -ex);
+    for (int v = 0; v < VW; ++v)
+#pragma unroll
+      for (int h = 0; h < RW; ++h) a[v][h] = ldexp(a[v][h], -ex);
   };
   auto store_rows = [&]() {
     if (lane < K)
 #pragma unroll
-      for (int h = 0; h < RW; ++h) {
-        const int i = trow(h, w);
-        if (i < rows) Qs[i + lane * LQ] = a[h];
-      }
-    __syncthreads();
+      for (int v = 0; v < VW; ++v)
+#pragma unroll
+        for (int h = 0; h < RW; ++h) {
+          const int i = trow(h, tm.vw(v));
+          if (i < rows) Qs[i + lane * LQ] = a[v][h];
+        }
+    tm.sync();
   };
   form_m();
   const double thr = 0.25 * eps * eps;
@@ -1014,27 +1194,27 @@ __global__ void __launch_bounds__(32 * kTW) k_truncate(MatView M, const Item* __
   bool certified = false;
   if (rows >= K && K >= 1) {
     store_rows();
-    gram_cta(Qs, LQ, rows, K, Gs, ldg, w, lane);
+    gram_t(Qs, LQ, rows, K, Gs, ldg, tm);
     double trace = 0.0;
     for (int j = 0; j < K; ++j) trace += Gs[j + j * ldg];
     const double tau = ldexp(thr, -2 * ex);
     const double delta = 4.0 * (double)(rows + K * K) * DBL_EPSILON * trace;
-    if (chol_cta(Gs, K, tau + delta, ldg, w, lane)) {
+    if (chol_t(Gs, K, tau + delta, ldg, tm)) {
       // The certificate's factor L (L L^* = M^* M - (tau + delta) I) is the
       // first Cholesky-QR pass: M L^{-*} deviates from orthonormality only
       // by (tau + delta) |(L L^*)^{-1}|; a polish (or a second full pass)
       // removes the rest.
-      apply_inverse_cta<RW>(Qs, LQ, a, rows, K, Gs, Xs, dinv, ldg, cs, w, lane);
-      certified = polish_cta<RW>(Qs, LQ, a, rows, K, Gs, ldg, w, lane) ||
-                  (cholqr_cta<RW>(Qs, LQ, a, rows, K, Gs, Xs, dinv, ldg, cs, w, lane) &&
-                   polish_cta<RW>(Qs, LQ, a, rows, K, Gs, ldg, w, lane));
+      apply_inverse_t<RW, NW>(Qs, LQ, a, rows, K, Gs, Xs, dinv, ldg, tm);
+      certified = polish_t<RW, NW>(Qs, LQ, a, rows, K, Gs, ldg, tm) ||
+                  (cholqr_t<RW, NW>(Qs, LQ, a, rows, K, Gs, Xs, dinv, ldg, tm) &&
+                   polish_t<RW, NW>(Qs, LQ, a, rows, K, Gs, ldg, tm));
       if (!certified) form_m();   // a factorisation broke down after the certificate
     }
   }
   int r = 0;
   if (certified) {
     r = K;   // Qs holds an orthonormal basis of range(M)
-    if (threadIdx.x == 0 && cnt) {
+    if (tm.lead() && lane == 0 && cnt) {
       cnt[0] = 0;
       cnt[1] = 0;
       cnt[2] = 1;
@@ -1046,41 +1226,55 @@ __global__ void __launch_bounds__(32 * kTW) k_truncate(MatView M, const Item* __
     // of M unchanged and hands the float64 Jacobi nearly orthogonal columns.
     if (K >= 2 && rows > 0) {
       store_rows();
-      float af[RW];
-      float vf[8];
+      float af[VW][RW];
+      float vf[VW][8];
 #pragma unroll
-      for (int h = 0; h < RW; ++h) af[h] = (float)a[h];
+      for (int v = 0; v < VW; ++v) {
 #pragma unroll
-      for (int jj = 0; jj < 8; ++jj) vf[jj] = (4 * jj + w == lane) ? 1.f : 0.f;
-      jacobi32_cta<RW>(af, vf, rows, K, cs, w, lane);
+        for (int h = 0; h < RW; ++h) af[v][h] = (float)a[v][h];
 #pragma unroll
-      for (int jj = 0; jj < 8; ++jj) {
-        const int j = 4 * jj + w;
-        if (j < K && lane < K) Xs[j + lane * ldg] = (double)vf[jj];
+        for (int jj = 0; jj < 8; ++jj) vf[v][jj] = (4 * jj + tm.vw(v) == lane) ? 1.f : 0.f;
       }
-      __syncthreads();
-      orthonormalize_cta(Xs, Gs, K, ldg, w, lane);
+      jacobi32_t<RW, NW>(af, vf, rows, K, tm);
 #pragma unroll
-      for (int h = 0; h < RW; ++h) a[h] = 0.0;
+      for (int v = 0; v < VW; ++v)
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+          const int j = 4 * jj + tm.vw(v);
+          if (j < K && lane < K) Xs[j + lane * ldg] = (double)vf[v][jj];
+        }
+      tm.sync();
+      orthonormalize_t(Xs, Gs, K, ldg, tm);
+#pragma unroll
+      for (int v = 0; v < VW; ++v)
+#pragma unroll
+        for (int h = 0; h < RW; ++h) a[v][h] = 0.0;
       if (lane < K)
         for (int j = 0; j < K; ++j) {
           const double vj = Xs[j + lane * ldg];
 #pragma unroll
-          for (int h = 0; h < RW; ++h) {
-            const int i = trow(h, w);
-            if (i < rows) a[h] = fma(Qs[i + j * LQ], vj, a[h]);
-          }
+          for (int v = 0; v < VW; ++v)
+#pragma unroll
+            for (int h = 0; h < RW; ++h) {
+              const int i = trow(h, tm.vw(v));
+              if (i < rows) a[v][h] = fma(Qs[i + j * LQ], vj, a[v][h]);
+            }
         }
     }
-    jacobi_cta<RW>(a, rows, K, cs, w, lane, w == 0 ? cnt : nullptr, err);
-    if (threadIdx.x == 0 && cnt) cnt[2] = 0;
+    jacobi_t<RW, NW>(a, rows, K, tm, cnt, err);
+    if (tm.lead() && lane == 0 && cnt) cnt[2] = 0;
     // singular values, order, rank
-    double s2c = 0.0;   // squared norm of this lane's scaled column
-    if (lane < K)
+    double s2p[VW];   // this lane's scaled column: squared norm per virtual warp
 #pragma unroll
-      for (int h = 0; h < RW; ++h)
-        if (trow(h, w) < rows) s2c = fma(a[h], a[h], s2c);
-    s2c = cs.sum1(s2c, w, lane);
+    for (int v = 0; v < VW; ++v) {
+      double x = 0.0;
+      if (lane < K)
+#pragma unroll
+        for (int h = 0; h < RW; ++h)
+          if (trow(h, tm.vw(v)) < rows) x = fma(a[v][h], a[v][h], x);
+      s2p[v] = x;
+    }
+    const double s2c = tm.sum1(s2p);
     const double s2 = lane < K ? ldexp(s2c, 2 * ex) : -1.0;   // unscaled
     int pos = 0;
     for (int d = 0; d < 32; ++d) {
@@ -1099,46 +1293,48 @@ __global__ void __launch_bounds__(32 * kTW) k_truncate(MatView M, const Item* __
     if (keep) {
       const double inv = 1.0 / sqrt(s2c);
 #pragma unroll
-      for (int h = 0; h < RW; ++h) {
-        const int i = trow(h, w);
-        if (i < rows) Qs[i + pos * LQ] = a[h] * inv;
-      }
+      for (int v = 0; v < VW; ++v)
+#pragma unroll
+        for (int h = 0; h < RW; ++h) {
+          const int i = trow(h, tm.vw(v));
+          if (i < rows) Qs[i + pos * LQ] = a[v][h] * inv;
+        }
     }
-    __syncthreads();
+    tm.sync();
   }
-  // R_t = Q^* V^ (r x K): warp w forms the rows p = w, w + 4, ...
+  // R_t = Q^* V^ (r x K): the warps split the rows p
   double* Rt = IB.Rt + (size_t)id * kSlot;
   if (lane < K)
-    for (int p = w; p < 32; p += kTW) {
-      double v = 0.0;
+    for (int p = tm.wp; p < 32; p += NW) {
+      double y = 0.0;
       if (p < r)
-        for (int i = 0; i < rows; ++i) v = fma(Qs[i + p * LQ], Vh[i + lane * LQ], v);
-      Rt[p + lane * 32] = v;
+        for (int i = 0; i < rows; ++i) y = fma(Qs[i + p * LQ], Vh[i + lane * LQ], y);
+      Rt[p + lane * 32] = y;
     }
-  if (threadIdx.x == 0) IB.rank[id] = r;
+  if (tm.lead() && lane == 0) IB.rank[id] = r;
   // outputs: leaf basis or the sons' transfer matrices
   if (it.flags & kItemLeaf) {
     double* Q = IB.Q + it.qoff;
     if (lane < r)
-      for (int i = w; i < rows; i += kTW) Q[i + (size_t)lane * rows] = Qs[i + lane * LQ];
+      for (int i = tm.wp; i < rows; i += NW) Q[i + (size_t)lane * rows] = Qs[i + lane * LQ];
   } else {
     double* F1 = IB.F + (size_t)it.son0 * kSlot;
     double* F2 = IB.F + (size_t)it.son1 * kSlot;
     if (lane < r) {
-      for (int p = w; p < r1; p += kTW) F1[p + lane * 32] = Qs[p + lane * LQ];
-      for (int p = w; p < r2; p += kTW) F2[p + lane * 32] = Qs[r1 + p + lane * LQ];
+      for (int p = tm.wp; p < r1; p += NW) F1[p + lane * 32] = Qs[p + lane * LQ];
+      for (int p = tm.wp; p < r2; p += NW) F2[p + lane * 32] = Qs[r1 + p + lane * LQ];
     }
   }
   if ((it.flags & kItemRoot) && !(it.flags & kItemTreeRoot)) {
     // E_t0 <- R_t0 [E_t0; 0]  (r x kf)
-    __syncthreads();   // R_t of every warp is written
+    tm.sync();   // R_t of every warp is written
     const double* E = pick(M.transfer, side) + (size_t)it.cluster * kcap * kcap;   // k x kf
     double* Fo = IB.F + (size_t)id * kSlot;
     if (lane < it.kf)
-      for (int p = w; p < r; p += kTW) {
-        double v = 0.0;
-        for (int q = 0; q < k; ++q) v = fma(Rt[p + q * 32], E[q + lane * kcap], v);
-        Fo[p + lane * 32] = v;
+      for (int p = tm.wp; p < r; p += NW) {
+        double y = 0.0;
+        for (int q = 0; q < k; ++q) y = fma(Rt[p + q * 32], E[q + lane * kcap], y);
+        Fo[p + lane * 32] = y;
       }
   }
 }
@@ -1383,9 +1579,35 @@ __global__ void k_near_add(const NearDesc* __restrict__ d, int n, int u) {
 
 // ------------------------------------------------------------ launchers
 static constexpr int kWarps = 4;
-static constexpr size_t kFoldSmem = (size_t)kWarps * (32 * kLdr + kCh + 1) * sizeof(double);
 
 static int blocks_for(int n) { return (n + kWarps - 1) / kWarps; }
+
+static int sm_count() {
+  static int cached[64] = {};
+  int dev = 0;
+  H2_CUDA(cudaGetDevice(&dev));
+  if (dev >= 0 && dev < 64 && cached[dev]) return cached[dev];
+  int sms = 0;
+  H2_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (dev >= 0 && dev < 64) cached[dev] = sms;
+  return sms;
+}
+
+// Four-warp teams while a launch holds at most kTW tasks per SM (every
+// task then has the float64 units of a whole SM, or a quarter at least);
+// one warp per task beyond, where the tasks fill the SMs anyway.  Both
+// forms compute the same bits.
+static bool wide_teams(int n) { return n <= kTW * sm_count(); }
+
+// Launch a fold kernel (template over the team width) for n tasks.
+#define H2_LAUNCH_FOLD(kern, n, stream, ...)                                                              \
+  do {                                                                                                   \
+    if (wide_teams(n))                                                                                   \
+      kern<kTW><<<(n), 32 * kTW, fold_doubles(kTW) * sizeof(double), (stream)>>>(__VA_ARGS__);           \
+    else                                                                                                 \
+      kern<1><<<blocks_for(n), 32 * kWarps, kWarps * fold_doubles(1) * sizeof(double), (stream)>>>(      \
+          __VA_ARGS__);                                                                                  \
+  } while (0)
 
 // Blocks of a persistent launch: as many as stay resident on the device at
 // once (at most `need`).
@@ -1403,11 +1625,19 @@ template <int MR>
 static void launch_truncate_mr(const MatView& M, const Item* items, const int32_t* list, int n, int u, int kl,
                                double eps, const double* A, const double* B, const ItemBuffers& IB, int* err,
                                cudaStream_t st) {
-  // one block of kTW warps per task
-  const size_t sm = trunc_smem_doubles(MR, kl) * sizeof(double);
-  static std::atomic<unsigned long long> attr{0};
-  smem_limit(k_truncate<MR>, trunc_smem_doubles(MR, kMaxCols) * sizeof(double), attr);
-  k_truncate<MR><<<n, 32 * kTW, sm, st>>>(M, items, list, n, u, kl, eps, A, B, IB, err);
+  static std::atomic<unsigned long long> attr4{0}, attr1{0};
+  if (wide_teams(n)) {
+    // one block of kTW warps per task
+    smem_limit(k_truncate<MR, kTW>, trunc_doubles(MR, kMaxCols, kTW) * sizeof(double), attr4);
+    k_truncate<MR, kTW><<<n, 32 * kTW, trunc_doubles(MR, kl, kTW) * sizeof(double), st>>>(M, items, list, n, u,
+                                                                                           kl, eps, A, B, IB, err);
+  } else {
+    // one warp per task, two tasks per block
+    constexpr int warps = 2;
+    smem_limit(k_truncate<MR, 1>, warps * trunc_doubles(MR, kMaxCols, 1) * sizeof(double), attr1);
+    k_truncate<MR, 1><<<(n + warps - 1) / warps, 32 * warps, warps * trunc_doubles(MR, kl, 1) * sizeof(double),
+                        st>>>(M, items, list, n, u, kl, eps, A, B, IB, err);
+  }
 }
 
 static void launch_truncate(const MatView& M, const Item* items, const int32_t* list, int n, int u, int kl,
@@ -1532,21 +1762,20 @@ void run_pipeline(const Pipeline& P) {
   start(H2_PHASE_EXACT, st);
   fork();
   if (ncl > 0) {
-    k_blockweights<<<blocks_for(ncl), 32 * kWarps, kFoldSmem, bs>>>(P.M, P.cl_list, ncl, P.BL, P.BW, P.err);
+    H2_LAUNCH_FOLD(k_blockweights, ncl, bs, P.M, P.cl_list, ncl, P.BL, P.BW, P.err);
     ++pl[H2_PHASE_EXACT];
   }
   for (int l = 0; l < L; ++l) {
     const int n = P.cl_ptr[l + 1] - P.cl_ptr[l];
     if (!n) continue;
-    k_baseweights<<<blocks_for(n), 32 * kWarps, kFoldSmem, bs>>>(P.M, P.cl_list + P.cl_ptr[l], n, P.BW, P.err);
+    H2_LAUNCH_FOLD(k_baseweights, n, bs, P.M, P.cl_list + P.cl_ptr[l], n, P.BW, P.err);
     ++pl[H2_PHASE_EXACT];
   }
   if (P.side) H2_CUDA(cudaEventRecord(P.join, P.side));
   for (int l = L - 1; l >= 0; --l) {
     const int n = P.lvl_ptr[l + 1] - P.lvl_ptr[l];
     if (!n) continue;
-    k_rfactor<<<blocks_for(n), 32 * kWarps, kFoldSmem, st>>>(P.M, P.items, P.lvl_list + P.lvl_ptr[l], n, P.u,
-                                                              P.A, P.B, P.IB, P.err);
+    H2_LAUNCH_FOLD(k_rfactor, n, st, P.M, P.items, P.lvl_list + P.lvl_ptr[l], n, P.u, P.A, P.B, P.IB, P.err);
     ++pl[H2_PHASE_EXACT];
   }
   if (P.n_norms > 0) {
@@ -1554,15 +1783,14 @@ void run_pipeline(const Pipeline& P) {
     ++pl[H2_PHASE_EXACT];
   }
   if (ni > 0) {
-    k_outside<<<blocks_for(ni), 32 * kWarps, kFoldSmem, st>>>(P.M, P.items, P.ents, P.lvl_list, ni, P.u, P.IB);
+    H2_LAUNCH_FOLD(k_outside, ni, st, P.M, P.items, P.ents, P.lvl_list, ni, P.u, P.IB);
     ++pl[H2_PHASE_EXACT];
   }
   if (P.side) H2_CUDA(cudaStreamWaitEvent(st, P.join, 0));
   for (int l = 0; l < L; ++l) {
     const int n = P.lvl_ptr[l + 1] - P.lvl_ptr[l];
     if (!n) continue;
-    k_weights<<<blocks_for(n), 32 * kWarps, kFoldSmem, st>>>(P.M, P.items, P.ents, P.lvl_list + P.lvl_ptr[l], n,
-                                                              P.u, P.BW, P.IB, P.err);
+    H2_LAUNCH_FOLD(k_weights, n, st, P.M, P.items, P.ents, P.lvl_list + P.lvl_ptr[l], n, P.u, P.BW, P.IB, P.err);
     ++pl[H2_PHASE_EXACT];
   }
   for (int l = L - 1; l >= 0; --l) {

@@ -177,3 +177,13 @@ def test_power_error_matches_oracle(ctx, config0):
     got = b.h2_lr_error(ctx, Za, Z, vd.data_ptr(), 20)
     assert abs(got - want) <= 1e-6 * max(want, 1e-12) + 1e-14, (got, want)
     assert want < 1e-2
+
+
+def test_command_line_example():
+    """python -m paper_1402_5056_gb300.fem_lr: factor, PCG and error on a
+    small problem."""
+    from paper_1402_5056_gb300 import fem_lr
+    out = fem_lr.main(["--cells", "24", "--eps", "1e-4"])
+    assert out["n"] == 23 * 23
+    assert out["cg_relres"] <= 1e-10 and out["cg_iterations"] <= 6
+    assert out["factor"]["updates"] > 0 and 0 < out["err_power"] < 1e-2

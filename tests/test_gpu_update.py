@@ -323,13 +323,20 @@ def test_full_batch_properties(ctx, full):
         b.h2_batch_free(P)
 
 
-def test_update_independent_of_its_batch(ctx, full):
+@pytest.mark.parametrize("mode", ["auto", "exact"])
+def test_update_independent_of_its_batch(ctx, full, mode):
     """An update computes the same bits whether it runs inside the 4096-update
-    batch (upper levels on k_fweights_wide, the others on k_fweights) or alone
-    (every level on k_fweights_wide): the Gram matrices of steps 2 and 3, the
-    certificate's R_t, the ranks, and the committed couplings."""
+    batch or alone: the Gram matrices of steps 2 and 3, R_t of step 4, the
+    ranks, and the committed couplings and bases.  Certified path: the upper
+    levels of the batch run on k_fweights_wide, the others on k_fweights,
+    the update alone on k_fweights_wide throughout.  Exact path: the levels
+    of the batch with many cluster tasks run one warp per task, the update
+    alone runs a block of four warps per task."""
     Zo, Zl, blocks, A, B = full
+    exact = mode == "exact"
     P = b.h2_batch_create(ctx, Zl, blocks, FULL_U)
+    if exact:
+        b.h2_batch_set_mode(P, b.MODE_EXACT)
     try:
         Acat, Bcat = concat_factors(P, A, B, FULL_U)
         dA = torch.from_numpy(Acat).cuda()
@@ -343,6 +350,8 @@ def test_update_independent_of_its_batch(ctx, full):
         for j in big + [int(x) for x in rng.choice(len(blocks), 2, replace=False)]:
             first, last = b.h2_batch_update_items(P, j)
             Q = b.h2_batch_create(ctx, Zl, [blocks[j]], FULL_U)
+            if exact:
+                b.h2_batch_set_mode(Q, b.MODE_EXACT)
             try:
                 a1, b1 = concat_factors(Q, [A[j]], [B[j]], FULL_U)
                 qa = torch.from_numpy(a1).cuda()
