@@ -44,6 +44,13 @@ Readings of what the paper leaves open (also listed in the design notes):
    u_max columns (u_max = 32 minus the largest rank among the clusters of
    both subtrees, at least 1), each group one local update; with
    u_max = None the update is applied whole.
+6. The approximate inverse (Remark on inversion) is built in a second H^2
+   matrix C with the same trees, starting from zero (every rank 0); the
+   blocks B12 = A11^-1 A12 and B21 = A21 A11^-1 go to a third zero matrix
+   T, the Schur complement S = A22 - A21 B12 overwrites A22 (A is consumed),
+   and the six products run in the order of the Remark, each one product
+   of Section 3.  A leaf is inverted by Doolittle's LU and two triangular
+   solves with the identity.
 """
 from __future__ import annotations
 
@@ -437,3 +444,62 @@ def mul(Z, X, Y, alpha: float, x: int, y: int, z: int, eps: float, cap=32):
     _mul(C, alpha, x, y, z, X, Y)
     return C.updates
 
+
+
+# ------------------------------------------- inversion (Remark on inversion)
+def zero_like(Z):
+    """An H^2 matrix with Z's trees and every rank, coupling and nearfield
+    entry zero (reading 6)."""
+    from .h2 import ClusterBasis, H2Matrix
+    V, W = ClusterBasis(Z.V.tree), ClusterBasis(Z.W.tree)
+    for cb in (V, W):
+        tr = cb.tree
+        for t in range(tr.n_clusters):
+            if tr.is_leaf(t):
+                cb.leaf[t] = np.zeros((tr.size[t], 0))
+            if t > 0:
+                cb.transfer[t] = np.zeros((0, 0))
+    out = H2Matrix(Z.blocks, V, W)
+    bt = Z.blocks
+    out.S = {b: np.zeros((0, 0)) for b in bt.admissible}
+    out.N = {b: np.zeros((Z.V.tree.size[bt.row[b]], Z.W.tree.size[bt.col[b]])) for b in bt.inadmissible}
+    return out
+
+
+def leaf_inverse(M: np.ndarray) -> np.ndarray:
+    """M^-1 of a dense diagonal leaf: Doolittle's LU, then R^-1 L^-1 I."""
+    F = lu_doolittle(M)
+    n = F.shape[0]
+    Y = solve_triangular(F, np.eye(n), lower=True, unit_diagonal=True)
+    return solve_triangular(F, Y, lower=False)
+
+
+def _inv(C: _Ctx, A, Cm, T, d):
+    """Cm|_d <- (A|_d)^-1 for a diagonal block d (Remark on inversion)."""
+    bt = A.blocks
+    if bt.kind[d] == BlockTree.NEAR:
+        Cm.N[d] = leaf_inverse(A.N[d])
+        return
+    t = bt.row[d]
+    t1, t2 = A.V.tree.sons[t]
+    d11, d12 = _son(bt, d, t1, t1), _son(bt, d, t1, t2)
+    d21, d22 = _son(bt, d, t2, t1), _son(bt, d, t2, t2)
+    _inv(C, A, Cm, T, d11)                                    # C11 = A11^-1
+    C.updates += mul(T, Cm, A, 1.0, d11, d12, d12, C.eps, C.cap)    # B12 = A11^-1 A12
+    C.updates += mul(T, A, Cm, 1.0, d21, d11, d21, C.eps, C.cap)    # B21 = A21 A11^-1
+    C.updates += mul(A, A, T, -1.0, d21, d12, d22, C.eps, C.cap)    # S = A22 - A21 B12
+    _inv(C, A, Cm, T, d22)                                    # C22 = S^-1
+    C.updates += mul(Cm, T, Cm, -1.0, d12, d22, d12, C.eps, C.cap)  # C12 = -B12 C22
+    C.updates += mul(Cm, Cm, T, -1.0, d22, d21, d21, C.eps, C.cap)  # C21 = -C22 B21
+    C.updates += mul(Cm, Cm, T, -1.0, d12, d21, d11, C.eps, C.cap)  # C11 = C11 - C12 B21
+
+
+def inverse(A, eps: float, cap=32):
+    """The approximate inverse of the square H^2 matrix A (Remark on
+    inversion, reading 6) as a new H^2 matrix with A's trees; A is consumed
+    (its lower right blocks hold Schur complements on return).  Returns the
+    inverse and statistics."""
+    Cm, T = zero_like(A), zero_like(A)
+    C = _Ctx(A, eps, cap)
+    _inv(C, A, Cm, T, 0)
+    return Cm, {"updates": C.updates}
