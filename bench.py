@@ -356,6 +356,57 @@ def lr_measure(b, ctx, cells_list, reps: int, oracle_cells):
     return out
 
 
+def inverse_measure(b, ctx, cells_list, oracle_cells):
+    """Approximate inverse of the 2D FEM matrix (h2_inverse, block Gauss
+    elimination): setup wall time, CG steps to 1e-10 preconditioned by the
+    inverse, ||I - C A||_2 estimated by the power iteration; the oracle's
+    inverse timed beside it for the sizes in oracle_cells."""
+    import torch
+    out = {}
+    for cells in cells_list:
+        M, seed = lr_problem(cells)
+        st = synth.streams(seed)
+        sigma = synth.checker_sigma(st["sigma"], M, 2)
+        opt = b.options(eps=LR_EPS, eta=2.0, leaf_size=32)
+        A = b.h2_build_fem(ctx, 2, cells, M, sigma, opt)
+        W = b.h2_build_fem(ctx, 2, cells, M, sigma, opt)   # consumed by the inversion
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Cm, info = b.h2_inverse(ctx, W, opt)
+        torch.cuda.synchronize()
+        setup = time.perf_counter() - t0
+        b.h2_matrix_free(W)
+        n = (cells - 1) ** 2
+        perm = b.h2_tree_permutation(A)
+        rhs = synth.fem_rhs(st["rhs"], n)[:, 0][perm]
+        bd = torch.from_numpy(np.ascontiguousarray(rhs)).cuda()
+        xd = torch.zeros(n, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        it, rr = b.h2_pcg_inverse(ctx, A, Cm, bd.data_ptr(), xd.data_ptr(), 1e-10, 100)
+        torch.cuda.synchronize()
+        cg_s = time.perf_counter() - t0
+        rec = {"n": n, "cells": cells, "checker": M, "eps": LR_EPS, "leaf": 32, "eta": 2.0, "setup_s": setup,
+               "updates": info["updates"], "products": info["products"], "max_rank": info["max_rank"],
+               "cg_iterations": it, "cg_relres": rr, "cg_s": cg_s}
+        if cells in oracle_cells:
+            from oracle.fem import h2_from_sparse, stiffness
+            from oracle.lr import inverse, pcg
+            K, pts = stiffness(cells, 2, sigma, M)
+            Zo = h2_from_sparse(K, pts, 32, 2.0, 1.0 / cells)
+            t0 = time.perf_counter()
+            Co, _ = inverse(Zo, LR_EPS)
+            t1 = time.perf_counter()
+            D = Co.dense()
+            Kp = K[Zo.V.tree.perm][:, Zo.V.tree.perm].tocsr()
+            _, it_o = pcg(lambda v: Kp @ v, rhs, lambda r: D @ r, 1e-10)
+            rec["oracle"] = {"setup_s": t1 - t0, "cg_iterations": it_o, "cores": 1, "kind": "oracle"}
+        out["%dx%d" % (cells, cells)] = rec
+        b.h2_matrix_free(Cm)
+        b.h2_matrix_free(A)
+    return out
+
+
 def run_reference(args, rank):
     if rank != 0:
         return 0
@@ -408,6 +459,8 @@ def main():
     ap.add_argument("--lr-cells", default="32",
                     help="comma-separated cells per side of the 2D FEM H2-LR problems to time ('' for none)")
     ap.add_argument("--lr-reps", type=int, default=3)
+    ap.add_argument("--inv-cells", default="32",
+                    help="comma-separated cells per side of the 2D FEM approximate inverses to time ('' for none)")
     ap.add_argument("--cpu-procs", type=int, default=0, help="host processes of the CPU baseline (0: all cores)")
     ap.add_argument("--count", type=int, default=WORK["count"],
                     help="updates per batch (profiling runs use fewer; the benchmark uses 4096)")
@@ -616,6 +669,10 @@ def main():
     cells_list = [int(x) for x in args.lr_cells.split(",") if x.strip()]
     if rank == 0 and world == 1 and cells_list:
         lr = lr_measure(b, ctx, cells_list, args.lr_reps, oracle_cells={32})
+    inv = None
+    inv_cells = [int(x) for x in args.inv_cells.split(",") if x.strip()]
+    if rank == 0 and world == 1 and inv_cells:
+        inv = inverse_measure(b, ctx, inv_cells, oracle_cells={32})
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -644,7 +701,7 @@ def main():
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "e2e_compact": e2e_compact,
             "gpu_launches": stats["launches"] * args.steps,
             "clocks": clocks, "phases": phases, "phases_serial": phases_serial, "exact_mode": exact_mode,
-            "matvec": mv, "lr": lr,
+            "matvec": mv, "lr": lr, "inverse": inv,
             "gflop_per_step": stats["flops"] / 1e9}
     if rank == 0:
         print(json.dumps(line))

@@ -460,6 +460,26 @@ h2_status h2_pcg(h2_ctx* ctx, const h2_matrix* A, const h2_matrix* LR, const dou
  * last ||w||.  Synchronizes. */
 h2_status h2_lr_error(h2_ctx* ctx, const h2_matrix* A, const h2_matrix* LR, double* v, int iters, double* err);
 
+/* Approximate inverse by block Gauss elimination (Section 3, Remark on
+ * inversion).  For a diagonal block with sons t1, t2: C11 = A11^-1
+ * (recursively), B12 = C11 A12, B21 = A21 C11, S = A22 - A21 B12,
+ * C22 = S^-1 (recursively), C12 = -B12 C22, C21 = -C22 B21,
+ * C11 <- C11 - C12 B21; a leaf is inverted by LU without pivoting and two
+ * triangular solves with the identity.  Every product is the product of
+ * Section 3 (as h2_mul, accuracy opt->eps) into a matrix that starts at
+ * zero.  *out receives a new H^2 matrix with A's trees (free it with
+ * h2_matrix_free).  A is consumed: its blocks below and right of the first
+ * son hold Schur complements on return (clone A to keep it).  stats (host,
+ * 3 entries, or NULL): local updates, product terms, largest rank of the
+ * inverse.  Synchronizes.  H2_EINVAL if A is not square with one tree; on
+ * any failure *out is NULL and A may have changed. */
+h2_status h2_inverse(h2_ctx* ctx, h2_matrix* A, const h2_options* opt, h2_matrix** out, int64_t* stats);
+
+/* h2_pcg with the approximate inverse C from h2_inverse as the
+ * preconditioner (z = C r by h2_matvec); same arguments and results. */
+h2_status h2_pcg_inverse(h2_ctx* ctx, const h2_matrix* A, const h2_matrix* C, const double* b, double* x, double tol,
+                         int maxit, int* iterations, double* relres);
+
 /* ----------------------------------------------------------- diagnostics */
 
 /* The float64 reciprocal the factorisation kernels use for their pivots

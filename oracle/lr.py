@@ -42,8 +42,8 @@ Readings of what the paper leaves open (also listed in the design notes):
    V_t (R^-* W_s S^*)^*.
 5. An update of rank u is applied in consecutive column groups of at most
    u_max columns (u_max = 32 minus the largest rank among the clusters of
-   both subtrees, at least 1), each group one local update; with
-   u_max = None the update is applied whole.
+   both subtrees, at least 1 and at most 31), each group one local update;
+   with u_max = None the update is applied whole.
 6. The approximate inverse (Remark on inversion) is built in a second H^2
    matrix C with the same trees, starting from zero (every rank 0); the
    blocks B12 = A11^-1 A12 and B21 = A21 A11^-1 go to a third zero matrix
@@ -110,7 +110,7 @@ def _apply_update(C: _Ctx, b: int, A: np.ndarray, B: np.ndarray):
                 kmax = max(kmax, Z.V.rank[t])
             for s in Z.W.tree.descendants(bt.col[b]):
                 kmax = max(kmax, Z.W.rank[s])
-            w = max(1, C.cap - kmax)
+            w = max(1, min(C.cap - 1, C.cap - kmax))
         w = min(w, u - j)
         d = local_update(Z, b, A[:, j:j + w], B[:, j:j + w], C.eps)
         Z2 = apply_delta(Z, d)

@@ -34,7 +34,8 @@ EXPORTS = [
     "h2_batch_update_items", "h2_batch_set_mode", "h2_batch_paths", "h2_lowrank_update",
     "h2_lowrank_update_noalloc", "h2_lowrank_update_sequence", "h2_matvec", "h2_block_to_dense",
     "h2_sequence_waves", "h2_check_reciprocal", "h2_debug_fail_allocation",
-    "h2_build_fem", "h2_lr_factor", "h2_lr_solve", "h2_pcg", "h2_lr_error", "h2_mul",
+    "h2_build_fem", "h2_lr_factor", "h2_lr_solve", "h2_pcg", "h2_lr_error", "h2_mul", "h2_inverse",
+    "h2_pcg_inverse",
 ]
 
 PHASES = ("base_weights", "rfactor", "norms", "weights", "truncate", "reproject", "exact", "bases")
@@ -118,6 +119,8 @@ _sig("h2_lr_factor", _int, _p, _p, C.POINTER(Options), _p)
 _sig("h2_lr_solve", _int, _p, _p, _i64, _p, _i64)
 _sig("h2_pcg", _int, _p, _p, _p, _p, _p, _dbl, _int, _p, _p)
 _sig("h2_lr_error", _int, _p, _p, _p, _p, _int, _p)
+_sig("h2_inverse", _int, _p, _p, _p, _p, _p)
+_sig("h2_pcg_inverse", _int, _p, _p, _p, _p, _p, _dbl, _int, _p, _p)
 _sig("h2_mul", _int, _p, _dbl, _p, _i64, _p, _i64, _p, _i64, _dbl, _p)
 _sig("h2_matvec", _int, _p, _p, _i64, _dbl, _p, _i64, _dbl, _p, _i64)
 _sig("h2_lowrank_update_sequence", _int, _p, _p, _i64, _p, _int, _p, _p, _dbl, _p)
@@ -540,6 +543,23 @@ def h2_lr_error(ctx, A, LR, v_dev: int, iters: int):
     err = C.c_double(0.0)
     _check(_lib.h2_lr_error(ctx, A, LR, C.c_void_p(v_dev), int(iters), C.byref(err)), ctx)
     return err.value
+
+
+def h2_inverse(ctx, A, opt):
+    """Approximate inverse of A (block Gauss elimination); A is consumed.
+    Returns (C, stats) with C a new matrix handle."""
+    out = C.c_void_p()
+    st = np.zeros(3, np.int64)
+    _check(_lib.h2_inverse(ctx, A, C.byref(opt), C.byref(out), _ptr(st)), ctx)
+    return out.value, {"updates": int(st[0]), "products": int(st[1]), "max_rank": int(st[2])}
+
+
+def h2_pcg_inverse(ctx, A, Cinv, b_dev: int, x_dev: int, tol: float, maxit: int):
+    it = C.c_int()
+    rr = C.c_double()
+    _check(_lib.h2_pcg_inverse(ctx, A, Cinv, C.c_void_p(b_dev), C.c_void_p(x_dev), float(tol), int(maxit),
+                               C.byref(it), C.byref(rr)), ctx)
+    return it.value, rr.value
 
 
 def h2_mul(ctx, alpha: float, X, bx: int, Y, by: int, Z, bz: int, eps: float) -> int:

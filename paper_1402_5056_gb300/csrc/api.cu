@@ -2240,6 +2240,29 @@ static void put(T* dst, const std::vector<T>& v, cudaStream_t st) {
 }
 
 
+void zero_matrix(h2_ctx* ctx, h2_matrix* Z) {
+  H2_REQUIRE(has_storage(Z), "zero_matrix: matrix has no device storage");
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = ctx->stream;
+  for (int sd = 0; sd < 2; ++sd) {
+    const ClusterTree& ct = tree_of(Z, sd);
+    DeviceBasis& b = basis_of(Z, sd);
+    int64_t tot = 0;
+    for (int32_t c = 0; c < ct.count(); ++c)
+      if (ct.leaf(c)) tot += ct.size[c] * Z->kcap;
+    if (tot) H2_CUDA(cudaMemsetAsync(b.d_leaf, 0, tot * sizeof(double), st));
+    H2_CUDA(cudaMemsetAsync(b.d_transfer, 0, (size_t)ct.count() * Z->kcap * Z->kcap * sizeof(double), st));
+    b.rank.assign(ct.count(), 0);
+    sync_ranks(b, st);
+  }
+  const size_t nadm = Z->blocks.adm.size();
+  if (nadm) H2_CUDA(cudaMemsetAsync(Z->d_S, 0, nadm * Z->kcap * Z->kcap * sizeof(double), st));
+  if (Z->near_len) H2_CUDA(cudaMemsetAsync(Z->d_N, 0, Z->near_len * sizeof(double), st));
+  // the host ranks are the source of the device copy: keep them alive until
+  // the copy ran
+  H2_CUDA(cudaStreamSynchronize(st));
+}
+
 UpdateEngine* engine_new() { return new UpdateEngine(); }
 
 void engine_delete(UpdateEngine* E) {

@@ -96,6 +96,10 @@ struct DeviceBasis {
   int64_t* d_leaf_off = nullptr;
 };
 
+// Z <- the zero matrix on Z's trees: every rank 0, couplings, nearfield
+// and basis storage zero (asynchronous on the context's stream).
+void zero_matrix(h2_ctx* ctx, h2_matrix* Z);
+
 // Reusable engine of in-place single updates (api.cu): persistent device
 // buffers, the exact path, base weights only for the clusters an update
 // reads.  Not thread-safe; one per driver.

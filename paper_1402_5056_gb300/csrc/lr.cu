@@ -30,8 +30,8 @@
 //     likewise with V_t (R^-* W_s S^*)^*;
 //  5. an update of rank u is applied in consecutive column groups of at
 //     most 32 - (largest rank among the clusters of both subtrees) columns
-//     (at least 1), each group one local update (the update kernels hold
-//     k_t + u <= 32 columns).
+//     (at least 1, at most 31), each group one local update (the update
+//     kernels hold k_t + u <= 32 columns and u <= 31).
 #include <algorithm>
 #include <array>
 #include <chrono>
@@ -420,7 +420,7 @@ void apply_update(Lr& L, int32_t b, const double* A, int64_t lda, const double* 
     const int32_t t = bt.row[b], s = bt.col[b];
     for (int32_t c = t; c < t + Z->rows.subtree[t]; ++c) kmax = std::max(kmax, Z->V.rank[c]);
     for (int32_t c = s; c < s + Z->cols.subtree[s]; ++c) kmax = std::max(kmax, Z->W.rank[c]);
-    const int w = std::min(std::max(1, kMaxCols - kmax), u - j);
+    const int w = std::min(std::min(kMaxCols - 1, std::max(1, kMaxCols - kmax)), u - j);
     if (!L.eng) L.eng = engine_new();
     engine_update(L.ctx, Z, L.eng, b, w, A + (size_t)j * lda, lda, B + (size_t)j * ldb, ldb, L.eps);
     ++L.updates;
@@ -846,6 +846,54 @@ void lr(Lr& L, int32_t d) {
   lr(L, d22);
 }
 
+// ---------------------------------------------- inversion (Remark on inversion)
+// C|_d <- (A|_d)^-1 for a diagonal block d: a leaf by Doolittle's LU and two
+// triangular solves with the identity; otherwise block Gauss elimination
+// with the six products of the Remark, B12 = A11^-1 A12 and B21 = A21 A11^-1
+// in T, the Schur complement S = A22 - A21 B12 in place of A22 (A is
+// consumed).  C and T start as zero matrices on A's trees.
+void product(Lr& L, h2_matrix* Z, const h2_matrix* X, const h2_matrix* Y, double alpha, int32_t x, int32_t y,
+             int32_t z) {
+  L.Z = Z;
+  L.X = X == Z ? nullptr : X;
+  L.Y = Y == Z ? nullptr : Y;
+  mul(L, alpha, x, y, z);
+}
+
+void leaf_inverse(Lr& L, const h2_matrix* A, h2_matrix* C, int32_t d) {
+  Timer tm(L.t_lu);
+  const int64_t m = csize(A, A->blocks.row[d]);
+  DArr F(m * m, L.st);
+  H2_CUDA(cudaMemcpyAsync(F.p, near_ptr(A, d), m * m * sizeof(double), cudaMemcpyDeviceToDevice, L.st));
+  launch_leaf_lu(F.p, (int)m, m, L.ctx->d_error, L.st);
+  double* X = near_ptr(C, d);
+  launch_eye(X, (int)m, m, L.st);
+  launch_trsm(0, F.p, (int)m, m, X, (int)m, m, L.st);   // L^-1
+  launch_trsm(1, F.p, (int)m, m, X, (int)m, m, L.st);   // R^-1 L^-1
+  H2_CUDA(cudaGetLastError());
+}
+
+void inv(Lr& L, h2_matrix* A, h2_matrix* C, h2_matrix* T, int32_t d) {
+  const BlockTree& bt = A->blocks;
+  if (bt.kind[d] == kNear) {
+    leaf_inverse(L, A, C, d);
+    return;
+  }
+  const ClusterTree& ct = A->rows;
+  const int32_t t = bt.row[d];
+  const int32_t t1 = ct.son0[t], t2 = ct.son1[t];
+  const int32_t d11 = son(bt, d, t1, t1), d12 = son(bt, d, t1, t2);
+  const int32_t d21 = son(bt, d, t2, t1), d22 = son(bt, d, t2, t2);
+  inv(L, A, C, T, d11);                          // C11 = A11^-1
+  product(L, T, C, A, 1.0, d11, d12, d12);       // B12 = A11^-1 A12
+  product(L, T, A, C, 1.0, d21, d11, d21);       // B21 = A21 A11^-1
+  product(L, A, A, T, -1.0, d21, d12, d22);      // S = A22 - A21 B12
+  inv(L, A, C, T, d22);                          // C22 = S^-1
+  product(L, C, T, C, -1.0, d12, d22, d12);      // C12 = -B12 C22
+  product(L, C, C, T, -1.0, d22, d21, d21);      // C21 = -C22 B21
+  product(L, C, C, T, -1.0, d12, d21, d11);      // C11 = C11 - C12 B21
+}
+
 void check_square(const h2_matrix* Z) {
   H2_REQUIRE(Z->rows.off == Z->cols.off && Z->rows.son0 == Z->cols.son0, "the matrix must be square with one tree");
   H2_REQUIRE(Z->blocks.kind[0] != kAdm, "the root block must not be admissible");
@@ -1111,6 +1159,49 @@ extern "C" h2_status h2_lr_factor(h2_ctx* ctx, h2_matrix* Z, const h2_options* o
   });
 }
 
+extern "C" h2_status h2_inverse(h2_ctx* ctx, h2_matrix* A, const h2_options* opt, h2_matrix** out,
+                                int64_t* stats) {
+  if (!ctx || !A || !opt || !out) return H2_EINVAL;
+  *out = nullptr;
+  h2_matrix* C = nullptr;
+  h2_matrix* T = nullptr;
+  h2_status st = lr_guard(ctx, [&] {
+    check_options(opt);
+    check_square(A);
+    DevGuard g(ctx->device);
+    h2_status s = h2_matrix_clone(ctx, A, &C);
+    if (s != H2_OK) throw Error(s, ctx->last_error);
+    s = h2_matrix_clone(ctx, A, &T);
+    if (s != H2_OK) throw Error(s, ctx->last_error);
+    zero_matrix(ctx, C);
+    zero_matrix(ctx, T);
+    Lr L;
+    L.ctx = ctx;
+    L.Z = A;
+    L.eps = opt->eps;
+    L.st = ctx->stream;
+    inv(L, A, C, T, 0);
+    H2_CUDA(cudaStreamSynchronize(L.st));
+    s = h2_ctx_synchronize(ctx);
+    if (s != H2_OK) throw Error(s, ctx->last_error);
+    if (stats) {
+      stats[0] = L.updates;
+      stats[1] = L.products;
+      int kmax = 0;
+      for (int32_t r : C->V.rank) kmax = std::max(kmax, r);
+      for (int32_t r : C->W.rank) kmax = std::max(kmax, r);
+      stats[2] = kmax;
+    }
+  });
+  h2_matrix_free(T);
+  if (st == H2_OK) {
+    *out = C;
+  } else {
+    h2_matrix_free(C);
+  }
+  return st;
+}
+
 extern "C" h2_status h2_lr_solve(h2_ctx* ctx, const h2_matrix* LR, int64_t nrhs, double* X, int64_t ldx) {
   if (!ctx || !LR || nrhs < 0 || (nrhs > 0 && !X)) return H2_EINVAL;
   return lr_guard(ctx, [&] {
@@ -1129,6 +1220,52 @@ extern "C" h2_status h2_lr_solve(h2_ctx* ctx, const h2_matrix* LR, int64_t nrhs,
   });
 }
 
+namespace {
+// Preconditioned conjugate gradients from x = 0 (Section 7), the
+// preconditioner given as precond(in, out) on device vectors.
+template <class Precond>
+void pcg_run(h2_ctx* ctx, const h2_matrix* A, Precond&& precond, const double* b, double* x, double tol, int maxit,
+             int* iterations, double* relres, DArr& z) {
+  const int64_t n = A->rows.n;
+  cudaStream_t st = ctx->stream;
+  DArr r(n, st), p(n, st), q(n, st), part(kDotBlocks, st), sc(4, st);
+  auto dot = [&](const double* u, const double* v) {
+    launch_dot(u, v, n, part.p, sc.p, st);
+    double h = 0.0;
+    H2_CUDA(cudaMemcpyAsync(&h, sc.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+    H2_CUDA(cudaStreamSynchronize(st));
+    return h;
+  };
+  zero(x, n, st);
+  H2_CUDA(cudaMemcpyAsync(r.p, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  const double nb = std::sqrt(dot(b, b));
+  int it = 0;
+  double res = nb > 0 ? 1.0 : 0.0;
+  if (nb > 0) {
+    precond(r.p, z.p);
+    H2_CUDA(cudaMemcpyAsync(p.p, z.p, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    double rz = dot(r.p, z.p);
+    for (it = 1; it <= maxit; ++it) {
+      h2_status s = h2_matvec(ctx, A, 1, 1.0, p.p, n, 0.0, q.p, n);
+      if (s != H2_OK) throw Error(s, ctx->last_error);
+      const double alpha = rz / dot(p.p, q.p);
+      launch_axpby(n, alpha, p.p, 1.0, x, st);
+      launch_axpby(n, -alpha, q.p, 1.0, r.p, st);
+      res = std::sqrt(dot(r.p, r.p)) / nb;
+      if (res <= tol) break;
+      precond(r.p, z.p);
+      const double rz2 = dot(r.p, z.p);
+      launch_axpby(n, 1.0, z.p, rz2 / rz, p.p, st);
+      rz = rz2;
+    }
+    if (it > maxit) it = maxit;
+  }
+  H2_CUDA(cudaStreamSynchronize(st));
+  if (iterations) *iterations = it;
+  if (relres) *relres = res;
+}
+}  // namespace
+
 extern "C" h2_status h2_pcg(h2_ctx* ctx, const h2_matrix* A, const h2_matrix* LR, const double* b, double* x,
                             double tol, int maxit, int* iterations, double* relres) {
   if (!ctx || !A || !b || !x || maxit < 0) return H2_EINVAL;
@@ -1136,14 +1273,7 @@ extern "C" h2_status h2_pcg(h2_ctx* ctx, const h2_matrix* A, const h2_matrix* LR
     const int64_t n = A->rows.n;
     DevGuard g(ctx->device);
     cudaStream_t st = ctx->stream;
-    DArr r(n, st), z(n, st), p(n, st), q(n, st), part(kDotBlocks, st), sc(4, st);
-    auto dot = [&](const double* u, const double* v) {
-      launch_dot(u, v, n, part.p, sc.p, st);
-      double h = 0.0;
-      H2_CUDA(cudaMemcpyAsync(&h, sc.p, sizeof(double), cudaMemcpyDeviceToHost, st));
-      H2_CUDA(cudaStreamSynchronize(st));
-      return h;
-    };
+    DArr z(n, st);
     auto precond = [&](const double* in, double* out) {
       H2_CUDA(cudaMemcpyAsync(out, in, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
       if (LR) {
@@ -1151,33 +1281,24 @@ extern "C" h2_status h2_pcg(h2_ctx* ctx, const h2_matrix* A, const h2_matrix* LR
         if (s != H2_OK) throw Error(s, ctx->last_error);
       }
     };
-    zero(x, n, st);
-    H2_CUDA(cudaMemcpyAsync(r.p, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    const double nb = std::sqrt(dot(b, b));
-    int it = 0;
-    double res = nb > 0 ? 1.0 : 0.0;
-    if (nb > 0) {
-      precond(r.p, z.p);
-      H2_CUDA(cudaMemcpyAsync(p.p, z.p, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-      double rz = dot(r.p, z.p);
-      for (it = 1; it <= maxit; ++it) {
-        h2_status s = h2_matvec(ctx, A, 1, 1.0, p.p, n, 0.0, q.p, n);
-        if (s != H2_OK) throw Error(s, ctx->last_error);
-        const double alpha = rz / dot(p.p, q.p);
-        launch_axpby(n, alpha, p.p, 1.0, x, st);
-        launch_axpby(n, -alpha, q.p, 1.0, r.p, st);
-        res = std::sqrt(dot(r.p, r.p)) / nb;
-        if (res <= tol) break;
-        precond(r.p, z.p);
-        const double rz2 = dot(r.p, z.p);
-        launch_axpby(n, 1.0, z.p, rz2 / rz, p.p, st);
-        rz = rz2;
-      }
-      if (it > maxit) it = maxit;
-    }
-    H2_CUDA(cudaStreamSynchronize(st));
-    if (iterations) *iterations = it;
-    if (relres) *relres = res;
+    pcg_run(ctx, A, precond, b, x, tol, maxit, iterations, relres, z);
+  });
+}
+
+extern "C" h2_status h2_pcg_inverse(h2_ctx* ctx, const h2_matrix* A, const h2_matrix* Cinv, const double* b,
+                                    double* x, double tol, int maxit, int* iterations, double* relres) {
+  if (!ctx || !A || !Cinv || !b || !x || maxit < 0) return H2_EINVAL;
+  return lr_guard(ctx, [&] {
+    const int64_t n = A->rows.n;
+    H2_REQUIRE(Cinv->rows.n == n && Cinv->cols.n == n, "h2_pcg_inverse: the inverse has another size");
+    DevGuard g(ctx->device);
+    cudaStream_t st = ctx->stream;
+    DArr z(n, st);
+    auto precond = [&](const double* in, double* out) {
+      h2_status s = h2_matvec(ctx, Cinv, 1, 1.0, in, n, 0.0, out, n);
+      if (s != H2_OK) throw Error(s, ctx->last_error);
+    };
+    pcg_run(ctx, A, precond, b, x, tol, maxit, iterations, relres, z);
   });
 }
 
