@@ -456,7 +456,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-sample", type=int, default=24)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--lr-cells", default="32",
+    ap.add_argument("--lr-cells", default="32,64",
                     help="comma-separated cells per side of the 2D FEM H2-LR problems to time ('' for none)")
     ap.add_argument("--lr-reps", type=int, default=3)
     ap.add_argument("--inv-cells", default="32",

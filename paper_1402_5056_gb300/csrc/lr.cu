@@ -139,7 +139,6 @@ struct Lr {
   size_t wcap = 0;
   int32_t* dlist = nullptr;
   size_t lcap = 0;
-  int* drank = nullptr;           // rank of a compressed temporary
   int64_t* dnear_off = nullptr;   // per nearfield slot, offset in Z->d_N
   UpdateEngine* eng = nullptr;    // persistent workspace of the local updates
   ~Lr() {
@@ -148,7 +147,6 @@ struct Lr {
     if (xh) cudaFree(xh);
     if (yh) cudaFree(yh);
     if (dlist) cudaFree(dlist);
-    if (drank) cudaFree(drank);
   }
 };
 
@@ -407,7 +405,6 @@ int32_t son(const BlockTree& bt, int32_t b, int32_t t, int32_t s) {
   throw Error(H2_EINTERNAL, "block tree: missing son");
 }
 
-std::pair<int32_t, int32_t> sons_of(const ClusterTree& ct, int32_t c) { return {ct.son0[c], ct.son1[c]}; }
 
 // ----------------------------------------------------------- local updates
 void apply_update(Lr& L, int32_t b, const double* A, int64_t lda, const double* B, int64_t ldb, int u) {
@@ -634,8 +631,20 @@ void apply_term(Lr& L, const Term& T) {
   if (T.u > 0) apply_update(L, T.z, T.A.p, mt, T.B.p, mr, T.u);
 }
 
-// the terms of a temporary stacked, extended by zeros to z, truncated (reading 2)
-void apply_temp(Lr& L, const Temp& tmp) {
+// Scratch of one temporary's truncation (reading 2).
+struct TempWork {
+  int64_t mt = 0, mr = 0;
+  int m = 0, ka = 0, kb = 0;
+  DArr A, B, tauA, tauB, C, W, TA, TB;
+};
+
+// The terms of every temporary of a product stacked into factor pairs,
+// extended by zeros to the target, and truncated at once: Householder QR of
+// both factors and the SVD of the core R_A R_B^* with the rank rule (one
+// block per temporary).  The temporaries depend only on the terms (reading
+// 1), so one batch of launches and one synchronisation serve the whole
+// product.  ranks[i] receives the rank of item i's temporary.
+void compress_temps(Lr& L, const std::vector<Item>& items, std::vector<TempWork>& work, std::vector<int>& ranks) {
   const double t0 = now_s();
   const double u0 = L.t_update;
   struct Done {
@@ -645,47 +654,88 @@ void apply_temp(Lr& L, const Temp& tmp) {
   } done{L, t0, u0};
   h2_matrix* Z = L.Z;
   const BlockTree& bt = Z->blocks;
-  const int32_t t = bt.row[tmp.z], r = bt.col[tmp.z];
-  const int64_t mt = csize(Z, t), mr = csize(Z, r);
-  int m = 0;
-  for (const Term& T : tmp.terms) m += T.u;
-  if (m == 0) return;
-  if (m > kCompressMax) throw Error(H2_EINTERNAL, "temporary of rank above 256");
-  DArr A(mt * m, L.st), B(mr * m, L.st);
-  zero(A.p, mt * m, L.st);
-  zero(B.p, mr * m, L.st);
-  int c = 0;
-  for (const Term& T : tmp.terms) {
-    if (T.u == 0) continue;
-    const int64_t a0 = Z->rows.off[T.tc] - Z->rows.off[t];
-    const int64_t b0 = Z->cols.off[T.rc] - Z->cols.off[r];
-    const int64_t rt = csize(Z, T.tc), rr = csize(Z, T.rc);
-    H2_CUDA(cudaMemcpy2DAsync(A.p + a0 + (size_t)c * mt, mt * sizeof(double), T.A.p, rt * sizeof(double),
-                              rt * sizeof(double), T.u, cudaMemcpyDeviceToDevice, L.st));
-    H2_CUDA(cudaMemcpy2DAsync(B.p + b0 + (size_t)c * mr, mr * sizeof(double), T.B.p, rr * sizeof(double),
-                              rr * sizeof(double), T.u, cudaMemcpyDeviceToDevice, L.st));
-    c += T.u;
+  std::vector<Compress> desc;
+  std::vector<size_t> which;
+  int max_core = 0;
+  for (size_t i = 0; i < items.size(); ++i) {
+    if (!items[i].temp) continue;
+    const Temp& tmp = items[i].tmp;
+    const int32_t t = bt.row[tmp.z], r = bt.col[tmp.z];
+    const int64_t mt = csize(Z, t), mr = csize(Z, r);
+    int m = 0;
+    for (const Term& T : tmp.terms) m += T.u;
+    if (m == 0) continue;
+    if (m > kCompressMax) throw Error(H2_EINTERNAL, "temporary of rank above 256");
+    TempWork& w = work[i];
+    w.mt = mt;
+    w.mr = mr;
+    w.m = m;
+    w.ka = (int)std::min<int64_t>(mt, m);
+    w.kb = (int)std::min<int64_t>(mr, m);
+    w.A = DArr(mt * m, L.st);
+    w.B = DArr(mr * m, L.st);
+    zero(w.A.p, mt * m, L.st);
+    zero(w.B.p, mr * m, L.st);
+    int c = 0;
+    for (const Term& T : tmp.terms) {
+      if (T.u == 0) continue;
+      const int64_t a0 = Z->rows.off[T.tc] - Z->rows.off[t];
+      const int64_t b0 = Z->cols.off[T.rc] - Z->cols.off[r];
+      const int64_t rt = csize(Z, T.tc), rr = csize(Z, T.rc);
+      H2_CUDA(cudaMemcpy2DAsync(w.A.p + a0 + (size_t)c * mt, mt * sizeof(double), T.A.p, rt * sizeof(double),
+                                rt * sizeof(double), T.u, cudaMemcpyDeviceToDevice, L.st));
+      H2_CUDA(cudaMemcpy2DAsync(w.B.p + b0 + (size_t)c * mr, mr * sizeof(double), T.B.p, rr * sizeof(double),
+                                rr * sizeof(double), T.u, cudaMemcpyDeviceToDevice, L.st));
+      c += T.u;
+    }
+    w.tauA = DArr(m, L.st);
+    w.tauB = DArr(m, L.st);
+    w.C = DArr((size_t)m * m, L.st);
+    w.W = DArr((size_t)m * m, L.st);
+    w.TA = DArr((size_t)m * m, L.st);
+    w.TB = DArr((size_t)m * m, L.st);
+    desc.push_back({w.A.p, w.B.p, (int)mt, (int)mr, m, w.ka, w.kb, w.tauA.p, w.tauB.p, w.C.p, w.W.p, w.TA.p, w.TB.p,
+                    nullptr});
+    which.push_back(i);
+    max_core = std::max(max_core, w.ka * w.kb + w.kb * w.kb);
+    ++L.n_temps;
+    L.temp_cols += m;
   }
-  // Householder QR of both factors, SVD of the core R_A R_B^*, rank rule,
-  // A' = Q_A U_r Sigma_r, B' = Q_B W_r
-  DArr tauA(m, L.st), tauB(m, L.st), C(m * m, L.st), W(m * m, L.st), TA(m * m, L.st), TB(m * m, L.st);
-  if (!L.drank) L.drank = static_cast<int*>(device_alloc(3 * sizeof(int)));   // rank, nonzero flags of A and B
-  launch_house_qr(A.p, mt, (int)mt, B.p, mr, (int)mr, m, tauA.p, tauB.p, L.drank + 1, L.st);
-  const int ka = (int)std::min<int64_t>(mt, m), kb = (int)std::min<int64_t>(mr, m);
-  launch_core_svd(A.p, mt, ka, B.p, mr, kb, m, L.eps, L.drank + 1, C.p, W.p, TA.p, TB.p, L.drank, L.st);
-  int rk = 0;
-  H2_CUDA(cudaMemcpyAsync(&rk, L.drank, sizeof(int), cudaMemcpyDeviceToHost, L.st));
+  const int n = (int)desc.size();
+  if (n == 0) return;
+  // device copies of the descriptors and the flags (rank, nonzero A, nonzero B)
+  const size_t dsz = (n * sizeof(Compress) + sizeof(double) - 1) / sizeof(double);
+  DArr dd(dsz, L.st), df((3 * (size_t)n * sizeof(int) + sizeof(double) - 1) / sizeof(double), L.st);
+  int* flags = reinterpret_cast<int*>(df.p);
+  for (int k = 0; k < n; ++k) desc[k].flags = flags + 3 * k;
+  H2_CUDA(cudaMemcpyAsync(dd.p, desc.data(), n * sizeof(Compress), cudaMemcpyHostToDevice, L.st));
+  launch_compress_batch(reinterpret_cast<const Compress*>(dd.p), n, max_core, L.eps, L.st);
+  H2_CUDA(cudaGetLastError());
+  std::vector<int> h(3 * (size_t)n);
+  H2_CUDA(cudaMemcpyAsync(h.data(), flags, h.size() * sizeof(int), cudaMemcpyDeviceToHost, L.st));
   {
     Timer tw(L.t_temp_wait);
     H2_CUDA(cudaStreamSynchronize(L.st));
   }
-  ++L.n_temps;
-  L.temp_cols += m;
-  if (rk == 0) return;
-  DArr A2(mt * rk, L.st), B2(mr * rk, L.st);
-  launch_apply_q(A.p, mt, (int)mt, tauA.p, TA.p, A2.p, B.p, mr, (int)mr, tauB.p, TB.p, B2.p, m, rk, L.st);
+  for (int k = 0; k < n; ++k) ranks[which[k]] = h[3 * k];
+}
+
+// A' = Q_A U_r Sigma_r, B' = Q_B W_r of a truncated temporary, added to its
+// target by one local update
+void finish_temp(Lr& L, const Temp& tmp, TempWork& w, int rk) {
+  if (w.m == 0 || rk == 0) return;
+  const double t0 = now_s();
+  const double u0 = L.t_update;
+  struct Done {
+    Lr& L;
+    double t0, u0;
+    ~Done() { L.t_temps += (now_s() - t0) - (L.t_update - u0); }
+  } done{L, t0, u0};
+  DArr A2(w.mt * rk, L.st), B2(w.mr * rk, L.st);
+  launch_apply_q(w.A.p, w.mt, (int)w.mt, w.tauA.p, w.TA.p, A2.p, w.B.p, w.mr, (int)w.mr, w.tauB.p, w.TB.p, B2.p,
+                 w.m, rk, L.st);
   H2_CUDA(cudaGetLastError());
-  apply_update(L, tmp.z, A2.p, mt, B2.p, mr, rk);
+  apply_update(L, tmp.z, A2.p, w.mt, B2.p, w.mr, rk);
 }
 
 void mul(Lr& L, double alpha, int32_t x, int32_t y, int32_t z) {
@@ -694,9 +744,13 @@ void mul(Lr& L, double alpha, int32_t x, int32_t y, int32_t z) {
     Timer tm(L.t_terms);
     collect(L, alpha, x, y, z, items);
   }
-  for (const Item& it : items) {
-    if (it.temp) apply_temp(L, it.tmp);
-    else apply_term(L, it.term);
+  std::vector<TempWork> work(items.size());
+  std::vector<int> ranks(items.size(), 0);
+  compress_temps(L, items, work, ranks);
+  for (size_t i = 0; i < items.size(); ++i) {
+    if (items[i].temp) finish_temp(L, items[i].tmp, work[i], ranks[i]);
+    else apply_term(L, items[i].term);
+    work[i] = TempWork();   // its scratch goes back to the stream-ordered pool
   }
 }
 

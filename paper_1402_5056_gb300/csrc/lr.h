@@ -70,17 +70,29 @@ void launch_leaf_lu(double* A, int m, int64_t lda, int* err, cudaStream_t st);
 //   kind 1: X <- R^-1 X  (R upper with the diagonal in F, X m x n)
 //   kind 2: X <- X R^-1  (X n x m)
 void launch_trsm(int kind, const double* F, int m, int64_t ldf, double* X, int n, int64_t ldx, cudaStream_t st);
-// truncation of a factor pair (A rows_a x m, B rows_b x m, m <= 256):
-// Householder QR of both in place (tau_a, tau_b: m entries each), the SVD
-// of the core R_A R_B^* by one-sided Jacobi and the rank rule (C, W: m x m
-// scratch; TA, TB: m x m, first r columns; *rank on the device), then
-// A' = Q_A [TA; 0] into OA (rows_a x r), B' = Q_B [TB; 0] into OB
-// nonzero (2 ints, device): whether A and B have a nonzero entry (written
-// by the QR; the core SVD returns rank 0 at once for a zero product)
-void launch_house_qr(double* A, int64_t lda, int rows_a, double* B, int64_t ldb, int rows_b, int m, double* tau_a,
-                     double* tau_b, int* nonzero, cudaStream_t st);
-void launch_core_svd(const double* A, int64_t lda, int ka, const double* B, int64_t ldb, int kb, int m, double eps,
-                     const int* nonzero, double* C, double* W, double* TA, double* TB, int* rank, cudaStream_t st);
+// Truncation of a factor pair (A mt x m, B mr x m, m <= 256): Householder
+// QR of both in place, the SVD of the core R_A R_B^* by one-sided Jacobi
+// and the rank rule, then A' = Q_A [U_r Sigma_r; 0], B' = Q_B [W_r; 0].
+// One temporary to truncate (device pointers): the factors A (ld mt) and B
+// (ld mr); ka = min(mt, m), kb = min(mr, m); scratch tauA, tauB (m), C, W
+// (m x m), TA, TB (m x m, first r columns: U_r Sigma_r and W_r); flags[0]
+// receives the rank, flags[1..2] whether A and B have a nonzero entry (a
+// zero product has rank 0 at once).
+struct Compress {
+  double* A;
+  double* B;
+  int mt, mr, m, ka, kb;
+  double* tauA;
+  double* tauB;
+  double* C;
+  double* W;
+  double* TA;
+  double* TB;
+  int* flags;
+};
+// QR and core SVD of n temporaries at once (one block per temporary and
+// side); max_core_doubles = the largest ka kb + kb kb
+void launch_compress_batch(const Compress* d, int n, int max_core_doubles, double eps, cudaStream_t st);
 void launch_apply_q(const double* A, int64_t lda, int rows_a, const double* tau_a, const double* TA, double* OA,
                     const double* B, int64_t ldb, int rows_b, const double* tau_b, const double* TB, double* OB,
                     int m, int r, cudaStream_t st);

@@ -297,12 +297,7 @@ __global__ void k_axpby(int64_t n, double a, const double* x, double b, double* 
 // A' B'^* is the truncated A B^* (B' has orthonormal columns).
 
 // QR of the rows x m matrix X (ld ldx) in place; tau (m entries).  One block.
-__global__ void __launch_bounds__(512) k_house_qr(double* XA, int64_t lda, int rows_a, double* XB, int64_t ldb, int rows_b, int m,
-                           double* tau_a, double* tau_b, int* nonzero) {
-  double* X = blockIdx.x == 0 ? XA : XB;
-  const int64_t ldx = blockIdx.x == 0 ? lda : ldb;
-  const int rows = blockIdx.x == 0 ? rows_a : rows_b;
-  double* tau = blockIdx.x == 0 ? tau_a : tau_b;
+__device__ __forceinline__ void house_qr_one(double* X, int64_t ldx, int rows, int m, double* tau, int* nonzero) {
   __shared__ double red[32];
   __shared__ double sh_beta, sh_tau, sh_scale;
   __shared__ int any;
@@ -316,7 +311,7 @@ __global__ void __launch_bounds__(512) k_house_qr(double* XA, int64_t lda, int r
     if (X[e % rows + (e / rows) * ldx] != 0.0) mine = 1;
   if (__any_sync(0xffffffffu, mine) && lane == 0) any = 1;
   __syncthreads();
-  if (tid == 0) nonzero[blockIdx.x] = any;
+  if (tid == 0) *nonzero = any;
   if (!any) {
     for (int j = tid; j < m; j += nt) tau[j] = 0.0;
     return;
@@ -368,6 +363,14 @@ __global__ void __launch_bounds__(512) k_house_qr(double* XA, int64_t lda, int r
   }
 }
 
+// every temporary of a product at once: block (side, temporary)
+__global__ void __launch_bounds__(512) k_house_qr_batch(const Compress* __restrict__ d, int n) {
+  const Compress c = d[blockIdx.y];
+  if (blockIdx.x == 0) house_qr_one(c.A, c.mt, c.mt, c.m, c.tauA, c.flags + 1);
+  else house_qr_one(c.B, c.mr, c.mr, c.m, c.tauB, c.flags + 2);
+  (void)n;
+}
+
 __device__ __forceinline__ int rr_partner(int i, int r, int n2, int& p, int& q) {
   if (i == 0) { p = r; q = n2 - 1; }
   else { p = (r + i) % (n2 - 1); q = (r - i + (n2 - 1)) % (n2 - 1); }
@@ -380,9 +383,9 @@ __device__ __forceinline__ int rr_partner(int i, int r, int n2, int& p, int& q) 
 // TB (kb x r, ld m), the rank into *rank.  One block.  With in_smem, C and W
 // live in dynamic shared memory instead (ld ka and kb): the same
 // arithmetic, without a round trip through the caches for every rotation.
-__global__ void __launch_bounds__(1024) k_core_svd(const double* XA, int64_t lda, int ka, const double* XB, int64_t ldb, int kb, int m,
-                           double eps, const int* nonzero, double* Cg, double* Wg, double* TA, double* TB, int* rank,
-                           int in_smem) {
+__device__ __forceinline__ void core_svd_one(const double* XA, int64_t lda, int ka, const double* XB, int64_t ldb,
+                                             int kb, int m, double eps, const int* nonzero, double* Cg, double* Wg,
+                                             double* TA, double* TB, int* rank, int in_smem) {
   extern __shared__ double csm[];
   __shared__ int order[256];
   __shared__ double nrm2[256];
@@ -508,6 +511,16 @@ __global__ void __launch_bounds__(1024) k_core_svd(const double* XA, int64_t lda
   for (int e = tid; e < kb * r; e += nt) TB[e % kb + (e / kb) * m] = W[e % kb + order[e / kb] * lw];
 }
 
+// every temporary of a product at once, one block each; C and W in shared
+// memory when ka kb + kb kb <= smem_doubles
+__global__ void __launch_bounds__(1024) k_core_svd_batch(const Compress* __restrict__ d, int n, double eps,
+                                                         int smem_doubles) {
+  const Compress c = d[blockIdx.x];
+  const int in_smem = c.ka * c.kb + c.kb * c.kb <= smem_doubles ? 1 : 0;
+  core_svd_one(c.A, c.mt, c.ka, c.B, c.mr, c.kb, c.m, eps, c.flags + 1, c.C, c.W, c.TA, c.TB, c.flags, in_smem);
+  (void)n;
+}
+
 // out (rows x r, ld ldo) = Q [T; 0] with Q = H_0 H_1 ... H_{k-1} stored in X
 // (reflections below the diagonal, tau); T is k x r (ld ldt).  One block
 // per factor (blockIdx 0: A side, 1: B side).
@@ -600,21 +613,15 @@ void launch_trsm(int kind, const double* F, int m, int64_t ldf, double* X, int n
   k_trsm<<<(unsigned)((n + warps - 1) / warps), 32 * warps, 0, st>>>(kind, F, m, ldf, X, n, ldx);
 }
 
-void launch_house_qr(double* A, int64_t lda, int rows_a, double* B, int64_t ldb, int rows_b, int m, double* tau_a,
-                     double* tau_b, int* nonzero, cudaStream_t st) {
-  k_house_qr<<<2, 512, 0, st>>>(A, lda, rows_a, B, ldb, rows_b, m, tau_a, tau_b, nonzero);
-}
-
-void launch_core_svd(const double* A, int64_t lda, int ka, const double* B, int64_t ldb, int kb, int m, double eps,
-                     const int* nonzero, double* C, double* W, double* TA, double* TB, int* rank, cudaStream_t st) {
-  // C and W in shared memory when they fit (most temporaries)
+void launch_compress_batch(const Compress* d, int n, int max_core_doubles, double eps, cudaStream_t st) {
+  if (n <= 0) return;
+  k_house_qr_batch<<<dim3(2, n), 512, 0, st>>>(d, n);
   constexpr size_t kMax = 160 * 1024;
   static std::atomic<unsigned long long> attr{0};
-  const size_t bytes = ((size_t)ka * kb + (size_t)kb * kb) * sizeof(double);
-  const int in_smem = bytes <= kMax ? 1 : 0;
-  if (in_smem) smem_limit(k_core_svd, kMax, attr);
-  k_core_svd<<<1, 1024, in_smem ? bytes : 0, st>>>(A, lda, ka, B, ldb, kb, m, eps, nonzero, C, W, TA, TB, rank,
-                                                   in_smem);
+  const size_t bytes = (size_t)max_core_doubles * sizeof(double);
+  const int fit = bytes <= kMax ? max_core_doubles : 0;
+  if (fit) smem_limit(k_core_svd_batch, kMax, attr);
+  k_core_svd_batch<<<n, 1024, (size_t)fit * sizeof(double), st>>>(d, n, eps, fit);
 }
 
 void launch_apply_q(const double* A, int64_t lda, int rows_a, const double* tau_a, const double* TA, double* OA,
