@@ -378,18 +378,142 @@ __device__ __forceinline__ int rr_partner(int i, int r, int n2, int& p, int& q) 
   return 0;
 }
 
+// One-sided Jacobi on the cols columns of X (rows x cols, ld ldx): X V = U
+// Sigma, the rotations accumulated into V (cols x cols, ld ldv).  Round-
+// robin pairs, one warp a pair.  Columns whose squared norm is below 1e-28
+// of the largest are at the rounding level of the product: they are not
+// rotated (rotating them need not converge, and they lie far below any
+// truncation threshold).  Rotate while |gamma| > 64 u sqrt(alpha beta): a
+// smaller threshold lies below the rounding of the dot products (up to 256
+// terms) and the sweeps would not end.  nrm2 (cols) is scratch.
+__device__ __forceinline__ void jacobi_cols(double* X, int ldx, int rows, int cols, double* V, int ldv,
+                                            double* nrm2) {
+  __shared__ int any_rot;
+  __shared__ double tiny;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  for (int j = tid; j < cols; j += nt) {
+    double v = 0.0;
+    for (int k = 0; k < rows; ++k) v = fma(X[k + j * ldx], X[k + j * ldx], v);
+    nrm2[j] = v;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double mx = 0.0;
+    for (int j = 0; j < cols; ++j) mx = fmax(mx, nrm2[j]);
+    tiny = 1e-28 * mx;
+  }
+  __syncthreads();
+  const int n2 = cols + (cols & 1);
+  const double tol2 = (64.0 * 2.220446049250313e-16) * (64.0 * 2.220446049250313e-16);
+  for (int sweep = 0; sweep < 40 && cols > 1; ++sweep) {
+    if (tid == 0) any_rot = 0;
+    __syncthreads();
+    for (int r = 0; r < n2 - 1; ++r) {
+      for (int i = warp; i < n2 / 2; i += nw) {
+        int p, q;
+        rr_partner(i, r, n2, p, q);
+        if (q >= cols) continue;
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int k = lane; k < rows; k += 32) {
+          const double x = X[k + p * ldx], y = X[k + q * ldx];
+          al = fma(x, x, al);
+          be = fma(y, y, be);
+          ga = fma(x, y, ga);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        }
+        if (ga * ga > tol2 * al * be && ga != 0.0 && al > tiny && be > tiny) {
+          const double zeta = (be - al) / (2.0 * ga);
+          const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
+          const double c = 1.0 / sqrt(fma(t, t, 1.0)), s = c * t;
+          for (int k = lane; k < rows; k += 32) {
+            const double x = X[k + p * ldx], y = X[k + q * ldx];
+            X[k + p * ldx] = c * x - s * y;
+            X[k + q * ldx] = s * x + c * y;
+          }
+          for (int k = lane; k < cols; k += 32) {
+            const double x = V[k + p * ldv], y = V[k + q * ldv];
+            V[k + p * ldv] = c * x - s * y;
+            V[k + q * ldv] = s * x + c * y;
+          }
+          if (lane == 0) any_rot = 1;
+        }
+      }
+      __syncthreads();
+    }
+    if (!any_rot) break;
+    __syncthreads();
+  }
+  // squared column norms = sigma^2
+  for (int j = tid; j < cols; j += nt) {
+    double v = 0.0;
+    for (int k = 0; k < rows; ++k) v = fma(X[k + j * ldx], X[k + j * ldx], v);
+    nrm2[j] = v;
+  }
+  __syncthreads();
+}
+
+// Descending order of the squared singular values nrm2 (cols) and the rank
+// rule: the smallest r with sum_{i>r} sigma_i^2 <= (eps/2)^2 sum sigma_i^2.
+// Thread 0 writes order and *rank; every thread returns the rank.
+__device__ __forceinline__ int rank_rule(const double* nrm2, int* order, int cols, double eps, int* rank) {
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < cols; ++i) order[i] = i;
+    for (int i = 1; i < cols; ++i) {
+      const int k = order[i];
+      int j = i - 1;
+      while (j >= 0 && nrm2[order[j]] < nrm2[k]) {
+        order[j + 1] = order[j];
+        --j;
+      }
+      order[j + 1] = k;
+    }
+    double total = 0.0;
+    for (int i = 0; i < cols; ++i) total += nrm2[i];
+    int r = cols;
+    if (total == 0.0) {
+      r = 0;
+    } else {
+      const double thr = 0.25 * eps * eps * total;
+      double tail = 0.0;
+      while (r > 0 && tail + nrm2[order[r - 1]] <= thr) {
+        tail += nrm2[order[r - 1]];
+        --r;
+      }
+    }
+    *rank = r;
+  }
+  __syncthreads();
+  return *rank;
+}
+
 // Core SVD and rank.  C (ka x kb, ld m, scratch), W (kb x kb, ld m,
-// scratch); writes T = U_r Sigma_r = C W_r (ka x r, ld m) into TA, W_r into
-// TB (kb x r, ld m), the rank into *rank.  One block.  With in_smem, C and W
-// live in dynamic shared memory instead (ld ka and kb): the same
-// arithmetic, without a round trip through the caches for every rotation.
+// scratch); writes T = U_r Sigma_r (ka x r, ld m) into TA and the right
+// singular vectors W_r (kb x r, ld m) into TB, the rank into *rank.  One
+// block.  With in_smem, C and W live in dynamic shared memory instead (ld ka
+// and kb).
+//
+// Up to 32 columns the one-sided Jacobi runs on C itself.  Wider cores (a
+// temporary stacking many terms) first go through a Householder QR with
+// column pivoting, C P = Q R, stopped once the trailing columns' norm is at
+// the rounding level of C (below 1e-15 ||C||_F): C = Q_p R_p P^* up to that
+// remainder, p the numerical rank.  The Jacobi then runs on the p columns of
+// M = R_p^* (kb x p): M V = U_M Sigma, so C = (Q_p V) Sigma (P U_M)^* -- the
+// same singular values and vectors as a Jacobi on all kb columns, with p^2
+// instead of kb^2 pairs.
 __device__ __forceinline__ void core_svd_one(const double* XA, int64_t lda, int ka, const double* XB, int64_t ldb,
                                              int kb, int m, double eps, const int* nonzero, double* Cg, double* Wg,
                                              double* TA, double* TB, int* rank, int in_smem) {
   extern __shared__ double csm[];
   __shared__ int order[256];
   __shared__ double nrm2[256];
-  __shared__ int any_rot;
+  __shared__ int perm[256];
+  __shared__ double tauc[256];
+  __shared__ int sh_p, sh_piv;
+  __shared__ double sh_beta, sh_tau, sh_scale, sh_delta2;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   if (!nonzero[0] || !nonzero[1]) {   // A B^* = 0
     if (tid == 0) *rank = 0;
@@ -406,109 +530,146 @@ __device__ __forceinline__ void core_svd_one(const double* XA, int64_t lda, int 
     for (int q = max(i, j); q < m; ++q) v = fma(XA[i + (int64_t)q * lda], XB[j + (int64_t)q * ldb], v);
     C[i + j * lc] = v;
   }
-  for (int e = tid; e < kb * kb; e += nt) W[e % kb + (e / kb) * lw] = (e % kb == e / kb) ? 1.0 : 0.0;
-  __syncthreads();
-  // columns whose squared norm is below 1e-28 of the largest are at the
-  // rounding level of the product: they are not rotated (rotating them
-  // need not converge, and they lie far below any truncation threshold)
-  for (int j = tid; j < kb; j += nt) {
-    double v = 0.0;
-    for (int k = 0; k < ka; ++k) v = fma(C[k + j * lc], C[k + j * lc], v);
-    nrm2[j] = v;
-  }
-  __syncthreads();
-  __shared__ double tiny;
-  if (tid == 0) {
-    double mx = 0.0;
-    for (int j = 0; j < kb; ++j) mx = fmax(mx, nrm2[j]);
-    tiny = 1e-28 * mx;
-  }
-  __syncthreads();
-  // one-sided Jacobi on the columns of C, round-robin pairs, one warp a pair
-  const int n2 = kb + (kb & 1);
-  // rotate while |gamma| > 64 u sqrt(alpha beta): a smaller threshold lies
-  // below the rounding of the dot products (up to 256 terms) and the sweeps
-  // would not end
-  const double tol2 = (64.0 * 2.220446049250313e-16) * (64.0 * 2.220446049250313e-16);
-  for (int sweep = 0; sweep < 40 && kb > 1; ++sweep) {
-    if (tid == 0) any_rot = 0;
+  if (kb <= 32) {
+    for (int e = tid; e < kb * kb; e += nt) W[e % kb + (e / kb) * lw] = (e % kb == e / kb) ? 1.0 : 0.0;
     __syncthreads();
-    for (int r = 0; r < n2 - 1; ++r) {
-      for (int i = warp; i < n2 / 2; i += nw) {
-        int p, q;
-        rr_partner(i, r, n2, p, q);
-        if (q >= kb) continue;
-        double al = 0.0, be = 0.0, ga = 0.0;
-        for (int k = lane; k < ka; k += 32) {
-          const double x = C[k + p * lc], y = C[k + q * lc];
-          al = fma(x, x, al);
-          be = fma(y, y, be);
-          ga = fma(x, y, ga);
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-          al += __shfl_xor_sync(0xffffffffu, al, o);
-          be += __shfl_xor_sync(0xffffffffu, be, o);
-          ga += __shfl_xor_sync(0xffffffffu, ga, o);
-        }
-        if (ga * ga > tol2 * al * be && ga != 0.0 && al > tiny && be > tiny) {
-          const double zeta = (be - al) / (2.0 * ga);
-          const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
-          const double c = 1.0 / sqrt(fma(t, t, 1.0)), s = c * t;
-          for (int k = lane; k < ka; k += 32) {
-            const double x = C[k + p * lc], y = C[k + q * lc];
-            C[k + p * lc] = c * x - s * y;
-            C[k + q * lc] = s * x + c * y;
-          }
-          for (int k = lane; k < kb; k += 32) {
-            const double x = W[k + p * lw], y = W[k + q * lw];
-            W[k + p * lw] = c * x - s * y;
-            W[k + q * lw] = s * x + c * y;
-          }
-          if (lane == 0) any_rot = 1;
+    jacobi_cols(C, lc, ka, kb, W, lw, nrm2);
+    const int r = rank_rule(nrm2, order, kb, eps, rank);
+    for (int e = tid; e < ka * r; e += nt) TA[e % ka + (e / ka) * m] = C[e % ka + order[e / ka] * lc];
+    for (int e = tid; e < kb * r; e += nt) TB[e % kb + (e / kb) * m] = W[e % kb + order[e / kb] * lw];
+    return;
+  }
+  // Householder QR with column pivoting, stopped at the rounding level
+  for (int c = tid; c < kb; c += nt) perm[c] = c;
+  __syncthreads();
+  const int kk = min(ka, kb);
+  if (tid == 0) sh_p = kk;
+  for (int j = 0; j < kk; ++j) {
+    // norms of the trailing columns over the rows j..ka-1
+    for (int c = j + warp; c < kb; c += nw) {
+      double v = 0.0;
+      for (int i = j + lane; i < ka; i += 32) v = fma(C[i + c * lc], C[i + c * lc], v);
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) nrm2[c] = v;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double tot = 0.0, best = -1.0;
+      int piv = j;
+      for (int c = j; c < kb; ++c) {
+        tot += nrm2[c];
+        if (nrm2[c] > best) {
+          best = nrm2[c];
+          piv = c;
         }
       }
-      __syncthreads();
+      if (j == 0) sh_delta2 = 1e-30 * tot;
+      if (tot <= sh_delta2) {
+        sh_p = j;
+        piv = -1;
+      } else {
+        const int t = perm[j];
+        perm[j] = perm[piv];
+        perm[piv] = t;
+      }
+      sh_piv = piv;
     }
-    if (!any_rot) break;
+    __syncthreads();
+    const int piv = sh_piv;
+    if (piv < 0) break;
+    if (piv != j)
+      for (int i = tid; i < ka; i += nt) {
+        const double t = C[i + j * lc];
+        C[i + j * lc] = C[i + piv * lc];
+        C[i + piv * lc] = t;
+      }
+    __syncthreads();
+    // reflection of column j (rows j..ka-1), the form of LAPACK's dlarfg
+    double* x = C + j + j * lc;
+    const int len = ka - j;
+    if (tid < 32) {
+      double sv = 0.0;
+      for (int i = 1 + lane; i < len; i += 32) sv = fma(x[i], x[i], sv);
+      for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
+      if (lane == 0) {
+        const double alpha = x[0];
+        if (sv == 0.0) {
+          sh_tau = 0.0;
+          sh_beta = alpha;
+          sh_scale = 0.0;
+        } else {
+          const double nrm = sqrt(fma(alpha, alpha, sv));
+          const double beta = alpha >= 0.0 ? -nrm : nrm;
+          sh_tau = (beta - alpha) / beta;
+          sh_scale = 1.0 / (alpha - beta);
+          sh_beta = beta;
+        }
+        tauc[j] = sh_tau;
+      }
+    }
+    __syncthreads();
+    const double t = sh_tau;
+    if (t != 0.0)
+      for (int i = 1 + tid; i < len; i += nt) x[i] *= sh_scale;
+    __syncthreads();
+    if (tid == 0) x[0] = sh_beta;
+    // apply H to the columns j+1..kb-1: one warp per column
+    if (t != 0.0)
+      for (int c = j + 1 + warp; c < kb; c += nw) {
+        double* y = C + j + c * lc;
+        double w = lane == 0 ? y[0] : 0.0;
+        for (int i = 1 + lane; i < len; i += 32) w = fma(x[i], y[i], w);
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+        w *= t;
+        if (lane == 0) y[0] -= w;
+        for (int i = 1 + lane; i < len; i += 32) y[i] = fma(-w, x[i], y[i]);
+      }
     __syncthreads();
   }
-  // squared column norms = sigma^2, descending order, rank rule
-  for (int j = tid; j < kb; j += nt) {
-    double v = 0.0;
-    for (int k = 0; k < ka; ++k) v = fma(C[k + j * lc], C[k + j * lc], v);
-    nrm2[j] = v;
-  }
   __syncthreads();
-  if (tid == 0) {
-    for (int i = 0; i < kb; ++i) order[i] = i;
-    for (int i = 1; i < kb; ++i) {
-      const int k = order[i];
-      int j = i - 1;
-      while (j >= 0 && nrm2[order[j]] < nrm2[k]) {
-        order[j + 1] = order[j];
-        --j;
-      }
-      order[j + 1] = k;
-    }
-    double total = 0.0;
-    for (int i = 0; i < kb; ++i) total += nrm2[i];
-    int r = kb;
-    if (total == 0.0) {
-      r = 0;
-    } else {
-      const double thr = 0.25 * eps * eps * total;
-      double tail = 0.0;
-      while (r > 0 && tail + nrm2[order[r - 1]] <= thr) {
-        tail += nrm2[order[r - 1]];
-        --r;
-      }
-    }
-    *rank = r;
+  const int p = sh_p;
+  if (p == 0) {
+    if (tid == 0) *rank = 0;
+    return;
   }
+  // M = R_p^* (kb x p) in W, V = I (p x p) in TB
+  for (int e = tid; e < kb * p; e += nt) {
+    const int c = e % kb, j = e / kb;
+    W[c + j * lw] = c >= j ? C[j + c * lc] : 0.0;
+  }
+  for (int e = tid; e < p * p; e += nt) TB[e % p + (e / p) * m] = (e % p == e / p) ? 1.0 : 0.0;
   __syncthreads();
-  const int r = *rank;
-  for (int e = tid; e < ka * r; e += nt) TA[e % ka + (e / ka) * m] = C[e % ka + order[e / ka] * lc];
-  for (int e = tid; e < kb * r; e += nt) TB[e % kb + (e / kb) * m] = W[e % kb + order[e / kb] * lw];
+  jacobi_cols(W, lw, kb, p, TB, m, nrm2);
+  const int r = rank_rule(nrm2, order, p, eps, rank);
+  // TA = Q_p [V_r Sigma_r; 0]: one warp per column, the reflections in
+  // reverse order
+  for (int i = warp; i < r; i += nw) {
+    const int jc = order[i];
+    const double sg = sqrt(nrm2[jc]);
+    double* y = TA + (int64_t)i * m;
+    for (int k = lane; k < ka; k += 32) y[k] = k < p ? TB[k + jc * m] * sg : 0.0;
+    __syncwarp();
+    for (int j = p - 1; j >= 0; --j) {
+      const double t = tauc[j];
+      if (t == 0.0) continue;
+      const double* v = C + j + j * lc;   // v_0 = 1 implied
+      const int len = ka - j;
+      double w = lane == 0 ? y[j] : 0.0;
+      for (int k = 1 + lane; k < len; k += 32) w = fma(v[k], y[j + k], w);
+      for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+      w *= t;
+      __syncwarp();
+      if (lane == 0) y[j] -= w;
+      for (int k = 1 + lane; k < len; k += 32) y[j + k] = fma(-w, v[k], y[j + k]);
+      __syncwarp();
+    }
+  }
+  __syncthreads();   // V (in TB) is read; TB now receives P U_M
+  for (int e = tid; e < kb * r; e += nt) {
+    const int c = e % kb, i = e / kb;
+    const int jc = order[i];
+    TB[perm[c] + (int64_t)i * m] = W[c + jc * lw] / sqrt(nrm2[jc]);
+  }
 }
 
 // every temporary of a product at once, one block each; C and W in shared
