@@ -281,6 +281,22 @@ h2_status h2_batch_item_tile(h2_ctx* ctx, const h2_batch* batch, int64_t item, i
 /* Cluster tasks of update j occupy items [first, last). */
 h2_status h2_batch_update_items(const h2_batch* batch, int64_t j, int64_t* first, int64_t* last);
 
+/* Size and rank statistics of an H^2 matrix (host data only; no device
+ * access, no synchronisation).  out (host, 12 entries): 0 n, 1 clusters per
+ * tree, 2 block-tree nodes, 3 admissible leaves, 4 inadmissible leaves,
+ * 5 depth of the cluster tree, 6 rank capacity of the storage, 7 largest
+ * row-basis rank, 8 largest column-basis rank, 9 bytes of device storage of
+ * the bases, transfers, couplings and nearfield (at the rank capacity; 0
+ * for a structure without device storage),
+ * 10 bytes of the values the representation holds at its ranks (leaf bases
+ * #t x k_t, transfers k_t x k_{t+}, couplings k_t x l_s, nearfield
+ * #t x #s), 11 sum of the row-basis ranks.  max_rank_per_level (host,
+ * depth + 1 entries, or NULL): the largest row-basis rank on each level of
+ * the cluster tree.  Floating-point work is reported per batch
+ * (h2_batch_stats, h2_batch_phase_stats) and per factorisation
+ * (h2_lr_factor's stats). */
+h2_status h2_stats(const h2_matrix* Z, int64_t* out, int32_t* max_rank_per_level);
+
 /* Y <- alpha Z X + beta Y for nrhs right-hand sides (Section 2: Eq. (vsw)
  * on the admissible leaves with the nested bases of Eq. (nested), dense
  * inadmissible leaves; the product the multiplication of Section 3 applies

@@ -34,7 +34,7 @@ EXPORTS = [
     "h2_batch_update_items", "h2_batch_set_mode", "h2_batch_paths", "h2_lowrank_update",
     "h2_lowrank_update_noalloc", "h2_lowrank_update_sequence", "h2_matvec", "h2_block_to_dense",
     "h2_sequence_waves", "h2_check_reciprocal", "h2_debug_fail_allocation",
-    "h2_build_fem", "h2_lr_factor", "h2_lr_solve", "h2_pcg", "h2_lr_error", "h2_mul", "h2_inverse",
+    "h2_stats", "h2_build_fem", "h2_lr_factor", "h2_lr_solve", "h2_pcg", "h2_lr_error", "h2_mul", "h2_inverse",
     "h2_pcg_inverse",
 ]
 
@@ -120,6 +120,7 @@ _sig("h2_lr_solve", _int, _p, _p, _i64, _p, _i64)
 _sig("h2_pcg", _int, _p, _p, _p, _p, _p, _dbl, _int, _p, _p)
 _sig("h2_lr_error", _int, _p, _p, _p, _p, _int, _p)
 _sig("h2_inverse", _int, _p, _p, _p, _p, _p)
+_sig("h2_stats", _int, _p, _p, _p)
 _sig("h2_pcg_inverse", _int, _p, _p, _p, _p, _p, _dbl, _int, _p, _p)
 _sig("h2_mul", _int, _p, _dbl, _p, _i64, _p, _i64, _p, _i64, _dbl, _p)
 _sig("h2_matvec", _int, _p, _p, _i64, _dbl, _p, _i64, _dbl, _p, _i64)
@@ -543,6 +544,19 @@ def h2_lr_error(ctx, A, LR, v_dev: int, iters: int):
     err = C.c_double(0.0)
     _check(_lib.h2_lr_error(ctx, A, LR, C.c_void_p(v_dev), int(iters), C.byref(err)), ctx)
     return err.value
+
+
+def h2_stats(Z):
+    """Size and rank statistics of an H^2 matrix (host data only)."""
+    out = np.zeros(12, np.int64)
+    depth = int(h2_tree_sizes(Z)["depth"])
+    lv = np.zeros(depth + 1, np.int32)
+    _check(_lib.h2_stats(Z, _ptr(out), _ptr(lv)))
+    keys = ("n", "n_clusters", "n_blocks", "n_admissible", "n_inadmissible", "depth", "rank_capacity",
+            "max_rank_rows", "max_rank_cols", "device_bytes", "value_bytes", "rank_sum_rows")
+    d = {k: int(v) for k, v in zip(keys, out)}
+    d["max_rank_per_level"] = [int(x) for x in lv]
+    return d
 
 
 def h2_inverse(ctx, A, opt):

@@ -452,6 +452,61 @@ extern "C" h2_status h2_tree_sizes(const h2_matrix* Z, int64_t* n, int64_t* n_cl
   return H2_OK;
 }
 
+extern "C" h2_status h2_stats(const h2_matrix* Z, int64_t* out, int32_t* max_rank_per_level) {
+  if (!Z || !out) return H2_EINVAL;
+  const ClusterTree& rt = Z->rows;
+  const ClusterTree& ct = Z->cols;
+  const BlockTree& bt = Z->blocks;
+  const std::vector<int32_t>& rv = Z->V.rank;
+  const std::vector<int32_t>& rw = Z->W.rank;
+  auto rank_at = [](const std::vector<int32_t>& r, int32_t c) { return c < (int32_t)r.size() ? r[c] : 0; };
+  int64_t kmax_v = 0, kmax_w = 0, ksum = 0, cap_bytes = 0, val = 0;
+  const int64_t kc = Z->kcap;
+  for (int s = 0; s < 2; ++s) {
+    const ClusterTree& tr = s == 0 ? rt : ct;
+    const std::vector<int32_t>& rk = s == 0 ? rv : rw;
+    for (int32_t c = 0; c < tr.count(); ++c) {
+      const int64_t k = rank_at(rk, c);
+      if (s == 0) {
+        kmax_v = std::max(kmax_v, k);
+        ksum += k;
+      } else {
+        kmax_w = std::max(kmax_w, k);
+      }
+      if (tr.leaf(c)) {
+        cap_bytes += tr.size[c] * kc;
+        val += tr.size[c] * k;
+      }
+      cap_bytes += kc * kc;
+      if (tr.father[c] >= 0) val += k * rank_at(rk, tr.father[c]);
+    }
+  }
+  int64_t near = 0;
+  for (int32_t b : bt.near) near += rt.size[bt.row[b]] * ct.size[bt.col[b]];
+  for (int32_t b : bt.adm) val += (int64_t)rank_at(rv, bt.row[b]) * rank_at(rw, bt.col[b]);
+  cap_bytes += (int64_t)bt.adm.size() * kc * kc + near;
+  val += near;
+  if (!has_storage(Z) || (!bt.near.empty() && Z->d_N == nullptr)) cap_bytes = 0;   // structure only
+  out[0] = rt.n;
+  out[1] = rt.count();
+  out[2] = bt.count();
+  out[3] = (int64_t)bt.adm.size();
+  out[4] = (int64_t)bt.near.size();
+  out[5] = rt.depth;
+  out[6] = kc;
+  out[7] = kmax_v;
+  out[8] = kmax_w;
+  out[9] = 8 * cap_bytes;
+  out[10] = 8 * val;
+  out[11] = ksum;
+  if (max_rank_per_level) {
+    for (int l = 0; l <= rt.depth; ++l) max_rank_per_level[l] = 0;
+    for (int32_t c = 0; c < rt.count(); ++c)
+      max_rank_per_level[rt.level[c]] = std::max(max_rank_per_level[rt.level[c]], rank_at(rv, c));
+  }
+  return H2_OK;
+}
+
 extern "C" h2_status h2_tree_clusters(const h2_matrix* Z, int64_t* offset, int64_t* size,
                                       int32_t* father, int32_t* son0, int32_t* son1, int32_t* level,
                                       int32_t* subtree) {

@@ -41,22 +41,37 @@ __device__ __forceinline__ double warp_sum(double v) {
 // quarter of the SM's float64 rate; a launch with few tasks (the
 // factorisation applies its updates one at a time) therefore gives every
 // task a block of kTW = 4 warps, one per sub-partition, and a launch with
-// many tasks (a batch) runs one warp per task without block barriers.  The
-// arithmetic is the same in both forms: the rows of a task are dealt to kTW
-// virtual warps, each forms its partial sums in row order, and the kTW
-// partial sums are added as (p0 + p1) + (p2 + p3) -- one warp plays all
-// four virtual warps when NW = 1.  An update gives the same bits whichever
-// form its launches take.
+// many tasks (a batch) runs one warp per task without block barriers.
+// (Eight warps per task, two per sub-partition, measured slower: 31.8 s
+// against 22.9 s for the local updates of the 128^2-cell factorisation.)  The arithmetic is the
+// same in both forms: the rows of a task are dealt to kTW virtual warps,
+// each forms its partial sums in row order, and the kTW partial sums are
+// added by one pairwise tree -- one warp plays all kTW virtual warps when
+// NW = 1.  An update gives the same bits whichever form its launches take.
 constexpr int kTW = 4;               // virtual warps of a task
 constexpr int kRW = kCh / kTW;       // rows of a 32-row chunk per virtual warp
+
+// pairwise sum of the kTW partials p[0..kTW), the same tree everywhere
+template <class T>
+__device__ __forceinline__ T tree_sum(const T* p) {
+  T q[kTW];
+#pragma unroll
+  for (int i = 0; i < kTW; ++i) q[i] = p[i];
+#pragma unroll
+  for (int h = 1; h < kTW; h <<= 1)
+#pragma unroll
+    for (int i = 0; i < kTW; i += 2 * h) q[i] = q[i] + q[i + h];
+  return q[0];
+}
 
 template <int NW>
 struct Team {
   static_assert(NW == 1 || NW == kTW, "a task runs on one warp or on kTW warps");
   static constexpr int VW = kTW / NW;   // virtual warps per warp
+  static constexpr int kBuf = 3 * 32 * kTW;
   int wp;        // warp of the task (0 when NW = 1)
   int lane;
-  double* buf;   // NW > 1: two buffers of 3 x 128 doubles for the sums
+  double* buf;   // NW > 1: two buffers of kBuf doubles for the sums
   int ph;
   __device__ __forceinline__ int vw(int v) const { return wp * VW + v; }
   __device__ __forceinline__ bool lead() const { return wp == 0; }
@@ -64,37 +79,46 @@ struct Team {
     if constexpr (NW > 1) __syncthreads();
     else __syncwarp();
   }
-  // Per-lane sums over the kTW virtual warps of x[v], added in warp order.
-  // NW > 1: one barrier per call; the two buffers alternate, so a buffer is
-  // written again only after every thread passed the barrier of the call in
-  // between.  Every thread of the team makes the same calls.
+  // the kTW partials of this lane, gathered from the warps' slots of b
+  template <class T>
+  __device__ __forceinline__ T gather_sum(const double* b) const {
+    T p[kTW];
+#pragma unroll
+    for (int w = 0; w < kTW; ++w) p[w] = (T)b[32 * w + lane];
+    return tree_sum(p);
+  }
+  // Per-lane sums over the kTW virtual warps of x[v], added by the same
+  // pairwise tree in both forms.  NW > 1: one barrier per call; the two
+  // buffers alternate, so a buffer is written again only after every
+  // thread passed the barrier of the call in between.  Every thread of the
+  // team makes the same calls.
   template <class T>
   __device__ __forceinline__ void sum3(const T (&x)[VW], const T (&y)[VW], const T (&z)[VW], T& sx, T& sy, T& sz) {
     if constexpr (NW == 1) {
-      sx = (x[0] + x[1]) + (x[2] + x[3]);
-      sy = (y[0] + y[1]) + (y[2] + y[3]);
-      sz = (z[0] + z[1]) + (z[2] + z[3]);
+      sx = tree_sum(x);
+      sy = tree_sum(y);
+      sz = tree_sum(z);
     } else {
-      double* b = buf + ph * 384;
+      double* b = buf + ph * kBuf;
       ph ^= 1;
       b[wp * 32 + lane] = x[0];
-      b[128 + wp * 32 + lane] = y[0];
-      b[256 + wp * 32 + lane] = z[0];
+      b[32 * kTW + wp * 32 + lane] = y[0];
+      b[64 * kTW + wp * 32 + lane] = z[0];
       __syncthreads();
-      sx = ((T)b[lane] + (T)b[32 + lane]) + ((T)b[64 + lane] + (T)b[96 + lane]);
-      sy = ((T)b[128 + lane] + (T)b[160 + lane]) + ((T)b[192 + lane] + (T)b[224 + lane]);
-      sz = ((T)b[256 + lane] + (T)b[288 + lane]) + ((T)b[320 + lane] + (T)b[352 + lane]);
+      sx = gather_sum<T>(b);
+      sy = gather_sum<T>(b + 32 * kTW);
+      sz = gather_sum<T>(b + 64 * kTW);
     }
   }
   __device__ __forceinline__ double sum1(const double (&x)[VW]) {
     if constexpr (NW == 1) {
-      return (x[0] + x[1]) + (x[2] + x[3]);
+      return tree_sum(x);
     } else {
-      double* b = buf + ph * 384;
+      double* b = buf + ph * kBuf;
       ph ^= 1;
       b[wp * 32 + lane] = x[0];
       __syncthreads();
-      return (b[lane] + b[32 + lane]) + (b[64 + lane] + b[96 + lane]);
+      return gather_sum<double>(b);
     }
   }
   // maximum over the warps of a value (exact in any order)
@@ -102,11 +126,14 @@ struct Team {
     if constexpr (NW == 1) {
       return x;
     } else {
-      double* b = buf + ph * 384;
+      double* b = buf + ph * kBuf;
       ph ^= 1;
       b[wp * 32 + lane] = x;
       __syncthreads();
-      return fmax(fmax(b[lane], b[32 + lane]), fmax(b[64 + lane], b[96 + lane]));
+      double m = b[lane];
+#pragma unroll
+      for (int w = 1; w < kTW; ++w) m = fmax(m, b[32 * w + lane]);
+      return m;
     }
   }
 };
@@ -205,8 +232,8 @@ __device__ __forceinline__ void store_tile_t(double* dst, const double* R, int n
 }
 
 // Shared memory of one task of the fold kernels (doubles): the R tile, the
-// pivot column and, for four-warp teams, the sum buffers.
-__host__ __device__ constexpr int fold_doubles(int nw) { return 32 * kLdr + 32 + (nw > 1 ? 768 : 0); }
+// pivot column and, for kTW-warp teams, the sum buffers.
+__host__ __device__ constexpr int fold_doubles(int nw) { return 32 * kLdr + 32 + (nw > 1 ? 2 * 96 * kTW : 0); }
 
 // Task index, team and shared memory of a task of a kernel launched with
 // one block of kTW warps per task (NW = kTW) or one warp per task (NW = 1);
@@ -250,7 +277,7 @@ __device__ __forceinline__ int jacobi_partner(int lane, int r, int n2) {
 // omega_b = sqrt(#T_t) / ||S_b||_F (block-relative reading).  Column side:
 // S_b instead of S_b^* and col(s).  Cluster lists encode side << 30 | id.
 template <int NW>
-__global__ void __launch_bounds__(128) k_blockweights(MatView M, const int32_t* __restrict__ list, int n,
+__global__ void __launch_bounds__(32 * kTW) k_blockweights(MatView M, const int32_t* __restrict__ list, int n,
                                                      BlockLists BL, BaseWeights BW, int* err) {
   extern __shared__ double smem[];
   Team<NW> tm;
@@ -304,7 +331,7 @@ __global__ void __launch_bounds__(128) k_blockweights(MatView M, const int32_t* 
 }
 
 template <int NW>
-__global__ void __launch_bounds__(128) k_baseweights(MatView M, const int32_t* __restrict__ list, int n,
+__global__ void __launch_bounds__(32 * kTW) k_baseweights(MatView M, const int32_t* __restrict__ list, int n,
                                                     BaseWeights BW, int* err) {
   extern __shared__ double smem[];
   Team<NW> tm;
@@ -353,7 +380,7 @@ __global__ void __launch_bounds__(128) k_baseweights(MatView M, const int32_t* _
 // Basis R-factors bottom-up: leaf qr_R((V_t, F|_t)); inner
 // qr_R([R_{t1} E~_{t1}; R_{t2} E~_{t2}]) with E~ = diag(E, I_u).
 template <int NW>
-__global__ void __launch_bounds__(128) k_rfactor(MatView M, const Item* __restrict__ items,
+__global__ void __launch_bounds__(32 * kTW) k_rfactor(MatView M, const Item* __restrict__ items,
                                                 const int32_t* __restrict__ list, int n, int u,
                                                 const double* __restrict__ A, const double* __restrict__ B,
                                                 ItemBuffers IB, int* err) {
@@ -492,7 +519,7 @@ __device__ __forceinline__ bool basis_orthonormal(const double* Rown, int k, int
 }
 
 template <int NW>
-__global__ void __launch_bounds__(128) k_outside(MatView M, const Item* __restrict__ items,
+__global__ void __launch_bounds__(32 * kTW) k_outside(MatView M, const Item* __restrict__ items,
                                                 const Entry* __restrict__ ents, const int32_t* __restrict__ list,
                                                 int n, int u, ItemBuffers IB) {
   extern __shared__ double smem[];
@@ -558,7 +585,7 @@ __global__ void __launch_bounds__(128) k_outside(MatView M, const Item* __restri
 }
 
 template <int NW>
-__global__ void __launch_bounds__(128) k_weights(MatView M, const Item* __restrict__ items,
+__global__ void __launch_bounds__(32 * kTW) k_weights(MatView M, const Item* __restrict__ items,
                                                 const Entry* __restrict__ ents, const int32_t* __restrict__ list,
                                                 int n, int u, BaseWeights BW, ItemBuffers IB, int* err) {
   extern __shared__ double smem[];
@@ -672,14 +699,14 @@ __global__ void __launch_bounds__(128) k_weights(MatView M, const Item* __restri
 // subtree root commits E_t0 <- R_t0 [E_t0; 0] (Eqs. (Qt_condensed),
 // (hatQt_condensed)).
 //
-// A task runs on a team (one warp, or a block of four).  Lane c owns column
+// A task runs on a team (one warp, or a block of kTW).  Lane c owns column
 // c.  Virtual warp w owns the rows i of the tall matrices with
-// (i / 2) mod 4 = w (two of every eight, see trow), register slot (v, h) of
+// (i / 2) mod kTW = w (two of every 2 kTW, see trow), register slot (v, h) of
 // a warp holding row trow(h, vw(v)); the K x K products are split by their
 // output rows over the warps of the team.
 
 // row of the tall matrices held in slot h of virtual warp w
-__device__ __forceinline__ int trow(int h, int w) { return 8 * (h >> 1) + 2 * w + (h & 1); }
+__device__ __forceinline__ int trow(int h, int w) { return 2 * kTW * (h >> 1) + 2 * w + (h & 1); }
 
 // One-sided (Hestenes) Jacobi on the K columns (a[v][h]: the team's rows,
 // zero beyond `rows`): on return the columns are U Sigma, mutually
@@ -709,7 +736,7 @@ __device__ __forceinline__ void jacobi_t(double (&a)[Team<NW>::VW][RW], int rows
         double x1 = 0.0, y1 = 0.0, g1 = 0.0;
 #pragma unroll
         for (int h = 0; h < RW / 2; ++h)
-          if (8 * h + 2 * w < rows) {
+          if (trow(2 * h, w) < rows) {
             const double r0 = a[v][2 * h], r1 = a[v][2 * h + 1];
             const double got = __shfl_sync(kFull, lo ? r1 : r0, p);
             const double xx = lo ? r0 : got;
@@ -777,10 +804,10 @@ __device__ __forceinline__ void jacobi_t(double (&a)[Team<NW>::VW][RW], int rows
 
 // Float32 one-sided Jacobi used as a preconditioner: rotates the float copy
 // af of the columns until they are orthogonal to float accuracy and
-// accumulates the rotations in V (vf[v][jj] = V[4 jj + vw(v)][lane]), so
+// accumulates the rotations in V (vf[v][jj] = V[kTW jj + vw(v)][lane]), so
 // that M V has nearly orthogonal columns.
 template <int RW, int NW>
-__device__ __forceinline__ void jacobi32_t(float (&af)[Team<NW>::VW][RW], float (&vf)[Team<NW>::VW][8], int rows,
+__device__ __forceinline__ void jacobi32_t(float (&af)[Team<NW>::VW][RW], float (&vf)[Team<NW>::VW][32 / kTW], int rows,
                                            int ncol, Team<NW>& tm) {
   constexpr int VW = Team<NW>::VW;
   const int lane = tm.lane;
@@ -832,8 +859,8 @@ __device__ __forceinline__ void jacobi32_t(float (&af)[Team<NW>::VW][RW], float 
               if (rot) af[v][h] = lo ? fmaf(c, af[v][h], -s * o) : fmaf(s, o, c * af[v][h]);
             }
 #pragma unroll
-          for (int jj = 0; jj < 8; ++jj)
-            if (4 * jj + tm.vw(v) < ncol) {
+          for (int jj = 0; jj < 32 / kTW; ++jj)
+            if (kTW * jj + tm.vw(v) < ncol) {
               const float o = __shfl_sync(kFull, vf[v][jj], p);
               if (rot) vf[v][jj] = lo ? fmaf(c, vf[v][jj], -s * o) : fmaf(s, o, c * vf[v][jj]);
             }
@@ -1059,14 +1086,14 @@ __device__ __forceinline__ bool polish_t(double* X, int ldx, double (&xr)[Team<N
 
 // Shared memory of one truncation task (doubles): V^ and Q (ld MR + 1, kl
 // columns each), two K x K tiles (ld ldg), 32 reciprocal pivots and, for a
-// four-warp team, the sum buffers.
+// kTW-warp team, the sum buffers.
 __host__ __device__ constexpr int trunc_ldg(int kl) { return (kl + 1) | 1; }
 __host__ __device__ constexpr size_t trunc_doubles(int mr, int kl, int nw) {
-  return 2 * (size_t)(mr + 1) * kl + 2 * (size_t)kl * trunc_ldg(kl) + 32 + (nw > 1 ? 768 : 0);
+  return 2 * (size_t)(mr + 1) * kl + 2 * (size_t)kl * trunc_ldg(kl) + 32 + (nw > 1 ? 2 * 96 * kTW : 0);
 }
 
 template <int MR, int NW>
-__global__ void __launch_bounds__(128) k_truncate(MatView M, const Item* __restrict__ items,
+__global__ void __launch_bounds__(32 * kTW) k_truncate(MatView M, const Item* __restrict__ items,
                                                  const int32_t* __restrict__ list, int n, int u, int kl, double eps,
                                                  const double* __restrict__ A, const double* __restrict__ B,
                                                  ItemBuffers IB, int* err) {
@@ -1227,20 +1254,20 @@ __global__ void __launch_bounds__(128) k_truncate(MatView M, const Item* __restr
     if (K >= 2 && rows > 0) {
       store_rows();
       float af[VW][RW];
-      float vf[VW][8];
+      float vf[VW][32 / kTW];
 #pragma unroll
       for (int v = 0; v < VW; ++v) {
 #pragma unroll
         for (int h = 0; h < RW; ++h) af[v][h] = (float)a[v][h];
 #pragma unroll
-        for (int jj = 0; jj < 8; ++jj) vf[v][jj] = (4 * jj + tm.vw(v) == lane) ? 1.f : 0.f;
+        for (int jj = 0; jj < 32 / kTW; ++jj) vf[v][jj] = (kTW * jj + tm.vw(v) == lane) ? 1.f : 0.f;
       }
       jacobi32_t<RW, NW>(af, vf, rows, K, tm);
 #pragma unroll
       for (int v = 0; v < VW; ++v)
 #pragma unroll
-        for (int jj = 0; jj < 8; ++jj) {
-          const int j = 4 * jj + tm.vw(v);
+        for (int jj = 0; jj < 32 / kTW; ++jj) {
+          const int j = kTW * jj + tm.vw(v);
           if (j < K && lane < K) Xs[j + lane * ldg] = (double)vf[v][jj];
         }
       tm.sync();
@@ -1593,11 +1620,11 @@ static int sm_count() {
   return sms;
 }
 
-// Four-warp teams while a launch holds at most kTW tasks per SM (every
+// kTW-warp teams while a launch holds at most four tasks per SM (every
 // task then has the float64 units of a whole SM, or a quarter at least);
 // one warp per task beyond, where the tasks fill the SMs anyway.  Both
 // forms compute the same bits.
-static bool wide_teams(int n) { return n <= kTW * sm_count(); }
+static bool wide_teams(int n) { return n <= 4 * sm_count(); }
 
 // Launch a fold kernel (template over the team width) for n tasks.
 #define H2_LAUNCH_FOLD(kern, n, stream, ...)                                                              \

@@ -202,3 +202,25 @@ def test_binding_rejects_short_host_buffers():
     finally:
         b.h2_batch_free(P)
         b.h2_matrix_free(Z)
+
+
+def test_stats_of_the_structure():
+    """h2_stats on a structure-only matrix: the counts of the oracle's trees,
+    rank 0 everywhere, device bytes of the empty storage, value bytes of the
+    nearfield alone."""
+    pts = synth.grid_points_2d(24)
+    Z = b.h2_matrix_create(None, pts, 16, 2.0, 0.0, 8)
+    try:
+        st = b.h2_stats(Z)
+    finally:
+        b.h2_matrix_free(Z)
+    ct = ClusterTree(pts, 16)
+    bt = BlockTree(ct, ct, 2.0)
+    assert st["n"] == len(pts) and st["n_clusters"] == ct.n_clusters and st["n_blocks"] == bt.n_blocks
+    assert st["n_admissible"] == len(bt.admissible) and st["n_inadmissible"] == len(bt.inadmissible)
+    assert st["depth"] == max(ct.level)
+    assert st["max_rank_rows"] == 0 and st["max_rank_cols"] == 0 and st["rank_sum_rows"] == 0
+    assert st["max_rank_per_level"] == [0] * (st["depth"] + 1)
+    near = sum(ct.size[bt.row[c]] * ct.size[bt.col[c]] for c in bt.inadmissible)
+    assert st["value_bytes"] == 8 * near
+    assert st["device_bytes"] == 0   # structure only: no device storage
