@@ -26,7 +26,10 @@ Readings of what the paper leaves open (also listed in the design notes):
 1. A product's terms are all computed from the matrix as it is when the
    product starts, then added in the order the recursion produces them (X
    and Y share bases with Z here, so an update of Z would otherwise change
-   the representation of later factors within the product).
+   the representation of later factors within the product).  The terms
+   for one target block that is not an inadmissible leaf are added
+   together: their factor pairs, in the recursion's order, form one factor
+   pair, added by one local update where the block's first term stands.
 2. Target (t, r) an admissible leaf while X and Y are subdivided: the
    sub-products go to temporaries (t', r'), t' in sons(t), r' in sons(r)
    (deeper sub-products are summed into their temporary exactly); each
@@ -245,9 +248,29 @@ def _mul(C: _Ctx, alpha, x, y, z, ZX=None, ZY=None):
     start); X, Y default to Z itself (the factorisation in place)."""
     out = []
     _collect(C.Z if ZX is None else ZX, C.Z if ZY is None else ZY, alpha, x, y, z, out)
+    bt = C.Z.blocks
+    groups = {}
+    for item in out:
+        if item[0] == "term" and bt.kind[item[1]] != BlockTree.NEAR:
+            groups.setdefault(item[1], []).append(item[3])
     for item in out:
         if item[0] == "term":
-            _apply_term(C, item[1], item[3])
+            z1 = item[1]
+            if bt.kind[z1] == BlockTree.NEAR:
+                _apply_term(C, z1, item[3])
+                continue
+            terms = groups.pop(z1, None)
+            if terms is None:        # added with the block's first term
+                continue
+            As, Bs = [], []
+            for term in terms:
+                if term[0] == "lr":
+                    A, B = term[1], term[2]
+                else:
+                    A, B = _factor_pair(term[1], term[2], term[3])
+                As.append(A)
+                Bs.append(B)
+            _apply_update(C, z1, np.hstack(As), np.hstack(Bs))
         else:
             z1, bucket = item[1], item[2]
             if not bucket:

@@ -14,7 +14,9 @@
 // Readings of what the paper leaves open (the same as the CPU oracle's):
 //  1. the terms of one product Z|_z += alpha X|_x Y|_y are all computed
 //     from the matrix as it is when the product starts, then added in the
-//     order the recursion produces them;
+//     order the recursion produces them; the terms for one target block
+//     that is not an inadmissible leaf are concatenated into one factor
+//     pair and added by one update where the block's first term stands;
 //  2. a target z that is an admissible leaf while X and Y are subdivided
 //     receives temporaries (t', r') for t' in sons(t), r' in sons(r): the
 //     terms below each are stacked into one factor pair, extended by zeros
@@ -738,19 +740,58 @@ void finish_temp(Lr& L, const Temp& tmp, TempWork& w, int rk) {
   apply_update(L, tmp.z, A2.p, w.mt, B2.p, w.mr, rk);
 }
 
+// The low-rank terms of a product for one target block that is not an
+// inadmissible leaf, concatenated in the recursion's order into one factor
+// pair and added by one local update (reading 1).
+void apply_terms(Lr& L, const std::vector<Item>& items, const std::vector<size_t>& idx) {
+  const Term& T0 = items[idx[0]].term;
+  if (idx.size() == 1) {
+    apply_term(L, T0);
+    return;
+  }
+  h2_matrix* Z = L.Z;
+  const int64_t mt = csize(Z, T0.tc), mr = csize(Z, T0.rc);
+  int u = 0;
+  for (size_t i : idx) u += items[i].term.u;
+  if (u == 0) return;
+  DArr A(mt * u, L.st), B(mr * u, L.st);
+  int c = 0;
+  for (size_t i : idx) {
+    const Term& T = items[i].term;
+    if (T.u == 0) continue;
+    H2_CUDA(cudaMemcpyAsync(A.p + (size_t)c * mt, T.A.p, mt * T.u * sizeof(double), cudaMemcpyDeviceToDevice, L.st));
+    H2_CUDA(cudaMemcpyAsync(B.p + (size_t)c * mr, T.B.p, mr * T.u * sizeof(double), cudaMemcpyDeviceToDevice, L.st));
+    c += T.u;
+  }
+  apply_update(L, T0.z, A.p, mt, B.p, mr, u);
+}
+
 void mul(Lr& L, double alpha, int32_t x, int32_t y, int32_t z) {
   std::vector<Item> items;
   {
     Timer tm(L.t_terms);
     collect(L, alpha, x, y, z, items);
   }
+  const BlockTree& bt = L.Z->blocks;
+  // the terms of each target block (not an inadmissible leaf), in order
+  std::map<int32_t, std::vector<size_t>> groups;
+  for (size_t i = 0; i < items.size(); ++i)
+    if (!items[i].temp && bt.kind[items[i].term.z] != kNear) groups[items[i].term.z].push_back(i);
   std::vector<TempWork> work(items.size());
   std::vector<int> ranks(items.size(), 0);
   compress_temps(L, items, work, ranks);
   for (size_t i = 0; i < items.size(); ++i) {
-    if (items[i].temp) finish_temp(L, items[i].tmp, work[i], ranks[i]);
-    else apply_term(L, items[i].term);
-    work[i] = TempWork();   // its scratch goes back to the stream-ordered pool
+    if (items[i].temp) {
+      finish_temp(L, items[i].tmp, work[i], ranks[i]);
+      work[i] = TempWork();   // its scratch goes back to the stream-ordered pool
+    } else if (bt.kind[items[i].term.z] == kNear) {
+      apply_term(L, items[i].term);
+    } else {
+      auto g = groups.find(items[i].term.z);
+      if (g == groups.end()) continue;   // added with the block's first term
+      apply_terms(L, items, g->second);
+      groups.erase(g);
+    }
   }
 }
 
