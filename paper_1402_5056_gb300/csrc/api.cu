@@ -808,6 +808,10 @@ struct h2_batch {
   std::vector<int32_t> lvl_maxrows;             // per level: bound on rows of the truncation
   std::vector<int32_t> lvl_leaves;              // per level: leaves (first in lvl_list)
   std::vector<int32_t> cl_list, cl_ptr;         // clusters of both sides by level (side << 30 | id)
+  // exact path, base weights B~ only for these clusters by level (empty:
+  // cl_list); the update engine computes them only where its cache of the
+  // unchanged matrix's weights is stale
+  std::vector<int32_t> bl_list, bl_ptr;
   int depth = 0;
   int kl = 0;                                   // max extended rank
   int64_t qlen = 0;
@@ -839,6 +843,7 @@ struct h2_batch {
   std::vector<int32_t> two;
   int32_t* d_lvl = nullptr;
   int32_t* d_cl = nullptr;
+  int32_t* d_bl = nullptr;
   ItemBuffers IB{};
   BaseWeights BW{};
   double* d_A = nullptr;   // staging for execute_host
@@ -1343,6 +1348,7 @@ void free_batch_device(h2_batch& P) {
   dfree(P.d_norms);
   dfree(P.d_lvl);
   dfree(P.d_cl);
+  dfree(P.d_bl);
   for (int sd = 0; sd < 2; ++sd) {
     dfree(P.BW.G[sd]);
     dfree(P.BW.B[sd]);
@@ -1405,6 +1411,8 @@ void execute(h2_ctx* ctx, h2_batch& P, const double* A, const double* B, double 
   pp.lvl_leaves = P.lvl_leaves.data();
   pp.cl_list = P.d_cl;
   pp.cl_ptr = P.cl_ptr.data();
+  pp.bl_list = P.bl_ptr.empty() ? nullptr : P.d_bl;
+  pp.bl_ptr = P.bl_ptr.empty() ? nullptr : P.bl_ptr.data();
   pp.levels = P.depth + 1;
   pp.n_updates = (int)P.count;
   pp.ncl[0] = Z->rows.count();
@@ -2272,7 +2280,13 @@ namespace h2 {
 struct UpdateEngine {
   h2_batch* P = nullptr;
   CommitScratch cs;
-  size_t c_items = 0, c_ents = 0, c_tasks = 0, c_two = 0, c_norms = 0, c_lvl = 0, c_cl = 0, c_q = 0;
+  size_t c_items = 0, c_ents = 0, c_tasks = 0, c_two = 0, c_norms = 0, c_lvl = 0, c_cl = 0, c_bl = 0, c_q = 0;
+  // The weights of the unchanged matrix kept between updates: G_t (the
+  // R-factor of the weighted blocks of t's block row) and B~_t (of the
+  // whole weight stack) of matrix wz stay in the device buffers and are
+  // valid where g_ok / b_ok is set.
+  const h2_matrix* wz = nullptr;
+  std::vector<uint8_t> g_ok[2], b_ok[2];
   size_t c_A = 0, c_B = 0;
   int32_t c_ncl[2] = {0, 0};
   int64_t updates = 0;
@@ -2319,6 +2333,37 @@ void zero_matrix(h2_ctx* ctx, h2_matrix* Z) {
 }
 
 UpdateEngine* engine_new() { return new UpdateEngine(); }
+
+void engine_touch(UpdateEngine* E, const h2_matrix* Z, int32_t b0) {
+  if (!E || E->wz != Z || E->g_ok[0].empty()) return;
+  const BlockTree& bt = Z->blocks;
+  const ClusterTree* tr[2] = {&Z->rows, &Z->cols};
+  const int32_t c0[2] = {bt.row[b0], bt.col[b0]};
+  std::vector<int32_t> dirty[2];
+  for (int sd = 0; sd < 2; ++sd) {
+    const ClusterTree& ct = *tr[sd];
+    // the subtree: its bases, transfers and every coupling of its block
+    // rows (columns) change
+    for (int32_t c = c0[sd]; c < c0[sd] + ct.subtree[c0[sd]]; ++c) dirty[sd].push_back(c);
+    // the other side's clusters of the blocks whose row (column) lies in
+    // the subtree: their couplings are reprojected
+    const std::vector<int32_t>& ptr = sd == 0 ? bt.row_ptr : bt.col_ptr;
+    const std::vector<int32_t>& adm = sd == 0 ? bt.row_adm : bt.col_adm;
+    for (int32_t c = c0[sd]; c < c0[sd] + ct.subtree[c0[sd]]; ++c)
+      for (int32_t e = ptr[c]; e < ptr[c + 1]; ++e) {
+        const int32_t b = bt.adm[adm[e]];
+        dirty[1 - sd].push_back(sd == 0 ? bt.col[b] : bt.row[b]);
+      }
+  }
+  for (int sd = 0; sd < 2; ++sd) {
+    const ClusterTree& ct = *tr[sd];
+    for (int32_t c : dirty[sd]) {
+      E->g_ok[sd][c] = 0;
+      // B~ of c and of everything below it depends on G_c
+      for (int32_t d = c; d < c + ct.subtree[c]; ++d) E->b_ok[sd][d] = 0;
+    }
+  }
+}
 
 void engine_delete(UpdateEngine* E) {
   if (!E) return;
@@ -2377,23 +2422,42 @@ void engine_update(h2_ctx* ctx, h2_matrix* Z, UpdateEngine* E, int32_t block, in
   P.mode = H2_MODE_EXACT;
   const auto c1 = clk::now();
   E->plan_s += std::chrono::duration<double>(c1 - c0).count();
-  // the weights of the unchanged matrix: only the clusters of the subtrees
-  // and their ancestors, by level
+  // the weights of the unchanged matrix the update reads, only where the
+  // cache lacks them: G_t of the subtrees' clusters, B~ of the ancestors
+  // (the subtree root's father and up), and G of an ancestor whose B~ is
+  // recomputed
   {
+    if (E->wz != Z || E->g_ok[0].size() != (size_t)tr[0]->count() ||
+        E->g_ok[1].size() != (size_t)tr[1]->count()) {
+      for (int sd = 0; sd < 2; ++sd) {
+        E->g_ok[sd].assign(tr[sd]->count(), 0);
+        E->b_ok[sd].assign(tr[sd]->count(), 0);
+      }
+      E->wz = Z;
+    }
     const int L = P.depth + 1;
-    std::vector<std::vector<int32_t>> by(L);
+    std::vector<std::vector<int32_t>> gby(L), bby(L);
     for (int sd = 0; sd < 2; ++sd) {
       const ClusterTree& ct = *tr[sd];
       const int32_t root = sd == 0 ? bt.row[block] : bt.col[block];
-      for (int32_t c = root; c < root + ct.subtree[root]; ++c) by[ct.level[c]].push_back((sd << 30) | c);
-      for (int32_t a = ct.father[root]; a >= 0; a = ct.father[a]) by[ct.level[a]].push_back((sd << 30) | a);
+      for (int32_t c = root; c < root + ct.subtree[root]; ++c)
+        if (!E->g_ok[sd][c]) gby[ct.level[c]].push_back((sd << 30) | c);
+      for (int32_t a = ct.father[root]; a >= 0; a = ct.father[a])
+        if (!E->b_ok[sd][a]) {
+          bby[ct.level[a]].push_back((sd << 30) | a);
+          if (!E->g_ok[sd][a]) gby[ct.level[a]].push_back((sd << 30) | a);
+        }
     }
-    P.cl_ptr.assign(L + 1, 0);
-    P.cl_list.clear();
-    for (int l = 0; l < L; ++l) {
-      P.cl_list.insert(P.cl_list.end(), by[l].begin(), by[l].end());
-      P.cl_ptr[l + 1] = (int32_t)P.cl_list.size();
-    }
+    auto flatten = [&](std::vector<std::vector<int32_t>>& by, std::vector<int32_t>& list, std::vector<int32_t>& ptr) {
+      ptr.assign(L + 1, 0);
+      list.clear();
+      for (int l = 0; l < L; ++l) {
+        list.insert(list.end(), by[l].begin(), by[l].end());
+        ptr[l + 1] = (int32_t)list.size();
+      }
+    };
+    flatten(gby, P.cl_list, P.cl_ptr);
+    flatten(bby, P.bl_list, P.bl_ptr);
   }
   // device buffers
   const size_t ni = P.items.size(), nt = P.tasks.size();
@@ -2436,6 +2500,7 @@ void engine_update(h2_ctx* ctx, h2_matrix* Z, UpdateEngine* E, int32_t block, in
   }
   ensure(P.d_lvl, E->c_lvl, P.lvl_list.size());
   ensure(P.d_cl, E->c_cl, P.cl_list.size());
+  ensure(P.d_bl, E->c_bl, P.bl_list.size());
   ensure(P.IB.Q, E->c_q, (size_t)P.qlen);
   for (int sd = 0; sd < 2; ++sd) {
     const int32_t ncl = tr[sd]->count();
@@ -2462,6 +2527,7 @@ void engine_update(h2_ctx* ctx, h2_matrix* Z, UpdateEngine* E, int32_t block, in
   put(P.d_norms, P.norms, st);
   put(P.d_lvl, P.lvl_list, st);
   put(P.d_cl, P.cl_list, st);
+  put(P.d_bl, P.bl_list, st);
   if (ni) H2_CUDA(cudaMemsetAsync(P.IB.jac, 0, 4 * ni * sizeof(unsigned long long), st));
   // the factors with leading dimension = rows
   ensure(P.d_A, E->c_A, (size_t)P.lenA);
@@ -2482,6 +2548,10 @@ void engine_update(h2_ctx* ctx, h2_matrix* Z, UpdateEngine* E, int32_t block, in
   // the commit reads the new ranks back (one synchronisation); its copies
   // stay in flight on the context's stream
   commit_update(ctx, &P, 0, P.d_A, P.d_B, Z, &E->cs);
+  // what this update computed is cached; what it changed is stale
+  for (int32_t e : P.cl_list) E->g_ok[e >> 30][e & 0x3fffffff] = 1;
+  for (int32_t e : P.bl_list) E->b_ok[e >> 30][e & 0x3fffffff] = 1;
+  engine_touch(E, Z, block);
   ++E->updates;
   E->total_s += std::chrono::duration<double>(clk::now() - c0).count();
 }

@@ -873,6 +873,7 @@ void lsolve(Lr& L, int32_t d, int32_t x) {
       lsolve_dense(L, d, Xh.p, mt, ls);
       expand(L, L.Z, 1, s, Ws.p, ms);
     }
+    engine_touch(L.eng, Z, x);   // a coupling written outside the update engine
     H2_CUDA(cudaMemsetAsync(coupling_ptr(Z, x), 0, (size_t)Z->kcap * Z->kcap * sizeof(double), L.st));
     apply_update(L, x, Xh.p, mt, Ws.p, ms, ls);
     return;
@@ -910,6 +911,7 @@ void rsolve(Lr& L, int32_t d, int32_t x) {
       rsolve_dense_t(L, d, Bh.p, ms, kt);
       expand(L, L.Z, 0, t, Vt.p, mt);
     }
+    engine_touch(L.eng, Z, x);   // a coupling written outside the update engine
     H2_CUDA(cudaMemsetAsync(coupling_ptr(Z, x), 0, (size_t)Z->kcap * Z->kcap * sizeof(double), L.st));
     apply_update(L, x, Vt.p, mt, Bh.p, ms, kt);
     return;

@@ -1792,10 +1792,12 @@ void run_pipeline(const Pipeline& P) {
     H2_LAUNCH_FOLD(k_blockweights, ncl, bs, P.M, P.cl_list, ncl, P.BL, P.BW, P.err);
     ++pl[H2_PHASE_EXACT];
   }
+  const int32_t* bl = P.bl_ptr ? P.bl_list : P.cl_list;
+  const int32_t* bp = P.bl_ptr ? P.bl_ptr : P.cl_ptr;
   for (int l = 0; l < L; ++l) {
-    const int n = P.cl_ptr[l + 1] - P.cl_ptr[l];
+    const int n = bp[l + 1] - bp[l];
     if (!n) continue;
-    H2_LAUNCH_FOLD(k_baseweights, n, bs, P.M, P.cl_list + P.cl_ptr[l], n, P.BW, P.err);
+    H2_LAUNCH_FOLD(k_baseweights, n, bs, P.M, bl + bp[l], n, P.BW, P.err);
     ++pl[H2_PHASE_EXACT];
   }
   if (P.side) H2_CUDA(cudaEventRecord(P.join, P.side));

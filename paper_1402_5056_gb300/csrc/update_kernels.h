@@ -47,6 +47,9 @@ struct Pipeline {
   const int32_t* lvl_leaves;    // host, per level: number of leaves (they come first in lvl_list)
   const int32_t* cl_list;       // all clusters of both sides sorted by level (side << 30 | id)
   const int32_t* cl_ptr;        // host, levels + 1 entries
+  // exact path: base weights only for these clusters by level (null: cl_list)
+  const int32_t* bl_list = nullptr;
+  const int32_t* bl_ptr = nullptr;   // host, levels + 1 entries
   int levels;
   int n_updates;
   int ncl[2];                   // clusters per side
