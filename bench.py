@@ -356,6 +356,41 @@ def lr_measure(b, ctx, cells_list, reps: int, oracle_cells):
     return out
 
 
+def lr_batch_measure(b, ctx, count: int, lo: int, hi: int):
+    """A batch of independent 2D FEM problems of uneven sizes (cells per
+    side uniform in lo..hi, 4 x 4 checkerboards, seeded): factorised one after
+    the other (h2_lr_factor) and side by side (h2_lr_factor_many, one host
+    thread and stream per problem in flight); factorisations per second of
+    both, and whether the results agree (update counts)."""
+    import torch
+    rng = np.random.default_rng(synth.SEED_BASE + 4)
+    cells = [int(c) for c in rng.integers(lo, hi + 1, count)]
+    sigmas = [synth.checker_sigma(np.random.default_rng(synth.SEED_BASE + 400 + i), 4, 2) for i in range(count)]
+    opt = b.options(eps=LR_EPS, eta=2.0, leaf_size=32)
+    build = lambda: [b.h2_build_fem(ctx, 2, c, 4, sg, opt) for c, sg in zip(cells, sigmas)]
+    Zs = build()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    one = [b.h2_lr_factor(ctx, Z, opt) for Z in Zs]
+    torch.cuda.synchronize()
+    seq = time.perf_counter() - t0
+    for Z in Zs:
+        b.h2_matrix_free(Z)
+    Zs = build()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    many = b.h2_lr_factor_many(ctx, Zs, opt, threads=count)
+    torch.cuda.synchronize()
+    par = time.perf_counter() - t0
+    for Z in Zs:
+        b.h2_matrix_free(Z)
+    return {"problems": count, "cells": cells, "n": [(c - 1) ** 2 for c in cells], "eps": LR_EPS,
+            "one_at_a_time_s": seq, "side_by_side_s": par,
+            "factorisations_per_s": {"one_at_a_time": count / seq, "side_by_side": count / par},
+            "speedup": seq / par,
+            "same_update_counts": [o["updates"] for o in one] == [m["updates"] for m in many]}
+
+
 def inverse_measure(b, ctx, cells_list, oracle_cells):
     """Approximate inverse of the 2D FEM matrix (h2_inverse, block Gauss
     elimination): setup wall time, CG steps to 1e-10 preconditioned by the
@@ -459,6 +494,8 @@ def main():
     ap.add_argument("--lr-cells", default="32,64",
                     help="comma-separated cells per side of the 2D FEM H2-LR problems to time ('' for none)")
     ap.add_argument("--lr-reps", type=int, default=3)
+    ap.add_argument("--batch-problems", type=int, default=16,
+                    help="independent FEM problems of the uneven batch (0: none)")
     ap.add_argument("--inv-cells", default="32",
                     help="comma-separated cells per side of the 2D FEM approximate inverses to time ('' for none)")
     ap.add_argument("--cpu-procs", type=int, default=0, help="host processes of the CPU baseline (0: all cores)")
@@ -669,6 +706,9 @@ def main():
     cells_list = [int(x) for x in args.lr_cells.split(",") if x.strip()]
     if rank == 0 and world == 1 and cells_list:
         lr = lr_measure(b, ctx, cells_list, args.lr_reps, oracle_cells={32})
+    lr_batch = None
+    if rank == 0 and world == 1 and args.batch_problems > 0:
+        lr_batch = lr_batch_measure(b, ctx, args.batch_problems, 24, 48)
     inv = None
     inv_cells = [int(x) for x in args.inv_cells.split(",") if x.strip()]
     if rank == 0 and world == 1 and inv_cells:
@@ -701,7 +741,7 @@ def main():
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "e2e_compact": e2e_compact,
             "gpu_launches": stats["launches"] * args.steps,
             "clocks": clocks, "phases": phases, "phases_serial": phases_serial, "exact_mode": exact_mode,
-            "matvec": mv, "lr": lr, "inverse": inv,
+            "matvec": mv, "lr": lr, "lr_batch": lr_batch, "inverse": inv,
             "gflop_per_step": stats["flops"] / 1e9}
     if rank == 0:
         print(json.dumps(line))

@@ -456,6 +456,19 @@ h2_status h2_lr_factor(h2_ctx* ctx, h2_matrix* Z, const h2_options* opt, int64_t
 h2_status h2_mul(h2_ctx* ctx, double alpha, const h2_matrix* X, int64_t bx, const h2_matrix* Y, int64_t by,
                  h2_matrix* Z, int64_t bz, double eps, int64_t* updates);
 
+/* h2_lr_factor of count independent matrices at once (Section 3 for each;
+ * batches of problems of different sizes): `threads` host threads (0: one
+ * per hardware thread, at most count) take the matrices in turn, each on a
+ * stream and context of its own on ctx's device, so that the few-task
+ * launches of the factorisations run side by side.  Every result equals
+ * h2_lr_factor of that matrix alone.  The matrices must be distinct; ctx's
+ * stream is synchronized first.  stats (host, 3 entries per matrix, or
+ * NULL): local updates, product terms, largest rank.  Synchronizes; on
+ * failure the status of the first failing matrix (in index order) with its
+ * index in the message, the other matrices factorised or not. */
+h2_status h2_lr_factor_many(h2_ctx* ctx, h2_matrix* const* Z, int64_t count, const h2_options* opt, int threads,
+                            int64_t* stats);
+
 /* X <- R^-1 L^-1 X for a factor from h2_lr_factor: block forward and
  * backward substitution (Section 3).  X: DEVICE n x nrhs, column-major, ld
  * ldx, rows in TREE order.  Synchronizes. */

@@ -1610,13 +1610,16 @@ static constexpr int kWarps = 4;
 static int blocks_for(int n) { return (n + kWarps - 1) / kWarps; }
 
 static int sm_count() {
-  static int cached[64] = {};
+  static std::atomic<int> cached[64];   // host threads may ask at once
   int dev = 0;
   H2_CUDA(cudaGetDevice(&dev));
-  if (dev >= 0 && dev < 64 && cached[dev]) return cached[dev];
+  if (dev >= 0 && dev < 64) {
+    const int c = cached[dev].load(std::memory_order_relaxed);
+    if (c) return c;
+  }
   int sms = 0;
   H2_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  if (dev >= 0 && dev < 64) cached[dev] = sms;
+  if (dev >= 0 && dev < 64) cached[dev].store(sms, std::memory_order_relaxed);
   return sms;
 }
 
