@@ -70,7 +70,7 @@ void launch_leaf_lu(double* A, int m, int64_t lda, int* err, cudaStream_t st);
 //   kind 1: X <- R^-1 X  (R upper with the diagonal in F, X m x n)
 //   kind 2: X <- X R^-1  (X n x m)
 void launch_trsm(int kind, const double* F, int m, int64_t ldf, double* X, int n, int64_t ldx, cudaStream_t st);
-// Truncation of a factor pair (A mt x m, B mr x m, m <= 256): Householder
+// Truncation of a factor pair (A mt x m, B mr x m, m <= kCompressMax): Householder
 // QR of both in place, the SVD of the core R_A R_B^* by one-sided Jacobi
 // and the rank rule, then A' = Q_A [U_r Sigma_r; 0], B' = Q_B [W_r; 0].
 // One temporary to truncate (device pointers): the factors A (ld mt) and B
@@ -96,7 +96,9 @@ void launch_compress_batch(const Compress* d, int n, int max_core_doubles, doubl
 void launch_apply_q(const double* A, int64_t lda, int rows_a, const double* tau_a, const double* TA, double* OA,
                     const double* B, int64_t ldb, int rows_b, const double* tau_b, const double* TB, double* OB,
                     int m, int r, cudaStream_t st);
-constexpr int kCompressMax = 256;
+// most columns a temporary may stack (the truncation kernels' per-column
+// shared arrays)
+constexpr int kCompressMax = 1024;
 // vectors of the conjugate gradients
 void launch_dot(const double* x, const double* y, int64_t n, double* partial, double* out, cudaStream_t st);
 void launch_axpby(int64_t n, double a, const double* x, double b, double* y, cudaStream_t st);

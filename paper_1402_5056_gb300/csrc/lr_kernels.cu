@@ -284,7 +284,7 @@ __global__ void k_axpby(int64_t n, double a, const double* x, double b, double* 
 }
 
 // ------------------------------------------------ factor-pair compression
-// Truncation of a factor pair (A, B) with m columns (m <= 256):
+// Truncation of a factor pair (A, B) with m columns (m <= kCompressMax):
 //  1. Householder QR of A (rows_a x m) and of B, in place, one thread block
 //     per factor: reflection j maps column j below the diagonal to zero
 //     (H = I - tau v v^*, v_j = 1, beta = -sign(alpha) ||x||, the form of
@@ -384,7 +384,7 @@ __device__ __forceinline__ int rr_partner(int i, int r, int n2, int& p, int& q) 
 // of the largest are at the rounding level of the product: they are not
 // rotated (rotating them need not converge, and they lie far below any
 // truncation threshold).  Rotate while |gamma| > 64 u sqrt(alpha beta): a
-// smaller threshold lies below the rounding of the dot products (up to 256
+// smaller threshold lies below the rounding of the dot products (up to 1024
 // terms) and the sweeps would not end.  nrm2 (cols) is scratch.
 __device__ __forceinline__ void jacobi_cols(double* X, int ldx, int rows, int cols, double* V, int ldv,
                                             double* nrm2) {
@@ -508,10 +508,10 @@ __device__ __forceinline__ void core_svd_one(const double* XA, int64_t lda, int 
                                              int kb, int m, double eps, const int* nonzero, double* Cg, double* Wg,
                                              double* TA, double* TB, int* rank, int in_smem) {
   extern __shared__ double csm[];
-  __shared__ int order[256];
-  __shared__ double nrm2[256];
-  __shared__ int perm[256];
-  __shared__ double tauc[256];
+  __shared__ int order[kCompressMax];
+  __shared__ double nrm2[kCompressMax];
+  __shared__ int perm[kCompressMax];
+  __shared__ double tauc[kCompressMax];
   __shared__ int sh_p, sh_piv;
   __shared__ double sh_beta, sh_tau, sh_scale, sh_delta2;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
