@@ -386,8 +386,15 @@ typedef enum { H2_FP64 = 0, H2_MIXED_FP32 = 1 } h2_precision;
  *  eta       admissibility parameter, max(diam t, diam s) <= eta dist(t, s);
  *  leaf_size clusters with more points are split;
  *  precision h2_precision;
- *  trunc_norm, weighting, max_rank: 0 (Frobenius norm, block-relative
- *            weights, no rank cap) -- the only supported values. */
+ *  trunc_norm, weighting: 0 (Frobenius norm, block-relative weights) --
+ *            the only supported values;
+ *  max_rank  0: no rank cap (the paper's method: the rank rule alone);
+ *            1..31: every local update of h2_lr_factor and h2_inverse
+ *            keeps at most max_rank columns per new cluster basis (its
+ *            leading singular directions), so that ranks stay within the
+ *            32-column limit of the update kernels on problems whose
+ *            ranks would exceed it.  The paper sets no cap; a cap changes
+ *            the result wherever it binds.  Other values: H2_EINVAL. */
 typedef struct {
   double eps;
   double eta;

@@ -18,7 +18,13 @@ leaves these open):
   floor(M * x_c) per axis, clamped to M - 1; the checker array is ordered
   x fastest;
 * the element matrix of a simplex e is sigma_e |e| G G^*, with G the
-  gradients of the barycentric coordinates (rows).
+  gradients of the barycentric coordinates (rows); an entry below 1e-12
+  of the element's largest diagonal entry is set to zero: its exact value
+  is zero (orthogonal gradients, the edge opposite a right angle), and the
+  gradients of rounded node coordinates only leave noise of ~1e-17 there,
+  which differs with the order of the arithmetic and, through the
+  block-relative truncation of the factorisation, would turn into rank-one
+  updates of rounding-level blocks.
 
 The H^2 form (Section 2): cluster tree of the interior nodes with support
 boxes (node box padded by h = 1/N per side), block tree with
@@ -79,6 +85,10 @@ def stiffness(N: int, dim: int, sigma: np.ndarray, M: int):
         idx = np.minimum((M * xc).astype(np.int64), M - 1)
         flat = idx[0] + M * idx[1] + (M * M * idx[2] if dim == 3 else 0)
         Ke = sigma[flat] * vol * (G @ G.T)
+        # an entry whose exact value is zero (two vertices whose gradients
+        # are orthogonal: the edge opposite a right angle) comes out of the
+        # rounded gradients as noise; it is zero
+        Ke[np.abs(Ke) <= 1e-12 * np.abs(np.diag(Ke)).max()] = 0.0
         glob = [sum(v[a] * nside ** a for a in range(dim)) for v in simplex]
         for a in range(dim + 1):
             for b in range(dim + 1):

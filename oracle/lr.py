@@ -65,9 +65,10 @@ from .update import apply_delta, local_update
 
 
 class _Ctx:
-    def __init__(self, Z, eps, cap):
+    def __init__(self, Z, eps, cap, rank_cap=None):
         self.Z = Z
         self.eps = float(eps)
+        self.rank_cap = rank_cap
         self.cap = cap
         self.updates = 0
         self.max_rank = 0
@@ -115,7 +116,7 @@ def _apply_update(C: _Ctx, b: int, A: np.ndarray, B: np.ndarray):
                 kmax = max(kmax, Z.W.rank[s])
             w = max(1, min(C.cap - 1, C.cap - kmax))
         w = min(w, u - j)
-        d = local_update(Z, b, A[:, j:j + w], B[:, j:j + w], C.eps)
+        d = local_update(Z, b, A[:, j:j + w], B[:, j:j + w], C.eps, max_rank=C.rank_cap)
         Z2 = apply_delta(Z, d)
         Z.V, Z.W, Z.S, Z.N = Z2.V, Z2.W, Z2.S, Z2.N
         C.updates += 1
@@ -400,10 +401,12 @@ def _lr(C: _Ctx, d):
     _lr(C, d22)
 
 
-def lr_factor(Z, eps: float, cap=32):
+def lr_factor(Z, eps: float, cap=32, rank_cap=None):
     """Factorise the H^2 matrix Z (square, same tree for rows and columns)
-    in place: on return Z holds L and R.  Returns statistics."""
-    C = _Ctx(Z, eps, cap)
+    in place: on return Z holds L and R.  ``rank_cap``: at most that many
+    columns per new cluster basis in every local update (the rank cap
+    option, off by default).  Returns statistics."""
+    C = _Ctx(Z, eps, cap, rank_cap)
     _lr(C, 0)
     return {"updates": C.updates, "max_rank": C.max_rank}
 
@@ -457,13 +460,13 @@ def power_error(apply_A, precond, n, iters=50, seed=0):
     return lam
 
 
-def mul(Z, X, Y, alpha: float, x: int, y: int, z: int, eps: float, cap=32):
+def mul(Z, X, Y, alpha: float, x: int, y: int, z: int, eps: float, cap=32, rank_cap=None):
     """The product of Section 3, Z|_z <- Z|_z + alpha X|_x Y|_y, for blocks
     x = (t, s), y = (s, r), z = (t, r) of the block tree the three H^2
     matrices share (X or Y may be Z itself); low-rank terms enter Z through
     local updates with accuracy eps.  Z is modified in place; returns the
     number of updates."""
-    C = _Ctx(Z, eps, cap)
+    C = _Ctx(Z, eps, cap, rank_cap)
     _mul(C, alpha, x, y, z, X, Y)
     return C.updates
 
@@ -508,21 +511,21 @@ def _inv(C: _Ctx, A, Cm, T, d):
     d11, d12 = _son(bt, d, t1, t1), _son(bt, d, t1, t2)
     d21, d22 = _son(bt, d, t2, t1), _son(bt, d, t2, t2)
     _inv(C, A, Cm, T, d11)                                    # C11 = A11^-1
-    C.updates += mul(T, Cm, A, 1.0, d11, d12, d12, C.eps, C.cap)    # B12 = A11^-1 A12
-    C.updates += mul(T, A, Cm, 1.0, d21, d11, d21, C.eps, C.cap)    # B21 = A21 A11^-1
-    C.updates += mul(A, A, T, -1.0, d21, d12, d22, C.eps, C.cap)    # S = A22 - A21 B12
+    C.updates += mul(T, Cm, A, 1.0, d11, d12, d12, C.eps, C.cap, C.rank_cap)    # B12 = A11^-1 A12
+    C.updates += mul(T, A, Cm, 1.0, d21, d11, d21, C.eps, C.cap, C.rank_cap)    # B21 = A21 A11^-1
+    C.updates += mul(A, A, T, -1.0, d21, d12, d22, C.eps, C.cap, C.rank_cap)    # S = A22 - A21 B12
     _inv(C, A, Cm, T, d22)                                    # C22 = S^-1
-    C.updates += mul(Cm, T, Cm, -1.0, d12, d22, d12, C.eps, C.cap)  # C12 = -B12 C22
-    C.updates += mul(Cm, Cm, T, -1.0, d22, d21, d21, C.eps, C.cap)  # C21 = -C22 B21
-    C.updates += mul(Cm, Cm, T, -1.0, d12, d21, d11, C.eps, C.cap)  # C11 = C11 - C12 B21
+    C.updates += mul(Cm, T, Cm, -1.0, d12, d22, d12, C.eps, C.cap, C.rank_cap)  # C12 = -B12 C22
+    C.updates += mul(Cm, Cm, T, -1.0, d22, d21, d21, C.eps, C.cap, C.rank_cap)  # C21 = -C22 B21
+    C.updates += mul(Cm, Cm, T, -1.0, d12, d21, d11, C.eps, C.cap, C.rank_cap)  # C11 = C11 - C12 B21
 
 
-def inverse(A, eps: float, cap=32):
+def inverse(A, eps: float, cap=32, rank_cap=None):
     """The approximate inverse of the square H^2 matrix A (Remark on
     inversion, reading 6) as a new H^2 matrix with A's trees; A is consumed
     (its lower right blocks hold Schur complements on return).  Returns the
     inverse and statistics."""
     Cm, T = zero_like(A), zero_like(A)
-    C = _Ctx(A, eps, cap)
+    C = _Ctx(A, eps, cap, rank_cap)
     _inv(C, A, Cm, T, 0)
     return Cm, {"updates": C.updates}

@@ -141,8 +141,11 @@ def extended_coupling(S: np.ndarray, t_in: bool, s_in: bool, u: int) -> np.ndarr
 
 
 def local_update(Z: H2Matrix, b0: int, A: np.ndarray, B: np.ndarray, eps: float,
-                 trace: dict | None = None) -> dict:
+                 trace: dict | None = None, max_rank: int | None = None) -> dict:
     """One local low-rank update; returns the delta without modifying Z.
+
+    ``max_rank`` (the rank cap option, off by default): every new cluster
+    basis keeps at most that many of its leading singular directions.
 
     The delta holds the new ranks, leaf bases and transfer matrices of the
     clusters in T_{t0} (row) and T_{s0} (column), the new coupling matrices
@@ -237,6 +240,8 @@ def local_update(Z: H2Matrix, b0: int, A: np.ndarray, B: np.ndarray, eps: float,
             else:
                 U, s_, _ = np.linalg.svd(M, full_matrices=False)
             r = rank_rule(s_, eps)
+            if max_rank is not None and max_rank > 0:
+                r = min(r, max_rank)
             Qh = U[:, :r]
             Rt[t] = Qh.T @ Vh
             rank[t] = r

@@ -502,8 +502,8 @@ def h2_debug_fail_allocation(n: int):
     _check(_lib.h2_debug_fail_allocation(int(n)))
 
 
-def options(eps=1e-4, eta=2.0, leaf_size=32, precision=0):
-    return Options(float(eps), float(eta), int(leaf_size), int(precision), 0, 0, 0)
+def options(eps=1e-4, eta=2.0, leaf_size=32, precision=0, max_rank=0):
+    return Options(float(eps), float(eta), int(leaf_size), int(precision), 0, 0, int(max_rank))
 
 
 def h2_build_fem(ctx, dim: int, cells: int, checker: int, sigma, opt):

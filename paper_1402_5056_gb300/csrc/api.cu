@@ -814,6 +814,7 @@ struct h2_batch {
   std::vector<int32_t> bl_list, bl_ptr;
   int depth = 0;
   int kl = 0;                                   // max extended rank
+  int max_rank = 0;                             // rank cap of the exact path's truncation (0: none)
   int64_t qlen = 0;
   // result packing (execute_host)
   std::vector<int64_t> res_task_off, res_item_off;
@@ -1426,6 +1427,7 @@ void execute(h2_ctx* ctx, h2_batch& P, const double* A, const double* B, double 
   pp.n_norms = (int)P.norms.size();
   pp.u = P.u;
   pp.kl = P.kl;
+  pp.max_rank = P.max_rank;
   pp.eps = eps;
   pp.A = A;
   pp.B = B;
@@ -2384,7 +2386,7 @@ void engine_times(const UpdateEngine* E, double* plan, double* launch, double* w
 }
 
 void engine_update(h2_ctx* ctx, h2_matrix* Z, UpdateEngine* E, int32_t block, int u, const double* A, int64_t lda,
-                   const double* B, int64_t ldb, double eps) {
+                   const double* B, int64_t ldb, double eps, int max_rank) {
   H2_REQUIRE(u >= 1 && u < kMaxCols, "update rank must be in 1..31");
   using clk = std::chrono::steady_clock;
   const auto c0 = clk::now();
@@ -2420,6 +2422,7 @@ void engine_update(h2_ctx* ctx, h2_matrix* Z, UpdateEngine* E, int32_t block, in
   P.norms.clear();
   plan_batch(P);
   P.mode = H2_MODE_EXACT;
+  P.max_rank = max_rank;
   const auto c1 = clk::now();
   E->plan_s += std::chrono::duration<double>(c1 - c0).count();
   // the weights of the unchanged matrix the update reads, only where the

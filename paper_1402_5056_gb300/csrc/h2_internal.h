@@ -110,16 +110,17 @@ int64_t engine_updates(const UpdateEngine* E);
 // seconds spent planning on the host, enqueueing the kernels, waiting for
 // the GPU before the commit, and in the whole calls
 void engine_times(const UpdateEngine* E, double* plan, double* launch, double* wait, double* total);
-// Z|_b <- trunc_eps(Z|_b + A B^*) in place (A: #t x u, ld lda; B: #s x u,
-// ld ldb; device); the new ranks are on the host on return, the device
-// work of the commit may still run on the context's stream.  Throws
-// h2::Error.
 // Z's block b0 is about to change, or has changed (an update of b0, or a
 // coupling written outside the engine): the engine's cached weights of the
 // clusters it affects are stale.  No effect for another matrix or a null E.
 void engine_touch(UpdateEngine* E, const h2_matrix* Z, int32_t b0);
+// Z|_b <- trunc_eps(Z|_b + A B^*) in place (A: #t x u, ld lda; B: #s x u,
+// ld ldb; device); the new ranks are on the host on return, the device
+// work of the commit may still run on the context's stream.  max_rank > 0:
+// every new basis keeps at most max_rank columns (0: the rank rule alone).
+// Throws h2::Error.
 void engine_update(h2_ctx* ctx, h2_matrix* Z, UpdateEngine* E, int32_t block, int u, const double* A, int64_t lda,
-                   const double* B, int64_t ldb, double eps);
+                   const double* B, int64_t ldb, double eps, int max_rank = 0);
 
 }  // namespace h2
 

@@ -129,6 +129,7 @@ struct Lr {
   const h2_matrix* X = nullptr;   // factors of the current product (nullptr: Z itself)
   const h2_matrix* Y = nullptr;
   double eps = 0.0;
+  int max_rank = 0;               // rank cap of every local update (0: none)
   cudaStream_t st = nullptr;
   int64_t updates = 0;
   int64_t products = 0;
@@ -423,7 +424,8 @@ void apply_update(Lr& L, int32_t b, const double* A, int64_t lda, const double* 
     for (int32_t c = s; c < s + Z->cols.subtree[s]; ++c) kmax = std::max(kmax, Z->W.rank[c]);
     const int w = std::min(std::min(kMaxCols - 1, std::max(1, kMaxCols - kmax)), u - j);
     if (!L.eng) L.eng = engine_new();
-    engine_update(L.ctx, Z, L.eng, b, w, A + (size_t)j * lda, lda, B + (size_t)j * ldb, ldb, L.eps);
+    engine_update(L.ctx, Z, L.eng, b, w, A + (size_t)j * lda, lda, B + (size_t)j * ldb, ldb, L.eps,
+                  L.max_rank);
     ++L.updates;
     j += w;
   }
@@ -669,7 +671,8 @@ void compress_temps(Lr& L, const std::vector<Item>& items, std::vector<TempWork>
     int m = 0;
     for (const Term& T : tmp.terms) m += T.u;
     if (m == 0) continue;
-    if (m > kCompressMax) throw Error(H2_EINTERNAL, "temporary of rank above 256");
+    if (m > kCompressMax)
+      throw Error(H2_EINTERNAL, "temporary stacking more than " + std::to_string(kCompressMax) + " columns");
     TempWork& w = work[i];
     w.mt = mt;
     w.mr = mr;
@@ -1006,7 +1009,8 @@ void check_square(const h2_matrix* Z) {
 // split into two triangles along its (i,j)-(i+1,j+1) diagonal (2D) or into
 // Kuhn's six tetrahedra around its main diagonal (3D); the element matrix
 // of a simplex e is sigma_e |e| G G^* with G the gradients of its
-// barycentric coordinates; interior nodes numbered x fastest.
+// barycentric coordinates, its entries below 1e-12 of its largest diagonal
+// entry set to zero (their exact value); interior nodes numbered x fastest.
 struct Csr {
   int64_t n = 0;
   std::vector<int64_t> ptr;
@@ -1110,13 +1114,23 @@ Csr fem_stiffness(int dim, int64_t N, int64_t M, const double* sigma, std::vecto
         mulp *= M;
       }
       const double sg = sigma[flat] * vol;
+      double Ke[4][4], dmax = 0.0;
+      for (int a = 0; a <= dim; ++a)
+        for (int c = 0; c <= dim; ++c) {
+          double g = 0.0;
+          for (int q = 0; q < dim; ++q) g += G[a][q] * G[c][q];
+          Ke[a][c] = sg * g;
+          if (a == c) dmax = std::max(dmax, std::fabs(Ke[a][a]));
+        }
       for (int a = 0; a <= dim; ++a) {
         if (gl[a] < 0) continue;
         for (int c = 0; c <= dim; ++c) {
           if (gl[c] < 0) continue;
-          double g = 0.0;
-          for (int q = 0; q < dim; ++q) g += G[a][q] * G[c][q];
-          trip.push_back({gl[a], gl[c], sg * g});
+          // an entry whose exact value is zero (orthogonal gradients: the
+          // edge opposite a right angle) carries only the rounding of the
+          // gradients; it is zero
+          const double v = std::fabs(Ke[a][c]) <= 1e-12 * dmax ? 0.0 : Ke[a][c];
+          trip.push_back({gl[a], gl[c], v});
         }
       }
     }
@@ -1155,8 +1169,10 @@ void check_options(const h2_options* opt) {
   H2_REQUIRE(opt, "options missing");
   H2_REQUIRE(std::isfinite(opt->eps) && opt->eps >= 0, "eps must be finite and >= 0");
   H2_REQUIRE(opt->precision == H2_FP64, "only H2_FP64 is built");
-  H2_REQUIRE(opt->trunc_norm == 0 && opt->weighting == 0 && opt->max_rank == 0,
-             "trunc_norm, weighting and max_rank must be 0");
+  H2_REQUIRE(opt->trunc_norm == 0 && opt->weighting == 0, "trunc_norm and weighting must be 0");
+  // a basis of rank max_rank must leave room for one more column in the
+  // 32-column extended basis of the next update
+  H2_REQUIRE(opt->max_rank >= 0 && opt->max_rank <= 31, "max_rank must be in 0..31");
 }
 }  // namespace
 
@@ -1227,6 +1243,7 @@ extern "C" h2_status h2_lr_factor(h2_ctx* ctx, h2_matrix* Z, const h2_options* o
     L.ctx = ctx;
     L.Z = Z;
     L.eps = eps;
+    L.max_rank = opt->max_rank;
     L.st = ctx->stream;
     lr(L, 0);
     H2_CUDA(cudaStreamSynchronize(L.st));
@@ -1278,6 +1295,7 @@ extern "C" h2_status h2_inverse(h2_ctx* ctx, h2_matrix* A, const h2_options* opt
     L.ctx = ctx;
     L.Z = A;
     L.eps = opt->eps;
+    L.max_rank = opt->max_rank;
     L.st = ctx->stream;
     inv(L, A, C, T, 0);
     H2_CUDA(cudaStreamSynchronize(L.st));

@@ -1096,7 +1096,7 @@ template <int MR, int NW>
 __global__ void __launch_bounds__(32 * kTW) k_truncate(MatView M, const Item* __restrict__ items,
                                                  const int32_t* __restrict__ list, int n, int u, int kl, double eps,
                                                  const double* __restrict__ A, const double* __restrict__ B,
-                                                 ItemBuffers IB, int* err) {
+                                                 ItemBuffers IB, int* err, int cap) {
   constexpr int RW = MR / kTW;   // rows per virtual warp
   constexpr int LQ = MR + 1;     // leading dimension of V^ and Q in shared memory
   constexpr int VW = Team<NW>::VW;
@@ -1219,7 +1219,7 @@ __global__ void __launch_bounds__(32 * kTW) k_truncate(MatView M, const Item* __
   unsigned long long* cnt = IB.jac + 4 * (size_t)id;
   // certified full-rank path: M^* M - (tau + delta) I positive definite
   bool certified = false;
-  if (rows >= K && K >= 1) {
+  if (rows >= K && K >= 1 && (cap <= 0 || K <= cap)) {   // (a rank cap below K truncates)
     store_rows();
     gram_t(Qs, LQ, rows, K, Gs, ldg, tm);
     double trace = 0.0;
@@ -1314,7 +1314,8 @@ __global__ void __launch_bounds__(32 * kTW) k_truncate(MatView M, const Item* __
       const int op = __shfl_sync(kFull, pos, d);
       if (d < K && op >= pos) tail += o;
     }
-    const bool keep = lane < K && rows > 0 && tail > thr;
+    // the rank rule; with the rank cap option, at most cap columns
+    const bool keep = lane < K && rows > 0 && tail > thr && (cap <= 0 || pos < cap);
     r = __popc(__ballot_sync(kFull, keep));
     __syncwarp();   // the warp's rows of M are read before Q overwrites them
     if (keep) {
@@ -1654,31 +1655,31 @@ static int persistent_blocks(Kern kern, int threads, size_t smem, int need) {
 template <int MR>
 static void launch_truncate_mr(const MatView& M, const Item* items, const int32_t* list, int n, int u, int kl,
                                double eps, const double* A, const double* B, const ItemBuffers& IB, int* err,
-                               cudaStream_t st) {
+                               int cap, cudaStream_t st) {
   static std::atomic<unsigned long long> attr4{0}, attr1{0};
   if (wide_teams(n)) {
     // one block of kTW warps per task
     smem_limit(k_truncate<MR, kTW>, trunc_doubles(MR, kMaxCols, kTW) * sizeof(double), attr4);
     k_truncate<MR, kTW><<<n, 32 * kTW, trunc_doubles(MR, kl, kTW) * sizeof(double), st>>>(M, items, list, n, u,
-                                                                                           kl, eps, A, B, IB, err);
+                                                                                           kl, eps, A, B, IB, err, cap);
   } else {
     // one warp per task, two tasks per block
     constexpr int warps = 2;
     smem_limit(k_truncate<MR, 1>, warps * trunc_doubles(MR, kMaxCols, 1) * sizeof(double), attr1);
     k_truncate<MR, 1><<<(n + warps - 1) / warps, 32 * warps, warps * trunc_doubles(MR, kl, 1) * sizeof(double),
-                        st>>>(M, items, list, n, u, kl, eps, A, B, IB, err);
+                        st>>>(M, items, list, n, u, kl, eps, A, B, IB, err, cap);
   }
 }
 
 static void launch_truncate(const MatView& M, const Item* items, const int32_t* list, int n, int u, int kl,
                             int max_rows, double eps, const double* A, const double* B, const ItemBuffers& IB,
-                            int* err, cudaStream_t st) {
+                            int* err, int cap, cudaStream_t st) {
   if (max_rows <= 32)
-    launch_truncate_mr<32>(M, items, list, n, u, kl, eps, A, B, IB, err, st);
+    launch_truncate_mr<32>(M, items, list, n, u, kl, eps, A, B, IB, err, cap, st);
   else if (max_rows <= 48)
-    launch_truncate_mr<48>(M, items, list, n, u, kl, eps, A, B, IB, err, st);
+    launch_truncate_mr<48>(M, items, list, n, u, kl, eps, A, B, IB, err, cap, st);
   else
-    launch_truncate_mr<64>(M, items, list, n, u, kl, eps, A, B, IB, err, st);
+    launch_truncate_mr<64>(M, items, list, n, u, kl, eps, A, B, IB, err, cap, st);
 }
 
 void run_pipeline(const Pipeline& P) {
@@ -1829,7 +1830,7 @@ void run_pipeline(const Pipeline& P) {
     const int n = P.lvl_ptr[l + 1] - P.lvl_ptr[l];
     if (!n) continue;
     launch_truncate(P.M, P.items, P.lvl_list + P.lvl_ptr[l], n, P.u, P.kl, P.lvl_rows[l], P.eps, P.A, P.B, P.IB,
-                    P.err, st);
+                    P.err, P.max_rank, st);
     ++pl[H2_PHASE_EXACT];
   }
   stop(H2_PHASE_EXACT, st);

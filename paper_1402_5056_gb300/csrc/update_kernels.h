@@ -50,6 +50,7 @@ struct Pipeline {
   // exact path: base weights only for these clusters by level (null: cl_list)
   const int32_t* bl_list = nullptr;
   const int32_t* bl_ptr = nullptr;   // host, levels + 1 entries
+  int max_rank = 0;                  // exact path: rank cap of the truncation (0: none)
   int levels;
   int n_updates;
   int ncl[2];                   // clusters per side

@@ -29,6 +29,8 @@ def main(argv=None) -> dict:
     ap.add_argument("--eta", type=float, default=2.0)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--tol", type=float, default=1e-10, help="relative residual of CG")
+    ap.add_argument("--max-rank", type=int, default=0,
+                    help="rank cap of every local update (0: none, the paper's method)")
     args = ap.parse_args(argv)
 
     import torch
@@ -38,7 +40,7 @@ def main(argv=None) -> dict:
     sigma = 10.0 ** rng.uniform(-2.0, 2.0, args.checker * args.checker)
     torch.cuda.set_device(0)
     ctx = b.h2_ctx_create(0, torch.cuda.current_stream().cuda_stream)
-    opt = b.options(eps=args.eps, eta=args.eta, leaf_size=args.leaf)
+    opt = b.options(eps=args.eps, eta=args.eta, leaf_size=args.leaf, max_rank=args.max_rank)
     try:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -60,7 +62,7 @@ def main(argv=None) -> dict:
         t4 = time.perf_counter()
         v0 = torch.from_numpy(rng.standard_normal(n)).cuda()
         err = b.h2_lr_error(ctx, A, F, v0.data_ptr(), 20)
-        out = {"n": n, "cells": args.cells, "checker": args.checker, "eps": args.eps,
+        out = {"n": n, "cells": args.cells, "checker": args.checker, "eps": args.eps, "max_rank": args.max_rank,
                "build_s": t1 - t0, "factor_s": t2 - t1, "cg_iterations": it, "cg_relres": rr,
                "cg_s": t4 - t3, "err_power": err, "factor": info}
         b.h2_matrix_free(F)

@@ -187,3 +187,39 @@ def test_command_line_example():
     assert out["n"] == 23 * 23
     assert out["cg_relres"] <= 1e-10 and out["cg_iterations"] <= 6
     assert out["factor"]["updates"] > 0 and 0 < out["err_power"] < 1e-2
+
+
+@pytest.mark.parametrize("cap", [3, 6])
+def test_lr_with_rank_cap_matches_oracle(ctx, cap):
+    """The rank cap option (h2_options.max_rank, off by default; the paper
+    sets no cap): every new basis keeps at most ``cap`` leading singular
+    directions, on both sides, and the factor is still parity-equal."""
+    N, leaf, eps = 24, 16, 1e-6
+    sigma, K, Zo, _ = _problem(2, N, 4, synth.SEED_BASE + 60, leaf)
+    info_o = lr_factor(Zo, eps, rank_cap=cap)
+    opt = b.options(eps=eps, leaf_size=leaf, max_rank=cap)
+    Z = b.h2_build_fem(ctx, 2, N, 4, sigma, opt)
+    try:
+        info = b.h2_lr_factor(ctx, Z, opt)
+        got = to_oracle(ctx, Z, Zo)
+        assert info_o["max_rank"] == cap and info["max_rank"] == cap
+        assert list(got.V.rank) == list(Zo.V.rank) and list(got.W.rank) == list(Zo.W.rank)
+        assert info["updates"] == info_o["updates"]
+        R = Zo.dense()
+        bt, tr = Zo.blocks, Zo.V.tree
+        assert_blockwise_dense(got.dense(), R, bt, tr, tr, TOL, "capped factor", floor=1e-12 * np.linalg.norm(R))
+    finally:
+        b.h2_matrix_free(Z)
+
+
+def test_rank_cap_out_of_range_is_rejected(ctx):
+    sigma, K, Zo, _ = _problem(2, 12, 4, synth.SEED_BASE + 61, 8)
+    opt = b.options(eps=1e-4, leaf_size=8)
+    Z = b.h2_build_fem(ctx, 2, 12, 4, sigma, opt)
+    try:
+        for cap in (-1, 32):
+            with pytest.raises(b.H2Error) as e:
+                b.h2_lr_factor(ctx, Z, b.options(eps=1e-4, leaf_size=8, max_rank=cap))
+            assert e.value.status == 1
+    finally:
+        b.h2_matrix_free(Z)

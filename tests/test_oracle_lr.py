@@ -143,3 +143,23 @@ def test_power_error_closed_form():
     c = 2.5
     e = power_error(lambda v: d * v, lambda r: r / c, len(d), iters=400, seed=1)
     assert abs(e - np.max(np.abs(1 - d / c))) <= 1e-6
+
+
+def test_rank_cap():
+    """The rank cap option: no basis rank above it; a cap above every rank
+    the factorisation reaches changes nothing."""
+    Z, A = _fem(24, 16, seed=9)
+    Z1, Z2 = Z.copy(), Z.copy()
+    info = lr_factor(Z1, 1e-4)
+    top = info["max_rank"]
+    assert top > 4
+    lr_factor(Z2, 1e-4, rank_cap=top)
+    np.testing.assert_array_equal(Z1.dense(), Z2.dense())
+    Z3 = Z.copy()
+    info3 = lr_factor(Z3, 1e-4, rank_cap=4)
+    assert max(Z3.V.rank) <= 4 and max(Z3.W.rank) <= 4 and info3["max_rank"] == 4
+    # still a preconditioner, a weaker one
+    D = Z3.dense()
+    n = D.shape[0]
+    Lm, Rm = np.tril(D, -1) + np.eye(n), np.triu(D)
+    assert np.linalg.norm(A - Lm @ Rm) <= 1e-1 * np.linalg.norm(A)

@@ -207,11 +207,12 @@ def test_lr_pins_catch_mutation(name, tmp_path):
 
 INVERSE_MUTATIONS = {
     "off-diagonal block of the inverse with the wrong sign": (
-        "mul(Cm, T, Cm, -1.0, d12, d22, d12, C.eps, C.cap)", "mul(Cm, T, Cm, 1.0, d12, d22, d12, C.eps, C.cap)"),
+        "mul(Cm, T, Cm, -1.0, d12, d22, d12, C.eps, C.cap, C.rank_cap)",
+        "mul(Cm, T, Cm, 1.0, d12, d22, d12, C.eps, C.cap, C.rank_cap)"),
     "C11 without the correction C12 B21": (
-        "    C.updates += mul(Cm, Cm, T, -1.0, d12, d21, d11, C.eps, C.cap)  # C11 = C11 - C12 B21\n", ""),
+        "    C.updates += mul(Cm, Cm, T, -1.0, d12, d21, d11, C.eps, C.cap, C.rank_cap)  # C11 = C11 - C12 B21\n", ""),
     "Schur complement without the product A21 B12": (
-        "mul(A, A, T, -1.0, d21, d12, d22, C.eps, C.cap)", "0"),
+        "mul(A, A, T, -1.0, d21, d12, d22, C.eps, C.cap, C.rank_cap)", "0"),
     "leaf inverse without the backward solve": (
         "return solve_triangular(F, Y, lower=False)", "return Y"),
 }
