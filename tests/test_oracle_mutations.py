@@ -195,6 +195,8 @@ LR_MUTATIONS = {
     "forward substitution on an admissible leaf keeps the old coupling": (
         "Ws = Z.W.dense(s)\n        Z.S[x] = np.zeros_like(Z.S[x])", "Ws = Z.W.dense(s)"),
     "conjugate directions not conjugated": ("p = z + (rz_new / rz) * p", "p = z.copy()"),
+    "rank cap not passed to the local update": (
+        "C.eps, max_rank=C.rank_cap)", "C.eps, max_rank=None)"),
 }
 
 
@@ -222,4 +224,20 @@ INVERSE_MUTATIONS = {
 def test_inverse_pins_catch_mutation(name, tmp_path):
     before, after = INVERSE_MUTATIONS[name]
     failed, out = _pins_fail(tmp_path, "lr.py", before, after, ["test_oracle_inverse.py"])
+    assert failed, out
+
+
+FEM_MUTATIONS = {
+    "element entries up to 60% of the diagonal taken for noise": (
+        "Ke[np.abs(Ke) <= 1e-12 * np.abs(np.diag(Ke)).max()] = 0.0",
+        "Ke[np.abs(Ke) <= 0.6 * np.abs(np.diag(Ke)).max()] = 0.0"),
+    "element matrix without the coefficient": (
+        "Ke = sigma[flat] * vol * (G @ G.T)", "Ke = vol * (G @ G.T)"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(FEM_MUTATIONS))
+def test_fem_pins_catch_mutation(name, tmp_path):
+    before, after = FEM_MUTATIONS[name]
+    failed, out = _pins_fail(tmp_path, "fem.py", before, after, ["test_oracle_fem.py"])
     assert failed, out
