@@ -94,6 +94,9 @@ __global__ void k_mv_coupling(MatvecArgs a) {
         const int ls = a.rank[1][s];
         const double* S = a.S + (size_t)slot * kcap * kcap + i;
         const double* xs = a.xh + (size_t)s * kcap * a.nrhs + (size_t)r0 * kcap;
+        // unrolled: the loads of several columns in flight (the sums keep
+        // their order)
+#pragma unroll 8
         for (int q = 0; q < ls; ++q) {
           const double sv = S[q * kcap];
 #pragma unroll
@@ -190,6 +193,7 @@ __global__ void k_mv_leaves(MatvecArgs a) {
       double acc[RB];
 #pragma unroll
       for (int j = 0; j < RB; ++j) acc[j] = 0.0;
+#pragma unroll 8
       for (int i = 0; i < kt; ++i) {
         const double v = Vl[p + (size_t)i * m];
 #pragma unroll
@@ -206,6 +210,7 @@ __global__ void k_mv_leaves(MatvecArgs a) {
           const int ms = a.size[1][s];
           const double* Nb = a.N + a.near_off[x] + row;
           const double* X = a.X + a.off[1][s] + (size_t)r0 * a.ldx;
+#pragma unroll 8
           for (int q = 0; q < ms; ++q) {
             const double nv = Nb[(size_t)q * mc];
 #pragma unroll
