@@ -123,3 +123,26 @@ def test_inverse_rejects_a_negative_accuracy(ctx):
         assert e.value.status == 1
     finally:
         b.h2_matrix_free(A)
+
+
+def test_inverse_with_rank_cap_matches_oracle(ctx):
+    """The rank cap option in the inverse (16 x 16 cells, leaf 16,
+    eps 1e-4, cap 4, below the uncapped inverse's largest rank 6)."""
+    sigma, K, Zo, _ = _problem(16, synth.SEED_BASE + 71, 16)
+    Co, info_o = inverse(Zo.copy(), 1e-4, rank_cap=4)
+    opt = b.options(eps=1e-4, leaf_size=16, max_rank=4)
+    A = b.h2_build_fem(ctx, 2, 16, 4, sigma, opt)
+    try:
+        Cm, info = b.h2_inverse(ctx, A, opt)
+    finally:
+        b.h2_matrix_free(A)
+    try:
+        got = to_oracle(ctx, Cm, Co)
+        assert max(Co.V.rank) == 4
+        assert list(got.V.rank) == list(Co.V.rank) and list(got.W.rank) == list(Co.W.rank)
+        assert info["updates"] == info_o["updates"]
+        R = Co.dense()
+        bt, tr = Zo.blocks, Zo.V.tree
+        assert_blockwise_dense(got.dense(), R, bt, tr, tr, TOL, "capped inverse", floor=1e-12 * np.linalg.norm(R))
+    finally:
+        b.h2_matrix_free(Cm)

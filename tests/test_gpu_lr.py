@@ -223,3 +223,24 @@ def test_rank_cap_out_of_range_is_rejected(ctx):
             assert e.value.status == 1
     finally:
         b.h2_matrix_free(Z)
+
+
+def test_lr_3d_matches_oracle(ctx):
+    """The factorisation of a 3D problem (8^3 cells in Kuhn tetrahedra,
+    n = 343, sigma on a 2 x 2 x 2 checkerboard, leaf 16, eps 1e-4): per-block
+    parity with the oracle at 1e-10, equal ranks and update counts."""
+    N, M, leaf, eps = 8, 2, 16, 1e-4
+    sigma, K, Zo, _ = _problem(3, N, M, synth.SEED_BASE + 70, leaf)
+    info_o = lr_factor(Zo, eps)
+    Z = _lib(ctx, 3, N, M, sigma, leaf, eps)
+    try:
+        info = b.h2_lr_factor(ctx, Z, b.options(eps=eps, leaf_size=leaf))
+        got = to_oracle(ctx, Z, Zo)
+        assert info_o["max_rank"] > 0
+        assert list(got.V.rank) == list(Zo.V.rank) and list(got.W.rank) == list(Zo.W.rank)
+        assert info["updates"] == info_o["updates"]
+        R = Zo.dense()
+        bt, tr = Zo.blocks, Zo.V.tree
+        assert_blockwise_dense(got.dense(), R, bt, tr, tr, TOL, "3D factor", floor=1e-12 * np.linalg.norm(R))
+    finally:
+        b.h2_matrix_free(Z)
