@@ -241,3 +241,24 @@ def test_fem_pins_catch_mutation(name, tmp_path):
     before, after = FEM_MUTATIONS[name]
     failed, out = _pins_fail(tmp_path, "fem.py", before, after, ["test_oracle_fem.py"])
     assert failed, out
+
+
+CHOL_MUTATIONS = {
+    "Schur complement of the Cholesky added instead of subtracted": (
+        "_mul_t(C, -1.0, d21, d21, d22, lower=True)", "_mul_t(C, 1.0, d21, d21, d22, lower=True)"),
+    "right solve without the X1 L21^* term": (
+        "        _mul_t(C, -1.0, _son(bt, x, t1, s1), _son(bt, d, s2, s1), _son(bt, x, t1, s2), lower=False)\n",
+        "        pass\n"),
+    "transposed admissible factor with its coupling not transposed": (
+        'return ("lr", alpha * (Xt @ Z.S[yh].T), Z.V.dense(r))', 'return ("lr", alpha * (Xt @ Z.S[yh]), Z.V.dense(r))'),
+    "backward solve reading the upper block instead of the factor's transpose": (
+        "Y1 = Y[:n1] - Z.block_dense(_son(bt, d, t2, t1)).T @ X2",
+        "Y1 = Y[:n1] - Z.block_dense(_son(bt, d, t1, t2)) @ X2"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CHOL_MUTATIONS))
+def test_chol_pins_catch_mutation(name, tmp_path):
+    before, after = CHOL_MUTATIONS[name]
+    failed, out = _pins_fail(tmp_path, "chol.py", before, after, ["test_oracle_chol.py"])
+    assert failed, out
