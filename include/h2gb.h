@@ -516,6 +516,35 @@ h2_status h2_inverse(h2_ctx* ctx, h2_matrix* A, const h2_options* opt, h2_matrix
 h2_status h2_pcg_inverse(h2_ctx* ctx, const h2_matrix* A, const h2_matrix* C, const double* b, double* x, double tol,
                          int maxit, int* iterations, double* relres);
 
+/* Approximate Cholesky factorisation A ~ L L^* of a symmetric positive
+ * definite H^2 matrix in place (Section 7's preconditioner, built with the
+ * algorithms of Section 3): on a diagonal block with sons t1, t2,
+ * L11 = chol(A11) (recursively), L21 = A21 L11^-* (block substitution over
+ * the sons of the column cluster; an admissible leaf V_t S W_s^* becomes
+ * V_t (L^-1 W_s S^*)^*, added by one local update), A22 <- A22 - L21 L21^*
+ * (the product of Section 3 with its second factor read transposed, only
+ * the blocks on or below the diagonal of a diagonal target), L22 =
+ * chol(A22); a leaf by dense Cholesky, its strictly upper part zeroed.
+ * On return the lower triangle of Z (with the diagonal) holds L; the
+ * strictly upper nearfield is never read and the strictly upper admissible
+ * blocks hold no part of the factor.  Z must be square with one tree;
+ * opt as for h2_lr_factor (max_rank included).  stats (host, 3 entries,
+ * optional): local updates, product terms, largest rank.  Synchronizes;
+ * H2_EDEVICE if a leaf pivot is not positive (A not positive definite to
+ * the accuracy reached). */
+h2_status h2_chol_factor(h2_ctx* ctx, h2_matrix* Z, const h2_options* opt, int64_t* stats);
+
+/* X <- L^-* L^-1 X for a factor from h2_chol_factor (block forward and
+ * backward substitution with L and its transpose).  X: DEVICE n x nrhs,
+ * column-major, ld ldx, rows in TREE order.  Synchronizes. */
+h2_status h2_chol_solve(h2_ctx* ctx, const h2_matrix* F, int64_t nrhs, double* X, int64_t ldx);
+
+/* h2_pcg with the Cholesky factor F from h2_chol_factor as the
+ * preconditioner (z = L^-* L^-1 r: symmetric positive definite, so CG is
+ * the method it is built for); same arguments and results. */
+h2_status h2_pcg_chol(h2_ctx* ctx, const h2_matrix* A, const h2_matrix* F, const double* b, double* x, double tol,
+                      int maxit, int* iterations, double* relres);
+
 /* ----------------------------------------------------------- diagnostics */
 
 /* The float64 reciprocal the factorisation kernels use for their pivots

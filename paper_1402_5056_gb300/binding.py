@@ -35,7 +35,7 @@ EXPORTS = [
     "h2_lowrank_update_noalloc", "h2_lowrank_update_sequence", "h2_matvec", "h2_block_to_dense",
     "h2_sequence_waves", "h2_check_reciprocal", "h2_debug_fail_allocation",
     "h2_stats", "h2_build_fem", "h2_lr_factor", "h2_lr_factor_many", "h2_lr_solve", "h2_pcg", "h2_lr_error", "h2_mul", "h2_inverse",
-    "h2_pcg_inverse",
+    "h2_pcg_inverse", "h2_chol_factor", "h2_chol_solve", "h2_pcg_chol",
 ]
 
 PHASES = ("base_weights", "rfactor", "norms", "weights", "truncate", "reproject", "exact", "bases")
@@ -123,6 +123,9 @@ _sig("h2_inverse", _int, _p, _p, _p, _p, _p)
 _sig("h2_stats", _int, _p, _p, _p)
 _sig("h2_lr_factor_many", _int, _p, _p, _i64, _p, _int, _p)
 _sig("h2_pcg_inverse", _int, _p, _p, _p, _p, _p, _dbl, _int, _p, _p)
+_sig("h2_chol_factor", _int, _p, _p, C.POINTER(Options), _p)
+_sig("h2_chol_solve", _int, _p, _p, _i64, _p, _i64)
+_sig("h2_pcg_chol", _int, _p, _p, _p, _p, _p, _dbl, _int, _p, _p)
 _sig("h2_mul", _int, _p, _dbl, _p, _i64, _p, _i64, _p, _i64, _dbl, _p)
 _sig("h2_matvec", _int, _p, _p, _i64, _dbl, _p, _i64, _dbl, _p, _i64)
 _sig("h2_lowrank_update_sequence", _int, _p, _p, _i64, _p, _int, _p, _p, _dbl, _p)
@@ -584,6 +587,26 @@ def h2_pcg_inverse(ctx, A, Cinv, b_dev: int, x_dev: int, tol: float, maxit: int)
     rr = C.c_double()
     _check(_lib.h2_pcg_inverse(ctx, A, Cinv, C.c_void_p(b_dev), C.c_void_p(x_dev), float(tol), int(maxit),
                                C.byref(it), C.byref(rr)), ctx)
+    return it.value, rr.value
+
+
+def h2_chol_factor(ctx, Z, opt):
+    """In-place approximate Cholesky factorisation; returns counts and the largest rank."""
+    st = np.zeros(3, dtype=np.int64)
+    _check(_lib.h2_chol_factor(ctx, Z, C.byref(opt), st.ctypes.data), ctx)
+    return {"updates": int(st[0]), "products": int(st[1]), "max_rank": int(st[2])}
+
+
+def h2_chol_solve(ctx, F, nrhs: int, X_dev: int, ldx: int):
+    _check(_lib.h2_chol_solve(ctx, F, int(nrhs), C.c_void_p(X_dev), int(ldx)), ctx)
+
+
+def h2_pcg_chol(ctx, A, F, b_dev: int, x_dev: int, tol: float, maxit: int):
+    """CG preconditioned by the Cholesky factor; returns (iterations, relative residual)."""
+    it = C.c_int()
+    rr = C.c_double()
+    _check(_lib.h2_pcg_chol(ctx, A, F, C.c_void_p(b_dev), C.c_void_p(x_dev), float(tol), int(maxit),
+                            C.byref(it), C.byref(rr)), ctx)
     return it.value, rr.value
 
 

@@ -272,6 +272,7 @@ static void check_device_error(h2_ctx* ctx) {
     if (e & kErrJacobi) m += " one-sided Jacobi did not converge;";
     if (e & kErrRank) m += " inconsistent ranks;";
     if (e & kErrPivot) m += " zero pivot in a leaf LU;";
+    if (e & kErrDefinite) m += " pivot not positive in a leaf Cholesky (matrix not positive definite);";
     throw Error(H2_EDEVICE, m);
   }
 }

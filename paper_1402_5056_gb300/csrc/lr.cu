@@ -130,6 +130,8 @@ struct Lr {
   const h2_matrix* Y = nullptr;
   double eps = 0.0;
   int max_rank = 0;               // rank cap of every local update (0: none)
+  bool yt = false;       // the product's second factor is read transposed (Cholesky)
+  bool lower = false;    // a diagonal target gets only its son blocks on or below the diagonal
   cudaStream_t st = nullptr;
   int64_t updates = 0;
   int64_t products = 0;
@@ -457,8 +459,132 @@ DArr identity(Lr& L, int64_t n) {
   return I;
 }
 
+// the term alpha X|_x (Y|_yh)^* when x or yh is a leaf (the product of the
+// Cholesky factorisation: x = (t, s), yh = (r, s), the product (t, r));
+// the transpose of an admissible block V_r S W_s^* is W_s S^* V_r^*, of a
+// dense leaf its transpose
+Term case2_t(Lr& L, double alpha, int32_t x, int32_t yh, bool near_target) {
+  const h2_matrix* Z = L.Z;
+  const h2_matrix* MX = L.X ? L.X : L.Z;
+  const h2_matrix* MY = L.Y ? L.Y : L.Z;
+  const BlockTree& bt = Z->blocks;
+  const int32_t t = bt.row[x], s = bt.col[x], r = bt.row[yh];
+  const int64_t mt = csize(Z, t), ms = csize(Z, s), mr = csize(Z, r);
+  Term T;
+  T.tc = t;
+  T.rc = r;
+  if (bt.kind[yh] == kAdm) {
+    // (X|_x W_s) S_yh^*, V_r
+    const int ks = rank_of(MY, 1, s), lr = rank_of(MY, 0, r);
+    T.u = lr;
+    if (lr == 0) return T;
+    DArr Ws(ms * std::max(ks, 1), L.st), Xt(mt * std::max(ks, 1), L.st);
+    T.A = DArr(mt * lr, L.st);
+    T.B = DArr(mr * lr, L.st);
+    if (ks > 0) {
+      expand(L, MY, 1, s, Ws.p, ms);
+      zero(Xt.p, mt * ks, L.st);
+      block_prod(L, MX, x, 0, 1.0, Ws.p, ms, Xt.p, mt, ks);
+      launch_gemm((int)mt, lr, ks, alpha, Xt.p, mt, 0, coupling_ptr(MY, yh), MY->kcap, 1, 0.0, T.A.p, mt, L.st);
+    } else {
+      zero(T.A.p, mt * lr, L.st);
+    }
+    expand(L, MY, 0, r, T.B.p, mr);
+    ++L.products;
+    return T;
+  }
+  if (bt.kind[x] == kAdm) {
+    // V_t, (Y|_yh W_s) S_x^*
+    const int kt = rank_of(MX, 0, t), ls = rank_of(MX, 1, s);
+    T.u = kt;
+    if (kt == 0) return T;
+    DArr Ws(ms * std::max(ls, 1), L.st), Yt(mr * std::max(ls, 1), L.st);
+    T.A = DArr(mt * kt, L.st);
+    T.B = DArr(mr * kt, L.st);
+    expand(L, MX, 0, t, T.A.p, mt);
+    if (ls > 0) {
+      expand(L, MX, 1, s, Ws.p, ms);
+      zero(Yt.p, mr * ls, L.st);
+      block_prod(L, MY, yh, 0, 1.0, Ws.p, ms, Yt.p, mr, ls);
+      launch_gemm((int)mr, kt, ls, alpha, Yt.p, mr, 0, coupling_ptr(MX, x), MX->kcap, 1, 0.0, T.B.p, mr, L.st);
+    } else {
+      zero(T.B.p, mr * kt, L.st);
+    }
+    ++L.products;
+    return T;
+  }
+  ++L.products;
+  const bool xn = bt.kind[x] == kNear, yn = bt.kind[yh] == kNear;
+  if (near_target) {
+    // P = alpha X Y^* (#t x #r)
+    T.dense = true;
+    T.A = DArr(mt * mr, L.st);
+    zero(T.A.p, mt * mr, L.st);
+    if (xn && yn) {
+      launch_gemm((int)mt, (int)mr, (int)ms, alpha, near_ptr(MX, x), mt, 0, near_ptr(MY, yh), mr, 1, 0.0, T.A.p, mt,
+                  L.st);
+    } else if (yn) {   // X subdivided: X (Y^*) by the block product
+      DArr Yt(ms * mr, L.st);
+      launch_transpose((int)mr, (int)ms, 1.0, near_ptr(MY, yh), mr, Yt.p, ms, L.st);
+      block_prod(L, MX, x, 0, alpha, Yt.p, ms, T.A.p, mt, (int)mr);
+    } else {           // Y subdivided: P^* = Y (alpha X^*)
+      DArr Xt(ms * mt, L.st), Pt(mr * mt, L.st);
+      launch_transpose((int)mt, (int)ms, alpha, near_ptr(MX, x), mt, Xt.p, ms, L.st);
+      zero(Pt.p, mr * mt, L.st);
+      block_prod(L, MY, yh, 0, 1.0, Xt.p, ms, Pt.p, mr, (int)mt);
+      launch_transpose((int)mr, (int)mt, 1.0, Pt.p, mr, T.A.p, mt, L.st);
+    }
+    return T;
+  }
+  // factor pair through the smallest dimension (reading 3)
+  if (xn && yn && ms <= std::min(mt, mr)) {
+    // alpha X and Y
+    T.u = (int)ms;
+    T.A = DArr(mt * ms, L.st);
+    T.B = DArr(mr * ms, L.st);
+    launch_axpby(mt * ms, alpha, near_ptr(MX, x), 0.0, T.A.p, L.st);
+    H2_CUDA(cudaMemcpyAsync(T.B.p, near_ptr(MY, yh), mr * ms * sizeof(double), cudaMemcpyDeviceToDevice, L.st));
+    return T;
+  }
+  if (mt <= mr) {
+    // (I, P^*): P^* = alpha Y X^* (#r x #t)
+    T.u = (int)mt;
+    T.A = identity(L, mt);
+    T.B = DArr(mr * mt, L.st);
+    zero(T.B.p, mr * mt, L.st);
+    if (xn && yn) {
+      launch_gemm((int)mr, (int)mt, (int)ms, alpha, near_ptr(MY, yh), mr, 0, near_ptr(MX, x), mt, 1, 0.0, T.B.p, mr,
+                  L.st);
+    } else if (xn) {   // Y subdivided: Y (alpha X^*) by the block product
+      DArr Xt(ms * mt, L.st);
+      launch_transpose((int)mt, (int)ms, alpha, near_ptr(MX, x), mt, Xt.p, ms, L.st);
+      block_prod(L, MY, yh, 0, 1.0, Xt.p, ms, T.B.p, mr, (int)mt);
+    } else {
+      throw Error(H2_EINTERNAL, "dense term: unexpected block kinds");
+    }
+    return T;
+  }
+  // (P, I): P = alpha X Y^* (#t x #r)
+  T.u = (int)mr;
+  T.A = DArr(mt * mr, L.st);
+  T.B = identity(L, mr);
+  zero(T.A.p, mt * mr, L.st);
+  if (xn && yn) {
+    launch_gemm((int)mt, (int)mr, (int)ms, alpha, near_ptr(MX, x), mt, 0, near_ptr(MY, yh), mr, 1, 0.0, T.A.p, mt,
+                L.st);
+  } else if (yn) {
+    DArr Yt(ms * mr, L.st);
+    launch_transpose((int)mr, (int)ms, 1.0, near_ptr(MY, yh), mr, Yt.p, ms, L.st);
+    block_prod(L, MX, x, 0, alpha, Yt.p, ms, T.A.p, mt, (int)mr);
+  } else {
+    throw Error(H2_EINTERNAL, "dense term: unexpected block kinds");
+  }
+  return T;
+}
+
 // the term alpha X|_x Y|_y when x or y is a leaf (Section 6, Case 2)
 Term case2(Lr& L, double alpha, int32_t x, int32_t y, bool near_target) {
+  if (L.yt) return case2_t(L, alpha, x, y, near_target);
   const h2_matrix* Z = L.Z;
   const h2_matrix* MX = L.X ? L.X : L.Z;   // the factors (the product's X and Y)
   const h2_matrix* MY = L.Y ? L.Y : L.Z;
@@ -578,11 +704,12 @@ void collect_virtual(Lr& L, double alpha, int32_t x, int32_t y, std::vector<Term
   const BlockTree& bt = L.Z->blocks;
   const ClusterTree& ct = L.Z->rows;
   if (bt.kind[x] == kSub && bt.kind[y] == kSub) {
-    const int32_t t = bt.row[x], s = bt.col[x], r = bt.col[y];
+    // with the second factor read transposed, y = (r, s)
+    const int32_t t = bt.row[x], s = bt.col[x], r = L.yt ? bt.row[y] : bt.col[y];
     for (int32_t s1 : {ct.son0[s], ct.son1[s]})
       for (int32_t t1 : {ct.son0[t], ct.son1[t]})
         for (int32_t r1 : {ct.son0[r], ct.son1[r]})
-          collect_virtual(L, alpha, son(bt, x, t1, s1), son(bt, y, s1, r1), bucket);
+          collect_virtual(L, alpha, son(bt, x, t1, s1), L.yt ? son(bt, y, r1, s1) : son(bt, y, s1, r1), bucket);
     return;
   }
   bucket.push_back(case2(L, alpha, x, y, false));
@@ -592,12 +719,16 @@ void collect(Lr& L, double alpha, int32_t x, int32_t y, int32_t z, std::vector<I
   const BlockTree& bt = L.Z->blocks;
   const ClusterTree& ct = L.Z->rows;
   if (bt.kind[x] == kSub && bt.kind[y] == kSub) {
-    const int32_t t = bt.row[x], s = bt.col[x], r = bt.col[y];
+    const int32_t t = bt.row[x], s = bt.col[x], r = L.yt ? bt.row[y] : bt.col[y];
     if (bt.kind[z] == kSub) {
+      const bool diag = bt.row[z] == bt.col[z];
       for (int32_t s1 : {ct.son0[s], ct.son1[s]})
         for (int32_t t1 : {ct.son0[t], ct.son1[t]})
-          for (int32_t r1 : {ct.son0[r], ct.son1[r]})
-            collect(L, alpha, son(bt, x, t1, s1), son(bt, y, s1, r1), son(bt, z, t1, r1), out);
+          for (int32_t r1 : {ct.son0[r], ct.son1[r]}) {
+            if (L.lower && diag && ct.off[t1] < ct.off[r1]) continue;   // strictly above the diagonal
+            collect(L, alpha, son(bt, x, t1, s1), L.yt ? son(bt, y, r1, s1) : son(bt, y, s1, r1), son(bt, z, t1, r1),
+                    out);
+          }
       return;
     }
     if (bt.kind[z] != kAdm) throw Error(H2_EINTERNAL, "inadmissible target of subdivided factors");
@@ -605,7 +736,8 @@ void collect(Lr& L, double alpha, int32_t x, int32_t y, int32_t z, std::vector<I
     for (int32_t s1 : {ct.son0[s], ct.son1[s]})
       for (int32_t t1 : {ct.son0[t], ct.son1[t]})
         for (int32_t r1 : {ct.son0[r], ct.son1[r]})
-          collect_virtual(L, alpha, son(bt, x, t1, s1), son(bt, y, s1, r1), temps[{t1, r1}]);
+          collect_virtual(L, alpha, son(bt, x, t1, s1), L.yt ? son(bt, y, r1, s1) : son(bt, y, s1, r1),
+                          temps[{t1, r1}]);
     for (int32_t t1 : {ct.son0[t], ct.son1[t]})
       for (int32_t r1 : {ct.son0[r], ct.son1[r]}) {
         Item it;
@@ -948,6 +1080,117 @@ void lr(Lr& L, int32_t d) {
   lr(L, d22);
 }
 
+// ------------------------------------------------ Cholesky (Section 7)
+// A ~ L L^* for a symmetric positive definite matrix, the recursion of the
+// LR with the lower factor's transpose in place of the upper factor: on a
+// diagonal block L11 = chol(A11), L21 = A21 L11^-*, A22 <- A22 - L21 L21^*,
+// L22 = chol(A22).  The factor is the lower triangle of the matrix; the
+// strictly upper nearfield is never read.
+
+// Y (#t x m) <- L|_{t x t}^-1 Y (lower with its diagonal)
+void lsolve_dense_n(Lr& L, int32_t d, double* Y, int64_t ldy, int m) {
+  const h2_matrix* Z = L.Z;
+  const BlockTree& bt = Z->blocks;
+  const int32_t t = bt.row[d];
+  if (bt.kind[d] == kNear) {
+    launch_trsm(3, near_ptr(Z, d), (int)csize(Z, t), csize(Z, t), Y, m, ldy, L.st);
+    return;
+  }
+  const int32_t t1 = Z->rows.son0[t], t2 = Z->rows.son1[t];
+  const int64_t n1 = csize(Z, t1);
+  lsolve_dense_n(L, son(bt, d, t1, t1), Y, ldy, m);
+  block_prod(L, L.Z, son(bt, d, t2, t1), 0, -1.0, Y, ldy, Y + n1, ldy, m);
+  lsolve_dense_n(L, son(bt, d, t2, t2), Y + n1, ldy, m);
+}
+
+// Y (#t x m) <- L|_{t x t}^-* Y
+void ltsolve_dense(Lr& L, int32_t d, double* Y, int64_t ldy, int m) {
+  const h2_matrix* Z = L.Z;
+  const BlockTree& bt = Z->blocks;
+  const int32_t t = bt.row[d];
+  if (bt.kind[d] == kNear) {
+    launch_trsm(4, near_ptr(Z, d), (int)csize(Z, t), csize(Z, t), Y, m, ldy, L.st);
+    return;
+  }
+  const int32_t t1 = Z->rows.son0[t], t2 = Z->rows.son1[t];
+  const int64_t n1 = csize(Z, t1);
+  ltsolve_dense(L, son(bt, d, t2, t2), Y + n1, ldy, m);
+  block_prod(L, L.Z, son(bt, d, t2, t1), 1, -1.0, Y + n1, ldy, Y, ldy, m);
+  ltsolve_dense(L, son(bt, d, t1, t1), Y, ldy, m);
+}
+
+// Z|_z += alpha Z|_x (Z|_yh)^*
+void mul_t(Lr& L, double alpha, int32_t x, int32_t yh, int32_t z, bool lower) {
+  struct Reset {
+    Lr& L;
+    ~Reset() {
+      L.yt = false;
+      L.lower = false;
+    }
+  } reset{L};
+  L.yt = true;
+  L.lower = lower;
+  mul(L, alpha, x, yh, z);
+}
+
+// Z|_x <- Z|_x L|_{s x s}^-* in place, x = (t, s), d = (s, s)
+void chol_rsolve(Lr& L, int32_t d, int32_t x) {
+  h2_matrix* Z = L.Z;
+  const BlockTree& bt = Z->blocks;
+  const int32_t t = bt.row[x], s = bt.col[x];
+  if (bt.kind[x] == kNear) {
+    const int64_t mt = csize(Z, t), ms = csize(Z, s);
+    Timer tm(L.t_solves);
+    // (X L^-*)^* = L^-1 X^*
+    DArr Yt(ms * mt, L.st);
+    launch_transpose((int)mt, (int)ms, 1.0, near_ptr(Z, x), mt, Yt.p, ms, L.st);
+    lsolve_dense_n(L, d, Yt.p, ms, (int)mt);
+    launch_transpose((int)ms, (int)mt, 1.0, Yt.p, ms, near_ptr(Z, x), mt, L.st);
+    return;
+  }
+  if (bt.kind[x] == kAdm) {
+    const int kt = rank_of(Z, 0, t), ls = rank_of(Z, 1, s);
+    if (ls == 0 || kt == 0) return;   // the block is zero
+    const int64_t mt = csize(Z, t), ms = csize(Z, s);
+    DArr Ws(ms * ls, L.st), Bh(ms * kt, L.st), Vt(mt * kt, L.st);
+    {
+      Timer tm(L.t_solves);
+      expand(L, L.Z, 1, s, Ws.p, ms);
+      launch_gemm((int)ms, kt, ls, 1.0, Ws.p, ms, 0, coupling_ptr(Z, x), Z->kcap, 1, 0.0, Bh.p, ms, L.st);
+      lsolve_dense_n(L, d, Bh.p, ms, kt);   // L^-1 W_s S^*
+      expand(L, L.Z, 0, t, Vt.p, mt);
+    }
+    engine_touch(L.eng, Z, x);   // a coupling written outside the update engine
+    H2_CUDA(cudaMemsetAsync(coupling_ptr(Z, x), 0, (size_t)Z->kcap * Z->kcap * sizeof(double), L.st));
+    apply_update(L, x, Vt.p, mt, Bh.p, ms, kt);
+    return;
+  }
+  const ClusterTree& ct = Z->rows;
+  const int32_t s1 = ct.son0[s], s2 = ct.son1[s];
+  for (int32_t t1 : {ct.son0[t], ct.son1[t]}) chol_rsolve(L, son(bt, d, s1, s1), son(bt, x, t1, s1));
+  for (int32_t t1 : {ct.son0[t], ct.son1[t]})
+    mul_t(L, -1.0, son(bt, x, t1, s1), son(bt, d, s2, s1), son(bt, x, t1, s2), false);
+  for (int32_t t1 : {ct.son0[t], ct.son1[t]}) chol_rsolve(L, son(bt, d, s2, s2), son(bt, x, t1, s2));
+}
+
+void chol(Lr& L, int32_t d) {
+  h2_matrix* Z = L.Z;
+  const BlockTree& bt = Z->blocks;
+  const int32_t t = bt.row[d];
+  if (bt.kind[d] == kNear) {
+    Timer tm(L.t_lu);
+    launch_leaf_chol(near_ptr(Z, d), (int)csize(Z, t), csize(Z, t), L.ctx->d_error, L.st);
+    return;
+  }
+  const ClusterTree& ct = Z->rows;
+  const int32_t t1 = ct.son0[t], t2 = ct.son1[t];
+  const int32_t d11 = son(bt, d, t1, t1), d21 = son(bt, d, t2, t1), d22 = son(bt, d, t2, t2);
+  chol(L, d11);
+  chol_rsolve(L, d11, d21);
+  mul_t(L, -1.0, d21, d21, d22, true);
+  chol(L, d22);
+}
+
 // ---------------------------------------------- inversion (Remark on inversion)
 // C|_d <- (A|_d)^-1 for a diagonal block d: a leaf by Doolittle's LU and two
 // triangular solves with the identity; otherwise block Gauss elimination
@@ -1275,6 +1518,51 @@ extern "C" h2_status h2_lr_factor(h2_ctx* ctx, h2_matrix* Z, const h2_options* o
   });
 }
 
+extern "C" h2_status h2_chol_factor(h2_ctx* ctx, h2_matrix* Z, const h2_options* opt, int64_t* stats) {
+  if (!ctx || !Z || !opt) return H2_EINVAL;
+  return lr_guard(ctx, [&] {
+    check_options(opt);
+    check_square(Z);
+    DevGuard g(ctx->device);
+    Lr L;
+    L.ctx = ctx;
+    L.Z = Z;
+    L.eps = opt->eps;
+    L.max_rank = opt->max_rank;
+    L.st = ctx->stream;
+    chol(L, 0);
+    H2_CUDA(cudaStreamSynchronize(L.st));
+    h2_status s = h2_ctx_synchronize(ctx);
+    if (s != H2_OK) throw Error(s, ctx->last_error);
+    if (stats) {
+      stats[0] = L.updates;
+      stats[1] = L.products;
+      int kmax = 0;
+      for (int32_t r : Z->V.rank) kmax = std::max(kmax, r);
+      for (int32_t r : Z->W.rank) kmax = std::max(kmax, r);
+      stats[2] = kmax;
+    }
+  });
+}
+
+extern "C" h2_status h2_chol_solve(h2_ctx* ctx, const h2_matrix* F, int64_t nrhs, double* X, int64_t ldx) {
+  if (!ctx || !F || nrhs < 0 || (nrhs > 0 && !X)) return H2_EINVAL;
+  return lr_guard(ctx, [&] {
+    H2_REQUIRE(ldx >= F->rows.n, "h2_chol_solve: leading dimension too small");
+    check_square(F);
+    if (nrhs == 0) return;
+    DevGuard g(ctx->device);
+    Lr L;
+    L.ctx = ctx;
+    L.Z = const_cast<h2_matrix*>(F);   // read only: solves never modify the factor
+    L.st = ctx->stream;
+    lsolve_dense_n(L, 0, X, ldx, (int)nrhs);
+    ltsolve_dense(L, 0, X, ldx, (int)nrhs);
+    H2_CUDA(cudaGetLastError());
+    H2_CUDA(cudaStreamSynchronize(L.st));
+  });
+}
+
 extern "C" h2_status h2_inverse(h2_ctx* ctx, h2_matrix* A, const h2_options* opt, h2_matrix** out,
                                 int64_t* stats) {
   if (!ctx || !A || !opt || !out) return H2_EINVAL;
@@ -1455,6 +1743,24 @@ extern "C" h2_status h2_pcg(h2_ctx* ctx, const h2_matrix* A, const h2_matrix* LR
         h2_status s = h2_lr_solve(ctx, LR, 1, out, n);
         if (s != H2_OK) throw Error(s, ctx->last_error);
       }
+    };
+    pcg_run(ctx, A, precond, b, x, tol, maxit, iterations, relres, z);
+  });
+}
+
+extern "C" h2_status h2_pcg_chol(h2_ctx* ctx, const h2_matrix* A, const h2_matrix* F, const double* b, double* x,
+                                 double tol, int maxit, int* iterations, double* relres) {
+  if (!ctx || !A || !F || !b || !x || maxit < 0) return H2_EINVAL;
+  return lr_guard(ctx, [&] {
+    const int64_t n = A->rows.n;
+    H2_REQUIRE(F->rows.n == n && F->cols.n == n, "h2_pcg_chol: the factor has another size");
+    DevGuard g(ctx->device);
+    cudaStream_t st = ctx->stream;
+    DArr z(n, st);
+    auto precond = [&](const double* in, double* out) {
+      H2_CUDA(cudaMemcpyAsync(out, in, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      h2_status s = h2_chol_solve(ctx, F, 1, out, n);
+      if (s != H2_OK) throw Error(s, ctx->last_error);
     };
     pcg_run(ctx, A, precond, b, x, tol, maxit, iterations, relres, z);
   });

@@ -65,6 +65,9 @@ void launch_eye(double* A, int n, int64_t lda, cudaStream_t st);
 // in-place LU without pivoting (Doolittle) of the m x m block A (ld lda);
 // a zero pivot sets bit 8 of *err
 void launch_leaf_lu(double* A, int m, int64_t lda, int* err, cudaStream_t st);
+// Cholesky factor (lower, strictly upper part zeroed) of a dense leaf in
+// place; a pivot that is not positive sets bit 512 of *err
+void launch_leaf_chol(double* A, int m, int64_t lda, int* err, cudaStream_t st);
 // triangular solves with the factor F (m x m, ld ldf):
 //   kind 0: X <- L^-1 X  (L unit lower in F, X m x n)
 //   kind 1: X <- R^-1 X  (R upper with the diagonal in F, X m x n)

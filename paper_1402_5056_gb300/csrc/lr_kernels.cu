@@ -198,12 +198,48 @@ __global__ void k_leaf_lu(double* A, int m, int64_t lda, int* err) {
   }
 }
 
+// Cholesky factor of a dense m x m leaf (m <= 64) in place, one warp, lane
+// i holding rows i and i + 32: right-looking, column k scaled by the root
+// of its pivot, then the lower triangle of the trailing block updated; the
+// strictly upper part is set to zero.  A pivot that is not positive sets
+// bit 512 of err (the matrix is not positive definite).
+__global__ void k_leaf_chol(double* A, int m, int64_t lda, int* err) {
+  const int lane = threadIdx.x;
+  for (int k = 0; k < m; ++k) {
+    const double piv = A[k + k * lda];
+    if (!(piv > 0.0) && lane == 0) atomicOr(err, 512);
+    const double rt = sqrt(piv);
+    __syncwarp();
+    for (int h = 0; h < 2; ++h) {
+      const int i = lane + 32 * h;
+      if (i > k && i < m) A[i + k * lda] = A[i + k * lda] / rt;
+      if (i == k) A[k + k * lda] = rt;
+    }
+    __syncwarp();
+    for (int h = 0; h < 2; ++h) {
+      const int i = lane + 32 * h;
+      if (i > k && i < m) {
+        const double l = A[i + k * lda];
+        for (int j = k + 1; j <= i; ++j) A[i + j * lda] = fma(-l, A[j + k * lda], A[i + j * lda]);
+      }
+    }
+    __syncwarp();
+  }
+  for (int h = 0; h < 2; ++h) {
+    const int i = lane + 32 * h;
+    if (i < m)
+      for (int j = i + 1; j < m; ++j) A[i + j * lda] = 0.0;
+  }
+}
+
 // Triangular solves with an m x m factor (m <= 64), one warp per
 // right-hand side, lane i holding entries i and i + 32; the solved entry of
 // each step is broadcast and the others updated column by column
 //   kind 0: column j of X, L x = y (unit lower)
 //   kind 1: column j of X, R x = y (upper)
 //   kind 2: row j of X, x R = y
+//   kind 3: column j of X, L x = y (lower with its diagonal)
+//   kind 4: column j of X, L^* x = y (L lower with its diagonal)
 __global__ void k_trsm(int kind, const double* F, int m, int64_t ldf, double* X, int n, int64_t ldx) {
   const int lane = threadIdx.x & 31;
   const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -215,7 +251,27 @@ __global__ void k_trsm(int kind, const double* F, int m, int64_t ldf, double* X,
     const int i = lane + 32 * h;
     r[h] = i < m ? x[i * stride] : 0.0;
   }
-  if (kind == 0) {
+  if (kind == 3) {
+    for (int k = 0; k < m; ++k) {
+      const int hk = k >> 5;
+      if ((k & 31) == lane) r[hk] = r[hk] / F[k + k * ldf];
+      const double xk = __shfl_sync(0xffffffffu, hk ? r[1] : r[0], k & 31);
+      for (int h = 0; h < 2; ++h) {
+        const int i = lane + 32 * h;
+        if (i > k && i < m) r[h] = fma(-F[i + k * ldf], xk, r[h]);
+      }
+    }
+  } else if (kind == 4) {
+    for (int k = m - 1; k >= 0; --k) {
+      const int hk = k >> 5;
+      if ((k & 31) == lane) r[hk] = r[hk] / F[k + k * ldf];
+      const double xk = __shfl_sync(0xffffffffu, hk ? r[1] : r[0], k & 31);
+      for (int h = 0; h < 2; ++h) {
+        const int i = lane + 32 * h;
+        if (i < k) r[h] = fma(-F[k + i * ldf], xk, r[h]);
+      }
+    }
+  } else if (kind == 0) {
     for (int k = 0; k < m; ++k) {
       const double xk = __shfl_sync(0xffffffffu, k < 32 ? r[0] : r[1], k & 31);
       for (int h = 0; h < 2; ++h) {
@@ -766,6 +822,10 @@ void launch_eye(double* A, int n, int64_t lda, cudaStream_t st) {
 
 void launch_leaf_lu(double* A, int m, int64_t lda, int* err, cudaStream_t st) {
   if (m > 0) k_leaf_lu<<<1, 32, 0, st>>>(A, m, lda, err);
+}
+
+void launch_leaf_chol(double* A, int m, int64_t lda, int* err, cudaStream_t st) {
+  if (m > 0) k_leaf_chol<<<1, 32, 0, st>>>(A, m, lda, err);
 }
 
 void launch_trsm(int kind, const double* F, int m, int64_t ldf, double* X, int n, int64_t ldx, cudaStream_t st) {

@@ -18,6 +18,7 @@ constexpr int kErrCols = 2;      // more than 32 columns
 constexpr int kErrJacobi = 4;    // one-sided Jacobi did not converge in the sweep limit
 constexpr int kErrRank = 8;      // inconsistent ranks
 constexpr int kErrPivot = 256;   // zero pivot in a leaf LU (H^2-LR)
+constexpr int kErrDefinite = 512;   // pivot not positive in a leaf Cholesky
 
 // One cluster of one side of one update ("cluster task").
 struct Item {

@@ -6,8 +6,9 @@ problem (Section 7's model problem) on one GPU.
 Builds the P1 stiffness matrix of -div(sigma grad u) = f on the unit square
 (u = 0 on the boundary, sigma piecewise constant on a checker x checker
 board with values 10^U(-2, 2)) as an H^2 matrix, factorises a copy into
-H^2-LR, runs preconditioned CG to 1e-10 for a N(0, 1) right-hand side and
-estimates ||I - (LR)^-1 A||_2 by the power iteration; prints one JSON line
+H^2-LR (or, with --chol, the approximate Cholesky factor), runs
+preconditioned CG to 1e-10 for a N(0, 1) right-hand side and estimates
+||I - (LR)^-1 A||_2 by the power iteration (LR only); prints one JSON line
 with the sizes, the times (wall clock around each call, synchronised) and
 the statistics of the factorisation.
 """
@@ -31,6 +32,8 @@ def main(argv=None) -> dict:
     ap.add_argument("--tol", type=float, default=1e-10, help="relative residual of CG")
     ap.add_argument("--max-rank", type=int, default=0,
                     help="rank cap of every local update (0: none, the paper's method)")
+    ap.add_argument("--chol", action="store_true",
+                    help="approximate Cholesky factorisation instead of the LR (Section 7's preconditioner)")
     args = ap.parse_args(argv)
 
     import torch
@@ -48,7 +51,7 @@ def main(argv=None) -> dict:
         F = b.h2_matrix_clone(ctx, A)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
-        info = b.h2_lr_factor(ctx, F, opt)
+        info = b.h2_chol_factor(ctx, F, opt) if args.chol else b.h2_lr_factor(ctx, F, opt)
         torch.cuda.synchronize()
         t2 = time.perf_counter()
         n = (args.cells - 1) ** 2
@@ -57,12 +60,14 @@ def main(argv=None) -> dict:
         xd = torch.zeros(n, dtype=torch.float64, device="cuda")
         torch.cuda.synchronize()
         t3 = time.perf_counter()
-        it, rr = b.h2_pcg(ctx, A, F, bd.data_ptr(), xd.data_ptr(), args.tol, 1000)
+        pcg = b.h2_pcg_chol if args.chol else b.h2_pcg
+        it, rr = pcg(ctx, A, F, bd.data_ptr(), xd.data_ptr(), args.tol, 1000)
         torch.cuda.synchronize()
         t4 = time.perf_counter()
         v0 = torch.from_numpy(rng.standard_normal(n)).cuda()
-        err = b.h2_lr_error(ctx, A, F, v0.data_ptr(), 20)
+        err = None if args.chol else b.h2_lr_error(ctx, A, F, v0.data_ptr(), 20)
         out = {"n": n, "cells": args.cells, "checker": args.checker, "eps": args.eps, "max_rank": args.max_rank,
+               "factorisation": "cholesky" if args.chol else "lr",
                "build_s": t1 - t0, "factor_s": t2 - t1, "cg_iterations": it, "cg_relres": rr,
                "cg_s": t4 - t3, "err_power": err, "factor": info}
         b.h2_matrix_free(F)
