@@ -290,11 +290,12 @@ def lr_problem(cells: int):
     return 4, synth.SEED_BASE + 100 + cells
 
 
-def lr_measure(b, ctx, cells_list, reps: int, oracle_cells):
+def lr_measure(b, ctx, cells_list, reps: int, oracle_cells, chol=False):
     """FEM matrix, H^2-LR setup (build + factorisation, wall clock; the
     recursion is driven from the host, every arithmetic step on the device),
     PCG steps to 1e-10 and the power-iteration error; the oracle's setup
-    timed beside it on the host for the sizes in oracle_cells."""
+    timed beside it on the host for the sizes in oracle_cells.  chol: the
+    approximate Cholesky factorisation instead (h2_chol_factor)."""
     import torch
     out = {}
     for cells in cells_list:
@@ -314,7 +315,7 @@ def lr_measure(b, ctx, cells_list, reps: int, oracle_cells):
             F = b.h2_build_fem(ctx, 2, cells, M, sigma, opt) if rep == 0 else b.h2_matrix_clone(ctx, A)
             torch.cuda.synchronize()
             t1 = time.perf_counter()
-            info = b.h2_lr_factor(ctx, F, opt)
+            info = b.h2_chol_factor(ctx, F, opt) if chol else b.h2_lr_factor(ctx, F, opt)
             torch.cuda.synchronize()
             t2 = time.perf_counter()
             builds.append(t1 - t0)
@@ -326,28 +327,30 @@ def lr_measure(b, ctx, cells_list, reps: int, oracle_cells):
         xd = torch.zeros(n, dtype=torch.float64, device="cuda")
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        it, rr = b.h2_pcg(ctx, A, F, bd.data_ptr(), xd.data_ptr(), 1e-10, 100)
+        it, rr = (b.h2_pcg_chol if chol else b.h2_pcg)(ctx, A, F, bd.data_ptr(), xd.data_ptr(), 1e-10, 100)
         torch.cuda.synchronize()
         cg_s = time.perf_counter() - t0
         v0 = torch.from_numpy(np.random.default_rng(3).standard_normal(n)).cuda()
-        err = b.h2_lr_error(ctx, A, F, v0.data_ptr(), 20)
+        err = (b.h2_chol_error if chol else b.h2_lr_error)(ctx, A, F, v0.data_ptr(), 20)
         rec = {"n": n, "cells": cells, "checker": M, "eps": LR_EPS, "leaf": 32, "eta": 2.0,
                "setup_s": min(factors), "factor_s_all": factors, "build_s": min(builds),
                "updates": info["updates"], "products": info["products"], "max_rank": info["max_rank"],
-               "seconds_by_activity": info["seconds"],
+               "seconds_by_activity": info.get("seconds"),
                "cg_iterations": it, "cg_relres": rr, "cg_s": cg_s, "err_power": err}
         if cells in oracle_cells:
             sys.path.insert(0, os.path.join(ROOT, "tests"))
             from oracle.fem import h2_from_sparse, stiffness
+            from oracle.chol import chol_factor, chol_solve
             from oracle.lr import lr_factor, lr_solve, pcg
             t0 = time.perf_counter()
             K, pts = stiffness(cells, 2, sigma, M)
             Zo = h2_from_sparse(K, pts, 32, 2.0, 1.0 / cells)
             t1 = time.perf_counter()
-            lr_factor(Zo, LR_EPS)
+            (chol_factor if chol else lr_factor)(Zo, LR_EPS)
             t2 = time.perf_counter()
             Kp = K[Zo.V.tree.perm][:, Zo.V.tree.perm].tocsr()
-            _, it_o = pcg(lambda v: Kp @ v, rhs, lambda r: lr_solve(Zo, r), 1e-10)
+            solve = chol_solve if chol else lr_solve
+            _, it_o = pcg(lambda v: Kp @ v, rhs, lambda r: solve(Zo, r), 1e-10)
             rec["oracle"] = {"setup_s": t2 - t1, "build_s": t1 - t0, "cg_iterations": it_o, "cores": 1,
                              "kind": "oracle"}
         out["%dx%d" % (cells, cells)] = rec
@@ -494,6 +497,8 @@ def main():
     ap.add_argument("--lr-cells", default="32,64",
                     help="comma-separated cells per side of the 2D FEM H2-LR problems to time ('' for none)")
     ap.add_argument("--lr-reps", type=int, default=3)
+    ap.add_argument("--chol-cells", default="32,64,128",
+                    help="comma-separated cells per side of the 2D FEM Cholesky factorisations to time ('' for none)")
     ap.add_argument("--batch-problems", type=int, default=16,
                     help="independent FEM problems of the uneven batch (0: none)")
     ap.add_argument("--inv-cells", default="32",
@@ -706,6 +711,10 @@ def main():
     cells_list = [int(x) for x in args.lr_cells.split(",") if x.strip()]
     if rank == 0 and world == 1 and cells_list:
         lr = lr_measure(b, ctx, cells_list, args.lr_reps, oracle_cells={32})
+    chol = None
+    chol_cells = [int(x) for x in args.chol_cells.split(",") if x.strip()]
+    if rank == 0 and world == 1 and chol_cells:
+        chol = lr_measure(b, ctx, chol_cells, 1, oracle_cells={32}, chol=True)
     lr_batch = None
     if rank == 0 and world == 1 and args.batch_problems > 0:
         lr_batch = lr_batch_measure(b, ctx, args.batch_problems, 24, 48)
@@ -741,7 +750,7 @@ def main():
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "e2e_compact": e2e_compact,
             "gpu_launches": stats["launches"] * args.steps,
             "clocks": clocks, "phases": phases, "phases_serial": phases_serial, "exact_mode": exact_mode,
-            "matvec": mv, "lr": lr, "lr_batch": lr_batch, "inverse": inv,
+            "matvec": mv, "lr": lr, "chol": chol, "lr_batch": lr_batch, "inverse": inv,
             "gflop_per_step": stats["flops"] / 1e9}
     if rank == 0:
         print(json.dumps(line))

@@ -545,6 +545,10 @@ h2_status h2_chol_solve(h2_ctx* ctx, const h2_matrix* F, int64_t nrhs, double* X
 h2_status h2_pcg_chol(h2_ctx* ctx, const h2_matrix* A, const h2_matrix* F, const double* b, double* x, double tol,
                       int maxit, int* iterations, double* relres);
 
+/* h2_lr_error for a factor from h2_chol_factor: ||I - (L L^*)^-1 A||_2 by
+ * the power iteration (Section 7, column Err); same arguments. */
+h2_status h2_chol_error(h2_ctx* ctx, const h2_matrix* A, const h2_matrix* F, double* v, int iters, double* err);
+
 /* ----------------------------------------------------------- diagnostics */
 
 /* The float64 reciprocal the factorisation kernels use for their pivots

@@ -35,7 +35,7 @@ EXPORTS = [
     "h2_lowrank_update_noalloc", "h2_lowrank_update_sequence", "h2_matvec", "h2_block_to_dense",
     "h2_sequence_waves", "h2_check_reciprocal", "h2_debug_fail_allocation",
     "h2_stats", "h2_build_fem", "h2_lr_factor", "h2_lr_factor_many", "h2_lr_solve", "h2_pcg", "h2_lr_error", "h2_mul", "h2_inverse",
-    "h2_pcg_inverse", "h2_chol_factor", "h2_chol_solve", "h2_pcg_chol",
+    "h2_pcg_inverse", "h2_chol_factor", "h2_chol_solve", "h2_pcg_chol", "h2_chol_error",
 ]
 
 PHASES = ("base_weights", "rfactor", "norms", "weights", "truncate", "reproject", "exact", "bases")
@@ -126,6 +126,7 @@ _sig("h2_pcg_inverse", _int, _p, _p, _p, _p, _p, _dbl, _int, _p, _p)
 _sig("h2_chol_factor", _int, _p, _p, C.POINTER(Options), _p)
 _sig("h2_chol_solve", _int, _p, _p, _i64, _p, _i64)
 _sig("h2_pcg_chol", _int, _p, _p, _p, _p, _p, _dbl, _int, _p, _p)
+_sig("h2_chol_error", _int, _p, _p, _p, _p, _int, _p)
 _sig("h2_mul", _int, _p, _dbl, _p, _i64, _p, _i64, _p, _i64, _dbl, _p)
 _sig("h2_matvec", _int, _p, _p, _i64, _dbl, _p, _i64, _dbl, _p, _i64)
 _sig("h2_lowrank_update_sequence", _int, _p, _p, _i64, _p, _int, _p, _p, _dbl, _p)
@@ -608,6 +609,12 @@ def h2_pcg_chol(ctx, A, F, b_dev: int, x_dev: int, tol: float, maxit: int):
     _check(_lib.h2_pcg_chol(ctx, A, F, C.c_void_p(b_dev), C.c_void_p(x_dev), float(tol), int(maxit),
                             C.byref(it), C.byref(rr)), ctx)
     return it.value, rr.value
+
+
+def h2_chol_error(ctx, A, F, v_dev: int, iters: int):
+    err = C.c_double(0.0)
+    _check(_lib.h2_chol_error(ctx, A, F, C.c_void_p(v_dev), int(iters), C.byref(err)), ctx)
+    return err.value
 
 
 def h2_mul(ctx, alpha: float, X, bx: int, Y, by: int, Z, bz: int, eps: float) -> int:

@@ -1783,38 +1783,62 @@ extern "C" h2_status h2_pcg_inverse(h2_ctx* ctx, const h2_matrix* A, const h2_ma
   });
 }
 
+namespace {
+// ||I - P A||_2 by the power iteration, P = solve(in place) (Section 7,
+// column Err): iters steps v <- w / ||w||, w = v - P A v
+template <class Solve>
+double power_error(h2_ctx* ctx, const h2_matrix* A, Solve&& solve, double* v, int iters) {
+  const int64_t n = A->rows.n;
+  cudaStream_t st = ctx->stream;
+  DArr w(n, st), part(kDotBlocks, st), sc(1, st);
+  auto norm = [&](const double* u) {
+    launch_dot(u, u, n, part.p, sc.p, st);
+    double h = 0.0;
+    H2_CUDA(cudaMemcpyAsync(&h, sc.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+    H2_CUDA(cudaStreamSynchronize(st));
+    return std::sqrt(h);
+  };
+  double nv = norm(v);
+  H2_REQUIRE(nv > 0, "power iteration: zero start vector");
+  launch_axpby(n, 1.0 / nv, v, 0.0, v, st);
+  double lam = 0.0;
+  for (int k = 0; k < iters; ++k) {
+    h2_status s = h2_matvec(ctx, A, 1, 1.0, v, n, 0.0, w.p, n);
+    if (s != H2_OK) throw Error(s, ctx->last_error);
+    solve(w.p);
+    launch_axpby(n, 1.0, v, -1.0, w.p, st);
+    lam = norm(w.p);
+    if (lam == 0.0) break;
+    launch_axpby(n, 1.0 / lam, w.p, 0.0, v, st);
+  }
+  H2_CUDA(cudaStreamSynchronize(st));
+  return lam;
+}
+}  // namespace
+
 extern "C" h2_status h2_lr_error(h2_ctx* ctx, const h2_matrix* A, const h2_matrix* LR, double* v, int iters,
                                  double* err) {
   if (!ctx || !A || !LR || !v || iters < 1 || !err) return H2_EINVAL;
   return lr_guard(ctx, [&] {
-    const int64_t n = A->rows.n;
     DevGuard g(ctx->device);
-    cudaStream_t st = ctx->stream;
-    DArr w(n, st), part(kDotBlocks, st), sc(1, st);
-    auto norm = [&](const double* u) {
-      launch_dot(u, u, n, part.p, sc.p, st);
-      double h = 0.0;
-      H2_CUDA(cudaMemcpyAsync(&h, sc.p, sizeof(double), cudaMemcpyDeviceToHost, st));
-      H2_CUDA(cudaStreamSynchronize(st));
-      return std::sqrt(h);
-    };
-    double nv = norm(v);
-    H2_REQUIRE(nv > 0, "h2_lr_error: zero start vector");
-    launch_axpby(n, 1.0 / nv, v, 0.0, v, st);
-    double lam = 0.0;
-    for (int k = 0; k < iters; ++k) {
-      // w = v - LR^-1 A v
-      h2_status s = h2_matvec(ctx, A, 1, 1.0, v, n, 0.0, w.p, n);
+    const int64_t n = A->rows.n;
+    *err = power_error(ctx, A, [&](double* w) {
+      h2_status s = h2_lr_solve(ctx, LR, 1, w, n);
       if (s != H2_OK) throw Error(s, ctx->last_error);
-      s = h2_lr_solve(ctx, LR, 1, w.p, n);
+    }, v, iters);
+  });
+}
+
+extern "C" h2_status h2_chol_error(h2_ctx* ctx, const h2_matrix* A, const h2_matrix* F, double* v, int iters,
+                                   double* err) {
+  if (!ctx || !A || !F || !v || iters < 1 || !err) return H2_EINVAL;
+  return lr_guard(ctx, [&] {
+    DevGuard g(ctx->device);
+    const int64_t n = A->rows.n;
+    *err = power_error(ctx, A, [&](double* w) {
+      h2_status s = h2_chol_solve(ctx, F, 1, w, n);
       if (s != H2_OK) throw Error(s, ctx->last_error);
-      launch_axpby(n, 1.0, v, -1.0, w.p, st);
-      lam = norm(w.p);
-      if (lam == 0.0) break;
-      launch_axpby(n, 1.0 / lam, w.p, 0.0, v, st);
-    }
-    H2_CUDA(cudaStreamSynchronize(st));
-    *err = lam;
+    }, v, iters);
   });
 }
 

@@ -8,7 +8,7 @@ Builds the P1 stiffness matrix of -div(sigma grad u) = f on the unit square
 board with values 10^U(-2, 2)) as an H^2 matrix, factorises a copy into
 H^2-LR (or, with --chol, the approximate Cholesky factor), runs
 preconditioned CG to 1e-10 for a N(0, 1) right-hand side and estimates
-||I - (LR)^-1 A||_2 by the power iteration (LR only); prints one JSON line
+||I - (LR)^-1 A||_2 (or ||I - (L L^*)^-1 A||_2) by the power iteration; prints one JSON line
 with the sizes, the times (wall clock around each call, synchronised) and
 the statistics of the factorisation.
 """
@@ -65,7 +65,7 @@ def main(argv=None) -> dict:
         torch.cuda.synchronize()
         t4 = time.perf_counter()
         v0 = torch.from_numpy(rng.standard_normal(n)).cuda()
-        err = None if args.chol else b.h2_lr_error(ctx, A, F, v0.data_ptr(), 20)
+        err = (b.h2_chol_error if args.chol else b.h2_lr_error)(ctx, A, F, v0.data_ptr(), 20)
         out = {"n": n, "cells": args.cells, "checker": args.checker, "eps": args.eps, "max_rank": args.max_rank,
                "factorisation": "cholesky" if args.chol else "lr",
                "build_s": t1 - t0, "factor_s": t2 - t1, "cg_iterations": it, "cg_relres": rr,

@@ -10,7 +10,8 @@ the CPU oracle (oracle.chol).
   with leaf 16: per-block parity with the oracle's factor at 1e-10, equal
   ranks and update counts, fewer updates than the LR, L L^* close to A;
 * h2_chol_solve equals the oracle's solve; CG preconditioned by the factor
-  (h2_pcg_chol) takes the oracle's number of steps +-1.
+  (h2_pcg_chol) takes the oracle's number of steps +-1; the power-iteration
+  Err (h2_chol_error) equals the oracle's.
 """
 import numpy as np
 import pytest
@@ -129,3 +130,17 @@ def test_chol_takes_fewer_updates_than_lr(ctx):
     finally:
         b.h2_matrix_free(Z1)
         b.h2_matrix_free(Z2)
+
+
+def test_chol_power_error_matches_oracle(ctx, factored):
+    """||I - (L L^*)^-1 A||_2 by the power iteration (Section 7, Err)."""
+    from oracle.lr import power_error
+    Z, Zo, K, info, info_o, st, A = factored
+    n = K.shape[0]
+    perm = Zo.V.tree.perm
+    Kp = K[perm][:, perm].tocsr()
+    want = power_error(lambda v: Kp @ v, lambda r: chol_solve(Zo, r), n, 20, seed=3)
+    vd = torch.from_numpy(np.random.default_rng(3).standard_normal(n)).cuda()
+    got = b.h2_chol_error(ctx, A, Z, vd.data_ptr(), 20)
+    assert abs(got - want) <= 1e-6 * max(want, 1e-12) + 1e-14, (got, want)
+    assert want < 1e-2
