@@ -359,12 +359,15 @@ def lr_measure(b, ctx, cells_list, reps: int, oracle_cells, chol=False):
     return out
 
 
-def lr_batch_measure(b, ctx, count: int, lo: int, hi: int):
+def lr_batch_measure(b, ctx, count: int, lo: int, hi: int, chol=False):
     """A batch of independent 2D FEM problems of uneven sizes (cells per
     side uniform in lo..hi, 4 x 4 checkerboards, seeded): factorised one after
     the other (h2_lr_factor) and side by side (h2_lr_factor_many, one host
     thread and stream per problem in flight); factorisations per second of
-    both, and whether the results agree (update counts)."""
+    both, and whether the results agree (update counts).  chol: the
+    Cholesky factorisation (h2_chol_factor, h2_chol_factor_many)."""
+    factor = b.h2_chol_factor if chol else b.h2_lr_factor
+    factor_many = b.h2_chol_factor_many if chol else b.h2_lr_factor_many
     import torch
     rng = np.random.default_rng(synth.SEED_BASE + 4)
     cells = [int(c) for c in rng.integers(lo, hi + 1, count)]
@@ -374,7 +377,7 @@ def lr_batch_measure(b, ctx, count: int, lo: int, hi: int):
     Zs = build()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    one = [b.h2_lr_factor(ctx, Z, opt) for Z in Zs]
+    one = [factor(ctx, Z, opt) for Z in Zs]
     torch.cuda.synchronize()
     seq = time.perf_counter() - t0
     for Z in Zs:
@@ -382,7 +385,7 @@ def lr_batch_measure(b, ctx, count: int, lo: int, hi: int):
     Zs = build()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    many = b.h2_lr_factor_many(ctx, Zs, opt, threads=count)
+    many = factor_many(ctx, Zs, opt, threads=count)
     torch.cuda.synchronize()
     par = time.perf_counter() - t0
     for Z in Zs:
@@ -715,9 +718,10 @@ def main():
     chol_cells = [int(x) for x in args.chol_cells.split(",") if x.strip()]
     if rank == 0 and world == 1 and chol_cells:
         chol = lr_measure(b, ctx, chol_cells, 1, oracle_cells={32}, chol=True)
-    lr_batch = None
+    lr_batch = chol_batch = None
     if rank == 0 and world == 1 and args.batch_problems > 0:
         lr_batch = lr_batch_measure(b, ctx, args.batch_problems, 24, 48)
+        chol_batch = lr_batch_measure(b, ctx, args.batch_problems, 24, 48, chol=True)
     inv = None
     inv_cells = [int(x) for x in args.inv_cells.split(",") if x.strip()]
     if rank == 0 and world == 1 and inv_cells:
@@ -750,7 +754,7 @@ def main():
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "e2e_compact": e2e_compact,
             "gpu_launches": stats["launches"] * args.steps,
             "clocks": clocks, "phases": phases, "phases_serial": phases_serial, "exact_mode": exact_mode,
-            "matvec": mv, "lr": lr, "chol": chol, "lr_batch": lr_batch, "inverse": inv,
+            "matvec": mv, "lr": lr, "chol": chol, "lr_batch": lr_batch, "chol_batch": chol_batch, "inverse": inv,
             "gflop_per_step": stats["flops"] / 1e9}
     if rank == 0:
         print(json.dumps(line))

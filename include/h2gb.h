@@ -534,6 +534,12 @@ h2_status h2_pcg_inverse(h2_ctx* ctx, const h2_matrix* A, const h2_matrix* C, co
  * the accuracy reached). */
 h2_status h2_chol_factor(h2_ctx* ctx, h2_matrix* Z, const h2_options* opt, int64_t* stats);
 
+/* h2_chol_factor of count independent matrices side by side, with the
+ * threads, streams, statistics and failure rules of h2_lr_factor_many;
+ * every result equals h2_chol_factor of that matrix alone. */
+h2_status h2_chol_factor_many(h2_ctx* ctx, h2_matrix* const* Z, int64_t count, const h2_options* opt, int threads,
+                              int64_t* stats);
+
 /* X <- L^-* L^-1 X for a factor from h2_chol_factor (block forward and
  * backward substitution with L and its transpose).  X: DEVICE n x nrhs,
  * column-major, ld ldx, rows in TREE order.  Synchronizes. */

@@ -35,7 +35,7 @@ EXPORTS = [
     "h2_lowrank_update_noalloc", "h2_lowrank_update_sequence", "h2_matvec", "h2_block_to_dense",
     "h2_sequence_waves", "h2_check_reciprocal", "h2_debug_fail_allocation",
     "h2_stats", "h2_build_fem", "h2_lr_factor", "h2_lr_factor_many", "h2_lr_solve", "h2_pcg", "h2_lr_error", "h2_mul", "h2_inverse",
-    "h2_pcg_inverse", "h2_chol_factor", "h2_chol_solve", "h2_pcg_chol", "h2_chol_error",
+    "h2_pcg_inverse", "h2_chol_factor", "h2_chol_solve", "h2_pcg_chol", "h2_chol_error", "h2_chol_factor_many",
 ]
 
 PHASES = ("base_weights", "rfactor", "norms", "weights", "truncate", "reproject", "exact", "bases")
@@ -127,6 +127,7 @@ _sig("h2_chol_factor", _int, _p, _p, C.POINTER(Options), _p)
 _sig("h2_chol_solve", _int, _p, _p, _i64, _p, _i64)
 _sig("h2_pcg_chol", _int, _p, _p, _p, _p, _p, _dbl, _int, _p, _p)
 _sig("h2_chol_error", _int, _p, _p, _p, _p, _int, _p)
+_sig("h2_chol_factor_many", _int, _p, _p, _i64, _p, _int, _p)
 _sig("h2_mul", _int, _p, _dbl, _p, _i64, _p, _i64, _p, _i64, _dbl, _p)
 _sig("h2_matvec", _int, _p, _p, _i64, _dbl, _p, _i64, _dbl, _p, _i64)
 _sig("h2_lowrank_update_sequence", _int, _p, _p, _i64, _p, _int, _p, _p, _dbl, _p)
@@ -538,6 +539,16 @@ def h2_lr_factor_many(ctx, Zs, opt, threads: int = 0):
     arr = (C.c_void_p * len(Zs))(*Zs)
     st = np.zeros(3 * max(len(Zs), 1), np.int64)
     _check(_lib.h2_lr_factor_many(ctx, arr, len(Zs), C.byref(opt), int(threads), _ptr(st)), ctx)
+    return [{"updates": int(st[3 * i]), "products": int(st[3 * i + 1]), "max_rank": int(st[3 * i + 2])}
+            for i in range(len(Zs))]
+
+
+def h2_chol_factor_many(ctx, Zs, opt, threads: int = 0):
+    """h2_chol_factor of independent matrices side by side; returns per-matrix
+    statistics (updates, products, max_rank)."""
+    arr = (C.c_void_p * len(Zs))(*Zs)
+    st = np.zeros(3 * max(len(Zs), 1), np.int64)
+    _check(_lib.h2_chol_factor_many(ctx, arr, len(Zs), C.byref(opt), int(threads), _ptr(st)), ctx)
     return [{"updates": int(st[3 * i]), "products": int(st[3 * i + 1]), "max_rank": int(st[3 * i + 2])}
             for i in range(len(Zs))]
 

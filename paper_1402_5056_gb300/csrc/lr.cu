@@ -1607,62 +1607,77 @@ extern "C" h2_status h2_inverse(h2_ctx* ctx, h2_matrix* A, const h2_options* opt
   return st;
 }
 
+namespace {
+// count independent factorisations side by side: `threads` host threads,
+// each with a stream and context of its own, take the matrices in turn
+using FactorFn = h2_status (*)(h2_ctx*, h2_matrix*, const h2_options*, int64_t*);
+void factor_many(h2_ctx* ctx, h2_matrix* const* Z, int64_t count, const h2_options* opt, int threads,
+                 int64_t* stats, const char* name, FactorFn factor) {
+  check_options(opt);
+  for (int64_t i = 0; i < count; ++i) {
+    H2_REQUIRE(Z[i] != nullptr, std::string(name) + ": matrix missing");
+    H2_REQUIRE(Z[i]->device == ctx->device, std::string(name) + ": matrix on another device");
+    check_square(Z[i]);
+    for (int64_t j = 0; j < i; ++j) H2_REQUIRE(Z[j] != Z[i], std::string(name) + ": a matrix appears twice");
+  }
+  if (count == 0) return;
+  DevGuard g(ctx->device);
+  H2_CUDA(cudaStreamSynchronize(ctx->stream));   // the matrices are ready
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const int64_t nt = std::min<int64_t>(count, threads > 0 ? threads : hw);
+  std::atomic<int64_t> next{0};
+  std::vector<h2_status> st(count, H2_OK);
+  std::vector<std::string> msg(count);
+  const int device = ctx->device;
+  // one host thread per stream and context: the factorisations' launches
+  // are few tasks each (the recursion applies one update at a time), so
+  // independent problems side by side fill the GPU
+  auto worker = [&]() {
+    cudaStream_t s = nullptr;
+    h2_ctx* c = nullptr;
+    h2_status cs = cudaSetDevice(device) == cudaSuccess &&
+                           cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess
+                       ? h2_ctx_create(device, s, &c)
+                       : H2_ECUDA;
+    for (;;) {
+      const int64_t i = next.fetch_add(1);
+      if (i >= count) break;
+      if (cs != H2_OK) {
+        st[i] = cs;
+        msg[i] = std::string(name) + ": no stream or context for a worker";
+        continue;
+      }
+      int64_t one[15] = {};
+      st[i] = factor(c, Z[i], opt, one);
+      if (st[i] != H2_OK) {
+        const char* m = h2_last_error(c);
+        msg[i] = m ? m : "";
+      } else if (stats) {
+        for (int k = 0; k < 3; ++k) stats[3 * i + k] = one[k];
+      }
+    }
+    if (c) h2_ctx_destroy(c);
+    if (s) cudaStreamDestroy(s);
+  };
+  std::vector<std::thread> pool;
+  for (int64_t t = 0; t < nt; ++t) pool.emplace_back(worker);
+  for (std::thread& t : pool) t.join();
+  for (int64_t i = 0; i < count; ++i)
+    if (st[i] != H2_OK) throw Error(st[i], "matrix " + std::to_string(i) + ": " + msg[i]);
+}
+}  // namespace
+
 extern "C" h2_status h2_lr_factor_many(h2_ctx* ctx, h2_matrix* const* Z, int64_t count, const h2_options* opt,
                                        int threads, int64_t* stats) {
   if (!ctx || count < 0 || (count > 0 && !Z) || !opt || threads < 0) return H2_EINVAL;
-  return lr_guard(ctx, [&] {
-    check_options(opt);
-    for (int64_t i = 0; i < count; ++i) {
-      H2_REQUIRE(Z[i] != nullptr, "h2_lr_factor_many: matrix missing");
-      H2_REQUIRE(Z[i]->device == ctx->device, "h2_lr_factor_many: matrix on another device");
-      check_square(Z[i]);
-      for (int64_t j = 0; j < i; ++j) H2_REQUIRE(Z[j] != Z[i], "h2_lr_factor_many: a matrix appears twice");
-    }
-    if (count == 0) return;
-    DevGuard g(ctx->device);
-    H2_CUDA(cudaStreamSynchronize(ctx->stream));   // the matrices are ready
-    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
-    const int64_t nt = std::min<int64_t>(count, threads > 0 ? threads : hw);
-    std::atomic<int64_t> next{0};
-    std::vector<h2_status> st(count, H2_OK);
-    std::vector<std::string> msg(count);
-    const int device = ctx->device;
-    // one host thread per stream and context: the factorisations' launches
-    // are few tasks each (the recursion applies one update at a time), so
-    // independent problems side by side fill the GPU
-    auto worker = [&]() {
-      cudaStream_t s = nullptr;
-      h2_ctx* c = nullptr;
-      h2_status cs = cudaSetDevice(device) == cudaSuccess &&
-                             cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess
-                         ? h2_ctx_create(device, s, &c)
-                         : H2_ECUDA;
-      for (;;) {
-        const int64_t i = next.fetch_add(1);
-        if (i >= count) break;
-        if (cs != H2_OK) {
-          st[i] = cs;
-          msg[i] = "h2_lr_factor_many: no stream or context for a worker";
-          continue;
-        }
-        int64_t one[15] = {};
-        st[i] = h2_lr_factor(c, Z[i], opt, one);
-        if (st[i] != H2_OK) {
-          const char* m = h2_last_error(c);
-          msg[i] = m ? m : "";
-        } else if (stats) {
-          for (int k = 0; k < 3; ++k) stats[3 * i + k] = one[k];
-        }
-      }
-      if (c) h2_ctx_destroy(c);
-      if (s) cudaStreamDestroy(s);
-    };
-    std::vector<std::thread> pool;
-    for (int64_t t = 0; t < nt; ++t) pool.emplace_back(worker);
-    for (std::thread& t : pool) t.join();
-    for (int64_t i = 0; i < count; ++i)
-      if (st[i] != H2_OK) throw Error(st[i], "matrix " + std::to_string(i) + ": " + msg[i]);
-  });
+  return lr_guard(ctx, [&] { factor_many(ctx, Z, count, opt, threads, stats, "h2_lr_factor_many", h2_lr_factor); });
+}
+
+extern "C" h2_status h2_chol_factor_many(h2_ctx* ctx, h2_matrix* const* Z, int64_t count, const h2_options* opt,
+                                         int threads, int64_t* stats) {
+  if (!ctx || count < 0 || (count > 0 && !Z) || !opt || threads < 0) return H2_EINVAL;
+  return lr_guard(ctx,
+                  [&] { factor_many(ctx, Z, count, opt, threads, stats, "h2_chol_factor_many", h2_chol_factor); });
 }
 
 extern "C" h2_status h2_lr_solve(h2_ctx* ctx, const h2_matrix* LR, int64_t nrhs, double* X, int64_t ldx) {

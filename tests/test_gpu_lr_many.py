@@ -1,6 +1,7 @@
-"""h2_lr_factor_many: independent factorisations side by side (batches of
-problems of different sizes).  Each result must be the bits of h2_lr_factor
-of that matrix alone: bases, couplings, nearfield and statistics."""
+"""h2_lr_factor_many and h2_chol_factor_many: independent factorisations
+side by side (batches of problems of different sizes).  Each result must be
+the bits of the factorisation of that matrix alone: bases, couplings,
+nearfield and statistics."""
 import numpy as np
 import pytest
 
@@ -49,6 +50,25 @@ def test_many_equals_one_by_one():
         with pytest.raises(b.H2Error) as e:
             b.h2_lr_factor_many(ctx, [alone[0], alone[0]], opt)
         assert e.value.status == 1
+    finally:
+        for Z in alone + many:
+            b.h2_matrix_free(Z)
+        b.h2_ctx_destroy(ctx)
+
+
+def test_chol_many_equals_one_by_one():
+    """h2_chol_factor_many: the same rule for the Cholesky factorisation."""
+    ctx = b.h2_ctx_create(0, torch.cuda.current_stream().cuda_stream)
+    opt = b.options(eps=1e-4, leaf_size=16)
+    alone = _problems(ctx, opt)
+    many = _problems(ctx, opt)
+    try:
+        want = [b.h2_chol_factor(ctx, Z, opt) for Z in alone]
+        got = b.h2_chol_factor_many(ctx, many, opt, threads=3)
+        for i in range(len(SIZES)):
+            assert got[i] == want[i] and want[i]["updates"] > 0
+            for x, y in zip(_state(ctx, many[i]), _state(ctx, alone[i])):
+                np.testing.assert_array_equal(x, y)
     finally:
         for Z in alone + many:
             b.h2_matrix_free(Z)
