@@ -224,3 +224,34 @@ def test_stats_of_the_structure():
     near = sum(ct.size[bt.row[c]] * ct.size[bt.col[c]] for c in bt.inadmissible)
     assert st["value_bytes"] == 8 * near
     assert st["device_bytes"] == 0   # structure only: no device storage
+
+
+def test_factorisation_entry_points_reject_missing_arguments():
+    """The factorisations, solves and preconditioned CG refuse a missing
+    context, matrix or vector with H2_EINVAL before any device work (no GPU
+    is touched)."""
+    import ctypes as C
+    lib = b._lib
+    pts = synth.grid_points_2d(8)
+    Z = b.h2_matrix_create(None, pts, 8, 2.0, 0.0, 4)
+    opt = b.options(eps=1e-4, leaf_size=8)
+    x = np.zeros(64)
+    try:
+        for name in ("h2_lr_factor", "h2_chol_factor"):
+            f = getattr(lib, name)
+            assert f(None, Z, C.byref(opt), None) == 1
+        arr = (C.c_void_p * 1)(Z)
+        for name in ("h2_lr_factor_many", "h2_chol_factor_many"):
+            f = getattr(lib, name)
+            assert f(None, arr, 1, C.byref(opt), 0, None) == 1
+        for name in ("h2_lr_solve", "h2_chol_solve"):
+            assert getattr(lib, name)(None, Z, 1, x.ctypes.data, 64) == 1
+        it, rr = C.c_int(), C.c_double()
+        for name in ("h2_pcg", "h2_pcg_chol", "h2_pcg_inverse"):
+            assert getattr(lib, name)(None, Z, Z, x.ctypes.data, x.ctypes.data, 1e-10, 10, C.byref(it),
+                                      C.byref(rr)) == 1
+        err = C.c_double()
+        for name in ("h2_lr_error", "h2_chol_error"):
+            assert getattr(lib, name)(None, Z, Z, x.ctypes.data, 5, C.byref(err)) == 1
+    finally:
+        b.h2_matrix_free(Z)
