@@ -144,3 +144,27 @@ def test_chol_power_error_matches_oracle(ctx, factored):
     got = b.h2_chol_error(ctx, A, Z, vd.data_ptr(), 20)
     assert abs(got - want) <= 1e-6 * max(want, 1e-12) + 1e-14, (got, want)
     assert want < 1e-2
+
+
+@pytest.mark.parametrize("N,leaf,dim,M,eps,seed,cap", [(24, 16, 2, 4, 1e-6, 60, 3), (8, 16, 3, 2, 1e-4, 70, 0)],
+                         ids=["24x24_cap3", "3d_8"])
+def test_chol_capped_and_3d_match_oracle(ctx, N, leaf, dim, M, eps, seed, cap):
+    """The rank cap option (reading 6) and a 3D problem (8^3 cells in Kuhn
+    tetrahedra): per block at 1e-10, equal ranks and update counts."""
+    sigma, K, Zo, _ = _problem(N, synth.SEED_BASE + seed, leaf, M, dim)
+    info_o = chol_factor(Zo, eps, rank_cap=cap or None)
+    opt = b.options(eps=eps, leaf_size=leaf, max_rank=cap)
+    Z = b.h2_build_fem(ctx, dim, N, M, sigma, opt)
+    try:
+        info = b.h2_chol_factor(ctx, Z, opt)
+        got = to_oracle(ctx, Z, Zo)
+        if cap:
+            assert info_o["max_rank"] == cap == info["max_rank"]
+        assert list(got.V.rank) == list(Zo.V.rank) and list(got.W.rank) == list(Zo.W.rank)
+        assert info["updates"] == info_o["updates"]
+        R = lower(Zo)
+        bt, tr = Zo.blocks, Zo.V.tree
+        assert_blockwise_dense(np.tril(got.dense()), R, bt, tr, tr, TOL, "Cholesky factor",
+                               floor=1e-12 * np.linalg.norm(R))
+    finally:
+        b.h2_matrix_free(Z)
