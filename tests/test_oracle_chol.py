@@ -15,6 +15,8 @@ Against what the mathematics fixes:
 * at eps = 1e-4 the factor reproduces A to O(eps), L L^* is symmetric
   positive definite, and CG preconditioned by it converges in a few steps
   (Table 1: m = 3 at the paper's accuracies).
+* without truncation the Cholesky factor is the LR's unit lower factor
+  scaled by the square roots of the LR's pivots (A = L U with U = D L^*).
 """
 import numpy as np
 import pytest
@@ -125,3 +127,21 @@ def test_chol_solve():
     B = np.random.default_rng(3).standard_normal((A.shape[0], 2))
     X = chol_solve(Z, B)
     assert np.linalg.norm(A @ X - B) <= 1e-10 * np.linalg.norm(B)
+
+
+def test_chol_is_the_scaled_lr_without_truncation():
+    """For a symmetric positive definite A, Doolittle's A = L U has
+    U = D L^*, so the Cholesky factor is L D^(1/2): the two oracle
+    factorisations, run without truncation, agree to rounding."""
+    from oracle.lr import lr_factor
+    Z1, A = _fem(16, 8, seed=13)
+    Z2 = Z1.copy()
+    chol_factor(Z1, 0.0, cap=None)
+    lr_factor(Z2, 0.0, cap=None)
+    D = Z2.dense()
+    n = D.shape[0]
+    Ld = np.tril(D, -1) + np.eye(n)
+    d = np.diag(D)
+    assert (d > 0).all()
+    Lc = lower(Z1)
+    assert np.linalg.norm(Lc - Ld * np.sqrt(d)) <= 1e-12 * np.linalg.norm(Lc)
