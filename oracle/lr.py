@@ -42,7 +42,8 @@ Readings of what the paper leaves open (also listed in the design notes):
 4. Forward substitution on an admissible leaf Y = V_t S W_s^*: X =
    (L^-1 V_t S) W_s^*, stored by setting S to zero and adding
    (L^-1 V_t S) W_s^* with a local update; X R = Y likewise with
-   V_t (R^-* W_s S^*)^*.
+   V_t (R^-* W_s S^*)^*.  A block whose basis has rank 0 on either side is
+   zero; it stays zero and takes no update.
 5. An update of rank u is applied in consecutive column groups of at most
    u_max columns (u_max = 32 minus the largest rank among the clusters of
    both subtrees, at least 1 and at most 31), each group one local update;
@@ -344,6 +345,8 @@ def _lsolve(C: _Ctx, d, x):
         return
     t, s = bt.row[x], bt.col[x]
     if bt.kind[x] == BlockTree.ADM:
+        if Z.S[x].size == 0:          # a rank-0 basis: the block is zero and stays zero
+            return
         Xh = lsolve_dense(Z, d, Z.V.dense(t) @ Z.S[x])        # reading 4
         Ws = Z.W.dense(s)
         Z.S[x] = np.zeros_like(Z.S[x])
@@ -368,6 +371,8 @@ def _rsolve(C: _Ctx, d, x):
         return
     t, s = bt.row[x], bt.col[x]
     if bt.kind[x] == BlockTree.ADM:
+        if Z.S[x].size == 0:          # a rank-0 basis: the block is zero and stays zero
+            return
         Bh = rsolve_dense(Z, d, Z.S[x] @ Z.W.dense(s).T).T    # reading 4
         Vt = Z.V.dense(t)
         Z.S[x] = np.zeros_like(Z.S[x])
