@@ -251,6 +251,9 @@ CHOL_MUTATIONS = {
         "        pass\n"),
     "transposed admissible factor with its coupling not transposed": (
         'return ("lr", alpha * (Xt @ Z.S[yh].T), Z.V.dense(r))', 'return ("lr", alpha * (Xt @ Z.S[yh]), Z.V.dense(r))'),
+    "diagonal target computing the blocks above the diagonal instead of below": (
+        "tree.offset[t1] < tree.offset[r1]", "tree.offset[t1] > tree.offset[r1]"),
+    "leaf Cholesky without the square root of the pivot": ("A[k, k] = np.sqrt(d)", "A[k, k] = d"),
     "backward solve reading the upper block instead of the factor's transpose": (
         "Y1 = Y[:n1] - Z.block_dense(_son(bt, d, t2, t1)).T @ X2",
         "Y1 = Y[:n1] - Z.block_dense(_son(bt, d, t1, t2)) @ X2"),
